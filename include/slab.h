@@ -1,0 +1,162 @@
+/*
+ * slab.h -- C ABI of the GB300 slab factor+solve library (libslab.so).
+ *
+ * The library factors and solves the finite-difference system A u = f of a
+ * second-order elliptic PDE on the unit square/cube with homogeneous Dirichlet
+ * data, by the two-level slab method of Yesypenko & Martinsson (SlabLU):
+ *   Stage 1 (Sec. 3, Algorithm 3): eliminate the interior of every slab of
+ *     width b, giving the block-tridiagonal reduced matrix T on the slab
+ *     interfaces (eqs. T11-T35), formed here exactly and densely;
+ *   Stage 2 (Sec. 4, Algorithm 1): block (Cholesky) LU sweep over T;
+ *   Solve (Algorithm 4): reduced load f~ (eqs. f1-f5), sweeping solve
+ *     (Algorithm 2), interior back-solve (eq. usol_even),
+ * with an FP64 stencil residual and iterative refinement on top of a factor
+ * kept in FP32 or FP64.
+ *
+ * Operator (Sec. 2.1 eq. "discretiation" with the sign of eq. "var_helm"):
+ *   (A u)_P = n^2 sum_{faces P~Q} k_PQ (u_P - u_Q) + q_P u_P,   u = 0 on the boundary,
+ *   k_PQ = (kappa_P + kappa_Q)/2 (DIFFUSION) or 1 (POISSON, HELMHOLTZ),
+ *   q_P = 0, or -(omega / c_P)^2 for HELMHOLTZ.
+ *
+ * Conventions shared by every entry point
+ *   - Node fields (kappa, c) have (n+1)^d FP64 entries, C order [z][y][x]
+ *     (x fastest), boundary nodes included.
+ *   - Vectors (f, u, r, lambda) have k blocks of (n-1)^d FP64 entries over the
+ *     interior nodes, layout [k][z][y][x], contiguous.
+ *   - Interface vectors (f~, u~) have k blocks of N_I*(n-1)^(d-1) FP64 entries,
+ *     layout [k][q][j]: interface q = 0..N_I-1 is the grid plane x = (q+1) b,
+ *     its nodes j ordered by y (then z), y fastest.
+ *   - Unless a parameter says "host", every pointer is a DEVICE pointer owned
+ *     by the caller.  With k == 0 right-hand sides a call does nothing and
+ *     its vector pointers may be NULL.  Calls are asynchronous on opts.stream except where a
+ *     host output is requested; those synchronise that stream before return.
+ *   - The handle owns all factor memory; release it with slab_destroy().
+ *   - No C++ exception crosses the ABI.  Errors are returned as slab_status;
+ *     the first CUDA error is also latched in the handle (slab_last_error).
+ *   - A handle may be used by one host thread at a time.
+ */
+#ifndef SLAB_H
+#define SLAB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SLAB_OK = 0,
+    SLAB_EINVAL = 1,        /* bad argument: b does not divide n, b < 2, k < 0, NULL pointer ... */
+    SLAB_ENOMEM = 2,        /* device allocation failed */
+    SLAB_ESINGULAR = 3,     /* non-positive / zero pivot in a factorisation */
+    SLAB_ENOCONV = 4,       /* refinement did not reach opts.rtol within opts.max_refine steps */
+    SLAB_ETIMEOUT = 5,      /* a bounded device-side wait gave up */
+    SLAB_ECUDA = 6,         /* a CUDA runtime call failed */
+    SLAB_EUNSUPPORTED = 7   /* valid request this build does not implement */
+} slab_status;
+
+typedef enum { SLAB_POISSON = 0, SLAB_DIFFUSION = 1, SLAB_HELMHOLTZ = 2 } slab_kind;
+
+typedef enum {
+    SLAB_PREC_FP64 = 0,     /* factor and solves in FP64 (the plain FP64 GPU path) */
+    SLAB_PREC_FP32 = 1      /* factor and solves in FP32; FP64 residual + refinement */
+} slab_precision;
+
+typedef struct {
+    int dim;                /* 2 or 3 */
+    int n;                  /* grid intervals per side, h = 1/n, (n-1)^d unknowns */
+} slab_grid;
+
+typedef struct {
+    int kind;               /* slab_kind */
+    const double* kappa;    /* device, (n+1)^d nodes; DIFFUSION only (NULL otherwise) */
+    const double* c;        /* device, (n+1)^d nodes; HELMHOLTZ only (NULL otherwise) */
+    double omega;           /* HELMHOLTZ angular frequency */
+} slab_coeffs;
+
+typedef struct {
+    int factor_prec;        /* slab_precision */
+    int pivot;              /* reserved: 0 */
+    double rtol;            /* refinement target for max_k ||f - A u||_2 / ||f||_2 */
+    int max_refine;         /* refinement steps after the first solve (0: a single pass) */
+    int krylov;             /* reserved: 0 */
+    void* stream;           /* cudaStream_t all work is ordered on (NULL: legacy default) */
+} slab_opts;
+
+typedef struct slab_handle slab_handle;
+
+/* Fill opts with the defaults: FP32 factor, rtol 1e-10, max_refine 30, default stream. */
+void slab_default_opts(slab_opts* opts);
+
+/*
+ * Factor A (Algorithm 3): Stage 1 for every slab in parallel, assembly of the
+ * reduced matrix T, Stage 2 sweep (Algorithm 1).  b is the interface spacing:
+ * interfaces at x = q b, q = 1..n/b-1, slab interiors b-1 nodes wide.
+ * Requires b >= 2 and n % b == 0, 2 <= b <= 33, n/b >= 2 (SLAB_EINVAL otherwise);
+ * dim == 2 (SLAB_EUNSUPPORTED otherwise); SPD kinds (SLAB_EUNSUPPORTED for
+ * HELMHOLTZ).  kappa/c are read during the call only.  On success *out is a
+ * new handle.  Synchronises opts->stream (returns after the factor is built).
+ */
+slab_status slab_factor(const slab_grid* grid, const slab_coeffs* coeffs, int b,
+                        const slab_opts* opts, slab_handle** out);
+
+/*
+ * Solve A u = f for k right-hand sides (Algorithm 4 + iterative refinement).
+ * f, u: device, [k][(n-1)^d]; u is overwritten.  relres_out: HOST, k entries
+ * (may be NULL) receiving ||f - A u||_2/||f||_2; iters_out: HOST (may be NULL)
+ * receiving the number of refinement steps taken.  Returns SLAB_ENOCONV when
+ * max_refine steps did not reach rtol (u then holds the last iterate).
+ */
+slab_status slab_solve(slab_handle* h, const double* f, double* u, int k,
+                       double* relres_out, int* iters_out);
+
+/* r = f - A u in FP64 for k vectors (stencil kernel; the eq. "discretiation" operator). */
+slab_status slab_apply_residual(slab_handle* h, const double* u, const double* f, double* r, int k);
+
+/* y = A x in FP64 for k vectors. */
+slab_status slab_apply(slab_handle* h, const double* x, double* y, int k);
+
+/*
+ * Adjoint solve and coefficient gradient (DIFFUSION).  Given dL/du (device,
+ * [k][(n-1)^d]) and the state u, solves A^T lambda = dL/du with the stored
+ * factors (A is symmetric here) and, if dLdkappa != NULL, accumulates into it
+ * (device, (n+1)^d, k gradients summed) dL/dkappa_p = -lambda^T (dA/dkappa_p) u.
+ */
+slab_status slab_adjoint(slab_handle* h, const double* dLdu, const double* u, double* lambda,
+                         double* dLdkappa, int k);
+
+/* --- phase-level entry points (one step of Algorithm 4 each, no refinement) --- */
+
+/* Reduced load on the interfaces, eqs. f1-f5: ftilde = f_I - A_IJ A_JJ^-1 f_J. */
+slab_status slab_reduced_rhs(slab_handle* h, const double* f, double* ftilde, int k);
+
+/* Algorithm 2 with the Stage-2 factors: utilde = T^-1 ftilde. */
+slab_status slab_interface_solve(slab_handle* h, const double* ftilde, double* utilde, int k);
+
+/* Eq. usol_even: u_J = A_JJ^-1 (f_J - A_JI utilde) per slab; u_I = utilde.  Writes all of u. */
+slab_status slab_interior_solve(slab_handle* h, const double* f, const double* utilde, double* u,
+                                int k);
+
+/*
+ * Copy one (n-1)^(d-1) square block of the reduced matrix T (as assembled,
+ * before Stage 2) to out (HOST, row-major, FP64): which = 0 gives T_qq, which
+ * = 1 gives T_{q,q+1} (q = 0..N_I-2).  Synchronises the stream.
+ */
+slab_status slab_get_T_block(slab_handle* h, int which, int q, double* out);
+
+/* Sizes: unknowns (n-1)^d, interface size (n-1)^(d-1), number of interfaces N_I. */
+slab_status slab_sizes(const slab_handle* h, int64_t* unknowns, int64_t* iface_size, int* n_ifaces);
+
+/* Bytes of device memory the handle holds. */
+int64_t slab_device_bytes(const slab_handle* h);
+
+/* Latched first error of the handle (SLAB_OK if none). */
+slab_status slab_last_error(const slab_handle* h);
+
+void slab_destroy(slab_handle* h);
+const char* slab_strerror(slab_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SLAB_H */

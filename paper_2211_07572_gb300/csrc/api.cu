@@ -1,0 +1,419 @@
+// C ABI of the slab factor+solve library: validation, device memory plan,
+// orchestration of the phases of Algorithms 3 and 4, and FP64 iterative
+// refinement on top of the (FP32 or FP64) factor.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "slab_internal.cuh"
+
+slab_status slab_cuda_check(slab_handle* h, cudaError_t e) {
+    (void)e;
+    if (h && h->err == SLAB_OK) h->err = SLAB_ECUDA;
+    return SLAB_ECUDA;
+}
+
+namespace {
+
+slab_status dalloc(slab_handle* h, void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) return SLAB_OK;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return SLAB_ENOMEM;
+    }
+    h->dev_bytes += (int64_t)bytes;
+    return SLAB_OK;
+}
+
+void dfree(void*& p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+void free_workspace(slab_handle* h) {
+    dfree(h->wYv); dfree(h->wGtb); dfree(h->wXs); dfree(h->wFi); dfree(h->wX); dfree(h->wZ);
+    dfree(h->wVp);
+    void* r = h->wR; dfree(r); h->wR = nullptr;
+    void* q = h->wNrm; dfree(q); h->wNrm = nullptr;
+    h->kcap = 0;
+    h->rcap = 0;
+}
+
+#define TRY(x)                            \
+    do {                                  \
+        slab_status _s = (x);             \
+        if (_s != SLAB_OK) return _s;     \
+    } while (0)
+
+// Solve workspace for up to kc right-hand sides per pass and k total (residual buffer).
+slab_status ensure_workspace(slab_handle* h, int k) {
+    const int kc = k < tree_kmax() ? k : tree_kmax();
+    const TreeDims& d = h->td;
+    const int64_t N = (int64_t)d.s * d.s;
+    static_assert(sizeof(double) == 8, "");
+    if (h->kcap < kc) {
+        const int64_t nodes = (int64_t)d.NS * (d.s + 1);
+        dfree(h->wYv); dfree(h->wGtb); dfree(h->wXs); dfree(h->wFi); dfree(h->wX); dfree(h->wZ);
+        h->kcap = 0;
+        TRY(dalloc(h, &h->wYv, nodes * d.m * kc * h->rsz));
+        TRY(dalloc(h, &h->wGtb, nodes * 2 * d.m * kc * h->rsz));
+        TRY(dalloc(h, &h->wXs, nodes * d.m * kc * h->rsz));
+        TRY(dalloc(h, &h->wFi, (int64_t)d.NS * 2 * d.s_pad * kc * h->rsz));
+        TRY(dalloc(h, &h->wX, (int64_t)d.NI * d.s_pad * kc * h->rsz));
+        TRY(dalloc(h, &h->wZ, (int64_t)d.NI * d.s_pad * kc * h->rsz));
+        h->kcap = kc;
+    }
+    return SLAB_OK;
+}
+
+// FP64 residual buffer and norms for k right-hand sides.
+slab_status ensure_resid(slab_handle* h, int k) {
+    const int64_t N = (int64_t)h->td.s * h->td.s;
+    if (h->rcap < k) {
+        void* r = h->wR; dfree(r); h->wR = nullptr;
+        void* q = h->wNrm; dfree(q); h->wNrm = nullptr;
+        h->rcap = 0;
+        TRY(dalloc(h, &r, (size_t)k * N * sizeof(double)));
+        h->wR = (double*)r;
+        TRY(dalloc(h, &q, (size_t)2 * k * sizeof(double)));
+        h->wNrm = (double*)q;
+        h->rcap = k;
+    }
+    return SLAB_OK;
+}
+
+template <typename T>
+slab_status solve_pass(slab_handle* h, const double* F, double fscale, double* U, int accumulate, int k) {
+    const int kc = h->kcap;
+    for (int r0 = 0; r0 < k; r0 += kc) {
+        const int K = (k - r0) < kc ? (k - r0) : kc;
+        TRY(tree_up_gather<T>(h, F, fscale, r0, K));
+        TRY(sweep_solve<T>(h, K));
+        TRY(tree_down_scatter<T>(h, U, accumulate, r0, K));
+    }
+    return SLAB_OK;
+}
+
+slab_status pass(slab_handle* h, const double* F, double fscale, double* U, int accumulate, int k) {
+    return h->prec == SLAB_PREC_FP64 ? solve_pass<double>(h, F, fscale, U, accumulate, k)
+                                     : solve_pass<float>(h, F, fscale, U, accumulate, k);
+}
+
+slab_status sync_status(slab_handle* h) {
+    SLAB_CK(h, cudaStreamSynchronize(h->stream));
+    unsigned st = 0;
+    SLAB_CK(h, cudaMemcpy(&st, h->dstatus, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (st & SLAB_DEV_NOTSPD) {
+        if (h->err == SLAB_OK) h->err = SLAB_ESINGULAR;
+        return SLAB_ESINGULAR;
+    }
+    return SLAB_OK;
+}
+
+template <typename T>
+slab_status factor_impl(slab_handle* h) {
+    TRY(tree_factor<T>(h));
+    TRY(assemble_T<T>(h));
+    TRY(sweep_factor<T>(h));
+    return SLAB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void slab_default_opts(slab_opts* o) {
+    if (!o) return;
+    o->factor_prec = SLAB_PREC_FP32;
+    o->pivot = 0;
+    o->rtol = 1e-10;
+    o->max_refine = 30;
+    o->krylov = 0;
+    o->stream = nullptr;
+}
+
+const char* slab_strerror(slab_status s) {
+    switch (s) {
+        case SLAB_OK: return "ok";
+        case SLAB_EINVAL: return "invalid argument";
+        case SLAB_ENOMEM: return "device allocation failed";
+        case SLAB_ESINGULAR: return "non-positive or zero pivot in a factorisation";
+        case SLAB_ENOCONV: return "iterative refinement did not reach the tolerance";
+        case SLAB_ETIMEOUT: return "bounded device wait gave up";
+        case SLAB_ECUDA: return "CUDA runtime error";
+        case SLAB_EUNSUPPORTED: return "unsupported configuration";
+    }
+    return "unknown status";
+}
+
+void slab_destroy(slab_handle* h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    free_workspace(h);
+    void* p;
+    p = h->AX; dfree(p); p = h->AY; dfree(p); p = h->DG; dfree(p); p = h->kappa; dfree(p);
+    dfree(h->tLinv); dfree(h->tZtb); dfree(h->tRtb); dfree(h->tZI); dfree(h->tRI);
+    dfree(h->Tb); dfree(h->To); dfree(h->Linv); dfree(h->Y); dfree(h->Swork);
+    p = h->dstatus; dfree(p);
+    delete h;
+}
+
+slab_status slab_factor(const slab_grid* grid, const slab_coeffs* co, int b, const slab_opts* opts,
+                        slab_handle** out) {
+    if (!grid || !co || !out) return SLAB_EINVAL;
+    *out = nullptr;
+    slab_opts o;
+    if (opts) o = *opts;
+    else slab_default_opts(&o);
+    const int n = grid->n;
+    if (grid->dim != 2 && grid->dim != 3) return SLAB_EINVAL;
+    if (b < 2 || n < 4 || n % b != 0 || n / b < 2) return SLAB_EINVAL;
+    if (co->kind < SLAB_POISSON || co->kind > SLAB_HELMHOLTZ) return SLAB_EINVAL;
+    if (co->kind == SLAB_DIFFUSION && !co->kappa) return SLAB_EINVAL;
+    if (co->kind == SLAB_HELMHOLTZ && !co->c) return SLAB_EINVAL;
+    if (o.factor_prec != SLAB_PREC_FP32 && o.factor_prec != SLAB_PREC_FP64) return SLAB_EINVAL;
+    if (grid->dim != 2) return SLAB_EUNSUPPORTED;
+    if (b - 1 > SLAB_MAXM) return SLAB_EUNSUPPORTED;
+    if (co->kind == SLAB_HELMHOLTZ) return SLAB_EUNSUPPORTED;
+
+    slab_handle* h = new (std::nothrow) slab_handle();
+    if (!h) return SLAB_ENOMEM;
+    std::memset(h, 0, sizeof(*h));
+    h->dim = grid->dim; h->n = n; h->b = b; h->kind = co->kind; h->omega = co->omega;
+    h->prec = o.factor_prec;
+    h->rsz = h->prec == SLAB_PREC_FP64 ? 8 : 4;
+    h->stream = (cudaStream_t)o.stream;
+    h->rtol = o.rtol;
+    h->max_refine = o.max_refine;
+    TreeDims& d = h->td;
+    d.s = n - 1;
+    d.s_pad = (d.s + SLAB_TILE - 1) / SLAB_TILE * SLAB_TILE;
+    d.m = b - 1;
+    d.H = tree_height_count(d.s);
+    d.NS = n / b;
+    d.NI = d.NS - 1;
+    d.b = b;
+    d.n = n;
+    h->nt = d.s_pad / SLAB_TILE;
+
+    slab_status st = SLAB_OK;
+    const size_t nodes2 = (size_t)(n + 1) * (n + 1);
+    const size_t R = h->rsz;
+    const int64_t tn = (int64_t)d.NS * (d.s + 1);
+    const int64_t blk = (int64_t)d.s_pad * d.s_pad;
+    void* p;
+#define ALLOC(field, bytes)                             \
+    do {                                                \
+        st = dalloc(h, &p, (bytes));                    \
+        if (st) { slab_destroy(h); return st; }         \
+        field = decltype(field)(p);                     \
+    } while (0)
+    ALLOC(h->AX, nodes2 * sizeof(double));
+    ALLOC(h->AY, nodes2 * sizeof(double));
+    ALLOC(h->DG, nodes2 * sizeof(double));
+    if (co->kind == SLAB_DIFFUSION) ALLOC(h->kappa, nodes2 * sizeof(double));
+    ALLOC(h->tLinv, tn * d.m * d.m * R);
+    ALLOC(h->tZtb, tn * 2 * d.m * d.m * R);
+    ALLOC(h->tRtb, tn * 4 * d.m * d.m * R);
+    ALLOC(h->tZI, (int64_t)d.NS * d.H * 2 * d.m * d.s_pad * R);
+    ALLOC(h->tRI, (int64_t)d.NS * d.H * 4 * d.m * d.s_pad * R);
+    ALLOC(h->Tb, d.NI * blk * R);
+    ALLOC(h->To, (d.NI - 1) * blk * R);
+    ALLOC(h->Linv, d.NI * blk * R);
+    ALLOC(h->Y, (d.NI - 1) * blk * R);
+    ALLOC(h->Swork, blk * R);
+    ALLOC(h->dstatus, sizeof(unsigned));
+#undef ALLOC
+#define CK(call)                                                               \
+    do {                                                                       \
+        if ((call) != cudaSuccess) { cudaGetLastError(); slab_destroy(h); return SLAB_ECUDA; } \
+    } while (0)
+    CK(cudaMemsetAsync(h->dstatus, 0, sizeof(unsigned), h->stream));
+    CK(cudaMemsetAsync(h->tZI, 0, (size_t)d.NS * d.H * 2 * d.m * d.s_pad * R, h->stream));
+    CK(cudaMemsetAsync(h->tRI, 0, (size_t)d.NS * d.H * 4 * d.m * d.s_pad * R, h->stream));
+    if (h->kappa)
+        CK(cudaMemcpyAsync(h->kappa, co->kappa, nodes2 * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+#undef CK
+    st = launch_coefficients(h, co->kappa, co->c);
+    if (!st) st = h->prec == SLAB_PREC_FP64 ? factor_impl<double>(h) : factor_impl<float>(h);
+    if (!st) st = sync_status(h);
+    if (st) {
+        slab_destroy(h);
+        return st;
+    }
+    *out = h;
+    return SLAB_OK;
+}
+
+slab_status slab_apply_residual(slab_handle* h, const double* u, const double* f, double* r, int k) {
+    if (!h || k < 0) return SLAB_EINVAL;
+    if (k == 0) return SLAB_OK;
+    if (!u || !f || !r) return SLAB_EINVAL;
+    return launch_residual(h, u, f, r, k, nullptr, nullptr);
+}
+
+slab_status slab_apply(slab_handle* h, const double* x, double* y, int k) {
+    if (!h || k < 0) return SLAB_EINVAL;
+    if (k == 0) return SLAB_OK;
+    if (!x || !y) return SLAB_EINVAL;
+    return launch_apply(h, x, y, k);
+}
+
+slab_status slab_solve(slab_handle* h, const double* f, double* u, int k, double* relres_out, int* iters_out) {
+    if (!h || k < 0) return SLAB_EINVAL;
+    if (k == 0) {
+        if (iters_out) *iters_out = 0;
+        return SLAB_OK;
+    }
+    if (!f || !u) return SLAB_EINVAL;
+    TRY(ensure_workspace(h, k));
+    const double h2 = 1.0 / ((double)h->n * (double)h->n);
+    TRY(pass(h, f, h2, u, 0, k));
+    int it = 0;
+    slab_status result = SLAB_OK;
+    if (h->max_refine > 0 || relres_out) {
+        TRY(ensure_resid(h, k));
+        std::vector<double> nrm(2 * (size_t)k);
+        double prev = -1.0;
+        int stall = 0;
+        for (;;) {
+            SLAB_CK(h, cudaMemsetAsync(h->wNrm, 0, 2 * k * sizeof(double), h->stream));
+            TRY(launch_residual(h, u, f, h->wR, k, h->wNrm, h->wNrm + k));
+            SLAB_CK(h, cudaMemcpyAsync(nrm.data(), h->wNrm, 2 * k * sizeof(double), cudaMemcpyDeviceToHost,
+                                       h->stream));
+            SLAB_CK(h, cudaStreamSynchronize(h->stream));
+            double worst = 0.0;
+            for (int q = 0; q < k; ++q) {
+                const double rr = nrm[q] > 0 ? std::sqrt(nrm[q] / (nrm[k + q] > 0 ? nrm[k + q] : 1.0)) : 0.0;
+                if (relres_out) relres_out[q] = rr;
+                if (!(rr <= worst)) worst = rr;
+            }
+            if (worst <= h->rtol) break;
+            // stagnation: two consecutive steps without halving the worst residual
+            stall = (prev > 0.0 && worst > 0.5 * prev) ? stall + 1 : 0;
+            prev = worst;
+            if (it >= h->max_refine || stall >= 2) {
+                result = h->max_refine > 0 ? SLAB_ENOCONV : SLAB_OK;
+                break;
+            }
+            TRY(pass(h, h->wR, h2, u, 1, k));
+            ++it;
+        }
+    }
+    if (iters_out) *iters_out = it;
+    return result;
+}
+
+slab_status slab_adjoint(slab_handle* h, const double* dLdu, const double* u, double* lambda, double* dLdkappa,
+                         int k) {
+    if (!h || k < 0) return SLAB_EINVAL;
+    if (k == 0) return SLAB_OK;
+    if (!dLdu || !lambda) return SLAB_EINVAL;
+    if (dLdkappa && (h->kind != SLAB_DIFFUSION || !u)) return SLAB_EINVAL;
+    // every supported operator is symmetric, so A^T lambda = dL/du is solved with the same factors
+    slab_status st = slab_solve(h, dLdu, lambda, k, nullptr, nullptr);
+    if (st != SLAB_OK && st != SLAB_ENOCONV) return st;
+    if (dLdkappa) TRY(launch_kappa_gradient(h, u, lambda, dLdkappa, k));
+    return st;
+}
+
+slab_status slab_reduced_rhs(slab_handle* h, const double* f, double* ftilde, int k) {
+    if (!h || k < 0) return SLAB_EINVAL;
+    if (k == 0) return SLAB_OK;
+    if (!f || !ftilde) return SLAB_EINVAL;
+    TRY(ensure_workspace(h, k));
+    const double h2 = 1.0 / ((double)h->n * (double)h->n);
+    for (int r0 = 0; r0 < k; r0 += h->kcap) {
+        const int K = (k - r0) < h->kcap ? (k - r0) : h->kcap;
+        if (h->prec == SLAB_PREC_FP64) {
+            TRY(tree_up_gather<double>(h, f, h2, r0, K));
+            TRY(export_ftilde_part<double>(h, ftilde, 1.0 / h2, r0, K));
+        } else {
+            TRY(tree_up_gather<float>(h, f, h2, r0, K));
+            TRY(export_ftilde_part<float>(h, ftilde, 1.0 / h2, r0, K));
+        }
+    }
+    return SLAB_OK;
+}
+
+slab_status slab_interface_solve(slab_handle* h, const double* ftilde, double* utilde, int k) {
+    if (!h || k < 0) return SLAB_EINVAL;
+    if (k == 0) return SLAB_OK;
+    if (!ftilde || !utilde) return SLAB_EINVAL;
+    TRY(ensure_workspace(h, k));
+    const double h2 = 1.0 / ((double)h->n * (double)h->n);
+    for (int r0 = 0; r0 < k; r0 += h->kcap) {
+        const int K = (k - r0) < h->kcap ? (k - r0) : h->kcap;
+        if (h->prec == SLAB_PREC_FP64) {
+            TRY(import_utilde_part<double>(h, ftilde, r0, K));
+            TRY(sweep_solve<double>(h, K));
+            TRY(export_ftilde_part<double>(h, utilde, h2, r0, K));
+        } else {
+            TRY(import_utilde_part<float>(h, ftilde, r0, K));
+            TRY(sweep_solve<float>(h, K));
+            TRY(export_ftilde_part<float>(h, utilde, h2, r0, K));
+        }
+    }
+    return SLAB_OK;
+}
+
+slab_status slab_interior_solve(slab_handle* h, const double* f, const double* utilde, double* u, int k) {
+    if (!h || k < 0) return SLAB_EINVAL;
+    if (k == 0) return SLAB_OK;
+    if (!f || !utilde || !u) return SLAB_EINVAL;
+    TRY(ensure_workspace(h, k));
+    const double h2 = 1.0 / ((double)h->n * (double)h->n);
+    for (int r0 = 0; r0 < k; r0 += h->kcap) {
+        const int K = (k - r0) < h->kcap ? (k - r0) : h->kcap;
+        if (h->prec == SLAB_PREC_FP64) {
+            TRY(tree_up_gather<double>(h, f, h2, r0, K));
+            TRY(import_utilde_part<double>(h, utilde, r0, K));
+            TRY(tree_down_scatter<double>(h, u, 0, r0, K));
+        } else {
+            TRY(tree_up_gather<float>(h, f, h2, r0, K));
+            TRY(import_utilde_part<float>(h, utilde, r0, K));
+            TRY(tree_down_scatter<float>(h, u, 0, r0, K));
+        }
+    }
+    return SLAB_OK;
+}
+
+slab_status slab_get_T_block(slab_handle* h, int which, int q, double* out) {
+    if (!h || !out || which < 0 || which > 1) return SLAB_EINVAL;
+    const TreeDims& d = h->td;
+    if (q < 0 || q >= (which == 0 ? d.NI : d.NI - 1)) return SLAB_EINVAL;
+    const int64_t blk = (int64_t)d.s_pad * d.s_pad;
+    const unsigned char* base = (const unsigned char*)(which == 0 ? h->Tb : h->To) + q * blk * h->rsz;
+    std::vector<unsigned char> tmp((size_t)blk * h->rsz);
+    SLAB_CK(h, cudaMemcpyAsync(tmp.data(), base, tmp.size(), cudaMemcpyDeviceToHost, h->stream));
+    SLAB_CK(h, cudaStreamSynchronize(h->stream));
+    const double sc = (double)h->n * (double)h->n;
+    for (int i = 0; i < d.s; ++i)
+        for (int j = 0; j < d.s; ++j) {
+            const int64_t e = (int64_t)i * d.s_pad + j;
+            const double v = h->rsz == 8 ? ((const double*)tmp.data())[e] : (double)((const float*)tmp.data())[e];
+            out[(int64_t)i * d.s + j] = sc * v;
+        }
+    return SLAB_OK;
+}
+
+slab_status slab_sizes(const slab_handle* h, int64_t* unknowns, int64_t* iface_size, int* n_ifaces) {
+    if (!h) return SLAB_EINVAL;
+    int64_t N = 1;
+    for (int i = 0; i < h->dim; ++i) N *= h->n - 1;
+    if (unknowns) *unknowns = N;
+    if (iface_size) *iface_size = N / (h->n - 1);
+    if (n_ifaces) *n_ifaces = h->td.NI;
+    return SLAB_OK;
+}
+
+int64_t slab_device_bytes(const slab_handle* h) { return h ? h->dev_bytes : 0; }
+
+slab_status slab_last_error(const slab_handle* h) { return h ? h->err : SLAB_EINVAL; }
+
+}  // extern "C"

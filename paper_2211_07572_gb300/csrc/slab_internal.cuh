@@ -1,0 +1,140 @@
+// Internal declarations of the slab factor+solve library (CUDA, sm_103a).
+//
+// Internal operator scaling: all factor data describe Ahat = h^2 A, so the
+// stencil entries are O(kappa) and the right-hand sides are h^2 f.
+//
+// Geometry (2-D).  Rows y = 1..s (s = n-1).  Slab t (0-based, t < NS = n/b)
+// holds the interior columns x = t b + 1 .. t b + m (m = b-1); interface q
+// (0-based, q < NI = NS-1) is the column x = (q+1) b, the right interface of
+// slab q and the left interface of slab q+1.
+//
+// Slab-interior elimination order: the rows of a slab are eliminated along a
+// binary "ruler" tree -- row c has height k = ctz(c); node c owns the segment
+// [c - 2^k + 1, min(s, c + 2^k - 1)] and is eliminated after its children
+// (cyclic reduction along y).  Eliminating node c condenses its segment onto
+// the row above the segment ("top"), the row below ("bot") and the interface
+// nodes of the segment's rows on both slab sides.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "slab.h"
+
+#define SLAB_TILE 64
+#define SLAB_MAXM 32          // largest slab interior width handled by the 2-D tree kernels
+
+// Device-side status word bits (set by kernels, read by the host after a phase).
+#define SLAB_DEV_NOTSPD 1u    // a Cholesky pivot was <= 0 or not finite
+
+struct TreeDims {
+    int s;        // rows per slab (= interface size in 2-D)
+    int s_pad;    // s rounded up to SLAB_TILE
+    int m;        // slab interior width
+    int H;        // tree heights 0..H-1
+    int NS, NI;   // slabs, interfaces
+    int b, n;
+};
+
+struct slab_handle {
+    int dim, n, b, kind;
+    double omega;
+    int prec;                 // slab_precision
+    size_t rsz;               // bytes of the factor scalar
+    TreeDims td;
+    int nt;                   // tiles per interface block (s_pad / 64)
+    cudaStream_t stream;
+    double rtol;
+    int max_refine;
+
+    // coefficient arrays over the (n+1)^2 nodes, h^2-scaled, FP64
+    double* AX;               // AX[y][x]: face (x,y)-(x+1,y)
+    double* AY;               // AY[y][x]: face (x,y)-(x,y+1)
+    double* DG;               // DG[y][x]: diagonal of Ahat at (x,y)
+    double* kappa;            // copy of the node coefficient (DIFFUSION), for the gradient
+
+    // Stage-1 factors (scalar = float or double)
+    void* tLinv;              // [NS][s+1][m*m]   inverse Cholesky factor of each separator row
+    void* tZtb;               // [NS][s+1][m*2m]  Z = Linv B for the top/bot rows
+    void* tRtb;               // [NS][s+1][2m*2m] condensed top/bot x top/bot block
+    void* tZI;                // [NS][H][2][m][s_pad]  Z for interface nodes, per height
+    void* tRI;                // [NS][H][2][2][m][s_pad] condensed top/bot x interface rows
+
+    // Stage-2 data
+    void* Tb;                 // [NI][s_pad][s_pad]  T_qq (kept as assembled)
+    void* To;                 // [NI-1][s_pad][s_pad] T_{q,q+1}
+    void* Linv;               // [NI][s_pad][s_pad] L_j^{-1}, S_j = L_j L_j^T
+    void* Y;                  // [NI-1][s_pad][s_pad] Y_j = L_j^{-1} T_{j,j+1}
+    void* Swork;              // [s_pad][s_pad]
+
+    unsigned int* dstatus;    // device status word
+
+    // solve workspace, sized for kcap right-hand sides
+    int kcap;
+    void* wYv;                // [NS][s+1][m][k]     y of each separator (up pass)
+    void* wGtb;               // [NS][s+1][2][m][k]  condensed top/bot load
+    void* wXs;                // [NS][s+1][m][k]     interior solution per row
+    void* wFi;                // [NS][2][s_pad][k]   interface load contributions
+    void* wX;                 // [NI][s_pad][k]
+    void* wZ;                 // [NI][s_pad][k]
+    void* wVp;                // down-pass partial sums
+    size_t wVp_elems;
+    double* wR;               // [rcap][N] FP64 residual
+    double* wNrm;             // [2 rcap] FP64 norms
+    int rcap;
+
+    int64_t dev_bytes;
+    slab_status err;
+};
+
+// ---------------------------------------------------------------- tree helpers (host+device)
+__host__ __device__ inline int tree_height_count(int s) {
+    int H = 0;
+    while ((1 << H) <= s) ++H;
+    return H;                      // root = 2^(H-1)
+}
+__host__ __device__ inline int tree_nodes_at(int s, int k) {
+    int p = 1 << k;
+    return p > s ? 0 : (s - p) / (2 * p) + 1;
+}
+// height of the right child of node c at height k (-1 if none)
+__host__ __device__ inline int tree_right_height(int s, int c, int k) {
+    if (k == 0 || c >= s) return -1;
+    for (int kk = k - 1; kk >= 0; --kk)
+        if (c + (1 << kk) <= s) return kk;
+    return -1;
+}
+
+// ---------------------------------------------------------------- launchers (defined in .cu files)
+// coefficients / stencil (stencil.cu)
+slab_status launch_coefficients(slab_handle* h, const double* kappa, const double* c);
+slab_status launch_residual(slab_handle* h, const double* u, const double* f, double* r, int k,
+                            double* nrm_r, double* nrm_f);   // nrm_* may be NULL (device, k each)
+slab_status launch_apply(slab_handle* h, const double* x, double* y, int k);
+slab_status launch_kappa_gradient(slab_handle* h, const double* u, const double* lam, double* g, int k);
+
+// stage 1 (tree.cu)
+int tree_kmax();   // right-hand sides per solve-phase launch
+template <typename T> slab_status tree_factor(slab_handle* h);
+// up pass + reduced load into the interface workspace X, for rhs [r0, r0+K) of F scaled by fscale
+template <typename T> slab_status tree_up_gather(slab_handle* h, const double* F, double fscale, int r0, int K);
+// down pass from X (interface solution) into U (FP64 [k][N]); accumulate: U += x instead of U = x
+template <typename T> slab_status tree_down_scatter(slab_handle* h, double* U, int accumulate, int r0, int K);
+template <typename T> slab_status export_ftilde_part(slab_handle* h, double* out, double scale, int r0, int K);
+template <typename T> slab_status import_utilde_part(slab_handle* h, const double* in, int r0, int K);
+
+// T assembly (assemble.cu)
+template <typename T> slab_status assemble_T(slab_handle* h);
+
+// stage 2 (dense.cu)
+template <typename T> slab_status sweep_factor(slab_handle* h);
+template <typename T> slab_status sweep_solve(slab_handle* h, int K);
+
+// error helper
+slab_status slab_cuda_check(slab_handle* h, cudaError_t e);
+#define SLAB_CK(h, call)                                             \
+    do {                                                             \
+        cudaError_t _e = (call);                                     \
+        if (_e != cudaSuccess) return slab_cuda_check((h), _e);      \
+    } while (0)
+#define SLAB_CK_LAUNCH(h) SLAB_CK(h, cudaGetLastError())

@@ -1,0 +1,578 @@
+// Stage 1: elimination of the slab interiors (Sec. 3.1, Algorithm 3 first loop)
+// and the parallel phases of Algorithm 4 (reduced load, eqs. f1-f5; interior
+// back-solve, eq. usol_even).
+//
+// Each slab's interior block A_JJ is eliminated by cyclic reduction along y:
+// the rows form a binary "ruler" tree (row c has height ctz(c)), and a launch
+// eliminates every node of one height in every slab at once.  Node c merges
+// the condensed systems of its two child segments through its separator row:
+//   S   = D_c + R_alpha[bot,bot] + R_beta[top,top]            (m x m, SPD)
+//   B   = couplings of row c to {top row, bot row, interface nodes of the segment}
+//   L L^T = S,   Z = L^{-1} B,   R_merged = R_others - Z^T Z.
+// Only the rows of R that belong to the top/bot rows are kept (the interface x
+// interface part is summed later by the fused T assembly), so the per-node work
+// is O(m^2 w) and the storage O(m s log s) per slab.
+#include "slab_internal.cuh"
+
+namespace {
+
+constexpr int MAXM = SLAB_MAXM;
+constexpr int SP = MAXM + 1;          // padded smem row stride for m x m
+constexpr int SP2 = 2 * MAXM + 1;     // padded smem row stride for m x 2m
+constexpr int TB_THREADS = 128;
+
+template <typename T>
+struct TreeArgs {
+    int s, s_pad, m, H, NS, b, n;
+    const double* AX;
+    const double* AY;
+    const double* DG;
+    T* Linv;
+    T* Ztb;
+    T* Rtb;
+    T* ZI;
+    T* RI;
+    unsigned* status;
+    __device__ int64_t node(int t, int c) const { return (int64_t)t * (s + 1) + c; }
+    __device__ T* linv(int t, int c) const { return Linv + node(t, c) * m * m; }
+    __device__ T* ztb(int t, int c) const { return Ztb + node(t, c) * 2 * m * m; }
+    __device__ T* rtb(int t, int c) const { return Rtb + node(t, c) * 4 * m * m; }
+    __device__ T* zi(int t, int k, int side) const {
+        return ZI + (((int64_t)t * H + k) * 2 + side) * m * s_pad;
+    }
+    __device__ T* ri(int t, int k, int tb, int side) const {
+        return RI + ((((int64_t)t * H + k) * 2 + tb) * 2 + side) * m * s_pad;
+    }
+};
+
+template <typename T>
+__device__ inline T dsqrt(T v) { return sqrt(v); }
+
+// In-place Cholesky of the m x m matrix S (lower) and Li = L^{-1}; all threads of the block.
+template <typename T>
+__device__ void chol_inv_small(T* S, T* Li, int m, unsigned* status) {
+    const int tid = threadIdx.x, nth = blockDim.x;
+    for (int k = 0; k < m; ++k) {
+        if (tid == 0) {
+            T d = S[k * SP + k];
+            if (!(d > T(0)) || !isfinite((double)d)) {
+                atomicOr(status, SLAB_DEV_NOTSPD);
+                d = T(1);
+            }
+            S[k * SP + k] = dsqrt(d);
+        }
+        __syncthreads();
+        if (tid > k && tid < m) S[tid * SP + k] /= S[k * SP + k];
+        __syncthreads();
+        const int r = m - k - 1;
+        for (int idx = tid; idx < r * r; idx += nth) {
+            const int i = k + 1 + idx / r, j = k + 1 + idx % r;
+            if (j <= i) S[i * SP + j] -= S[i * SP + k] * S[j * SP + k];
+        }
+        __syncthreads();
+    }
+    for (int i = 0; i < m; ++i) {
+        if (tid < m) {
+            const int j = tid;
+            T v = T(0);
+            if (j <= i) {
+                T acc = (i == j) ? T(1) : T(0);
+                for (int l = j; l < i; ++l) acc -= S[i * SP + l] * Li[l * SP + j];
+                v = acc / S[i * SP + i];
+            }
+            Li[i * SP + j] = v;
+        }
+        __syncthreads();
+    }
+}
+
+// One height of the cyclic reduction in every slab.
+// grid = (node index a at this height, column chunk, slab t); block = TB_THREADS.
+template <typename T>
+__global__ void __launch_bounds__(TB_THREADS) tree_factor_kernel(TreeArgs<T> A, int k) {
+    __shared__ T S[MAXM * SP];
+    __shared__ T Li[MAXM * SP];
+    __shared__ T Bt[MAXM * SP2];       // B, then Z = Li B in place
+    T* Zt = Bt;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int t = blockIdx.z;
+    const int c = (2 * blockIdx.x + 1) << k;
+    const int s = A.s, m = A.m;
+    if (c > s) return;
+    const int lo = c - (1 << k) + 1;
+    const int hi = min(s, c + (1 << k) - 1);
+    const int w = hi - lo + 1;
+    const int ncols = 2 * w;
+    const int q0 = blockIdx.y * TB_THREADS;
+    if (blockIdx.y > 0 && q0 >= ncols) return;
+    const int alpha = k > 0 ? c - (1 << (k - 1)) : 0;
+    const int kb = tree_right_height(s, c, k);
+    const int beta = kb >= 0 ? c + (1 << kb) : 0;
+    const int x0 = t * A.b + 1;
+    const int np1 = A.n + 1;
+    const double* DGr = A.DG + (int64_t)c * np1;
+    const double* AXr = A.AX + (int64_t)c * np1;
+    const T* Ra = alpha ? A.rtb(t, alpha) : nullptr;
+    const T* Rb = beta ? A.rtb(t, beta) : nullptr;
+    const int m2 = 2 * m;
+
+    // S = D_c + R_alpha[bot,bot] + R_beta[top,top];  B = [top | bot] couplings
+    for (int idx = tid; idx < m * m; idx += nth) {
+        const int i = idx / m, j = idx % m;
+        double v = 0.0;
+        if (i == j) v = DGr[x0 + i];
+        else if (j == i + 1) v = -AXr[x0 + i];
+        else if (j == i - 1) v = -AXr[x0 + j];
+        T tv = (T)v;
+        if (Ra) tv += Ra[(m + i) * m2 + (m + j)];
+        if (Rb) tv += Rb[i * m2 + j];
+        S[i * SP + j] = tv;
+    }
+    for (int idx = tid; idx < m * m2; idx += nth) {
+        const int i = idx / m2, j = idx % m2;
+        T v = T(0);
+        if (j < m) {
+            if (Ra) v = Ra[(m + i) * m2 + j];                       // alpha's bot row x its top column
+            else if (i == j && c - 1 >= 1) v = (T)(-A.AY[(int64_t)(c - 1) * np1 + x0 + i]);
+        } else {
+            const int jj = j - m;
+            if (Rb) v = Rb[i * m2 + m + jj];                        // beta's top row x its bot column
+            else if (i == jj && c + 1 <= s) v = (T)(-A.AY[(int64_t)c * np1 + x0 + i]);
+        }
+        Bt[i * SP2 + j] = v;
+    }
+    __syncthreads();
+    chol_inv_small<T>(S, Li, m, A.status);
+    // Z = Li B, in place; a thread owns a column, rows from the bottom (Li is lower triangular)
+    for (int j = tid; j < m2; j += nth)
+        for (int i = m - 1; i >= 0; --i) {
+            T acc = T(0);
+            for (int l = 0; l <= i; ++l) acc += Li[i * SP + l] * Bt[l * SP2 + j];
+            Bt[i * SP2 + j] = acc;
+        }
+    __syncthreads();
+    if (blockIdx.y == 0) {
+        T* Lg = A.linv(t, c);
+        for (int idx = tid; idx < m * m; idx += nth) Lg[idx] = Li[(idx / m) * SP + idx % m];
+        T* Zg = A.ztb(t, c);
+        for (int idx = tid; idx < m * m2; idx += nth) Zg[idx] = Zt[(idx / m2) * SP2 + idx % m2];
+        T* Rg = A.rtb(t, c);
+        for (int idx = tid; idx < m2 * m2; idx += nth) {
+            const int a = idx / m2, bcol = idx % m2;
+            T v = T(0);
+            for (int l = 0; l < m; ++l) v -= Zt[l * SP2 + a] * Zt[l * SP2 + bcol];
+            if (a < m && bcol < m && Ra) v += Ra[a * m2 + bcol];                     // alpha top x top
+            if (a >= m && bcol >= m && Rb) v += Rb[a * m2 + bcol];                   // beta bot x bot
+            Rg[idx] = v;
+        }
+    }
+    // interface columns of the segment: one thread per column
+    const int q = q0 + tid;
+    if (q < ncols) {
+        const int side = q / w;
+        const int j = lo + q % w;
+        const int rr = j - 1;
+        const int sp = A.s_pad;
+        T bvec[MAXM];
+#pragma unroll
+        for (int i = 0; i < MAXM; ++i) bvec[i] = T(0);
+        if (j < c) {
+            const T* src = A.ri(t, k - 1, 1, side) + rr;
+#pragma unroll
+            for (int i = 0; i < MAXM; ++i) if (i < m) bvec[i] = src[(int64_t)i * sp];
+        } else if (j == c) {
+            if (side == 0) {
+                if (t >= 1) bvec[0] = (T)(-AXr[x0 - 1]);
+            } else {
+                if (t <= A.NS - 2) {
+#pragma unroll
+                    for (int i = 0; i < MAXM; ++i) if (i == m - 1) bvec[i] = (T)(-AXr[x0 + m - 1]);
+                }
+            }
+        } else {
+            const T* src = A.ri(t, kb, 0, side) + rr;
+#pragma unroll
+            for (int i = 0; i < MAXM; ++i) if (i < m) bvec[i] = src[(int64_t)i * sp];
+        }
+        T z[MAXM];
+#pragma unroll
+        for (int i = 0; i < MAXM; ++i) {
+            T acc = T(0);
+#pragma unroll
+            for (int l = 0; l < MAXM; ++l)
+                if (l <= i && i < m) acc += Li[i * SP + l] * bvec[l];
+            z[i] = acc;
+        }
+        T* zd = A.zi(t, k, side) + rr;
+#pragma unroll
+        for (int i = 0; i < MAXM; ++i) if (i < m) zd[(int64_t)i * sp] = z[i];
+        // condensed top/bot rows for this interface column
+        const T* rta = (j < c) ? A.ri(t, k - 1, 0, side) + rr : nullptr;
+        const T* rbb = (j > c) ? A.ri(t, kb, 1, side) + rr : nullptr;
+        T* rtd = A.ri(t, k, 0, side) + rr;
+        T* rbd = A.ri(t, k, 1, side) + rr;
+        for (int a = 0; a < m; ++a) {
+            T vt = rta ? rta[(int64_t)a * sp] : T(0);
+            T vb = rbb ? rbb[(int64_t)a * sp] : T(0);
+#pragma unroll
+            for (int i = 0; i < MAXM; ++i)
+                if (i < m) {
+                    vt -= Zt[i * SP2 + a] * z[i];
+                    vb -= Zt[i * SP2 + m + a] * z[i];
+                }
+            rtd[(int64_t)a * sp] = vt;
+            rbd[(int64_t)a * sp] = vb;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ solve phases
+template <typename T>
+struct SolveArgs {
+    TreeArgs<T> tr;
+    int K;            // right-hand sides in this call (<= kcap)
+    int kcap;         // stride of the right-hand-side index
+    T* Yv;            // [NS][s+1][m][kcap]
+    T* Gtb;           // [NS][s+1][2][m][kcap]
+    T* Xs;            // [NS][s+1][m][kcap]
+    T* Fi;            // [NS][2][s_pad][kcap]
+    T* X;             // [NI][s_pad][kcap]
+    __device__ int64_t nodeoff(int t, int c) const { return (int64_t)t * (tr.s + 1) + c; }
+    __device__ T* yv(int t, int c) const { return Yv + nodeoff(t, c) * tr.m * kcap; }
+    __device__ T* gtb(int t, int c, int tb) const { return Gtb + (nodeoff(t, c) * 2 + tb) * tr.m * kcap; }
+    __device__ T* xs(int t, int c) const { return Xs + nodeoff(t, c) * tr.m * kcap; }
+    __device__ T* fi(int t, int side) const { return Fi + ((int64_t)t * 2 + side) * tr.s_pad * kcap; }
+    __device__ T* xi(int q) const { return X + (int64_t)q * tr.s_pad * kcap; }
+};
+
+constexpr int KMAX = 64;   // right-hand sides handled per launch
+
+// Up pass of one height: y = Li (f_c + G_alpha[bot] + G_beta[top]); condensed top/bot load;
+// interface load Fi -= Z_I^T y.  grid = (node, chunk, slab).
+template <typename T>
+__global__ void __launch_bounds__(TB_THREADS) tree_up_kernel(SolveArgs<T> P, int k, const double* F,
+                                                             double fscale, int r0) {
+    __shared__ T Li[MAXM * SP];
+    __shared__ T Zt[MAXM * SP2];
+    __shared__ T y[MAXM * KMAX];
+    const TreeArgs<T>& A = P.tr;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int t = blockIdx.z;
+    const int c = (2 * blockIdx.x + 1) << k;
+    const int s = A.s, m = A.m, K = P.K, kc = P.kcap;
+    if (c > s) return;
+    const int lo = c - (1 << k) + 1;
+    const int hi = min(s, c + (1 << k) - 1);
+    const int w = hi - lo + 1;
+    const int ncols = 2 * w;
+    const int q0 = blockIdx.y * TB_THREADS;
+    if (blockIdx.y > 0 && q0 >= ncols) return;
+    const int alpha = k > 0 ? c - (1 << (k - 1)) : 0;
+    const int kb = tree_right_height(s, c, k);
+    const int beta = kb >= 0 ? c + (1 << kb) : 0;
+    const int x0 = t * A.b + 1;
+    const int m2 = 2 * m;
+    const T* Lg = A.linv(t, c);
+    const T* Zg = A.ztb(t, c);
+    for (int idx = tid; idx < m * m; idx += nth) Li[(idx / m) * SP + idx % m] = Lg[idx];
+    for (int idx = tid; idx < m * m2; idx += nth) Zt[(idx / m2) * SP2 + idx % m2] = Zg[idx];
+    // g into y (temporarily)
+    const int64_t N = (int64_t)s * s;
+    for (int idx = tid; idx < m * K; idx += nth) {
+        const int i = idx / K, r = idx % K;
+        T g = (T)(fscale * F[(int64_t)(r0 + r) * N + (int64_t)(c - 1) * s + (x0 - 1 + i)]);
+        if (alpha) g += P.gtb(t, alpha, 1)[i * kc + r];
+        if (beta) g += P.gtb(t, beta, 0)[i * kc + r];
+        y[i * KMAX + r] = g;
+    }
+    __syncthreads();
+    // y = Li g in place: a thread owns a right-hand side, rows from the bottom
+    for (int r = tid; r < K; r += nth)
+        for (int i = m - 1; i >= 0; --i) {
+            T a = T(0);
+            for (int l = 0; l <= i; ++l) a += Li[i * SP + l] * y[l * KMAX + r];
+            y[i * KMAX + r] = a;
+        }
+    __syncthreads();
+    if (blockIdx.y == 0) {
+        T* yd = P.yv(t, c);
+        for (int idx = tid; idx < m * K; idx += nth) yd[(idx / K) * kc + idx % K] = y[(idx / K) * KMAX + idx % K];
+        T* gt = P.gtb(t, c, 0);
+        T* gb = P.gtb(t, c, 1);
+        for (int idx = tid; idx < m * K; idx += nth) {
+            const int a = idx / K, r = idx % K;
+            T vt = alpha ? P.gtb(t, alpha, 0)[a * kc + r] : T(0);
+            T vb = beta ? P.gtb(t, beta, 1)[a * kc + r] : T(0);
+            for (int i = 0; i < m; ++i) {
+                vt -= Zt[i * SP2 + a] * y[i * KMAX + r];
+                vb -= Zt[i * SP2 + m + a] * y[i * KMAX + r];
+            }
+            gt[a * kc + r] = vt;
+            gb[a * kc + r] = vb;
+        }
+    }
+    // interface load: Fi[side][rr][r] -= sum_i Z_I[i][rr] y[i][r]
+    const int qend = min(ncols, q0 + TB_THREADS);
+    for (int idx = tid; idx < (qend - q0) * K; idx += nth) {
+        const int q = q0 + idx / K, r = idx % K;
+        const int side = q / w;
+        const int rr = lo + q % w - 1;
+        const T* z = A.zi(t, k, side) + rr;
+        T acc = T(0);
+        for (int i = 0; i < m; ++i) acc += z[(int64_t)i * A.s_pad] * y[i * KMAX + r];
+        P.fi(t, side)[(int64_t)rr * kc + r] -= acc;
+    }
+}
+
+// Down pass of one height: x_c = Li^T (y - Z_top x_top - Z_bot x_bot - Z_I u_I).
+// grid = (node, 1, slab); the node's interface columns are reduced in 32-wide chunks.
+template <typename T>
+__global__ void __launch_bounds__(TB_THREADS) tree_down_kernel(SolveArgs<T> P, int k, double* U,
+                                                               int accumulate, int r0) {
+    constexpr int CJ = 16;             // interface columns per reduction chunk
+    __shared__ T Li[MAXM * SP];
+    __shared__ T V[MAXM * KMAX];
+    __shared__ T zc[MAXM * (CJ + 1)];
+    __shared__ T uc[CJ * KMAX];
+    const TreeArgs<T>& A = P.tr;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int t = blockIdx.z;
+    const int c = (2 * blockIdx.x + 1) << k;
+    const int s = A.s, m = A.m, K = P.K, kc = P.kcap;
+    if (c > s) return;
+    const int lo = c - (1 << k) + 1;
+    const int hi = min(s, c + (1 << k) - 1);
+    const int w = hi - lo + 1;
+    const int x0 = t * A.b + 1;
+    const int m2 = 2 * m;
+    const T* Lg = A.linv(t, c);
+    const T* Zg = A.ztb(t, c);
+    for (int idx = tid; idx < m * m; idx += nth) Li[(idx / m) * SP + idx % m] = Lg[idx];
+    const T* xt = (lo - 1 >= 1) ? P.xs(t, lo - 1) : nullptr;
+    const T* xb = (hi + 1 <= s) ? P.xs(t, hi + 1) : nullptr;
+    const T* yv = P.yv(t, c);
+    for (int idx = tid; idx < m * K; idx += nth) {
+        const int i = idx / K, r = idx % K;
+        T v = yv[i * kc + r];
+        for (int a = 0; a < m; ++a) {
+            if (xt) v -= Zg[i * m2 + a] * xt[a * kc + r];
+            if (xb) v -= Zg[i * m2 + m + a] * xb[a * kc + r];
+        }
+        V[i * KMAX + r] = v;
+    }
+    // interface contributions, 32 columns at a time, both sides
+    for (int side = 0; side < 2; ++side) {
+        const int q = side == 0 ? t - 1 : t;         // interface index bordering this side
+        if (q < 0 || q >= A.NS - 1) continue;
+        const T* zsrc = A.zi(t, k, side);
+        const T* usrc = P.xi(q);
+        for (int j0 = lo - 1; j0 < hi; j0 += CJ) {
+            const int nj = min(CJ, hi - j0);
+            __syncthreads();
+            for (int idx = tid; idx < m * CJ; idx += nth) {
+                const int i = idx / CJ, jj = idx % CJ;
+                zc[i * (CJ + 1) + jj] = jj < nj ? zsrc[(int64_t)i * A.s_pad + j0 + jj] : T(0);
+            }
+            for (int idx = tid; idx < CJ * K; idx += nth) {
+                const int jj = idx / K, r = idx % K;
+                uc[jj * KMAX + r] = jj < nj ? usrc[(int64_t)(j0 + jj) * kc + r] : T(0);
+            }
+            __syncthreads();
+            for (int idx = tid; idx < m * K; idx += nth) {
+                const int i = idx / K, r = idx % K;
+                T acc = T(0);
+#pragma unroll
+                for (int jj = 0; jj < CJ; ++jj) acc += zc[i * (CJ + 1) + jj] * uc[jj * KMAX + r];
+                V[i * KMAX + r] -= acc;
+            }
+        }
+    }
+    __syncthreads();
+    // x = Li^T V in place: a thread owns a right-hand side, rows from the top
+    for (int r = tid; r < K; r += nth)
+        for (int i = 0; i < m; ++i) {
+            T acc = T(0);
+            for (int l = i; l < m; ++l) acc += Li[l * SP + i] * V[l * KMAX + r];
+            V[i * KMAX + r] = acc;
+        }
+    __syncthreads();
+    T* xd = P.xs(t, c);
+    const int64_t N = (int64_t)s * s;
+    for (int idx = tid; idx < m * K; idx += nth) {
+        const int i = idx / K, r = idx % K;
+        const T acc = V[i * KMAX + r];
+        xd[i * kc + r] = acc;
+        double* up = U + (int64_t)(r0 + r) * N + (int64_t)(c - 1) * s + (x0 - 1 + i);
+        if (accumulate) *up += (double)acc;
+        else *up = (double)acc;
+    }
+}
+
+// X[q][rr][r] = fscale f[r][rr][x_q] + Fi[q][R][rr][r] + Fi[q+1][L][rr][r]  (padding rows zero)
+template <typename T>
+__global__ void gather_ftilde_kernel(SolveArgs<T> P, const double* F, double fscale, int r0) {
+    const TreeArgs<T>& A = P.tr;
+    const int q = blockIdx.y;
+    const int K = P.K, kc = P.kcap;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)A.s_pad * K) return;
+    const int rr = (int)(idx / K), r = (int)(idx % K);
+    T v = T(0);
+    if (rr < A.s) {
+        const int64_t N = (int64_t)A.s * A.s;
+        const int xq = (q + 1) * A.b;
+        v = (T)(fscale * F[(int64_t)(r0 + r) * N + (int64_t)rr * A.s + (xq - 1)]);
+        v += P.fi(q, 1)[(int64_t)rr * kc + r] + P.fi(q + 1, 0)[(int64_t)rr * kc + r];
+    }
+    P.xi(q)[(int64_t)rr * kc + r] = v;
+}
+
+template <typename T>
+__global__ void scatter_utilde_kernel(SolveArgs<T> P, double* U, int accumulate, int r0) {
+    const TreeArgs<T>& A = P.tr;
+    const int q = blockIdx.y;
+    const int K = P.K, kc = P.kcap;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)A.s * K) return;
+    const int rr = (int)(idx % A.s), r = (int)(idx / A.s);
+    const int64_t N = (int64_t)A.s * A.s;
+    const int xq = (q + 1) * A.b;
+    double* up = U + (int64_t)(r0 + r) * N + (int64_t)rr * A.s + (xq - 1);
+    const double v = (double)P.xi(q)[(int64_t)rr * kc + r];
+    if (accumulate) *up += v;
+    else *up = v;
+}
+
+// ftilde (FP64, [k][q][j]) <-> X (scalar, [q][j][r])
+template <typename T>
+__global__ void export_x_kernel(SolveArgs<T> P, double* out, double scale, int NI, int r0) {
+    const TreeArgs<T>& A = P.tr;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t per = (int64_t)NI * A.s;
+    if (idx >= per * P.K) return;
+    const int r = (int)(idx / per);
+    const int64_t rem = idx % per;
+    const int q = (int)(rem / A.s), rr = (int)(rem % A.s);
+    out[(int64_t)(r0 + r) * per + rem] = scale * (double)P.xi(q)[(int64_t)rr * P.kcap + r];
+}
+template <typename T>
+__global__ void import_x_kernel(SolveArgs<T> P, const double* in, int NI, int r0) {
+    const TreeArgs<T>& A = P.tr;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t per = (int64_t)NI * A.s_pad;
+    if (idx >= per * P.K) return;
+    const int r = (int)(idx / per);
+    const int64_t rem = idx % per;
+    const int q = (int)(rem / A.s_pad), rr = (int)(rem % A.s_pad);
+    P.xi(q)[(int64_t)rr * P.kcap + r] =
+        rr < A.s ? (T)in[(int64_t)(r0 + r) * NI * A.s + (int64_t)q * A.s + rr] : T(0);
+}
+
+template <typename T>
+TreeArgs<T> make_tree_args(slab_handle* h) {
+    TreeArgs<T> a;
+    a.s = h->td.s; a.s_pad = h->td.s_pad; a.m = h->td.m; a.H = h->td.H; a.NS = h->td.NS;
+    a.b = h->b; a.n = h->n;
+    a.AX = h->AX; a.AY = h->AY; a.DG = h->DG;
+    a.Linv = (T*)h->tLinv; a.Ztb = (T*)h->tZtb; a.Rtb = (T*)h->tRtb; a.ZI = (T*)h->tZI; a.RI = (T*)h->tRI;
+    a.status = h->dstatus;
+    return a;
+}
+
+template <typename T>
+SolveArgs<T> make_solve_args(slab_handle* h, int K) {
+    SolveArgs<T> p;
+    p.tr = make_tree_args<T>(h);
+    p.K = K; p.kcap = h->kcap;
+    p.Yv = (T*)h->wYv; p.Gtb = (T*)h->wGtb; p.Xs = (T*)h->wXs; p.Fi = (T*)h->wFi; p.X = (T*)h->wX;
+    return p;
+}
+
+inline int chunks_at(int s, int k) {
+    const int wmax = min(s, (1 << (k + 1)) - 1);
+    return (2 * wmax + TB_THREADS - 1) / TB_THREADS;
+}
+
+}  // namespace
+
+template <typename T>
+slab_status tree_factor(slab_handle* h) {
+    TreeArgs<T> a = make_tree_args<T>(h);
+    const TreeDims& d = h->td;
+    for (int k = 0; k < d.H; ++k) {
+        const int cnt = tree_nodes_at(d.s, k);
+        if (!cnt) continue;
+        dim3 grid(cnt, chunks_at(d.s, k), d.NS);
+        tree_factor_kernel<T><<<grid, TB_THREADS, 0, h->stream>>>(a, k);
+        SLAB_CK_LAUNCH(h);
+    }
+    return SLAB_OK;
+}
+
+// Up pass over all heights for right-hand sides [r0, r0+K) of F (FP64, [k][N]) scaled by fscale,
+// then the reduced load f~ into X.
+template <typename T>
+slab_status tree_up_gather(slab_handle* h, const double* F, double fscale, int r0, int K) {
+    SolveArgs<T> p = make_solve_args<T>(h, K);
+    const TreeDims& d = h->td;
+    SLAB_CK(h, cudaMemsetAsync(h->wFi, 0, (size_t)d.NS * 2 * d.s_pad * h->kcap * h->rsz, h->stream));
+    for (int k = 0; k < d.H; ++k) {
+        const int cnt = tree_nodes_at(d.s, k);
+        if (!cnt) continue;
+        dim3 grid(cnt, chunks_at(d.s, k), d.NS);
+        tree_up_kernel<T><<<grid, TB_THREADS, 0, h->stream>>>(p, k, F, fscale, r0);
+        SLAB_CK_LAUNCH(h);
+    }
+    dim3 g2((unsigned)(((int64_t)d.s_pad * K + 255) / 256), d.NI);
+    gather_ftilde_kernel<T><<<g2, 256, 0, h->stream>>>(p, F, fscale, r0);
+    SLAB_CK_LAUNCH(h);
+    return SLAB_OK;
+}
+
+template <typename T>
+slab_status tree_down_scatter(slab_handle* h, double* U, int accumulate, int r0, int K) {
+    SolveArgs<T> p = make_solve_args<T>(h, K);
+    const TreeDims& d = h->td;
+    for (int k = d.H - 1; k >= 0; --k) {
+        const int cnt = tree_nodes_at(d.s, k);
+        if (!cnt) continue;
+        dim3 grid(cnt, 1, d.NS);
+        tree_down_kernel<T><<<grid, TB_THREADS, 0, h->stream>>>(p, k, U, accumulate, r0);
+        SLAB_CK_LAUNCH(h);
+    }
+    dim3 g2((unsigned)(((int64_t)d.s * K + 255) / 256), d.NI);
+    scatter_utilde_kernel<T><<<g2, 256, 0, h->stream>>>(p, U, accumulate, r0);
+    SLAB_CK_LAUNCH(h);
+    return SLAB_OK;
+}
+
+template <typename T>
+slab_status export_ftilde_part(slab_handle* h, double* out, double scale, int r0, int K) {
+    SolveArgs<T> p = make_solve_args<T>(h, K);
+    const int64_t tot = (int64_t)h->td.NI * h->td.s * K;
+    export_x_kernel<T><<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>(p, out, scale, h->td.NI, r0);
+    SLAB_CK_LAUNCH(h);
+    return SLAB_OK;
+}
+
+template <typename T>
+slab_status import_utilde_part(slab_handle* h, const double* in, int r0, int K) {
+    SolveArgs<T> p = make_solve_args<T>(h, K);
+    const int64_t tot = (int64_t)h->td.NI * h->td.s_pad * K;
+    import_x_kernel<T><<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>(p, in, h->td.NI, r0);
+    SLAB_CK_LAUNCH(h);
+    return SLAB_OK;
+}
+
+int tree_kmax() { return KMAX; }
+
+template slab_status tree_factor<float>(slab_handle*);
+template slab_status tree_factor<double>(slab_handle*);
+template slab_status tree_up_gather<float>(slab_handle*, const double*, double, int, int);
+template slab_status tree_up_gather<double>(slab_handle*, const double*, double, int, int);
+template slab_status tree_down_scatter<float>(slab_handle*, double*, int, int, int);
+template slab_status tree_down_scatter<double>(slab_handle*, double*, int, int, int);
+template slab_status export_ftilde_part<float>(slab_handle*, double*, double, int, int);
+template slab_status export_ftilde_part<double>(slab_handle*, double*, double, int, int);
+template slab_status import_utilde_part<float>(slab_handle*, const double*, int, int);
+template slab_status import_utilde_part<double>(slab_handle*, const double*, int, int);

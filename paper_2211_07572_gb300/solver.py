@@ -1,0 +1,175 @@
+"""Thin PyTorch-facing wrapper over the C ABI (include/slab.h).
+
+PyTorch provides device memory and the stream; every arithmetic step runs in
+libslab.so.  Tensors passed in must be CUDA float64 and contiguous; they are
+never copied to the host except for the explicit host outputs (relative
+residuals, T blocks).
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional, Tuple
+
+import numpy as np
+import torch
+
+from . import _lib
+
+_PREC = {"fp64": _lib.PREC_FP64, "fp32": _lib.PREC_FP32}
+
+
+def _dev(x, device) -> torch.Tensor:
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        x = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64))
+    x = x.to(device=device, dtype=torch.float64)
+    return x.contiguous()
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+class SlabSolver:
+    """Factor A for one grid/coefficient set (Algorithm 3) and solve with it (Algorithm 4).
+
+    dim, n: grid (unit square/cube, h = 1/n); b: interface spacing (b | n);
+    kind: 0 Poisson, 1 diffusion -div(kappa grad u), 2 Helmholtz -Lap u - (omega/c)^2 u;
+    kappa / c: node fields with (n+1)^dim entries; precision: "fp32" (FP32 factor, FP64
+    refinement) or "fp64" (plain FP64 path).
+    """
+
+    def __init__(self, dim: int, n: int, b: int, kind: int, kappa=None, c=None, omega: float = 0.0,
+                 precision: str = "fp32", rtol: float = 1e-10, max_refine: int = 30,
+                 stream: Optional[torch.cuda.Stream] = None, device=None):
+        self.lib = _lib.load()
+        self.device = (torch.device(device) if device is not None
+                       else torch.device("cuda", torch.cuda.current_device()))
+        self.dim, self.n, self.b, self.kind = dim, n, b, kind
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._kappa = _dev(kappa, self.device)
+        self._c = _dev(c, self.device)
+        grid = _lib.SlabGrid(dim, n)
+        co = _lib.SlabCoeffs(kind, _ptr(self._kappa), _ptr(self._c), float(omega))
+        opts = _lib.SlabOpts()
+        self.lib.slab_default_opts(ctypes.byref(opts))
+        opts.factor_prec = _PREC[precision]
+        opts.rtol = float(rtol)
+        opts.max_refine = int(max_refine)
+        opts.stream = ctypes.c_void_p(self.stream.cuda_stream)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _lib.check(self.lib.slab_factor(ctypes.byref(grid), ctypes.byref(co), int(b), ctypes.byref(opts),
+                                            ctypes.byref(h)), "slab_factor")
+        self.h = h
+        N = ctypes.c_int64(); s = ctypes.c_int64(); ni = ctypes.c_int()
+        self.lib.slab_sizes(self.h, ctypes.byref(N), ctypes.byref(s), ctypes.byref(ni))
+        self.N, self.s, self.NI = N.value, s.value, ni.value
+
+    # ------------------------------------------------------------------ helpers
+    def _vec(self, x, k=None) -> torch.Tensor:
+        x = _dev(x, self.device)
+        if x.dim() == 1:
+            x = x.view(1, -1)
+        x = x.reshape(-1, self.N)
+        return x
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.slab_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def device_bytes(self) -> int:
+        return int(self.lib.slab_device_bytes(self.h))
+
+    # ------------------------------------------------------------------ API
+    def solve(self, f, u: Optional[torch.Tensor] = None, allow_noconv: bool = False
+              ) -> Tuple[torch.Tensor, np.ndarray, int]:
+        """u = A^-1 f with refinement; returns (u, relres per rhs, refinement steps)."""
+        f = self._vec(f)
+        k = f.shape[0]
+        if u is None:
+            u = torch.empty_like(f)
+        rel = (ctypes.c_double * max(k, 1))()
+        it = ctypes.c_int()
+        st = self.lib.slab_solve(self.h, _ptr(f), _ptr(u), k, rel, ctypes.byref(it))
+        _lib.check(st, "slab_solve", allow=(_lib.SLAB_ENOCONV,) if allow_noconv else ())
+        return u, np.array(rel[:k]), it.value
+
+    def residual(self, u, f) -> torch.Tensor:
+        u, f = self._vec(u), self._vec(f)
+        r = torch.empty_like(f)
+        _lib.check(self.lib.slab_apply_residual(self.h, _ptr(u), _ptr(f), _ptr(r), f.shape[0]), "residual")
+        return r
+
+    def apply(self, x) -> torch.Tensor:
+        x = self._vec(x)
+        y = torch.empty_like(x)
+        _lib.check(self.lib.slab_apply(self.h, _ptr(x), _ptr(y), x.shape[0]), "apply")
+        return y
+
+    def adjoint(self, dLdu, u=None, allow_noconv: bool = False) -> Tuple[torch.Tensor, Optional[torch.Tensor]]:
+        g = self._vec(dLdu)
+        lam = torch.empty_like(g)
+        grad = None
+        if u is not None:
+            u = self._vec(u)
+            grad = torch.zeros((self.n + 1,) * self.dim, dtype=torch.float64, device=self.device)
+        st = self.lib.slab_adjoint(self.h, _ptr(g), _ptr(u), _ptr(lam), _ptr(grad), g.shape[0])
+        _lib.check(st, "slab_adjoint", allow=(_lib.SLAB_ENOCONV,) if allow_noconv else ())
+        return lam, grad
+
+    def reduced_rhs(self, f) -> torch.Tensor:
+        f = self._vec(f)
+        out = torch.empty((f.shape[0], self.NI * self.s), dtype=torch.float64, device=self.device)
+        _lib.check(self.lib.slab_reduced_rhs(self.h, _ptr(f), _ptr(out), f.shape[0]), "reduced_rhs")
+        return out
+
+    def interface_solve(self, ftilde) -> torch.Tensor:
+        ft = _dev(ftilde, self.device).reshape(-1, self.NI * self.s)
+        out = torch.empty_like(ft)
+        _lib.check(self.lib.slab_interface_solve(self.h, _ptr(ft), _ptr(out), ft.shape[0]), "interface_solve")
+        return out
+
+    def interior_solve(self, f, utilde) -> torch.Tensor:
+        f = self._vec(f)
+        ut = _dev(utilde, self.device).reshape(-1, self.NI * self.s)
+        u = torch.empty_like(f)
+        _lib.check(self.lib.slab_interior_solve(self.h, _ptr(f), _ptr(ut), _ptr(u), f.shape[0]),
+                   "interior_solve")
+        return u
+
+    def T_block(self, which: int, q: int) -> np.ndarray:
+        out = np.empty((self.s, self.s), dtype=np.float64)
+        _lib.check(self.lib.slab_get_T_block(self.h, which, q, out.ctypes.data_as(ctypes.c_void_p)), "T_block")
+        return out
+
+
+class SlabSolveFunction(torch.autograd.Function):
+    """u = A(kappa)^-1 f for the diffusion operator; backward by the adjoint solve.
+
+    dL/df = lambda and dL/dkappa = -lambda^T (dA/dkappa) u with A^T lambda = dL/du.
+    """
+
+    @staticmethod
+    def forward(ctx, kappa, f, n: int, b: int, precision: str = "fp32"):
+        solver = SlabSolver(2, n, b, _lib.DIFFUSION, kappa=kappa.detach(), precision=precision, rtol=1e-13)
+        u, _, _ = solver.solve(f.detach(), allow_noconv=True)
+        ctx.solver = solver
+        ctx.save_for_backward(u)
+        return u.view_as(f)
+
+    @staticmethod
+    def backward(ctx, gu):
+        (u,) = ctx.saved_tensors
+        lam, gk = ctx.solver.adjoint(gu.contiguous(), u, allow_noconv=True)
+        ctx.solver.close()
+        return gk, lam.view_as(gu), None, None, None
