@@ -115,6 +115,12 @@ def run_gpu(args):
         s.close()
         return rel, it
 
+    if args.once:
+        # a single step, for profilers (no timing claims)
+        rel, it = step(f, u)
+        torch.cuda.synchronize()
+        print(json.dumps({"once": True, "config": W, "max_relres": float(np.max(rel)), "refine_steps": it}))
+        return
     for _ in range(args.warmup):
         rel, it = step(f, u)
     # L2 is flushed implicitly: every step streams > 10 GB of factors and vectors (>> 129 MB L2)
@@ -258,6 +264,7 @@ def main():
     ap.add_argument("--k", type=int, default=0)
     ap.add_argument("--ref-n", type=int, default=512)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--once", action="store_true", help="run one step only (for profilers)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

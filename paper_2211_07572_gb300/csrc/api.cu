@@ -38,8 +38,14 @@ void dfree(void*& p) {
 void free_workspace(slab_handle* h) {
     dfree(h->wYv); dfree(h->wGtb); dfree(h->wXs); dfree(h->wFi); dfree(h->wX); dfree(h->wZ);
     dfree(h->wVp);
+    dfree(h->wVtk);
+    dfree(h->wPart);
+    void* tk0 = h->wTickets; dfree(tk0); h->wTickets = nullptr;
     void* r = h->wR; dfree(r); h->wR = nullptr;
     void* q = h->wNrm; dfree(q); h->wNrm = nullptr;
+    void* rp = h->red_part; dfree(rp); h->red_part = nullptr;
+    void* tk = h->red_tickets; dfree(tk); h->red_tickets = nullptr;
+    h->red_cap = h->ticket_cap = 0;
     h->kcap = 0;
     h->rcap = 0;
 }
@@ -67,6 +73,20 @@ slab_status ensure_workspace(slab_handle* h, int k) {
         TRY(dalloc(h, &h->wX, (int64_t)d.NI * d.s_pad * kc * h->rsz));
         TRY(dalloc(h, &h->wZ, (int64_t)d.NI * d.s_pad * kc * h->rsz));
         h->kcap = kc;
+    }
+    if (!h->wVtk) {
+        const size_t e = tree_down_ws_elems(d.s, d.m, d.NS);
+        TRY(dalloc(h, &h->wVp, (e ? e : 1) * h->rsz));
+        const size_t nt = tree_down_tickets(d.s, d.NS);
+        TRY(dalloc(h, &h->wVtk, nt * sizeof(unsigned)));
+        SLAB_CK(h, cudaMemsetAsync(h->wVtk, 0, nt * sizeof(unsigned), h->stream));
+    }
+    if (!h->wPart) {
+        TRY(dalloc(h, &h->wPart, (int64_t)(d.s_pad / SLAB_TILE) * SLAB_SPLITK * SLAB_TILE * SLAB_TILE * h->rsz));
+        void* tk = nullptr;
+        TRY(dalloc(h, &tk, (size_t)(d.s_pad / SLAB_TILE) * sizeof(unsigned)));
+        h->wTickets = (unsigned*)tk;
+        SLAB_CK(h, cudaMemsetAsync(h->wTickets, 0, (size_t)(d.s_pad / SLAB_TILE) * sizeof(unsigned), h->stream));
     }
     return SLAB_OK;
 }

@@ -23,6 +23,7 @@
 
 #define SLAB_TILE 64
 #define SLAB_MAXM 32          // largest slab interior width handled by the 2-D tree kernels
+#define SLAB_SPLITK 8         // K splits of the skinny solve products
 
 // Device-side status word bits (set by kernels, read by the host after a phase).
 #define SLAB_DEV_NOTSPD 1u    // a Cholesky pivot was <= 0 or not finite
@@ -77,11 +78,16 @@ struct slab_handle {
     void* wFi;                // [NS][2][s_pad][k]   interface load contributions
     void* wX;                 // [NI][s_pad][k]
     void* wZ;                 // [NI][s_pad][k]
-    void* wVp;                // down-pass partial sums
-    size_t wVp_elems;
+    void* wVp;                // down-pass partial sums of split nodes
+    void* wVtk;               // down-pass tickets (self-resetting)
+    void* wPart;              // [s_pad/64][SLAB_SPLITK][64][64] skinny-product partial tiles
+    unsigned* wTickets;       // [s_pad/64] self-resetting tile counters
     double* wR;               // [rcap][N] FP64 residual
     double* wNrm;             // [2 rcap] FP64 norms
     int rcap;
+    double* red_part;         // residual-norm partial sums (per block, per right-hand side)
+    unsigned* red_tickets;    // per right-hand-side block counters (self-resetting)
+    size_t red_cap, ticket_cap;
 
     int64_t dev_bytes;
     slab_status err;
@@ -115,6 +121,8 @@ slab_status launch_kappa_gradient(slab_handle* h, const double* u, const double*
 
 // stage 1 (tree.cu)
 int tree_kmax();   // right-hand sides per solve-phase launch
+size_t tree_down_ws_elems(int s, int m, int NS);
+size_t tree_down_tickets(int s, int NS);
 template <typename T> slab_status tree_factor(slab_handle* h);
 // up pass + reduced load into the interface workspace X, for rhs [r0, r0+K) of F scaled by fscale
 template <typename T> slab_status tree_up_gather(slab_handle* h, const double* F, double fscale, int r0, int K);

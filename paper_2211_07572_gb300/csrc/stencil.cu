@@ -33,74 +33,110 @@ __global__ void coeff_kernel(int n, int kind, const double* __restrict__ kappa,
     DG[P] = d;
 }
 
-// r = f - A u (or y = A x with f == nullptr, sign flipped), 2-D, k right-hand sides.
-// Block: 256 threads along x, one grid row per y, blockIdx.z over right-hand-side chunks.
+// r = f - A u (RESID) or y = A u, 2-D, k right-hand sides.  Block: 256 threads along x; each
+// block covers ST_ROWS grid rows and a group of up to ST_Q right-hand sides (blockIdx.z), so the
+// five coefficients of a node are read once per group.
+// Norms: each block writes its partial sums of r^2 and f^2 per right-hand side to part; the last
+// block of a group (ticket counter) adds the partials in block order, so the sums are deterministic.
+constexpr int ST_ROWS = 8;
+constexpr int ST_Q = 8;
 template <bool RESID>
-__global__ void __launch_bounds__(256) stencil2d_kernel(int n, const double* __restrict__ AX,
+__global__ void __launch_bounds__(256) stencil2d_kernel(int n, int k, const double* __restrict__ AX,
                                                         const double* __restrict__ AY,
                                                         const double* __restrict__ DG,
                                                         const double* __restrict__ u,
                                                         const double* __restrict__ f, double* r,
-                                                        int k, int kchunk, double* nrm_r,
-                                                        double* nrm_f) {
+                                                        double* nrm_r, double* nrm_f, double* part,
+                                                        unsigned* tickets) {
     const int s = n - 1;
     const int np1 = n + 1;
+    const int q0 = blockIdx.z * ST_Q;
+    const int nq = min(ST_Q, k - q0);
     const int x = blockIdx.x * blockDim.x + threadIdx.x + 1;   // 1..s
-    const int y = blockIdx.y + 1;
-    const int r0 = blockIdx.z * kchunk;
-    const int r1 = min(k, r0 + kchunk);
     const double n2 = (double)n * (double)n;
-    const bool act = x <= s;
-    double dg = 0, aw = 0, ae = 0, as = 0, an = 0;
-    if (act) {
-        const int64_t P = (int64_t)y * np1 + x;
-        dg = DG[P];
-        aw = AX[P - 1];
-        ae = AX[P];
-        as = AY[P - np1];
-        an = AY[P];
-    }
-    __shared__ double red[2][8];
     const int64_t N = (int64_t)s * s;
-    for (int q = r0; q < r1; ++q) {
-        double rr = 0.0, ff = 0.0;
-        if (act) {
-            const double* uq = u + q * N;
-            const int64_t i = (int64_t)(y - 1) * s + (x - 1);
-            const double uc = uq[i];
-            const double uw = x > 1 ? uq[i - 1] : 0.0;
-            const double ue = x < s ? uq[i + 1] : 0.0;
-            const double us = y > 1 ? uq[i - s] : 0.0;
-            const double un = y < s ? uq[i + s] : 0.0;
-            const double Au = n2 * (dg * uc - aw * uw - ae * ue - as * us - an * un);
-            if (RESID) {
-                const double fv = f[q * N + i];
-                rr = fv - Au;
-                ff = fv;
-                r[q * N + i] = rr;
-            } else {
-                r[q * N + i] = Au;
-            }
-        }
-        if (RESID && nrm_r) {
-            double a = rr * rr, b = ff * ff;
+    double rr2[ST_Q], ff2[ST_Q];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                a += __shfl_xor_sync(0xffffffffu, a, o);
-                b += __shfl_xor_sync(0xffffffffu, b, o);
+    for (int q = 0; q < ST_Q; ++q) rr2[q] = ff2[q] = 0.0;
+    if (x <= s) {
+        for (int yy = 0; yy < ST_ROWS; ++yy) {
+            const int y = blockIdx.y * ST_ROWS + yy + 1;
+            if (y > s) break;
+            const int64_t P = (int64_t)y * np1 + x;
+            const int64_t i = (int64_t)(y - 1) * s + (x - 1);
+            const double dg = n2 * DG[P];
+            const double aw = x > 1 ? n2 * AX[P - 1] : 0.0;
+            const double ae = x < s ? n2 * AX[P] : 0.0;
+            const double as = y > 1 ? n2 * AY[P - np1] : 0.0;
+            const double an = y < s ? n2 * AY[P] : 0.0;
+            const int64_t iw = x > 1 ? i - 1 : i, ie = x < s ? i + 1 : i;
+            const int64_t is = y > 1 ? i - s : i, in = y < s ? i + s : i;
+#pragma unroll
+            for (int q = 0; q < ST_Q; ++q) {
+                if (q < nq) {
+                    const double* uq = u + (q0 + q) * N;
+                    const double Au = dg * uq[i] - aw * uq[iw] - ae * uq[ie] - as * uq[is] - an * uq[in];
+                    if (RESID) {
+                        const double fv = f[(q0 + q) * N + i];
+                        const double rv = fv - Au;
+                        r[(q0 + q) * N + i] = rv;
+                        rr2[q] += rv * rv;
+                        ff2[q] += fv * fv;
+                    } else {
+                        r[(q0 + q) * N + i] = Au;
+                    }
+                }
             }
-            const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-            if (l == 0) { red[0][w] = a; red[1][w] = b; }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                double sa = 0, sb = 0;
-                for (int t = 0; t < 8; ++t) { sa += red[0][t]; sb += red[1][t]; }
-                atomicAdd(nrm_r + q, sa);
-                if (nrm_f) atomicAdd(nrm_f + q, sb);
-            }
-            __syncthreads();
         }
     }
+    if (!RESID || !nrm_r) return;
+    __shared__ double red[2][ST_Q][8];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+    for (int q = 0; q < ST_Q; ++q) {
+        double a = rr2[q], b = ff2[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            b += __shfl_xor_sync(0xffffffffu, b, o);
+        }
+        if (l == 0) { red[0][q][w] = a; red[1][q][w] = b; }
+    }
+    __syncthreads();
+    const int nblk = gridDim.x * gridDim.y;
+    const int bid = blockIdx.y * gridDim.x + blockIdx.x;
+    __shared__ bool last;
+    if (threadIdx.x < 2 * ST_Q) {
+        const int which = threadIdx.x / ST_Q, q = threadIdx.x % ST_Q;
+        double sum = 0;
+        for (int t = 0; t < 8; ++t) sum += red[which][q][t];
+        if (q < nq) part[(((int64_t)(q0 + q)) * nblk + bid) * 2 + which] = sum;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(tickets + blockIdx.z, 1u) == (unsigned)(nblk - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    __shared__ double red2[256];
+    for (int qq = 0; qq < 2 * nq; ++qq) {
+        const int q = qq >> 1, which = qq & 1;
+        double sum = 0;
+        for (int t = threadIdx.x; t < nblk; t += blockDim.x)
+            sum += __ldcg(part + (((int64_t)(q0 + q)) * nblk + t) * 2 + which);
+        red2[threadIdx.x] = sum;
+        __syncthreads();
+        for (int o = 128; o > 0; o >>= 1) {
+            if (threadIdx.x < o) red2[threadIdx.x] += red2[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            if (which == 0) nrm_r[q0 + q] = red2[0];
+            else if (nrm_f) nrm_f[q0 + q] = red2[0];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) tickets[blockIdx.z] = 0;   // ready for the next launch
 }
 
 // dL/dkappa_p += -sum_{faces f containing p} (1/2) n^2 (lam_P - lam_Q)(u_P - u_Q), summed over k pairs.
@@ -141,16 +177,28 @@ slab_status launch_coefficients(slab_handle* h, const double* kappa, const doubl
     return SLAB_OK;
 }
 
-static int kchunk_for(int k) { return k <= 8 ? k : 8; }
-
 slab_status launch_residual(slab_handle* h, const double* u, const double* f, double* r, int k,
                             double* nrm_r, double* nrm_f) {
     const int n = h->n, s = n - 1;
     if (k <= 0) return SLAB_OK;
-    const int kc = kchunk_for(k);
-    dim3 grid((s + 255) / 256, s, (k + kc - 1) / kc);
-    stencil2d_kernel<true><<<grid, 256, 0, h->stream>>>(n, h->AX, h->AY, h->DG, u, f, r, k, kc,
-                                                        nrm_r, nrm_f);
+    dim3 grid((s + 255) / 256, (s + ST_ROWS - 1) / ST_ROWS, (k + ST_Q - 1) / ST_Q);
+    double* part = nullptr;
+    unsigned* tickets = nullptr;
+    if (nrm_r) {
+        const size_t need = (size_t)k * grid.x * grid.y * 2;
+        if (h->red_cap < need || h->ticket_cap < (size_t)k) {
+            if (h->red_part) cudaFree(h->red_part);
+            if (h->red_tickets) cudaFree(h->red_tickets);
+            h->red_part = nullptr; h->red_tickets = nullptr; h->red_cap = h->ticket_cap = 0;
+            SLAB_CK(h, cudaMalloc((void**)&h->red_part, need * sizeof(double)));
+            SLAB_CK(h, cudaMalloc((void**)&h->red_tickets, (size_t)k * sizeof(unsigned)));
+            SLAB_CK(h, cudaMemsetAsync(h->red_tickets, 0, (size_t)k * sizeof(unsigned), h->stream));
+            h->red_cap = need; h->ticket_cap = k;
+        }
+        part = h->red_part; tickets = h->red_tickets;
+    }
+    stencil2d_kernel<true><<<grid, 256, 0, h->stream>>>(n, k, h->AX, h->AY, h->DG, u, f, r, nrm_r, nrm_f,
+                                                        part, tickets);
     SLAB_CK_LAUNCH(h);
     return SLAB_OK;
 }
@@ -158,10 +206,9 @@ slab_status launch_residual(slab_handle* h, const double* u, const double* f, do
 slab_status launch_apply(slab_handle* h, const double* x, double* y, int k) {
     const int n = h->n, s = n - 1;
     if (k <= 0) return SLAB_OK;
-    const int kc = kchunk_for(k);
-    dim3 grid((s + 255) / 256, s, (k + kc - 1) / kc);
-    stencil2d_kernel<false><<<grid, 256, 0, h->stream>>>(n, h->AX, h->AY, h->DG, x, nullptr, y, k,
-                                                         kc, nullptr, nullptr);
+    dim3 grid((s + 255) / 256, (s + ST_ROWS - 1) / ST_ROWS, (k + ST_Q - 1) / ST_Q);
+    stencil2d_kernel<false><<<grid, 256, 0, h->stream>>>(n, k, h->AX, h->AY, h->DG, x, nullptr, y, nullptr,
+                                                         nullptr, nullptr, nullptr);
     SLAB_CK_LAUNCH(h);
     return SLAB_OK;
 }

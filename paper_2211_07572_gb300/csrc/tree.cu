@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(TB_THREADS) tree_up_kernel(SolveArgs<T> P, int
     // g into y (temporarily)
     const int64_t N = (int64_t)s * s;
     for (int idx = tid; idx < m * K; idx += nth) {
-        const int i = idx / K, r = idx % K;
+        const int r = idx / m, i = idx % m;       // consecutive threads read consecutive x
         T g = (T)(fscale * F[(int64_t)(r0 + r) * N + (int64_t)(c - 1) * s + (x0 - 1 + i)]);
         if (alpha) g += P.gtb(t, alpha, 1)[i * kc + r];
         if (beta) g += P.gtb(t, beta, 0)[i * kc + r];
@@ -325,15 +325,21 @@ __global__ void __launch_bounds__(TB_THREADS) tree_up_kernel(SolveArgs<T> P, int
 }
 
 // Down pass of one height: x_c = Li^T (y - Z_top x_top - Z_bot x_bot - Z_I u_I).
-// grid = (node, 1, slab); the node's interface columns are reduced in 32-wide chunks.
+// grid = (node, chunk, slab).  A node's 2w interface columns are split into chunks of DCW; each
+// CTA reduces its chunk into a partial Z_I u_I (m x K).  Nodes with one chunk finish in place;
+// otherwise the partials go to ws and the last CTA of the node (ticket) adds them in chunk order
+// and finishes the node.
+constexpr int DCW = 256;
 template <typename T>
 __global__ void __launch_bounds__(TB_THREADS) tree_down_kernel(SolveArgs<T> P, int k, double* U,
-                                                               int accumulate, int r0) {
-    constexpr int CJ = 16;             // interface columns per reduction chunk
+                                                               int accumulate, int r0, T* ws,
+                                                               unsigned* tickets) {
+    constexpr int CJ = 16;             // interface columns per smem stage
     __shared__ T Li[MAXM * SP];
     __shared__ T V[MAXM * KMAX];
     __shared__ T zc[MAXM * (CJ + 1)];
     __shared__ T uc[CJ * KMAX];
+    __shared__ bool last;
     const TreeArgs<T>& A = P.tr;
     const int tid = threadIdx.x, nth = blockDim.x;
     const int t = blockIdx.z;
@@ -343,39 +349,53 @@ __global__ void __launch_bounds__(TB_THREADS) tree_down_kernel(SolveArgs<T> P, i
     const int lo = c - (1 << k) + 1;
     const int hi = min(s, c + (1 << k) - 1);
     const int w = hi - lo + 1;
+    const int nch = (2 * w + DCW - 1) / DCW;
+    if ((int)blockIdx.y >= nch) return;
+    const int qa = blockIdx.y * DCW, qb = min(2 * w, qa + DCW);
     const int x0 = t * A.b + 1;
     const int m2 = 2 * m;
-    const T* Lg = A.linv(t, c);
+    for (int idx = tid; idx < m * K; idx += nth) V[(idx / K) * KMAX + idx % K] = T(0);
+    // partial Z_I u_I over columns [qa, qb) of [left side rows lo..hi | right side rows lo..hi];
+    // chunk 0 also takes the 2m top/bot columns Z_tb [x_top; x_bot]
     const T* Zg = A.ztb(t, c);
-    for (int idx = tid; idx < m * m; idx += nth) Li[(idx / m) * SP + idx % m] = Lg[idx];
     const T* xt = (lo - 1 >= 1) ? P.xs(t, lo - 1) : nullptr;
     const T* xb = (hi + 1 <= s) ? P.xs(t, hi + 1) : nullptr;
-    const T* yv = P.yv(t, c);
-    for (int idx = tid; idx < m * K; idx += nth) {
-        const int i = idx / K, r = idx % K;
-        T v = yv[i * kc + r];
-        for (int a = 0; a < m; ++a) {
-            if (xt) v -= Zg[i * m2 + a] * xt[a * kc + r];
-            if (xb) v -= Zg[i * m2 + m + a] * xb[a * kc + r];
+    for (int part = (blockIdx.y == 0 ? 0 : 1); part < 3; ++part) {
+        // part 0: top/bot columns; parts 1, 2: interface columns of the left / right side
+        int ca, cb;
+        const T* zsrc;
+        int64_t zld;
+        if (part == 0) {
+            ca = 0; cb = m2; zsrc = Zg; zld = m2;
+        } else {
+            const int side = part - 1;
+            const int q = side == 0 ? t - 1 : t;
+            ca = max(qa, side * w); cb = min(qb, (side + 1) * w);
+            if (ca >= cb || q < 0 || q >= A.NS - 1) continue;
+            zsrc = A.zi(t, k, side) + (lo - 1) - side * w;   // column index = q0 + jj
+            zld = A.s_pad;
         }
-        V[i * KMAX + r] = v;
-    }
-    // interface contributions, 32 columns at a time, both sides
-    for (int side = 0; side < 2; ++side) {
-        const int q = side == 0 ? t - 1 : t;         // interface index bordering this side
-        if (q < 0 || q >= A.NS - 1) continue;
-        const T* zsrc = A.zi(t, k, side);
-        const T* usrc = P.xi(q);
-        for (int j0 = lo - 1; j0 < hi; j0 += CJ) {
-            const int nj = min(CJ, hi - j0);
+        const T* usrc = part == 0 ? nullptr : P.xi(part == 1 ? t - 1 : t) + (int64_t)((lo - 1) - (part - 1) * w) * kc;
+        for (int q0 = ca; q0 < cb; q0 += CJ) {
+            const int nj = min(CJ, cb - q0);
             __syncthreads();
             for (int idx = tid; idx < m * CJ; idx += nth) {
                 const int i = idx / CJ, jj = idx % CJ;
-                zc[i * (CJ + 1) + jj] = jj < nj ? zsrc[(int64_t)i * A.s_pad + j0 + jj] : T(0);
+                zc[i * (CJ + 1) + jj] = jj < nj ? zsrc[(int64_t)i * zld + q0 + jj] : T(0);
             }
             for (int idx = tid; idx < CJ * K; idx += nth) {
                 const int jj = idx / K, r = idx % K;
-                uc[jj * KMAX + r] = jj < nj ? usrc[(int64_t)(j0 + jj) * kc + r] : T(0);
+                T v = T(0);
+                if (jj < nj) {
+                    const int col = q0 + jj;
+                    if (part == 0) {
+                        const T* xv = col < m ? xt : xb;
+                        v = xv ? xv[(col % m) * kc + r] : T(0);
+                    } else {
+                        v = usrc[(int64_t)col * kc + r];
+                    }
+                }
+                uc[jj * KMAX + r] = v;
             }
             __syncthreads();
             for (int idx = tid; idx < m * K; idx += nth) {
@@ -383,13 +403,40 @@ __global__ void __launch_bounds__(TB_THREADS) tree_down_kernel(SolveArgs<T> P, i
                 T acc = T(0);
 #pragma unroll
                 for (int jj = 0; jj < CJ; ++jj) acc += zc[i * (CJ + 1) + jj] * uc[jj * KMAX + r];
-                V[i * KMAX + r] -= acc;
+                V[i * KMAX + r] += acc;
             }
         }
     }
     __syncthreads();
-    // x = Li^T V in place: a thread owns a right-hand side, rows from the top
-    for (int r = tid; r < K; r += nth)
+    if (nch > 1) {
+        T* wsn = ws + ((int64_t)(t * gridDim.x + blockIdx.x) * nch) * m * KMAX;
+        for (int idx = tid; idx < m * K; idx += nth)
+            wsn[(int64_t)blockIdx.y * m * KMAX + idx] = V[(idx / K) * KMAX + idx % K];
+        __threadfence();
+        __syncthreads();
+        unsigned* tk = tickets + (int64_t)t * gridDim.x + blockIdx.x;
+        if (tid == 0) last = atomicAdd(tk, 1u) == (unsigned)(nch - 1);
+        __syncthreads();
+        if (!last) return;
+        __threadfence();
+        for (int idx = tid; idx < m * K; idx += nth) {
+            T v = T(0);
+            for (int ch = 0; ch < nch; ++ch) v += __ldcg(wsn + (int64_t)ch * m * KMAX + idx);
+            V[(idx / K) * KMAX + idx % K] = v;
+        }
+        if (tid == 0) *tk = 0;
+    }
+    // finish the node: V = y - V;  x = Li^T V
+    const T* Lg = A.linv(t, c);
+    for (int idx = tid; idx < m * m; idx += nth) Li[(idx / m) * SP + idx % m] = Lg[idx];
+    const T* yv = P.yv(t, c);
+    __syncthreads();
+    for (int idx = tid; idx < m * K; idx += nth) {
+        const int i = idx / K, r = idx % K;
+        V[i * KMAX + r] = yv[i * kc + r] - V[i * KMAX + r];
+    }
+    __syncthreads();
+    for (int r = tid; r < K; r += nth)       // x = Li^T V in place, rows from the top
         for (int i = 0; i < m; ++i) {
             T acc = T(0);
             for (int l = i; l < m; ++l) acc += Li[l * SP + i] * V[l * KMAX + r];
@@ -400,11 +447,14 @@ __global__ void __launch_bounds__(TB_THREADS) tree_down_kernel(SolveArgs<T> P, i
     const int64_t N = (int64_t)s * s;
     for (int idx = tid; idx < m * K; idx += nth) {
         const int i = idx / K, r = idx % K;
-        const T acc = V[i * KMAX + r];
-        xd[i * kc + r] = acc;
+        xd[i * kc + r] = V[i * KMAX + r];
+    }
+    for (int idx = tid; idx < m * K; idx += nth) {   // consecutive threads write consecutive x
+        const int r = idx / m, i = idx % m;
+        const double v = (double)V[i * KMAX + r];
         double* up = U + (int64_t)(r0 + r) * N + (int64_t)(c - 1) * s + (x0 - 1 + i);
-        if (accumulate) *up += (double)acc;
-        else *up = (double)acc;
+        if (accumulate) *up += v;
+        else *up = v;
     }
 }
 
@@ -536,8 +586,10 @@ slab_status tree_down_scatter(slab_handle* h, double* U, int accumulate, int r0,
     for (int k = d.H - 1; k >= 0; --k) {
         const int cnt = tree_nodes_at(d.s, k);
         if (!cnt) continue;
-        dim3 grid(cnt, 1, d.NS);
-        tree_down_kernel<T><<<grid, TB_THREADS, 0, h->stream>>>(p, k, U, accumulate, r0);
+        const int wmax = min(d.s, (1 << (k + 1)) - 1);
+        dim3 grid(cnt, (2 * wmax + DCW - 1) / DCW, d.NS);
+        tree_down_kernel<T><<<grid, TB_THREADS, 0, h->stream>>>(p, k, U, accumulate, r0, (T*)h->wVp,
+                                                                 (unsigned*)h->wVtk);
         SLAB_CK_LAUNCH(h);
     }
     dim3 g2((unsigned)(((int64_t)d.s * K + 255) / 256), d.NI);
@@ -565,6 +617,21 @@ slab_status import_utilde_part(slab_handle* h, const double* in, int r0, int K) 
 }
 
 int tree_kmax() { return KMAX; }
+
+// Scratch elements of the down-pass partial sums (largest height with split nodes) and tickets.
+size_t tree_down_ws_elems(int s, int m, int NS) {
+    size_t best = 0;
+    const int H = tree_height_count(s);
+    for (int k = 0; k < H; ++k) {
+        const int wmax = min(s, (1 << (k + 1)) - 1);
+        const int nch = (2 * wmax + DCW - 1) / DCW;
+        if (nch <= 1) continue;
+        const size_t e = (size_t)NS * tree_nodes_at(s, k) * nch * m * KMAX;
+        if (e > best) best = e;
+    }
+    return best;
+}
+size_t tree_down_tickets(int s, int NS) { return (size_t)NS * (s / 2 + 1); }
 
 template slab_status tree_factor<float>(slab_handle*);
 template slab_status tree_factor<double>(slab_handle*);
