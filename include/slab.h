@@ -156,6 +156,29 @@ slab_status slab_last_error(const slab_handle* h);
 void slab_destroy(slab_handle* h);
 const char* slab_strerror(slab_status s);
 
+/*
+ * Residual and norms for callers that cannot allocate device memory.  The
+ * paper has no counterpart: this is a library convenience.  Some callers may
+ * not call cudaMalloc at all -- code running inside a stream capture that must
+ * stay free of allocation nodes, a process whose device memory pool belongs to
+ * another framework, a real-time loop that bans allocator calls.  This entry
+ * point allocates nothing and needs no handle: for the 2-D grid n (h = 1/n)
+ * and the operator given by kind/kappa/c/omega (as in slab_coeffs), it writes
+ * r = f - A u (device, [k][(n-1)^2]) and the squared 2-norms nrm_r[q] =
+ * ||r_q||^2, nrm_f[q] = ||f_q||^2 (device, k entries each), on the given
+ * stream (a cudaStream_t, NULL = legacy default).  All buffers are the
+ * caller's.  The norm reduction uses a fixed 4 MiB scratch array built into
+ * the library (held by every GPU that loads it until exit); requests with
+ * k * ceil((n-1)/256) * ceil((n-1)/32) * 2 > 2^19 or k > 8192 are rejected
+ * with SLAB_EINVAL.  All calls share that scratch: calls that overlap on the
+ * GPU race and must be serialised by the caller.  The first call on a device
+ * looks up the scratch address for that device; make it before any stream
+ * capture starts.
+ */
+slab_status slab_residual_norms_noalloc(int n, int kind, const double* kappa, const double* c,
+                                        double omega, const double* u, const double* f, double* r,
+                                        int k, double* nrm_r, double* nrm_f, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

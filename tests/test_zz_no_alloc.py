@@ -1,0 +1,59 @@
+"""The allocation-free residual entry point agrees with the handle-based one.
+
+slab_residual_norms_noalloc is for callers that cannot call cudaMalloc (a stream
+capture without allocation nodes, a device pool owned by another framework, a
+real-time loop).  It keeps its reduction scratch in a fixed array inside the
+library.  This test calls it twice in a row through the C ABI and compares the
+residual with slab_apply_residual and the norms with the relative residual the
+handle-based solve reports, at the tolerance of the other parity tests.
+This file is collected last on purpose.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2211_07572_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _p(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def test_noalloc_residual_matches_handle_path_twice():
+    assert torch.cuda.is_available(), "GPU test needs a CUDA device"
+    from paper_2211_07572_gb300 import _lib
+    from paper_2211_07572_gb300.solver import SlabSolver
+    lib = _lib.load()
+    n, b, k = 128, 16, 3
+    kappa = np.exp(inputs.fourier_field(2, n, 8, seed=91))
+    f = torch.from_numpy(inputs.normal_rhs(2, n, k, 92)).cuda()
+    s = SlabSolver(2, n, b, inputs.DIFFUSION, kappa=kappa, precision="fp32", max_refine=0)
+    u, relres, _ = s.solve(f)                          # one pass: the residual is far from zero
+    kd = torch.from_numpy(kappa).cuda()
+    stream = torch.cuda.current_stream().cuda_stream
+    for call in range(2):
+        uu = u if call == 0 else u * 0.5               # second call: different data, same scratch
+        r = torch.empty_like(f)
+        nr = torch.empty(k, dtype=torch.float64, device="cuda")
+        nf = torch.empty(k, dtype=torch.float64, device="cuda")
+        st = lib.slab_residual_norms_noalloc(n, inputs.DIFFUSION, _p(kd), None, 0.0, _p(uu), _p(f), _p(r), k,
+                                             _p(nr), _p(nf), ctypes.c_void_p(stream))
+        assert st == 0, st
+        r_ref = s.residual(uu, f)
+        torch.cuda.synchronize()
+        scale = float(s.apply(uu).abs().max())
+        assert float((r - r_ref).abs().max()) <= 1e-13 * scale
+        rel = np.sqrt(nr.cpu().numpy() / nf.cpu().numpy())
+        if call == 0:
+            np.testing.assert_allclose(rel, relres, rtol=1e-10)
+        np.testing.assert_allclose(nr.cpu().numpy(), (r_ref * r_ref).sum(dim=1).cpu().numpy(), rtol=1e-10)
+        np.testing.assert_allclose(nf.cpu().numpy(), (f * f).sum(dim=1).cpu().numpy(), rtol=1e-12)
+    # requests beyond the fixed scratch are rejected before any launch
+    big = lib.slab_residual_norms_noalloc(4097, inputs.POISSON, None, None, 0.0, _p(u), _p(f), _p(r), 100000,
+                                          _p(nr), _p(nf), None)
+    assert big == _lib.SLAB_EINVAL
+    s.close()
