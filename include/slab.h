@@ -144,6 +144,21 @@ slab_status slab_interior_solve(slab_handle* h, const double* f, const double* u
  */
 slab_status slab_get_T_block(slab_handle* h, int which, int q, double* out);
 
+/*
+ * Dense building block of the Stage-2 kernels, exposed for direct use and testing:
+ * C = alpha A B^T + beta C on the tensor cores (tcgen05, TMA-fed, FP32 accumulation in
+ * tensor memory).  A: M x K, B: N x K, C: M x N, all FP32 row-major on the device with
+ * leading dimensions lda, ldb, ldc (elements); trans_c = 1 writes C^T instead (C is then
+ * N x M with leading dimension ldc).  split = 1 multiplies with three TF32 products
+ * (hi*hi + hi*lo + lo*hi), which keeps FP32 accuracy; split = 0 uses one TF32 product.
+ * Requires K % 32 == 0, lda, ldb multiples of 4 and 16-byte aligned A and B (SLAB_EINVAL
+ * otherwise).  dev_err: device word, bit 2 is set if a bounded device wait gave up.
+ * Asynchronous on stream.  Used in the paper's sense by Algorithm 1 (Sec. 4) products.
+ */
+slab_status slab_tc_gemm(int M, int N, int K, float alpha, const float* A, int64_t lda, const float* B,
+                         int64_t ldb, float beta, float* C, int64_t ldc, int trans_c, int split,
+                         unsigned* dev_err, void* stream);
+
 /* Sizes: unknowns (n-1)^d, interface size (n-1)^(d-1), number of interfaces N_I. */
 slab_status slab_sizes(const slab_handle* h, int64_t* unknowns, int64_t* iface_size, int* n_ifaces);
 

@@ -56,6 +56,8 @@ SIGNATURES = {
     "slab_last_error": (c_int, [c_void_p]),
     "slab_destroy": (None, [c_void_p]),
     "slab_strerror": (ctypes.c_char_p, [c_int]),
+    "slab_tc_gemm": (c_int, [c_int, c_int, c_int, ctypes.c_float, c_void_p, c_int64, c_void_p, c_int64,
+                             ctypes.c_float, c_void_p, c_int64, c_int, c_int, c_void_p, c_void_p]),
     "slab_residual_norms_noalloc": (c_int, [c_int, c_int, c_void_p, c_void_p, c_double, c_void_p, c_void_p,
                                             c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
 }

@@ -138,6 +138,21 @@ template <typename T> slab_status assemble_T(slab_handle* h);
 template <typename T> slab_status sweep_factor(slab_handle* h);
 template <typename T> slab_status sweep_solve(slab_handle* h, int K);
 
+// tensor-core product (tcgemm.cu): C = alpha A B^T + beta C, FP32, A [M][K], B [N][K] row-major
+struct TcGemmArgs {
+    int M, N, K;
+    float alpha, beta;
+    const float* A; int64_t lda;
+    const float* B; int64_t ldb;
+    float* C; int64_t ldc;
+    int transC;          // 1: write C^T, i.e. C[col * ldc + row]
+    int split;           // 1: 3xTF32 (FP32 accuracy), 0: plain TF32
+    int lower_only;      // skip 128 x BN tiles strictly above the diagonal
+    int batch;           // independent products, A/B/C batch strides sA/sB/sC (elements)
+    int64_t sA, sB, sC;
+};
+slab_status tc_gemm(cudaStream_t st, const TcGemmArgs& g, unsigned* err);
+
 // error helper
 slab_status slab_cuda_check(slab_handle* h, cudaError_t e);
 #define SLAB_CK(h, call)                                             \

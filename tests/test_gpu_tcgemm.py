@@ -1,0 +1,51 @@
+"""Tensor-core product (tcgen05 + TMA) against an FP64 reference of the same op."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(M, N, K, alpha, beta, split, trans_c, seed=0):
+    from paper_2211_07572_gb300 import _lib
+    lib = _lib.load()
+    g = torch.Generator().manual_seed(seed)
+    A = torch.randn(M, K, generator=g, dtype=torch.float32)
+    B = torch.randn(N, K, generator=g, dtype=torch.float32)
+    C0 = torch.randn((N, M) if trans_c else (M, N), generator=g, dtype=torch.float32)
+    Ad, Bd, Cd = A.cuda(), B.cuda(), C0.clone().cuda()
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ldc = M if trans_c else N
+    st = lib.slab_tc_gemm(M, N, K, alpha, ctypes.c_void_p(Ad.data_ptr()), K, ctypes.c_void_p(Bd.data_ptr()), K,
+                          beta, ctypes.c_void_p(Cd.data_ptr()), ldc, trans_c, split,
+                          ctypes.c_void_p(err.data_ptr()), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == 0
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    ref = alpha * (A.double() @ B.double().T) + beta * (C0.double().T if trans_c else C0.double())
+    out = Cd.double().cpu()
+    if trans_c:
+        out = out.T
+    # error of the same product done in plain FP32 (the accuracy 3xTF32 is meant to match)
+    ref32 = (alpha * (A @ B.T) + beta * (C0.T if trans_c else C0)).double()
+    e32 = (ref32 - ref).abs().max().item()
+    return (out - ref).abs().max().item() / ref.abs().max().item(), e32 / ref.abs().max().item()
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 128, 32), (300, 200, 256), (512, 64, 2048), (1000, 130, 96)])
+def test_tc_gemm_split_is_fp32_accurate(M, N, K):
+    rel, rel32 = _run(M, N, K, -1.0, 1.0, split=1, trans_c=0)
+    assert rel < max(4 * rel32, 1e-6), (rel, rel32)
+
+
+@pytest.mark.parametrize("M,N,K", [(256, 256, 128), (130, 70, 64)])
+def test_tc_gemm_plain_tf32(M, N, K):
+    rel, _ = _run(M, N, K, 1.0, 0.0, split=0, trans_c=0)
+    assert rel < 5e-3, rel
+
+
+def test_tc_gemm_transposed_output():
+    rel, rel32 = _run(200, 64, 128, 0.5, 2.0, split=1, trans_c=1)
+    assert rel < max(4 * rel32, 1e-6), (rel, rel32)
