@@ -128,6 +128,10 @@ slab_status sync_status(slab_handle* h) {
     SLAB_CK(h, cudaStreamSynchronize(h->stream));
     unsigned st = 0;
     SLAB_CK(h, cudaMemcpy(&st, h->dstatus, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (st & SLAB_DEV_TIMEOUT) {
+        if (h->err == SLAB_OK) h->err = SLAB_ETIMEOUT;
+        return SLAB_ETIMEOUT;
+    }
     if (st & SLAB_DEV_NOTSPD) {
         if (h->err == SLAB_OK) h->err = SLAB_ESINGULAR;
         return SLAB_ESINGULAR;
@@ -178,7 +182,7 @@ void slab_destroy(slab_handle* h) {
     void* p;
     p = h->AX; dfree(p); p = h->AY; dfree(p); p = h->DG; dfree(p); p = h->kappa; dfree(p);
     dfree(h->tLinv); dfree(h->tZtb); dfree(h->tRtb); dfree(h->tZI); dfree(h->tRI);
-    dfree(h->Tb); dfree(h->To); dfree(h->Linv); dfree(h->Y); dfree(h->Swork);
+    dfree(h->Tb); dfree(h->To); dfree(h->Fct); dfree(h->Linv); dfree(h->Y);
     p = h->dstatus; dfree(p);
     delete h;
 }
@@ -244,9 +248,9 @@ slab_status slab_factor(const slab_grid* grid, const slab_coeffs* co, int b, con
     ALLOC(h->tRI, (int64_t)d.NS * d.H * 4 * d.m * d.s_pad * R);
     ALLOC(h->Tb, d.NI * blk * R);
     ALLOC(h->To, (d.NI - 1) * blk * R);
+    ALLOC(h->Fct, d.NI * 3 * blk * R);
     ALLOC(h->Linv, d.NI * blk * R);
     ALLOC(h->Y, (d.NI - 1) * blk * R);
-    ALLOC(h->Swork, blk * R);
     ALLOC(h->dstatus, sizeof(unsigned));
 #undef ALLOC
 #define CK(call)                                                               \

@@ -2,16 +2,21 @@
 // (Sec. 4, Algorithm 1) and the sweeping solve (Algorithm 2).
 //
 // T is symmetric positive definite for the SPD kinds, so Algorithm 1's
-// S_1 = T_11, S_{j+1} = T_{j+1,j+1} - T_{j+1,j} S_j^{-1} T_{j,j+1} is carried
-// out as a block Cholesky: S_j = L_j L_j^T, Y_j = L_j^{-1} T_{j,j+1},
-// S_{j+1} = T_{j+1,j+1} - Y_j^T Y_j.  The stored factors are L_j^{-1} and Y_j, so
-// Algorithm 2 becomes products only:
+// S_1 = T_11, S_{j+1} = T_{j+1,j+1} - T_{j+1,j} S_j^{-1} T_{j,j+1} is carried out as a
+// block Cholesky: S_j = L_j L_j^T, Y_j = L_j^{-1} T_{j,j+1}, S_{j+1} = T_{j+1,j+1} - Y_j^T Y_j.
+//
+// Per interface block j the tall matrix W_j = [S_j ; T_{j+1,j} ; I] (3 s_pad x s_pad, the
+// middle block absent for the final interface) is eliminated column panel by column panel
+// (64 columns): the panel kernel factors the 64 x 64 diagonal tile and multiplies every tile
+// below it by L_kk^{-T}; one product C -= A B^T then updates everything right of the panel.
+// Rows r of the identity block stay zero in columns < r, so panel kb only touches its first
+// (kb+1)*64 rows.  Afterwards the lower blocks of W_j hold Y_j^T and L_j^{-T}, and
+// S_{j+1} = T_{j+1,j+1} - Y_j^T (Y_j^T)^T is one more product.  In FP32 every product runs on
+// the tensor cores (tcgen05, 3xTF32); the FP64 path uses the same structure on SIMT units.
+//
+// Algorithm 2 then needs products only (vectors stored right-hand-side major, [k][s_pad]):
 //   forward   z_j = L_j^{-1} (f_j - Y_{j-1}^T z_{j-1})
 //   backward  u_j = L_j^{-T} (z_j - Y_j u_{j+1}).
-// L_j^{-1} and Y_j come out of one right-looking elimination of [S_j | T_{j,j+1} | I]
-// in 64 x 64 tiles: per tile column a panel kernel (Cholesky of the diagonal
-// tile, its inverse, and the panel / right-hand-side row products) and a
-// trailing-update kernel.
 #include "slab_internal.cuh"
 
 namespace {
@@ -19,7 +24,7 @@ namespace {
 constexpr int TL = SLAB_TILE;   // 64
 constexpr int TLP = TL + 1;
 
-// C(64x64) += alpha * op(A) op(B) over K (multiple of 16); 256 threads, 4x4 per thread.
+// C(64x64) += op(A) op(B) over [k0, k1) (multiple of 16); 256 threads, 4x4 per thread.
 // op(A)(i,k) = TA ? A[k*lda+i] : A[i*lda+k];  op(B)(k,j) = TB ? B[j*ldb+k] : B[k*ldb+j].
 // Columns j >= ncols of B are treated as zero (and not loaded).
 template <typename T, bool TA, bool TB>
@@ -55,69 +60,56 @@ __device__ inline void tile_gemm(T acc[4][4], const T* __restrict__ A, int64_t l
     }
 }
 
-// C = beta C + alpha op(A) op(B), M and K multiples of 64, N arbitrary (<= ldc).
-// tri: 0 full; 1 A lower triangular (k < (row tile + 1) * 64); 2 op(A) upper (k >= row tile * 64);
-// lower_only: skip output tiles above the diagonal.
-template <typename T, bool TA, bool TB>
-__global__ void __launch_bounds__(256) gemm_kernel(int M, int N, int K, T alpha, const T* A,
-                                                   int64_t lda, const T* B, int64_t ldb, T beta,
-                                                   T* C, int64_t ldc, int tri, int lower_only) {
+// SIMT C = beta C + alpha A B^T (A [M][K], B [N][K] row-major), K multiple of 16.
+// transC writes C^T; lower_only skips 64 x 64 output tiles above the diagonal.
+template <typename T>
+__global__ void __launch_bounds__(256) gemm_tn_kernel(int M, int N, int K, T alpha, const T* A, int64_t lda,
+                                                      const T* B, int64_t ldb, T beta, T* C, int64_t ldc,
+                                                      int transC, int lower_only) {
     __shared__ T sA[16 * TLP];
     __shared__ T sB[16 * TLP];
     const int bj = blockIdx.x, bi = blockIdx.y;
     if (lower_only && bj > bi) return;
     const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
-    int k0 = 0, k1 = K;
-    if (tri == 1) k1 = min(K, (bi + 1) * TL);
-    if (tri == 2) k0 = bi * TL;
     T acc[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
-    const T* Ab = TA ? A + (int64_t)bi * TL : A + (int64_t)bi * TL * lda;
-    const T* Bb = TB ? B + (int64_t)bj * TL * ldb : B + (int64_t)bj * TL;
     const int ncols = min(TL, N - bj * TL);
-    tile_gemm<T, TA, TB>(acc, Ab, lda, Bb, ldb, k0, k1, ncols, sA, sB);
+    tile_gemm<T, false, true>(acc, A + (int64_t)bi * TL * lda, lda, B + (int64_t)bj * TL * ldb, ldb, 0, K, ncols,
+                              sA, sB);
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
             const int r = bi * TL + ty + 16 * a, c = bj * TL + tx + 16 * b;
             if (r < M && c < N) {
-                T* p = C + (int64_t)r * ldc + c;
+                T* p = transC ? C + (int64_t)c * ldc + r : C + (int64_t)r * ldc + c;
                 *p = (beta == T(0) ? T(0) : beta * *p) + alpha * acc[a][b];
             }
         }
 }
 
-// Skinny product for the sweeping solve: C (M x N, N <= 64) = beta C + alpha op(A) B, A square
-// M x K.  The K range is split over gridDim.y CTAs per 64-row tile; every CTA writes its partial
-// tile to ws, and the last CTA of a tile (ticket counter) sums the partials in split order, so the
-// result does not depend on scheduling.  tri as in gemm_kernel.
-template <typename T, bool TA>
-__global__ void __launch_bounds__(256) gemm_skinny_kernel(int M, int N, int K, T alpha, const T* A,
-                                                          int64_t lda, const T* B, int64_t ldb, T beta,
-                                                          T* C, int64_t ldc, int tri, T* ws,
-                                                          unsigned* tickets) {
+// SIMT skinny variant (N <= 64) of the same product, K split over gridDim.y CTAs per row tile;
+// partial tiles go to ws and the last CTA of a tile (ticket) adds them in split order.
+template <typename T>
+__global__ void __launch_bounds__(256) gemm_tn_skinny_kernel(int M, int N, int K, T alpha, const T* A,
+                                                             int64_t lda, const T* B, int64_t ldb, T beta, T* C,
+                                                             int64_t ldc, int transC, T* ws, unsigned* tickets) {
     __shared__ T sA[16 * TLP];
     __shared__ T sB[16 * TLP];
     __shared__ bool last;
     const int bi = blockIdx.x, sp = blockIdx.y, KS = gridDim.y;
     const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
     const int kchunk = K / KS;
-    int k0 = sp * kchunk, k1 = k0 + kchunk;
-    if (tri == 1) k1 = min(k1, (bi + 1) * TL);
-    if (tri == 2) k0 = max(k0, bi * TL);
+    const int k0 = sp * kchunk, k1 = k0 + kchunk;
     T acc[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
-    if (k0 < k1) {
-        const T* Ab = TA ? A + (int64_t)bi * TL : A + (int64_t)bi * TL * lda;
-        tile_gemm<T, TA, false>(acc, Ab, lda, B, ldb, k0, k1, N, sA, sB);
-    }
+    tile_gemm<T, false, true>(acc, A + (int64_t)bi * TL * lda, lda, B, ldb, k0, k1, N, sA, sB);
     T* w = ws + ((int64_t)bi * KS + sp) * TL * TL;
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -136,227 +128,194 @@ __global__ void __launch_bounds__(256) gemm_skinny_kernel(int M, int N, int K, T
         for (int q = 0; q < KS; ++q) v += __ldcg(w0 + (int64_t)q * TL * TL + e);
         const int gr = bi * TL + r;
         if (gr < M && c < N) {
-            T* p = C + (int64_t)gr * ldc + c;
+            T* p = transC ? C + (int64_t)c * ldc + gr : C + (int64_t)gr * ldc + c;
             *p = (beta == T(0) ? T(0) : beta * *p) + alpha * v;
         }
     }
     if (tid == 0) tickets[bi] = 0;
 }
 
-// Cholesky of the 64 x 64 tile in smem (lower, stride TLP), L in place, and Li = L^{-1}.
-// 256 threads.  Blocked by 16 columns: warp 0 factors the 16 x 16 diagonal block with warp
-// barriers only, one thread per row solves the panel below it, all threads update the rest.
-// The inverse is formed blockwise: 16 x 16 diagonal inverses (one warp each, one lane per
-// column), then block diagonals d = 1..3 from Li_IJ = -Li_II sum_{K=J}^{I-1} L_IK Li_KJ.
+// Cholesky L L^T = S of the 64 x 64 tile S (smem, stride TLP; lower triangle read) and
+// Li = L^{-1} (written to smem, stride TLP), by 256 threads in 4 x 4 register blocks: thread
+// (ti, tj) keeps block (ti, tj) of the matrix under elimination and of X, which starts as I and
+// ends as L^{-1}.  Block step kt: the diagonal thread factors and inverts its 4 x 4 block
+// (reciprocal square roots refined by one Newton step); the owners of block column kt form
+// L_ik = A_ik L_kk^{-T}, the owners of block row kt of X apply L_kk^{-1}; then every thread
+// applies the rank-4 updates to its blocks (right-looking Cholesky and forward elimination of
+// [S | I] in one sweep, 16 steps with two barriers each).  A non-positive or non-finite pivot
+// sets SLAB_DEV_NOTSPD and continues with 1.
+template <typename T> __device__ __forceinline__ T rsqrt_nr(T a);
+template <> __device__ __forceinline__ float rsqrt_nr<float>(float a) {
+    float r = rsqrtf(a);
+    return r * (1.5f - 0.5f * a * r * r);
+}
+template <> __device__ __forceinline__ double rsqrt_nr<double>(double a) {
+    double r = rsqrt(a);
+    return r * (1.5 - 0.5 * a * r * r);
+}
 template <typename T>
-__device__ void chol_inv_tile(T* S, T* Li, T* W, unsigned* status) {
-    constexpr int NB = 16;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int c0 = 0; c0 < TL; c0 += NB) {
-        if (warp == 0) {
-            for (int k = 0; k < NB; ++k) {
-                const int kk = c0 + k;
-                T d = S[kk * TLP + kk];
-                const bool bad = !(d > T(0)) || !isfinite((double)d);
-                if (bad) d = T(1);
-                d = sqrt(d);
-                __syncwarp();
-                if (lane == k) {
-                    S[kk * TLP + kk] = d;
-                    if (bad) atomicOr(status, SLAB_DEV_NOTSPD);
+__device__ void chol_inv_tile(const T* S, T* Li, unsigned* status) {
+    __shared__ T dinv[16];          // L_kk^{-1} (4x4 lower, row-major)
+    __shared__ T colb[64 * 4];      // column block kt of L: rows x 4
+    __shared__ T xrow[4 * 64];      // row block kt of X: 4 x cols
+    const int t = threadIdx.x, ti = t >> 4, tj = t & 15;
+    T a[4][4], x[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            a[r][c] = S[(4 * ti + r) * TLP + 4 * tj + c];
+            x[r][c] = (ti == tj && r == c) ? T(1) : T(0);
+        }
+    for (int kt = 0; kt < 16; ++kt) {
+        if (ti == kt && tj == kt) {               // 4x4 Cholesky and inverse in registers
+            T l[4][4], li[4][4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) { l[r][c] = T(0); li[r][c] = T(0); }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                T d = a[c][c];
+#pragma unroll
+                for (int p = 0; p < c; ++p) d -= l[c][p] * l[c][p];
+                if (!(d > T(0)) || !isfinite((double)d)) { atomicOr(status, SLAB_DEV_NOTSPD); d = T(1); }
+                const T rd = rsqrt_nr<T>(d);
+                l[c][c] = d * rd;
+#pragma unroll
+                for (int r = c + 1; r < 4; ++r) {
+                    T v = a[r][c];
+#pragma unroll
+                    for (int p = 0; p < c; ++p) v -= l[r][p] * l[c][p];
+                    l[r][c] = v * rd;
                 }
-                if (lane > k && lane < NB) S[(c0 + lane) * TLP + kk] /= d;
-                __syncwarp();
-                if (lane > k && lane < NB) {
-                    const T lik = S[(c0 + lane) * TLP + kk];
-                    for (int j = k + 1; j <= lane; ++j) S[(c0 + lane) * TLP + c0 + j] -= lik * S[(c0 + j) * TLP + kk];
+                li[c][c] = rd;
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+#pragma unroll
+                for (int r = c + 1; r < 4; ++r) {
+                    T v = T(0);
+#pragma unroll
+                    for (int p = c; p < r; ++p) v -= l[r][p] * li[p][c];
+                    li[r][c] = v * li[r][r];
                 }
-                __syncwarp();
-            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) dinv[r * 4 + c] = li[r][c];
         }
         __syncthreads();
-        const int nrow = TL - c0 - NB;
-        if (tid < nrow) {                       // row i: x L_bb^T = S[i, c0:c0+NB]
-            const int i = c0 + NB + tid;
-            T x[NB];
+        if (tj == kt && ti > kt) {                // L_ik = A_ik L_kk^{-T}
+            T o[4][4];
 #pragma unroll
-            for (int j = 0; j < NB; ++j) {
-                T v = S[i * TLP + c0 + j];
+            for (int r = 0; r < 4; ++r)
 #pragma unroll
-                for (int l = 0; l < j; ++l) v -= x[l] * S[(c0 + j) * TLP + c0 + l];
-                x[j] = v / S[(c0 + j) * TLP + c0 + j];
-            }
+                for (int c = 0; c < 4; ++c) {
+                    T v = T(0);
 #pragma unroll
-            for (int j = 0; j < NB; ++j) S[i * TLP + c0 + j] = x[j];
+                    for (int p = 0; p <= c; ++p) v += a[r][p] * dinv[c * 4 + p];
+                    o[r][c] = v;
+                }
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) colb[(4 * ti + r) * 4 + c] = o[r][c];
+        }
+        if (ti == kt && tj <= kt) {               // X_kt,j = L_kk^{-1} X_kt,j
+            T o[4][4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    T v = T(0);
+#pragma unroll
+                    for (int p = 0; p <= r; ++p) v += dinv[r * 4 + p] * x[p][c];
+                    o[r][c] = v;
+                }
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) { x[r][c] = o[r][c]; xrow[r * 64 + 4 * tj + c] = o[r][c]; }
         }
         __syncthreads();
-        for (int idx = tid; idx < nrow * nrow; idx += blockDim.x) {
-            const int i = c0 + NB + idx / nrow, j = c0 + NB + idx % nrow;
-            if (j <= i) {
-                T acc = T(0);
+        if (ti > kt) {
+            T li_[4][4];
 #pragma unroll
-                for (int l = 0; l < NB; ++l) acc += S[i * TLP + c0 + l] * S[j * TLP + c0 + l];
-                S[i * TLP + j] -= acc;
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int p = 0; p < 4; ++p) li_[r][p] = colb[(4 * ti + r) * 4 + p];
+            if (tj > kt && tj <= ti) {            // A_ij -= L_ik L_jk^T
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    T lj[4];
+#pragma unroll
+                    for (int p = 0; p < 4; ++p) lj[p] = colb[(4 * tj + c) * 4 + p];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+#pragma unroll
+                        for (int p = 0; p < 4; ++p) a[r][c] -= li_[r][p] * lj[p];
+                }
+            }
+            if (tj <= kt) {                       // X_ij -= L_ik X_kt,j
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    T xk[4];
+#pragma unroll
+                    for (int p = 0; p < 4; ++p) xk[p] = xrow[p * 64 + 4 * tj + c];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+#pragma unroll
+                        for (int p = 0; p < 4; ++p) x[r][c] -= li_[r][p] * xk[p];
+                }
             }
         }
-        __syncthreads();
     }
-    // zero the strict upper triangle of Li, diagonal-block inverses (warp w < 4 owns block w)
-    for (int idx = tid; idx < TL * TL; idx += blockDim.x) {
-        const int i = idx / TL, j = idx % TL;
-        if (j > i) Li[i * TLP + j] = T(0);
-    }
-    if (warp < 4 && lane < NB) {
-        const int b0 = warp * NB, j = lane;
-        for (int i = j; i < NB; ++i) {
-            T v = (i == j) ? T(1) : T(0);
-            for (int l = j; l < i; ++l) v -= S[(b0 + i) * TLP + b0 + l] * Li[(b0 + l) * TLP + b0 + j];
-            Li[(b0 + i) * TLP + b0 + j] = v / S[(b0 + i) * TLP + b0 + i];
-        }
-        for (int i = 0; i < j; ++i) Li[(b0 + i) * TLP + b0 + j] = T(0);
-    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) Li[(4 * ti + r) * TLP + 4 * tj + c] = (tj <= ti) ? x[r][c] : T(0);
     __syncthreads();
-    for (int dd = 1; dd < TL / NB; ++dd) {
-        const int nblk = TL / NB - dd;         // blocks (I, J = I - dd)
-        // W_IJ = sum_{K=J}^{I-1} L_IK Li_KJ
-        for (int idx = tid; idx < nblk * NB * NB; idx += blockDim.x) {
-            const int bI = dd + idx / (NB * NB), r = (idx / NB) % NB, c = idx % NB;
-            const int bJ = bI - dd;
-            T acc = T(0);
-            for (int K = bJ; K < bI; ++K)
-#pragma unroll
-                for (int l = 0; l < NB; ++l)
-                    acc += S[(bI * NB + r) * TLP + K * NB + l] * Li[(K * NB + l) * TLP + bJ * NB + c];
-            W[(idx / (NB * NB)) * NB * NB + r * NB + c] = acc;
-        }
-        __syncthreads();
-        for (int idx = tid; idx < nblk * NB * NB; idx += blockDim.x) {
-            const int bI = dd + idx / (NB * NB), r = (idx / NB) % NB, c = idx % NB;
-            const int bJ = bI - dd;
-            T acc = T(0);
-#pragma unroll
-            for (int l = 0; l < NB; ++l)
-                acc -= Li[(bI * NB + r) * TLP + bI * NB + l] * W[(idx / (NB * NB)) * NB * NB + l * NB + c];
-            Li[(bI * NB + r) * TLP + bJ * NB + c] = acc;
-        }
-        __syncthreads();
-    }
 }
 
+// Panel of tile column kb of the tall matrix Wt (leading dimension ld): every CTA factors the
+// diagonal tile Wt[kb][kb] and CTA x replaces the tile Wt[kb+1+x][kb] by itself times L_kk^{-T}.
 template <typename T>
-struct SweepArgs {
-    int nt, s_pad;
-    T* Sw;        // S_j under elimination
-    T* Yj;        // right-hand side block -> Y_j (may be null for the last block)
-    T* Bj;        // identity -> L_j^{-1}
-    unsigned* status;
-    __device__ T* sw(int i, int c) const { return Sw + ((int64_t)i * TL) * s_pad + (int64_t)c * TL; }
-    __device__ T* y(int i, int c) const { return Yj + ((int64_t)i * TL) * s_pad + (int64_t)c * TL; }
-    __device__ T* bb(int i, int c) const { return Bj + ((int64_t)i * TL) * s_pad + (int64_t)c * TL; }
-};
-
-// Panel of tile column kb.  blockIdx.x: [0, nP) rows below the diagonal; [nP, nP+nY) Y row-block
-// tiles; [nP+nY, ...) L^{-1} row-block tiles (columns <= kb).
-template <typename T>
-__global__ void __launch_bounds__(256) panel_kernel(SweepArgs<T> P, int kb, int hasY) {
+__global__ void __launch_bounds__(256) panel_kernel(T* Wt, int64_t ld, int kb, unsigned* status) {
     extern __shared__ unsigned char smem_raw[];
     T* S = reinterpret_cast<T*>(smem_raw);
     T* Li = S + TL * TLP;
     T* X = Li + TL * TLP;
-    T* W = X + TL * TLP;                  // 3 x 16 x 16 scratch of the blocked inverse
     const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
-    const int nt = P.nt;
-    const int nP = nt - kb - 1;
-    const int nY = hasY ? nt : 0;
-    int e = blockIdx.x;
-    int kind, idx;
-    if (e < nP) { kind = 0; idx = kb + 1 + e; }
-    else if (e < nP + nY) { kind = 1; idx = e - nP; }
-    else { kind = 2; idx = e - nP - nY; }
-    const T* D = P.sw(kb, kb);
-    for (int i = tid; i < TL * TL; i += 256) S[(i / TL) * TLP + i % TL] = D[(int64_t)(i / TL) * P.s_pad + i % TL];
-    T* src = kind == 0 ? P.sw(idx, kb) : (kind == 1 ? P.y(kb, idx) : P.bb(kb, idx));
-    for (int i = tid; i < TL * TL; i += 256) X[(i / TL) * TLP + i % TL] = src[(int64_t)(i / TL) * P.s_pad + i % TL];
+    const int r = kb + 1 + blockIdx.x;
+    const T* D = Wt + (int64_t)kb * TL * ld + (int64_t)kb * TL;
+    T* src = Wt + (int64_t)r * TL * ld + (int64_t)kb * TL;
+    for (int i = tid; i < TL * TL; i += 256) {
+        S[(i / TL) * TLP + i % TL] = D[(int64_t)(i / TL) * ld + i % TL];
+        X[(i / TL) * TLP + i % TL] = src[(int64_t)(i / TL) * ld + i % TL];
+    }
     __syncthreads();
-    chol_inv_tile<T>(S, Li, W, P.status);
+    chol_inv_tile<T>(S, Li, status);
     T acc[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
-    if (kind == 0) {      // out = X Li^T
-        for (int l = 0; l < TL; ++l) {
-            T av[4], bv[4];
+    for (int l = 0; l < TL; ++l) {        // out = X Li^T
+        T av[4], bv[4];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) av[a] = X[(ty + 16 * a) * TLP + l];
+        for (int a = 0; a < 4; ++a) av[a] = X[(ty + 16 * a) * TLP + l];
 #pragma unroll
-            for (int b = 0; b < 4; ++b) bv[b] = Li[(tx + 16 * b) * TLP + l];
+        for (int b = 0; b < 4; ++b) bv[b] = Li[(tx + 16 * b) * TLP + l];
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
+        for (int a = 0; a < 4; ++a)
 #pragma unroll
-                for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
-        }
-    } else {              // out = Li X
-        for (int l = 0; l < TL; ++l) {
-            T av[4], bv[4];
-#pragma unroll
-            for (int a = 0; a < 4; ++a) av[a] = Li[(ty + 16 * a) * TLP + l];
-#pragma unroll
-            for (int b = 0; b < 4; ++b) bv[b] = X[l * TLP + tx + 16 * b];
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-                for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
-        }
+            for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
     }
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b)
-            src[(int64_t)(ty + 16 * a) * P.s_pad + tx + 16 * b] = acc[a][b];
-}
-
-// Trailing update of tile column kb.  blockIdx.x enumerates: lower trailing tiles of S,
-// then Y tiles (rows > kb, all columns), then L^{-1} tiles (rows > kb, columns <= kb).
-template <typename T>
-__global__ void __launch_bounds__(256) trailing_kernel(SweepArgs<T> P, int kb, int hasY) {
-    __shared__ T sA[16 * TLP];
-    __shared__ T sB[16 * TLP];
-    const int nt = P.nt;
-    const int R = nt - kb - 1;
-    const int nS = R * (R + 1) / 2;
-    const int nY = hasY ? R * nt : 0;
-    int e = blockIdx.x;
-    T acc[4][4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
-    T* C;
-    if (e < nS) {
-        int ii = (int)((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
-        while ((ii + 1) * (ii + 2) / 2 <= e) ++ii;
-        while (ii * (ii + 1) / 2 > e) --ii;
-        const int jj = e - ii * (ii + 1) / 2;
-        const int i = kb + 1 + ii, i2 = kb + 1 + jj;
-        tile_gemm<T, false, true>(acc, P.sw(i, kb), P.s_pad, P.sw(i2, kb), P.s_pad, 0, TL, TL, sA, sB);
-        C = P.sw(i, i2);
-    } else if (e < nS + nY) {
-        e -= nS;
-        const int i = kb + 1 + e / nt, c = e % nt;
-        tile_gemm<T, false, false>(acc, P.sw(i, kb), P.s_pad, P.y(kb, c), P.s_pad, 0, TL, TL, sA, sB);
-        C = P.y(i, c);
-    } else {
-        e -= nS + nY;
-        const int i = kb + 1 + e / (kb + 1), c = e % (kb + 1);
-        tile_gemm<T, false, false>(acc, P.sw(i, kb), P.s_pad, P.bb(kb, c), P.s_pad, 0, TL, TL, sA, sB);
-        C = P.bb(i, c);
-    }
-    const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) C[(int64_t)(ty + 16 * a) * P.s_pad + tx + 16 * b] -= acc[a][b];
+        for (int b = 0; b < 4; ++b) src[(int64_t)(ty + 16 * a) * ld + tx + 16 * b] = acc[a][b];
 }
 
 template <typename T>
@@ -366,105 +325,157 @@ __global__ void set_identity_kernel(T* B, int s_pad) {
     B[idx] = (idx / s_pad == idx % s_pad) ? T(1) : T(0);
 }
 
-template <typename T, bool TA, bool TB>
-slab_status gemm(slab_handle* h, int M, int N, int K, T alpha, const T* A, int64_t lda, const T* B,
-                 int64_t ldb, T beta, T* C, int64_t ldc, int tri, int lower_only) {
-    dim3 grid((N + TL - 1) / TL, M / TL);
-    gemm_kernel<T, TA, TB><<<grid, 256, 0, h->stream>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc,
-                                                        tri, lower_only);
+// out = in^T for an n x n block (both row-major, leading dimension n), 32 x 32 smem tiles.
+template <typename T>
+__global__ void transpose_kernel(const T* __restrict__ in, T* __restrict__ out, int n) {
+    __shared__ T tile[32][33];
+    const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        const int r = by + j, c = bx + threadIdx.x;
+        if (r < n && c < n) tile[j][threadIdx.x] = in[(int64_t)r * n + c];
+    }
+    __syncthreads();
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        const int r = bx + j, c = by + threadIdx.x;
+        if (r < n && c < n) out[(int64_t)r * n + c] = tile[threadIdx.x][j];
+    }
+}
+
+template <typename T>
+slab_status transpose(slab_handle* h, const T* in, T* out, int n) {
+    dim3 grid((n + 31) / 32, (n + 31) / 32);
+    transpose_kernel<T><<<grid, dim3(32, 8), 0, h->stream>>>(in, out, n);
     SLAB_CK_LAUNCH(h);
     return SLAB_OK;
 }
 
-template <typename T, bool TA>
-slab_status gemm_skinny(slab_handle* h, int M, int N, int K, T alpha, const T* A, int64_t lda, const T* B,
-                        int64_t ldb, T beta, T* C, int64_t ldc, int tri) {
-    int KS = K / 256;
-    if (KS < 1) KS = 1;
-    if (KS > SLAB_SPLITK) KS = SLAB_SPLITK;
-    while (K % (KS * 16)) --KS;
-    dim3 grid(M / TL, KS);
-    gemm_skinny_kernel<T, TA><<<grid, 256, 0, h->stream>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, tri,
-                                                           (T*)h->wPart, h->wTickets);
+// C = beta C + alpha A B^T on the unit of this precision: tensor cores for FP32, SIMT for FP64.
+template <typename T>
+slab_status gemm_tn(slab_handle* h, int M, int N, int K, T alpha, const T* A, int64_t lda, const T* B, int64_t ldb,
+                    T beta, T* C, int64_t ldc, int transC, int lower_only);
+
+template <>
+slab_status gemm_tn<float>(slab_handle* h, int M, int N, int K, float alpha, const float* A, int64_t lda,
+                           const float* B, int64_t ldb, float beta, float* C, int64_t ldc, int transC,
+                           int lower_only) {
+    TcGemmArgs g;
+    g.M = M; g.N = N; g.K = K; g.alpha = alpha; g.beta = beta;
+    g.A = A; g.lda = lda; g.B = B; g.ldb = ldb; g.C = C; g.ldc = ldc;
+    g.transC = transC; g.split = 1; g.lower_only = lower_only;
+    g.batch = 1; g.sA = g.sB = g.sC = 0;
+    g.ksplit = 1; g.part = nullptr;
+    if (N <= 64 && !lower_only && h->wPart) {     // skinny: split K over CTAs
+        int ks = 1;
+        while (2 * ks <= SLAB_SPLITK && (M + 127) / 128 * ks < 148 && K % (2 * ks * 32) == 0) ks *= 2;
+        g.ksplit = ks;
+        g.part = (float*)h->wPart;
+    }
+    const slab_status st = tc_gemm(h->stream, g, h->dstatus);
+    if (st == SLAB_ECUDA && h->err == SLAB_OK) h->err = SLAB_ECUDA;
+    return st;
+}
+
+template <>
+slab_status gemm_tn<double>(slab_handle* h, int M, int N, int K, double alpha, const double* A, int64_t lda,
+                            const double* B, int64_t ldb, double beta, double* C, int64_t ldc, int transC,
+                            int lower_only) {
+    if (N <= 64 && !lower_only && h->wTickets) {
+        int KS = K / 256;
+        if (KS < 1) KS = 1;
+        if (KS > SLAB_SPLITK) KS = SLAB_SPLITK;
+        while (K % (KS * 16)) --KS;
+        dim3 grid((M + TL - 1) / TL, KS);
+        gemm_tn_skinny_kernel<double><<<grid, 256, 0, h->stream>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc,
+                                                                   transC, (double*)h->wPart, h->wTickets);
+    } else {
+        dim3 grid((N + TL - 1) / TL, (M + TL - 1) / TL);
+        gemm_tn_kernel<double><<<grid, 256, 0, h->stream>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, transC,
+                                                            lower_only);
+    }
     SLAB_CK_LAUNCH(h);
     return SLAB_OK;
 }
 
 }  // namespace
 
+// Factor-phase layout: Fct[j] = [S_j ; Y_j^T ; L_j^{-T}] (3 s_pad x s_pad; for the last j the
+// L^{-T} block sits right below S), plus the transposed copies Lin[j] = L_j^{-1} and Yn[j] = Y_j
+// for the solve products.
 template <typename T>
 slab_status sweep_factor(slab_handle* h) {
     const int NI = h->td.NI, sp = h->td.s_pad, nt = h->nt;
     const int64_t blk = (int64_t)sp * sp;
     T* Tb = (T*)h->Tb;
     T* To = (T*)h->To;
-    T* Linv = (T*)h->Linv;
-    T* Y = (T*)h->Y;
-    T* Sw = (T*)h->Swork;
-    const size_t smem = (3 * TL * TLP + 3 * 16 * 16) * sizeof(T);
+    T* F = (T*)h->Fct;
+    T* Lin = (T*)h->Linv;
+    T* Yn = (T*)h->Y;
+    const size_t smem = 3 * TL * TLP * sizeof(T);
     SLAB_CK(h, cudaFuncSetAttribute(panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    slab_status st;
     for (int j = 0; j < NI; ++j) {
-        SLAB_CK(h, cudaMemcpyAsync(Sw, Tb + j * blk, blk * sizeof(T), cudaMemcpyDeviceToDevice, h->stream));
-        if (j > 0) {
-            slab_status st = gemm<T, true, false>(h, sp, sp, sp, T(-1), Y + (j - 1) * blk, sp,
-                                                  Y + (j - 1) * blk, sp, T(1), Sw, sp, 0, 1);
-            if (st) return st;
-        }
+        T* W = F + j * 3 * blk;
         const int hasY = j < NI - 1;
-        if (hasY)
-            SLAB_CK(h, cudaMemcpyAsync(Y + j * blk, To + j * blk, blk * sizeof(T), cudaMemcpyDeviceToDevice,
-                                       h->stream));
-        set_identity_kernel<T><<<(unsigned)((blk + 255) / 256), 256, 0, h->stream>>>(Linv + j * blk, sp);
+        T* S = W;
+        T* Yt = W + blk;
+        T* LT = W + (hasY ? 2 : 1) * blk;
+        SLAB_CK(h, cudaMemcpyAsync(S, Tb + j * blk, blk * sizeof(T), cudaMemcpyDeviceToDevice, h->stream));
+        if (j > 0) {           // S_j = T_jj - Y_{j-1}^T Y_{j-1}  (lower tiles)
+            const T* Yp = F + (j - 1) * 3 * blk + blk;
+            if ((st = gemm_tn<T>(h, sp, sp, sp, T(-1), Yp, sp, Yp, sp, T(1), S, sp, 0, 1))) return st;
+        }
+        set_identity_kernel<T><<<(unsigned)((blk + 255) / 256), 256, 0, h->stream>>>(LT, sp);
         SLAB_CK_LAUNCH(h);
-        SweepArgs<T> P;
-        P.nt = nt; P.s_pad = sp; P.Sw = Sw; P.Yj = hasY ? Y + j * blk : nullptr; P.Bj = Linv + j * blk;
-        P.status = h->dstatus;
+        if (hasY && (st = transpose<T>(h, To + j * blk, Yt, sp))) return st;      // T_{j+1,j}
+        const int lt0 = (hasY ? 2 : 1) * sp;         // first row of the identity block
         for (int kb = 0; kb < nt; ++kb) {
-            const int nP = nt - kb - 1, nY = hasY ? nt : 0, nB = kb + 1;
-            panel_kernel<T><<<nP + nY + nB, 256, smem, h->stream>>>(P, kb, hasY);
+            const int rows = lt0 + (kb + 1) * TL;      // identity rows below are still zero here
+            const int nrt = rows / TL - kb - 1;
+            panel_kernel<T><<<nrt, 256, smem, h->stream>>>(W, sp, kb, h->dstatus);
             SLAB_CK_LAUNCH(h);
-            const int R = nt - kb - 1;
-            const int ntr = R * (R + 1) / 2 + (hasY ? R * nt : 0) + R * (kb + 1);
-            if (ntr > 0) {
-                trailing_kernel<T><<<ntr, 256, 0, h->stream>>>(P, kb, hasY);
-                SLAB_CK_LAUNCH(h);
+            const int c0 = (kb + 1) * TL;
+            if (c0 < sp) {
+                const T* P = W + (int64_t)c0 * sp + (int64_t)kb * TL;             // panel rows below the diagonal
+                if ((st = gemm_tn<T>(h, rows - c0, sp - c0, TL, T(-1), P, sp, P, sp, T(1), W + (int64_t)c0 * sp + c0,
+                                     sp, 0, 1)))
+                    return st;
             }
         }
+        if ((st = transpose<T>(h, LT, Lin + j * blk, sp))) return st;
+        if (hasY && (st = transpose<T>(h, Yt, Yn + j * blk, sp))) return st;
     }
     return SLAB_OK;
 }
 
-// Algorithm 2 on the interface workspace X ([NI][s_pad][kcap], columns 0..K-1), result in X.
+// Algorithm 2 on the interface workspace X ([NI][kcap][s_pad], right-hand sides 0..K-1), result in X.
 template <typename T>
 slab_status sweep_solve(slab_handle* h, int K) {
     const int NI = h->td.NI, sp = h->td.s_pad;
     const int64_t blk = (int64_t)sp * sp;
     const int64_t vb = (int64_t)sp * h->kcap;
-    const int ld = h->kcap;
-    T* Linv = (T*)h->Linv;
-    T* Y = (T*)h->Y;
+    T* F = (T*)h->Fct;
+    T* Lin = (T*)h->Linv;
+    T* Yn = (T*)h->Y;
     T* X = (T*)h->wX;
     T* Z = (T*)h->wZ;
     slab_status st;
     for (int j = 0; j < NI; ++j) {        // forward: z_j = L_j^{-1} (f_j - Y_{j-1}^T z_{j-1})
         if (j > 0) {
-            st = gemm_skinny<T, true>(h, sp, K, sp, T(-1), Y + (j - 1) * blk, sp, Z + (j - 1) * vb, ld, T(1),
-                                      X + j * vb, ld, 0);
-            if (st) return st;
+            const T* Yt = F + (j - 1) * 3 * blk + blk;
+            if ((st = gemm_tn<T>(h, sp, K, sp, T(-1), Yt, sp, Z + (j - 1) * vb, sp, T(1), X + j * vb, sp, 1, 0)))
+                return st;
         }
-        st = gemm_skinny<T, false>(h, sp, K, sp, T(1), Linv + j * blk, sp, X + j * vb, ld, T(0), Z + j * vb,
-                                   ld, 1);
-        if (st) return st;
+        if ((st = gemm_tn<T>(h, sp, K, sp, T(1), Lin + j * blk, sp, X + j * vb, sp, T(0), Z + j * vb, sp, 1, 0)))
+            return st;
     }
     for (int j = NI - 1; j >= 0; --j) {   // backward: u_j = L_j^{-T} (z_j - Y_j u_{j+1})
         if (j < NI - 1) {
-            st = gemm_skinny<T, false>(h, sp, K, sp, T(-1), Y + j * blk, sp, X + (j + 1) * vb, ld, T(1),
-                                       Z + j * vb, ld, 0);
-            if (st) return st;
+            if ((st = gemm_tn<T>(h, sp, K, sp, T(-1), Yn + j * blk, sp, X + (j + 1) * vb, sp, T(1), Z + j * vb, sp,
+                                 1, 0)))
+                return st;
         }
-        st = gemm_skinny<T, true>(h, sp, K, sp, T(1), Linv + j * blk, sp, Z + j * vb, ld, T(0), X + j * vb, ld,
-                                  2);
-        if (st) return st;
+        const T* LT = F + j * 3 * blk + (j < NI - 1 ? 2 : 1) * blk;
+        if ((st = gemm_tn<T>(h, sp, K, sp, T(1), LT, sp, Z + j * vb, sp, T(0), X + j * vb, sp, 1, 0))) return st;
     }
     return SLAB_OK;
 }

@@ -27,6 +27,7 @@
 
 // Device-side status word bits (set by kernels, read by the host after a phase).
 #define SLAB_DEV_NOTSPD 1u    // a Cholesky pivot was <= 0 or not finite
+#define SLAB_DEV_TIMEOUT 2u   // a bounded device-side wait gave up (tensor-core pipeline)
 
 struct TreeDims {
     int s;        // rows per slab (= interface size in 2-D)
@@ -64,9 +65,9 @@ struct slab_handle {
     // Stage-2 data
     void* Tb;                 // [NI][s_pad][s_pad]  T_qq (kept as assembled)
     void* To;                 // [NI-1][s_pad][s_pad] T_{q,q+1}
+    void* Fct;                // [NI][3][s_pad][s_pad]: S_j (then L_j), L_j^{-T}, Y_j^T
     void* Linv;               // [NI][s_pad][s_pad] L_j^{-1}, S_j = L_j L_j^T
     void* Y;                  // [NI-1][s_pad][s_pad] Y_j = L_j^{-1} T_{j,j+1}
-    void* Swork;              // [s_pad][s_pad]
 
     unsigned int* dstatus;    // device status word
 
@@ -76,8 +77,8 @@ struct slab_handle {
     void* wGtb;               // [NS][s+1][2][m][k]  condensed top/bot load
     void* wXs;                // [NS][s+1][m][k]     interior solution per row
     void* wFi;                // [NS][2][s_pad][k]   interface load contributions
-    void* wX;                 // [NI][s_pad][k]
-    void* wZ;                 // [NI][s_pad][k]
+    void* wX;                 // [NI][k][s_pad]  interface vectors, right-hand-side major
+    void* wZ;                 // [NI][k][s_pad]
     void* wVp;                // down-pass partial sums of split nodes
     void* wVtk;               // down-pass tickets (self-resetting)
     void* wPart;              // [s_pad/64][SLAB_SPLITK][64][64] skinny-product partial tiles
@@ -150,6 +151,8 @@ struct TcGemmArgs {
     int lower_only;      // skip 128 x BN tiles strictly above the diagonal
     int batch;           // independent products, A/B/C batch strides sA/sB/sC (elements)
     int64_t sA, sB, sC;
+    int ksplit;          // > 1: K split over CTAs, partial sums in part[ksplit][M][N] (batch must be 1)
+    float* part;
 };
 slab_status tc_gemm(cudaStream_t st, const TcGemmArgs& g, unsigned* err);
 

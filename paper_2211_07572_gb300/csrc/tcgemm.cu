@@ -110,14 +110,15 @@ struct TcCfg {
     static constexpr int A_BYTES = BM * BK * 4;
     static constexpr int B_BYTES = BN * BK * 4;
     static constexpr int STAGE_BYTES = (SPLIT ? 2 : 1) * (A_BYTES + B_BYTES);
-    static constexpr int SMEM = STAGES * STAGE_BYTES + 1024;   // + alignment slack
+    static constexpr int EPI_BYTES = 4 * 32 * 33 * 4;            // per-warp 32 x 32 staging tiles
+    static constexpr int SMEM = STAGES * STAGE_BYTES + EPI_BYTES + 1024;   // + alignment slack
 };
 
 template <int BN, bool SPLIT>
 __global__ void __launch_bounds__(256, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N,
                    int K, float alpha, float beta, float* C, int64_t ldc, int64_t c_bstride, int transC,
-                   int lower_only, unsigned* err) {
+                   int lower_only, int ksplit, float* part, unsigned* err) {
     using Cfg = TcCfg<BN, SPLIT>;
     constexpr int STAGES = Cfg::STAGES;
     extern __shared__ __align__(1024) uint8_t tc_smem[];
@@ -125,10 +126,14 @@ __global__ void __launch_bounds__(256, 1)
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int abort_flag;
 
-    const int bn = blockIdx.x, bm = blockIdx.y, bz = blockIdx.z;
+    // with ksplit > 1 (single product), blockIdx.z is the K split: K range [zs K/ksplit, (zs+1) K/ksplit)
+    const int bn = blockIdx.x, bm = blockIdx.y;
+    const int zs = ksplit > 1 ? (int)blockIdx.z : 0;
+    const int bz = ksplit > 1 ? 0 : (int)blockIdx.z;
     if (lower_only && bn * BN >= (bm + 1) * BM) return;        // tile strictly above the diagonal
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nk = K / BK;
+    const int nk = K / ksplit / BK;
+    const int k0 = zs * nk * BK;
     uint8_t* base = (uint8_t*)(((uintptr_t)tc_smem + 1023) & ~(uintptr_t)1023);
     auto a_hi = [&](int s) { return base + s * Cfg::STAGE_BYTES; };
     auto b_hi = [&](int s) { return base + s * Cfg::STAGE_BYTES + Cfg::A_BYTES; };
@@ -162,8 +167,8 @@ __global__ void __launch_bounds__(256, 1)
                     break;
                 }
                 mbar_expect_tx(&full_bar[s], Cfg::A_BYTES + Cfg::B_BYTES);
-                tma_load_3d(a_hi(s), &tmA, &full_bar[s], kt * BK, bm * BM, bz);
-                tma_load_3d(b_hi(s), &tmB, &full_bar[s], kt * BK, bn * BN, bz);
+                tma_load_3d(a_hi(s), &tmA, &full_bar[s], k0 + kt * BK, bm * BM, bz);
+                tma_load_3d(b_hi(s), &tmB, &full_bar[s], k0 + kt * BK, bn * BN, bz);
                 issued = kt + 1;
             }
             if (abort_flag)                                     // let the copies already issued land
@@ -252,17 +257,50 @@ __global__ void __launch_bounds__(256, 1)
             const int rw = warp - 4;
             const int row = bm * BM + rw * 32 + lane;
             float* Cb = C + (int64_t)bz * c_bstride;
+            float* stg = reinterpret_cast<float*>(base + STAGES * Cfg::STAGE_BYTES) + rw * 32 * 33;
 #pragma unroll 1
             for (int cc = 0; cc < BN / 32; ++cc) {
                 float v[32];
                 tmem_ld32(tmem + ((uint32_t)(rw * 32) << 16) + (uint32_t)(cc * 32), v);
-                if (row < M) {
+                if (!transC && ksplit == 1) {
+                    // row-major C: stage the 32 x 32 block, then each lane walks a column of it so
+                    // a warp instruction covers 32 consecutive floats of one row of C; all 32 old
+                    // values are loaded before any store so the loads overlap
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const int col = bn * BN + cc * 32 + j;
-                        if (col < N) {
-                            float* p = transC ? Cb + (int64_t)col * ldc + row : Cb + (int64_t)row * ldc + col;
-                            *p = alpha * v[j] + (beta != 0.f ? beta * *p : 0.f);
+                    for (int j = 0; j < 32; ++j) stg[lane * 33 + j] = v[j];
+                    __syncwarp();
+                    const int col = bn * BN + cc * 32 + lane;
+                    const int row0 = bm * BM + rw * 32;
+                    float old[32];
+#pragma unroll
+                    for (int r = 0; r < 32; ++r)
+                        old[r] = (beta != 0.f && row0 + r < M && col < N) ? Cb[(int64_t)(row0 + r) * ldc + col] : 0.f;
+#pragma unroll
+                    for (int r = 0; r < 32; ++r)
+                        if (row0 + r < M && col < N)
+                            Cb[(int64_t)(row0 + r) * ldc + col] = alpha * stg[r * 33 + lane] + beta * old[r];
+                    __syncwarp();
+                    continue;
+                }
+                if (row < M) {
+                    if (ksplit > 1) {                            // raw partial sums, reduced later
+                        float* pb = part + (int64_t)zs * M * N;
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            const int col = bn * BN + cc * 32 + j;
+                            if (col < N) pb[transC ? (int64_t)col * M + row : (int64_t)row * N + col] = v[j];
+                        }
+                    } else {                                     // C^T: lanes write consecutive rows
+                        float old[32];
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            const int col = bn * BN + cc * 32 + j;
+                            old[j] = (beta != 0.f && col < N) ? Cb[(int64_t)col * ldc + row] : 0.f;
+                        }
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            const int col = bn * BN + cc * 32 + j;
+                            if (col < N) Cb[(int64_t)col * ldc + row] = alpha * v[j] + beta * old[j];
                         }
                     }
                 }
@@ -275,6 +313,20 @@ __global__ void __launch_bounds__(256, 1)
         tc_fence_after();
         tmem_dealloc(tmem, BN);
     }
+}
+
+// C = alpha sum_s part[s] + beta C, part laid out like C (transC: [N][M], else [M][N]), fixed order.
+__global__ void splitk_reduce_kernel(int M, int N, int ks, const float* __restrict__ part, float alpha, float beta,
+                                     float* C, int64_t ldc, int transC) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t tot = (int64_t)M * N;
+    if (e >= tot) return;
+    float v = 0.f;
+    for (int s = 0; s < ks; ++s) v += part[(int64_t)s * tot + e];
+    int64_t idx;
+    if (transC) idx = (e / M) * ldc + (e % M);          // e = col * M + row
+    else idx = (e / N) * ldc + (e % N);                 // e = row * N + col
+    C[idx] = alpha * v + (beta != 0.f ? beta * C[idx] : 0.f);
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -321,10 +373,18 @@ slab_status launch_tc(cudaStream_t st, const TcGemmArgs& g, unsigned* err) {
             return SLAB_ECUDA;
         attr_set = true;
     }
-    dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, g.batch);
+    const int ks = g.ksplit > 1 ? g.ksplit : 1;
+    dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, ks > 1 ? ks : g.batch);
     tc_gemm_kernel<BN, SPLIT><<<grid, 256, smem, st>>>(ta, tb, g.M, g.N, g.K, g.alpha, g.beta, g.C, g.ldc, g.sC,
-                                                       g.transC, g.lower_only, err);
-    return cudaGetLastError() == cudaSuccess ? SLAB_OK : SLAB_ECUDA;
+                                                       g.transC, g.lower_only, ks, g.part, err);
+    if (cudaGetLastError() != cudaSuccess) return SLAB_ECUDA;
+    if (ks > 1) {
+        const int64_t tot = (int64_t)g.M * g.N;
+        splitk_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(g.M, g.N, ks, g.part, g.alpha, g.beta,
+                                                                           g.C, g.ldc, g.transC);
+        if (cudaGetLastError() != cudaSuccess) return SLAB_ECUDA;
+    }
+    return SLAB_OK;
 }
 
 }  // namespace
@@ -333,6 +393,7 @@ slab_status launch_tc(cudaStream_t st, const TcGemmArgs& g, unsigned* err) {
 slab_status tc_gemm(cudaStream_t st, const TcGemmArgs& g, unsigned* err) {
     if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return SLAB_OK;
     if (g.K <= 0 || g.K % BK) return SLAB_EINVAL;
+    if (g.ksplit > 1 && (g.batch != 1 || g.K % (g.ksplit * BK) || !g.part)) return SLAB_EINVAL;
     if (g.lda % 4 || g.ldb % 4 || g.sA % 4 || g.sB % 4) return SLAB_EINVAL;       // 16-byte strides
     if (((uintptr_t)g.A & 15) || ((uintptr_t)g.B & 15)) return SLAB_EINVAL;      // 16-byte base
     const bool narrow = g.N <= 64;
@@ -349,5 +410,6 @@ extern "C" slab_status slab_tc_gemm(int M, int N, int K, float alpha, const floa
     g.A = A; g.lda = lda; g.B = B; g.ldb = ldb; g.C = C; g.ldc = ldc;
     g.transC = trans_c; g.split = split; g.lower_only = 0;
     g.batch = 1; g.sA = g.sB = g.sC = 0;
+    g.ksplit = 1; g.part = nullptr;
     return tc_gemm((cudaStream_t)stream, g, dev_err);
 }

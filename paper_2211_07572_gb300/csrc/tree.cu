@@ -236,13 +236,13 @@ struct SolveArgs {
     T* Gtb;           // [NS][s+1][2][m][kcap]
     T* Xs;            // [NS][s+1][m][kcap]
     T* Fi;            // [NS][2][s_pad][kcap]
-    T* X;             // [NI][s_pad][kcap]
+    T* X;             // [NI][kcap][s_pad]  right-hand-side major
     __device__ int64_t nodeoff(int t, int c) const { return (int64_t)t * (tr.s + 1) + c; }
     __device__ T* yv(int t, int c) const { return Yv + nodeoff(t, c) * tr.m * kcap; }
     __device__ T* gtb(int t, int c, int tb) const { return Gtb + (nodeoff(t, c) * 2 + tb) * tr.m * kcap; }
     __device__ T* xs(int t, int c) const { return Xs + nodeoff(t, c) * tr.m * kcap; }
     __device__ T* fi(int t, int side) const { return Fi + ((int64_t)t * 2 + side) * tr.s_pad * kcap; }
-    __device__ T* xi(int q) const { return X + (int64_t)q * tr.s_pad * kcap; }
+    __device__ T* xi(int q) const { return X + (int64_t)q * tr.s_pad * kcap; }   // [kcap][s_pad]
 };
 
 constexpr int KMAX = 64;   // right-hand sides handled per launch
@@ -375,7 +375,7 @@ __global__ void __launch_bounds__(TB_THREADS) tree_down_kernel(SolveArgs<T> P, i
             zsrc = A.zi(t, k, side) + (lo - 1) - side * w;   // column index = q0 + jj
             zld = A.s_pad;
         }
-        const T* usrc = part == 0 ? nullptr : P.xi(part == 1 ? t - 1 : t) + (int64_t)((lo - 1) - (part - 1) * w) * kc;
+        const T* usrc = part == 0 ? nullptr : P.xi(part == 1 ? t - 1 : t) + ((lo - 1) - (part - 1) * w);
         for (int q0 = ca; q0 < cb; q0 += CJ) {
             const int nj = min(CJ, cb - q0);
             __syncthreads();
@@ -384,7 +384,7 @@ __global__ void __launch_bounds__(TB_THREADS) tree_down_kernel(SolveArgs<T> P, i
                 zc[i * (CJ + 1) + jj] = jj < nj ? zsrc[(int64_t)i * zld + q0 + jj] : T(0);
             }
             for (int idx = tid; idx < CJ * K; idx += nth) {
-                const int jj = idx / K, r = idx % K;
+                const int jj = idx % CJ, r = idx / CJ;
                 T v = T(0);
                 if (jj < nj) {
                     const int col = q0 + jj;
@@ -392,7 +392,7 @@ __global__ void __launch_bounds__(TB_THREADS) tree_down_kernel(SolveArgs<T> P, i
                         const T* xv = col < m ? xt : xb;
                         v = xv ? xv[(col % m) * kc + r] : T(0);
                     } else {
-                        v = usrc[(int64_t)col * kc + r];
+                        v = usrc[(int64_t)r * A.s_pad + col];
                     }
                 }
                 uc[jj * KMAX + r] = v;
@@ -458,7 +458,7 @@ __global__ void __launch_bounds__(TB_THREADS) tree_down_kernel(SolveArgs<T> P, i
     }
 }
 
-// X[q][rr][r] = fscale f[r][rr][x_q] + Fi[q][R][rr][r] + Fi[q+1][L][rr][r]  (padding rows zero)
+// X[q][r][rr] = fscale f[r][rr][x_q] + Fi[q][R][rr][r] + Fi[q+1][L][rr][r]  (padding rows zero)
 template <typename T>
 __global__ void gather_ftilde_kernel(SolveArgs<T> P, const double* F, double fscale, int r0) {
     const TreeArgs<T>& A = P.tr;
@@ -466,7 +466,7 @@ __global__ void gather_ftilde_kernel(SolveArgs<T> P, const double* F, double fsc
     const int K = P.K, kc = P.kcap;
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (int64_t)A.s_pad * K) return;
-    const int rr = (int)(idx / K), r = (int)(idx % K);
+    const int r = (int)(idx / A.s_pad), rr = (int)(idx % A.s_pad);
     T v = T(0);
     if (rr < A.s) {
         const int64_t N = (int64_t)A.s * A.s;
@@ -474,7 +474,7 @@ __global__ void gather_ftilde_kernel(SolveArgs<T> P, const double* F, double fsc
         v = (T)(fscale * F[(int64_t)(r0 + r) * N + (int64_t)rr * A.s + (xq - 1)]);
         v += P.fi(q, 1)[(int64_t)rr * kc + r] + P.fi(q + 1, 0)[(int64_t)rr * kc + r];
     }
-    P.xi(q)[(int64_t)rr * kc + r] = v;
+    P.xi(q)[(int64_t)r * A.s_pad + rr] = v;
 }
 
 template <typename T>
@@ -488,7 +488,7 @@ __global__ void scatter_utilde_kernel(SolveArgs<T> P, double* U, int accumulate,
     const int64_t N = (int64_t)A.s * A.s;
     const int xq = (q + 1) * A.b;
     double* up = U + (int64_t)(r0 + r) * N + (int64_t)rr * A.s + (xq - 1);
-    const double v = (double)P.xi(q)[(int64_t)rr * kc + r];
+    const double v = (double)P.xi(q)[(int64_t)r * A.s_pad + rr];
     if (accumulate) *up += v;
     else *up = v;
 }
@@ -503,7 +503,7 @@ __global__ void export_x_kernel(SolveArgs<T> P, double* out, double scale, int N
     const int r = (int)(idx / per);
     const int64_t rem = idx % per;
     const int q = (int)(rem / A.s), rr = (int)(rem % A.s);
-    out[(int64_t)(r0 + r) * per + rem] = scale * (double)P.xi(q)[(int64_t)rr * P.kcap + r];
+    out[(int64_t)(r0 + r) * per + rem] = scale * (double)P.xi(q)[(int64_t)r * A.s_pad + rr];
 }
 template <typename T>
 __global__ void import_x_kernel(SolveArgs<T> P, const double* in, int NI, int r0) {
@@ -514,7 +514,7 @@ __global__ void import_x_kernel(SolveArgs<T> P, const double* in, int NI, int r0
     const int r = (int)(idx / per);
     const int64_t rem = idx % per;
     const int q = (int)(rem / A.s_pad), rr = (int)(rem % A.s_pad);
-    P.xi(q)[(int64_t)rr * P.kcap + r] =
+    P.xi(q)[(int64_t)r * A.s_pad + rr] =
         rr < A.s ? (T)in[(int64_t)(r0 + r) * NI * A.s + (int64_t)q * A.s + rr] : T(0);
 }
 
