@@ -3,8 +3,11 @@
 Workload (one "step" = the whole hot path): -div(kappa grad u) = f on the unit
 square, n = 2048 (2047^2 unknowns), slab spacing b = 32, kappa = exp(g) with g
 a seeded 16-mode Fourier field of unit variance, 64 right-hand sides f ~ N(0,1);
-FP32 factor (Stage 1 tree, T assembly, Stage 2 block Cholesky sweep) followed
-by the solve with FP64 stencil residual refinement until max relres <= 1e-10.
+FP32 factor (Stage-1 slab trees, T assembly, Stage-2 block Cholesky sweep on the
+tensor cores) followed by the solve with FP64 stencil-residual refinement until
+max relres <= 1e-10.  Inputs are resident in HBM when the timed region starts;
+every step streams several GB of factors and vectors (far more than the 129 MB
+L2), so no explicit L2 flush is needed.
 
 Prints one JSON line.  `--impl reference` times the CPU oracle instead.
 """
@@ -12,7 +15,6 @@ from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import subprocess
 import sys
@@ -23,8 +25,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "factor+solve s at 1e-10 rel. residual vs plain FP64 GPU; dense TFLOP/s % of peak"
-WORKLOAD = dict(workload="2D var-coef diffusion n=2048 b=32 k=64 (kappa=exp(16-mode field)), FP32 factor + FP64 refinement",
+WORKLOAD = dict(workload="2D var-coef diffusion n=2048 b=32 k=64 (kappa=exp(16-mode field), f~N(0,1)), "
+                         "FP32 factor + FP64 refinement to 1e-10",
                 n=2048, b=32, k=64, rtol=1e-10)
+SMS = 152
+FP32_LANES_PER_SM = 128
 
 
 def _peaks():
@@ -39,7 +44,6 @@ class ClockSampler:
 
     def __init__(self):
         self.samples = []
-        self._stop = threading.Event()
         self._proc = None
 
     def start(self):
@@ -70,20 +74,96 @@ class ClockSampler:
                 self._proc.kill()
 
     def summary(self):
-        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
-        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = sorted(x for x in (num(s[0]) for s in self.samples) if x is not None)
+        mx = [x for x in (num(s[1]) for s in self.samples) if x is not None]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for s in self.samples for i in range(4) if s[3 + i].lower() == "active"})
-        sm_sorted = sorted(sm)
-        return {"sm_mhz": sm_sorted[len(sm_sorted) // 2] if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(self.samples)}
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
 
 
-def a4_flops(s_pad: int, NI: int) -> float:
-    """Algorithmic flops of the Stage-2 block Cholesky sweep (per interface block: Cholesky s^3/3,
-    triangular inverse s^3/3, Y = L^-1 T_{j,j+1} s^3, Schur update Y^T Y s^3 on the lower half)."""
-    s = float(s_pad)
-    return NI * (s ** 3 / 3 + s ** 3 / 3) + (NI - 1) * (s ** 3 + s ** 3)
+# ----------------------------------------------------------------------------- algorithmic work model
+def tree_nodes(s):
+    """(c, k, w) of every node of the ruler tree over rows 1..s."""
+    out = []
+    k = 0
+    while (1 << k) <= s:
+        p = 1 << k
+        c = p
+        while c <= s:
+            lo, hi = c - p + 1, min(s, c + p - 1)
+            out.append((c, k, hi - lo + 1))
+            c += 2 * p
+        k += 1
+    return out
+
+
+def work_model(n, b, k, passes):
+    """Algorithmic flops (or bytes) per kernel class for one factor + `passes` solve passes."""
+    s = n - 1
+    sp = (s + 63) // 64 * 64
+    m = b - 1
+    NS, NI = n // b, n // b - 1
+    nodes = tree_nodes(s)
+    W = {}
+    # Stage 1 tree factor: per node Cholesky + inverse (2/3 m^3), Z = Li B (m^2 * 2m), R update (2m)^2 m,
+    # interface columns 2w: z = Li b (m^2), two m x m products (2 m^2)
+    W["tree_factor"] = NS * sum(2 * (2 * m ** 3 / 3 + 2 * m ** 3 + 4 * m ** 3 + 2 * w * 3 * m * m)
+                                for (_, _, w) in nodes)
+    W["assemble_T"] = 4.0 * sp * sp * (2 * NI - 1)                      # bytes of T written (FP32)
+    # Stage 2: panel CTAs (Cholesky+inverse 2/3 * 64^3 + product 2 * 64^3), trailing products, Schur update
+    pan = trail = 0.0
+    for j in range(NI):
+        lt0 = (2 if j < NI - 1 else 1) * sp
+        for kb in range(sp // 64):
+            rows = lt0 + (kb + 1) * 64
+            nrt = rows // 64 - kb - 1
+            pan += nrt * (2 * 64 ** 3 + 2 * 64 ** 3 / 3)
+            c0 = (kb + 1) * 64
+            if c0 < sp:
+                nn = sp - c0
+                trail += 2 * 64 * (nn * (nn + 1) / 2 + (rows - sp) * nn)
+    W["panel"] = pan
+    W["trailing"] = trail
+    W["schur_update"] = (NI - 1) * sp * sp * (sp + 1.0)
+    W["sweep_products"] = passes * (4 * NI - 2) * 2.0 * sp * sp * k
+    W["tree_up"] = passes * NS * k * sum(2 * (m * (m + 1) / 2 + 2 * m * m + 2 * w * m) for (_, _, w) in nodes)
+    W["tree_down"] = passes * NS * k * sum(2 * (2 * m * m + 2 * w * m + m * (m + 1) / 2) for (_, _, w) in nodes)
+    W["stencil"] = passes * 24.0 * s * s * k                            # bytes: read u, f; write r (FP64)
+    return W
+
+
+BOUND = {"tree_factor": "alu", "assemble_T": "hbm", "panel": "alu", "trailing": "tensor",
+         "schur_update": "tensor", "sweep_products": "tensor", "tree_up": "alu", "tree_down": "alu",
+         "stencil": "hbm"}
+
+
+def roofline_for(cls, ms, count, work, peaks, clocks):
+    bound = BOUND.get(cls, "alu")
+    t = ms * 1e-3
+    if bound == "hbm":
+        achieved = work[cls] / t / 1e9
+        peak = peaks.get("hbm_gbs", 6801.0)
+        unit, src = "GB/s", "measured copy bandwidth (MEASURED_PEAKS.json)"
+    elif bound == "tensor":
+        achieved = work[cls] / t / 1e12
+        bf16 = peaks.get("bf16_tflops", 1891.8)
+        peak = bf16 * 1.1 / 2.25
+        unit, src = "TFLOP/s", ("measured bf16 dense x 1.1/2.25 (tf32 nominal ratio); algorithmic FP32 flops, "
+                                "the 3xTF32 split executes 3 MMAs per flop")
+    else:
+        mhz = peaks.get("sm_max_mhz", 2070.0)
+        achieved = work[cls] / t / 1e12
+        peak = SMS * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+        unit, src = "TFLOP/s", f"FP32 FMA issue rate {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x {mhz:.0f} MHz"
+    return {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
+            "traffic": None, "kernel": cls, "launches": count, "avg_launch_us": ms * 1e3 / max(count, 1),
+            "peak_source": src}
 
 
 def run_gpu(args):
@@ -108,74 +188,76 @@ def run_gpu(args):
     stream = torch.cuda.current_stream(dev)
     prec = args.precision
 
-    def step(f_in, u_out):
-        s = SlabSolver(2, n, b, inputs.DIFFUSION, kappa=kappa, precision=prec, rtol=W["rtol"], max_refine=40,
-                       stream=stream, device=dev)
+    def make():
+        return SlabSolver(2, n, b, inputs.DIFFUSION, kappa=kappa, precision=prec, rtol=W["rtol"], max_refine=40,
+                          stream=stream, device=dev)
+
+    def step(f_in, u_out, counts=None):
+        s = make()
         _, rel, it = s.solve(f_in, u_out, allow_noconv=True)
+        if counts is not None:
+            counts.append(sum(s.profile_read()[1].values()))
         s.close()
         return rel, it
 
     if args.once:
-        # a single step, for profilers (no timing claims)
         rel, it = step(f, u)
         torch.cuda.synchronize()
         print(json.dumps({"once": True, "config": W, "max_relres": float(np.max(rel)), "refine_steps": it}))
         return
     for _ in range(args.warmup):
         rel, it = step(f, u)
-    # L2 is flushed implicitly: every step streams > 10 GB of factors and vectors (>> 129 MB L2)
     sampler = ClockSampler()
     sampler.start()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    rels, its = [], []
+    rels, its, launches = [], [], []
     for _ in range(args.steps):
-        rel, it = step(f, u)
+        rel, it = step(f, u, launches)
         rels.append(float(np.max(rel)))
         its.append(it)
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
-    # end to end through the public API with host buffers: H2D of f, D2H of u inside the region
+    # end to end through the public API with host buffers: H2D of f and D2H of u inside the region
     u_host = torch.empty_like(f_host).pin_memory()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(max(1, args.steps // 2)):
+    ne2e = max(1, args.steps // 2)
+    for _ in range(ne2e):
         fd = f_host.to(dev, non_blocking=True)
         ud = torch.empty_like(fd)
         step(fd, ud)
         u_host.copy_(ud, non_blocking=True)
         torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / max(1, args.steps // 2)
+    e2e_s = (time.perf_counter() - t0) / ne2e
     sampler.stop()
     clocks = sampler.summary()
 
-    # phase split of one extra step (events between phases)
-    s_pad = (n - 1 + 63) // 64 * 64
-    NI = n // b - 1
-    t_fac = torch.cuda.Event(enable_timing=True)
+    # one instrumented step: phase split and per-kernel-class device time (events on the launch stream)
     t_f0 = torch.cuda.Event(enable_timing=True)
+    t_fac = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
     t_f0.record(stream)
     s = SlabSolver(2, n, b, inputs.DIFFUSION, kappa=kappa, precision=prec, rtol=W["rtol"], max_refine=40,
-                   stream=stream, device=dev)
+                   stream=stream, device=dev, profile=True)
     t_fac.record(stream)
     _, rel1, it1 = s.solve(f, u, allow_noconv=True)
-    t_end = torch.cuda.Event(enable_timing=True)
     t_end.record(stream)
     torch.cuda.synchronize()
+    cls_ms, cls_cnt = s.profile_read()
+    s.close()
     factor_ms = t_f0.elapsed_time(t_fac)
     solve_ms = t_fac.elapsed_time(t_end)
-    s.close()
-
+    passes = it1 + 1
+    work = work_model(n, b, k, passes)
     peaks = _peaks()
-    flops = a4_flops(s_pad, NI)
-    # the factor phase is the dominant dense part; report its FP32 SIMT rate against the
-    # tf32 tensor peak derived from the measured bf16 peak (nominal ratio 1.1 / 2.25)
-    bf16 = peaks.get("bf16_tflops")
-    tf32_peak = bf16 * 1.1 / 2.25 if bf16 else 1891.8 * 1.1 / 2.25
-    achieved = flops / (factor_ms * 1e-3) / 1e12
+    dom = max((c for c in cls_ms if c in BOUND), key=lambda c: cls_ms[c])
+    roof = roofline_for(dom, cls_ms[dom], cls_cnt[dom], work, peaks, clocks)
+    dense = {c: roofline_for(c, cls_ms[c], cls_cnt[c], work, peaks, clocks)
+             for c in ("trailing", "schur_update", "sweep_products") if cls_ms.get(c, 0) > 0}
     line = {
         "metric": METRIC,
         "value": ms / 1e3,
@@ -187,24 +269,55 @@ def run_gpu(args):
         "higher_is_better": False,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32 factor / f64 refinement" if prec == "fp32" else "f64",
+        "dtype": "f32 factor (3xTF32 tensor products) / f64 residual+refinement" if prec == "fp32" else "f64",
         "data": "synthetic",
-        "config": dict(W, precision=prec, l2="inputs and factors >> L2 (no explicit flush)"),
+        "config": dict(W, precision=prec, l2="every step streams > 10 GB (>> 129 MB L2); no explicit flush"),
         "max_relres": max(rels),
         "refine_steps": its,
         "phase_ms": {"factor": factor_ms, "solve_refine": solve_ms},
-        "roofline": {"bound": "tensor", "achieved": achieved, "peak": tf32_peak, "unit": "TFLOP/s",
-                     "frac": achieved / tf32_peak, "traffic": None,
-                     "kernel": "Stage-2 sweep factor (whole factor phase timed)",
-                     "peak_source": "measured bf16 x 1.1/2.25 (tf32)"},
+        "kernel_ms": {c: round(v, 3) for c, v in cls_ms.items()},
+        "kernel_launches": cls_cnt,
+        "roofline": roof,
+        "dense_rooflines": dense,
         "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(f_host.numel() * 8),
                 "d2h_bytes_per_step": int(u_host.numel() * 8)},
-        "gpu_launches": None,
+        "gpu_launches": int(np.mean(launches)) if launches else None,
         "clocks": clocks,
     }
+    if args.fp64_comparator and prec == "fp32":
+        line["fp64_gpu"] = fp64_comparator(n, b, kappa, f, stream, dev)
+        line["fp64_gpu"]["mixed_speedup"] = line["fp64_gpu"]["value"] / line["value"]
     if args.cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(n, b, k)
     print(json.dumps(line))
+
+
+def fp64_comparator(n, b, kappa, f, stream, dev):
+    """Plain FP64 GPU path: same algorithm, all FP64, one pass (no refinement)."""
+    import numpy as np
+    import torch
+
+    from paper_2211_07572_gb300 import inputs
+    from paper_2211_07572_gb300.solver import SlabSolver
+    u = torch.empty_like(f)
+
+    def one():
+        s = SlabSolver(2, n, b, inputs.DIFFUSION, kappa=kappa, precision="fp64", rtol=1.0, max_refine=0,
+                       stream=stream, device=dev)
+        _, rel, _ = s.solve(f, u)
+        s.close()
+        return rel
+
+    one()                                                    # warm-up
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    rel = one()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return {"value": e0.elapsed_time(e1) / 1e3, "unit": "s", "max_relres": float(np.max(rel)),
+            "path": "FP64 factor and solve on the same kernels (SIMT FP64), single pass"}
 
 
 def cpu_baseline(n_full, b, k, n_sample=512):
@@ -238,7 +351,7 @@ def run_reference(args):
     vals = []
     t0 = time.perf_counter()
     for _ in range(args.warmup):
-        cpu_baseline(n, b, k, n_sample=256)
+        cpu_baseline(n, b, k, n_sample=128)
     for _ in range(args.steps):
         vals.append(cpu_baseline(n, b, k, n_sample=args.ref_n))
     v = sum(x["value"] for x in vals) / len(vals)
@@ -264,8 +377,12 @@ def main():
     ap.add_argument("--k", type=int, default=0)
     ap.add_argument("--ref-n", type=int, default=512)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-fp64", dest="fp64_comparator", action="store_false")
     ap.add_argument("--once", action="store_true", help="run one step only (for profilers)")
     args = ap.parse_args()
+    if args.gpus != 1:
+        # one GPU per run here: the method's multi-GPU form is replicas of independent problems
+        pass
     if args.impl == "reference":
         run_reference(args)
     else:

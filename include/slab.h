@@ -81,6 +81,7 @@ typedef struct {
     int max_refine;         /* refinement steps after the first solve (0: a single pass) */
     int krylov;             /* reserved: 0 */
     void* stream;           /* cudaStream_t all work is ordered on (NULL: legacy default) */
+    int profile;            /* 1: time every kernel launch from the start (see slab_profile) */
 } slab_opts;
 
 typedef struct slab_handle slab_handle;
@@ -158,6 +159,23 @@ slab_status slab_get_T_block(slab_handle* h, int which, int q, double* out);
 slab_status slab_tc_gemm(int M, int N, int K, float alpha, const float* A, int64_t lda, const float* B,
                          int64_t ldb, float beta, float* C, int64_t ldc, int trans_c, int split,
                          unsigned* dev_err, void* stream);
+
+/*
+ * Measurement support.  Kernel classes of the library, for per-class timing:
+ *   0 coefficient setup (A0), 1 slab tree factor (A1/A2), 2 T assembly (A3),
+ *   3 panel factor of Stage 2 (A4), 4 Stage-2 trailing update (A4, tensor cores in FP32),
+ *   5 Stage-2 Schur update S_{j+1} = T - Y^T Y (A4), 6 interface sweep products (A6),
+ *   7 tree up pass + reduced load (A5), 8 tree down pass (A7), 9 FP64 stencil residual (A8),
+ *   10 other (transposes, reductions, scatter/gather, gradient).
+ * slab_profile(h, 1) starts recording a CUDA event pair around every launch on the handle's
+ * stream; slab_profile_read fills ms[c] (summed device time) and launches[c] (HOST arrays
+ * of n <= SLAB_KERNEL_CLASSES entries) for the launches since the previous read, then
+ * clears the record; it synchronises the stream.  Launch counts are kept even when timing
+ * is off.  Timing adds an event record per launch; keep it off for timed runs.
+ */
+#define SLAB_KERNEL_CLASSES 11
+slab_status slab_profile(slab_handle* h, int enable);
+slab_status slab_profile_read(slab_handle* h, double* ms, int64_t* launches, int n);
 
 /* Sizes: unknowns (n-1)^d, interface size (n-1)^(d-1), number of interfaces N_I. */
 slab_status slab_sizes(const slab_handle* h, int64_t* unknowns, int64_t* iface_size, int* n_ifaces);

@@ -11,6 +11,8 @@ c_int, c_double, c_void_p, c_int64 = ctypes.c_int, ctypes.c_double, ctypes.c_voi
 
 SLAB_OK, SLAB_EINVAL, SLAB_ENOMEM, SLAB_ESINGULAR, SLAB_ENOCONV, SLAB_ETIMEOUT, SLAB_ECUDA, SLAB_EUNSUPPORTED = range(8)
 POISSON, DIFFUSION, HELMHOLTZ = 0, 1, 2
+KERNEL_CLASSES = ("coeff", "tree_factor", "assemble_T", "panel", "trailing", "schur_update", "sweep_products",
+                  "tree_up", "tree_down", "stencil", "other")
 PREC_FP64, PREC_FP32 = 0, 1
 
 
@@ -24,7 +26,7 @@ class SlabCoeffs(ctypes.Structure):
 
 class SlabOpts(ctypes.Structure):
     _fields_ = [("factor_prec", c_int), ("pivot", c_int), ("rtol", c_double), ("max_refine", c_int),
-                ("krylov", c_int), ("stream", c_void_p)]
+                ("krylov", c_int), ("stream", c_void_p), ("profile", c_int)]
 
 
 class SlabError(RuntimeError):
@@ -56,6 +58,8 @@ SIGNATURES = {
     "slab_last_error": (c_int, [c_void_p]),
     "slab_destroy": (None, [c_void_p]),
     "slab_strerror": (ctypes.c_char_p, [c_int]),
+    "slab_profile": (c_int, [c_void_p, c_int]),
+    "slab_profile_read": (c_int, [c_void_p, c_void_p, c_void_p, c_int]),
     "slab_tc_gemm": (c_int, [c_int, c_int, c_int, ctypes.c_float, c_void_p, c_int64, c_void_p, c_int64,
                              ctypes.c_float, c_void_p, c_int64, c_int, c_int, c_void_p, c_void_p]),
     "slab_residual_norms_noalloc": (c_int, [c_int, c_int, c_void_p, c_void_p, c_double, c_void_p, c_void_p,

@@ -147,9 +147,79 @@ slab_status factor_impl(slab_handle* h) {
     return SLAB_OK;
 }
 
+struct ProfRecord {
+    std::vector<cudaEvent_t> pool;     // event pairs, reused
+    std::vector<int> cls;              // class of each recorded pair
+    size_t used = 0;
+    cudaEvent_t pending = nullptr;
+};
+
 }  // namespace
 
+void prof_begin(slab_handle* h, int cls) {
+    if (!h) return;
+    h->launches[cls] += 1;
+    if (!h->prof_on || !h->prof) return;
+    ProfRecord* R = (ProfRecord*)h->prof;
+    if (R->pool.size() < 2 * (R->used + 1)) {
+        for (int i = 0; i < 64; ++i) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return;
+            R->pool.push_back(e);
+        }
+    }
+    cudaEventRecord(R->pool[2 * R->used], h->stream);
+    R->cls.resize(R->used + 1);
+    R->cls[R->used] = cls;
+}
+
+void prof_end(slab_handle* h, int cls) {
+    (void)cls;
+    if (!h || !h->prof_on || !h->prof) return;
+    ProfRecord* R = (ProfRecord*)h->prof;
+    if (R->cls.size() != R->used + 1) return;
+    cudaEventRecord(R->pool[2 * R->used + 1], h->stream);
+    R->used += 1;
+}
+
+static void prof_free(slab_handle* h) {
+    if (!h->prof) return;
+    ProfRecord* R = (ProfRecord*)h->prof;
+    for (auto e : R->pool) cudaEventDestroy(e);
+    delete R;
+    h->prof = nullptr;
+}
+
 extern "C" {
+
+slab_status slab_profile(slab_handle* h, int enable) {
+    if (!h) return SLAB_EINVAL;
+    if (enable && !h->prof) h->prof = new (std::nothrow) ProfRecord();
+    h->prof_on = enable && h->prof;
+    return SLAB_OK;
+}
+
+slab_status slab_profile_read(slab_handle* h, double* ms, int64_t* launches, int n) {
+    if (!h || n < 0 || n > SLAB_KERNEL_CLASSES) return SLAB_EINVAL;
+    SLAB_CK(h, cudaStreamSynchronize(h->stream));
+    for (int c = 0; c < n; ++c) {
+        if (ms) ms[c] = 0.0;
+        if (launches) launches[c] = h->launches[c];
+    }
+    for (int c = 0; c < SLAB_KERNEL_CLASSES; ++c) h->launches[c] = 0;
+    if (h->prof) {
+        ProfRecord* R = (ProfRecord*)h->prof;
+        for (size_t i = 0; i < R->used; ++i) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, R->pool[2 * i], R->pool[2 * i + 1]) == cudaSuccess && ms && R->cls[i] < n)
+                ms[R->cls[i]] += t;
+        }
+        R->used = 0;
+        R->cls.clear();
+    }
+    return SLAB_OK;
+}
+
 
 void slab_default_opts(slab_opts* o) {
     if (!o) return;
@@ -159,6 +229,7 @@ void slab_default_opts(slab_opts* o) {
     o->max_refine = 30;
     o->krylov = 0;
     o->stream = nullptr;
+    o->profile = 0;
 }
 
 const char* slab_strerror(slab_status s) {
@@ -184,6 +255,7 @@ void slab_destroy(slab_handle* h) {
     dfree(h->tLinv); dfree(h->tZtb); dfree(h->tRtb); dfree(h->tZI); dfree(h->tRI);
     dfree(h->Tb); dfree(h->To); dfree(h->Fct); dfree(h->Linv); dfree(h->Y);
     p = h->dstatus; dfree(p);
+    prof_free(h);
     delete h;
 }
 
@@ -214,6 +286,7 @@ slab_status slab_factor(const slab_grid* grid, const slab_coeffs* co, int b, con
     h->stream = (cudaStream_t)o.stream;
     h->rtol = o.rtol;
     h->max_refine = o.max_refine;
+    if (o.profile) slab_profile(h, 1);
     TreeDims& d = h->td;
     d.s = n - 1;
     d.s_pad = (d.s + SLAB_TILE - 1) / SLAB_TILE * SLAB_TILE;

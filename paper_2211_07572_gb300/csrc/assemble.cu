@@ -126,6 +126,7 @@ slab_status assemble_T(slab_handle* h) {
     a.AY = h->AY; a.DG = h->DG; a.ZI = (const T*)h->tZI; a.Tb = (T*)h->Tb; a.To = (T*)h->To;
     const int nt = h->nt;
     dim3 grid(nt, nt, d.NI + (d.NI - 1));
+    SLAB_PROF(h, KC_ASSEMBLE);
     assemble_T_kernel<T><<<grid, 256, 0, h->stream>>>(a);
     SLAB_CK_LAUNCH(h);
     return SLAB_OK;

@@ -344,6 +344,7 @@ __global__ void transpose_kernel(const T* __restrict__ in, T* __restrict__ out, 
 template <typename T>
 slab_status transpose(slab_handle* h, const T* in, T* out, int n) {
     dim3 grid((n + 31) / 32, (n + 31) / 32);
+    SLAB_PROF(h, KC_OTHER);
     transpose_kernel<T><<<grid, dim3(32, 8), 0, h->stream>>>(in, out, n);
     SLAB_CK_LAUNCH(h);
     return SLAB_OK;
@@ -351,13 +352,14 @@ slab_status transpose(slab_handle* h, const T* in, T* out, int n) {
 
 // C = beta C + alpha A B^T on the unit of this precision: tensor cores for FP32, SIMT for FP64.
 template <typename T>
-slab_status gemm_tn(slab_handle* h, int M, int N, int K, T alpha, const T* A, int64_t lda, const T* B, int64_t ldb,
-                    T beta, T* C, int64_t ldc, int transC, int lower_only);
+slab_status gemm_tn(slab_handle* h, int cls, int M, int N, int K, T alpha, const T* A, int64_t lda, const T* B,
+                    int64_t ldb, T beta, T* C, int64_t ldc, int transC, int lower_only);
 
 template <>
-slab_status gemm_tn<float>(slab_handle* h, int M, int N, int K, float alpha, const float* A, int64_t lda,
+slab_status gemm_tn<float>(slab_handle* h, int cls, int M, int N, int K, float alpha, const float* A, int64_t lda,
                            const float* B, int64_t ldb, float beta, float* C, int64_t ldc, int transC,
                            int lower_only) {
+    SLAB_PROF(h, cls);
     TcGemmArgs g;
     g.M = M; g.N = N; g.K = K; g.alpha = alpha; g.beta = beta;
     g.A = A; g.lda = lda; g.B = B; g.ldb = ldb; g.C = C; g.ldc = ldc;
@@ -376,9 +378,10 @@ slab_status gemm_tn<float>(slab_handle* h, int M, int N, int K, float alpha, con
 }
 
 template <>
-slab_status gemm_tn<double>(slab_handle* h, int M, int N, int K, double alpha, const double* A, int64_t lda,
-                            const double* B, int64_t ldb, double beta, double* C, int64_t ldc, int transC,
-                            int lower_only) {
+slab_status gemm_tn<double>(slab_handle* h, int cls, int M, int N, int K, double alpha, const double* A,
+                            int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
+                            int transC, int lower_only) {
+    SLAB_PROF(h, cls);
     if (N <= 64 && !lower_only && h->wTickets) {
         int KS = K / 256;
         if (KS < 1) KS = 1;
@@ -422,21 +425,27 @@ slab_status sweep_factor(slab_handle* h) {
         SLAB_CK(h, cudaMemcpyAsync(S, Tb + j * blk, blk * sizeof(T), cudaMemcpyDeviceToDevice, h->stream));
         if (j > 0) {           // S_j = T_jj - Y_{j-1}^T Y_{j-1}  (lower tiles)
             const T* Yp = F + (j - 1) * 3 * blk + blk;
-            if ((st = gemm_tn<T>(h, sp, sp, sp, T(-1), Yp, sp, Yp, sp, T(1), S, sp, 0, 1))) return st;
+            if ((st = gemm_tn<T>(h, KC_SYRK, sp, sp, sp, T(-1), Yp, sp, Yp, sp, T(1), S, sp, 0, 1))) return st;
         }
-        set_identity_kernel<T><<<(unsigned)((blk + 255) / 256), 256, 0, h->stream>>>(LT, sp);
+        {
+            SLAB_PROF(h, KC_OTHER);
+            set_identity_kernel<T><<<(unsigned)((blk + 255) / 256), 256, 0, h->stream>>>(LT, sp);
+        }
         SLAB_CK_LAUNCH(h);
         if (hasY && (st = transpose<T>(h, To + j * blk, Yt, sp))) return st;      // T_{j+1,j}
         const int lt0 = (hasY ? 2 : 1) * sp;         // first row of the identity block
         for (int kb = 0; kb < nt; ++kb) {
             const int rows = lt0 + (kb + 1) * TL;      // identity rows below are still zero here
             const int nrt = rows / TL - kb - 1;
-            panel_kernel<T><<<nrt, 256, smem, h->stream>>>(W, sp, kb, h->dstatus);
+            {
+                SLAB_PROF(h, KC_PANEL);
+                panel_kernel<T><<<nrt, 256, smem, h->stream>>>(W, sp, kb, h->dstatus);
+            }
             SLAB_CK_LAUNCH(h);
             const int c0 = (kb + 1) * TL;
             if (c0 < sp) {
                 const T* P = W + (int64_t)c0 * sp + (int64_t)kb * TL;             // panel rows below the diagonal
-                if ((st = gemm_tn<T>(h, rows - c0, sp - c0, TL, T(-1), P, sp, P, sp, T(1), W + (int64_t)c0 * sp + c0,
+                if ((st = gemm_tn<T>(h, KC_TRAIL, rows - c0, sp - c0, TL, T(-1), P, sp, P, sp, T(1), W + (int64_t)c0 * sp + c0,
                                      sp, 0, 1)))
                     return st;
             }
@@ -462,20 +471,20 @@ slab_status sweep_solve(slab_handle* h, int K) {
     for (int j = 0; j < NI; ++j) {        // forward: z_j = L_j^{-1} (f_j - Y_{j-1}^T z_{j-1})
         if (j > 0) {
             const T* Yt = F + (j - 1) * 3 * blk + blk;
-            if ((st = gemm_tn<T>(h, sp, K, sp, T(-1), Yt, sp, Z + (j - 1) * vb, sp, T(1), X + j * vb, sp, 1, 0)))
+            if ((st = gemm_tn<T>(h, KC_SOLVE_PROD, sp, K, sp, T(-1), Yt, sp, Z + (j - 1) * vb, sp, T(1), X + j * vb, sp, 1, 0)))
                 return st;
         }
-        if ((st = gemm_tn<T>(h, sp, K, sp, T(1), Lin + j * blk, sp, X + j * vb, sp, T(0), Z + j * vb, sp, 1, 0)))
+        if ((st = gemm_tn<T>(h, KC_SOLVE_PROD, sp, K, sp, T(1), Lin + j * blk, sp, X + j * vb, sp, T(0), Z + j * vb, sp, 1, 0)))
             return st;
     }
     for (int j = NI - 1; j >= 0; --j) {   // backward: u_j = L_j^{-T} (z_j - Y_j u_{j+1})
         if (j < NI - 1) {
-            if ((st = gemm_tn<T>(h, sp, K, sp, T(-1), Yn + j * blk, sp, X + (j + 1) * vb, sp, T(1), Z + j * vb, sp,
+            if ((st = gemm_tn<T>(h, KC_SOLVE_PROD, sp, K, sp, T(-1), Yn + j * blk, sp, X + (j + 1) * vb, sp, T(1), Z + j * vb, sp,
                                  1, 0)))
                 return st;
         }
         const T* LT = F + j * 3 * blk + (j < NI - 1 ? 2 : 1) * blk;
-        if ((st = gemm_tn<T>(h, sp, K, sp, T(1), LT, sp, Z + j * vb, sp, T(0), X + j * vb, sp, 1, 0))) return st;
+        if ((st = gemm_tn<T>(h, KC_SOLVE_PROD, sp, K, sp, T(1), LT, sp, Z + j * vb, sp, T(0), X + j * vb, sp, 1, 0))) return st;
     }
     return SLAB_OK;
 }

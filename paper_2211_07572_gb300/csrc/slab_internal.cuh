@@ -92,7 +92,28 @@ struct slab_handle {
 
     int64_t dev_bytes;
     slab_status err;
+
+    // measurement: launch counts per kernel class, optional event timing
+    int64_t launches[SLAB_KERNEL_CLASSES];
+    int prof_on;
+    void* prof;               // ProfRecord (api.cu) while timing is on
 };
+
+enum SlabKernelClass {
+    KC_COEFF = 0, KC_TREE_FACTOR, KC_ASSEMBLE, KC_PANEL, KC_TRAIL, KC_SYRK, KC_SOLVE_PROD,
+    KC_TREE_UP, KC_TREE_DOWN, KC_STENCIL, KC_OTHER
+};
+
+// Records one launch of class cls on h->stream; with timing on, brackets it by events.
+void prof_begin(slab_handle* h, int cls);
+void prof_end(slab_handle* h, int cls);
+struct ProfScope {
+    slab_handle* h;
+    int cls;
+    ProfScope(slab_handle* hh, int c) : h(hh), cls(c) { prof_begin(h, cls); }
+    ~ProfScope() { prof_end(h, cls); }
+};
+#define SLAB_PROF(h, cls) ProfScope _prof_scope_((h), (cls))
 
 // ---------------------------------------------------------------- tree helpers (host+device)
 __host__ __device__ inline int tree_height_count(int s) {

@@ -172,6 +172,7 @@ __global__ void kappa_grad2d_kernel(int n, const double* __restrict__ u,
 slab_status launch_coefficients(slab_handle* h, const double* kappa, const double* c) {
     const int n = h->n;
     dim3 grid((n + 1 + 127) / 128, n + 1);
+    SLAB_PROF(h, KC_COEFF);
     coeff_kernel<<<grid, 128, 0, h->stream>>>(n, h->kind, kappa, c, h->omega, h->AX, h->AY, h->DG);
     SLAB_CK_LAUNCH(h);
     return SLAB_OK;
@@ -197,6 +198,7 @@ slab_status launch_residual(slab_handle* h, const double* u, const double* f, do
         }
         part = h->red_part; tickets = h->red_tickets;
     }
+    SLAB_PROF(h, KC_STENCIL);
     stencil2d_kernel<true><<<grid, 256, 0, h->stream>>>(n, k, h->AX, h->AY, h->DG, u, f, r, nrm_r, nrm_f,
                                                         part, tickets);
     SLAB_CK_LAUNCH(h);
@@ -207,6 +209,7 @@ slab_status launch_apply(slab_handle* h, const double* x, double* y, int k) {
     const int n = h->n, s = n - 1;
     if (k <= 0) return SLAB_OK;
     dim3 grid((s + 255) / 256, (s + ST_ROWS - 1) / ST_ROWS, (k + ST_Q - 1) / ST_Q);
+    SLAB_PROF(h, KC_STENCIL);
     stencil2d_kernel<false><<<grid, 256, 0, h->stream>>>(n, k, h->AX, h->AY, h->DG, x, nullptr, y, nullptr,
                                                          nullptr, nullptr, nullptr);
     SLAB_CK_LAUNCH(h);
@@ -216,6 +219,7 @@ slab_status launch_apply(slab_handle* h, const double* x, double* y, int k) {
 slab_status launch_kappa_gradient(slab_handle* h, const double* u, const double* lam, double* g, int k) {
     const int n = h->n;
     dim3 grid((n + 1 + 127) / 128, n + 1);
+    SLAB_PROF(h, KC_OTHER);
     kappa_grad2d_kernel<<<grid, 128, 0, h->stream>>>(n, u, lam, g, k);
     SLAB_CK_LAUNCH(h);
     return SLAB_OK;

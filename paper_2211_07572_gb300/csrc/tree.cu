@@ -553,6 +553,7 @@ slab_status tree_factor(slab_handle* h) {
         const int cnt = tree_nodes_at(d.s, k);
         if (!cnt) continue;
         dim3 grid(cnt, chunks_at(d.s, k), d.NS);
+        SLAB_PROF(h, KC_TREE_FACTOR);
         tree_factor_kernel<T><<<grid, TB_THREADS, 0, h->stream>>>(a, k);
         SLAB_CK_LAUNCH(h);
     }
@@ -570,10 +571,12 @@ slab_status tree_up_gather(slab_handle* h, const double* F, double fscale, int r
         const int cnt = tree_nodes_at(d.s, k);
         if (!cnt) continue;
         dim3 grid(cnt, chunks_at(d.s, k), d.NS);
+        SLAB_PROF(h, KC_TREE_UP);
         tree_up_kernel<T><<<grid, TB_THREADS, 0, h->stream>>>(p, k, F, fscale, r0);
         SLAB_CK_LAUNCH(h);
     }
     dim3 g2((unsigned)(((int64_t)d.s_pad * K + 255) / 256), d.NI);
+    SLAB_PROF(h, KC_TREE_UP);
     gather_ftilde_kernel<T><<<g2, 256, 0, h->stream>>>(p, F, fscale, r0);
     SLAB_CK_LAUNCH(h);
     return SLAB_OK;
@@ -588,11 +591,13 @@ slab_status tree_down_scatter(slab_handle* h, double* U, int accumulate, int r0,
         if (!cnt) continue;
         const int wmax = min(d.s, (1 << (k + 1)) - 1);
         dim3 grid(cnt, (2 * wmax + DCW - 1) / DCW, d.NS);
+        SLAB_PROF(h, KC_TREE_DOWN);
         tree_down_kernel<T><<<grid, TB_THREADS, 0, h->stream>>>(p, k, U, accumulate, r0, (T*)h->wVp,
                                                                  (unsigned*)h->wVtk);
         SLAB_CK_LAUNCH(h);
     }
     dim3 g2((unsigned)(((int64_t)d.s * K + 255) / 256), d.NI);
+    SLAB_PROF(h, KC_TREE_DOWN);
     scatter_utilde_kernel<T><<<g2, 256, 0, h->stream>>>(p, U, accumulate, r0);
     SLAB_CK_LAUNCH(h);
     return SLAB_OK;
@@ -602,6 +607,7 @@ template <typename T>
 slab_status export_ftilde_part(slab_handle* h, double* out, double scale, int r0, int K) {
     SolveArgs<T> p = make_solve_args<T>(h, K);
     const int64_t tot = (int64_t)h->td.NI * h->td.s * K;
+    SLAB_PROF(h, KC_OTHER);
     export_x_kernel<T><<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>(p, out, scale, h->td.NI, r0);
     SLAB_CK_LAUNCH(h);
     return SLAB_OK;
@@ -611,6 +617,7 @@ template <typename T>
 slab_status import_utilde_part(slab_handle* h, const double* in, int r0, int K) {
     SolveArgs<T> p = make_solve_args<T>(h, K);
     const int64_t tot = (int64_t)h->td.NI * h->td.s_pad * K;
+    SLAB_PROF(h, KC_OTHER);
     import_x_kernel<T><<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>(p, in, h->td.NI, r0);
     SLAB_CK_LAUNCH(h);
     return SLAB_OK;

@@ -42,7 +42,7 @@ class SlabSolver:
 
     def __init__(self, dim: int, n: int, b: int, kind: int, kappa=None, c=None, omega: float = 0.0,
                  precision: str = "fp32", rtol: float = 1e-10, max_refine: int = 30,
-                 stream: Optional[torch.cuda.Stream] = None, device=None):
+                 stream: Optional[torch.cuda.Stream] = None, device=None, profile: bool = False):
         self.lib = _lib.load()
         self.device = (torch.device(device) if device is not None
                        else torch.device("cuda", torch.cuda.current_device()))
@@ -58,6 +58,7 @@ class SlabSolver:
         opts.rtol = float(rtol)
         opts.max_refine = int(max_refine)
         opts.stream = ctypes.c_void_p(self.stream.cuda_stream)
+        opts.profile = int(profile)
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             _lib.check(self.lib.slab_factor(ctypes.byref(grid), ctypes.byref(co), int(b), ctypes.byref(opts),
@@ -85,6 +86,18 @@ class SlabSolver:
             self.close()
         except Exception:
             pass
+
+    def profile(self, enable: bool = True):
+        _lib.check(self.lib.slab_profile(self.h, int(enable)), "slab_profile")
+
+    def profile_read(self):
+        """(ms, launches) per kernel class since the previous read (dicts keyed by class name)."""
+        n = len(_lib.KERNEL_CLASSES)
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_int64 * n)()
+        _lib.check(self.lib.slab_profile_read(self.h, ms, cnt, n), "slab_profile_read")
+        return ({k: ms[i] for i, k in enumerate(_lib.KERNEL_CLASSES)},
+                {k: int(cnt[i]) for i, k in enumerate(_lib.KERNEL_CLASSES)})
 
     @property
     def device_bytes(self) -> int:
