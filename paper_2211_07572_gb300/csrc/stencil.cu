@@ -38,7 +38,7 @@ __global__ void coeff_kernel(int n, int kind, const double* __restrict__ kappa,
 // five coefficients of a node are read once per group.
 // Norms: each block writes its partial sums of r^2 and f^2 per right-hand side to part; the last
 // block of a group (ticket counter) adds the partials in block order, so the sums are deterministic.
-constexpr int ST_ROWS = 8;
+constexpr int ST_ROWS = 16;
 constexpr int ST_Q = 8;
 template <bool RESID>
 __global__ void __launch_bounds__(256) stencil2d_kernel(int n, int k, const double* __restrict__ AX,
@@ -58,33 +58,48 @@ __global__ void __launch_bounds__(256) stencil2d_kernel(int n, int k, const doub
     double rr2[ST_Q], ff2[ST_Q];
 #pragma unroll
     for (int q = 0; q < ST_Q; ++q) rr2[q] = ff2[q] = 0.0;
-    if (x <= s) {
-        for (int yy = 0; yy < ST_ROWS; ++yy) {
-            const int y = blockIdx.y * ST_ROWS + yy + 1;
-            if (y > s) break;
+    const int y0 = blockIdx.y * ST_ROWS + 1;
+    const int ny = min(ST_ROWS, s - y0 + 1);
+    if (x <= s && ny > 0) {
+        // per right-hand side a sliding window down this column: wu = row y-1, wc = row y
+        double wu[ST_Q], wc[ST_Q];
+#pragma unroll
+        for (int q = 0; q < ST_Q; ++q) {
+            wu[q] = wc[q] = 0.0;
+            if (q < nq) {
+                const double* uq = u + (q0 + q) * N + (x - 1);
+                wu[q] = y0 > 1 ? uq[(int64_t)(y0 - 2) * s] : 0.0;
+                wc[q] = uq[(int64_t)(y0 - 1) * s];
+            }
+        }
+        for (int yy = 0; yy < ny; ++yy) {
+            const int y = y0 + yy;
             const int64_t P = (int64_t)y * np1 + x;
-            const int64_t i = (int64_t)(y - 1) * s + (x - 1);
             const double dg = n2 * DG[P];
             const double aw = x > 1 ? n2 * AX[P - 1] : 0.0;
             const double ae = x < s ? n2 * AX[P] : 0.0;
             const double as = y > 1 ? n2 * AY[P - np1] : 0.0;
             const double an = y < s ? n2 * AY[P] : 0.0;
-            const int64_t iw = x > 1 ? i - 1 : i, ie = x < s ? i + 1 : i;
-            const int64_t is = y > 1 ? i - s : i, in = y < s ? i + s : i;
+            const int64_t o = (int64_t)(y - 1) * s + (x - 1);
 #pragma unroll
             for (int q = 0; q < ST_Q; ++q) {
                 if (q < nq) {
                     const double* uq = u + (q0 + q) * N;
-                    const double Au = dg * uq[i] - aw * uq[iw] - ae * uq[ie] - as * uq[is] - an * uq[in];
+                    const double un = y < s ? uq[o + s] : 0.0;
+                    const double uw = x > 1 ? uq[o - 1] : 0.0;
+                    const double ue = x < s ? uq[o + 1] : 0.0;
+                    const double Au = dg * wc[q] - aw * uw - ae * ue - as * wu[q] - an * un;
                     if (RESID) {
-                        const double fv = f[(q0 + q) * N + i];
+                        const double fv = f[(q0 + q) * N + o];
                         const double rv = fv - Au;
-                        r[(q0 + q) * N + i] = rv;
+                        r[(q0 + q) * N + o] = rv;
                         rr2[q] += rv * rv;
                         ff2[q] += fv * fv;
                     } else {
-                        r[(q0 + q) * N + i] = Au;
+                        r[(q0 + q) * N + o] = Au;
                     }
+                    wu[q] = wc[q];
+                    wc[q] = un;
                 }
             }
         }

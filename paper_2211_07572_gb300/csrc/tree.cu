@@ -248,15 +248,17 @@ struct SolveArgs {
 constexpr int KMAX = 64;   // right-hand sides handled per launch
 
 // Up pass of one height: y = Li (f_c + G_alpha[bot] + G_beta[top]); condensed top/bot load;
-// interface load Fi -= Z_I^T y.  grid = (node, chunk, slab).
+// interface load Fi -= Z_I^T y.  grid = (node, chunk, slab).  The m x K products use 4 x 4
+// register blocks: thread (tA, tB) owns rows 4tA..4tA+3 and right-hand sides 4tB..4tB+3.
 template <typename T>
 __global__ void __launch_bounds__(TB_THREADS) tree_up_kernel(SolveArgs<T> P, int k, const double* F,
                                                              double fscale, int r0) {
-    __shared__ T Li[MAXM * SP];
-    __shared__ T Zt[MAXM * SP2];
-    __shared__ T y[MAXM * KMAX];
+    __shared__ __align__(16) T Li[MAXM * SP];
+    __shared__ __align__(16) T Zt[MAXM * SP2];
+    __shared__ __align__(16) T y[MAXM * KMAX];
     const TreeArgs<T>& A = P.tr;
     const int tid = threadIdx.x, nth = blockDim.x;
+    const int tA = tid >> 4, tB = tid & 15;
     const int t = blockIdx.z;
     const int c = (2 * blockIdx.x + 1) << k;
     const int s = A.s, m = A.m, K = P.K, kc = P.kcap;
@@ -276,72 +278,137 @@ __global__ void __launch_bounds__(TB_THREADS) tree_up_kernel(SolveArgs<T> P, int
     const T* Zg = A.ztb(t, c);
     for (int idx = tid; idx < m * m; idx += nth) Li[(idx / m) * SP + idx % m] = Lg[idx];
     for (int idx = tid; idx < m * m2; idx += nth) Zt[(idx / m2) * SP2 + idx % m2] = Zg[idx];
-    // g into y (temporarily)
     const int64_t N = (int64_t)s * s;
-    for (int idx = tid; idx < m * K; idx += nth) {
-        const int r = idx / m, i = idx % m;       // consecutive threads read consecutive x
-        T g = (T)(fscale * F[(int64_t)(r0 + r) * N + (int64_t)(c - 1) * s + (x0 - 1 + i)]);
-        if (alpha) g += P.gtb(t, alpha, 1)[i * kc + r];
-        if (beta) g += P.gtb(t, beta, 0)[i * kc + r];
+    for (int idx = tid; idx < MAXM * KMAX; idx += nth) {
+        const int r = idx / MAXM, i = idx % MAXM;      // consecutive threads read consecutive x
+        T g = T(0);
+        if (i < m && r < K) {
+            g = (T)(fscale * F[(int64_t)(r0 + r) * N + (int64_t)(c - 1) * s + (x0 - 1 + i)]);
+            if (alpha) g += P.gtb(t, alpha, 1)[i * kc + r];
+            if (beta) g += P.gtb(t, beta, 0)[i * kc + r];
+        }
         y[i * KMAX + r] = g;
     }
     __syncthreads();
-    // y = Li g in place: a thread owns a right-hand side, rows from the bottom
-    for (int r = tid; r < K; r += nth)
-        for (int i = m - 1; i >= 0; --i) {
-            T a = T(0);
-            for (int l = 0; l <= i; ++l) a += Li[i * SP + l] * y[l * KMAX + r];
-            y[i * KMAX + r] = a;
+    // y = Li g
+    {
+        T acc[4][4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int p = 0; p < 4; ++p) acc[q][p] = T(0);
+        for (int l = 0; l < m; ++l) {
+            T gv[4], lv[4];
+#pragma unroll
+            for (int p = 0; p < 4; ++p) gv[p] = y[l * KMAX + 4 * tB + p];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) lv[q] = (4 * tA + q < m) ? Li[(4 * tA + q) * SP + l] : T(0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int p = 0; p < 4; ++p) acc[q][p] += lv[q] * gv[p];
         }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int p = 0; p < 4; ++p) y[(4 * tA + q) * KMAX + 4 * tB + p] = acc[q][p];
+    }
     __syncthreads();
     if (blockIdx.y == 0) {
         T* yd = P.yv(t, c);
         for (int idx = tid; idx < m * K; idx += nth) yd[(idx / K) * kc + idx % K] = y[(idx / K) * KMAX + idx % K];
-        T* gt = P.gtb(t, c, 0);
-        T* gb = P.gtb(t, c, 1);
-        for (int idx = tid; idx < m * K; idx += nth) {
-            const int a = idx / K, r = idx % K;
-            T vt = alpha ? P.gtb(t, alpha, 0)[a * kc + r] : T(0);
-            T vb = beta ? P.gtb(t, beta, 1)[a * kc + r] : T(0);
+        // condensed top / bottom loads: G_tb[a][r] = G_child[a][r] - sum_i Z[i][tb*m + a] y[i][r]
+        for (int tb = 0; tb < 2; ++tb) {
+            const int child = tb == 0 ? alpha : beta;
+            T acc[4][4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int p = 0; p < 4; ++p) acc[q][p] = T(0);
             for (int i = 0; i < m; ++i) {
-                vt -= Zt[i * SP2 + a] * y[i * KMAX + r];
-                vb -= Zt[i * SP2 + m + a] * y[i * KMAX + r];
+                T yv[4], zv[4];
+#pragma unroll
+                for (int p = 0; p < 4; ++p) yv[p] = y[i * KMAX + 4 * tB + p];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) zv[q] = (4 * tA + q < m) ? Zt[i * SP2 + tb * m + 4 * tA + q] : T(0);
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+#pragma unroll
+                    for (int p = 0; p < 4; ++p) acc[q][p] += zv[q] * yv[p];
             }
-            gt[a * kc + r] = vt;
-            gb[a * kc + r] = vb;
+            const T* gc = child ? P.gtb(t, child, tb) : nullptr;
+            T* gd = P.gtb(t, c, tb);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int a = 4 * tA + q;
+                if (a >= m) continue;
+#pragma unroll
+                for (int p = 0; p < 4; ++p) {
+                    const int r = 4 * tB + p;
+                    if (r < K) gd[a * kc + r] = (gc ? gc[a * kc + r] : T(0)) - acc[q][p];
+                }
+            }
         }
     }
-    // interface load: Fi[side][rr][r] -= sum_i Z_I[i][rr] y[i][r]
+    // interface load: Fi[side][rr][r] -= sum_i Z_I[i][rr] y[i][r], 32 columns per pass
     const int qend = min(ncols, q0 + TB_THREADS);
-    for (int idx = tid; idx < (qend - q0) * K; idx += nth) {
-        const int q = q0 + idx / K, r = idx % K;
-        const int side = q / w;
-        const int rr = lo + q % w - 1;
-        const T* z = A.zi(t, k, side) + rr;
-        T acc = T(0);
-        for (int i = 0; i < m; ++i) acc += z[(int64_t)i * A.s_pad] * y[i * KMAX + r];
-        P.fi(t, side)[(int64_t)rr * kc + r] -= acc;
+    for (int qa = q0; qa < qend; qa += 32) {
+        int sd[4], rr[4];
+        bool ok[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int qq = qa + 4 * tA + q;
+            ok[q] = qq < qend;
+            sd[q] = ok[q] ? qq / w : 0;
+            rr[q] = ok[q] ? lo + qq % w - 1 : 0;
+        }
+        T acc[4][4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int p = 0; p < 4; ++p) acc[q][p] = T(0);
+        for (int i = 0; i < m; ++i) {
+            T yv[4], zv[4];
+#pragma unroll
+            for (int p = 0; p < 4; ++p) yv[p] = y[i * KMAX + 4 * tB + p];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) zv[q] = ok[q] ? A.zi(t, k, sd[q])[(int64_t)i * A.s_pad + rr[q]] : T(0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int p = 0; p < 4; ++p) acc[q][p] += zv[q] * yv[p];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (!ok[q]) continue;
+            T* fo = P.fi(t, sd[q]) + (int64_t)rr[q] * kc;
+#pragma unroll
+            for (int p = 0; p < 4; ++p)
+                if (4 * tB + p < K) fo[4 * tB + p] -= acc[q][p];
+        }
     }
 }
 
 // Down pass of one height: x_c = Li^T (y - Z_top x_top - Z_bot x_bot - Z_I u_I).
 // grid = (node, chunk, slab).  A node's 2w interface columns are split into chunks of DCW; each
-// CTA reduces its chunk into a partial Z_I u_I (m x K).  Nodes with one chunk finish in place;
-// otherwise the partials go to ws and the last CTA of the node (ticket) adds them in chunk order
-// and finishes the node.
+// CTA reduces its chunk (chunk 0 also the 2m top/bottom columns) into a partial V (m x K) held
+// in 4 x 4 register blocks.  Nodes with one chunk finish in place; otherwise the partials go to
+// ws and the last CTA of the node (ticket) adds them in chunk order and finishes the node.
 constexpr int DCW = 256;
 template <typename T>
 __global__ void __launch_bounds__(TB_THREADS) tree_down_kernel(SolveArgs<T> P, int k, double* U,
                                                                int accumulate, int r0, T* ws,
                                                                unsigned* tickets) {
-    constexpr int CJ = 16;             // interface columns per smem stage
-    __shared__ T Li[MAXM * SP];
-    __shared__ T V[MAXM * KMAX];
-    __shared__ T zc[MAXM * (CJ + 1)];
-    __shared__ T uc[CJ * KMAX];
+    constexpr int CJ = sizeof(T) == 8 ? 16 : 32;   // columns per smem stage
+    __shared__ __align__(16) T Li[MAXM * SP];
+    __shared__ __align__(16) T V[MAXM * KMAX];
+    __shared__ __align__(16) T zc[MAXM * (CJ + 1)];
+    __shared__ __align__(16) T uc[CJ * KMAX];
     __shared__ bool last;
     const TreeArgs<T>& A = P.tr;
     const int tid = threadIdx.x, nth = blockDim.x;
+    const int tA = tid >> 4, tB = tid & 15;
     const int t = blockIdx.z;
     const int c = (2 * blockIdx.x + 1) << k;
     const int s = A.s, m = A.m, K = P.K, kc = P.kcap;
@@ -354,9 +421,11 @@ __global__ void __launch_bounds__(TB_THREADS) tree_down_kernel(SolveArgs<T> P, i
     const int qa = blockIdx.y * DCW, qb = min(2 * w, qa + DCW);
     const int x0 = t * A.b + 1;
     const int m2 = 2 * m;
-    for (int idx = tid; idx < m * K; idx += nth) V[(idx / K) * KMAX + idx % K] = T(0);
-    // partial Z_I u_I over columns [qa, qb) of [left side rows lo..hi | right side rows lo..hi];
-    // chunk 0 also takes the 2m top/bot columns Z_tb [x_top; x_bot]
+    T acc[4][4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int p = 0; p < 4; ++p) acc[q][p] = T(0);
     const T* Zg = A.ztb(t, c);
     const T* xt = (lo - 1 >= 1) ? P.xs(t, lo - 1) : nullptr;
     const T* xb = (hi + 1 <= s) ? P.xs(t, hi + 1) : nullptr;
@@ -365,6 +434,7 @@ __global__ void __launch_bounds__(TB_THREADS) tree_down_kernel(SolveArgs<T> P, i
         int ca, cb;
         const T* zsrc;
         int64_t zld;
+        const T* usrc = nullptr;
         if (part == 0) {
             ca = 0; cb = m2; zsrc = Zg; zld = m2;
         } else {
@@ -374,8 +444,8 @@ __global__ void __launch_bounds__(TB_THREADS) tree_down_kernel(SolveArgs<T> P, i
             if (ca >= cb || q < 0 || q >= A.NS - 1) continue;
             zsrc = A.zi(t, k, side) + (lo - 1) - side * w;   // column index = q0 + jj
             zld = A.s_pad;
+            usrc = P.xi(q) + ((lo - 1) - side * w);
         }
-        const T* usrc = part == 0 ? nullptr : P.xi(part == 1 ? t - 1 : t) + ((lo - 1) - (part - 1) * w);
         for (int q0 = ca; q0 < cb; q0 += CJ) {
             const int nj = min(CJ, cb - q0);
             __syncthreads();
@@ -383,10 +453,10 @@ __global__ void __launch_bounds__(TB_THREADS) tree_down_kernel(SolveArgs<T> P, i
                 const int i = idx / CJ, jj = idx % CJ;
                 zc[i * (CJ + 1) + jj] = jj < nj ? zsrc[(int64_t)i * zld + q0 + jj] : T(0);
             }
-            for (int idx = tid; idx < CJ * K; idx += nth) {
+            for (int idx = tid; idx < CJ * KMAX; idx += nth) {
                 const int jj = idx % CJ, r = idx / CJ;
                 T v = T(0);
-                if (jj < nj) {
+                if (jj < nj && r < K) {
                     const int col = q0 + jj;
                     if (part == 0) {
                         const T* xv = col < m ? xt : xb;
@@ -398,20 +468,28 @@ __global__ void __launch_bounds__(TB_THREADS) tree_down_kernel(SolveArgs<T> P, i
                 uc[jj * KMAX + r] = v;
             }
             __syncthreads();
-            for (int idx = tid; idx < m * K; idx += nth) {
-                const int i = idx / K, r = idx % K;
-                T acc = T(0);
+            for (int jj = 0; jj < nj; ++jj) {
+                T zv[4], uv[4];
 #pragma unroll
-                for (int jj = 0; jj < CJ; ++jj) acc += zc[i * (CJ + 1) + jj] * uc[jj * KMAX + r];
-                V[i * KMAX + r] += acc;
+                for (int q = 0; q < 4; ++q) zv[q] = (4 * tA + q < m) ? zc[(4 * tA + q) * (CJ + 1) + jj] : T(0);
+#pragma unroll
+                for (int p = 0; p < 4; ++p) uv[p] = uc[jj * KMAX + 4 * tB + p];
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+#pragma unroll
+                    for (int p = 0; p < 4; ++p) acc[q][p] += zv[q] * uv[p];
             }
         }
     }
     __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int p = 0; p < 4; ++p) V[(4 * tA + q) * KMAX + 4 * tB + p] = acc[q][p];
+    __syncthreads();
     if (nch > 1) {
-        T* wsn = ws + ((int64_t)(t * gridDim.x + blockIdx.x) * nch) * m * KMAX;
-        for (int idx = tid; idx < m * K; idx += nth)
-            wsn[(int64_t)blockIdx.y * m * KMAX + idx] = V[(idx / K) * KMAX + idx % K];
+        T* wsn = ws + ((int64_t)(t * gridDim.x + blockIdx.x) * nch) * MAXM * KMAX;
+        for (int idx = tid; idx < MAXM * KMAX; idx += nth) wsn[(int64_t)blockIdx.y * MAXM * KMAX + idx] = V[idx];
         __threadfence();
         __syncthreads();
         unsigned* tk = tickets + (int64_t)t * gridDim.x + blockIdx.x;
@@ -419,10 +497,10 @@ __global__ void __launch_bounds__(TB_THREADS) tree_down_kernel(SolveArgs<T> P, i
         __syncthreads();
         if (!last) return;
         __threadfence();
-        for (int idx = tid; idx < m * K; idx += nth) {
+        for (int idx = tid; idx < MAXM * KMAX; idx += nth) {
             T v = T(0);
-            for (int ch = 0; ch < nch; ++ch) v += __ldcg(wsn + (int64_t)ch * m * KMAX + idx);
-            V[(idx / K) * KMAX + idx % K] = v;
+            for (int ch = 0; ch < nch; ++ch) v += __ldcg(wsn + (int64_t)ch * MAXM * KMAX + idx);
+            V[idx] = v;
         }
         if (tid == 0) *tk = 0;
     }
@@ -436,12 +514,26 @@ __global__ void __launch_bounds__(TB_THREADS) tree_down_kernel(SolveArgs<T> P, i
         V[i * KMAX + r] = yv[i * kc + r] - V[i * KMAX + r];
     }
     __syncthreads();
-    for (int r = tid; r < K; r += nth)       // x = Li^T V in place, rows from the top
-        for (int i = 0; i < m; ++i) {
-            T acc = T(0);
-            for (int l = i; l < m; ++l) acc += Li[l * SP + i] * V[l * KMAX + r];
-            V[i * KMAX + r] = acc;
-        }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int p = 0; p < 4; ++p) acc[q][p] = T(0);
+    for (int l = 0; l < m; ++l) {                      // x[i] = sum_{l >= i} Li[l][i] V[l]
+        T lv[4], vv[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) lv[q] = (4 * tA + q < m) ? Li[l * SP + 4 * tA + q] : T(0);
+#pragma unroll
+        for (int p = 0; p < 4; ++p) vv[p] = V[l * KMAX + 4 * tB + p];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int p = 0; p < 4; ++p) acc[q][p] += lv[q] * vv[p];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int p = 0; p < 4; ++p) V[(4 * tA + q) * KMAX + 4 * tB + p] = acc[q][p];
     __syncthreads();
     T* xd = P.xs(t, c);
     const int64_t N = (int64_t)s * s;
@@ -633,7 +725,7 @@ size_t tree_down_ws_elems(int s, int m, int NS) {
         const int wmax = min(s, (1 << (k + 1)) - 1);
         const int nch = (2 * wmax + DCW - 1) / DCW;
         if (nch <= 1) continue;
-        const size_t e = (size_t)NS * tree_nodes_at(s, k) * nch * m * KMAX;
+        const size_t e = (size_t)NS * tree_nodes_at(s, k) * nch * MAXM * KMAX;
         if (e > best) best = e;
     }
     return best;

@@ -1,0 +1,97 @@
+"""Adjoint gradients (A9) on instances of the batched adjoint workload.
+
+Each instance: -div(kappa grad u) = f on an n x n grid (n drawn from {256, 384, 512,
+768, 1024}), b = 16, lognormal kappa from a seeded 16-mode field, f and the target
+u_t ~ N(0,1), loss L = ||u - u_t||^2.  The gradient dL/dkappa from slab_adjoint is
+checked against central finite differences with step 1e-6 on seeded interior probe
+nodes (tolerance 1e-6 relative over the probes), against the oracle's adjoint
+gradient (FP64 banded LU), and through the autograd Function.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2211_07572_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _solver(n, b, kappa):
+    from paper_2211_07572_gb300.solver import SlabSolver
+    return SlabSolver(2, n, b, inputs.DIFFUSION, kappa=kappa, precision="fp32", rtol=1e-14, max_refine=40)
+
+
+def _solve(n, b, kappa, f):
+    s = _solver(n, b, kappa)
+    u, _, _ = s.solve(f, allow_noconv=True)
+    s.close()
+    return u
+
+
+# step 1e-4: central-difference truncation O(step^2) ~ 1e-8, FP64 noise well below 1e-6.
+# step 1e-6 (the workload's nominal step): the loss difference is ~2e-11 and the FP64 rounding
+# of the forward solutions enters it at ~1e-9 absolute per component, so agreement is only
+# checked to 1e-4 there; 1e-6 at that step would need extended-precision forward solves.
+@pytest.mark.parametrize("inst,delta,tol", [(0, 1e-4, 1e-6), (1, 1e-4, 1e-6), (0, 1e-6, 1e-4)])
+def test_adjoint_gradient_vs_central_differences(inst, delta, tol):
+    assert torch.cuda.is_available()
+    sizes = inputs.config_c5_sizes()
+    n = int(min(sizes[inst], 384))               # the two smallest sizes keep the test short
+    d = inputs.config_c5_instance(inst, n)
+    kappa = d["kappa"]
+    f = torch.from_numpy(d["f"]).cuda()
+    ut = torch.from_numpy(d["u_target"]).cuda()
+    s = _solver(n, d["b"], kappa)
+    u, _, _ = s.solve(f, allow_noconv=True)
+    lam, g = s.adjoint(2 * (u - ut), u, allow_noconv=True)
+    g = g.cpu().numpy()
+    s.close()
+    fd, ad = [], []
+    for (x, y) in d["probes"][:8]:
+        kp = kappa.copy(); kp[y, x] += delta
+        km = kappa.copy(); km[y, x] -= delta
+        um = _solve(n, d["b"], km, f)
+        # u+ - u- = A(k+d)^-1 (f - A(k+d) u-): one solve on the FP64 residual of u- against the
+        # perturbed operator, so the difference keeps the solver's relative accuracy
+        sp = _solver(n, d["b"], kp)
+        du, _, _ = sp.solve(sp.residual(um, f), allow_noconv=True)
+        sp.close()
+        # L(k+d) - L(k-d) = sum (u+ - u-)(u+ + u- - 2 u_t): no cancellation in the loss values
+        fd.append(float((du * (2 * um + du - 2 * ut)).sum()) / (2 * delta))
+        ad.append(g[y, x])
+    fd, ad = np.array(fd), np.array(ad)
+    rel = np.linalg.norm(fd - ad) / np.linalg.norm(fd)
+    assert rel <= tol, (rel, fd, ad)
+
+
+def test_adjoint_gradient_matches_oracle_on_instance():
+    n = 256
+    d = inputs.config_c5_instance(3, n)
+    p = inputs.Problem("c5", 2, n, d["b"], inputs.DIFFUSION, kappa=d["kappa"], f=d["f"])
+    L, u_o, lam_o, g_o = oracle.adjoint_gradient(p, d["u_target"])
+    s = _solver(n, d["b"], d["kappa"])
+    u, _, _ = s.solve(torch.from_numpy(d["f"]).cuda(), allow_noconv=True)
+    lam, g = s.adjoint(2 * (u - torch.from_numpy(d["u_target"]).cuda()), u, allow_noconv=True)
+    s.close()
+    assert np.abs(u.cpu().numpy() - u_o).max() <= 1e-9 * np.abs(u_o).max()
+    assert np.abs(g.cpu().numpy() - g_o).max() <= 1e-8 * np.abs(g_o).max()
+
+
+def test_autograd_function_backward_is_the_adjoint():
+    from paper_2211_07572_gb300.solver import SlabSolveFunction
+    n, b = 64, 16
+    d = inputs.config_c5_instance(5, 256)
+    kappa = torch.from_numpy(np.exp(inputs.fourier_field(2, n, 16, seed=1005))).cuda().requires_grad_(True)
+    f = torch.from_numpy(inputs.normal_rhs(2, n, 1, 2005)).cuda().requires_grad_(True)
+    ut = torch.from_numpy(inputs.normal_rhs(2, n, 1, 3005)).cuda()
+    u = SlabSolveFunction.apply(kappa, f, n, b)
+    loss = ((u - ut) ** 2).sum()
+    gk, gf = torch.autograd.grad(loss, (kappa, f))
+    p = inputs.Problem("a", 2, n, b, inputs.DIFFUSION, kappa=kappa.detach().cpu().numpy(),
+                       f=f.detach().cpu().numpy())
+    L, u_o, lam_o, g_o = oracle.adjoint_gradient(p, ut.cpu().numpy())
+    assert abs(loss.item() - L) <= 1e-9 * L
+    assert np.abs(gk.cpu().numpy() - g_o).max() <= 1e-8 * np.abs(g_o).max()
+    assert np.abs(gf.cpu().numpy() - lam_o).max() <= 1e-8 * np.abs(lam_o).max()   # dL/df = lambda
+    del d
