@@ -94,9 +94,12 @@ void slab_default_opts(slab_opts* opts);
  * reduced matrix T, Stage 2 sweep (Algorithm 1).  b is the interface spacing:
  * interfaces at x = q b, q = 1..n/b-1, slab interiors b-1 nodes wide.
  * Requires b >= 2 and n % b == 0, 2 <= b <= 33, n/b >= 2 (SLAB_EINVAL otherwise);
- * dim == 2 (SLAB_EUNSUPPORTED otherwise); SPD kinds (SLAB_EUNSUPPORTED for
- * HELMHOLTZ).  kappa/c are read during the call only.  On success *out is a
- * new handle.  Synchronises opts->stream (returns after the factor is built).
+ * dim == 2 (SLAB_EUNSUPPORTED otherwise).  POISSON and DIFFUSION are factored by
+ * Cholesky (slab separators and Stage 2); HELMHOLTZ (indefinite) by Gauss-Jordan
+ * with partial pivoting, both in the slab separators and for S_j^{-1} in Stage 2
+ * (Algorithm 1 as printed), in opts.factor_prec.  A zero / non-positive pivot
+ * returns SLAB_ESINGULAR.  kappa/c are read during the call only.  On success
+ * *out is a new handle.  Synchronises opts->stream (returns after the factor).
  */
 slab_status slab_factor(const slab_grid* grid, const slab_coeffs* coeffs, int b,
                         const slab_opts* opts, slab_handle** out);

@@ -253,6 +253,7 @@ void slab_destroy(slab_handle* h) {
     void* p;
     p = h->AX; dfree(p); p = h->AY; dfree(p); p = h->DG; dfree(p); p = h->kappa; dfree(p);
     dfree(h->tLinv); dfree(h->tZtb); dfree(h->tRtb); dfree(h->tZI); dfree(h->tRI);
+    dfree(h->tWtb); dfree(h->tWI); dfree(h->ToT); dfree(h->dscratch);
     dfree(h->Tb); dfree(h->To); dfree(h->Fct); dfree(h->Linv); dfree(h->Y);
     p = h->dstatus; dfree(p);
     prof_free(h);
@@ -275,7 +276,6 @@ slab_status slab_factor(const slab_grid* grid, const slab_coeffs* co, int b, con
     if (o.factor_prec != SLAB_PREC_FP32 && o.factor_prec != SLAB_PREC_FP64) return SLAB_EINVAL;
     if (grid->dim != 2) return SLAB_EUNSUPPORTED;
     if (b - 1 > SLAB_MAXM) return SLAB_EUNSUPPORTED;
-    if (co->kind == SLAB_HELMHOLTZ) return SLAB_EUNSUPPORTED;
 
     slab_handle* h = new (std::nothrow) slab_handle();
     if (!h) return SLAB_ENOMEM;
@@ -322,6 +322,12 @@ slab_status slab_factor(const slab_grid* grid, const slab_coeffs* co, int b, con
     ALLOC(h->Tb, d.NI * blk * R);
     ALLOC(h->To, (d.NI - 1) * blk * R);
     ALLOC(h->Fct, d.NI * 3 * blk * R);
+    if (co->kind == SLAB_HELMHOLTZ) {
+        ALLOC(h->tWtb, tn * 2 * d.m * d.m * R);
+        ALLOC(h->tWI, (int64_t)d.NS * d.H * 2 * d.m * d.s_pad * R);
+        ALLOC(h->ToT, (d.NI - 1) * blk * R);
+    }
+    ALLOC(h->dscratch, 256);
     ALLOC(h->Linv, d.NI * blk * R);
     ALLOC(h->Y, (d.NI - 1) * blk * R);
     ALLOC(h->dstatus, sizeof(unsigned));
@@ -333,6 +339,7 @@ slab_status slab_factor(const slab_grid* grid, const slab_coeffs* co, int b, con
     CK(cudaMemsetAsync(h->dstatus, 0, sizeof(unsigned), h->stream));
     CK(cudaMemsetAsync(h->tZI, 0, (size_t)d.NS * d.H * 2 * d.m * d.s_pad * R, h->stream));
     CK(cudaMemsetAsync(h->tRI, 0, (size_t)d.NS * d.H * 4 * d.m * d.s_pad * R, h->stream));
+    if (h->tWI) CK(cudaMemsetAsync(h->tWI, 0, (size_t)d.NS * d.H * 2 * d.m * d.s_pad * R, h->stream));
     if (h->kappa)
         CK(cudaMemcpyAsync(h->kappa, co->kappa, nodes2 * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
 #undef CK

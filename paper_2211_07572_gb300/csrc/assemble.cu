@@ -4,7 +4,8 @@
 // For slab t the condensed matrix on its interface nodes is
 //   M_t[p,p'] = - sum_{heights k} [p, p' in the same height-k segment] Z_{t,k}[:,p] . Z_{t,k}[:,p'],
 // where Z_{t,k} (m x s per slab side) holds the Z = L^{-1} B columns of the
-// height-k separators (zero for rows no height-k node owns).  Then
+// height-k separators (zero for rows no height-k node owns); for the indefinite kind the
+// product is B_{t,k}[:,p] . W_{t,k}[:,p'] with W = S^{-1} B.  Then
 //   T_qq      = A_qq + M_q[R,R] + M_{q+1}[L,L],      T_{q,q+1} = M_{q+1}[L,R]
 // (A_{q,q+1} = 0 for b >= 2).  Each 64 x 64 output tile is written once; with
 // 64-aligned tiles, heights k >= 5 need no mask (a tile lies inside one
@@ -19,11 +20,15 @@ struct AsmArgs {
     int s, s_pad, m, H, NS, NI, b, n;
     const double* AY;
     const double* DG;
-    const T* ZI;
+    const T* ZI;       // left factors: Z (SPD kinds) or B (indefinite kind)
+    const T* ZR;       // right factors: Z (SPD kinds) or W = S^{-1} B (indefinite kind)
     T* Tb;
     T* To;
     __device__ const T* zi(int t, int k, int side) const {
         return ZI + (((int64_t)t * H + k) * 2 + side) * m * s_pad;
+    }
+    __device__ const T* zr(int t, int k, int side) const {
+        return ZR + (((int64_t)t * H + k) * 2 + side) * m * s_pad;
     }
 };
 
@@ -43,7 +48,7 @@ __device__ void add_contribution(const AsmArgs<T>& A, int t, int sa, int sb, int
             masked = true;
         }
         const T* za = A.zi(t, k, sa) + (int64_t)u * SLAB_TILE;
-        const T* zb = A.zi(t, k, sb) + (int64_t)v * SLAB_TILE;
+        const T* zb = A.zr(t, k, sb) + (int64_t)v * SLAB_TILE;
         __syncthreads();
         for (int idx = tid; idx < m * SLAB_TILE; idx += blockDim.x) {
             const int i = idx / SLAB_TILE, j = idx % SLAB_TILE;
@@ -124,6 +129,7 @@ slab_status assemble_T(slab_handle* h) {
     const TreeDims& d = h->td;
     a.s = d.s; a.s_pad = d.s_pad; a.m = d.m; a.H = d.H; a.NS = d.NS; a.NI = d.NI; a.b = h->b; a.n = h->n;
     a.AY = h->AY; a.DG = h->DG; a.ZI = (const T*)h->tZI; a.Tb = (T*)h->Tb; a.To = (T*)h->To;
+    a.ZR = h->kind == SLAB_HELMHOLTZ ? (const T*)h->tWI : (const T*)h->tZI;
     const int nt = h->nt;
     dim3 grid(nt, nt, d.NI + (d.NI - 1));
     SLAB_PROF(h, KC_ASSEMBLE);

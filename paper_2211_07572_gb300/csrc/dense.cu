@@ -399,13 +399,207 @@ slab_status gemm_tn<double>(slab_handle* h, int cls, int M, int N, int K, double
     return SLAB_OK;
 }
 
+// ---------------------------------------------------------------- indefinite kind (Helmholtz)
+// Gauss-Jordan inversion of G = [S | I] (sp x 2sp, row-major, ld 2sp) with partial pivoting over
+// the whole column (first row of largest |g_ik|): one column per three launches.
+template <typename T>
+__global__ void __launch_bounds__(1024) gj_pivot_kernel(const T* G, int sp, int k, int* piv, T* pval,
+                                                       unsigned* status) {
+    __shared__ T bv[32];
+    __shared__ int bi[32];
+    const int ld = 2 * sp;
+    T best = T(-1);
+    int bidx = k;
+    for (int i = k + threadIdx.x; i < sp; i += blockDim.x) {
+        const T v = fabs(G[(int64_t)i * ld + k]);
+        if (v > best) { best = v; bidx = i; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+        if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; }
+    }
+    if ((threadIdx.x & 31) == 0) { bv[threadIdx.x >> 5] = best; bi[threadIdx.x >> 5] = bidx; }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int nw = blockDim.x >> 5;
+        best = threadIdx.x < nw ? bv[threadIdx.x] : T(-1);
+        bidx = threadIdx.x < nw ? bi[threadIdx.x] : k;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+            if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; }
+        }
+        if (threadIdx.x == 0) {
+            const T v = G[(int64_t)bidx * ld + k];
+            *piv = bidx;
+            if (!(best > T(0)) || !isfinite((double)v)) {
+                atomicOr(status, SLAB_DEV_NOTSPD);
+                *pval = T(1);
+            } else {
+                *pval = v;
+            }
+        }
+    }
+}
+
+// swap rows k and p, then scale row k by 1 / pivot (columns k+1 .. 2sp-1; column k is not read again)
+template <typename T>
+__global__ void gj_swap_scale_kernel(T* G, int sp, int k, const int* piv, const T* pval) {
+    const int j = k + 1 + blockIdx.x * blockDim.x + threadIdx.x;
+    const int ld = 2 * sp;
+    if (j >= ld) return;
+    const int p = *piv;
+    const T rp = T(1) / *pval;
+    T a = G[(int64_t)k * ld + j];
+    if (p != k) {
+        const T b = G[(int64_t)p * ld + j];
+        G[(int64_t)p * ld + j] = a;
+        a = b;
+    }
+    G[(int64_t)k * ld + j] = a * rp;
+}
+
+// column k multipliers of the swapped matrix: only row p changed in column k
+template <typename T>
+__global__ void gj_swap_col_kernel(T* G, int sp, int k, const int* piv) {
+    const int p = *piv;
+    if (threadIdx.x == 0 && blockIdx.x == 0 && p != k) {
+        const int ld = 2 * sp;
+        const T a = G[(int64_t)k * ld + k];
+        G[(int64_t)k * ld + k] = G[(int64_t)p * ld + k];
+        G[(int64_t)p * ld + k] = a;
+    }
+}
+
+// G[i][j] -= G[i][k] G[k][j] for i != k, j > k  (column k is left as is)
+template <typename T>
+__global__ void gj_eliminate_kernel(T* G, int sp, int k) {
+    const int j = k + 1 + blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y * blockDim.y + threadIdx.y;
+    const int ld = 2 * sp;
+    if (j >= ld || i >= sp || i == k) return;
+    G[(int64_t)i * ld + j] -= G[(int64_t)i * ld + k] * G[(int64_t)k * ld + j];
+}
+
+template <typename T>
+slab_status gj_invert(slab_handle* h, T* G, int sp, int* piv, T* pval) {
+    const int ld = 2 * sp;
+    for (int k = 0; k < sp; ++k) {
+        {
+            SLAB_PROF(h, KC_PANEL);
+            gj_pivot_kernel<T><<<1, 1024, 0, h->stream>>>(G, sp, k, piv, pval, h->dstatus);
+        }
+        SLAB_CK_LAUNCH(h);
+        const int nc = ld - k - 1;
+        if (nc > 0) {
+            SLAB_PROF(h, KC_PANEL);
+            gj_swap_col_kernel<T><<<1, 32, 0, h->stream>>>(G, sp, k, piv);
+            gj_swap_scale_kernel<T><<<(nc + 255) / 256, 256, 0, h->stream>>>(G, sp, k, piv, pval);
+        }
+        SLAB_CK_LAUNCH(h);
+        if (nc > 0) {
+            SLAB_PROF(h, KC_TRAIL);
+            dim3 blk(32, 8), grid((nc + 31) / 32, (sp + 7) / 8);
+            gj_eliminate_kernel<T><<<grid, blk, 0, h->stream>>>(G, sp, k);
+        }
+        SLAB_CK_LAUNCH(h);
+    }
+    return SLAB_OK;
+}
+
+template <typename T>
+__global__ void set_aug_identity_kernel(T* G, int sp) {     // right half of [S | I] := I
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)sp * sp) return;
+    const int i = (int)(idx / sp), j = (int)(idx % sp);
+    G[(int64_t)i * 2 * sp + sp + j] = i == j ? T(1) : T(0);
+}
+
 }  // namespace
+
+// Indefinite kind: Algorithm 1 as printed, S_1 = T_11, S_{j+1} = T_{j+1,j+1} - T_{j+1,j} W_j with
+// W_j = S_j^{-1} T_{j,j+1}; S_j^{-1} by pivoted Gauss-Jordan.  Stored: S_j^{-1} (in Linv),
+// W_j (in Y) and T_{j+1,j} (in ToT).  Work arrays: [S | I] and W_j^T in Fct.
+template <typename T>
+slab_status sweep_factor_indef(slab_handle* h) {
+    const int NI = h->td.NI, sp = h->td.s_pad;
+    const int64_t blk = (int64_t)sp * sp;
+    T* Tb = (T*)h->Tb;
+    T* To = (T*)h->To;
+    T* ToT = (T*)h->ToT;
+    T* Sinv = (T*)h->Linv;
+    T* Wn = (T*)h->Y;
+    T* G = (T*)h->Fct;                   // [S | I], sp x 2sp
+    T* Wt = G + 2 * blk;                 // W_j^T
+    int* piv = (int*)h->dscratch;        // pivot row and value of the current column
+    T* pval = (T*)((char*)h->dscratch + 64);
+    slab_status st;
+    for (int j = 0; j < NI; ++j) {
+        SLAB_CK(h, cudaMemcpy2DAsync(G, 2 * sp * sizeof(T), Tb + j * blk, sp * sizeof(T), sp * sizeof(T), sp,
+                                     cudaMemcpyDeviceToDevice, h->stream));
+        if (j > 0 && (st = gemm_tn<T>(h, KC_SYRK, sp, sp, sp, T(-1), ToT + (j - 1) * blk, sp, Wt, sp, T(1), G,
+                                      2 * sp, 0, 0)))
+            return st;                                          // S_j = T_jj - T_{j,j-1} W_{j-1}
+        {
+            SLAB_PROF(h, KC_OTHER);
+            set_aug_identity_kernel<T><<<(unsigned)((blk + 255) / 256), 256, 0, h->stream>>>(G, sp);
+        }
+        SLAB_CK_LAUNCH(h);
+        if ((st = gj_invert<T>(h, G, sp, piv, pval))) return st;
+        SLAB_CK(h, cudaMemcpy2DAsync(Sinv + j * blk, sp * sizeof(T), G + sp, 2 * sp * sizeof(T), sp * sizeof(T), sp,
+                                     cudaMemcpyDeviceToDevice, h->stream));
+        if (j < NI - 1) {
+            if ((st = transpose<T>(h, To + j * blk, ToT + j * blk, sp))) return st;   // T_{j+1,j}
+            // W_j^T = T_{j+1,j} S_j^{-T}
+            if ((st = gemm_tn<T>(h, KC_TRAIL, sp, sp, sp, T(1), ToT + j * blk, sp, Sinv + j * blk, sp, T(0), Wt,
+                                 sp, 0, 0)))
+                return st;
+            if ((st = transpose<T>(h, Wt, Wn + j * blk, sp))) return st;
+        }
+    }
+    return SLAB_OK;
+}
+
+// Algorithm 2 for the indefinite kind on X ([NI][kcap][s_pad]):
+//   forward  z_j = S_j^{-1} f_j,  f_{j+1} -= T_{j+1,j} z_j;   backward  u_j = z_j - W_j u_{j+1}.
+template <typename T>
+slab_status sweep_solve_indef(slab_handle* h, int K) {
+    const int NI = h->td.NI, sp = h->td.s_pad;
+    const int64_t blk = (int64_t)sp * sp;
+    const int64_t vb = (int64_t)sp * h->kcap;
+    T* Sinv = (T*)h->Linv;
+    T* Wn = (T*)h->Y;
+    T* ToT = (T*)h->ToT;
+    T* X = (T*)h->wX;
+    T* Z = (T*)h->wZ;
+    slab_status st;
+    for (int j = 0; j < NI; ++j) {
+        if ((st = gemm_tn<T>(h, KC_SOLVE_PROD, sp, K, sp, T(1), Sinv + j * blk, sp, X + j * vb, sp, T(0), Z + j * vb,
+                             sp, 1, 0)))
+            return st;
+        if (j < NI - 1 && (st = gemm_tn<T>(h, KC_SOLVE_PROD, sp, K, sp, T(-1), ToT + j * blk, sp, Z + j * vb, sp,
+                                           T(1), X + (j + 1) * vb, sp, 1, 0)))
+            return st;
+    }
+    for (int j = NI - 1; j >= 0; --j) {
+        SLAB_CK(h, cudaMemcpyAsync(X + j * vb, Z + j * vb, (size_t)K * sp * sizeof(T), cudaMemcpyDeviceToDevice,
+                                   h->stream));
+        if (j < NI - 1 && (st = gemm_tn<T>(h, KC_SOLVE_PROD, sp, K, sp, T(-1), Wn + j * blk, sp, X + (j + 1) * vb, sp,
+                                           T(1), X + j * vb, sp, 1, 0)))
+            return st;
+    }
+    return SLAB_OK;
+}
 
 // Factor-phase layout: Fct[j] = [S_j ; Y_j^T ; L_j^{-T}] (3 s_pad x s_pad; for the last j the
 // L^{-T} block sits right below S), plus the transposed copies Lin[j] = L_j^{-1} and Yn[j] = Y_j
 // for the solve products.
 template <typename T>
 slab_status sweep_factor(slab_handle* h) {
+    if (h->kind == SLAB_HELMHOLTZ) return sweep_factor_indef<T>(h);
     const int NI = h->td.NI, sp = h->td.s_pad, nt = h->nt;
     const int64_t blk = (int64_t)sp * sp;
     T* Tb = (T*)h->Tb;
@@ -459,6 +653,7 @@ slab_status sweep_factor(slab_handle* h) {
 // Algorithm 2 on the interface workspace X ([NI][kcap][s_pad], right-hand sides 0..K-1), result in X.
 template <typename T>
 slab_status sweep_solve(slab_handle* h, int K) {
+    if (h->kind == SLAB_HELMHOLTZ) return sweep_solve_indef<T>(h, K);
     const int NI = h->td.NI, sp = h->td.s_pad;
     const int64_t blk = (int64_t)sp * sp;
     const int64_t vb = (int64_t)sp * h->kcap;

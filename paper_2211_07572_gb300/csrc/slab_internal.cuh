@@ -61,6 +61,9 @@ struct slab_handle {
     void* tRtb;               // [NS][s+1][2m*2m] condensed top/bot x top/bot block
     void* tZI;                // [NS][H][2][m][s_pad]  Z for interface nodes, per height
     void* tRI;                // [NS][H][2][2][m][s_pad] condensed top/bot x interface rows
+    void* tWtb;               // Helmholtz only: [NS][s+1][m*2m] W = S^{-1} B (top/bot columns)
+    void* tWI;                // Helmholtz only: [NS][H][2][m][s_pad] W for the interface columns
+    void* ToT;                // Helmholtz only: [NI-1][s_pad][s_pad] T_{q+1,q} (row-major)
 
     // Stage-2 data
     void* Tb;                 // [NI][s_pad][s_pad]  T_qq (kept as assembled)
@@ -70,6 +73,7 @@ struct slab_handle {
     void* Y;                  // [NI-1][s_pad][s_pad] Y_j = L_j^{-1} T_{j,j+1}
 
     unsigned int* dstatus;    // device status word
+    void* dscratch;           // 256 bytes of device scratch (pivot search results)
 
     // solve workspace, sized for kcap right-hand sides
     int kcap;

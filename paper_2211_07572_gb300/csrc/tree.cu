@@ -32,6 +32,8 @@ struct TreeArgs {
     T* Rtb;
     T* ZI;
     T* RI;
+    T* Wtb;           // indefinite kind: W = S^{-1} B for the top/bot columns (else null)
+    T* WI;            // indefinite kind: W = S^{-1} B for the interface columns, per height
     unsigned* status;
     __device__ int64_t node(int t, int c) const { return (int64_t)t * (s + 1) + c; }
     __device__ T* linv(int t, int c) const { return Linv + node(t, c) * m * m; }
@@ -39,6 +41,10 @@ struct TreeArgs {
     __device__ T* rtb(int t, int c) const { return Rtb + node(t, c) * 4 * m * m; }
     __device__ T* zi(int t, int k, int side) const {
         return ZI + (((int64_t)t * H + k) * 2 + side) * m * s_pad;
+    }
+    __device__ T* wtb(int t, int c) const { return Wtb + node(t, c) * 2 * m * m; }
+    __device__ T* wi(int t, int k, int side) const {
+        return WI + (((int64_t)t * H + k) * 2 + side) * m * s_pad;
     }
     __device__ T* ri(int t, int k, int tb, int side) const {
         return RI + ((((int64_t)t * H + k) * 2 + tb) * 2 + side) * m * s_pad;
@@ -86,14 +92,79 @@ __device__ void chol_inv_small(T* S, T* Li, int m, unsigned* status) {
     }
 }
 
+// Inverse of the m x m matrix S (smem, stride SP; destroyed) into Si by Gauss-Jordan elimination
+// of [S | I] with partial pivoting (first row of largest |s_ik| wins); all threads of the block.
+// A zero or non-finite pivot sets SLAB_DEV_NOTSPD and continues with 1.
+template <typename T>
+__device__ void gj_inv_small(T* S, T* Si, int m, unsigned* status) {
+    __shared__ int piv;
+    __shared__ T prow;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    for (int idx = tid; idx < m * m; idx += nth) Si[(idx / m) * SP + idx % m] = (idx / m == idx % m) ? T(1) : T(0);
+    __syncthreads();
+    for (int k = 0; k < m; ++k) {
+        if (tid < 32) {                                  // pivot search in column k, rows k..m-1
+            T best = T(-1);
+            int bi = k;
+            for (int i = k + tid; i < m; i += 32) {
+                const T v = fabs(S[i * SP + k]);
+                if (v > best) { best = v; bi = i; }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+            }
+            if (tid == 0) {
+                piv = bi;
+                const T pv = S[bi * SP + k];
+                if (!(best > T(0)) || !isfinite((double)pv)) {
+                    atomicOr(status, SLAB_DEV_NOTSPD);
+                    prow = T(1);
+                } else {
+                    prow = T(1) / pv;
+                }
+            }
+        }
+        __syncthreads();
+        const int p = piv;
+        const T rp = prow;
+        if (p != k)
+            for (int j = tid; j < 2 * m; j += nth) {     // swap rows k and p of [S | Si]
+                T* a = j < m ? S + k * SP + j : Si + k * SP + (j - m);
+                T* b = j < m ? S + p * SP + j : Si + p * SP + (j - m);
+                const T tmp = *a; *a = *b; *b = tmp;
+            }
+        __syncthreads();
+        for (int j = tid; j < 2 * m; j += nth) {         // scale the pivot row
+            if (j < m) S[k * SP + j] *= rp;
+            else Si[k * SP + (j - m)] *= rp;
+        }
+        __syncthreads();
+        for (int idx = tid; idx < m * 2 * m; idx += nth) {
+            const int i = idx / (2 * m), j = idx % (2 * m);
+            if (i == k) continue;
+            const T f = S[i * SP + k];
+            if (j < m) { if (j != k) S[i * SP + j] -= f * S[k * SP + j]; }
+            else Si[i * SP + (j - m)] -= f * Si[k * SP + (j - m)];
+        }
+        __syncthreads();
+        for (int i = tid; i < m; i += nth) if (i != k) S[i * SP + k] = T(0);
+        __syncthreads();
+    }
+}
+
 // One height of the cyclic reduction in every slab.
 // grid = (node index a at this height, column chunk, slab t); block = TB_THREADS.
-template <typename T>
+// SPD kinds: L L^T = S, Z = L^{-1} B; stored Linv, Z.  Indefinite kind: S^{-1} by pivoted
+// Gauss-Jordan, W = S^{-1} B; stored S^{-1}, B (in the Z arrays) and W.  In both cases the
+// condensed rows are R_merged = R_others - B^T S^{-1} B (= Z^T Z in the SPD form).
+template <typename T, bool INDEF>
 __global__ void __launch_bounds__(TB_THREADS) tree_factor_kernel(TreeArgs<T> A, int k) {
-    __shared__ T S[MAXM * SP];
+    __shared__ T S[MAXM * SP2];        // S (stride SP); indefinite kind: then W (stride SP2)
     __shared__ T Li[MAXM * SP];
-    __shared__ T Bt[MAXM * SP2];       // B, then Z = Li B in place
-    T* Zt = Bt;
+    __shared__ T Bt[MAXM * SP2];       // B; SPD kind: then Z = Li B in place
     const int tid = threadIdx.x, nth = blockDim.x;
     const int t = blockIdx.z;
     const int c = (2 * blockIdx.x + 1) << k;
@@ -142,25 +213,42 @@ __global__ void __launch_bounds__(TB_THREADS) tree_factor_kernel(TreeArgs<T> A, 
         Bt[i * SP2 + j] = v;
     }
     __syncthreads();
-    chol_inv_small<T>(S, Li, m, A.status);
-    // Z = Li B, in place; a thread owns a column, rows from the bottom (Li is lower triangular)
-    for (int j = tid; j < m2; j += nth)
-        for (int i = m - 1; i >= 0; --i) {
+    T* Wt = S;
+    if (INDEF) {
+        gj_inv_small<T>(S, Li, m, A.status);                        // Li = S^{-1}
+        for (int idx = tid; idx < m * m2; idx += nth) {             // W = S^{-1} B (into S's buffer)
+            const int i = idx / m2, j = idx % m2;
             T acc = T(0);
-            for (int l = 0; l <= i; ++l) acc += Li[i * SP + l] * Bt[l * SP2 + j];
-            Bt[i * SP2 + j] = acc;
+            for (int l = 0; l < m; ++l) acc += Li[i * SP + l] * Bt[l * SP2 + j];
+            Wt[i * SP2 + j] = acc;
         }
+    } else {
+        chol_inv_small<T>(S, Li, m, A.status);
+        // Z = Li B, in place; a thread owns a column, rows from the bottom (Li is lower triangular)
+        for (int j = tid; j < m2; j += nth)
+            for (int i = m - 1; i >= 0; --i) {
+                T acc = T(0);
+                for (int l = 0; l <= i; ++l) acc += Li[i * SP + l] * Bt[l * SP2 + j];
+                Bt[i * SP2 + j] = acc;
+            }
+    }
     __syncthreads();
+    const T* Zl = Bt;                  // left factor of the update: Z (SPD) or B (indefinite)
+    const T* Zr = INDEF ? Wt : Bt;     // right factor: Z (SPD) or W (indefinite)
     if (blockIdx.y == 0) {
         T* Lg = A.linv(t, c);
         for (int idx = tid; idx < m * m; idx += nth) Lg[idx] = Li[(idx / m) * SP + idx % m];
         T* Zg = A.ztb(t, c);
-        for (int idx = tid; idx < m * m2; idx += nth) Zg[idx] = Zt[(idx / m2) * SP2 + idx % m2];
+        for (int idx = tid; idx < m * m2; idx += nth) Zg[idx] = Bt[(idx / m2) * SP2 + idx % m2];
+        if (INDEF) {
+            T* Wg = A.wtb(t, c);
+            for (int idx = tid; idx < m * m2; idx += nth) Wg[idx] = Wt[(idx / m2) * SP2 + idx % m2];
+        }
         T* Rg = A.rtb(t, c);
         for (int idx = tid; idx < m2 * m2; idx += nth) {
             const int a = idx / m2, bcol = idx % m2;
             T v = T(0);
-            for (int l = 0; l < m; ++l) v -= Zt[l * SP2 + a] * Zt[l * SP2 + bcol];
+            for (int l = 0; l < m; ++l) v -= Zl[l * SP2 + a] * Zr[l * SP2 + bcol];
             if (a < m && bcol < m && Ra) v += Ra[a * m2 + bcol];                     // alpha top x top
             if (a >= m && bcol >= m && Rb) v += Rb[a * m2 + bcol];                   // beta bot x bot
             Rg[idx] = v;
@@ -194,19 +282,29 @@ __global__ void __launch_bounds__(TB_THREADS) tree_factor_kernel(TreeArgs<T> A, 
 #pragma unroll
             for (int i = 0; i < MAXM; ++i) if (i < m) bvec[i] = src[(int64_t)i * sp];
         }
-        T z[MAXM];
+        T z[MAXM];                     // SPD: z = Li b; indefinite: w = S^{-1} b
 #pragma unroll
         for (int i = 0; i < MAXM; ++i) {
             T acc = T(0);
 #pragma unroll
             for (int l = 0; l < MAXM; ++l)
-                if (l <= i && i < m) acc += Li[i * SP + l] * bvec[l];
+                if ((INDEF || l <= i) && l < m && i < m) acc += Li[i * SP + l] * bvec[l];
             z[i] = acc;
         }
         T* zd = A.zi(t, k, side) + rr;
+        if (INDEF) {
+            T* wd = A.wi(t, k, side) + rr;
 #pragma unroll
-        for (int i = 0; i < MAXM; ++i) if (i < m) zd[(int64_t)i * sp] = z[i];
-        // condensed top/bot rows for this interface column
+            for (int i = 0; i < MAXM; ++i)
+                if (i < m) {
+                    zd[(int64_t)i * sp] = bvec[i];
+                    wd[(int64_t)i * sp] = z[i];
+                }
+        } else {
+#pragma unroll
+            for (int i = 0; i < MAXM; ++i) if (i < m) zd[(int64_t)i * sp] = z[i];
+        }
+        // condensed top/bot rows for this interface column: R - Zl^T z  (Zl = Z or B)
         const T* rta = (j < c) ? A.ri(t, k - 1, 0, side) + rr : nullptr;
         const T* rbb = (j > c) ? A.ri(t, kb, 1, side) + rr : nullptr;
         T* rtd = A.ri(t, k, 0, side) + rr;
@@ -217,8 +315,8 @@ __global__ void __launch_bounds__(TB_THREADS) tree_factor_kernel(TreeArgs<T> A, 
 #pragma unroll
             for (int i = 0; i < MAXM; ++i)
                 if (i < m) {
-                    vt -= Zt[i * SP2 + a] * z[i];
-                    vb -= Zt[i * SP2 + m + a] * z[i];
+                    vt -= Zl[i * SP2 + a] * z[i];
+                    vb -= Zl[i * SP2 + m + a] * z[i];
                 }
             rtd[(int64_t)a * sp] = vt;
             rbd[(int64_t)a * sp] = vb;
@@ -396,7 +494,7 @@ __global__ void __launch_bounds__(TB_THREADS) tree_up_kernel(SolveArgs<T> P, int
 // in 4 x 4 register blocks.  Nodes with one chunk finish in place; otherwise the partials go to
 // ws and the last CTA of the node (ticket) adds them in chunk order and finishes the node.
 constexpr int DCW = 256;
-template <typename T>
+template <typename T, bool INDEF>
 __global__ void __launch_bounds__(TB_THREADS) tree_down_kernel(SolveArgs<T> P, int k, double* U,
                                                                int accumulate, int r0, T* ws,
                                                                unsigned* tickets) {
@@ -426,7 +524,7 @@ __global__ void __launch_bounds__(TB_THREADS) tree_down_kernel(SolveArgs<T> P, i
     for (int q = 0; q < 4; ++q)
 #pragma unroll
         for (int p = 0; p < 4; ++p) acc[q][p] = T(0);
-    const T* Zg = A.ztb(t, c);
+    const T* Zg = INDEF ? A.wtb(t, c) : A.ztb(t, c);    // SPD: Z; indefinite: W = S^{-1} B
     const T* xt = (lo - 1 >= 1) ? P.xs(t, lo - 1) : nullptr;
     const T* xb = (hi + 1 <= s) ? P.xs(t, hi + 1) : nullptr;
     for (int part = (blockIdx.y == 0 ? 0 : 1); part < 3; ++part) {
@@ -442,7 +540,7 @@ __global__ void __launch_bounds__(TB_THREADS) tree_down_kernel(SolveArgs<T> P, i
             const int q = side == 0 ? t - 1 : t;
             ca = max(qa, side * w); cb = min(qb, (side + 1) * w);
             if (ca >= cb || q < 0 || q >= A.NS - 1) continue;
-            zsrc = A.zi(t, k, side) + (lo - 1) - side * w;   // column index = q0 + jj
+            zsrc = (INDEF ? A.wi(t, k, side) : A.zi(t, k, side)) + (lo - 1) - side * w;   // column = q0 + jj
             zld = A.s_pad;
             usrc = P.xi(q) + ((lo - 1) - side * w);
         }
@@ -504,37 +602,41 @@ __global__ void __launch_bounds__(TB_THREADS) tree_down_kernel(SolveArgs<T> P, i
         }
         if (tid == 0) *tk = 0;
     }
-    // finish the node: V = y - V;  x = Li^T V
-    const T* Lg = A.linv(t, c);
-    for (int idx = tid; idx < m * m; idx += nth) Li[(idx / m) * SP + idx % m] = Lg[idx];
+    // finish the node: V = y - V; SPD: x = Li^T V, indefinite: x = V (y already holds S^{-1} g)
     const T* yv = P.yv(t, c);
+    if (!INDEF) {
+        const T* Lg = A.linv(t, c);
+        for (int idx = tid; idx < m * m; idx += nth) Li[(idx / m) * SP + idx % m] = Lg[idx];
+    }
     __syncthreads();
     for (int idx = tid; idx < m * K; idx += nth) {
         const int i = idx / K, r = idx % K;
         V[i * KMAX + r] = yv[i * kc + r] - V[i * KMAX + r];
     }
     __syncthreads();
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-        for (int p = 0; p < 4; ++p) acc[q][p] = T(0);
-    for (int l = 0; l < m; ++l) {                      // x[i] = sum_{l >= i} Li[l][i] V[l]
-        T lv[4], vv[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) lv[q] = (4 * tA + q < m) ? Li[l * SP + 4 * tA + q] : T(0);
-#pragma unroll
-        for (int p = 0; p < 4; ++p) vv[p] = V[l * KMAX + 4 * tB + p];
+    if (!INDEF) {
 #pragma unroll
         for (int q = 0; q < 4; ++q)
 #pragma unroll
-            for (int p = 0; p < 4; ++p) acc[q][p] += lv[q] * vv[p];
+            for (int p = 0; p < 4; ++p) acc[q][p] = T(0);
+        for (int l = 0; l < m; ++l) {                      // x[i] = sum_{l >= i} Li[l][i] V[l]
+            T lv[4], vv[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) lv[q] = (4 * tA + q < m) ? Li[l * SP + 4 * tA + q] : T(0);
+#pragma unroll
+            for (int p = 0; p < 4; ++p) vv[p] = V[l * KMAX + 4 * tB + p];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int p = 0; p < 4; ++p) acc[q][p] += lv[q] * vv[p];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int p = 0; p < 4; ++p) V[(4 * tA + q) * KMAX + 4 * tB + p] = acc[q][p];
+        __syncthreads();
     }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-        for (int p = 0; p < 4; ++p) V[(4 * tA + q) * KMAX + 4 * tB + p] = acc[q][p];
-    __syncthreads();
     T* xd = P.xs(t, c);
     const int64_t N = (int64_t)s * s;
     for (int idx = tid; idx < m * K; idx += nth) {
@@ -617,6 +719,7 @@ TreeArgs<T> make_tree_args(slab_handle* h) {
     a.b = h->b; a.n = h->n;
     a.AX = h->AX; a.AY = h->AY; a.DG = h->DG;
     a.Linv = (T*)h->tLinv; a.Ztb = (T*)h->tZtb; a.Rtb = (T*)h->tRtb; a.ZI = (T*)h->tZI; a.RI = (T*)h->tRI;
+    a.Wtb = (T*)h->tWtb; a.WI = (T*)h->tWI;
     a.status = h->dstatus;
     return a;
 }
@@ -641,12 +744,14 @@ template <typename T>
 slab_status tree_factor(slab_handle* h) {
     TreeArgs<T> a = make_tree_args<T>(h);
     const TreeDims& d = h->td;
+    const bool indef = h->kind == SLAB_HELMHOLTZ;
     for (int k = 0; k < d.H; ++k) {
         const int cnt = tree_nodes_at(d.s, k);
         if (!cnt) continue;
         dim3 grid(cnt, chunks_at(d.s, k), d.NS);
         SLAB_PROF(h, KC_TREE_FACTOR);
-        tree_factor_kernel<T><<<grid, TB_THREADS, 0, h->stream>>>(a, k);
+        if (indef) tree_factor_kernel<T, true><<<grid, TB_THREADS, 0, h->stream>>>(a, k);
+        else tree_factor_kernel<T, false><<<grid, TB_THREADS, 0, h->stream>>>(a, k);
         SLAB_CK_LAUNCH(h);
     }
     return SLAB_OK;
@@ -684,8 +789,12 @@ slab_status tree_down_scatter(slab_handle* h, double* U, int accumulate, int r0,
         const int wmax = min(d.s, (1 << (k + 1)) - 1);
         dim3 grid(cnt, (2 * wmax + DCW - 1) / DCW, d.NS);
         SLAB_PROF(h, KC_TREE_DOWN);
-        tree_down_kernel<T><<<grid, TB_THREADS, 0, h->stream>>>(p, k, U, accumulate, r0, (T*)h->wVp,
-                                                                 (unsigned*)h->wVtk);
+        if (h->kind == SLAB_HELMHOLTZ)
+            tree_down_kernel<T, true><<<grid, TB_THREADS, 0, h->stream>>>(p, k, U, accumulate, r0, (T*)h->wVp,
+                                                                          (unsigned*)h->wVtk);
+        else
+            tree_down_kernel<T, false><<<grid, TB_THREADS, 0, h->stream>>>(p, k, U, accumulate, r0, (T*)h->wVp,
+                                                                           (unsigned*)h->wVtk);
         SLAB_CK_LAUNCH(h);
     }
     dim3 g2((unsigned)(((int64_t)d.s * K + 255) / 256), d.NI);
