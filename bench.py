@@ -3,8 +3,8 @@
 Workload (one "step" = the whole hot path): -div(kappa grad u) = f on the unit
 square, n = 2048 (2047^2 unknowns), slab spacing b = 32, kappa = exp(g) with g
 a seeded 16-mode Fourier field of unit variance, 64 right-hand sides f ~ N(0,1);
-FP32 factor (Stage-1 slab trees, T assembly, Stage-2 block Cholesky sweep on the
-tensor cores) followed by the solve with FP64 stencil-residual refinement until
+FP32 factor (Stage-1 slab trees, T assembly, Stage-2 block Cholesky of T in the
+odd-even order, or Algorithm 1's sweep with --stage2 sweep, on the tensor cores) followed by the solve with FP64 stencil-residual refinement until
 max relres <= 1e-10.  Inputs are resident in HBM when the timed region starts;
 every step streams several GB of factors and vectors (far more than the 129 MB
 L2), so no explicit L2 flush is needed.
@@ -103,8 +103,23 @@ def tree_nodes(s):
     return out
 
 
-def work_model(n, b, k, passes):
-    """Algorithmic flops (or bytes) per kernel class for one factor + `passes` solve passes."""
+def oddeven_levels(NI):
+    """(nb, nc) per level of the odd-even order: blocks eliminated, and those with a right neighbour."""
+    out, step = [], 1
+    while step < NI:
+        nrem = (NI - 1) // step + 1
+        if nrem < 2:
+            break
+        out.append((nrem // 2, (nrem - 1) // 2))
+        step *= 2
+    return out
+
+
+def work_model(n, b, k, passes, stage2="sweep"):
+    """Algorithmic flops (or bytes) per kernel class for one factor + `passes` solve passes.
+
+    Explicit inverse factors (L^{-1}, L^{-T}) are stored and applied as dense blocks, so
+    their products count as dense (2 s^3 per s x s x s product; s(s+1)s for a lower-half update)."""
     s = n - 1
     sp = (s + 63) // 64 * 64
     m = b - 1
@@ -119,7 +134,7 @@ def work_model(n, b, k, passes):
     # Stage 2: panel CTAs (Cholesky+inverse 2/3 * 64^3 + product 2 * 64^3), trailing products, Schur update
     pan = trail = 0.0
     for j in range(NI):
-        lt0 = (2 if j < NI - 1 else 1) * sp
+        lt0 = sp if stage2 == "oddeven" else (2 if j < NI - 1 else 1) * sp
         for kb in range(sp // 64):
             rows = lt0 + (kb + 1) * 64
             nrt = rows // 64 - kb - 1
@@ -130,8 +145,14 @@ def work_model(n, b, k, passes):
                 trail += 2 * 64 * (nn * (nn + 1) / 2 + (rows - sp) * nn)
     W["panel"] = pan
     W["trailing"] = trail
-    W["schur_update"] = (NI - 1) * sp * sp * (sp + 1.0)
-    W["sweep_products"] = passes * (4 * NI - 2) * 2.0 * sp * sp * k
+    if stage2 == "oddeven":
+        lv = oddeven_levels(NI)
+        nb, nc = sum(x for x, _ in lv), sum(y for _, y in lv)
+        W["schur_update"] = nb * (2.0 * sp ** 3 + sp * sp * (sp + 1.0)) + nc * (4.0 * sp ** 3 + sp * sp * (sp + 1.0))
+        W["sweep_products"] = passes * (4 * nb + 2 * nc + 2) * 2.0 * sp * sp * k
+    else:
+        W["schur_update"] = (NI - 1) * sp * sp * (sp + 1.0)
+        W["sweep_products"] = passes * (4 * NI - 2) * 2.0 * sp * sp * k
     W["tree_up"] = passes * NS * k * sum(2 * (m * (m + 1) / 2 + 2 * m * m + 2 * w * m) for (_, _, w) in nodes)
     W["tree_down"] = passes * NS * k * sum(2 * (2 * m * m + 2 * w * m + m * (m + 1) / 2) for (_, _, w) in nodes)
     W["stencil"] = passes * 24.0 * s * s * k                            # bytes: read u, f; write r (FP64)
@@ -188,9 +209,13 @@ def run_gpu(args):
     stream = torch.cuda.current_stream(dev)
     prec = args.precision
 
+    NI = n // b - 1
+    stage2 = args.stage2 if args.stage2 != "auto" else ("oddeven" if NI >= 4 else "sweep")
+    W["stage2"] = stage2
+
     def make():
         return SlabSolver(2, n, b, inputs.DIFFUSION, kappa=kappa, precision=prec, rtol=W["rtol"], max_refine=40,
-                          stream=stream, device=dev)
+                          stream=stream, device=dev, stage2=stage2)
 
     def step(f_in, u_out, counts=None):
         s = make()
@@ -242,7 +267,7 @@ def run_gpu(args):
     t_end = torch.cuda.Event(enable_timing=True)
     t_f0.record(stream)
     s = SlabSolver(2, n, b, inputs.DIFFUSION, kappa=kappa, precision=prec, rtol=W["rtol"], max_refine=40,
-                   stream=stream, device=dev, profile=True)
+                   stream=stream, device=dev, profile=True, stage2=stage2)
     t_fac.record(stream)
     _, rel1, it1 = s.solve(f, u, allow_noconv=True)
     t_end.record(stream)
@@ -252,7 +277,7 @@ def run_gpu(args):
     factor_ms = t_f0.elapsed_time(t_fac)
     solve_ms = t_fac.elapsed_time(t_end)
     passes = it1 + 1
-    work = work_model(n, b, k, passes)
+    work = work_model(n, b, k, passes, stage2)
     peaks = _peaks()
     dom = max((c for c in cls_ms if c in BOUND), key=lambda c: cls_ms[c])
     roof = roofline_for(dom, cls_ms[dom], cls_cnt[dom], work, peaks, clocks)
@@ -285,14 +310,14 @@ def run_gpu(args):
         "clocks": clocks,
     }
     if args.fp64_comparator and prec == "fp32":
-        line["fp64_gpu"] = fp64_comparator(n, b, kappa, f, stream, dev)
+        line["fp64_gpu"] = fp64_comparator(n, b, kappa, f, stream, dev, stage2)
         line["fp64_gpu"]["mixed_speedup"] = line["fp64_gpu"]["value"] / line["value"]
     if args.cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(n, b, k)
     print(json.dumps(line))
 
 
-def fp64_comparator(n, b, kappa, f, stream, dev):
+def fp64_comparator(n, b, kappa, f, stream, dev, stage2):
     """Plain FP64 GPU path: same algorithm, all FP64, one pass (no refinement)."""
     import numpy as np
     import torch
@@ -303,7 +328,7 @@ def fp64_comparator(n, b, kappa, f, stream, dev):
 
     def one():
         s = SlabSolver(2, n, b, inputs.DIFFUSION, kappa=kappa, precision="fp64", rtol=1.0, max_refine=0,
-                       stream=stream, device=dev)
+                       stream=stream, device=dev, stage2=stage2)
         _, rel, _ = s.solve(f, u)
         s.close()
         return rel
@@ -379,6 +404,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-fp64", dest="fp64_comparator", action="store_false")
     ap.add_argument("--once", action="store_true", help="run one step only (for profilers)")
+    ap.add_argument("--stage2", default="auto", choices=["auto", "sweep", "oddeven"],
+                    help="elimination order of T (auto: odd-even for 4 or more interfaces)")
     args = ap.parse_args()
     if args.gpus != 1:
         # one GPU per run here: the method's multi-GPU form is replicas of independent problems

@@ -62,6 +62,22 @@ typedef enum {
     SLAB_PREC_FP32 = 1      /* factor and solves in FP32; FP64 residual + refinement */
 } slab_precision;
 
+/*
+ * Elimination order of the block-tridiagonal reduced matrix T in Stage 2.
+ * SWEEP: the sequential block elimination of Algorithm 1 (one block after another).
+ * ODDEVEN: the odd-even order the paper names as the more parallel alternative
+ * (Sec. 4 remark on the elimination order; conclusion): log2(N_I) levels, each
+ * eliminating every other remaining block in one batch; Cholesky based, so POISSON
+ * and DIFFUSION only (SLAB_EUNSUPPORTED for HELMHOLTZ).  It holds about 9 s_pad^2
+ * numbers per interface in the factor versus about 5 for SWEEP.
+ * AUTO: ODDEVEN for POISSON / DIFFUSION with N_I >= 4, SWEEP otherwise.
+ */
+typedef enum {
+    SLAB_STAGE2_AUTO = 0,
+    SLAB_STAGE2_SWEEP = 1,
+    SLAB_STAGE2_ODDEVEN = 2
+} slab_stage2;
+
 typedef struct {
     int dim;                /* 2 or 3 */
     int n;                  /* grid intervals per side, h = 1/n, (n-1)^d unknowns */
@@ -82,16 +98,18 @@ typedef struct {
     int krylov;             /* reserved: 0 */
     void* stream;           /* cudaStream_t all work is ordered on (NULL: legacy default) */
     int profile;            /* 1: time every kernel launch from the start (see slab_profile) */
+    int stage2;             /* slab_stage2 */
 } slab_opts;
 
 typedef struct slab_handle slab_handle;
 
-/* Fill opts with the defaults: FP32 factor, rtol 1e-10, max_refine 30, default stream. */
+/* Fill opts with the defaults: FP32 factor, rtol 1e-10, max_refine 30, default stream,
+ * SLAB_STAGE2_AUTO. */
 void slab_default_opts(slab_opts* opts);
 
 /*
  * Factor A (Algorithm 3): Stage 1 for every slab in parallel, assembly of the
- * reduced matrix T, Stage 2 sweep (Algorithm 1).  b is the interface spacing:
+ * reduced matrix T, Stage 2 (Algorithm 1's sweep or the odd-even order, opts.stage2).  b is the interface spacing:
  * interfaces at x = q b, q = 1..n/b-1, slab interiors b-1 nodes wide.
  * Requires b >= 2 and n % b == 0, 2 <= b <= 33, n/b >= 2 (SLAB_EINVAL otherwise);
  * dim == 2 (SLAB_EUNSUPPORTED otherwise).  POISSON and DIFFUSION are factored by

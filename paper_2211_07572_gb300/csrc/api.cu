@@ -230,6 +230,7 @@ void slab_default_opts(slab_opts* o) {
     o->krylov = 0;
     o->stream = nullptr;
     o->profile = 0;
+    o->stage2 = SLAB_STAGE2_AUTO;
 }
 
 const char* slab_strerror(slab_status s) {
@@ -255,6 +256,8 @@ void slab_destroy(slab_handle* h) {
     dfree(h->tLinv); dfree(h->tZtb); dfree(h->tRtb); dfree(h->tZI); dfree(h->tRI);
     dfree(h->tWtb); dfree(h->tWI); dfree(h->ToT); dfree(h->dscratch);
     dfree(h->Tb); dfree(h->To); dfree(h->Fct); dfree(h->Linv); dfree(h->Y);
+    dfree(h->crD); dfree(h->crE); dfree(h->crW); dfree(h->crLT);
+    dfree(h->crPt); dfree(h->crP); dfree(h->crQt); dfree(h->crQ);
     p = h->dstatus; dfree(p);
     prof_free(h);
     delete h;
@@ -274,8 +277,10 @@ slab_status slab_factor(const slab_grid* grid, const slab_coeffs* co, int b, con
     if (co->kind == SLAB_DIFFUSION && !co->kappa) return SLAB_EINVAL;
     if (co->kind == SLAB_HELMHOLTZ && !co->c) return SLAB_EINVAL;
     if (o.factor_prec != SLAB_PREC_FP32 && o.factor_prec != SLAB_PREC_FP64) return SLAB_EINVAL;
+    if (o.stage2 < SLAB_STAGE2_AUTO || o.stage2 > SLAB_STAGE2_ODDEVEN) return SLAB_EINVAL;
     if (grid->dim != 2) return SLAB_EUNSUPPORTED;
     if (b - 1 > SLAB_MAXM) return SLAB_EUNSUPPORTED;
+    if (o.stage2 == SLAB_STAGE2_ODDEVEN && co->kind == SLAB_HELMHOLTZ) return SLAB_EUNSUPPORTED;
 
     slab_handle* h = new (std::nothrow) slab_handle();
     if (!h) return SLAB_ENOMEM;
@@ -321,7 +326,20 @@ slab_status slab_factor(const slab_grid* grid, const slab_coeffs* co, int b, con
     ALLOC(h->tRI, (int64_t)d.NS * d.H * 4 * d.m * d.s_pad * R);
     ALLOC(h->Tb, d.NI * blk * R);
     ALLOC(h->To, (d.NI - 1) * blk * R);
-    ALLOC(h->Fct, d.NI * 3 * blk * R);
+    h->stage2 = o.stage2 == SLAB_STAGE2_ODDEVEN ||
+                (o.stage2 == SLAB_STAGE2_AUTO && co->kind != SLAB_HELMHOLTZ && d.NI >= 4);
+    if (h->stage2) {
+        ALLOC(h->crD, d.NI * blk * R);
+        ALLOC(h->crE, (d.NI > 1 ? d.NI - 1 : 1) * blk * R);
+        ALLOC(h->crW, (int64_t)cr_max_batch(d.NI) * 2 * blk * R);
+        ALLOC(h->crLT, d.NI * blk * R);
+        ALLOC(h->crPt, d.NI * blk * R);
+        ALLOC(h->crP, d.NI * blk * R);
+        ALLOC(h->crQt, d.NI * blk * R);
+        ALLOC(h->crQ, d.NI * blk * R);
+    } else {
+        ALLOC(h->Fct, d.NI * 3 * blk * R);
+    }
     if (co->kind == SLAB_HELMHOLTZ) {
         ALLOC(h->tWtb, tn * 2 * d.m * d.m * R);
         ALLOC(h->tWI, (int64_t)d.NS * d.H * 2 * d.m * d.s_pad * R);
@@ -329,7 +347,7 @@ slab_status slab_factor(const slab_grid* grid, const slab_coeffs* co, int b, con
     }
     ALLOC(h->dscratch, 256);
     ALLOC(h->Linv, d.NI * blk * R);
-    ALLOC(h->Y, (d.NI - 1) * blk * R);
+    if (!h->stage2) ALLOC(h->Y, (d.NI - 1) * blk * R);
     ALLOC(h->dstatus, sizeof(unsigned));
 #undef ALLOC
 #define CK(call)                                                               \

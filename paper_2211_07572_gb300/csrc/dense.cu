@@ -17,6 +17,9 @@
 // Algorithm 2 then needs products only (vectors stored right-hand-side major, [k][s_pad]):
 //   forward   z_j = L_j^{-1} (f_j - Y_{j-1}^T z_{j-1})
 //   backward  u_j = L_j^{-T} (z_j - Y_j u_{j+1}).
+#include <algorithm>
+#include <vector>
+
 #include "slab_internal.cuh"
 
 namespace {
@@ -65,10 +68,16 @@ __device__ inline void tile_gemm(T acc[4][4], const T* __restrict__ A, int64_t l
 template <typename T>
 __global__ void __launch_bounds__(256) gemm_tn_kernel(int M, int N, int K, T alpha, const T* A, int64_t lda,
                                                       const T* B, int64_t ldb, T beta, T* C, int64_t ldc,
-                                                      int transC, int lower_only) {
-    __shared__ T sA[16 * TLP];
-    __shared__ T sB[16 * TLP];
+                                                      int transC, int lower_only, int64_t sA, int64_t sB,
+                                                      int64_t sC) {
+    __shared__ T sA_[16 * TLP];
+    __shared__ T sB_[16 * TLP];
+    T* sAm = sA_;
+    T* sBm = sB_;
     const int bj = blockIdx.x, bi = blockIdx.y;
+    A += (int64_t)blockIdx.z * sA;
+    B += (int64_t)blockIdx.z * sB;
+    C += (int64_t)blockIdx.z * sC;
     if (lower_only && bj > bi) return;
     const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
     T acc[4][4];
@@ -78,7 +87,7 @@ __global__ void __launch_bounds__(256) gemm_tn_kernel(int M, int N, int K, T alp
         for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
     const int ncols = min(TL, N - bj * TL);
     tile_gemm<T, false, true>(acc, A + (int64_t)bi * TL * lda, lda, B + (int64_t)bj * TL * ldb, ldb, 0, K, ncols,
-                              sA, sB);
+                              sAm, sBm);
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -281,13 +290,14 @@ __device__ void chol_inv_tile(const T* S, T* Li, unsigned* status) {
 // Panel of tile column kb of the tall matrix Wt (leading dimension ld): every CTA factors the
 // diagonal tile Wt[kb][kb] and CTA x replaces the tile Wt[kb+1+x][kb] by itself times L_kk^{-T}.
 template <typename T>
-__global__ void __launch_bounds__(256) panel_kernel(T* Wt, int64_t ld, int kb, unsigned* status) {
+__global__ void __launch_bounds__(256) panel_kernel(T* Wt, int64_t ld, int kb, unsigned* status, int64_t bstride) {
     extern __shared__ unsigned char smem_raw[];
     T* S = reinterpret_cast<T*>(smem_raw);
     T* Li = S + TL * TLP;
     T* X = Li + TL * TLP;
     const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
     const int r = kb + 1 + blockIdx.x;
+    Wt += (int64_t)blockIdx.y * bstride;                 // batch of independent tall matrices
     const T* D = Wt + (int64_t)kb * TL * ld + (int64_t)kb * TL;
     T* src = Wt + (int64_t)r * TL * ld + (int64_t)kb * TL;
     for (int i = tid; i < TL * TL; i += 256) {
@@ -325,10 +335,13 @@ __global__ void set_identity_kernel(T* B, int s_pad) {
     B[idx] = (idx / s_pad == idx % s_pad) ? T(1) : T(0);
 }
 
-// out = in^T for an n x n block (both row-major, leading dimension n), 32 x 32 smem tiles.
+// out = in^T for an n x n block (both row-major, leading dimension n), 32 x 32 smem tiles;
+// blockIdx.z selects one of a batch of blocks sin / sout elements apart.
 template <typename T>
-__global__ void transpose_kernel(const T* __restrict__ in, T* __restrict__ out, int n) {
+__global__ void transpose_kernel(const T* __restrict__ in, T* __restrict__ out, int n, int64_t sin, int64_t sout) {
     __shared__ T tile[32][33];
+    in += (int64_t)blockIdx.z * sin;
+    out += (int64_t)blockIdx.z * sout;
     const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
     for (int j = threadIdx.y; j < 32; j += blockDim.y) {
         const int r = by + j, c = bx + threadIdx.x;
@@ -342,12 +355,18 @@ __global__ void transpose_kernel(const T* __restrict__ in, T* __restrict__ out, 
 }
 
 template <typename T>
-slab_status transpose(slab_handle* h, const T* in, T* out, int n) {
-    dim3 grid((n + 31) / 32, (n + 31) / 32);
+slab_status transpose_batched(slab_handle* h, const T* in, int64_t sin, T* out, int64_t sout, int n, int batch) {
+    if (batch <= 0) return SLAB_OK;
+    dim3 grid((n + 31) / 32, (n + 31) / 32, batch);
     SLAB_PROF(h, KC_OTHER);
-    transpose_kernel<T><<<grid, dim3(32, 8), 0, h->stream>>>(in, out, n);
+    transpose_kernel<T><<<grid, dim3(32, 8), 0, h->stream>>>(in, out, n, sin, sout);
     SLAB_CK_LAUNCH(h);
     return SLAB_OK;
+}
+
+template <typename T>
+slab_status transpose(slab_handle* h, const T* in, T* out, int n) {
+    return transpose_batched<T>(h, in, 0, out, 0, n, 1);
 }
 
 // C = beta C + alpha A B^T on the unit of this precision: tensor cores for FP32, SIMT for FP64.
@@ -393,7 +412,7 @@ slab_status gemm_tn<double>(slab_handle* h, int cls, int M, int N, int K, double
     } else {
         dim3 grid((N + TL - 1) / TL, (M + TL - 1) / TL);
         gemm_tn_kernel<double><<<grid, 256, 0, h->stream>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, transC,
-                                                            lower_only);
+                                                            lower_only, 0, 0, 0);
     }
     SLAB_CK_LAUNCH(h);
     return SLAB_OK;
@@ -518,6 +537,41 @@ __global__ void set_aug_identity_kernel(T* G, int sp) {     // right half of [S 
     G[(int64_t)i * 2 * sp + sp + j] = i == j ? T(1) : T(0);
 }
 
+// Batched C_b = beta C_b + alpha A_b B_b^T, b < batch, with element strides sA, sB, sC.
+template <typename T>
+slab_status gemm_tn_batched(slab_handle* h, int cls, int M, int N, int K, T alpha, const T* A, int64_t lda,
+                            int64_t sA, const T* B, int64_t ldb, int64_t sB, T beta, T* C, int64_t ldc,
+                            int64_t sC, int transC, int lower_only, int batch);
+
+template <>
+slab_status gemm_tn_batched<float>(slab_handle* h, int cls, int M, int N, int K, float alpha, const float* A,
+                                   int64_t lda, int64_t sA, const float* B, int64_t ldb, int64_t sB, float beta,
+                                   float* C, int64_t ldc, int64_t sC, int transC, int lower_only, int batch) {
+    SLAB_PROF(h, cls);
+    TcGemmArgs g;
+    g.M = M; g.N = N; g.K = K; g.alpha = alpha; g.beta = beta;
+    g.A = A; g.lda = lda; g.B = B; g.ldb = ldb; g.C = C; g.ldc = ldc;
+    g.transC = transC; g.split = 1; g.lower_only = lower_only;
+    g.batch = batch; g.sA = sA; g.sB = sB; g.sC = sC;
+    g.ksplit = 1; g.part = nullptr;
+    const slab_status st = tc_gemm(h->stream, g, h->dstatus);
+    if (st == SLAB_ECUDA && h->err == SLAB_OK) h->err = SLAB_ECUDA;
+    return st;
+}
+
+template <>
+slab_status gemm_tn_batched<double>(slab_handle* h, int cls, int M, int N, int K, double alpha, const double* A,
+                                    int64_t lda, int64_t sA, const double* B, int64_t ldb, int64_t sB,
+                                    double beta, double* C, int64_t ldc, int64_t sC, int transC, int lower_only,
+                                    int batch) {
+    SLAB_PROF(h, cls);
+    dim3 grid((N + TL - 1) / TL, (M + TL - 1) / TL, batch);
+    gemm_tn_kernel<double><<<grid, 256, 0, h->stream>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, transC,
+                                                        lower_only, sA, sB, sC);
+    SLAB_CK_LAUNCH(h);
+    return SLAB_OK;
+}
+
 }  // namespace
 
 // Indefinite kind: Algorithm 1 as printed, S_1 = T_11, S_{j+1} = T_{j+1,j+1} - T_{j+1,j} W_j with
@@ -600,6 +654,7 @@ slab_status sweep_solve_indef(slab_handle* h, int K) {
 template <typename T>
 slab_status sweep_factor(slab_handle* h) {
     if (h->kind == SLAB_HELMHOLTZ) return sweep_factor_indef<T>(h);
+    if (h->stage2) return cr_factor<T>(h);
     const int NI = h->td.NI, sp = h->td.s_pad, nt = h->nt;
     const int64_t blk = (int64_t)sp * sp;
     T* Tb = (T*)h->Tb;
@@ -633,7 +688,7 @@ slab_status sweep_factor(slab_handle* h) {
             const int nrt = rows / TL - kb - 1;
             {
                 SLAB_PROF(h, KC_PANEL);
-                panel_kernel<T><<<nrt, 256, smem, h->stream>>>(W, sp, kb, h->dstatus);
+                panel_kernel<T><<<nrt, 256, smem, h->stream>>>(W, sp, kb, h->dstatus, 0);
             }
             SLAB_CK_LAUNCH(h);
             const int c0 = (kb + 1) * TL;
@@ -654,6 +709,7 @@ slab_status sweep_factor(slab_handle* h) {
 template <typename T>
 slab_status sweep_solve(slab_handle* h, int K) {
     if (h->kind == SLAB_HELMHOLTZ) return sweep_solve_indef<T>(h, K);
+    if (h->stage2) return cr_solve<T>(h, K);
     const int NI = h->td.NI, sp = h->td.s_pad;
     const int64_t blk = (int64_t)sp * sp;
     const int64_t vb = (int64_t)sp * h->kcap;
@@ -684,7 +740,203 @@ slab_status sweep_solve(slab_handle* h, int K) {
     return SLAB_OK;
 }
 
+// ------------------------------------------------------------------ odd-even elimination order
+// The odd-even order for eliminating the blocks of T (Sec. 4, remark on the elimination order;
+// conclusion).  Each level eliminates the blocks at odd positions among the remaining ones; the
+// remaining blocks of level l are the multiples of 2^l, so the eliminated ones o = 2^l (2i+1) and
+// their neighbours a = o - 2^l, c = o + 2^l (absent past the last block) are uniformly strided,
+// and every step of a level is one batched launch.  With D the current diagonal blocks and
+// E_i the current block coupling i to its right remaining neighbour:
+//   L_o L_o^T = D_o,  P_o = L_o^{-1} E_a^T,  Q_o = L_o^{-1} E_o,
+//   D_a -= P_o^T P_o,  D_c -= Q_o^T Q_o,  E_a <- -P_o^T Q_o.
+// Stored per eliminated block: L^{-1} (Linv), L^{-T}, P^T, P, Q^T, Q.  Solve: forward
+// y_o = L_o^{-1} b_o, b_a -= P_o^T y_o, b_c -= Q_o^T y_o level by level; the last block
+// x = L^{-T} L^{-1} b; backward x_o = L_o^{-T} (y_o - P_o x_a - Q_o x_c).
+struct CrLevel {
+    int o0, step, nb, nc;     // first eliminated block, its neighbour distance, #eliminated, #with a c
+};
+
+static std::vector<CrLevel> cr_levels(int NI, int* last) {
+    std::vector<CrLevel> L;
+    int step = 1;
+    while (step < NI) {                          // remaining: 0, step, 2 step, ... < NI
+        const int nrem = (NI - 1) / step + 1;
+        if (nrem < 2) break;
+        CrLevel lv;
+        lv.o0 = step;
+        lv.step = step;
+        lv.nb = nrem / 2;                        // positions 1, 3, 5, ... < nrem
+        lv.nc = (nrem - 1) / 2;                  // those with position + 1 < nrem
+        L.push_back(lv);
+        step *= 2;
+    }
+    *last = 0;
+    return L;
+}
+
+int cr_max_batch(int NI) {
+    int last = 0;
+    std::vector<CrLevel> L = cr_levels(NI, &last);
+    int b = 1;
+    for (auto& lv : L) b = std::max(b, lv.nb);
+    return b;
+}
+
+template <typename T>
+__global__ void set_identity_batched_kernel(T* B, int s_pad, int64_t stride) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t n2 = (int64_t)s_pad * s_pad;
+    if (idx >= n2) return;
+    B[(int64_t)blockIdx.y * stride + idx] = (idx / s_pad == idx % s_pad) ? T(1) : T(0);
+}
+
+// Cholesky with L^{-1} and L^{-T} of nb blocks D[o0 + i st] as one batch of tall eliminations
+// [D ; I] in the work buffer (2 s_pad x s_pad per block).
+template <typename T>
+static slab_status cr_potrf_batch(slab_handle* h, int o0, int st_blk, int nb) {
+    const int sp = h->td.s_pad, nt = h->nt;
+    const int64_t blk = (int64_t)sp * sp;
+    T* D = (T*)h->crD;
+    T* W = (T*)h->crW;
+    T* LT = (T*)h->crLT;
+    T* Lin = (T*)h->Linv;
+    const size_t smem = 3 * TL * TLP * sizeof(T);
+    const int64_t sb = (int64_t)st_blk * blk;
+    for (int i = 0; i < nb; ++i)
+        SLAB_CK(h, cudaMemcpyAsync(W + i * 2 * blk, D + o0 * blk + i * sb, blk * sizeof(T), cudaMemcpyDeviceToDevice,
+                                   h->stream));
+    {
+        SLAB_PROF(h, KC_OTHER);
+        set_identity_batched_kernel<T><<<dim3((unsigned)((blk + 255) / 256), nb), 256, 0, h->stream>>>(W + blk, sp,
+                                                                                                      2 * blk);
+    }
+    SLAB_CK_LAUNCH(h);
+    slab_status st;
+    for (int kb = 0; kb < nt; ++kb) {
+        const int rows = sp + (kb + 1) * TL;          // identity rows below are still zero here
+        const int nrt = rows / TL - kb - 1;
+        {
+            SLAB_PROF(h, KC_PANEL);
+            panel_kernel<T><<<dim3(nrt, nb), 256, smem, h->stream>>>(W, sp, kb, h->dstatus, 2 * blk);
+        }
+        SLAB_CK_LAUNCH(h);
+        const int c0 = (kb + 1) * TL;
+        if (c0 < sp) {
+            const T* P = W + (int64_t)c0 * sp + (int64_t)kb * TL;
+            if ((st = gemm_tn_batched<T>(h, KC_TRAIL, rows - c0, sp - c0, TL, T(-1), P, sp, 2 * blk, P, sp, 2 * blk,
+                                         T(1), W + (int64_t)c0 * sp + c0, sp, 2 * blk, 0, 1, nb)))
+                return st;
+        }
+    }
+    for (int i = 0; i < nb; ++i)
+        SLAB_CK(h, cudaMemcpyAsync(LT + o0 * blk + i * sb, W + i * 2 * blk + blk, blk * sizeof(T),
+                                   cudaMemcpyDeviceToDevice, h->stream));
+    return transpose_batched<T>(h, LT + o0 * blk, sb, Lin + o0 * blk, sb, sp, nb);
+}
+
+template <typename T>
+slab_status cr_factor(slab_handle* h) {
+    const int NI = h->td.NI, sp = h->td.s_pad;
+    const int64_t blk = (int64_t)sp * sp;
+    T* D = (T*)h->crD;
+    T* E = (T*)h->crE;
+    T* Et = (T*)h->crW;                  // free between the batched Cholesky steps
+    T* Lin = (T*)h->Linv;
+    T* Pt = (T*)h->crPt;
+    T* P = (T*)h->crP;
+    T* Qt = (T*)h->crQt;
+    T* Q = (T*)h->crQ;
+    const size_t smem = 3 * TL * TLP * sizeof(T);
+    SLAB_CK(h, cudaFuncSetAttribute(panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SLAB_CK(h, cudaMemcpyAsync(D, h->Tb, NI * blk * sizeof(T), cudaMemcpyDeviceToDevice, h->stream));
+    if (NI > 1)
+        SLAB_CK(h, cudaMemcpyAsync(E, h->To, (NI - 1) * blk * sizeof(T), cudaMemcpyDeviceToDevice, h->stream));
+    int last = 0;
+    const std::vector<CrLevel> levels = cr_levels(NI, &last);
+    slab_status st;
+    for (const CrLevel& lv : levels) {
+        const int o0 = lv.o0, a0 = lv.o0 - lv.step, c0 = lv.o0 + lv.step, nb = lv.nb, nc = lv.nc;
+        const int64_t sb = 2 * (int64_t)lv.step * blk;           // stride between consecutive o (and a, c)
+        if ((st = cr_potrf_batch<T>(h, o0, 2 * lv.step, nb))) return st;
+        // P_o^T = E_a L_o^{-T};  Q_o^T = E_o^T L_o^{-T}
+        if ((st = gemm_tn_batched<T>(h, KC_SYRK, sp, sp, sp, T(1), E + a0 * blk, sp, sb, Lin + o0 * blk, sp, sb, T(0),
+                                     Pt + o0 * blk, sp, sb, 0, 0, nb)))
+            return st;
+        if (nc > 0) {
+            if ((st = transpose_batched<T>(h, E + o0 * blk, sb, Et, blk, sp, nc))) return st;
+            if ((st = gemm_tn_batched<T>(h, KC_SYRK, sp, sp, sp, T(1), Et, sp, blk, Lin + o0 * blk, sp, sb, T(0),
+                                         Qt + o0 * blk, sp, sb, 0, 0, nc)))
+                return st;
+        }
+        // D_a -= P_o^T P_o (lower tiles)
+        if ((st = gemm_tn_batched<T>(h, KC_SYRK, sp, sp, sp, T(-1), Pt + o0 * blk, sp, sb, Pt + o0 * blk, sp, sb, T(1),
+                                     D + a0 * blk, sp, sb, 0, 1, nb)))
+            return st;
+        if (nc > 0) {
+            // D_c -= Q_o^T Q_o (lower tiles);  E_a = -P_o^T Q_o
+            if ((st = gemm_tn_batched<T>(h, KC_SYRK, sp, sp, sp, T(-1), Qt + o0 * blk, sp, sb, Qt + o0 * blk, sp, sb,
+                                         T(1), D + c0 * blk, sp, sb, 0, 1, nc)))
+                return st;
+            if ((st = gemm_tn_batched<T>(h, KC_SYRK, sp, sp, sp, T(-1), Pt + o0 * blk, sp, sb, Qt + o0 * blk, sp, sb,
+                                         T(0), E + a0 * blk, sp, sb, 0, 0, nc)))
+                return st;
+            if ((st = transpose_batched<T>(h, Qt + o0 * blk, sb, Q + o0 * blk, sb, sp, nc))) return st;
+        }
+        if ((st = transpose_batched<T>(h, Pt + o0 * blk, sb, P + o0 * blk, sb, sp, nb))) return st;
+    }
+    return cr_potrf_batch<T>(h, last, 1, 1);
+}
+
+template <typename T>
+slab_status cr_solve(slab_handle* h, int K) {
+    const int NI = h->td.NI, sp = h->td.s_pad;
+    const int64_t blk = (int64_t)sp * sp;
+    const int64_t vb = (int64_t)sp * h->kcap;
+    T* Lin = (T*)h->Linv;
+    T* LT = (T*)h->crLT;
+    T* Pt = (T*)h->crPt;
+    T* P = (T*)h->crP;
+    T* Qt = (T*)h->crQt;
+    T* Q = (T*)h->crQ;
+    T* X = (T*)h->wX;
+    T* Z = (T*)h->wZ;
+    int last = 0;
+    const std::vector<CrLevel> levels = cr_levels(NI, &last);
+    slab_status st;
+    // out_i (K x sp, RHS-major) = beta out_i + alpha M_i v_i for the nbat strided blocks i;
+    // a single product takes the split-K path
+#define PROD(Mx, m0, V, v0, OUT, w0, alpha_, beta_, nbat, sm, sv)                                                   \
+    if ((st = (nbat) == 1                                                                                          \
+                  ? gemm_tn<T>(h, KC_SOLVE_PROD, sp, K, sp, T(alpha_), Mx + (m0) * blk, sp, V + (v0) * vb, sp,      \
+                               T(beta_), OUT + (w0) * vb, sp, 1, 0)                                               \
+                  : gemm_tn_batched<T>(h, KC_SOLVE_PROD, sp, K, sp, T(alpha_), Mx + (m0) * blk, sp, (sm) * blk,    \
+                                       V + (v0) * vb, sp, (sv) * vb, T(beta_), OUT + (w0) * vb, sp, (sv) * vb, 1, \
+                                       0, (nbat))))                                                                \
+    return st
+    for (const CrLevel& lv : levels) {
+        const int o0 = lv.o0, a0 = lv.o0 - lv.step, c0 = lv.o0 + lv.step, s2 = 2 * lv.step;
+        PROD(Lin, o0, X, o0, Z, o0, 1, 0, lv.nb, s2, s2);
+        PROD(Pt, o0, Z, o0, X, a0, -1, 1, lv.nb, s2, s2);
+        if (lv.nc > 0) PROD(Qt, o0, Z, o0, X, c0, -1, 1, lv.nc, s2, s2);
+    }
+    PROD(Lin, last, X, last, Z, last, 1, 0, 1, 1, 1);
+    PROD(LT, last, Z, last, X, last, 1, 0, 1, 1, 1);
+    for (size_t l = levels.size(); l-- > 0;) {
+        const CrLevel& lv = levels[l];
+        const int o0 = lv.o0, a0 = lv.o0 - lv.step, c0 = lv.o0 + lv.step, s2 = 2 * lv.step;
+        PROD(P, o0, X, a0, Z, o0, -1, 1, lv.nb, s2, s2);
+        if (lv.nc > 0) PROD(Q, o0, X, c0, Z, o0, -1, 1, lv.nc, s2, s2);
+        PROD(LT, o0, Z, o0, X, o0, 1, 0, lv.nb, s2, s2);
+    }
+#undef PROD
+    return SLAB_OK;
+}
+
 template slab_status sweep_factor<float>(slab_handle*);
 template slab_status sweep_factor<double>(slab_handle*);
 template slab_status sweep_solve<float>(slab_handle*, int);
 template slab_status sweep_solve<double>(slab_handle*, int);
+template slab_status cr_factor<float>(slab_handle*);
+template slab_status cr_factor<double>(slab_handle*);
+template slab_status cr_solve<float>(slab_handle*, int);
+template slab_status cr_solve<double>(slab_handle*, int);

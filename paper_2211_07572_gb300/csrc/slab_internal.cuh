@@ -64,6 +64,8 @@ struct slab_handle {
     void* tWtb;               // Helmholtz only: [NS][s+1][m*2m] W = S^{-1} B (top/bot columns)
     void* tWI;                // Helmholtz only: [NS][H][2][m][s_pad] W for the interface columns
     void* ToT;                // Helmholtz only: [NI-1][s_pad][s_pad] T_{q+1,q} (row-major)
+    int stage2;               // 0: sequential sweep (Algorithm 1), 1: odd-even elimination order
+    void *crD, *crE, *crW, *crLT, *crPt, *crP, *crQt, *crQ;   // odd-even order storage
 
     // Stage-2 data
     void* Tb;                 // [NI][s_pad][s_pad]  T_qq (kept as assembled)
@@ -163,6 +165,10 @@ template <typename T> slab_status assemble_T(slab_handle* h);
 // stage 2 (dense.cu)
 template <typename T> slab_status sweep_factor(slab_handle* h);
 template <typename T> slab_status sweep_solve(slab_handle* h, int K);
+// odd-even elimination order of T (SPD kinds)
+int cr_max_batch(int NI);
+template <typename T> slab_status cr_factor(slab_handle* h);
+template <typename T> slab_status cr_solve(slab_handle* h, int K);
 
 // tensor-core product (tcgemm.cu): C = alpha A B^T + beta C, FP32, A [M][K], B [N][K] row-major
 struct TcGemmArgs {

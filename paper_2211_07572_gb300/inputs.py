@@ -145,32 +145,37 @@ def constant_helmholtz(n: int, b: int, omega: float, rhs_seed: int = 7, k: int =
                    c=np.ones((n + 1, n + 1)), omega=omega, f=normal_rhs(2, n, k, rhs_seed))
 
 
-# The five workloads (sizes and seeds of the paper-shaped synthetic configs).
-def config_c1() -> Problem:
+# The workloads, named by what they are (sizes and seeds fixed here).
+def poisson_sine_128() -> Problem:
+    """Poisson, n = 128, b = 16, manufactured sine solution."""
     return poisson_sine(128, 16)
 
 
-def config_c2(k: int = 64, n: int = 2048, b: int = 32) -> Problem:
+def diffusion_2d_2048(k: int = 64, n: int = 2048, b: int = 32) -> Problem:
+    """2-D variable-coefficient diffusion, n = 2048, b = 32, 64 random loads."""
     return diffusion(n, b, k, dim=2, n_modes=16, field_seed=2, rhs_seed=102)
 
 
-def config_c3(n: int = 4096, b: int = 32) -> Problem:
+def helmholtz_2d_4096(n: int = 4096, b: int = 32) -> Problem:
+    """2-D variable-speed Helmholtz, n = 4096, b = 32, 10 points per wavelength, point source."""
     return helmholtz(n, b, dim=2, n_modes=8, field_seed=3)
 
 
-def config_c4(k: int = 16, n: int = 96, b: int = 8) -> Problem:
+def diffusion_3d_96(k: int = 16, n: int = 96, b: int = 8) -> Problem:
+    """3-D variable-coefficient diffusion, n = 96, b = 8, 16 random loads."""
     return diffusion(n, b, k, dim=3, n_modes=8, field_seed=4, rhs_seed=104)
 
 
-C5_SIZES = (256, 384, 512, 768, 1024)
+ADJOINT_BATCH_SIZES = (256, 384, 512, 768, 1024)
 
 
-def config_c5_sizes(count: int = 256, seed: int = 5) -> np.ndarray:
+def adjoint_batch_sizes(count: int = 256, seed: int = 5) -> np.ndarray:
+    """Grid sizes n of the batched adjoint workload's instances (uneven mix)."""
     rng = np.random.default_rng(seed)
-    return np.asarray(C5_SIZES)[rng.integers(0, len(C5_SIZES), size=count)]
+    return np.asarray(ADJOINT_BATCH_SIZES)[rng.integers(0, len(ADJOINT_BATCH_SIZES), size=count)]
 
 
-def config_c5_instance(i: int, n: int, b: int = 16) -> dict:
+def adjoint_instance(i: int, n: int, b: int = 16) -> dict:
     """Instance i of the batched adjoint workload: kappa, f, u_target and 32 probe nodes."""
     g = fourier_field(2, n, 16, 1000 + i, normalize="var")
     f = normal_rhs(2, n, 1, 2000 + i)

@@ -16,6 +16,7 @@ import torch
 from . import _lib
 
 _PREC = {"fp64": _lib.PREC_FP64, "fp32": _lib.PREC_FP32}
+_STAGE2 = {"auto": 0, "sweep": 1, "oddeven": 2}
 
 
 def _dev(x, device) -> torch.Tensor:
@@ -42,7 +43,8 @@ class SlabSolver:
 
     def __init__(self, dim: int, n: int, b: int, kind: int, kappa=None, c=None, omega: float = 0.0,
                  precision: str = "fp32", rtol: float = 1e-10, max_refine: int = 30,
-                 stream: Optional[torch.cuda.Stream] = None, device=None, profile: bool = False):
+                 stream: Optional[torch.cuda.Stream] = None, device=None, profile: bool = False,
+                 stage2: str = "auto"):
         self.lib = _lib.load()
         self.device = (torch.device(device) if device is not None
                        else torch.device("cuda", torch.cuda.current_device()))
@@ -59,6 +61,7 @@ class SlabSolver:
         opts.max_refine = int(max_refine)
         opts.stream = ctypes.c_void_p(self.stream.cuda_stream)
         opts.profile = int(profile)
+        opts.stage2 = _STAGE2[stage2]
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             _lib.check(self.lib.slab_factor(ctypes.byref(grid), ctypes.byref(co), int(b), ctypes.byref(opts),

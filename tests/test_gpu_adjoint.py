@@ -36,9 +36,9 @@ def _solve(n, b, kappa, f):
 @pytest.mark.parametrize("inst,delta,tol", [(0, 1e-4, 1e-6), (1, 1e-4, 1e-6), (0, 1e-6, 1e-4)])
 def test_adjoint_gradient_vs_central_differences(inst, delta, tol):
     assert torch.cuda.is_available()
-    sizes = inputs.config_c5_sizes()
+    sizes = inputs.adjoint_batch_sizes()
     n = int(min(sizes[inst], 384))               # the two smallest sizes keep the test short
-    d = inputs.config_c5_instance(inst, n)
+    d = inputs.adjoint_instance(inst, n)
     kappa = d["kappa"]
     f = torch.from_numpy(d["f"]).cuda()
     ut = torch.from_numpy(d["u_target"]).cuda()
@@ -67,8 +67,8 @@ def test_adjoint_gradient_vs_central_differences(inst, delta, tol):
 
 def test_adjoint_gradient_matches_oracle_on_instance():
     n = 256
-    d = inputs.config_c5_instance(3, n)
-    p = inputs.Problem("c5", 2, n, d["b"], inputs.DIFFUSION, kappa=d["kappa"], f=d["f"])
+    d = inputs.adjoint_instance(3, n)
+    p = inputs.Problem("adjoint", 2, n, d["b"], inputs.DIFFUSION, kappa=d["kappa"], f=d["f"])
     L, u_o, lam_o, g_o = oracle.adjoint_gradient(p, d["u_target"])
     s = _solver(n, d["b"], d["kappa"])
     u, _, _ = s.solve(torch.from_numpy(d["f"]).cuda(), allow_noconv=True)
@@ -81,7 +81,7 @@ def test_adjoint_gradient_matches_oracle_on_instance():
 def test_autograd_function_backward_is_the_adjoint():
     from paper_2211_07572_gb300.solver import SlabSolveFunction
     n, b = 64, 16
-    d = inputs.config_c5_instance(5, 256)
+    d = inputs.adjoint_instance(5, 256)
     kappa = torch.from_numpy(np.exp(inputs.fourier_field(2, n, 16, seed=1005))).cuda().requires_grad_(True)
     f = torch.from_numpy(inputs.normal_rhs(2, n, 1, 2005)).cuda().requires_grad_(True)
     ut = torch.from_numpy(inputs.normal_rhs(2, n, 1, 3005)).cuda()

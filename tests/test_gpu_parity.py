@@ -25,10 +25,10 @@ def _need_cuda():
     oracle.build()
 
 
-def _solver(p, precision="fp64", rtol=1e-10, max_refine=30):
+def _solver(p, precision="fp64", rtol=1e-10, max_refine=30, stage2="auto"):
     from paper_2211_07572_gb300.solver import SlabSolver
     return SlabSolver(p.dim, p.n, p.b, p.kind, kappa=p.kappa, c=p.c, omega=p.omega, precision=precision,
-                      rtol=rtol, max_refine=max_refine)
+                      rtol=rtol, max_refine=max_refine, stage2=stage2)
 
 
 def _problem(n, b, kind, k=2, seed=0):
@@ -98,6 +98,29 @@ def test_interface_solve_matches_oracle(n, b, kind, precision):
     assert np.abs(ut - ut_o).max() <= tol * np.abs(ut_o).max()
 
 
+@pytest.mark.parametrize("stage2", ["sweep", "oddeven"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("n,b", [(48, 16), (64, 16), (96, 16), (96, 8), (40, 2)])
+def test_stage2_orders_match_oracle(n, b, precision, stage2):
+    """Both elimination orders of T (Algorithm 1's sweep and the odd-even order) give
+    u~ = T^-1 f~ of the oracle; N_I = 2, 3, 5, 11, 19 covers levels with and without a
+    right neighbour for the last eliminated block.  T itself is left intact by the factor."""
+    p = _problem(n, b, inputs.DIFFUSION, k=3, seed=5)
+    s = _solver(p, precision, stage2=stage2)
+    A = oracle.assemble_problem(p)
+    Td, Tl, Tu = oracle.reduced_system(A, 2, n, b)
+    ft = oracle.reduced_rhs(A, p.f, 2, n, b)
+    ut_o = np.concatenate(oracle.sweep_solve(Tl, Tu, oracle.sweep_build(Td, Tl, Tu), ft), axis=1)
+    ut = s.interface_solve(torch.from_numpy(np.concatenate(ft, axis=1)).cuda()).cpu().numpy()
+    tol = 1e-10 if precision == "fp64" else 1e-3
+    assert np.abs(ut - ut_o).max() <= tol * np.abs(ut_o).max()
+    scale = max(np.abs(t).max() for t in Td)
+    last = len(Td) - 1
+    assert np.abs(s.T_block(0, last) - Td[last]).max() <= TOL[precision] * scale
+    if Tu:
+        assert np.abs(s.T_block(1, 0) - Tu[0]).max() <= TOL[precision] * scale
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("n,b,kind", CASES[:4])
 def test_interior_solve_matches_oracle(n, b, kind, precision):
@@ -112,9 +135,9 @@ def test_interior_solve_matches_oracle(n, b, kind, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_poisson_c1_closed_form(precision):
-    """C1 (n = 128, b = 16): the discrete solution is exactly r sin(pi x) sin(pi y)."""
-    p = inputs.config_c1()
+def test_poisson_sine_closed_form(precision):
+    """Poisson n = 128, b = 16: the discrete solution is exactly r sin(pi x) sin(pi y)."""
+    p = inputs.poisson_sine_128()
     s = _solver(p, precision, rtol=1e-13)
     u, rel, it = s.solve(torch.from_numpy(p.f).cuda(), allow_noconv=True)   # 1e-13 is below the FP64 floor
     u = u.cpu().numpy()
@@ -127,11 +150,12 @@ def test_poisson_c1_closed_form(precision):
     assert np.linalg.norm(u - oracle.solve(p)) / np.linalg.norm(exact) <= 1e-10
 
 
+@pytest.mark.parametrize("stage2", ["sweep", "oddeven"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_diffusion_solve_matches_oracle(precision):
-    """End to end (A0-A8) on a C2-shaped problem at a size the oracle finishes in seconds."""
+def test_diffusion_solve_matches_oracle(precision, stage2):
+    """End to end (A0-A8) on a problem shaped like the n = 2048 diffusion workload at a size the oracle finishes in seconds."""
     p = inputs.diffusion(256, 16, k=4, n_modes=16, field_seed=2, rhs_seed=102)
-    s = _solver(p, precision, rtol=1e-13)
+    s = _solver(p, precision, rtol=1e-13, stage2=stage2)
     u, rel, it = s.solve(torch.from_numpy(p.f).cuda(), allow_noconv=True)
     u = u.cpu().numpy()
     A = oracle.assemble_problem(p)
@@ -181,6 +205,12 @@ def test_invalid_arguments_are_rejected():
     # a coefficient field with a non-positive region makes the operator indefinite
     bad = p.kappa.copy()
     bad[20:40, 20:40] = -1.0
+    for stage2 in ("sweep", "oddeven"):
+        with pytest.raises(SlabError) as ei:
+            _solver(inputs.Problem("x", 2, 64, 8, inputs.DIFFUSION, kappa=bad), stage2=stage2)
+        assert ei.value.status == 3
+    # the odd-even order is Cholesky based: not offered for the indefinite kind
+    hp = inputs.helmholtz(64, 8, n_modes=8, field_seed=3)
     with pytest.raises(SlabError) as ei:
-        _solver(inputs.Problem("x", 2, 64, 8, inputs.DIFFUSION, kappa=bad))
-    assert ei.value.status == 3
+        _solver(hp, stage2="oddeven")
+    assert ei.value.status == 7

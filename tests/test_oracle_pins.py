@@ -76,10 +76,10 @@ def test_diffusion_symmetric_and_row_sums(oracle_mod):
 # --------------------------------------------------------------------------- solves
 
 def test_poisson_sine_closed_form_n128(oracle_mod):
-    """C1: the discrete solution is exactly r sin sin, r from the golden file."""
+    """Poisson n = 128: the discrete solution is exactly r sin sin, r from the golden file."""
     gold = {int(l.split()[0]): float(l.split()[1]) for l in open(os.path.join(GOLD, "poisson_sine.txt"))
             if l.strip() and not l.startswith("#")}
-    p = inputs.config_c1()
+    p = inputs.poisson_sine_128()
     u = oracle_mod.solve(p)
     r = gold[128]
     err = np.abs(u - r * p.u_exact).max() / np.abs(r * p.u_exact).max()
