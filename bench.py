@@ -27,7 +27,10 @@ sys.path.insert(0, ROOT)
 METRIC = "factor+solve s at 1e-10 rel. residual vs plain FP64 GPU; dense TFLOP/s % of peak"
 WORKLOAD = dict(workload="2D var-coef diffusion n=2048 b=32 k=64 (kappa=exp(16-mode field), f~N(0,1)), "
                          "FP32 factor + FP64 refinement to 1e-10",
-                n=2048, b=32, k=64, rtol=1e-10)
+                n=2048, b=32, k=64, rtol=1e-10, kind="diffusion")
+HELMHOLTZ = dict(workload="2D Helmholtz n=4096 b=32 k=1 (c=1+0.3 r, 8-mode field, 10 points per wavelength, "
+                          "point source), FP32 pivoted factor + FP64 refinement to 1e-10",
+                 n=4096, b=32, k=1, rtol=1e-10, kind="helmholtz")
 SMS = 152
 FP32_LANES_PER_SM = 128
 
@@ -115,7 +118,7 @@ def oddeven_levels(NI):
     return out
 
 
-def work_model(n, b, k, passes, stage2="sweep"):
+def work_model(n, b, k, passes, stage2="sweep", kind="diffusion"):
     """Algorithmic flops (or bytes) per kernel class for one factor + `passes` solve passes.
 
     Explicit inverse factors (L^{-1}, L^{-T}) are stored and applied as dense blocks, so
@@ -145,6 +148,27 @@ def work_model(n, b, k, passes, stage2="sweep"):
                 trail += 2 * 64 * (nn * (nn + 1) / 2 + (rows - sp) * nn)
     W["panel"] = pan
     W["trailing"] = trail
+    if kind == "helmholtz":
+        # blocked Gauss-Jordan of [S | T | I] over [T | T]: rank-64 updates of the top and bottom rows
+        pan = trail = 0.0
+        for j in range(NI):
+            wt = (3 if j < NI - 1 else 2) * sp
+            for kb in range(sp // 64):
+                c0 = 64 * kb
+                trail += 2.0 * sp * (wt - c0 - 64) * 64
+                if j < NI - 1:
+                    trail += 2.0 * sp * (2 * sp - c0 - 64) * 64
+                pan += 2.0 * 64 * 64 * (wt - c0 - 64) + 2.0 * 64 ** 3
+        W["panel"] = pan
+        W["trailing"] = trail
+        W["schur_update"] = 0.0
+        W["sweep_products"] = passes * (3 * NI - 2) * 2.0 * sp * sp * k
+        W["tree_up"] = passes * NS * k * sum(2 * (m * m + 2 * m * m + 2 * w * m) for (_, _, w) in nodes)
+        W["tree_down"] = passes * NS * k * sum(2 * (2 * m * m + 2 * w * m) for (_, _, w) in nodes)
+        W["stencil"] = passes * 24.0 * s * s * k
+        W["tree_factor"] = NS * sum(2 * (2 * m ** 3 + 2 * m ** 3 + 4 * m ** 3 + 2 * w * 3 * m * m)
+                                    for (_, _, w) in nodes)
+        return W
     if stage2 == "oddeven":
         lv = oddeven_levels(NI)
         nb, nc = sum(x for x, _ in lv), sum(y for _, y in lv)
@@ -194,28 +218,42 @@ def run_gpu(args):
     from paper_2211_07572_gb300 import inputs
     from paper_2211_07572_gb300.solver import SlabSolver
 
-    W = dict(WORKLOAD)
+    W = dict(HELMHOLTZ if args.workload == "helmholtz4096" else WORKLOAD)
+    helm = W["kind"] == "helmholtz"
     if args.n:
         W.update(n=args.n, b=args.b or W["b"], k=args.k or W["k"])
-        W["workload"] = f"2D var-coef diffusion n={W['n']} b={W['b']} k={W['k']}"
+        W["workload"] = (f"2D Helmholtz n={W['n']} b={W['b']} point source" if helm else
+                         f"2D var-coef diffusion n={W['n']} b={W['b']} k={W['k']}")
     n, b, k = W["n"], W["b"], W["k"]
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
-    p = inputs.diffusion(n, b, k=0, n_modes=16, field_seed=2, rhs_seed=102)
-    kappa = torch.from_numpy(p.kappa).to(dev)
-    f_host = torch.from_numpy(inputs.normal_rhs(2, n, k, 102)).pin_memory()
+    if helm:
+        p = inputs.helmholtz(n, b, dim=2, n_modes=8, field_seed=3)
+        coeff = dict(kind=inputs.HELMHOLTZ, c=torch.from_numpy(p.c).to(dev), omega=p.omega)
+        f_host = torch.from_numpy(np.ascontiguousarray(p.f[:k])).pin_memory()
+    else:
+        p = inputs.diffusion(n, b, k=0, n_modes=16, field_seed=2, rhs_seed=102)
+        coeff = dict(kind=inputs.DIFFUSION, kappa=torch.from_numpy(p.kappa).to(dev))
+        f_host = torch.from_numpy(inputs.normal_rhs(2, n, k, 102)).pin_memory()
     f = f_host.to(dev)
     u = torch.empty_like(f)
     stream = torch.cuda.current_stream(dev)
     prec = args.precision
 
     NI = n // b - 1
-    stage2 = args.stage2 if args.stage2 != "auto" else ("oddeven" if NI >= 4 else "sweep")
+    if helm:
+        stage2 = "sweep"
+    else:
+        stage2 = args.stage2 if args.stage2 != "auto" else ("oddeven" if NI >= 4 and prec == "fp32" else "sweep")
     W["stage2"] = stage2
 
+    def solver(precision, **kw):
+        kk = dict(coeff)
+        kind = kk.pop("kind")
+        return SlabSolver(2, n, b, kind, precision=precision, stream=stream, device=dev, **kk, **kw)
+
     def make():
-        return SlabSolver(2, n, b, inputs.DIFFUSION, kappa=kappa, precision=prec, rtol=W["rtol"], max_refine=40,
-                          stream=stream, device=dev, stage2=stage2)
+        return solver(prec, rtol=W["rtol"], max_refine=40, stage2=stage2)
 
     def step(f_in, u_out, counts=None):
         s = make()
@@ -266,8 +304,7 @@ def run_gpu(args):
     t_fac = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     t_f0.record(stream)
-    s = SlabSolver(2, n, b, inputs.DIFFUSION, kappa=kappa, precision=prec, rtol=W["rtol"], max_refine=40,
-                   stream=stream, device=dev, profile=True, stage2=stage2)
+    s = solver(prec, rtol=W["rtol"], max_refine=40, profile=True, stage2=stage2)
     t_fac.record(stream)
     _, rel1, it1 = s.solve(f, u, allow_noconv=True)
     t_end.record(stream)
@@ -277,7 +314,7 @@ def run_gpu(args):
     factor_ms = t_f0.elapsed_time(t_fac)
     solve_ms = t_fac.elapsed_time(t_end)
     passes = it1 + 1
-    work = work_model(n, b, k, passes, stage2)
+    work = work_model(n, b, k, passes, stage2, W["kind"])
     peaks = _peaks()
     dom = max((c for c in cls_ms if c in BOUND), key=lambda c: cls_ms[c])
     roof = roofline_for(dom, cls_ms[dom], cls_cnt[dom], work, peaks, clocks)
@@ -310,25 +347,22 @@ def run_gpu(args):
         "clocks": clocks,
     }
     if args.fp64_comparator and prec == "fp32":
-        line["fp64_gpu"] = fp64_comparator(n, b, kappa, f, stream, dev, stage2)
+        line["fp64_gpu"] = fp64_comparator(lambda: solver("fp64", rtol=1.0, max_refine=0), f)
         line["fp64_gpu"]["mixed_speedup"] = line["fp64_gpu"]["value"] / line["value"]
     if args.cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(n, b, k)
+        line["cpu_baseline"] = cpu_baseline(n, b, k, kind=W["kind"], n_sample=256 if helm else 512)
     print(json.dumps(line))
 
 
-def fp64_comparator(n, b, kappa, f, stream, dev, stage2):
+def fp64_comparator(make64, f):
     """Plain FP64 GPU path: same algorithm, all FP64, one pass (no refinement)."""
     import numpy as np
     import torch
-
-    from paper_2211_07572_gb300 import inputs
-    from paper_2211_07572_gb300.solver import SlabSolver
     u = torch.empty_like(f)
+    stream = torch.cuda.current_stream()
 
     def one():
-        s = SlabSolver(2, n, b, inputs.DIFFUSION, kappa=kappa, precision="fp64", rtol=1.0, max_refine=0,
-                       stream=stream, device=dev, stage2=stage2)
+        s = make64()
         _, rel, _ = s.solve(f, u)
         s.close()
         return rel
@@ -345,18 +379,22 @@ def fp64_comparator(n, b, kappa, f, stream, dev, stage2):
             "path": "FP64 factor and solve on the same kernels (SIMT FP64), single pass"}
 
 
-def cpu_baseline(n_full, b, k, n_sample=512):
+def cpu_baseline(n_full, b, k, n_sample=512, kind="diffusion"):
     """Oracle (banded LU, FP64) on a bounded sample of the workload: n = n_sample, same b, k rhs.
 
     Extrapolated to the full size by the banded-LU cost model: factor ~ n^4, solve ~ k n^3.
+    The Helmholtz sample keeps 10 points per wavelength and pivots (partial pivoting).
     """
     import oracle
     from paper_2211_07572_gb300 import inputs
     oracle.build()
-    p = inputs.diffusion(n_sample, b, k=k, n_modes=16, field_seed=2, rhs_seed=102)
+    if kind == "helmholtz":
+        p = inputs.helmholtz(n_sample, b, dim=2, n_modes=8, field_seed=3)
+    else:
+        p = inputs.diffusion(n_sample, b, k=k, n_modes=16, field_seed=2, rhs_seed=102)
     t0 = time.perf_counter()
     A = oracle.assemble_problem(p)
-    lu = oracle.BandLU(A, n_sample - 1, pivot=False)
+    lu = oracle.BandLU(A, n_sample - 1, pivot=kind == "helmholtz")
     t1 = time.perf_counter()
     u = lu.solve(p.f)
     t2 = time.perf_counter()
@@ -404,6 +442,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-fp64", dest="fp64_comparator", action="store_false")
     ap.add_argument("--once", action="store_true", help="run one step only (for profilers)")
+    ap.add_argument("--workload", default="diffusion2048", choices=["diffusion2048", "helmholtz4096"],
+                    help="diffusion2048: the default bench line; helmholtz4096: the indefinite workload")
     ap.add_argument("--stage2", default="auto", choices=["auto", "sweep", "oddeven"],
                     help="elimination order of T (auto: odd-even for 4 or more interfaces)")
     args = ap.parse_args()

@@ -70,7 +70,9 @@ typedef enum {
  * eliminating every other remaining block in one batch; Cholesky based, so POISSON
  * and DIFFUSION only (SLAB_EUNSUPPORTED for HELMHOLTZ).  It holds about 9 s_pad^2
  * numbers per interface in the factor versus about 5 for SWEEP.
- * AUTO: ODDEVEN for POISSON / DIFFUSION with N_I >= 4, SWEEP otherwise.
+ * ODDEVEN does about 4x the dense flops of SWEEP but in log2(N_I) batched levels, which pays
+ * on the tensor-core (FP32) path; on the SIMT FP64 path SWEEP is faster.
+ * AUTO: ODDEVEN for POISSON / DIFFUSION with N_I >= 4 and an FP32 factor, SWEEP otherwise.
  */
 typedef enum {
     SLAB_STAGE2_AUTO = 0,
@@ -99,12 +101,16 @@ typedef struct {
     void* stream;           /* cudaStream_t all work is ordered on (NULL: legacy default) */
     int profile;            /* 1: time every kernel launch from the start (see slab_profile) */
     int stage2;             /* slab_stage2 */
+    int interface_prec;     /* slab_precision of Stage 2 (the interface elimination and sweep),
+                               or -1: FP64 for HELMHOLTZ with an FP32 factor, else factor_prec.
+                               FP32 slab trees with an FP64 interface system is the mixed mode;
+                               an FP64 factor with an FP32 interface is SLAB_EINVAL */
 } slab_opts;
 
 typedef struct slab_handle slab_handle;
 
 /* Fill opts with the defaults: FP32 factor, rtol 1e-10, max_refine 30, default stream,
- * SLAB_STAGE2_AUTO. */
+ * SLAB_STAGE2_AUTO, interface_prec -1. */
 void slab_default_opts(slab_opts* opts);
 
 /*
@@ -114,8 +120,10 @@ void slab_default_opts(slab_opts* opts);
  * Requires b >= 2 and n % b == 0, 2 <= b <= 33, n/b >= 2 (SLAB_EINVAL otherwise);
  * dim == 2 (SLAB_EUNSUPPORTED otherwise).  POISSON and DIFFUSION are factored by
  * Cholesky (slab separators and Stage 2); HELMHOLTZ (indefinite) by Gauss-Jordan
- * with partial pivoting, both in the slab separators and for S_j^{-1} in Stage 2
- * (Algorithm 1 as printed), in opts.factor_prec.  A zero / non-positive pivot
+ * with partial pivoting in the slab separators, and in Stage 2 (Algorithm 1 as printed) by a
+ * blocked Gauss-Jordan elimination of [S_j | T_{j,j+1} | I] with tournament pivoting
+ * (64-column panels; each panel's pivot rows are the winners of pairwise partial-pivoting
+ * eliminations over groups of 128 candidate rows), in opts.factor_prec.  A zero / non-positive pivot
  * returns SLAB_ESINGULAR.  kappa/c are read during the call only.  On success
  * *out is a new handle.  Synchronises opts->stream (returns after the factor).
  */
@@ -127,7 +135,9 @@ slab_status slab_factor(const slab_grid* grid, const slab_coeffs* coeffs, int b,
  * f, u: device, [k][(n-1)^d]; u is overwritten.  relres_out: HOST, k entries
  * (may be NULL) receiving ||f - A u||_2/||f||_2; iters_out: HOST (may be NULL)
  * receiving the number of refinement steps taken.  Returns SLAB_ENOCONV when
- * max_refine steps did not reach rtol (u then holds the last iterate).
+ * max_refine steps did not reach rtol, when the residual stagnated (two steps without halving
+ * the worst relative residual), or when it is not finite (relres_out then holds NaN); u holds
+ * the last iterate.
  */
 slab_status slab_solve(slab_handle* h, const double* f, double* u, int k,
                        double* relres_out, int* iters_out);

@@ -27,7 +27,7 @@ class SlabCoeffs(ctypes.Structure):
 class SlabOpts(ctypes.Structure):
     _fields_ = [("factor_prec", c_int), ("pivot", c_int), ("rtol", c_double), ("max_refine", c_int),
                 ("krylov", c_int), ("stream", c_void_p), ("profile", c_int),
-                ("stage2", c_int)]
+                ("stage2", c_int), ("interface_prec", c_int)]
 
 
 class SlabError(RuntimeError):

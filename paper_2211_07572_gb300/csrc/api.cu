@@ -7,6 +7,9 @@
 #include <new>
 #include <vector>
 
+#include <cstdio>
+#include <limits>
+
 #include "slab_internal.cuh"
 
 slab_status slab_cuda_check(slab_handle* h, cudaError_t e) {
@@ -65,6 +68,7 @@ slab_status ensure_workspace(slab_handle* h, int k) {
     if (h->kcap < kc) {
         const int64_t nodes = (int64_t)d.NS * (d.s + 1);
         dfree(h->wYv); dfree(h->wGtb); dfree(h->wXs); dfree(h->wFi); dfree(h->wX); dfree(h->wZ);
+        dfree(h->wX2); dfree(h->wZ2);
         h->kcap = 0;
         TRY(dalloc(h, &h->wYv, nodes * d.m * kc * h->rsz));
         TRY(dalloc(h, &h->wGtb, nodes * 2 * d.m * kc * h->rsz));
@@ -72,6 +76,10 @@ slab_status ensure_workspace(slab_handle* h, int k) {
         TRY(dalloc(h, &h->wFi, (int64_t)d.NS * 2 * d.s_pad * kc * h->rsz));
         TRY(dalloc(h, &h->wX, (int64_t)d.NI * d.s_pad * kc * h->rsz));
         TRY(dalloc(h, &h->wZ, (int64_t)d.NI * d.s_pad * kc * h->rsz));
+        if (h->prec2 != h->prec) {
+            TRY(dalloc(h, &h->wX2, (int64_t)d.NI * d.s_pad * kc * h->rsz2));
+            TRY(dalloc(h, &h->wZ2, (int64_t)d.NI * d.s_pad * kc * h->rsz2));
+        }
         h->kcap = kc;
     }
     if (!h->wVtk) {
@@ -82,7 +90,7 @@ slab_status ensure_workspace(slab_handle* h, int k) {
         SLAB_CK(h, cudaMemsetAsync(h->wVtk, 0, nt * sizeof(unsigned), h->stream));
     }
     if (!h->wPart) {
-        TRY(dalloc(h, &h->wPart, (int64_t)(d.s_pad / SLAB_TILE) * SLAB_SPLITK * SLAB_TILE * SLAB_TILE * h->rsz));
+        TRY(dalloc(h, &h->wPart, (int64_t)(d.s_pad / SLAB_TILE) * SLAB_SPLITK * SLAB_TILE * SLAB_TILE * 8));
         void* tk = nullptr;
         TRY(dalloc(h, &tk, (size_t)(d.s_pad / SLAB_TILE) * sizeof(unsigned)));
         h->wTickets = (unsigned*)tk;
@@ -107,13 +115,38 @@ slab_status ensure_resid(slab_handle* h, int k) {
     return SLAB_OK;
 }
 
+// Mixed mode: the interface sweep runs in the Stage-2 scalar on wX2 / wZ2, which this view
+// swaps in for wX / wZ for its lifetime.
+struct Stage2Vectors {
+    slab_handle* h;
+    explicit Stage2Vectors(slab_handle* hh) : h(hh) { swap(); }
+    ~Stage2Vectors() { swap(); }
+    void swap() {
+        void* t = h->wX; h->wX = h->wX2; h->wX2 = t;
+        t = h->wZ; h->wZ = h->wZ2; h->wZ2 = t;
+    }
+};
+
+// Algorithm 2 on the interface vectors wX (Stage-1 scalar), in the Stage-2 scalar.
+slab_status interface_sweep(slab_handle* h, int K) {
+    if (h->prec2 == h->prec)
+        return h->prec == SLAB_PREC_FP64 ? sweep_solve<double>(h, K) : sweep_solve<float>(h, K);
+    const int64_t n = (int64_t)h->td.NI * h->kcap * h->td.s_pad;
+    TRY(widen_to_double(h, (const float*)h->wX, (double*)h->wX2, n));
+    {
+        Stage2Vectors v(h);
+        TRY(sweep_solve<double>(h, K));
+    }
+    return narrow_to_float(h, (const double*)h->wX2, (float*)h->wX, n);
+}
+
 template <typename T>
 slab_status solve_pass(slab_handle* h, const double* F, double fscale, double* U, int accumulate, int k) {
     const int kc = h->kcap;
     for (int r0 = 0; r0 < k; r0 += kc) {
         const int K = (k - r0) < kc ? (k - r0) : kc;
         TRY(tree_up_gather<T>(h, F, fscale, r0, K));
-        TRY(sweep_solve<T>(h, K));
+        TRY(interface_sweep(h, K));
         TRY(tree_down_scatter<T>(h, U, accumulate, r0, K));
     }
     return SLAB_OK;
@@ -123,6 +156,23 @@ slab_status pass(slab_handle* h, const double* F, double fscale, double* U, int 
     return h->prec == SLAB_PREC_FP64 ? solve_pass<double>(h, F, fscale, U, accumulate, k)
                                      : solve_pass<float>(h, F, fscale, U, accumulate, k);
 }
+
+}  // namespace
+
+bool slab_debug() {
+    static const bool on = std::getenv("SLAB_DEBUG") != nullptr;
+    return on;
+}
+
+unsigned slab_debug_status(slab_handle* h, const char* where, int a, int b) {
+    cudaStreamSynchronize(h->stream);
+    unsigned st = 0;
+    cudaMemcpy(&st, h->dstatus, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    if (st) std::fprintf(stderr, "slab: status 0x%x after %s (%d, %d)\n", st, where, a, b);
+    return st;
+}
+
+namespace {
 
 slab_status sync_status(slab_handle* h) {
     SLAB_CK(h, cudaStreamSynchronize(h->stream));
@@ -142,9 +192,23 @@ slab_status sync_status(slab_handle* h) {
 template <typename T>
 slab_status factor_impl(slab_handle* h) {
     TRY(tree_factor<T>(h));
-    TRY(assemble_T<T>(h));
-    TRY(sweep_factor<T>(h));
-    return SLAB_OK;
+    if (h->prec2 == h->prec) {
+        TRY(assemble_T<T>(h));
+        return sweep_factor<T>(h);
+    }
+    // mixed mode: assemble T in the Stage-1 scalar, widen it, eliminate in the Stage-2 scalar
+    void* Tb2 = h->Tb;
+    void* To2 = h->To;
+    h->Tb = h->Tb1;
+    h->To = h->To1;
+    const slab_status st = assemble_T<T>(h);
+    h->Tb = Tb2;
+    h->To = To2;
+    TRY(st);
+    const int64_t blk = (int64_t)h->td.s_pad * h->td.s_pad;
+    TRY(widen_to_double(h, (const float*)h->Tb1, (double*)h->Tb, h->td.NI * blk));
+    TRY(widen_to_double(h, (const float*)h->To1, (double*)h->To, (h->td.NI - 1) * blk));
+    return sweep_factor<double>(h);
 }
 
 struct ProfRecord {
@@ -251,12 +315,13 @@ void slab_destroy(slab_handle* h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
     free_workspace(h);
+    dfree(h->wX2); dfree(h->wZ2);
     void* p;
     p = h->AX; dfree(p); p = h->AY; dfree(p); p = h->DG; dfree(p); p = h->kappa; dfree(p);
     dfree(h->tLinv); dfree(h->tZtb); dfree(h->tRtb); dfree(h->tZI); dfree(h->tRI);
-    dfree(h->tWtb); dfree(h->tWI); dfree(h->ToT); dfree(h->dscratch);
+    dfree(h->tWtb); dfree(h->tWI); dfree(h->ToT); dfree(h->dscratch); dfree(h->gjw);
     dfree(h->Tb); dfree(h->To); dfree(h->Fct); dfree(h->Linv); dfree(h->Y);
-    dfree(h->crD); dfree(h->crE); dfree(h->crW); dfree(h->crLT);
+    dfree(h->crD); dfree(h->crE); dfree(h->crW); dfree(h->crLT); dfree(h->Tb1); dfree(h->To1);
     dfree(h->crPt); dfree(h->crP); dfree(h->crQt); dfree(h->crQ);
     p = h->dstatus; dfree(p);
     prof_free(h);
@@ -278,6 +343,10 @@ slab_status slab_factor(const slab_grid* grid, const slab_coeffs* co, int b, con
     if (co->kind == SLAB_HELMHOLTZ && !co->c) return SLAB_EINVAL;
     if (o.factor_prec != SLAB_PREC_FP32 && o.factor_prec != SLAB_PREC_FP64) return SLAB_EINVAL;
     if (o.stage2 < SLAB_STAGE2_AUTO || o.stage2 > SLAB_STAGE2_ODDEVEN) return SLAB_EINVAL;
+    int prec2 = o.interface_prec;
+    if (prec2 == -1) prec2 = (co->kind == SLAB_HELMHOLTZ) ? SLAB_PREC_FP64 : o.factor_prec;
+    if (prec2 != SLAB_PREC_FP32 && prec2 != SLAB_PREC_FP64) return SLAB_EINVAL;
+    if (o.factor_prec == SLAB_PREC_FP64 && prec2 == SLAB_PREC_FP32) return SLAB_EINVAL;
     if (grid->dim != 2) return SLAB_EUNSUPPORTED;
     if (b - 1 > SLAB_MAXM) return SLAB_EUNSUPPORTED;
     if (o.stage2 == SLAB_STAGE2_ODDEVEN && co->kind == SLAB_HELMHOLTZ) return SLAB_EUNSUPPORTED;
@@ -288,6 +357,8 @@ slab_status slab_factor(const slab_grid* grid, const slab_coeffs* co, int b, con
     h->dim = grid->dim; h->n = n; h->b = b; h->kind = co->kind; h->omega = co->omega;
     h->prec = o.factor_prec;
     h->rsz = h->prec == SLAB_PREC_FP64 ? 8 : 4;
+    h->prec2 = prec2;
+    h->rsz2 = h->prec2 == SLAB_PREC_FP64 ? 8 : 4;
     h->stream = (cudaStream_t)o.stream;
     h->rtol = o.rtol;
     h->max_refine = o.max_refine;
@@ -306,6 +377,7 @@ slab_status slab_factor(const slab_grid* grid, const slab_coeffs* co, int b, con
     slab_status st = SLAB_OK;
     const size_t nodes2 = (size_t)(n + 1) * (n + 1);
     const size_t R = h->rsz;
+    const size_t R2 = h->rsz2;
     const int64_t tn = (int64_t)d.NS * (d.s + 1);
     const int64_t blk = (int64_t)d.s_pad * d.s_pad;
     void* p;
@@ -324,30 +396,38 @@ slab_status slab_factor(const slab_grid* grid, const slab_coeffs* co, int b, con
     ALLOC(h->tRtb, tn * 4 * d.m * d.m * R);
     ALLOC(h->tZI, (int64_t)d.NS * d.H * 2 * d.m * d.s_pad * R);
     ALLOC(h->tRI, (int64_t)d.NS * d.H * 4 * d.m * d.s_pad * R);
-    ALLOC(h->Tb, d.NI * blk * R);
-    ALLOC(h->To, (d.NI - 1) * blk * R);
+    ALLOC(h->Tb, d.NI * blk * R2);
+    ALLOC(h->To, (d.NI - 1) * blk * R2);
+    if (h->prec2 != h->prec) {
+        ALLOC(h->Tb1, d.NI * blk * R);
+        ALLOC(h->To1, (d.NI - 1) * blk * R);
+    }
     h->stage2 = o.stage2 == SLAB_STAGE2_ODDEVEN ||
-                (o.stage2 == SLAB_STAGE2_AUTO && co->kind != SLAB_HELMHOLTZ && d.NI >= 4);
+                (o.stage2 == SLAB_STAGE2_AUTO && co->kind != SLAB_HELMHOLTZ && d.NI >= 4 &&
+                 h->prec2 == SLAB_PREC_FP32);
     if (h->stage2) {
-        ALLOC(h->crD, d.NI * blk * R);
-        ALLOC(h->crE, (d.NI > 1 ? d.NI - 1 : 1) * blk * R);
-        ALLOC(h->crW, (int64_t)cr_max_batch(d.NI) * 2 * blk * R);
-        ALLOC(h->crLT, d.NI * blk * R);
-        ALLOC(h->crPt, d.NI * blk * R);
-        ALLOC(h->crP, d.NI * blk * R);
-        ALLOC(h->crQt, d.NI * blk * R);
-        ALLOC(h->crQ, d.NI * blk * R);
+        ALLOC(h->crD, d.NI * blk * R2);
+        ALLOC(h->crE, (d.NI > 1 ? d.NI - 1 : 1) * blk * R2);
+        ALLOC(h->crW, (int64_t)cr_max_batch(d.NI) * 2 * blk * R2);
+        ALLOC(h->crLT, d.NI * blk * R2);
+        ALLOC(h->crPt, d.NI * blk * R2);
+        ALLOC(h->crP, d.NI * blk * R2);
+        ALLOC(h->crQt, d.NI * blk * R2);
+        ALLOC(h->crQ, d.NI * blk * R2);
+    } else if (co->kind == SLAB_HELMHOLTZ) {
+        ALLOC(h->Fct, 5 * blk * R2);                    // augmented system [S | T | I] over [T | T]
+        ALLOC(h->gjw, gj_work_bytes(d.s_pad, R2));
     } else {
-        ALLOC(h->Fct, d.NI * 3 * blk * R);
+        ALLOC(h->Fct, d.NI * 3 * blk * R2);
     }
     if (co->kind == SLAB_HELMHOLTZ) {
         ALLOC(h->tWtb, tn * 2 * d.m * d.m * R);
         ALLOC(h->tWI, (int64_t)d.NS * d.H * 2 * d.m * d.s_pad * R);
-        ALLOC(h->ToT, (d.NI - 1) * blk * R);
+        ALLOC(h->ToT, (d.NI - 1) * blk * R2);
     }
     ALLOC(h->dscratch, 256);
-    ALLOC(h->Linv, d.NI * blk * R);
-    if (!h->stage2) ALLOC(h->Y, (d.NI - 1) * blk * R);
+    ALLOC(h->Linv, d.NI * blk * R2);
+    if (!h->stage2) ALLOC(h->Y, (d.NI - 1) * blk * R2);
     ALLOC(h->dstatus, sizeof(unsigned));
 #undef ALLOC
 #define CK(call)                                                               \
@@ -368,6 +448,9 @@ slab_status slab_factor(const slab_grid* grid, const slab_coeffs* co, int b, con
         slab_destroy(h);
         return st;
     }
+    dfree(h->Tb1);                                     // mixed-mode assembly buffers
+    dfree(h->To1);
+    h->Tb1 = h->To1 = nullptr;
     *out = h;
     return SLAB_OK;
 }
@@ -410,10 +493,21 @@ slab_status slab_solve(slab_handle* h, const double* f, double* u, int k, double
                                        h->stream));
             SLAB_CK(h, cudaStreamSynchronize(h->stream));
             double worst = 0.0;
+            bool finite = true;
             for (int q = 0; q < k; ++q) {
-                const double rr = nrm[q] > 0 ? std::sqrt(nrm[q] / (nrm[k + q] > 0 ? nrm[k + q] : 1.0)) : 0.0;
+                double rr;
+                if (!std::isfinite(nrm[q])) {           // the iterate holds Inf / NaN
+                    rr = std::numeric_limits<double>::quiet_NaN();
+                    finite = false;
+                } else {
+                    rr = nrm[q] > 0 ? std::sqrt(nrm[q] / (nrm[k + q] > 0 ? nrm[k + q] : 1.0)) : 0.0;
+                }
                 if (relres_out) relres_out[q] = rr;
                 if (!(rr <= worst)) worst = rr;
+            }
+            if (!finite) {
+                result = SLAB_ENOCONV;
+                break;
             }
             if (worst <= h->rtol) break;
             // stagnation: two consecutive steps without halving the worst residual
@@ -471,7 +565,12 @@ slab_status slab_interface_solve(slab_handle* h, const double* ftilde, double* u
     const double h2 = 1.0 / ((double)h->n * (double)h->n);
     for (int r0 = 0; r0 < k; r0 += h->kcap) {
         const int K = (k - r0) < h->kcap ? (k - r0) : h->kcap;
-        if (h->prec == SLAB_PREC_FP64) {
+        if (h->prec2 != h->prec) {
+            Stage2Vectors v(h);
+            TRY(import_utilde_part<double>(h, ftilde, r0, K));
+            TRY(sweep_solve<double>(h, K));
+            TRY(export_ftilde_part<double>(h, utilde, h2, r0, K));
+        } else if (h->prec == SLAB_PREC_FP64) {
             TRY(import_utilde_part<double>(h, ftilde, r0, K));
             TRY(sweep_solve<double>(h, K));
             TRY(export_ftilde_part<double>(h, utilde, h2, r0, K));
@@ -510,15 +609,15 @@ slab_status slab_get_T_block(slab_handle* h, int which, int q, double* out) {
     const TreeDims& d = h->td;
     if (q < 0 || q >= (which == 0 ? d.NI : d.NI - 1)) return SLAB_EINVAL;
     const int64_t blk = (int64_t)d.s_pad * d.s_pad;
-    const unsigned char* base = (const unsigned char*)(which == 0 ? h->Tb : h->To) + q * blk * h->rsz;
-    std::vector<unsigned char> tmp((size_t)blk * h->rsz);
+    const unsigned char* base = (const unsigned char*)(which == 0 ? h->Tb : h->To) + q * blk * h->rsz2;
+    std::vector<unsigned char> tmp((size_t)blk * h->rsz2);
     SLAB_CK(h, cudaMemcpyAsync(tmp.data(), base, tmp.size(), cudaMemcpyDeviceToHost, h->stream));
     SLAB_CK(h, cudaStreamSynchronize(h->stream));
     const double sc = (double)h->n * (double)h->n;
     for (int i = 0; i < d.s; ++i)
         for (int j = 0; j < d.s; ++j) {
             const int64_t e = (int64_t)i * d.s_pad + j;
-            const double v = h->rsz == 8 ? ((const double*)tmp.data())[e] : (double)((const float*)tmp.data())[e];
+            const double v = h->rsz2 == 8 ? ((const double*)tmp.data())[e] : (double)((const float*)tmp.data())[e];
             out[(int64_t)i * d.s + j] = sc * v;
         }
     return SLAB_OK;

@@ -18,6 +18,7 @@
 //   forward   z_j = L_j^{-1} (f_j - Y_{j-1}^T z_{j-1})
 //   backward  u_j = L_j^{-T} (z_j - Y_j u_{j+1}).
 #include <algorithm>
+#include <cstdio>
 #include <vector>
 
 #include "slab_internal.cuh"
@@ -419,122 +420,320 @@ slab_status gemm_tn<double>(slab_handle* h, int cls, int M, int N, int K, double
 }
 
 // ---------------------------------------------------------------- indefinite kind (Helmholtz)
-// Gauss-Jordan inversion of G = [S | I] (sp x 2sp, row-major, ld 2sp) with partial pivoting over
-// the whole column (first row of largest |g_ik|): one column per three launches.
+// Blocked Gauss-Jordan elimination of the augmented system of interface j
+//   top    Gt = [ S_j        | T_{j,j+1}    | I ]      (s_pad x wt, wt = 3 s_pad; 2 s_pad for the last j)
+//   bottom Gb = [ T_{j+1,j}  | T_{j+1,j+1}      ]      (s_pad x 2 s_pad)
+// eliminating the S_j columns in panels of 64.  At the end the top rows hold (in pivot order)
+// [I | S_j^{-1} T_{j,j+1} | S_j^{-1}] and the bottom right block is S_{j+1} of Algorithm 1.
+// Rows are never swapped: perm[c] records the physical top row that pivots on column c.
+// Pivot rows of a panel are chosen by tournament pivoting: warps run partial-pivoting
+// elimination on 128-row groups of the not-yet-pivoted rows, keep 64 winners each, and winners
+// are merged pairwise (original row values) up to one set of 64.  The panel step is then
+//   A11 = G[piv, panel],  X = A11^{-1} G[piv, rest],  G[piv, rest] = X,
+//   G[other, rest] -= G[other, panel] X       (tensor-core rank-64 update).
+constexpr int GJ_LEAF = 128;          // rows per tournament group
+constexpr int GJ_WARPS = 2;           // tournament warps per CTA
+
+struct GjWork {
+    int* act;         // [2][s_pad] not-yet-pivoted top rows, double-buffered by panel parity
+    int* perm;        // [s_pad] physical row pivoting on column c
+    int* pflag;       // [s_pad] panel index + 1 at which the row pivoted (0: not yet)
+    int* cand;        // tournament winner sets, [nodes][64]
+    unsigned* tick;   // tournament tickets, [nodes]
+    int* piv;         // [64] pivot rows of the current panel
+};
+
+__host__ __device__ inline int gj_level_count(int L, int l) {          // nodes at tournament level l
+    int c = L;
+    for (int i = 0; i < l; ++i) c = (c + 1) / 2;
+    return c;
+}
+__host__ __device__ inline int gj_level_off(int L, int l) {
+    int o = 0, c = L;
+    for (int i = 0; i < l; ++i) { o += c; c = (c + 1) / 2; }
+    return o;
+}
+__host__ __device__ inline int gj_nodes(int L) {                       // all nodes, leaves to root
+    int o = 0, c = L;
+    while (c > 1) { o += c; c = (c + 1) / 2; }
+    return o + 1;
+}
+
+// Partial-pivoting elimination by one warp on nr (64..128) rows x 64 columns held in A (stride 65);
+// rows[] are the physical G rows of A's rows.  Writes the 64 chosen physical rows, in order, to out.
 template <typename T>
-__global__ void __launch_bounds__(1024) gj_pivot_kernel(const T* G, int sp, int k, int* piv, T* pval,
-                                                       unsigned* status) {
-    __shared__ T bv[32];
-    __shared__ int bi[32];
-    const int ld = 2 * sp;
-    T best = T(-1);
-    int bidx = k;
-    for (int i = k + threadIdx.x; i < sp; i += blockDim.x) {
-        const T v = fabs(G[(int64_t)i * ld + k]);
-        if (v > best) { best = v; bidx = i; }
-    }
+__device__ void gj_warp_gepp(T* A, const int* rows, int nr, int* out) {
+    const int lane = threadIdx.x & 31;
+    bool chosen[4] = {false, false, false, false};
+    for (int j = 0; j < 64; ++j) {
+        T best = T(-1);
+        int bi = 1 << 30;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const T ob = __shfl_xor_sync(0xffffffffu, best, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
-        if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; }
-    }
-    if ((threadIdx.x & 31) == 0) { bv[threadIdx.x >> 5] = best; bi[threadIdx.x >> 5] = bidx; }
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        const int nw = blockDim.x >> 5;
-        best = threadIdx.x < nw ? bv[threadIdx.x] : T(-1);
-        bidx = threadIdx.x < nw ? bi[threadIdx.x] : k;
+        for (int q = 0; q < 4; ++q) {
+            const int r = lane + 32 * q;
+            if (r < nr && !chosen[q]) {
+                T v = fabs(A[r * 65 + j]);
+                if (v != v) v = T(INFINITY);                  // a NaN is picked, and flagged at A11^{-1}
+                if (v > best) { best = v; bi = r; }
+            }
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             const T ob = __shfl_xor_sync(0xffffffffu, best, o);
-            const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
-            if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; }
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
         }
-        if (threadIdx.x == 0) {
-            const T v = G[(int64_t)bidx * ld + k];
-            *piv = bidx;
-            if (!(best > T(0)) || !isfinite((double)v)) {
-                atomicOr(status, SLAB_DEV_NOTSPD);
-                *pval = T(1);
-            } else {
-                *pval = v;
+        if (bi >= nr) bi = 0;                             // not reached: nr >= 64 unchosen candidates
+        if ((bi & 31) == lane) chosen[bi >> 5] = true;
+        if (lane == 0) out[j] = rows[bi];
+        const T pv = A[bi * 65 + j];
+        if (best > T(0)) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int r = lane + 32 * q;
+                if (r < nr && !chosen[q]) {
+                    const T l = A[r * 65 + j] / pv;
+                    for (int c = j + 1; c < 64; ++c) A[r * 65 + c] -= l * A[bi * 65 + c];
+                }
             }
         }
+        __syncwarp();
     }
 }
 
-// swap rows k and p, then scale row k by 1 / pivot (columns k+1 .. 2sp-1; column k is not read again)
+// One launch per panel: leaves, pairwise merges (ticketed, deterministic), and at the root the
+// panel's pivot rows, their flags and perm entries, and the compacted list of remaining rows.
 template <typename T>
-__global__ void gj_swap_scale_kernel(T* G, int sp, int k, const int* piv, const T* pval) {
-    const int j = k + 1 + blockIdx.x * blockDim.x + threadIdx.x;
-    const int ld = 2 * sp;
-    if (j >= ld) return;
-    const int p = *piv;
-    const T rp = T(1) / *pval;
-    T a = G[(int64_t)k * ld + j];
-    if (p != k) {
-        const T b = G[(int64_t)p * ld + j];
-        G[(int64_t)p * ld + j] = a;
-        a = b;
-    }
-    G[(int64_t)k * ld + j] = a * rp;
-}
-
-// column k multipliers of the swapped matrix: only row p changed in column k
-template <typename T>
-__global__ void gj_swap_col_kernel(T* G, int sp, int k, const int* piv) {
-    const int p = *piv;
-    if (threadIdx.x == 0 && blockIdx.x == 0 && p != k) {
-        const int ld = 2 * sp;
-        const T a = G[(int64_t)k * ld + k];
-        G[(int64_t)k * ld + k] = G[(int64_t)p * ld + k];
-        G[(int64_t)p * ld + k] = a;
-    }
-}
-
-// G[i][j] -= G[i][k] G[k][j] for i != k, j > k  (column k is left as is)
-template <typename T>
-__global__ void gj_eliminate_kernel(T* G, int sp, int k) {
-    const int j = k + 1 + blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = blockIdx.y * blockDim.y + threadIdx.y;
-    const int ld = 2 * sp;
-    if (j >= ld || i >= sp || i == k) return;
-    G[(int64_t)i * ld + j] -= G[(int64_t)i * ld + k] * G[(int64_t)k * ld + j];
-}
-
-template <typename T>
-slab_status gj_invert(slab_handle* h, T* G, int sp, int* piv, T* pval) {
-    const int ld = 2 * sp;
-    for (int k = 0; k < sp; ++k) {
-        {
-            SLAB_PROF(h, KC_PANEL);
-            gj_pivot_kernel<T><<<1, 1024, 0, h->stream>>>(G, sp, k, piv, pval, h->dstatus);
+__global__ void __launch_bounds__(32 * GJ_WARPS) gj_tournament_kernel(const T* __restrict__ G, int64_t ld,
+                                                                       int c0, int panel, int nact, GjWork w,
+                                                                       const int* act, int* act_next) {
+    extern __shared__ unsigned char gj_smem[];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    T* A = reinterpret_cast<T*>(gj_smem) + (size_t)wid * GJ_LEAF * 65;
+    __shared__ int rows_s[GJ_WARPS][GJ_LEAF];
+    int* rows = rows_s[wid];
+    const int L = (nact + GJ_LEAF - 1) / GJ_LEAF;
+    int node = blockIdx.x * GJ_WARPS + wid;
+    if (node >= L) return;
+    int lvl = 0;
+    int nr = min(GJ_LEAF, nact - node * GJ_LEAF);
+    for (int i = lane; i < nr; i += 32) rows[i] = act[node * GJ_LEAF + i];
+    while (true) {
+        __syncwarp();
+        for (int idx = lane; idx < nr * 64; idx += 32) {
+            const int r = idx >> 6, c = idx & 63;
+            A[r * 65 + c] = G[(int64_t)rows[r] * ld + c0 + c];
         }
-        SLAB_CK_LAUNCH(h);
-        const int nc = ld - k - 1;
-        if (nc > 0) {
-            SLAB_PROF(h, KC_PANEL);
-            gj_swap_col_kernel<T><<<1, 32, 0, h->stream>>>(G, sp, k, piv);
-            gj_swap_scale_kernel<T><<<(nc + 255) / 256, 256, 0, h->stream>>>(G, sp, k, piv, pval);
-        }
-        SLAB_CK_LAUNCH(h);
-        if (nc > 0) {
-            SLAB_PROF(h, KC_TRAIL);
-            dim3 blk(32, 8), grid((nc + 31) / 32, (sp + 7) / 8);
-            gj_eliminate_kernel<T><<<grid, blk, 0, h->stream>>>(G, sp, k);
-        }
-        SLAB_CK_LAUNCH(h);
+        __syncwarp();
+        int* out = w.cand + (gj_level_off(L, lvl) + node) * 64;
+        gj_warp_gepp<T>(A, rows, nr, out);
+        __syncwarp();
+        if (gj_level_count(L, lvl) == 1) break;         // root
+        const int parent = node >> 1;
+        const int nchild = ((node ^ 1) < gj_level_count(L, lvl)) ? 2 : 1;
+        __threadfence();
+        unsigned tk = 0;
+        if (lane == 0) tk = atomicAdd(w.tick + gj_level_off(L, lvl + 1) + parent, 1u);
+        tk = __shfl_sync(0xffffffffu, tk, 0);
+        if ((int)tk + 1 < nchild) return;               // the sibling finishes the merge
+        __threadfence();
+        const int* c0p = w.cand + (gj_level_off(L, lvl) + 2 * parent) * 64;
+        nr = nchild * 64;
+        for (int i = lane; i < nr; i += 32) rows[i] = __ldcg(c0p + i);
+        node = parent;
+        ++lvl;
     }
-    return SLAB_OK;
+    // root: the panel's pivot rows
+    const int* win = w.cand + (gj_level_off(L, lvl) + node) * 64;
+    for (int i = lane; i < 64; i += 32) {
+        const int r = __ldcg(win + i);
+        w.piv[i] = r;
+        w.perm[c0 + i] = r;
+        w.pflag[r] = panel + 1;
+    }
+    __syncwarp();
+    __threadfence();
+    // every other warp has taken its ticket: reset them for the next panel
+    for (int i = lane; i < gj_nodes(L); i += 32) w.tick[i] = 0u;
+    // remaining rows, in order
+    int base = 0;
+    for (int i0 = 0; i0 < nact; i0 += 32) {
+        const int i = i0 + lane;
+        int r = -1;
+        bool keep = false;
+        if (i < nact) {
+            r = act[i];
+            keep = __ldcg(w.pflag + r) != panel + 1;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        if (keep) act_next[base + __popc(bal & ((1u << lane) - 1u))] = r;
+        base += __popc(bal);
+    }
+}
+
+// A11^{-1} of the panel's pivot rows by Gauss-Jordan with partial pivoting on [A11 | I] in smem.
+template <typename T>
+__global__ void __launch_bounds__(256) gj_a11_inverse_kernel(const T* __restrict__ G, int64_t ld, int c0,
+                                                             const int* piv, T* Ainv, unsigned* status) {
+    extern __shared__ unsigned char gj_smem[];
+    T (*M)[129] = reinterpret_cast<T (*)[129]>(gj_smem);     // [A11 | I], 64 x 128 (+1 pad)
+    __shared__ int pr;
+    const int tid = threadIdx.x;
+    for (int idx = tid; idx < 64 * 64; idx += 256) {
+        const int i = idx >> 6, j = idx & 63;
+        M[i][j] = G[(int64_t)piv[i] * ld + c0 + j];
+        M[i][64 + j] = i == j ? T(1) : T(0);
+    }
+    __syncthreads();
+    for (int k = 0; k < 64; ++k) {
+        if (tid < 32) {
+            T best = T(-1);
+            int bi = k;
+            for (int i = k + tid; i < 64; i += 32) {
+                const T v = fabs(M[i][k]);
+                if (v > best) { best = v; bi = i; }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+            }
+            if (tid == 0) {
+                if (!(best > T(0)) || !isfinite((double)best)) {
+                    atomicOr(status, SLAB_DEV_NOTSPD);
+                    M[bi][k] = T(1);
+                }
+                pr = bi;
+            }
+        }
+        __syncthreads();
+        const int p = pr;
+        if (p != k)
+            for (int j = tid; j < 128; j += 256) {
+                const T t = M[k][j];
+                M[k][j] = M[p][j];
+                M[p][j] = t;
+            }
+        __syncthreads();
+        const T rp = T(1) / M[k][k];
+        __syncthreads();
+        for (int j = tid; j < 128; j += 256) M[k][j] *= rp;
+        __syncthreads();
+        for (int idx = tid; idx < 64 * 128; idx += 256) {
+            const int i = idx >> 7, j = idx & 127;
+            if (i != k && j != k) M[i][j] -= M[i][k] * M[k][j];
+        }
+        __syncthreads();
+        if (tid < 64 && tid != k) M[tid][k] = T(0);
+        __syncthreads();
+    }
+    for (int idx = tid; idx < 64 * 64; idx += 256) Ainv[idx] = M[idx >> 6][64 + (idx & 63)];
+}
+
+// blockIdx.y == 0: X = A11^{-1} G[piv, col0 .. col0+63] for 64 columns of the rest (cols >= c0+64),
+// written to G[piv, cols] and to XT[col - (c0+64)][0..63].
+// blockIdx.y == 1: Pbuf[r][0..63] = G[r][panel] for the top rows (0 for this panel's pivots)
+// and the bottom rows.
+template <typename T>
+__global__ void __launch_bounds__(256) gj_panel_apply_kernel(T* Gt, int64_t ldt, const T* __restrict__ Gb,
+                                                             int64_t ldb, int sp, int wt, int c0, int panel,
+                                                             const int* piv, const int* pflag,
+                                                             const T* __restrict__ Ainv, T* XT, T* Pbuf) {
+    extern __shared__ unsigned char gj_smem[];
+    T (*Ai)[65] = reinterpret_cast<T (*)[65]>(gj_smem);
+    T (*Bc)[65] = Ai + 64;
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+    if (blockIdx.y == 1) {
+        const int64_t rows = 2 * (int64_t)sp;
+        for (int64_t idx = (int64_t)blockIdx.x * 256 + tid; idx < rows * 64; idx += (int64_t)gridDim.x * 256) {
+            const int r = (int)(idx >> 6), c = (int)(idx & 63);
+            T v;
+            if (r < sp) v = pflag[r] == panel + 1 ? T(0) : Gt[(int64_t)r * ldt + c0 + c];
+            else v = Gb[(int64_t)(r - sp) * ldb + c0 + c];
+            Pbuf[idx] = v;
+        }
+        return;
+    }
+    const int cb = c0 + 64 + blockIdx.x * 64;           // first column of this block
+    if (cb >= wt) return;
+    const int nc = min(64, wt - cb);
+    for (int idx = tid; idx < 64 * 64; idx += 256) {
+        const int i = idx >> 6, j = idx & 63;
+        Ai[i][j] = Ainv[idx];
+        Bc[i][j] = j < nc ? Gt[(int64_t)piv[i] * ldt + cb + j] : T(0);
+    }
+    __syncthreads();
+    T acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b2 = 0; b2 < 4; ++b2) acc[a][b2] = T(0);
+    for (int l = 0; l < 64; ++l) {
+        T av[4], bv[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) av[a] = Ai[ty + 16 * a][l];
+#pragma unroll
+        for (int b2 = 0; b2 < 4; ++b2) bv[b2] = Bc[l][tx + 16 * b2];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b2 = 0; b2 < 4; ++b2) acc[a][b2] += av[a] * bv[b2];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b2 = 0; b2 < 4; ++b2) Bc[ty + 16 * a][tx + 16 * b2] = acc[a][b2];
+    __syncthreads();
+    for (int idx = tid; idx < 64 * 64; idx += 256) {
+        const int i = idx >> 6, j = idx & 63;            // row of X, column in block
+        if (j < nc) Gt[(int64_t)piv[i] * ldt + cb + j] = Bc[i][j];
+    }
+    for (int idx = tid; idx < 64 * 64; idx += 256) {
+        const int j = idx >> 6, i = idx & 63;            // XT row = column, 64 consecutive i
+        if (j < nc) XT[(int64_t)(cb - c0 - 64 + j) * 64 + i] = Bc[i][j];
+    }
+}
+
+// Build the augmented system of interface j.  S comes from Tb[0] (j = 0) or from the bottom
+// right block of the previous elimination (copied before the bottom block is rebuilt).
+template <typename T>
+__global__ void gj_fill_top_kernel(T* Gt, int sp, int wt, const T* __restrict__ S, int64_t lds,
+                                   const T* __restrict__ T12) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)sp * wt) return;
+    const int i = (int)(idx / wt), c = (int)(idx % wt);
+    T v;
+    if (c < sp) v = S[(int64_t)i * lds + c];
+    else if (T12 && c < 2 * sp) v = T12[(int64_t)i * sp + (c - sp)];
+    else v = (c - (wt - sp)) == i ? T(1) : T(0);
+    Gt[idx] = v;
 }
 
 template <typename T>
-__global__ void set_aug_identity_kernel(T* G, int sp) {     // right half of [S | I] := I
+__global__ void gj_fill_bottom_kernel(T* Gb, int sp, const T* __restrict__ T12, const T* __restrict__ T22) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)sp * 2 * sp) return;
+    const int i = (int)(idx / (2 * sp)), c = (int)(idx % (2 * sp));
+    Gb[idx] = c < sp ? T12[(int64_t)c * sp + i] : T22[(int64_t)i * sp + (c - sp)];   // T_{j+1,j} = T_{j,j+1}^T
+}
+
+// Sinv[i] = Gt[perm[i]][wt-sp ..], W[i] = Gt[perm[i]][sp .. 2sp) (W optional)
+template <typename T>
+__global__ void gj_gather_kernel(const T* __restrict__ Gt, int sp, int wt, const int* perm, T* Sinv, T* W) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (int64_t)sp * sp) return;
-    const int i = (int)(idx / sp), j = (int)(idx % sp);
-    G[(int64_t)i * 2 * sp + sp + j] = i == j ? T(1) : T(0);
+    const int i = (int)(idx / sp), c = (int)(idx % sp);
+    const T* row = Gt + (int64_t)perm[i] * wt;
+    Sinv[idx] = row[wt - sp + c];
+    if (W) W[idx] = row[sp + c];
+}
+
+template <typename T>
+__global__ void gj_init_rows_kernel(int* act, int* pflag, int sp) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < sp) { act[i] = i; pflag[i] = 0; }
 }
 
 // Batched C_b = beta C_b + alpha A_b B_b^T, b < batch, with element strides sA, sB, sC.
@@ -575,46 +774,149 @@ slab_status gemm_tn_batched<double>(slab_handle* h, int cls, int M, int N, int K
 }  // namespace
 
 // Indefinite kind: Algorithm 1 as printed, S_1 = T_11, S_{j+1} = T_{j+1,j+1} - T_{j+1,j} W_j with
-// W_j = S_j^{-1} T_{j,j+1}; S_j^{-1} by pivoted Gauss-Jordan.  Stored: S_j^{-1} (in Linv),
-// W_j (in Y) and T_{j+1,j} (in ToT).  Work arrays: [S | I] and W_j^T in Fct.
+// W_j = S_j^{-1} T_{j,j+1}, all three from one blocked Gauss-Jordan elimination of the augmented
+// system (see above).  Stored: S_j^{-1} (in Linv), W_j (in Y) and T_{j+1,j} (in ToT).
+// Work: Gt, Gb in Fct; Pbuf, XT, A11^{-1} and the pivot bookkeeping in gjw.
 template <typename T>
 slab_status sweep_factor_indef(slab_handle* h) {
-    const int NI = h->td.NI, sp = h->td.s_pad;
+    const int NI = h->td.NI, sp = h->td.s_pad, nt = h->nt;
     const int64_t blk = (int64_t)sp * sp;
     T* Tb = (T*)h->Tb;
     T* To = (T*)h->To;
     T* ToT = (T*)h->ToT;
     T* Sinv = (T*)h->Linv;
     T* Wn = (T*)h->Y;
-    T* G = (T*)h->Fct;                   // [S | I], sp x 2sp
-    T* Wt = G + 2 * blk;                 // W_j^T
-    int* piv = (int*)h->dscratch;        // pivot row and value of the current column
-    T* pval = (T*)((char*)h->dscratch + 64);
+    T* Gt = (T*)h->Fct;                  // sp x 3sp
+    T* Gb = Gt + 3 * blk;                // sp x 2sp
+    char* wb = (char*)h->gjw;
+    T* Pbuf = (T*)wb;                    wb += (size_t)2 * sp * 64 * sizeof(T);
+    T* XT = (T*)wb;                      wb += (size_t)3 * sp * 64 * sizeof(T);
+    T* Ainv = (T*)wb;                    wb += (size_t)64 * 64 * sizeof(T);
+    GjWork w;
+    int* act0 = (int*)wb;                wb += (size_t)2 * sp * sizeof(int);
+    w.act = act0;
+    w.perm = (int*)wb;                   wb += (size_t)sp * sizeof(int);
+    w.pflag = (int*)wb;                  wb += (size_t)sp * sizeof(int);
+    const int nodes = gj_nodes((sp + GJ_LEAF - 1) / GJ_LEAF);
+    w.cand = (int*)wb;                   wb += (size_t)nodes * 64 * sizeof(int);
+    w.tick = (unsigned*)wb;              wb += (size_t)nodes * sizeof(unsigned);
+    w.piv = (int*)wb;
+    const size_t tsmem = (size_t)GJ_WARPS * GJ_LEAF * 65 * sizeof(T);
+    const size_t ismem = (size_t)64 * 129 * sizeof(T);
+    const size_t asmem = (size_t)2 * 64 * 65 * sizeof(T);
+    SLAB_CK(h, cudaFuncSetAttribute(gj_tournament_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)tsmem));
+    SLAB_CK(h, cudaFuncSetAttribute(gj_a11_inverse_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)ismem));
+    SLAB_CK(h, cudaFuncSetAttribute(gj_panel_apply_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)asmem));
+    SLAB_CK(h, cudaMemsetAsync(w.tick, 0, (size_t)nodes * sizeof(unsigned), h->stream));
     slab_status st;
     for (int j = 0; j < NI; ++j) {
-        SLAB_CK(h, cudaMemcpy2DAsync(G, 2 * sp * sizeof(T), Tb + j * blk, sp * sizeof(T), sp * sizeof(T), sp,
-                                     cudaMemcpyDeviceToDevice, h->stream));
-        if (j > 0 && (st = gemm_tn<T>(h, KC_SYRK, sp, sp, sp, T(-1), ToT + (j - 1) * blk, sp, Wt, sp, T(1), G,
-                                      2 * sp, 0, 0)))
-            return st;                                          // S_j = T_jj - T_{j,j-1} W_{j-1}
+        const bool hasNext = j < NI - 1;
+        const int wt = (hasNext ? 3 : 2) * sp;
         {
             SLAB_PROF(h, KC_OTHER);
-            set_aug_identity_kernel<T><<<(unsigned)((blk + 255) / 256), 256, 0, h->stream>>>(G, sp);
+            const int64_t n1 = (int64_t)sp * wt;
+            gj_fill_top_kernel<T><<<(unsigned)((n1 + 255) / 256), 256, 0, h->stream>>>(
+                Gt, sp, wt, j == 0 ? Tb : Gb + sp, j == 0 ? sp : 2 * sp, hasNext ? To + j * blk : nullptr);
+            SLAB_CK_LAUNCH(h);
+            if (hasNext) {
+                const int64_t n2 = 2 * blk;
+                gj_fill_bottom_kernel<T><<<(unsigned)((n2 + 255) / 256), 256, 0, h->stream>>>(Gb, sp, To + j * blk,
+                                                                                             Tb + (j + 1) * blk);
+                SLAB_CK_LAUNCH(h);
+            }
+            gj_init_rows_kernel<T><<<(sp + 255) / 256, 256, 0, h->stream>>>(act0, w.pflag, sp);
+            SLAB_CK_LAUNCH(h);
         }
-        SLAB_CK_LAUNCH(h);
-        if ((st = gj_invert<T>(h, G, sp, piv, pval))) return st;
-        SLAB_CK(h, cudaMemcpy2DAsync(Sinv + j * blk, sp * sizeof(T), G + sp, 2 * sp * sizeof(T), sp * sizeof(T), sp,
-                                     cudaMemcpyDeviceToDevice, h->stream));
-        if (j < NI - 1) {
-            if ((st = transpose<T>(h, To + j * blk, ToT + j * blk, sp))) return st;   // T_{j+1,j}
-            // W_j^T = T_{j+1,j} S_j^{-T}
-            if ((st = gemm_tn<T>(h, KC_TRAIL, sp, sp, sp, T(1), ToT + j * blk, sp, Sinv + j * blk, sp, T(0), Wt,
-                                 sp, 0, 0)))
+        for (int kb = 0; kb < nt; ++kb) {
+            const int c0 = kb * 64;
+            const int nact = sp - c0;
+            const int* act = act0 + (kb & 1) * sp;
+            int* act_next = act0 + ((kb + 1) & 1) * sp;
+            const int L = (nact + GJ_LEAF - 1) / GJ_LEAF;
+            {
+                SLAB_PROF(h, KC_PANEL);
+                gj_tournament_kernel<T><<<(L + GJ_WARPS - 1) / GJ_WARPS, 32 * GJ_WARPS, tsmem, h->stream>>>(
+                    Gt, wt, c0, kb, nact, w, act, act_next);
+                SLAB_CK_LAUNCH(h);
+                gj_a11_inverse_kernel<T><<<1, 256, ismem, h->stream>>>(Gt, wt, c0, w.piv, Ainv, h->dstatus);
+                SLAB_CK_LAUNCH(h);
+                const int ncol = wt - c0 - 64;
+                dim3 grid((unsigned)std::max((ncol + 63) / 64, 64), 2);
+                gj_panel_apply_kernel<T><<<grid, 256, asmem, h->stream>>>(Gt, wt, Gb, 2 * sp, sp, wt, c0, kb, w.piv,
+                                                                     w.pflag, Ainv, XT, Pbuf);
+                SLAB_CK_LAUNCH(h);
+            }
+            // G[other, rest] -= Pbuf X : top rows over all remaining columns, bottom rows up to 2 sp
+            const int nt_top = wt - c0 - 64;
+            if ((st = gemm_tn<T>(h, KC_TRAIL, sp, nt_top, 64, T(-1), Pbuf, 64, XT, 64, T(1), Gt + c0 + 64, wt, 0, 0)))
                 return st;
-            if ((st = transpose<T>(h, Wt, Wn + j * blk, sp))) return st;
+            const int nb_bot = 2 * sp - c0 - 64;
+            if (hasNext && (st = gemm_tn<T>(h, KC_TRAIL, sp, nb_bot, 64, T(-1), Pbuf + (int64_t)sp * 64, 64, XT, 64,
+                                            T(1), Gb + c0 + 64, 2 * sp, 0, 0)))
+                return st;
+            if (slab_debug()) {
+                if (slab_debug_status(h, "interface elimination (interface, panel)", j, kb)) return SLAB_ESINGULAR;
+                // pivot bookkeeping: distinct pivot rows drawn from the active list, act_next = act - piv
+                std::vector<int> hp(64), ha(nact), hn(nact > 64 ? nact - 64 : 1);
+                cudaMemcpy(hp.data(), w.piv, 64 * sizeof(int), cudaMemcpyDeviceToHost);
+                cudaMemcpy(ha.data(), act, nact * sizeof(int), cudaMemcpyDeviceToHost);
+                if (nact > 64) cudaMemcpy(hn.data(), act_next, (nact - 64) * sizeof(int), cudaMemcpyDeviceToHost);
+                std::vector<char> inA(sp, 0), inP(sp, 0);
+                bool bad = false;
+                for (int r : ha) inA[r] = 1;
+                for (int r : hp) { if (r < 0 || r >= sp || !inA[r] || inP[r]) bad = true; else inP[r] = 1; }
+                size_t q = 0;
+                for (int r : ha) if (!inP[r]) { if (q >= hn.size() || hn[q] != r) bad = true; ++q; }
+                if (bad) {
+                    std::fprintf(stderr, "slab: pivot bookkeeping inconsistent at (%d, %d)\n", j, kb);
+                    return SLAB_ESINGULAR;
+                }
+            }
         }
+        {
+            SLAB_PROF(h, KC_OTHER);
+            gj_gather_kernel<T><<<(unsigned)((blk + 255) / 256), 256, 0, h->stream>>>(Gt, sp, wt, w.perm,
+                                                                                    Sinv + j * blk,
+                                                                                    hasNext ? Wn + j * blk : nullptr);
+            SLAB_CK_LAUNCH(h);
+        }
+        if (hasNext && (st = transpose<T>(h, To + j * blk, ToT + j * blk, sp))) return st;   // T_{j+1,j}
     }
     return SLAB_OK;
+}
+
+template <typename S, typename D>
+__global__ void convert_kernel(const S* __restrict__ src, D* __restrict__ dst, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = (D)src[i];
+}
+
+slab_status widen_to_double(slab_handle* h, const float* src, double* dst, int64_t n) {
+    if (n <= 0) return SLAB_OK;
+    SLAB_PROF(h, KC_OTHER);
+    convert_kernel<float, double><<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, h->stream>>>(
+        src, dst, n);
+    SLAB_CK_LAUNCH(h);
+    return SLAB_OK;
+}
+
+slab_status narrow_to_float(slab_handle* h, const double* src, float* dst, int64_t n) {
+    if (n <= 0) return SLAB_OK;
+    SLAB_PROF(h, KC_OTHER);
+    convert_kernel<double, float><<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, h->stream>>>(
+        src, dst, n);
+    SLAB_CK_LAUNCH(h);
+    return SLAB_OK;
+}
+
+// Bytes of the indefinite-kind Stage-2 work area (gjw).
+size_t gj_work_bytes(int sp, size_t rsz) {
+    const int nodes = gj_nodes((sp + GJ_LEAF - 1) / GJ_LEAF);
+    return (size_t)(2 + 3) * sp * 64 * rsz + 64 * 64 * rsz + (size_t)4 * sp * sizeof(int) +
+           (size_t)nodes * 64 * sizeof(int) + (size_t)nodes * sizeof(unsigned) + 64 * sizeof(int) + 256;
 }
 
 // Algorithm 2 for the indefinite kind on X ([NI][kcap][s_pad]):

@@ -29,6 +29,11 @@
 #define SLAB_DEV_NOTSPD 1u    // a Cholesky pivot was <= 0 or not finite
 #define SLAB_DEV_TIMEOUT 2u   // a bounded device-side wait gave up (tensor-core pipeline)
 
+// Diagnostics: with the environment variable SLAB_DEBUG set, the factor synchronises after each
+// phase step and reports on stderr where a pivot failure first appeared.
+bool slab_debug();
+unsigned slab_debug_status(slab_handle* h, const char* where, int a, int b);
+
 struct TreeDims {
     int s;        // rows per slab (= interface size in 2-D)
     int s_pad;    // s rounded up to SLAB_TILE
@@ -41,8 +46,12 @@ struct TreeDims {
 struct slab_handle {
     int dim, n, b, kind;
     double omega;
-    int prec;                 // slab_precision
-    size_t rsz;               // bytes of the factor scalar
+    int prec;                 // slab_precision of Stage 1 (slab trees, T assembly, tree solves)
+    size_t rsz;               // bytes of the Stage-1 scalar
+    int prec2;                // slab_precision of Stage 2 (interface elimination and sweep)
+    size_t rsz2;              // bytes of the Stage-2 scalar
+    void *Tb1, *To1;          // mixed mode: T assembled in the Stage-1 scalar (factor only)
+    void *wX2, *wZ2;          // mixed mode: interface vectors in the Stage-2 scalar
     TreeDims td;
     int nt;                   // tiles per interface block (s_pad / 64)
     cudaStream_t stream;
@@ -75,7 +84,8 @@ struct slab_handle {
     void* Y;                  // [NI-1][s_pad][s_pad] Y_j = L_j^{-1} T_{j,j+1}
 
     unsigned int* dstatus;    // device status word
-    void* dscratch;           // 256 bytes of device scratch (pivot search results)
+    void* dscratch;           // 256 bytes of device scratch
+    void* gjw;                // indefinite kind: Stage-2 Gauss-Jordan work area (gj_work_bytes)
 
     // solve workspace, sized for kcap right-hand sides
     int kcap;
@@ -167,6 +177,9 @@ template <typename T> slab_status sweep_factor(slab_handle* h);
 template <typename T> slab_status sweep_solve(slab_handle* h, int K);
 // odd-even elimination order of T (SPD kinds)
 int cr_max_batch(int NI);
+size_t gj_work_bytes(int s_pad, size_t rsz);
+slab_status widen_to_double(slab_handle* h, const float* src, double* dst, int64_t n);
+slab_status narrow_to_float(slab_handle* h, const double* src, float* dst, int64_t n);
 template <typename T> slab_status cr_factor(slab_handle* h);
 template <typename T> slab_status cr_solve(slab_handle* h, int K);
 

@@ -753,6 +753,7 @@ slab_status tree_factor(slab_handle* h) {
         if (indef) tree_factor_kernel<T, true><<<grid, TB_THREADS, 0, h->stream>>>(a, k);
         else tree_factor_kernel<T, false><<<grid, TB_THREADS, 0, h->stream>>>(a, k);
         SLAB_CK_LAUNCH(h);
+        if (slab_debug() && slab_debug_status(h, "slab tree factor (height, nodes)", k, cnt)) return SLAB_ESINGULAR;
     }
     return SLAB_OK;
 }

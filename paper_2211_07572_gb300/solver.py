@@ -38,13 +38,15 @@ class SlabSolver:
     dim, n: grid (unit square/cube, h = 1/n); b: interface spacing (b | n);
     kind: 0 Poisson, 1 diffusion -div(kappa grad u), 2 Helmholtz -Lap u - (omega/c)^2 u;
     kappa / c: node fields with (n+1)^dim entries; precision: "fp32" (FP32 factor, FP64
-    refinement) or "fp64" (plain FP64 path).
+    refinement) or "fp64" (plain FP64 path); stage2: "auto", "sweep" (Algorithm 1) or
+    "oddeven"; interface_precision: precision of the interface system (default: "fp64" for
+    Helmholtz with an FP32 factor, else the factor precision).
     """
 
     def __init__(self, dim: int, n: int, b: int, kind: int, kappa=None, c=None, omega: float = 0.0,
                  precision: str = "fp32", rtol: float = 1e-10, max_refine: int = 30,
                  stream: Optional[torch.cuda.Stream] = None, device=None, profile: bool = False,
-                 stage2: str = "auto"):
+                 stage2: str = "auto", interface_precision: Optional[str] = None):
         self.lib = _lib.load()
         self.device = (torch.device(device) if device is not None
                        else torch.device("cuda", torch.cuda.current_device()))
@@ -62,6 +64,7 @@ class SlabSolver:
         opts.stream = ctypes.c_void_p(self.stream.cuda_stream)
         opts.profile = int(profile)
         opts.stage2 = _STAGE2[stage2]
+        opts.interface_prec = -1 if interface_precision is None else _PREC[interface_precision]
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             _lib.check(self.lib.slab_factor(ctypes.byref(grid), ctypes.byref(co), int(b), ctypes.byref(opts),

@@ -25,10 +25,10 @@ def _need_cuda():
     oracle.build()
 
 
-def _solver(p, precision="fp64", rtol=1e-10, max_refine=30, stage2="auto"):
+def _solver(p, precision="fp64", rtol=1e-10, max_refine=30, stage2="auto", iprec=None):
     from paper_2211_07572_gb300.solver import SlabSolver
     return SlabSolver(p.dim, p.n, p.b, p.kind, kappa=p.kappa, c=p.c, omega=p.omega, precision=precision,
-                      rtol=rtol, max_refine=max_refine, stage2=stage2)
+                      rtol=rtol, max_refine=max_refine, stage2=stage2, interface_precision=iprec)
 
 
 def _problem(n, b, kind, k=2, seed=0):
@@ -165,6 +165,25 @@ def test_diffusion_solve_matches_oracle(precision, stage2):
     assert err.max() <= 1e-8, err
     if precision == "fp32":
         assert 1 <= it <= 30
+
+
+@pytest.mark.parametrize("stage2", ["sweep", "oddeven"])
+def test_mixed_precision_matches_oracle(stage2):
+    """FP32 slab trees with the interface system in FP64 (both elimination orders): T blocks are
+    the FP32 assembly widened, the refined solution matches the oracle."""
+    p = inputs.diffusion(256, 16, k=2, n_modes=16, field_seed=2, rhs_seed=103)
+    s = _solver(p, "fp32", rtol=1e-13, stage2=stage2, iprec="fp64")
+    A = oracle.assemble_problem(p)
+    Td, Tl, Tu = oracle.reduced_system(A, 2, p.n, p.b)
+    scale = max(np.abs(t).max() for t in Td)
+    assert np.abs(s.T_block(0, 3) - Td[3]).max() <= TOL["fp32"] * scale
+    u, rel, it = s.solve(torch.from_numpy(p.f).cuda(), allow_noconv=True)
+    uo = oracle.solve(p)
+    assert oracle.relres(A, u.cpu().numpy(), p.f).max() <= 1e-10
+    assert (np.linalg.norm(u.cpu().numpy() - uo, axis=1) / np.linalg.norm(uo, axis=1)).max() <= 1e-8
+    s.close()
+    with pytest.raises(Exception):
+        _solver(p, "fp64", iprec="fp32")                    # an FP64 factor with an FP32 interface
 
 
 def test_many_rhs_chunks_and_empty():
