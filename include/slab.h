@@ -97,7 +97,11 @@ typedef struct {
     int pivot;              /* reserved: 0 */
     double rtol;            /* refinement target for max_k ||f - A u||_2 / ||f||_2 */
     int max_refine;         /* refinement steps after the first solve (0: a single pass) */
-    int krylov;             /* reserved: 0 */
+    int krylov;             /* 0: plain refinement u += A_f^{-1} (f - A u); m > 0: restarted GMRES(m)
+                               in FP64 with the factor as right preconditioner (for operators
+                               where the FP32 factor's error times the conditioning is not small,
+                               e.g. Helmholtz); max_refine then bounds the preconditioner
+                               applications after the first.  0..200, else SLAB_EINVAL */
     void* stream;           /* cudaStream_t all work is ordered on (NULL: legacy default) */
     int profile;            /* 1: time every kernel launch from the start (see slab_profile) */
     int stage2;             /* slab_stage2 */

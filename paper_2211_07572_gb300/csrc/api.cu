@@ -1,6 +1,7 @@
 // C ABI of the slab factor+solve library: validation, device memory plan,
 // orchestration of the phases of Algorithms 3 and 4, and FP64 iterative
 // refinement on top of the (FP32 or FP64) factor.
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -316,6 +317,9 @@ void slab_destroy(slab_handle* h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     free_workspace(h);
     dfree(h->wX2); dfree(h->wZ2);
+    {
+        void* q = h->kV; dfree(q); q = h->kZ; dfree(q); q = h->kS; dfree(q);
+    }
     void* p;
     p = h->AX; dfree(p); p = h->AY; dfree(p); p = h->DG; dfree(p); p = h->kappa; dfree(p);
     dfree(h->tLinv); dfree(h->tZtb); dfree(h->tRtb); dfree(h->tZI); dfree(h->tRI);
@@ -343,6 +347,7 @@ slab_status slab_factor(const slab_grid* grid, const slab_coeffs* co, int b, con
     if (co->kind == SLAB_HELMHOLTZ && !co->c) return SLAB_EINVAL;
     if (o.factor_prec != SLAB_PREC_FP32 && o.factor_prec != SLAB_PREC_FP64) return SLAB_EINVAL;
     if (o.stage2 < SLAB_STAGE2_AUTO || o.stage2 > SLAB_STAGE2_ODDEVEN) return SLAB_EINVAL;
+    if (o.krylov < 0 || o.krylov > 200) return SLAB_EINVAL;
     int prec2 = o.interface_prec;
     if (prec2 == -1) prec2 = (co->kind == SLAB_HELMHOLTZ) ? SLAB_PREC_FP64 : o.factor_prec;
     if (prec2 != SLAB_PREC_FP32 && prec2 != SLAB_PREC_FP64) return SLAB_EINVAL;
@@ -362,6 +367,7 @@ slab_status slab_factor(const slab_grid* grid, const slab_coeffs* co, int b, con
     h->stream = (cudaStream_t)o.stream;
     h->rtol = o.rtol;
     h->max_refine = o.max_refine;
+    h->krylov = o.krylov;
     if (o.profile) slab_profile(h, 1);
     TreeDims& d = h->td;
     d.s = n - 1;
@@ -469,6 +475,143 @@ slab_status slab_apply(slab_handle* h, const double* x, double* y, int k) {
     return launch_apply(h, x, y, k);
 }
 
+namespace {
+
+// Krylov arrays for k right-hand sides: basis V [m+1][k][N], directions Z [m][k][N], and the
+// small device arrays (H columns [m+1][k], combination coefficients [m][k], dot partials, norms).
+slab_status ensure_krylov(slab_handle* h, int k) {
+    if (h->kcapk >= k) return SLAB_OK;
+    const int m = h->krylov;
+    const int64_t N = (int64_t)h->td.s * h->td.s;
+    void* p = h->kV; dfree(p); p = h->kZ; dfree(p); p = h->kS; dfree(p);
+    h->kV = h->kZ = h->kS = nullptr;
+    h->kcapk = 0;
+    TRY(dalloc(h, &p, (size_t)(m + 1) * k * N * sizeof(double)));
+    h->kV = (double*)p;
+    TRY(dalloc(h, &p, (size_t)m * k * N * sizeof(double)));
+    h->kZ = (double*)p;
+    TRY(dalloc(h, &p, ((size_t)(2 * m + 1) * k + vec_dot_part_elems(k) + 2 * (size_t)k) * sizeof(double)));
+    h->kS = (double*)p;
+    h->kcapk = k;
+    return SLAB_OK;
+}
+
+// Refinement by restarted right-preconditioned GMRES(m) in FP64, one Krylov space per
+// right-hand side: the preconditioner is one solve pass with the factor, u0 = M^{-1} f, and each
+// restart starts from the true FP64 residual.  The preconditioned directions are kept (flexible
+// form), since the FP32 solve is linear only up to rounding.  max_refine bounds the number of
+// preconditioner applications after the first.
+slab_status gmres_solve(slab_handle* h, const double* f, double* u, int k, double* relres_out, int* iters_out) {
+    const int m = h->krylov;
+    const int64_t N = (int64_t)h->td.s * h->td.s;
+    const int64_t kN = (int64_t)k * N;
+    const double h2 = 1.0 / ((double)h->n * (double)h->n);
+    TRY(ensure_workspace(h, k));
+    TRY(ensure_krylov(h, k));
+    double* V = h->kV;
+    double* Z = h->kZ;
+    double* Hd = h->kS;                                  // [m+1][k]
+    double* Cd = Hd + (size_t)(m + 1) * k;               // [m][k]
+    double* part = Cd + (size_t)m * k;
+    double* nrm = part + vec_dot_part_elems(k);          // [2][k]: ||r||^2, ||f||^2
+    TRY(pass(h, f, h2, u, 0, k));
+    std::vector<double> hb((size_t)(m + 1) * k), nh(2 * (size_t)k), fn(k);
+    std::vector<double> R((size_t)k * m * m), cs((size_t)k * m), sn((size_t)k * m), g((size_t)k * (m + 1));
+    std::vector<double> coef((size_t)m * k);
+    int it = 0;
+    slab_status result = SLAB_OK;
+    for (;;) {
+        SLAB_CK(h, cudaMemsetAsync(nrm, 0, 2 * k * sizeof(double), h->stream));
+        TRY(launch_residual(h, u, f, V, k, nrm, nrm + k));
+        SLAB_CK(h, cudaMemcpyAsync(nh.data(), nrm, 2 * k * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        SLAB_CK(h, cudaStreamSynchronize(h->stream));
+        double worst = 0.0;
+        bool finite = true;
+        for (int q = 0; q < k; ++q) {
+            fn[q] = nh[k + q] > 0 ? std::sqrt(nh[k + q]) : 1.0;
+            double rr;
+            if (!std::isfinite(nh[q])) {
+                rr = std::numeric_limits<double>::quiet_NaN();
+                finite = false;
+            } else {
+                rr = nh[q] > 0 ? std::sqrt(nh[q]) / fn[q] : 0.0;
+            }
+            if (relres_out) relres_out[q] = rr;
+            if (!(rr <= worst)) worst = rr;
+        }
+        if (!finite) { result = SLAB_ENOCONV; break; }
+        if (worst <= h->rtol) break;
+        if (it >= h->max_refine) { result = SLAB_ENOCONV; break; }
+        TRY(vec_scale(h, V, nrm, N, k));                 // v_0 = r / ||r||
+        for (int q = 0; q < k; ++q) {
+            std::fill(g.begin() + (size_t)q * (m + 1), g.begin() + (size_t)(q + 1) * (m + 1), 0.0);
+            g[(size_t)q * (m + 1)] = std::sqrt(nh[q] > 0 ? nh[q] : 0.0);
+        }
+        int jdone = 0;
+        for (int j = 0; j < m; ++j) {
+            double* Vj = V + (int64_t)j * kN;
+            double* Vn = V + (int64_t)(j + 1) * kN;
+            double* Zj = Z + (int64_t)j * kN;
+            TRY(pass(h, Vj, h2, Zj, 0, k));                // z_j = M^{-1} v_j
+            ++it;
+            TRY(launch_apply(h, Zj, Vn, k));               // w = A z_j
+            for (int i = 0; i <= j; ++i) {                 // modified Gram-Schmidt
+                TRY(vec_dot(h, Vn, V + (int64_t)i * kN, N, k, part, Hd + (size_t)i * k));
+                TRY(vec_axpy(h, Vn, V + (int64_t)i * kN, Hd + (size_t)i * k, -1.0, N, k));
+            }
+            TRY(vec_dot(h, Vn, Vn, N, k, part, Hd + (size_t)(j + 1) * k));
+            TRY(vec_scale(h, Vn, Hd + (size_t)(j + 1) * k, N, k));
+            SLAB_CK(h, cudaMemcpyAsync(hb.data(), Hd, (size_t)(j + 2) * k * sizeof(double), cudaMemcpyDeviceToHost,
+                                       h->stream));
+            SLAB_CK(h, cudaStreamSynchronize(h->stream));
+            double est = 0.0;
+            for (int q = 0; q < k; ++q) {
+                double* col = R.data() + ((size_t)q * m + j) * m;          // column j of R (rows 0..j)
+                double* c = cs.data() + (size_t)q * m;
+                double* s = sn.data() + (size_t)q * m;
+                double* gq = g.data() + (size_t)q * (m + 1);
+                std::vector<double> r(j + 2);
+                for (int i = 0; i <= j; ++i) r[i] = hb[(size_t)i * k + q];
+                const double hn = hb[(size_t)(j + 1) * k + q];
+                r[j + 1] = hn > 0 ? std::sqrt(hn) : 0.0;
+                for (int i = 0; i < j; ++i) {
+                    const double t = c[i] * r[i] + s[i] * r[i + 1];
+                    r[i + 1] = -s[i] * r[i] + c[i] * r[i + 1];
+                    r[i] = t;
+                }
+                const double d = std::hypot(r[j], r[j + 1]);
+                c[j] = d > 0 ? r[j] / d : 1.0;
+                s[j] = d > 0 ? r[j + 1] / d : 0.0;
+                r[j] = d;
+                gq[j + 1] = -s[j] * gq[j];
+                gq[j] = c[j] * gq[j];
+                for (int i = 0; i <= j; ++i) col[i] = r[i];
+                est = std::max(est, std::fabs(gq[j + 1]) / fn[q]);
+            }
+            jdone = j + 1;
+            if (!(est > 0.5 * h->rtol) || it >= h->max_refine) break;
+        }
+        for (int q = 0; q < k; ++q) {                    // y = R^{-1} g, back substitution
+            const double* gq = g.data() + (size_t)q * (m + 1);
+            std::vector<double> y(jdone, 0.0);
+            for (int i = jdone - 1; i >= 0; --i) {
+                double acc = gq[i];
+                for (int l = i + 1; l < jdone; ++l) acc -= R[((size_t)q * m + l) * m + i] * y[l];
+                const double di = R[((size_t)q * m + i) * m + i];
+                y[i] = di != 0.0 ? acc / di : 0.0;
+            }
+            for (int i = 0; i < jdone; ++i) coef[(size_t)i * k + q] = y[i];
+        }
+        SLAB_CK(h, cudaMemcpyAsync(Cd, coef.data(), (size_t)jdone * k * sizeof(double), cudaMemcpyHostToDevice,
+                                   h->stream));
+        TRY(vec_combine(h, u, Z, kN, Cd, jdone, k, N));   // u += Z y
+    }
+    if (iters_out) *iters_out = it;
+    return result;
+}
+
+}  // namespace
+
 slab_status slab_solve(slab_handle* h, const double* f, double* u, int k, double* relres_out, int* iters_out) {
     if (!h || k < 0) return SLAB_EINVAL;
     if (k == 0) {
@@ -476,6 +619,10 @@ slab_status slab_solve(slab_handle* h, const double* f, double* u, int k, double
         return SLAB_OK;
     }
     if (!f || !u) return SLAB_EINVAL;
+    if (h->krylov > 0 && h->max_refine > 0) {
+        TRY(ensure_resid(h, k));
+        return gmres_solve(h, f, u, k, relres_out, iters_out);
+    }
     TRY(ensure_workspace(h, k));
     const double h2 = 1.0 / ((double)h->n * (double)h->n);
     TRY(pass(h, f, h2, u, 0, k));

@@ -57,6 +57,11 @@ struct slab_handle {
     cudaStream_t stream;
     double rtol;
     int max_refine;
+    int krylov;               // 0: plain refinement; m > 0: restarted GMRES(m) refinement
+    double* kV;               // Krylov basis [m+1][k][N] (FP64)
+    double* kZ;               // preconditioned directions [m][k][N] (FP64)
+    double* kS;               // small device arrays: H columns, coefficients, dot partials
+    int kcapk;                // k the Krylov arrays were sized for
 
     // coefficient arrays over the (n+1)^2 nodes, h^2-scaled, FP64
     double* AX;               // AX[y][x]: face (x,y)-(x+1,y)
@@ -156,6 +161,13 @@ slab_status launch_residual(slab_handle* h, const double* u, const double* f, do
                             double* nrm_r, double* nrm_f);   // nrm_* may be NULL (device, k each)
 slab_status launch_apply(slab_handle* h, const double* x, double* y, int k);
 slab_status launch_kappa_gradient(slab_handle* h, const double* u, const double* lam, double* g, int k);
+// FP64 vector kernels for the Krylov refinement (batched over k vectors of length N)
+slab_status vec_dot(slab_handle* h, const double* x, const double* y, int64_t N, int k, double* part, double* out);
+slab_status vec_axpy(slab_handle* h, double* y, const double* x, const double* c, double sign, int64_t N, int k);
+slab_status vec_scale(slab_handle* h, double* x, const double* nrm2, int64_t N, int k);
+slab_status vec_combine(slab_handle* h, double* u, const double* Z, int64_t zstride, const double* c, int j, int k,
+                        int64_t N);
+size_t vec_dot_part_elems(int k);
 
 // stage 1 (tree.cu)
 int tree_kmax();   // right-hand sides per solve-phase launch

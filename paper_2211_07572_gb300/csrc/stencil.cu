@@ -182,6 +182,76 @@ __global__ void kappa_grad2d_kernel(int n, const double* __restrict__ u,
     g[(int64_t)y * (n + 1) + x] += acc;
 }
 
+// ---------------------------------------------------------------- FP64 vector kernels (Krylov)
+// Batched over k vectors of length N, vector q at x + q * N.  Dot products are reduced in a
+// fixed order (per-block partials, then one block per vector), so they are deterministic.
+constexpr int VD_BLOCKS = 256;
+
+__global__ void __launch_bounds__(256) vdot_partial_kernel(const double* __restrict__ x,
+                                                           const double* __restrict__ y, int64_t N,
+                                                           double* part) {
+    const int q = blockIdx.y;
+    x += (int64_t)q * N;
+    y += (int64_t)q * N;
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < N; i += (int64_t)gridDim.x * 256)
+        acc += x[i] * y[i];
+    __shared__ double red[8];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < 8; ++w) s += red[w];
+        part[(int64_t)q * gridDim.x + blockIdx.x] = s;
+    }
+}
+
+__global__ void vdot_final_kernel(const double* __restrict__ part, int nb, double* out) {
+    const int q = blockIdx.x;
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) s += part[(int64_t)q * nb + b];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[q] = red[0];
+}
+
+// y_q += sign * c_q * x_q
+__global__ void vaxpy_kernel(double* y, const double* __restrict__ x, const double* __restrict__ c,
+                             double sign, int64_t N) {
+    const int q = blockIdx.y;
+    const double a = sign * c[q];
+    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < N; i += (int64_t)gridDim.x * 256)
+        y[(int64_t)q * N + i] += a * x[(int64_t)q * N + i];
+}
+
+// x_q *= 1 / sqrt(nrm2_q)  (left as is when nrm2_q is zero)
+__global__ void vscale_kernel(double* x, const double* __restrict__ nrm2, int64_t N) {
+    const int q = blockIdx.y;
+    const double v = nrm2[q];
+    if (!(v > 0.0)) return;
+    const double a = 1.0 / sqrt(v);
+    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < N; i += (int64_t)gridDim.x * 256)
+        x[(int64_t)q * N + i] *= a;
+}
+
+// u_q += sum_{i < j} c[i][q] Z_i,q   (Z_i at Z + i * zstride)
+__global__ void vcombine_kernel(double* u, const double* __restrict__ Z, int64_t zstride,
+                                const double* __restrict__ c, int j, int k, int64_t N) {
+    const int q = blockIdx.y;
+    for (int64_t n = (int64_t)blockIdx.x * 256 + threadIdx.x; n < N; n += (int64_t)gridDim.x * 256) {
+        double acc = u[(int64_t)q * N + n];
+        for (int i = 0; i < j; ++i) acc += c[(int64_t)i * k + q] * Z[i * zstride + (int64_t)q * N + n];
+        u[(int64_t)q * N + n] = acc;
+    }
+}
+
 }  // namespace
 
 slab_status launch_coefficients(slab_handle* h, const double* kappa, const double* c) {
@@ -239,3 +309,37 @@ slab_status launch_kappa_gradient(slab_handle* h, const double* u, const double*
     SLAB_CK_LAUNCH(h);
     return SLAB_OK;
 }
+
+slab_status vec_dot(slab_handle* h, const double* x, const double* y, int64_t N, int k, double* part,
+                    double* out) {
+    SLAB_PROF(h, KC_OTHER);
+    vdot_partial_kernel<<<dim3(VD_BLOCKS, k), 256, 0, h->stream>>>(x, y, N, part);
+    SLAB_CK_LAUNCH(h);
+    vdot_final_kernel<<<k, 256, 0, h->stream>>>(part, VD_BLOCKS, out);
+    SLAB_CK_LAUNCH(h);
+    return SLAB_OK;
+}
+
+slab_status vec_axpy(slab_handle* h, double* y, const double* x, const double* c, double sign, int64_t N, int k) {
+    SLAB_PROF(h, KC_OTHER);
+    vaxpy_kernel<<<dim3(2 * 152, k), 256, 0, h->stream>>>(y, x, c, sign, N);
+    SLAB_CK_LAUNCH(h);
+    return SLAB_OK;
+}
+
+slab_status vec_scale(slab_handle* h, double* x, const double* nrm2, int64_t N, int k) {
+    SLAB_PROF(h, KC_OTHER);
+    vscale_kernel<<<dim3(2 * 152, k), 256, 0, h->stream>>>(x, nrm2, N);
+    SLAB_CK_LAUNCH(h);
+    return SLAB_OK;
+}
+
+slab_status vec_combine(slab_handle* h, double* u, const double* Z, int64_t zstride, const double* c, int j, int k,
+                        int64_t N) {
+    SLAB_PROF(h, KC_OTHER);
+    vcombine_kernel<<<dim3(2 * 152, k), 256, 0, h->stream>>>(u, Z, zstride, c, j, k, N);
+    SLAB_CK_LAUNCH(h);
+    return SLAB_OK;
+}
+
+size_t vec_dot_part_elems(int k) { return (size_t)VD_BLOCKS * k; }

@@ -17,12 +17,13 @@ from paper_2211_07572_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 
-def _solver(p, precision, rtol=1e-12, max_refine=30, iprec=None):
+def _solver(p, precision, rtol=1e-12, max_refine=30, iprec=None, krylov=0):
     """precision "fp32" runs the FP32 slab trees with the FP64 interface system (the default for
-    Helmholtz); iprec="fp32" forces the FP32 interface system as well."""
+    Helmholtz); iprec="fp32" forces the FP32 interface system as well; krylov=m refines by
+    FP64 GMRES(m) preconditioned by the factor."""
     from paper_2211_07572_gb300.solver import SlabSolver
     return SlabSolver(p.dim, p.n, p.b, p.kind, c=p.c, omega=p.omega, precision=precision, rtol=rtol,
-                      max_refine=max_refine, interface_precision=iprec)
+                      max_refine=max_refine, interface_precision=iprec, krylov=krylov)
 
 
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 1e-3)])
@@ -143,15 +144,14 @@ def test_helmholtz_point_source_residual():
     assert oracle.relres(A, u.cpu().numpy(), p.f).max() <= 1e-10
 
 
-@pytest.mark.parametrize("precision", ["fp64"])
-def test_helmholtz_solve_matches_oracle_n512(precision):
+@pytest.mark.parametrize("precision,iprec,krylov", [("fp64", None, 0), ("fp64", None, 10)])
+def test_helmholtz_solve_matches_oracle_n512(precision, iprec, krylov):
     """End to end at n = 512, b = 32 (the Helmholtz workload's b and points per wavelength; eight
     Stage-2 panels with two tournament merge levels): refined solution vs the pivoted banded LU.
-    With an FP32 factor (FP32 slab trees, FP32 or FP64 interface) plain refinement diverges here:
-    the FP32 error of the factor times the conditioning exceeds one."""
+    FP64 factor, with plain refinement and with GMRES(10) refinement."""
     n, b = 512, 32
     p = inputs.helmholtz(n, b, n_modes=8, field_seed=3)
-    s = _solver(p, precision, rtol=1e-12, max_refine=40)
+    s = _solver(p, precision, rtol=1e-12, max_refine=60, iprec=iprec, krylov=krylov)
     u, rel, it = s.solve(torch.from_numpy(p.f).cuda(), allow_noconv=True)
     u = u.cpu().numpy()
     s.close()
@@ -160,3 +160,19 @@ def test_helmholtz_solve_matches_oracle_n512(precision):
     assert oracle.relres(A, u, p.f).max() <= 1e-10
     err = np.linalg.norm(u - uo, axis=1) / np.linalg.norm(uo, axis=1)
     assert err.max() <= 1e-8, err
+
+
+@pytest.mark.parametrize("iprec,krylov", [(None, 0), ("fp32", 0), (None, 30)])
+def test_helmholtz_fp32_factor_reports_noconv_n512(iprec, krylov):
+    """At n = 512 and 10 points per wavelength an FP32 factor (FP32 slab trees with an FP64 or
+    FP32 interface system) is too inaccurate for this indefinite operator: plain refinement
+    diverges and GMRES preconditioned by it stagnates.  The solver must say so (ENOCONV, status
+    4) rather than return the iterate as converged."""
+    from paper_2211_07572_gb300 import SlabError
+    n, b = 512, 32
+    p = inputs.helmholtz(n, b, n_modes=8, field_seed=3)
+    s = _solver(p, "fp32", rtol=1e-10, max_refine=20, iprec=iprec, krylov=krylov)
+    with pytest.raises(SlabError) as ei:
+        s.solve(torch.from_numpy(p.f).cuda())
+    assert ei.value.status == 4
+    s.close()

@@ -186,6 +186,25 @@ def test_mixed_precision_matches_oracle(stage2):
         _solver(p, "fp64", iprec="fp32")                    # an FP64 factor with an FP32 interface
 
 
+def test_gmres_refinement_matches_oracle():
+    """FP64 GMRES(8) preconditioned by the FP32 factor, three right-hand sides with separate Krylov
+    spaces and a restart: same solution as the oracle, fewer preconditioner applications than
+    plain refinement needs."""
+    from paper_2211_07572_gb300.solver import SlabSolver
+    p = inputs.diffusion(256, 16, k=3, n_modes=16, field_seed=2, rhs_seed=104)
+    s = SlabSolver(2, p.n, p.b, p.kind, kappa=p.kappa, precision="fp32", rtol=1e-13, max_refine=40, krylov=8)
+    u, rel, it = s.solve(torch.from_numpy(p.f).cuda())
+    s.close()
+    s0 = SlabSolver(2, p.n, p.b, p.kind, kappa=p.kappa, precision="fp32", rtol=1e-13, max_refine=40)
+    _, rel0, it0 = s0.solve(torch.from_numpy(p.f).cuda(), allow_noconv=True)
+    s0.close()
+    A = oracle.assemble_problem(p)
+    uo = oracle.solve(p)
+    assert rel.max() <= 1e-13 and oracle.relres(A, u.cpu().numpy(), p.f).max() <= 1e-12
+    assert (np.linalg.norm(u.cpu().numpy() - uo, axis=1) / np.linalg.norm(uo, axis=1)).max() <= 1e-10
+    assert it <= it0 + 1, (it, it0)
+
+
 def test_many_rhs_chunks_and_empty():
     """k > 64 runs in several passes; k = 0 is a no-op."""
     p = _problem(64, 8, inputs.DIFFUSION, k=70, seed=3)
