@@ -41,6 +41,7 @@ void dfree(void*& p) {
 
 void free_workspace(slab_handle* h) {
     dfree(h->wYv); dfree(h->wGtb); dfree(h->wXs); dfree(h->wFi); dfree(h->wX); dfree(h->wZ);
+    dfree(h->t3y); dfree(h->t3G); dfree(h->t3x); dfree(h->t3Fi); dfree(h->t3xI);
     dfree(h->wVp);
     dfree(h->wVtk);
     dfree(h->wPart);
@@ -60,21 +61,50 @@ void free_workspace(slab_handle* h) {
         if (_s != SLAB_OK) return _s;     \
     } while (0)
 
+// Stage-1 solve phases by dimension
+template <typename T>
+slab_status up_gather(slab_handle* h, const double* F, double fscale, int r0, int K) {
+    return h->dim == 3 ? tree3d_up_gather<T>(h, F, fscale, r0, K) : tree_up_gather<T>(h, F, fscale, r0, K);
+}
+template <typename T>
+slab_status down_scatter(slab_handle* h, double* U, int accumulate, int r0, int K) {
+    return h->dim == 3 ? tree3d_down_scatter<T>(h, U, accumulate, r0, K) : tree_down_scatter<T>(h, U, accumulate, r0, K);
+}
+template <typename T>
+slab_status export_x(slab_handle* h, double* out, double scale, int r0, int K) {
+    return h->dim == 3 ? tree3d_export<T>(h, out, scale, r0, K) : export_ftilde_part<T>(h, out, scale, r0, K);
+}
+template <typename T>
+slab_status import_x(slab_handle* h, const double* in, int r0, int K) {
+    return h->dim == 3 ? tree3d_import<T>(h, in, r0, K) : import_utilde_part<T>(h, in, r0, K);
+}
+
 // Solve workspace for up to kc right-hand sides per pass and k total (residual buffer).
 slab_status ensure_workspace(slab_handle* h, int k) {
     const int kc = k < tree_kmax() ? k : tree_kmax();
     const TreeDims& d = h->td;
-    const int64_t N = (int64_t)d.s * d.s;
+    const int64_t N = d.N;
     static_assert(sizeof(double) == 8, "");
     if (h->kcap < kc) {
         const int64_t nodes = (int64_t)d.NS * (d.s + 1);
         dfree(h->wYv); dfree(h->wGtb); dfree(h->wXs); dfree(h->wFi); dfree(h->wX); dfree(h->wZ);
         dfree(h->wX2); dfree(h->wZ2);
+        dfree(h->t3y); dfree(h->t3G); dfree(h->t3x); dfree(h->t3Fi); dfree(h->t3xI);
         h->kcap = 0;
-        TRY(dalloc(h, &h->wYv, nodes * d.m * kc * h->rsz));
-        TRY(dalloc(h, &h->wGtb, nodes * 2 * d.m * kc * h->rsz));
-        TRY(dalloc(h, &h->wXs, nodes * d.m * kc * h->rsz));
-        TRY(dalloc(h, &h->wFi, (int64_t)d.NS * 2 * d.s_pad * kc * h->rsz));
+        if (h->dim == 3) {
+            const int64_t nn = tree3d_nodes(h->t3plan);
+            const int64_t Mp = tree3d_mpad(h->t3plan);
+            TRY(dalloc(h, &h->t3y, nn * kc * Mp * h->rsz));
+            TRY(dalloc(h, &h->t3x, nn * kc * Mp * h->rsz));
+            TRY(dalloc(h, &h->t3G, nn * kc * 2 * Mp * h->rsz));
+            TRY(dalloc(h, &h->t3Fi, (int64_t)d.NS * 2 * kc * d.s_pad * h->rsz));
+            TRY(dalloc(h, &h->t3xI, tree3d_xI_elems(h->t3plan) * kc * h->rsz));
+        } else {
+            TRY(dalloc(h, &h->wYv, nodes * d.m * kc * h->rsz));
+            TRY(dalloc(h, &h->wGtb, nodes * 2 * d.m * kc * h->rsz));
+            TRY(dalloc(h, &h->wXs, nodes * d.m * kc * h->rsz));
+            TRY(dalloc(h, &h->wFi, (int64_t)d.NS * 2 * d.s_pad * kc * h->rsz));
+        }
         TRY(dalloc(h, &h->wX, (int64_t)d.NI * d.s_pad * kc * h->rsz));
         TRY(dalloc(h, &h->wZ, (int64_t)d.NI * d.s_pad * kc * h->rsz));
         if (h->prec2 != h->prec) {
@@ -83,7 +113,7 @@ slab_status ensure_workspace(slab_handle* h, int k) {
         }
         h->kcap = kc;
     }
-    if (!h->wVtk) {
+    if (!h->wVtk && h->dim == 2) {
         const size_t e = tree_down_ws_elems(d.s, d.m, d.NS);
         TRY(dalloc(h, &h->wVp, (e ? e : 1) * h->rsz));
         const size_t nt = tree_down_tickets(d.s, d.NS);
@@ -102,7 +132,7 @@ slab_status ensure_workspace(slab_handle* h, int k) {
 
 // FP64 residual buffer and norms for k right-hand sides.
 slab_status ensure_resid(slab_handle* h, int k) {
-    const int64_t N = (int64_t)h->td.s * h->td.s;
+    const int64_t N = h->td.N;
     if (h->rcap < k) {
         void* r = h->wR; dfree(r); h->wR = nullptr;
         void* q = h->wNrm; dfree(q); h->wNrm = nullptr;
@@ -146,9 +176,15 @@ slab_status solve_pass(slab_handle* h, const double* F, double fscale, double* U
     const int kc = h->kcap;
     for (int r0 = 0; r0 < k; r0 += kc) {
         const int K = (k - r0) < kc ? (k - r0) : kc;
-        TRY(tree_up_gather<T>(h, F, fscale, r0, K));
-        TRY(interface_sweep(h, K));
-        TRY(tree_down_scatter<T>(h, U, accumulate, r0, K));
+        if (h->dim == 3) {
+            TRY(tree3d_up_gather<T>(h, F, fscale, r0, K));
+            TRY(interface_sweep(h, K));
+            TRY(tree3d_down_scatter<T>(h, U, accumulate, r0, K));
+        } else {
+            TRY(tree_up_gather<T>(h, F, fscale, r0, K));
+            TRY(interface_sweep(h, K));
+            TRY(tree_down_scatter<T>(h, U, accumulate, r0, K));
+        }
     }
     return SLAB_OK;
 }
@@ -190,11 +226,18 @@ slab_status sync_status(slab_handle* h) {
     return SLAB_OK;
 }
 
+// Stage 1 and the assembly of T (into h->Tb / h->To in the Stage-1 scalar)
+template <typename T>
+slab_status stage1_impl(slab_handle* h) {
+    if (h->dim == 3) return tree3d_factor<T>(h);
+    TRY(tree_factor<T>(h));
+    return assemble_T<T>(h);
+}
+
 template <typename T>
 slab_status factor_impl(slab_handle* h) {
-    TRY(tree_factor<T>(h));
     if (h->prec2 == h->prec) {
-        TRY(assemble_T<T>(h));
+        TRY(stage1_impl<T>(h));
         return sweep_factor<T>(h);
     }
     // mixed mode: assemble T in the Stage-1 scalar, widen it, eliminate in the Stage-2 scalar
@@ -202,7 +245,7 @@ slab_status factor_impl(slab_handle* h) {
     void* To2 = h->To;
     h->Tb = h->Tb1;
     h->To = h->To1;
-    const slab_status st = assemble_T<T>(h);
+    const slab_status st = stage1_impl<T>(h);
     h->Tb = Tb2;
     h->To = To2;
     TRY(st);
@@ -324,6 +367,10 @@ void slab_destroy(slab_handle* h) {
     p = h->AX; dfree(p); p = h->AY; dfree(p); p = h->DG; dfree(p); p = h->kappa; dfree(p);
     dfree(h->tLinv); dfree(h->tZtb); dfree(h->tRtb); dfree(h->tZI); dfree(h->tRI);
     dfree(h->tWtb); dfree(h->tWI); dfree(h->ToT); dfree(h->dscratch); dfree(h->gjw);
+    p = h->AZ; dfree(p);
+    dfree(h->t3Lin); dfree(h->t3LT); dfree(h->t3Ztb); dfree(h->t3ZtbT); dfree(h->t3ZIT); dfree(h->t3ZI);
+    dfree(h->t3Rtb); dfree(h->t3RI); dfree(h->t3W);
+    if (h->t3plan) tree3d_plan_free(h->t3plan);
     dfree(h->Tb); dfree(h->To); dfree(h->Fct); dfree(h->Linv); dfree(h->Y);
     dfree(h->crD); dfree(h->crE); dfree(h->crW); dfree(h->crLT); dfree(h->Tb1); dfree(h->To1);
     dfree(h->crPt); dfree(h->crP); dfree(h->crQt); dfree(h->crQ);
@@ -352,8 +399,8 @@ slab_status slab_factor(const slab_grid* grid, const slab_coeffs* co, int b, con
     if (prec2 == -1) prec2 = (co->kind == SLAB_HELMHOLTZ) ? SLAB_PREC_FP64 : o.factor_prec;
     if (prec2 != SLAB_PREC_FP32 && prec2 != SLAB_PREC_FP64) return SLAB_EINVAL;
     if (o.factor_prec == SLAB_PREC_FP64 && prec2 == SLAB_PREC_FP32) return SLAB_EINVAL;
-    if (grid->dim != 2) return SLAB_EUNSUPPORTED;
-    if (b - 1 > SLAB_MAXM) return SLAB_EUNSUPPORTED;
+    if (grid->dim == 2 && b - 1 > SLAB_MAXM) return SLAB_EUNSUPPORTED;
+    if (grid->dim == 3 && co->kind == SLAB_HELMHOLTZ) return SLAB_EUNSUPPORTED;
     if (o.stage2 == SLAB_STAGE2_ODDEVEN && co->kind == SLAB_HELMHOLTZ) return SLAB_EUNSUPPORTED;
 
     slab_handle* h = new (std::nothrow) slab_handle();
@@ -371,7 +418,9 @@ slab_status slab_factor(const slab_grid* grid, const slab_coeffs* co, int b, con
     if (o.profile) slab_profile(h, 1);
     TreeDims& d = h->td;
     d.s = n - 1;
-    d.s_pad = (d.s + SLAB_TILE - 1) / SLAB_TILE * SLAB_TILE;
+    d.si = grid->dim == 3 ? d.s * d.s : d.s;
+    d.N = (int64_t)d.si * d.s;
+    d.s_pad = (d.si + SLAB_TILE - 1) / SLAB_TILE * SLAB_TILE;
     d.m = b - 1;
     d.H = tree_height_count(d.s);
     d.NS = n / b;
@@ -381,7 +430,7 @@ slab_status slab_factor(const slab_grid* grid, const slab_coeffs* co, int b, con
     h->nt = d.s_pad / SLAB_TILE;
 
     slab_status st = SLAB_OK;
-    const size_t nodes2 = (size_t)(n + 1) * (n + 1);
+    const size_t nodes2 = (size_t)(n + 1) * (n + 1) * (grid->dim == 3 ? (size_t)(n + 1) : 1);
     const size_t R = h->rsz;
     const size_t R2 = h->rsz2;
     const int64_t tn = (int64_t)d.NS * (d.s + 1);
@@ -397,11 +446,27 @@ slab_status slab_factor(const slab_grid* grid, const slab_coeffs* co, int b, con
     ALLOC(h->AY, nodes2 * sizeof(double));
     ALLOC(h->DG, nodes2 * sizeof(double));
     if (co->kind == SLAB_DIFFUSION) ALLOC(h->kappa, nodes2 * sizeof(double));
-    ALLOC(h->tLinv, tn * d.m * d.m * R);
-    ALLOC(h->tZtb, tn * 2 * d.m * d.m * R);
-    ALLOC(h->tRtb, tn * 4 * d.m * d.m * R);
-    ALLOC(h->tZI, (int64_t)d.NS * d.H * 2 * d.m * d.s_pad * R);
-    ALLOC(h->tRI, (int64_t)d.NS * d.H * 4 * d.m * d.s_pad * R);
+    if (grid->dim == 3) {
+        ALLOC(h->AZ, nodes2 * sizeof(double));
+        h->t3plan = tree3d_plan(d.s, d.m, d.NS);
+        const int64_t nn = tree3d_nodes(h->t3plan);
+        const int64_t Mp = tree3d_mpad(h->t3plan);
+        ALLOC(h->t3Lin, nn * Mp * Mp * R);
+        ALLOC(h->t3LT, nn * Mp * Mp * R);
+        ALLOC(h->t3Ztb, nn * 2 * Mp * Mp * R);
+        ALLOC(h->t3ZtbT, nn * 2 * Mp * Mp * R);
+        ALLOC(h->t3ZIT, tree3d_zit_elems(h->t3plan) * R);
+        ALLOC(h->t3ZI, tree3d_zit_elems(h->t3plan) * R);
+        ALLOC(h->t3Rtb, nn * 4 * Mp * Mp * R);
+        ALLOC(h->t3RI, (int64_t)d.NS * d.H * 4 * Mp * d.s_pad * R);
+        ALLOC(h->t3W, tree3d_work_elems(h->t3plan) * R);
+    } else {
+        ALLOC(h->tLinv, tn * d.m * d.m * R);
+        ALLOC(h->tZtb, tn * 2 * d.m * d.m * R);
+        ALLOC(h->tRtb, tn * 4 * d.m * d.m * R);
+        ALLOC(h->tZI, (int64_t)d.NS * d.H * 2 * d.m * d.s_pad * R);
+        ALLOC(h->tRI, (int64_t)d.NS * d.H * 4 * d.m * d.s_pad * R);
+    }
     ALLOC(h->Tb, d.NI * blk * R2);
     ALLOC(h->To, (d.NI - 1) * blk * R2);
     if (h->prec2 != h->prec) {
@@ -441,8 +506,8 @@ slab_status slab_factor(const slab_grid* grid, const slab_coeffs* co, int b, con
         if ((call) != cudaSuccess) { cudaGetLastError(); slab_destroy(h); return SLAB_ECUDA; } \
     } while (0)
     CK(cudaMemsetAsync(h->dstatus, 0, sizeof(unsigned), h->stream));
-    CK(cudaMemsetAsync(h->tZI, 0, (size_t)d.NS * d.H * 2 * d.m * d.s_pad * R, h->stream));
-    CK(cudaMemsetAsync(h->tRI, 0, (size_t)d.NS * d.H * 4 * d.m * d.s_pad * R, h->stream));
+    if (h->tZI) CK(cudaMemsetAsync(h->tZI, 0, (size_t)d.NS * d.H * 2 * d.m * d.s_pad * R, h->stream));
+    if (h->tRI) CK(cudaMemsetAsync(h->tRI, 0, (size_t)d.NS * d.H * 4 * d.m * d.s_pad * R, h->stream));
     if (h->tWI) CK(cudaMemsetAsync(h->tWI, 0, (size_t)d.NS * d.H * 2 * d.m * d.s_pad * R, h->stream));
     if (h->kappa)
         CK(cudaMemcpyAsync(h->kappa, co->kappa, nodes2 * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
@@ -457,6 +522,9 @@ slab_status slab_factor(const slab_grid* grid, const slab_coeffs* co, int b, con
     dfree(h->Tb1);                                     // mixed-mode assembly buffers
     dfree(h->To1);
     h->Tb1 = h->To1 = nullptr;
+    dfree(h->t3Rtb);                                   // 3-D factor-only arrays
+    dfree(h->t3RI);
+    dfree(h->t3W);
     *out = h;
     return SLAB_OK;
 }
@@ -482,7 +550,7 @@ namespace {
 slab_status ensure_krylov(slab_handle* h, int k) {
     if (h->kcapk >= k) return SLAB_OK;
     const int m = h->krylov;
-    const int64_t N = (int64_t)h->td.s * h->td.s;
+    const int64_t N = h->td.N;
     void* p = h->kV; dfree(p); p = h->kZ; dfree(p); p = h->kS; dfree(p);
     h->kV = h->kZ = h->kS = nullptr;
     h->kcapk = 0;
@@ -503,7 +571,7 @@ slab_status ensure_krylov(slab_handle* h, int k) {
 // preconditioner applications after the first.
 slab_status gmres_solve(slab_handle* h, const double* f, double* u, int k, double* relres_out, int* iters_out) {
     const int m = h->krylov;
-    const int64_t N = (int64_t)h->td.s * h->td.s;
+    const int64_t N = h->td.N;
     const int64_t kN = (int64_t)k * N;
     const double h2 = 1.0 / ((double)h->n * (double)h->n);
     TRY(ensure_workspace(h, k));
@@ -678,6 +746,7 @@ slab_status slab_adjoint(slab_handle* h, const double* dLdu, const double* u, do
     if (k == 0) return SLAB_OK;
     if (!dLdu || !lambda) return SLAB_EINVAL;
     if (dLdkappa && (h->kind != SLAB_DIFFUSION || !u)) return SLAB_EINVAL;
+    if (dLdkappa && h->dim != 2) return SLAB_EUNSUPPORTED;
     // every supported operator is symmetric, so A^T lambda = dL/du is solved with the same factors
     slab_status st = slab_solve(h, dLdu, lambda, k, nullptr, nullptr);
     if (st != SLAB_OK && st != SLAB_ENOCONV) return st;
@@ -694,11 +763,11 @@ slab_status slab_reduced_rhs(slab_handle* h, const double* f, double* ftilde, in
     for (int r0 = 0; r0 < k; r0 += h->kcap) {
         const int K = (k - r0) < h->kcap ? (k - r0) : h->kcap;
         if (h->prec == SLAB_PREC_FP64) {
-            TRY(tree_up_gather<double>(h, f, h2, r0, K));
-            TRY(export_ftilde_part<double>(h, ftilde, 1.0 / h2, r0, K));
+            TRY(up_gather<double>(h, f, h2, r0, K));
+            TRY(export_x<double>(h, ftilde, 1.0 / h2, r0, K));
         } else {
-            TRY(tree_up_gather<float>(h, f, h2, r0, K));
-            TRY(export_ftilde_part<float>(h, ftilde, 1.0 / h2, r0, K));
+            TRY(up_gather<float>(h, f, h2, r0, K));
+            TRY(export_x<float>(h, ftilde, 1.0 / h2, r0, K));
         }
     }
     return SLAB_OK;
@@ -714,17 +783,17 @@ slab_status slab_interface_solve(slab_handle* h, const double* ftilde, double* u
         const int K = (k - r0) < h->kcap ? (k - r0) : h->kcap;
         if (h->prec2 != h->prec) {
             Stage2Vectors v(h);
-            TRY(import_utilde_part<double>(h, ftilde, r0, K));
+            TRY(import_x<double>(h, ftilde, r0, K));
             TRY(sweep_solve<double>(h, K));
-            TRY(export_ftilde_part<double>(h, utilde, h2, r0, K));
+            TRY(export_x<double>(h, utilde, h2, r0, K));
         } else if (h->prec == SLAB_PREC_FP64) {
-            TRY(import_utilde_part<double>(h, ftilde, r0, K));
+            TRY(import_x<double>(h, ftilde, r0, K));
             TRY(sweep_solve<double>(h, K));
-            TRY(export_ftilde_part<double>(h, utilde, h2, r0, K));
+            TRY(export_x<double>(h, utilde, h2, r0, K));
         } else {
-            TRY(import_utilde_part<float>(h, ftilde, r0, K));
+            TRY(import_x<float>(h, ftilde, r0, K));
             TRY(sweep_solve<float>(h, K));
-            TRY(export_ftilde_part<float>(h, utilde, h2, r0, K));
+            TRY(export_x<float>(h, utilde, h2, r0, K));
         }
     }
     return SLAB_OK;
@@ -739,13 +808,13 @@ slab_status slab_interior_solve(slab_handle* h, const double* f, const double* u
     for (int r0 = 0; r0 < k; r0 += h->kcap) {
         const int K = (k - r0) < h->kcap ? (k - r0) : h->kcap;
         if (h->prec == SLAB_PREC_FP64) {
-            TRY(tree_up_gather<double>(h, f, h2, r0, K));
-            TRY(import_utilde_part<double>(h, utilde, r0, K));
-            TRY(tree_down_scatter<double>(h, u, 0, r0, K));
+            TRY(up_gather<double>(h, f, h2, r0, K));
+            TRY(import_x<double>(h, utilde, r0, K));
+            TRY(down_scatter<double>(h, u, 0, r0, K));
         } else {
-            TRY(tree_up_gather<float>(h, f, h2, r0, K));
-            TRY(import_utilde_part<float>(h, utilde, r0, K));
-            TRY(tree_down_scatter<float>(h, u, 0, r0, K));
+            TRY(up_gather<float>(h, f, h2, r0, K));
+            TRY(import_x<float>(h, utilde, r0, K));
+            TRY(down_scatter<float>(h, u, 0, r0, K));
         }
     }
     return SLAB_OK;
@@ -761,11 +830,11 @@ slab_status slab_get_T_block(slab_handle* h, int which, int q, double* out) {
     SLAB_CK(h, cudaMemcpyAsync(tmp.data(), base, tmp.size(), cudaMemcpyDeviceToHost, h->stream));
     SLAB_CK(h, cudaStreamSynchronize(h->stream));
     const double sc = (double)h->n * (double)h->n;
-    for (int i = 0; i < d.s; ++i)
-        for (int j = 0; j < d.s; ++j) {
+    for (int i = 0; i < d.si; ++i)
+        for (int j = 0; j < d.si; ++j) {
             const int64_t e = (int64_t)i * d.s_pad + j;
             const double v = h->rsz2 == 8 ? ((const double*)tmp.data())[e] : (double)((const float*)tmp.data())[e];
-            out[(int64_t)i * d.s + j] = sc * v;
+            out[(int64_t)i * d.si + j] = sc * v;
         }
     return SLAB_OK;
 }

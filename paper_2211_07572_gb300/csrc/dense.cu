@@ -1242,3 +1242,114 @@ template slab_status cr_factor<float>(slab_handle*);
 template slab_status cr_factor<double>(slab_handle*);
 template slab_status cr_solve<float>(slab_handle*, int);
 template slab_status cr_solve<double>(slab_handle*, int);
+
+// ---------------------------------------------------------------- exported dense helpers
+namespace {
+// out[c][r] = in[r][c] for a rows x cols block (leading dimensions ldin, ldout), batched by blockIdx.z
+template <typename T>
+__global__ void transpose_rect_kernel(const T* __restrict__ in, int64_t ldin, int64_t sin, T* __restrict__ out,
+                                      int64_t ldout, int64_t sout, int rows, int cols) {
+    __shared__ T tile[32][33];
+    in += (int64_t)blockIdx.z * sin;
+    out += (int64_t)blockIdx.z * sout;
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        const int r = r0 + j, c = c0 + threadIdx.x;
+        if (r < rows && c < cols) tile[j][threadIdx.x] = in[(int64_t)r * ldin + c];
+    }
+    __syncthreads();
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        const int c = c0 + j, r = r0 + threadIdx.x;
+        if (r < rows && c < cols) out[(int64_t)c * ldout + r] = tile[threadIdx.x][j];
+    }
+}
+
+template <typename T>
+__global__ void copy_batched_kernel(const T* __restrict__ in, int64_t sin, T* __restrict__ out, int64_t sout,
+                                    int64_t n) {
+    in += (int64_t)blockIdx.y * sin;
+    out += (int64_t)blockIdx.y * sout;
+    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256) out[i] = in[i];
+}
+}  // namespace
+
+template <typename T>
+slab_status dense_gemm(slab_handle* h, int cls, int M, int N, int K, T alpha, const T* A, int64_t lda, int64_t sA,
+                       const T* B, int64_t ldb, int64_t sB, T beta, T* C, int64_t ldc, int64_t sC, int transC,
+                       int lower_only, int batch) {
+    if (batch <= 0 || M <= 0 || N <= 0) return SLAB_OK;
+    if (batch == 1) return gemm_tn<T>(h, cls, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, transC, lower_only);
+    return gemm_tn_batched<T>(h, cls, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, transC, lower_only,
+                              batch);
+}
+
+template <typename T>
+slab_status dense_transpose(slab_handle* h, const T* in, int64_t ldin, int64_t sin, T* out, int64_t ldout,
+                            int64_t sout, int rows, int cols, int batch) {
+    if (batch <= 0 || rows <= 0 || cols <= 0) return SLAB_OK;
+    for (int b0 = 0; b0 < batch; b0 += 65535) {
+        const int nb = std::min(65535, batch - b0);
+        dim3 grid((cols + 31) / 32, (rows + 31) / 32, nb);
+        SLAB_PROF(h, KC_OTHER);
+        transpose_rect_kernel<T><<<grid, dim3(32, 8), 0, h->stream>>>(in + b0 * sin, ldin, sin, out + b0 * sout,
+                                                                      ldout, sout, rows, cols);
+        SLAB_CK_LAUNCH(h);
+    }
+    return SLAB_OK;
+}
+
+template <typename T>
+slab_status dense_copy(slab_handle* h, const T* in, int64_t sin, T* out, int64_t sout, int64_t n, int batch) {
+    if (batch <= 0 || n <= 0) return SLAB_OK;
+    for (int b0 = 0; b0 < batch; b0 += 65535) {
+        const int nb = std::min(65535, batch - b0);
+        SLAB_PROF(h, KC_OTHER);
+        copy_batched_kernel<T><<<dim3((unsigned)std::min<int64_t>((n + 255) / 256, 64), nb), 256, 0, h->stream>>>(
+            in + b0 * sin, sin, out + b0 * sout, sout, n);
+        SLAB_CK_LAUNCH(h);
+    }
+    return SLAB_OK;
+}
+
+// Cholesky of the leading ncols x ncols block of a batch of tall matrices (row-major, ld = ncols,
+// bstride apart) whose rows below are eliminated with it: rows [ncols, ident0) receive B^T L^{-T},
+// rows [ident0, ident0 + ncols), which must hold the identity, receive L^{-T}.
+template <typename T>
+slab_status dense_tall_cholesky(slab_handle* h, T* W, int ncols, int ident0, int batch, int64_t bstride) {
+    const size_t smem = 3 * TL * TLP * sizeof(T);
+    SLAB_CK(h, cudaFuncSetAttribute(panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    slab_status st;
+    const int nt = ncols / TL;
+    for (int kb = 0; kb < nt; ++kb) {
+        const int rows = ident0 + (kb + 1) * TL;      // identity rows below are still zero in these columns
+        const int nrt = rows / TL - kb - 1;
+        for (int b0 = 0; b0 < batch; b0 += 65535) {
+            const int nb = std::min(65535, batch - b0);
+            SLAB_PROF(h, KC_PANEL);
+            panel_kernel<T><<<dim3(nrt, nb), 256, smem, h->stream>>>(W + b0 * bstride, ncols, kb, h->dstatus, bstride);
+            SLAB_CK_LAUNCH(h);
+        }
+        const int c0 = (kb + 1) * TL;
+        if (c0 < ncols) {
+            const T* P = W + (int64_t)c0 * ncols + (int64_t)kb * TL;
+            if ((st = dense_gemm<T>(h, KC_TRAIL, rows - c0, ncols - c0, TL, T(-1), P, ncols, bstride, P, ncols, bstride,
+                                    T(1), W + (int64_t)c0 * ncols + c0, ncols, bstride, 0, 1, batch)))
+                return st;
+        }
+    }
+    return SLAB_OK;
+}
+
+template slab_status dense_gemm<float>(slab_handle*, int, int, int, int, float, const float*, int64_t, int64_t,
+                                       const float*, int64_t, int64_t, float, float*, int64_t, int64_t, int, int, int);
+template slab_status dense_gemm<double>(slab_handle*, int, int, int, int, double, const double*, int64_t, int64_t,
+                                        const double*, int64_t, int64_t, double, double*, int64_t, int64_t, int, int,
+                                        int);
+template slab_status dense_transpose<float>(slab_handle*, const float*, int64_t, int64_t, float*, int64_t, int64_t,
+                                            int, int, int);
+template slab_status dense_transpose<double>(slab_handle*, const double*, int64_t, int64_t, double*, int64_t,
+                                             int64_t, int, int, int);
+template slab_status dense_copy<float>(slab_handle*, const float*, int64_t, float*, int64_t, int64_t, int);
+template slab_status dense_copy<double>(slab_handle*, const double*, int64_t, double*, int64_t, int64_t, int);
+template slab_status dense_tall_cholesky<float>(slab_handle*, float*, int, int, int, int64_t);
+template slab_status dense_tall_cholesky<double>(slab_handle*, double*, int, int, int, int64_t);

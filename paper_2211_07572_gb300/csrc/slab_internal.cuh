@@ -35,8 +35,10 @@ bool slab_debug();
 unsigned slab_debug_status(slab_handle* h, const char* where, int a, int b);
 
 struct TreeDims {
-    int s;        // rows per slab (= interface size in 2-D)
-    int s_pad;    // s rounded up to SLAB_TILE
+    int s;        // rows per slab, n - 1 (= interface size in 2-D)
+    int si;       // interface unknowns (n-1)^(d-1)
+    int64_t N;    // unknowns (n-1)^d
+    int s_pad;    // si rounded up to SLAB_TILE
     int m;        // slab interior width
     int H;        // tree heights 0..H-1
     int NS, NI;   // slabs, interfaces
@@ -68,6 +70,15 @@ struct slab_handle {
     double* AY;               // AY[y][x]: face (x,y)-(x,y+1)
     double* DG;               // DG[y][x]: diagonal of Ahat at (x,y)
     double* kappa;            // copy of the node coefficient (DIFFUSION), for the gradient
+    double* AZ;               // 3-D: AZ[z][y][x]: face (x,y,z)-(x,y,z+1)
+
+    // 3-D Stage 1 (tree3d.cu): per-node dense factors, node ids height-major (see Tree3Plan)
+    struct Tree3Plan* t3plan;
+    void *t3Lin, *t3LT;       // [node][Mp][Mp]  L^{-1}, L^{-T}
+    void *t3Ztb, *t3ZtbT;     // [node][Mp][2Mp] Z_tb = L^{-1} B_tb, and its transpose
+    void *t3ZIT, *t3ZI;       // per height [node][2 wsp][Mp] (Z_I)^T and [node][Mp][2 wsp] Z_I
+    void *t3Rtb, *t3RI, *t3W; // factor only: condensed R [node][2Mp][2Mp], RI [t][k][side][tb][Mp][s_pad], work
+    void *t3y, *t3G, *t3x, *t3Fi, *t3xI;   // solve workspace
 
     // Stage-1 factors (scalar = float or double)
     void* tLinv;              // [NS][s+1][m*m]   inverse Cholesky factor of each separator row
@@ -190,6 +201,31 @@ template <typename T> slab_status sweep_solve(slab_handle* h, int K);
 // odd-even elimination order of T (SPD kinds)
 int cr_max_batch(int NI);
 size_t gj_work_bytes(int s_pad, size_t rsz);
+// 3-D slabs
+struct Tree3Plan* tree3d_plan(int s, int m, int NS);
+void tree3d_plan_free(struct Tree3Plan* P);
+int64_t tree3d_nodes(const struct Tree3Plan* P);
+int tree3d_mpad(const struct Tree3Plan* P);
+int64_t tree3d_zit_elems(const struct Tree3Plan* P);
+int64_t tree3d_work_elems(const struct Tree3Plan* P);
+int64_t tree3d_xI_elems(const struct Tree3Plan* P);
+template <typename T> slab_status tree3d_factor(slab_handle* h);
+template <typename T> slab_status tree3d_up_gather(slab_handle* h, const double* F, double fscale, int r0, int K);
+template <typename T> slab_status tree3d_down_scatter(slab_handle* h, double* U, int accumulate, int r0, int K);
+template <typename T> slab_status tree3d_export(slab_handle* h, double* out, double scale, int r0, int K);
+template <typename T> slab_status tree3d_import(slab_handle* h, const double* in, int r0, int K);
+// dense building blocks (tensor-core products for FP32, SIMT for FP64); batch > 1 uses strides
+template <typename T>
+slab_status dense_gemm(slab_handle* h, int cls, int M, int N, int K, T alpha, const T* A, int64_t lda, int64_t sA,
+                       const T* B, int64_t ldb, int64_t sB, T beta, T* C, int64_t ldc, int64_t sC, int transC,
+                       int lower_only, int batch);
+template <typename T>
+slab_status dense_transpose(slab_handle* h, const T* in, int64_t ldin, int64_t sin, T* out, int64_t ldout,
+                            int64_t sout, int rows, int cols, int batch);
+template <typename T>
+slab_status dense_copy(slab_handle* h, const T* in, int64_t sin, T* out, int64_t sout, int64_t n, int batch);
+template <typename T>
+slab_status dense_tall_cholesky(slab_handle* h, T* W, int ncols, int ident0, int batch, int64_t bstride);
 slab_status widen_to_double(slab_handle* h, const float* src, double* dst, int64_t n);
 slab_status narrow_to_float(slab_handle* h, const double* src, float* dst, int64_t n);
 template <typename T> slab_status cr_factor(slab_handle* h);

@@ -182,6 +182,57 @@ __global__ void kappa_grad2d_kernel(int n, const double* __restrict__ u,
     g[(int64_t)y * (n + 1) + x] += acc;
 }
 
+// ---------------------------------------------------------------- three dimensions
+// Seven-point operator on the (n-1)^3 interior nodes, layout [z][y][x]; coefficient arrays over the
+// (n+1)^3 nodes: AX / AY / AZ the face toward +x / +y / +z, DG the diagonal, all h^2-scaled.
+__global__ void coeff3_kernel(int n, int kind, const double* __restrict__ kappa, double* AX, double* AY, double* AZ,
+                              double* DG) {
+    const int np1 = n + 1;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y, z = blockIdx.z;
+    if (x > n) return;
+    const int64_t P = ((int64_t)z * np1 + y) * np1 + x;
+    const int64_t sy = np1, sz = (int64_t)np1 * np1;
+    auto face = [&](int64_t a, int64_t b2) -> double {
+        return kind == SLAB_DIFFUSION ? 0.5 * (kappa[a] + kappa[b2]) : 1.0;
+    };
+    AX[P] = x < n ? face(P, P + 1) : 0.0;
+    AY[P] = y < n ? face(P, P + sy) : 0.0;
+    AZ[P] = z < n ? face(P, P + sz) : 0.0;
+    double d = 0.0;
+    if (x >= 1 && x < n && y >= 1 && y < n && z >= 1 && z < n)
+        d = face(P, P - 1) + face(P, P + 1) + face(P, P - sy) + face(P, P + sy) + face(P, P - sz) + face(P, P + sz);
+    DG[P] = d;
+}
+
+// r = f - A u (RESID) or y = A u for k vectors; one thread per x, blockIdx.y = y, blockIdx.z = (z, rhs)
+template <bool RESID>
+__global__ void __launch_bounds__(128) stencil3d_kernel(int n, int k, const double* __restrict__ AX,
+                                                        const double* __restrict__ AY, const double* __restrict__ AZ,
+                                                        const double* __restrict__ DG, const double* __restrict__ u,
+                                                        const double* __restrict__ f, double* r) {
+    const int s = n - 1, np1 = n + 1;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x + 1;
+    const int y = blockIdx.y + 1;
+    const int z = blockIdx.z % s + 1, q = blockIdx.z / s;
+    if (x > s || q >= k) return;
+    const double n2 = (double)n * (double)n;
+    const int64_t N = (int64_t)s * s * s;
+    const int64_t P = ((int64_t)z * np1 + y) * np1 + x;
+    const int64_t o = ((int64_t)(z - 1) * s + (y - 1)) * s + (x - 1);
+    const double* uq = u + (int64_t)q * N;
+    double Au = DG[P] * uq[o];
+    if (x > 1) Au -= AX[P - 1] * uq[o - 1];
+    if (x < s) Au -= AX[P] * uq[o + 1];
+    if (y > 1) Au -= AY[P - np1] * uq[o - s];
+    if (y < s) Au -= AY[P] * uq[o + s];
+    if (z > 1) Au -= AZ[P - (int64_t)np1 * np1] * uq[o - (int64_t)s * s];
+    if (z < s) Au -= AZ[P] * uq[o + (int64_t)s * s];
+    Au *= n2;
+    if (RESID) r[(int64_t)q * N + o] = f[(int64_t)q * N + o] - Au;
+    else r[(int64_t)q * N + o] = Au;
+}
+
 // ---------------------------------------------------------------- FP64 vector kernels (Krylov)
 // Batched over k vectors of length N, vector q at x + q * N.  Dot products are reduced in a
 // fixed order (per-block partials, then one block per vector), so they are deterministic.
@@ -256,6 +307,13 @@ __global__ void vcombine_kernel(double* u, const double* __restrict__ Z, int64_t
 
 slab_status launch_coefficients(slab_handle* h, const double* kappa, const double* c) {
     const int n = h->n;
+    if (h->dim == 3) {
+        SLAB_PROF(h, KC_COEFF);
+        coeff3_kernel<<<dim3((n + 1 + 127) / 128, n + 1, n + 1), 128, 0, h->stream>>>(n, h->kind, kappa, h->AX, h->AY,
+                                                                                    h->AZ, h->DG);
+        SLAB_CK_LAUNCH(h);
+        return SLAB_OK;
+    }
     dim3 grid((n + 1 + 127) / 128, n + 1);
     SLAB_PROF(h, KC_COEFF);
     coeff_kernel<<<grid, 128, 0, h->stream>>>(n, h->kind, kappa, c, h->omega, h->AX, h->AY, h->DG);
@@ -267,6 +325,26 @@ slab_status launch_residual(slab_handle* h, const double* u, const double* f, do
                             double* nrm_r, double* nrm_f) {
     const int n = h->n, s = n - 1;
     if (k <= 0) return SLAB_OK;
+    if (h->dim == 3) {
+        {
+            SLAB_PROF(h, KC_STENCIL);
+            stencil3d_kernel<true><<<dim3((s + 127) / 128, s, s * k), 128, 0, h->stream>>>(n, k, h->AX, h->AY, h->AZ,
+                                                                                           h->DG, u, f, r);
+            SLAB_CK_LAUNCH(h);
+        }
+        if (!nrm_r) return SLAB_OK;
+        const size_t need = vec_dot_part_elems(k);
+        if (h->red_cap < need) {
+            if (h->red_part) cudaFree(h->red_part);
+            h->red_part = nullptr; h->red_cap = 0;
+            SLAB_CK(h, cudaMalloc((void**)&h->red_part, need * sizeof(double)));
+            h->red_cap = need;
+        }
+        const int64_t N = (int64_t)s * s * s;
+        slab_status st = vec_dot(h, r, r, N, k, h->red_part, nrm_r);
+        if (!st && nrm_f) st = vec_dot(h, f, f, N, k, h->red_part, nrm_f);
+        return st;
+    }
     dim3 grid((s + 255) / 256, (s + ST_ROWS - 1) / ST_ROWS, (k + ST_Q - 1) / ST_Q);
     double* part = nullptr;
     unsigned* tickets = nullptr;
@@ -293,6 +371,13 @@ slab_status launch_residual(slab_handle* h, const double* u, const double* f, do
 slab_status launch_apply(slab_handle* h, const double* x, double* y, int k) {
     const int n = h->n, s = n - 1;
     if (k <= 0) return SLAB_OK;
+    if (h->dim == 3) {
+        SLAB_PROF(h, KC_STENCIL);
+        stencil3d_kernel<false><<<dim3((s + 127) / 128, s, s * k), 128, 0, h->stream>>>(n, k, h->AX, h->AY, h->AZ,
+                                                                                        h->DG, x, nullptr, y);
+        SLAB_CK_LAUNCH(h);
+        return SLAB_OK;
+    }
     dim3 grid((s + 255) / 256, (s + ST_ROWS - 1) / ST_ROWS, (k + ST_Q - 1) / ST_Q);
     SLAB_PROF(h, KC_STENCIL);
     stencil2d_kernel<false><<<grid, 256, 0, h->stream>>>(n, k, h->AX, h->AY, h->DG, x, nullptr, y, nullptr,
