@@ -28,6 +28,9 @@ METRIC = "factor+solve s at 1e-10 rel. residual vs plain FP64 GPU; dense TFLOP/s
 WORKLOAD = dict(workload="2D var-coef diffusion n=2048 b=32 k=64 (kappa=exp(16-mode field), f~N(0,1)), "
                          "FP32 factor + FP64 refinement to 1e-10",
                 n=2048, b=32, k=64, rtol=1e-10, kind="diffusion")
+DIFFUSION3D = dict(workload="3D var-coef diffusion n=96 b=8 k=16 (kappa=exp(8-mode 3-D field), f~N(0,1)), "
+                            "FP32 factor + FP64 refinement to 1e-10",
+                   n=96, b=8, k=16, rtol=1e-10, kind="diffusion3d")
 HELMHOLTZ = dict(workload="2D Helmholtz n=4096 b=32 k=1 (c=1+0.3 r, 8-mode field, 10 points per wavelength, "
                           "point source), FP32 pivoted factor + FP64 refinement to 1e-10",
                  n=4096, b=32, k=1, rtol=1e-10, kind="helmholtz")
@@ -118,11 +121,70 @@ def oddeven_levels(NI):
     return out
 
 
+def work_model_3d(n, b, k, passes, stage2):
+    """Algorithmic flops per kernel class for the 3-D path (dense per-node tree along z)."""
+    s = n - 1
+    m = b - 1
+    M = m * s
+    Mp = (M + 63) // 64 * 64
+    si = s * s
+    sp = (si + 63) // 64 * 64
+    NS, NI = n // b, n // b - 1
+    W = {k_: 0.0 for k_ in ("tree_factor", "assemble_T", "panel", "trailing", "schur_update", "sweep_products",
+                            "tree_up", "tree_down", "stencil")}
+    for (c, kk, w) in tree_nodes(s):
+        wl = w * s
+        wmax = min(s, (1 << (kk + 1)) - 1)
+        wsp = (wmax * s + 63) // 64 * 64
+        ident0 = 3 * Mp + 2 * wsp
+        for kb in range(Mp // 64):                     # batched tall Cholesky of [S; B^T; I]
+            rows = ident0 + (kb + 1) * 64
+            W["panel"] += NS * (rows // 64 - kb - 1) * (2 * 64 ** 3 + 2 * 64 ** 3 / 3)
+            c0 = (kb + 1) * 64
+            if c0 < Mp:
+                nn = Mp - c0
+                W["trailing"] += NS * 2 * 64 * (nn * (nn + 1) / 2 + (rows - Mp) * nn)
+        W["schur_update"] += NS * (2.0 * (2 * Mp) ** 2 * Mp + 2 * 2.0 * 2 * Mp * wl * Mp)
+        W["assemble_T"] += NS * 3 * 2.0 * wl * wl * Mp
+        W["tree_up"] += passes * NS * k * (2.0 * Mp * Mp + 2.0 * 2 * Mp * Mp + 2.0 * 2 * wsp * Mp)
+        W["tree_down"] += passes * NS * k * (2.0 * Mp * 2 * Mp + 2.0 * Mp * 2 * wsp + 2.0 * Mp * Mp)
+    W2 = work_model_stage2(sp, NI, k, passes, stage2)
+    for key in ("panel", "trailing", "schur_update", "sweep_products"):
+        W[key] += W2[key]
+    W["stencil"] = passes * 24.0 * s ** 3 * k
+    return W
+
+
+def work_model_stage2(sp, NI, k, passes, stage2):
+    """Stage-2 (SPD) flops: tall Cholesky panels and trailing updates, Schur updates, solve products."""
+    W = {"panel": 0.0, "trailing": 0.0}
+    for j in range(NI):
+        lt0 = sp if stage2 == "oddeven" else (2 if j < NI - 1 else 1) * sp
+        for kb in range(sp // 64):
+            rows = lt0 + (kb + 1) * 64
+            W["panel"] += (rows // 64 - kb - 1) * (2 * 64 ** 3 + 2 * 64 ** 3 / 3)
+            c0 = (kb + 1) * 64
+            if c0 < sp:
+                nn = sp - c0
+                W["trailing"] += 2 * 64 * (nn * (nn + 1) / 2 + (rows - sp) * nn)
+    if stage2 == "oddeven":
+        lv = oddeven_levels(NI)
+        nb, nc = sum(x for x, _ in lv), sum(y for _, y in lv)
+        W["schur_update"] = nb * (2.0 * sp ** 3 + sp * sp * (sp + 1.0)) + nc * (4.0 * sp ** 3 + sp * sp * (sp + 1.0))
+        W["sweep_products"] = passes * (4 * nb + 2 * nc + 2) * 2.0 * sp * sp * k
+    else:
+        W["schur_update"] = (NI - 1) * sp * sp * (sp + 1.0)
+        W["sweep_products"] = passes * (4 * NI - 2) * 2.0 * sp * sp * k
+    return W
+
+
 def work_model(n, b, k, passes, stage2="sweep", kind="diffusion"):
     """Algorithmic flops (or bytes) per kernel class for one factor + `passes` solve passes.
 
     Explicit inverse factors (L^{-1}, L^{-T}) are stored and applied as dense blocks, so
     their products count as dense (2 s^3 per s x s x s product; s(s+1)s for a lower-half update)."""
+    if kind == "diffusion3d":
+        return work_model_3d(n, b, k, passes, stage2)
     s = n - 1
     sp = (s + 63) // 64 * 64
     m = b - 1
@@ -188,8 +250,11 @@ BOUND = {"tree_factor": "alu", "assemble_T": "hbm", "panel": "alu", "trailing": 
          "stencil": "hbm"}
 
 
-def roofline_for(cls, ms, count, work, peaks, clocks):
-    bound = BOUND.get(cls, "alu")
+BOUND3 = dict(BOUND, assemble_T="tensor", tree_up="tensor", tree_down="tensor")
+
+
+def roofline_for(cls, ms, count, work, peaks, clocks, bounds=None):
+    bound = (bounds or BOUND).get(cls, "alu")
     t = ms * 1e-3
     if bound == "hbm":
         achieved = work[cls] / t / 1e9
@@ -218,8 +283,9 @@ def run_gpu(args):
     from paper_2211_07572_gb300 import inputs
     from paper_2211_07572_gb300.solver import SlabSolver
 
-    W = dict(HELMHOLTZ if args.workload == "helmholtz4096" else WORKLOAD)
+    W = dict({"helmholtz4096": HELMHOLTZ, "diffusion3d96": DIFFUSION3D}.get(args.workload, WORKLOAD))
     helm = W["kind"] == "helmholtz"
+    dim = 3 if W["kind"] == "diffusion3d" else 2
     if args.n:
         W.update(n=args.n, b=args.b or W["b"], k=args.k or W["k"])
         W["workload"] = (f"2D Helmholtz n={W['n']} b={W['b']} point source" if helm else
@@ -231,6 +297,10 @@ def run_gpu(args):
         p = inputs.helmholtz(n, b, dim=2, n_modes=8, field_seed=3)
         coeff = dict(kind=inputs.HELMHOLTZ, c=torch.from_numpy(p.c).to(dev), omega=p.omega)
         f_host = torch.from_numpy(np.ascontiguousarray(p.f[:k])).pin_memory()
+    elif dim == 3:
+        p = inputs.diffusion(n, b, k=0, dim=3, n_modes=8, field_seed=4, rhs_seed=104)
+        coeff = dict(kind=inputs.DIFFUSION, kappa=torch.from_numpy(p.kappa).to(dev))
+        f_host = torch.from_numpy(inputs.normal_rhs(3, n, k, 104)).pin_memory()
     else:
         p = inputs.diffusion(n, b, k=0, n_modes=16, field_seed=2, rhs_seed=102)
         coeff = dict(kind=inputs.DIFFUSION, kappa=torch.from_numpy(p.kappa).to(dev))
@@ -250,10 +320,12 @@ def run_gpu(args):
     def solver(precision, **kw):
         kk = dict(coeff)
         kind = kk.pop("kind")
-        return SlabSolver(2, n, b, kind, precision=precision, stream=stream, device=dev, **kk, **kw)
+        return SlabSolver(dim, n, b, kind, precision=precision, stream=stream, device=dev, **kk, **kw)
+
+    W["krylov"] = args.krylov
 
     def make():
-        return solver(prec, rtol=W["rtol"], max_refine=40, stage2=stage2)
+        return solver(prec, rtol=W["rtol"], max_refine=40, stage2=stage2, krylov=args.krylov)
 
     def step(f_in, u_out, counts=None):
         s = make()
@@ -304,7 +376,7 @@ def run_gpu(args):
     t_fac = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     t_f0.record(stream)
-    s = solver(prec, rtol=W["rtol"], max_refine=40, profile=True, stage2=stage2)
+    s = solver(prec, rtol=W["rtol"], max_refine=40, profile=True, stage2=stage2, krylov=args.krylov)
     t_fac.record(stream)
     _, rel1, it1 = s.solve(f, u, allow_noconv=True)
     t_end.record(stream)
@@ -316,10 +388,12 @@ def run_gpu(args):
     passes = it1 + 1
     work = work_model(n, b, k, passes, stage2, W["kind"])
     peaks = _peaks()
-    dom = max((c for c in cls_ms if c in BOUND), key=lambda c: cls_ms[c])
-    roof = roofline_for(dom, cls_ms[dom], cls_cnt[dom], work, peaks, clocks)
-    dense = {c: roofline_for(c, cls_ms[c], cls_cnt[c], work, peaks, clocks)
-             for c in ("trailing", "schur_update", "sweep_products") if cls_ms.get(c, 0) > 0}
+    bmap = BOUND3 if dim == 3 else BOUND
+    dom = max((c for c in cls_ms if c in bmap and work.get(c, 0) > 0), key=lambda c: cls_ms[c])
+    roof = roofline_for(dom, cls_ms[dom], cls_cnt[dom], work, peaks, clocks, bmap)
+    dense_cls = ("trailing", "schur_update", "sweep_products") + (("assemble_T", "tree_up", "tree_down") if dim == 3 else ())
+    dense = {c: roofline_for(c, cls_ms[c], cls_cnt[c], work, peaks, clocks, bmap)
+             for c in dense_cls if cls_ms.get(c, 0) > 0}
     line = {
         "metric": METRIC,
         "value": ms / 1e3,
@@ -350,7 +424,7 @@ def run_gpu(args):
         line["fp64_gpu"] = fp64_comparator(lambda: solver("fp64", rtol=1.0, max_refine=0), f)
         line["fp64_gpu"]["mixed_speedup"] = line["fp64_gpu"]["value"] / line["value"]
     if args.cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(n, b, k, kind=W["kind"], n_sample=256 if helm else 512)
+        line["cpu_baseline"] = cpu_baseline(n, b, k, kind=W["kind"], n_sample=256 if helm else (32 if dim == 3 else 512))
     print(json.dumps(line))
 
 
@@ -388,22 +462,27 @@ def cpu_baseline(n_full, b, k, n_sample=512, kind="diffusion"):
     import oracle
     from paper_2211_07572_gb300 import inputs
     oracle.build()
+    dim = 3 if kind == "diffusion3d" else 2
     if kind == "helmholtz":
         p = inputs.helmholtz(n_sample, b, dim=2, n_modes=8, field_seed=3)
+    elif dim == 3:
+        p = inputs.diffusion(n_sample, b, k=k, dim=3, n_modes=8, field_seed=4, rhs_seed=104)
     else:
         p = inputs.diffusion(n_sample, b, k=k, n_modes=16, field_seed=2, rhs_seed=102)
     t0 = time.perf_counter()
     A = oracle.assemble_problem(p)
-    lu = oracle.BandLU(A, n_sample - 1, pivot=kind == "helmholtz")
+    lu = oracle.BandLU(A, (n_sample - 1) ** (dim - 1), pivot=kind == "helmholtz")
     t1 = time.perf_counter()
     u = lu.solve(p.f)
     t2 = time.perf_counter()
     rr = float(oracle.relres(A, u, p.f).max())
     scale = (n_full / n_sample)
-    est = (t1 - t0) * scale ** 4 + (t2 - t1) * scale ** 3
+    # banded LU: factor ~ N w^2, solve ~ k N w (N = n^d, w = n^(d-1))
+    est = (t1 - t0) * scale ** (3 * dim - 2) + (t2 - t1) * scale ** (2 * dim - 1)
     return {"value": est, "unit": "s", "cores": oracle.threads(), "kind": "oracle",
             "sample": f"banded LU FP64 at n={n_sample} (b={b}, k={k}): factor {t1 - t0:.2f} s, "
-                      f"solve {t2 - t1:.2f} s, relres {rr:.1e}; extrapolated to n={n_full} by n^4 / k n^3"}
+                      f"solve {t2 - t1:.2f} s, relres {rr:.1e}; extrapolated to n={n_full} by n^{3 * dim - 2} / "
+                      f"k n^{2 * dim - 1}"}
 
 
 def run_reference(args):
@@ -442,8 +521,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-fp64", dest="fp64_comparator", action="store_false")
     ap.add_argument("--once", action="store_true", help="run one step only (for profilers)")
-    ap.add_argument("--workload", default="diffusion2048", choices=["diffusion2048", "helmholtz4096"],
-                    help="diffusion2048: the default bench line; helmholtz4096: the indefinite workload")
+    ap.add_argument("--workload", default="diffusion2048", choices=["diffusion2048", "helmholtz4096", "diffusion3d96"],
+                    help="diffusion2048: the default bench line; helmholtz4096, diffusion3d96: the other workloads")
+    ap.add_argument("--krylov", type=int, default=0, help="0: plain refinement; m: FP64 GMRES(m) refinement")
     ap.add_argument("--stage2", default="auto", choices=["auto", "sweep", "oddeven"],
                     help="elimination order of T (auto: odd-even for 4 or more interfaces)")
     args = ap.parse_args()
