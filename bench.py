@@ -239,14 +239,17 @@ def work_model(n, b, k, passes, stage2="sweep", kind="diffusion"):
     else:
         W["schur_update"] = (NI - 1) * sp * sp * (sp + 1.0)
         W["sweep_products"] = passes * (4 * NI - 2) * 2.0 * sp * sp * k
-    W["tree_up"] = passes * NS * k * sum(2 * (m * (m + 1) / 2 + 2 * m * m + 2 * w * m) for (_, _, w) in nodes)
-    W["tree_down"] = passes * NS * k * sum(2 * (2 * m * m + 2 * w * m + m * (m + 1) / 2) for (_, _, w) in nodes)
+    # tree passes: algorithmic HBM bytes per node (factor blocks once, vectors once, FP64 f read / u update)
+    W["tree_up"] = passes * NS * sum(4 * 3 * m * m + 8 * m * k + (8 * m * k if kk > 0 else 0) + 4 * 2 * w * m
+                                     + 16 * w * k + 4 * m * k + 8 * m * k for (_, kk, w) in nodes)
+    W["tree_down"] = passes * NS * sum(4 * 3 * m * m + 4 * m * k + 8 * m * k + 8 * w * m + 8 * w * k + 4 * m * k
+                                       + 16 * m * k for (_, _, w) in nodes)
     W["stencil"] = passes * 24.0 * s * s * k                            # bytes: read u, f; write r (FP64)
     return W
 
 
 BOUND = {"tree_factor": "alu", "assemble_T": "hbm", "panel": "alu", "trailing": "tensor",
-         "schur_update": "tensor", "sweep_products": "tensor", "tree_up": "alu", "tree_down": "alu",
+         "schur_update": "tensor", "sweep_products": "tensor", "tree_up": "hbm", "tree_down": "hbm",
          "stencil": "hbm"}
 
 

@@ -701,11 +701,13 @@ slab_status slab_solve(slab_handle* h, const double* f, double* u, int k, double
         std::vector<double> nrm(2 * (size_t)k);
         double prev = -1.0;
         int stall = 0;
+        bool have_f = false;                        // ||f||^2 is computed with the first residual only
         for (;;) {
-            SLAB_CK(h, cudaMemsetAsync(h->wNrm, 0, 2 * k * sizeof(double), h->stream));
-            TRY(launch_residual(h, u, f, h->wR, k, h->wNrm, h->wNrm + k));
-            SLAB_CK(h, cudaMemcpyAsync(nrm.data(), h->wNrm, 2 * k * sizeof(double), cudaMemcpyDeviceToHost,
-                                       h->stream));
+            SLAB_CK(h, cudaMemsetAsync(h->wNrm, 0, (have_f ? 1 : 2) * k * sizeof(double), h->stream));
+            TRY(launch_residual(h, u, f, h->wR, k, h->wNrm, have_f ? nullptr : h->wNrm + k));
+            SLAB_CK(h, cudaMemcpyAsync(nrm.data(), h->wNrm, (have_f ? 1 : 2) * k * sizeof(double),
+                                       cudaMemcpyDeviceToHost, h->stream));
+            have_f = true;
             SLAB_CK(h, cudaStreamSynchronize(h->stream));
             double worst = 0.0;
             bool finite = true;

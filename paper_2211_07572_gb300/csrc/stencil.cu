@@ -40,7 +40,7 @@ __global__ void coeff_kernel(int n, int kind, const double* __restrict__ kappa,
 // block of a group (ticket counter) adds the partials in block order, so the sums are deterministic.
 constexpr int ST_ROWS = 16;
 constexpr int ST_Q = 8;
-template <bool RESID>
+template <bool RESID, bool NORMF>
 __global__ void __launch_bounds__(256) stencil2d_kernel(int n, int k, const double* __restrict__ AX,
                                                         const double* __restrict__ AY,
                                                         const double* __restrict__ DG,
@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(256) stencil2d_kernel(int n, int k, const doub
                         const double rv = fv - Au;
                         r[(q0 + q) * N + o] = rv;
                         rr2[q] += rv * rv;
-                        ff2[q] += fv * fv;
+                        if (NORMF) ff2[q] += fv * fv;
                     } else {
                         r[(q0 + q) * N + o] = Au;
                     }
@@ -362,8 +362,12 @@ slab_status launch_residual(slab_handle* h, const double* u, const double* f, do
         part = h->red_part; tickets = h->red_tickets;
     }
     SLAB_PROF(h, KC_STENCIL);
-    stencil2d_kernel<true><<<grid, 256, 0, h->stream>>>(n, k, h->AX, h->AY, h->DG, u, f, r, nrm_r, nrm_f,
-                                                        part, tickets);
+    if (nrm_f)
+        stencil2d_kernel<true, true><<<grid, 256, 0, h->stream>>>(n, k, h->AX, h->AY, h->DG, u, f, r, nrm_r, nrm_f,
+                                                                  part, tickets);
+    else
+        stencil2d_kernel<true, false><<<grid, 256, 0, h->stream>>>(n, k, h->AX, h->AY, h->DG, u, f, r, nrm_r,
+                                                                   nullptr, part, tickets);
     SLAB_CK_LAUNCH(h);
     return SLAB_OK;
 }
@@ -380,8 +384,8 @@ slab_status launch_apply(slab_handle* h, const double* x, double* y, int k) {
     }
     dim3 grid((s + 255) / 256, (s + ST_ROWS - 1) / ST_ROWS, (k + ST_Q - 1) / ST_Q);
     SLAB_PROF(h, KC_STENCIL);
-    stencil2d_kernel<false><<<grid, 256, 0, h->stream>>>(n, k, h->AX, h->AY, h->DG, x, nullptr, y, nullptr,
-                                                         nullptr, nullptr, nullptr);
+    stencil2d_kernel<false, false><<<grid, 256, 0, h->stream>>>(n, k, h->AX, h->AY, h->DG, x, nullptr, y, nullptr,
+                                                                nullptr, nullptr, nullptr);
     SLAB_CK_LAUNCH(h);
     return SLAB_OK;
 }

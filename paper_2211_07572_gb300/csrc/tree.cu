@@ -344,6 +344,18 @@ struct SolveArgs {
 };
 
 constexpr int KMAX = 64;   // right-hand sides handled per launch
+constexpr int LP = 36;     // smem row stride of the 32-row blocks read 4 at a time (16-byte aligned)
+
+// four consecutive smem values (16-byte aligned): one 128-bit load for float, two for double
+__device__ inline void lds4(const float* p, float v[4]) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ inline void lds4(const double* p, double v[4]) {
+    const double2 a = *reinterpret_cast<const double2*>(p);
+    const double2 b = *reinterpret_cast<const double2*>(p + 2);
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
 
 // Up pass of one height: y = Li (f_c + G_alpha[bot] + G_beta[top]); condensed top/bot load;
 // interface load Fi -= Z_I^T y.  grid = (node, chunk, slab).  The m x K products use 4 x 4
@@ -354,6 +366,9 @@ __global__ void __launch_bounds__(TB_THREADS) tree_up_kernel(SolveArgs<T> P, int
     __shared__ __align__(16) T Li[MAXM * SP];
     __shared__ __align__(16) T Zt[MAXM * SP2];
     __shared__ __align__(16) T y[MAXM * KMAX];
+    // 32 interface columns of Z_I, staged per pass; Zt is no longer read by then
+    T* const zs = Zt;
+    static_assert(SP2 >= LP, "staging area must fit in Zt");
     const TreeArgs<T>& A = P.tr;
     const int tid = threadIdx.x, nth = blockDim.x;
     const int tA = tid >> 4, tB = tid & 15;
@@ -374,14 +389,19 @@ __global__ void __launch_bounds__(TB_THREADS) tree_up_kernel(SolveArgs<T> P, int
     const int m2 = 2 * m;
     const T* Lg = A.linv(t, c);
     const T* Zg = A.ztb(t, c);
-    for (int idx = tid; idx < m * m; idx += nth) Li[(idx / m) * SP + idx % m] = Lg[idx];
-    for (int idx = tid; idx < m * m2; idx += nth) Zt[(idx / m2) * SP2 + idx % m2] = Zg[idx];
+    // rows of Li / Zt by warp (4 warps), columns by lane: no runtime division
+    for (int i = tid >> 5; i < m; i += nth >> 5) {
+        const int j = tid & 31;
+        if (j < m) Li[i * SP + j] = Lg[i * m + j];
+        if (j < m2) Zt[i * SP2 + j] = Zg[i * m2 + j];
+        if (j + 32 < m2) Zt[i * SP2 + j + 32] = Zg[i * m2 + j + 32];
+    }
     const int64_t N = (int64_t)s * s;
     for (int idx = tid; idx < MAXM * KMAX; idx += nth) {
         const int r = idx / MAXM, i = idx % MAXM;      // consecutive threads read consecutive x
         T g = T(0);
         if (i < m && r < K) {
-            g = (T)(fscale * F[(int64_t)(r0 + r) * N + (int64_t)(c - 1) * s + (x0 - 1 + i)]);
+            g = (T)F[(int64_t)(r0 + r) * N + (int64_t)(c - 1) * s + (x0 - 1 + i)] * (T)fscale;
             if (alpha) g += P.gtb(t, alpha, 1)[i * kc + r];
             if (beta) g += P.gtb(t, beta, 0)[i * kc + r];
         }
@@ -397,8 +417,7 @@ __global__ void __launch_bounds__(TB_THREADS) tree_up_kernel(SolveArgs<T> P, int
             for (int p = 0; p < 4; ++p) acc[q][p] = T(0);
         for (int l = 0; l < m; ++l) {
             T gv[4], lv[4];
-#pragma unroll
-            for (int p = 0; p < 4; ++p) gv[p] = y[l * KMAX + 4 * tB + p];
+            lds4(y + l * KMAX + 4 * tB, gv);
 #pragma unroll
             for (int q = 0; q < 4; ++q) lv[q] = (4 * tA + q < m) ? Li[(4 * tA + q) * SP + l] : T(0);
 #pragma unroll
@@ -415,7 +434,10 @@ __global__ void __launch_bounds__(TB_THREADS) tree_up_kernel(SolveArgs<T> P, int
     __syncthreads();
     if (blockIdx.y == 0) {
         T* yd = P.yv(t, c);
-        for (int idx = tid; idx < m * K; idx += nth) yd[(idx / K) * kc + idx % K] = y[(idx / K) * KMAX + idx % K];
+        for (int i = tid >> 6; i < m; i += nth >> 6) {
+            const int r = tid & 63;
+            if (r < K) yd[i * kc + r] = y[i * KMAX + r];
+        }
         // condensed top / bottom loads: G_tb[a][r] = G_child[a][r] - sum_i Z[i][tb*m + a] y[i][r]
         for (int tb = 0; tb < 2; ++tb) {
             const int child = tb == 0 ? alpha : beta;
@@ -426,8 +448,7 @@ __global__ void __launch_bounds__(TB_THREADS) tree_up_kernel(SolveArgs<T> P, int
                 for (int p = 0; p < 4; ++p) acc[q][p] = T(0);
             for (int i = 0; i < m; ++i) {
                 T yv[4], zv[4];
-#pragma unroll
-                for (int p = 0; p < 4; ++p) yv[p] = y[i * KMAX + 4 * tB + p];
+                lds4(y + i * KMAX + 4 * tB, yv);
 #pragma unroll
                 for (int q = 0; q < 4; ++q) zv[q] = (4 * tA + q < m) ? Zt[i * SP2 + tb * m + 4 * tA + q] : T(0);
 #pragma unroll
@@ -449,8 +470,34 @@ __global__ void __launch_bounds__(TB_THREADS) tree_up_kernel(SolveArgs<T> P, int
             }
         }
     }
-    // interface load: Fi[side][rr][r] -= sum_i Z_I[i][rr] y[i][r], 32 columns per pass
+    // interface load: Fi[side][rr][r] -= sum_i Z_I[i][rr] y[i][r]
     const int qend = min(ncols, q0 + TB_THREADS);
+    if (qend - q0 <= 16) {
+        // few columns (low heights): thread = (column, group of RB right-hand sides)
+        const int nq = qend - q0;
+        const int RB = nq <= 2 ? 1 : (nq <= 4 ? 2 : (nq <= 8 ? 4 : 8));
+        const int groups = KMAX / RB;
+        const int qq = tid / groups, r0b = (tid % groups) * RB;
+        if (qq < nq && r0b < K) {
+            const int col = q0 + qq;
+            const int sd = col / w, rr = lo + col % w - 1;
+            const T* zcol = A.zi(t, k, sd) + rr;
+            T acc[8];
+#pragma unroll
+            for (int p = 0; p < 8; ++p) acc[p] = T(0);
+            for (int i = 0; i < m; ++i) {
+                const T z = zcol[(int64_t)i * A.s_pad];
+#pragma unroll
+                for (int p = 0; p < 8; ++p)
+                    if (p < RB) acc[p] += z * y[i * KMAX + r0b + p];
+            }
+            T* fo = P.fi(t, sd) + (int64_t)rr * kc;
+#pragma unroll
+            for (int p = 0; p < 8; ++p)
+                if (p < RB && r0b + p < K) fo[r0b + p] -= acc[p];
+        }
+        return;
+    }
     for (int qa = q0; qa < qend; qa += 32) {
         int sd[4], rr[4];
         bool ok[4];
@@ -461,6 +508,18 @@ __global__ void __launch_bounds__(TB_THREADS) tree_up_kernel(SolveArgs<T> P, int
             sd[q] = ok[q] ? qq / w : 0;
             rr[q] = ok[q] ? lo + qq % w - 1 : 0;
         }
+        // stage Z_I[i][columns qa .. qa+31] (rows by warp, columns by lane: coalesced)
+        __syncthreads();
+        for (int i = tid >> 5; i < MAXM; i += nth >> 5) {
+            const int qq = qa + (tid & 31);
+            T z = T(0);
+            if (i < m && qq < qend) {
+                const int sdq = qq >= w, rq = lo + (sdq ? qq - w : qq) - 1;
+                z = A.zi(t, k, sdq)[(int64_t)i * A.s_pad + rq];
+            }
+            zs[i * LP + (tid & 31)] = z;
+        }
+        __syncthreads();
         T acc[4][4];
 #pragma unroll
         for (int q = 0; q < 4; ++q)
@@ -468,10 +527,8 @@ __global__ void __launch_bounds__(TB_THREADS) tree_up_kernel(SolveArgs<T> P, int
             for (int p = 0; p < 4; ++p) acc[q][p] = T(0);
         for (int i = 0; i < m; ++i) {
             T yv[4], zv[4];
-#pragma unroll
-            for (int p = 0; p < 4; ++p) yv[p] = y[i * KMAX + 4 * tB + p];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) zv[q] = ok[q] ? A.zi(t, k, sd[q])[(int64_t)i * A.s_pad + rr[q]] : T(0);
+            lds4(y + i * KMAX + 4 * tB, yv);
+            lds4(zs + i * LP + 4 * tA, zv);
 #pragma unroll
             for (int q = 0; q < 4; ++q)
 #pragma unroll
@@ -493,15 +550,24 @@ __global__ void __launch_bounds__(TB_THREADS) tree_up_kernel(SolveArgs<T> P, int
 // CTA reduces its chunk (chunk 0 also the 2m top/bottom columns) into a partial V (m x K) held
 // in 4 x 4 register blocks.  Nodes with one chunk finish in place; otherwise the partials go to
 // ws and the last CTA of the node (ticket) adds them in chunk order and finishes the node.
-constexpr int DCW = 256;
+constexpr int DCW = 256;      // largest chunk; heights with few nodes use smaller chunks (down_chunk)
+constexpr int DCW_MIN = 32;
+
+// Interface columns per CTA of the down pass at a height with `nodes` nodes of 2 wmax columns:
+// enough CTAs to fill the GPU (about 4 per SM) without chunks narrower than DCW_MIN.
+inline int down_chunk(int nodes, int wmax) {
+    int c = DCW;
+    while (c > DCW_MIN && (int64_t)nodes * ((2 * wmax + c - 1) / c) < 4 * 152) c /= 2;
+    return c;
+}
 template <typename T, bool INDEF>
 __global__ void __launch_bounds__(TB_THREADS) tree_down_kernel(SolveArgs<T> P, int k, double* U,
                                                                int accumulate, int r0, T* ws,
-                                                               unsigned* tickets) {
+                                                               unsigned* tickets, int dcw) {
     constexpr int CJ = sizeof(T) == 8 ? 16 : 32;   // columns per smem stage
-    __shared__ __align__(16) T Li[MAXM * SP];
+    __shared__ __align__(16) T Li[MAXM * LP];          // Li[l][i], zero for i >= m
     __shared__ __align__(16) T V[MAXM * KMAX];
-    __shared__ __align__(16) T zc[MAXM * (CJ + 1)];
+    __shared__ __align__(16) T zc[CJ * LP];            // zc[jj][i]: column jj of the stage, rows i
     __shared__ __align__(16) T uc[CJ * KMAX];
     __shared__ bool last;
     const TreeArgs<T>& A = P.tr;
@@ -514,9 +580,9 @@ __global__ void __launch_bounds__(TB_THREADS) tree_down_kernel(SolveArgs<T> P, i
     const int lo = c - (1 << k) + 1;
     const int hi = min(s, c + (1 << k) - 1);
     const int w = hi - lo + 1;
-    const int nch = (2 * w + DCW - 1) / DCW;
+    const int nch = (2 * w + dcw - 1) / dcw;
     if ((int)blockIdx.y >= nch) return;
-    const int qa = blockIdx.y * DCW, qb = min(2 * w, qa + DCW);
+    const int qa = blockIdx.y * dcw, qb = min(2 * w, qa + dcw);
     const int x0 = t * A.b + 1;
     const int m2 = 2 * m;
     T acc[4][4];
@@ -527,56 +593,59 @@ __global__ void __launch_bounds__(TB_THREADS) tree_down_kernel(SolveArgs<T> P, i
     const T* Zg = INDEF ? A.wtb(t, c) : A.ztb(t, c);    // SPD: Z; indefinite: W = S^{-1} B
     const T* xt = (lo - 1 >= 1) ? P.xs(t, lo - 1) : nullptr;
     const T* xb = (hi + 1 <= s) ? P.xs(t, hi + 1) : nullptr;
-    for (int part = (blockIdx.y == 0 ? 0 : 1); part < 3; ++part) {
-        // part 0: top/bot columns; parts 1, 2: interface columns of the left / right side
-        int ca, cb;
-        const T* zsrc;
-        int64_t zld;
-        const T* usrc = nullptr;
-        if (part == 0) {
-            ca = 0; cb = m2; zsrc = Zg; zld = m2;
-        } else {
-            const int side = part - 1;
-            const int q = side == 0 ? t - 1 : t;
-            ca = max(qa, side * w); cb = min(qb, (side + 1) * w);
-            if (ca >= cb || q < 0 || q >= A.NS - 1) continue;
-            zsrc = (INDEF ? A.wi(t, k, side) : A.zi(t, k, side)) + (lo - 1) - side * w;   // column = q0 + jj
-            zld = A.s_pad;
-            usrc = P.xi(q) + ((lo - 1) - side * w);
-        }
-        for (int q0 = ca; q0 < cb; q0 += CJ) {
-            const int nj = min(CJ, cb - q0);
-            __syncthreads();
-            for (int idx = tid; idx < m * CJ; idx += nth) {
-                const int i = idx / CJ, jj = idx % CJ;
-                zc[i * (CJ + 1) + jj] = jj < nj ? zsrc[(int64_t)i * zld + q0 + jj] : T(0);
-            }
-            for (int idx = tid; idx < CJ * KMAX; idx += nth) {
-                const int jj = idx % CJ, r = idx / CJ;
-                T v = T(0);
-                if (jj < nj && r < K) {
-                    const int col = q0 + jj;
-                    if (part == 0) {
-                        const T* xv = col < m ? xt : xb;
-                        v = xv ? xv[(col % m) * kc + r] : T(0);
-                    } else {
-                        v = usrc[(int64_t)r * A.s_pad + col];
-                    }
+    // one list of columns: the 2m top/bot columns (chunk 0 only), then this chunk's interface
+    // columns of the left (ic < w) and right side; staged CJ at a time
+    const int ntb = blockIdx.y == 0 ? m2 : 0;
+    const int ntot = ntb + (qb - qa);
+    const T* ZIl = (t >= 1) ? (INDEF ? A.wi(t, k, 0) : A.zi(t, k, 0)) + (lo - 1) : nullptr;
+    const T* ZIr = (t < A.NS - 1) ? (INDEF ? A.wi(t, k, 1) : A.zi(t, k, 1)) + (lo - 1) : nullptr;
+    const T* Ul = (t >= 1) ? P.xi(t - 1) + (lo - 1) : nullptr;
+    const T* Ur = (t < A.NS - 1) ? P.xi(t) + (lo - 1) : nullptr;
+    for (int v0 = 0; v0 < ntot; v0 += CJ) {
+        const int nj = min(CJ, ntot - v0);
+        __syncthreads();
+        for (int idx = tid; idx < MAXM * CJ; idx += nth) {
+            const int i = idx / CJ, jj = idx % CJ;
+            const int col = v0 + jj;
+            T z = T(0);
+            if (jj < nj && i < m) {
+                if (col < ntb) {
+                    z = Zg[(int64_t)i * m2 + col];
+                } else {
+                    const int ic = qa + col - ntb;
+                    const bool right = ic >= w;
+                    const T* zs = right ? ZIr : ZIl;
+                    if (zs) z = zs[(int64_t)i * A.s_pad + (right ? ic - w : ic)];
                 }
-                uc[jj * KMAX + r] = v;
             }
-            __syncthreads();
-            for (int jj = 0; jj < nj; ++jj) {
-                T zv[4], uv[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) zv[q] = (4 * tA + q < m) ? zc[(4 * tA + q) * (CJ + 1) + jj] : T(0);
-#pragma unroll
-                for (int p = 0; p < 4; ++p) uv[p] = uc[jj * KMAX + 4 * tB + p];
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-#pragma unroll
-                    for (int p = 0; p < 4; ++p) acc[q][p] += zv[q] * uv[p];
+            zc[jj * LP + i] = z;
+        }
+        for (int idx = tid; idx < CJ * KMAX; idx += nth) {
+            const int jj = idx % CJ, r = idx / CJ;
+            const int col = v0 + jj;
+            T v = T(0);
+            if (jj < nj && r < K) {
+                if (col < ntb) {
+                    const T* xv = col < m ? xt : xb;
+                    if (xv) v = xv[(col < m ? col : col - m) * kc + r];
+                } else {
+                    const int ic = qa + col - ntb;
+                    const bool right = ic >= w;
+                    const T* us = right ? Ur : Ul;
+                    if (us) v = us[(int64_t)r * A.s_pad + (right ? ic - w : ic)];
+                }
             }
+            uc[jj * KMAX + r] = v;
+        }
+        __syncthreads();
+        for (int jj = 0; jj < nj; ++jj) {
+            T zv[4], uv[4];
+            lds4(zc + jj * LP + 4 * tA, zv);
+            lds4(uc + jj * KMAX + 4 * tB, uv);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int p = 0; p < 4; ++p) acc[q][p] += zv[q] * uv[p];
         }
     }
     __syncthreads();
@@ -606,12 +675,15 @@ __global__ void __launch_bounds__(TB_THREADS) tree_down_kernel(SolveArgs<T> P, i
     const T* yv = P.yv(t, c);
     if (!INDEF) {
         const T* Lg = A.linv(t, c);
-        for (int idx = tid; idx < m * m; idx += nth) Li[(idx / m) * SP + idx % m] = Lg[idx];
+        for (int i = tid >> 5; i < MAXM; i += nth >> 5) {
+            const int j = tid & 31;
+            Li[i * LP + j] = (i < m && j < m) ? Lg[i * m + j] : T(0);
+        }
     }
     __syncthreads();
-    for (int idx = tid; idx < m * K; idx += nth) {
-        const int i = idx / K, r = idx % K;
-        V[i * KMAX + r] = yv[i * kc + r] - V[i * KMAX + r];
+    for (int i = tid >> 6; i < m; i += nth >> 6) {          // r = lane pair index, no runtime division
+        const int r = tid & 63;
+        if (r < K) V[i * KMAX + r] = yv[i * kc + r] - V[i * KMAX + r];
     }
     __syncthreads();
     if (!INDEF) {
@@ -621,10 +693,8 @@ __global__ void __launch_bounds__(TB_THREADS) tree_down_kernel(SolveArgs<T> P, i
             for (int p = 0; p < 4; ++p) acc[q][p] = T(0);
         for (int l = 0; l < m; ++l) {                      // x[i] = sum_{l >= i} Li[l][i] V[l]
             T lv[4], vv[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) lv[q] = (4 * tA + q < m) ? Li[l * SP + 4 * tA + q] : T(0);
-#pragma unroll
-            for (int p = 0; p < 4; ++p) vv[p] = V[l * KMAX + 4 * tB + p];
+            lds4(Li + l * LP + 4 * tA, lv);
+            lds4(V + l * KMAX + 4 * tB, vv);
 #pragma unroll
             for (int q = 0; q < 4; ++q)
 #pragma unroll
@@ -639,16 +709,18 @@ __global__ void __launch_bounds__(TB_THREADS) tree_down_kernel(SolveArgs<T> P, i
     }
     T* xd = P.xs(t, c);
     const int64_t N = (int64_t)s * s;
-    for (int idx = tid; idx < m * K; idx += nth) {
-        const int i = idx / K, r = idx % K;
-        xd[i * kc + r] = V[i * KMAX + r];
+    for (int i = tid >> 6; i < m; i += nth >> 6) {
+        const int r = tid & 63;
+        if (r < K) xd[i * kc + r] = V[i * KMAX + r];
     }
-    for (int idx = tid; idx < m * K; idx += nth) {   // consecutive threads write consecutive x
-        const int r = idx / m, i = idx % m;
-        const double v = (double)V[i * KMAX + r];
-        double* up = U + (int64_t)(r0 + r) * N + (int64_t)(c - 1) * s + (x0 - 1 + i);
-        if (accumulate) *up += v;
-        else *up = v;
+    for (int r = tid >> 5; r < K; r += nth >> 5) {      // consecutive lanes write consecutive x
+        const int i = tid & 31;
+        if (i < m) {
+            const double v = (double)V[i * KMAX + r];
+            double* up = U + (int64_t)(r0 + r) * N + (int64_t)(c - 1) * s + (x0 - 1 + i);
+            if (accumulate) *up += v;
+            else *up = v;
+        }
     }
 }
 
@@ -788,14 +860,15 @@ slab_status tree_down_scatter(slab_handle* h, double* U, int accumulate, int r0,
         const int cnt = tree_nodes_at(d.s, k);
         if (!cnt) continue;
         const int wmax = min(d.s, (1 << (k + 1)) - 1);
-        dim3 grid(cnt, (2 * wmax + DCW - 1) / DCW, d.NS);
+        const int dcw = down_chunk(cnt * d.NS, wmax);
+        dim3 grid(cnt, (2 * wmax + dcw - 1) / dcw, d.NS);
         SLAB_PROF(h, KC_TREE_DOWN);
         if (h->kind == SLAB_HELMHOLTZ)
             tree_down_kernel<T, true><<<grid, TB_THREADS, 0, h->stream>>>(p, k, U, accumulate, r0, (T*)h->wVp,
-                                                                          (unsigned*)h->wVtk);
+                                                                          (unsigned*)h->wVtk, dcw);
         else
             tree_down_kernel<T, false><<<grid, TB_THREADS, 0, h->stream>>>(p, k, U, accumulate, r0, (T*)h->wVp,
-                                                                           (unsigned*)h->wVtk);
+                                                                           (unsigned*)h->wVtk, dcw);
         SLAB_CK_LAUNCH(h);
     }
     dim3 g2((unsigned)(((int64_t)d.s * K + 255) / 256), d.NI);
@@ -833,7 +906,7 @@ size_t tree_down_ws_elems(int s, int m, int NS) {
     const int H = tree_height_count(s);
     for (int k = 0; k < H; ++k) {
         const int wmax = min(s, (1 << (k + 1)) - 1);
-        const int nch = (2 * wmax + DCW - 1) / DCW;
+        const int nch = (2 * wmax + DCW_MIN - 1) / DCW_MIN;
         if (nch <= 1) continue;
         const size_t e = (size_t)NS * tree_nodes_at(s, k) * nch * MAXM * KMAX;
         if (e > best) best = e;
