@@ -54,3 +54,42 @@ def test_tc_gemm_plain_tf32(M, N, K):
 def test_tc_gemm_transposed_output():
     rel, rel32 = _run(200, 64, 128, 0.5, 2.0, split=1, trans_c=1)
     assert rel < max(16 * rel32, 1e-6), (rel, rel32)
+
+
+def test_tc_gemm_schur_shape_rate():
+    """The odd-even Schur update shape of the n = 2048 workload (2048^3, C -= A B^T) in 3xTF32:
+    sampled rows against FP64, and the event-timed rate reported for the record."""
+    from paper_2211_07572_gb300 import _lib
+    lib = _lib.load()
+    M = N = K = 2048
+    g = torch.Generator(device="cuda").manual_seed(5)
+    A = torch.randn(M, K, generator=g, device="cuda")
+    B = torch.randn(N, K, generator=g, device="cuda")
+    C = torch.randn(M, N, generator=g, device="cuda")
+    C0 = C.clone()
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def run():
+        st = lib.slab_tc_gemm(M, N, K, -1.0, ctypes.c_void_p(A.data_ptr()), K, ctypes.c_void_p(B.data_ptr()), K,
+                              1.0, ctypes.c_void_p(C.data_ptr()), N, 0, 1, ctypes.c_void_p(err.data_ptr()),
+                              ctypes.c_void_p(stream.cuda_stream))
+        assert st == 0
+
+    run()
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    rows = torch.arange(0, M, 97, device="cuda")
+    ref = C0[rows].double() - A[rows].double() @ B.double().T
+    ref32 = (C0[rows] - A[rows] @ B.T).double()
+    e = (C[rows].double() - ref).abs().max().item()
+    e32 = (ref32 - ref).abs().max().item()
+    assert e <= 16 * e32, (e, e32)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(5):
+        run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 5
+    print(f"tc_gemm 2048^3 3xTF32: {ms:.3f} ms, {2 * M * N * K / ms / 1e9:.1f} TFLOP/s algorithmic")
