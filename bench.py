@@ -254,6 +254,7 @@ BOUND = {"tree_factor": "alu", "assemble_T": "hbm", "panel": "alu", "trailing": 
 
 
 BOUND3 = dict(BOUND, assemble_T="tensor", tree_up="tensor", tree_down="tensor")
+SPLIT_NOTE = "the 3xTF32 split executes 3 MMAs per flop"
 
 
 def roofline_for(cls, ms, count, work, peaks, clocks, bounds=None):
@@ -268,7 +269,7 @@ def roofline_for(cls, ms, count, work, peaks, clocks, bounds=None):
         bf16 = peaks.get("bf16_tflops", 1891.8)
         peak = bf16 * 1.1 / 2.25
         unit, src = "TFLOP/s", ("measured bf16 dense x 1.1/2.25 (tf32 nominal ratio); algorithmic FP32 flops, "
-                                "the 3xTF32 split executes 3 MMAs per flop")
+                                + SPLIT_NOTE)
     else:
         mhz = peaks.get("sm_max_mhz", 2070.0)
         achieved = work[cls] / t / 1e12
@@ -314,10 +315,13 @@ def run_gpu(args):
     prec = args.precision
 
     NI = n // b - 1
+    global SPLIT_NOTE
+    if prec == "tf32":
+        SPLIT_NOTE = "factor products in one TF32 pass (1 MMA per flop), solve products 3xTF32"
     if helm:
         stage2 = "sweep"
     else:
-        stage2 = args.stage2 if args.stage2 != "auto" else ("oddeven" if NI >= 4 and prec == "fp32" else "sweep")
+        stage2 = args.stage2 if args.stage2 != "auto" else ("oddeven" if NI >= 4 and prec != "fp64" else "sweep")
     W["stage2"] = stage2
 
     def solver(precision, **kw):
@@ -408,7 +412,9 @@ def run_gpu(args):
         "higher_is_better": False,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32 factor (3xTF32 tensor products) / f64 residual+refinement" if prec == "fp32" else "f64",
+        "dtype": {"fp32": "f32 factor (3xTF32 tensor products) / f64 residual+refinement",
+                  "tf32": "f32 factor (single-pass TF32 tensor products) / f64 residual+refinement",
+                  "fp64": "f64"}[prec],
         "data": "synthetic",
         "config": dict(W, precision=prec, l2="every step streams > 10 GB (>> 129 MB L2); no explicit flush"),
         "max_relres": max(rels),
@@ -423,7 +429,7 @@ def run_gpu(args):
         "gpu_launches": int(np.mean(launches)) if launches else None,
         "clocks": clocks,
     }
-    if args.fp64_comparator and prec == "fp32":
+    if args.fp64_comparator and prec != "fp64":
         line["fp64_gpu"] = fp64_comparator(lambda: solver("fp64", rtol=1.0, max_refine=0), f)
         line["fp64_gpu"]["mixed_speedup"] = line["fp64_gpu"]["value"] / line["value"]
     if args.cpu_baseline:
@@ -516,7 +522,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "tf32"])
     ap.add_argument("--n", type=int, default=0)
     ap.add_argument("--b", type=int, default=0)
     ap.add_argument("--k", type=int, default=0)

@@ -59,7 +59,10 @@ typedef enum { SLAB_POISSON = 0, SLAB_DIFFUSION = 1, SLAB_HELMHOLTZ = 2 } slab_k
 
 typedef enum {
     SLAB_PREC_FP64 = 0,     /* factor and solves in FP64 (the plain FP64 GPU path) */
-    SLAB_PREC_FP32 = 1      /* factor and solves in FP32; FP64 residual + refinement */
+    SLAB_PREC_FP32 = 1,     /* factor and solves in FP32; FP64 residual + refinement */
+    SLAB_PREC_TF32 = 2      /* as FP32, but the factor's tensor-core products run in one TF32 pass
+                               (10-bit mantissa) instead of the 3xTF32 split; the solves keep the
+                               split.  Trades refinement steps for factor time. */
 } slab_precision;
 
 /*
@@ -145,6 +148,32 @@ slab_status slab_factor(const slab_grid* grid, const slab_coeffs* coeffs, int b,
  */
 slab_status slab_solve(slab_handle* h, const double* f, double* u, int k,
                        double* relres_out, int* iters_out);
+
+/*
+ * Batches of independent problems (uneven sizes allowed; the batched adjoint workload).
+ * slab_factor_batched factors count problems: problem i has grids[i], coeffs[i], b[i] and
+ * opts (opts->stream is ignored: every handle gets a stream of its own, created here and
+ * destroyed by slab_destroy).  Up to `workers` host threads (0: 8) drive the problems
+ * concurrently, so small problems overlap on the GPU.  out[i] receives the handle, or NULL
+ * if problem i failed; the first failure's status is returned (the other handles stay valid
+ * and must still be destroyed).  Synchronises before returning.
+ */
+slab_status slab_factor_batched(int count, const slab_grid* grids, const slab_coeffs* coeffs, const int* b,
+                                const slab_opts* opts, int workers, slab_handle** out);
+
+/*
+ * slab_solve on every handle of a batch: f[i], u[i] device pointers ([k[i]][N_i]),
+ * relres_out[i] host arrays of k[i] entries (or NULL), iters_out host, count entries (or NULL).
+ * Returns the first non-OK status (SLAB_ENOCONV included); all problems are attempted.
+ */
+slab_status slab_solve_batched(int count, slab_handle* const* h, const double* const* f, double* const* u,
+                               const int* k, double* const* relres_out, int* iters_out, int workers);
+
+/* slab_adjoint on every handle of a batch (dLdkappa[i] may be NULL).  Status as slab_solve_batched;
+ * synchronises every handle's stream before returning. */
+slab_status slab_adjoint_batched(int count, slab_handle* const* h, const double* const* dLdu,
+                                 const double* const* u, double* const* lambda, double* const* dLdkappa,
+                                 const int* k, int workers);
 
 /* r = f - A u in FP64 for k vectors (stencil kernel; the eq. "discretiation" operator). */
 slab_status slab_apply_residual(slab_handle* h, const double* u, const double* f, double* r, int k);

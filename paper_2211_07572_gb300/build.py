@@ -56,7 +56,7 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
             if l.strip():
                 sys.stderr.write(l)
     tmp = LIB + f".tmp{os.getpid()}"
-    r = subprocess.run([NVCC] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"], capture_output=True,
+    r = subprocess.run([NVCC] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart", "-lpthread"], capture_output=True,
                        text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")

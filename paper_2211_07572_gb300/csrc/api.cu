@@ -2,6 +2,8 @@
 // orchestration of the phases of Algorithms 3 and 4, and FP64 iterative
 // refinement on top of the (FP32 or FP64) factor.
 #include <algorithm>
+#include <atomic>
+#include <thread>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -358,6 +360,7 @@ const char* slab_strerror(slab_status s) {
 void slab_destroy(slab_handle* h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
+    const cudaStream_t own = h->own_stream ? h->stream : nullptr;
     free_workspace(h);
     dfree(h->wX2); dfree(h->wZ2);
     {
@@ -371,6 +374,7 @@ void slab_destroy(slab_handle* h) {
     dfree(h->t3Lin); dfree(h->t3LT); dfree(h->t3Ztb); dfree(h->t3ZtbT); dfree(h->t3ZIT); dfree(h->t3ZI);
     dfree(h->t3Rtb); dfree(h->t3RI); dfree(h->t3W);
     if (h->t3plan) tree3d_plan_free(h->t3plan);
+    if (own) cudaStreamDestroy(own);
     dfree(h->Tb); dfree(h->To); dfree(h->Fct); dfree(h->Linv); dfree(h->Y);
     dfree(h->crD); dfree(h->crE); dfree(h->crW); dfree(h->crLT); dfree(h->Tb1); dfree(h->To1);
     dfree(h->crPt); dfree(h->crP); dfree(h->crQt); dfree(h->crQ);
@@ -392,7 +396,10 @@ slab_status slab_factor(const slab_grid* grid, const slab_coeffs* co, int b, con
     if (co->kind < SLAB_POISSON || co->kind > SLAB_HELMHOLTZ) return SLAB_EINVAL;
     if (co->kind == SLAB_DIFFUSION && !co->kappa) return SLAB_EINVAL;
     if (co->kind == SLAB_HELMHOLTZ && !co->c) return SLAB_EINVAL;
-    if (o.factor_prec != SLAB_PREC_FP32 && o.factor_prec != SLAB_PREC_FP64) return SLAB_EINVAL;
+    if (o.factor_prec < SLAB_PREC_FP64 || o.factor_prec > SLAB_PREC_TF32) return SLAB_EINVAL;
+    const int want_tf32 = o.factor_prec == SLAB_PREC_TF32 || o.interface_prec == SLAB_PREC_TF32;
+    if (o.factor_prec == SLAB_PREC_TF32) o.factor_prec = SLAB_PREC_FP32;
+    if (o.interface_prec == SLAB_PREC_TF32) o.interface_prec = SLAB_PREC_FP32;
     if (o.stage2 < SLAB_STAGE2_AUTO || o.stage2 > SLAB_STAGE2_ODDEVEN) return SLAB_EINVAL;
     if (o.krylov < 0 || o.krylov > 200) return SLAB_EINVAL;
     int prec2 = o.interface_prec;
@@ -409,6 +416,7 @@ slab_status slab_factor(const slab_grid* grid, const slab_coeffs* co, int b, con
     h->dim = grid->dim; h->n = n; h->b = b; h->kind = co->kind; h->omega = co->omega;
     h->prec = o.factor_prec;
     h->rsz = h->prec == SLAB_PREC_FP64 ? 8 : 4;
+    h->tf32 = want_tf32;
     h->prec2 = prec2;
     h->rsz2 = h->prec2 == SLAB_PREC_FP64 ? 8 : 4;
     h->stream = (cudaStream_t)o.stream;
@@ -513,7 +521,9 @@ slab_status slab_factor(const slab_grid* grid, const slab_coeffs* co, int b, con
         CK(cudaMemcpyAsync(h->kappa, co->kappa, nodes2 * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
 #undef CK
     st = launch_coefficients(h, co->kappa, co->c);
+    h->tf32_now = h->tf32;
     if (!st) st = h->prec == SLAB_PREC_FP64 ? factor_impl<double>(h) : factor_impl<float>(h);
+    h->tf32_now = 0;
     if (!st) st = sync_status(h);
     if (st) {
         slab_destroy(h);
@@ -856,3 +866,79 @@ int64_t slab_device_bytes(const slab_handle* h) { return h ? h->dev_bytes : 0; }
 slab_status slab_last_error(const slab_handle* h) { return h ? h->err : SLAB_EINVAL; }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ batches of independent problems
+namespace {
+
+// run body(i) for i < count on up to `workers` host threads (each drives its own handles' streams)
+template <typename F>
+slab_status run_batch(int count, int workers, F body) {
+    if (count <= 0) return SLAB_OK;
+    if (workers <= 0) workers = 8;
+    workers = std::min(workers, count);
+    int device = 0;
+    cudaGetDevice(&device);
+    std::atomic<int> next(0);
+    std::vector<slab_status> st(count, SLAB_OK);
+    auto work = [&]() {
+        cudaSetDevice(device);
+        for (int i = next.fetch_add(1); i < count; i = next.fetch_add(1)) st[i] = body(i);
+    };
+    std::vector<std::thread> pool;
+    for (int w = 1; w < workers; ++w) pool.emplace_back(work);
+    work();
+    for (auto& t : pool) t.join();
+    for (int i = 0; i < count; ++i)
+        if (st[i] != SLAB_OK) return st[i];
+    return SLAB_OK;
+}
+
+}  // namespace
+
+slab_status slab_factor_batched(int count, const slab_grid* grids, const slab_coeffs* coeffs, const int* b,
+                                const slab_opts* opts, int workers, slab_handle** out) {
+    if (count < 0 || (count > 0 && (!grids || !coeffs || !b || !out))) return SLAB_EINVAL;
+    slab_opts base;
+    if (opts) base = *opts;
+    else slab_default_opts(&base);
+    return run_batch(count, workers, [&](int i) -> slab_status {
+        out[i] = nullptr;
+        cudaStream_t s = nullptr;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            return SLAB_ECUDA;
+        }
+        slab_opts o = base;
+        o.stream = s;
+        slab_handle* h = nullptr;
+        const slab_status st = slab_factor(&grids[i], &coeffs[i], b[i], &o, &h);
+        if (st != SLAB_OK) {
+            cudaStreamDestroy(s);
+            return st;
+        }
+        h->own_stream = 1;
+        out[i] = h;
+        return SLAB_OK;
+    });
+}
+
+slab_status slab_solve_batched(int count, slab_handle* const* h, const double* const* f, double* const* u,
+                               const int* k, double* const* relres_out, int* iters_out, int workers) {
+    if (count < 0 || (count > 0 && (!h || !f || !u || !k))) return SLAB_EINVAL;
+    return run_batch(count, workers, [&](int i) -> slab_status {
+        return slab_solve(h[i], f[i], u[i], k[i], relres_out ? relres_out[i] : nullptr,
+                          iters_out ? &iters_out[i] : nullptr);
+    });
+}
+
+slab_status slab_adjoint_batched(int count, slab_handle* const* h, const double* const* dLdu,
+                                 const double* const* u, double* const* lambda, double* const* dLdkappa,
+                                 const int* k, int workers) {
+    if (count < 0 || (count > 0 && (!h || !dLdu || !lambda || !k))) return SLAB_EINVAL;
+    return run_batch(count, workers, [&](int i) -> slab_status {
+        const slab_status st =
+            slab_adjoint(h[i], dLdu[i], u ? u[i] : nullptr, lambda[i], dLdkappa ? dLdkappa[i] : nullptr, k[i]);
+        if (h[i] && h[i]->stream) cudaStreamSynchronize(h[i]->stream);
+        return st;
+    });
+}

@@ -383,7 +383,7 @@ slab_status gemm_tn<float>(slab_handle* h, int cls, int M, int N, int K, float a
     TcGemmArgs g;
     g.M = M; g.N = N; g.K = K; g.alpha = alpha; g.beta = beta;
     g.A = A; g.lda = lda; g.B = B; g.ldb = ldb; g.C = C; g.ldc = ldc;
-    g.transC = transC; g.split = 1; g.lower_only = lower_only;
+    g.transC = transC; g.split = h->tf32_now ? 0 : 1; g.lower_only = lower_only;
     g.batch = 1; g.sA = g.sB = g.sC = 0;
     g.ksplit = 1; g.part = nullptr;
     if (N <= 64 && !lower_only && h->wPart) {     // skinny: split K over CTAs
@@ -750,7 +750,7 @@ slab_status gemm_tn_batched<float>(slab_handle* h, int cls, int M, int N, int K,
     TcGemmArgs g;
     g.M = M; g.N = N; g.K = K; g.alpha = alpha; g.beta = beta;
     g.A = A; g.lda = lda; g.B = B; g.ldb = ldb; g.C = C; g.ldc = ldc;
-    g.transC = transC; g.split = 1; g.lower_only = lower_only;
+    g.transC = transC; g.split = h->tf32_now ? 0 : 1; g.lower_only = lower_only;
     g.batch = batch; g.sA = sA; g.sB = sB; g.sC = sC;
     g.ksplit = 1; g.part = nullptr;
     const slab_status st = tc_gemm(h->stream, g, h->dstatus);

@@ -51,12 +51,15 @@ struct slab_handle {
     int prec;                 // slab_precision of Stage 1 (slab trees, T assembly, tree solves)
     size_t rsz;               // bytes of the Stage-1 scalar
     int prec2;                // slab_precision of Stage 2 (interface elimination and sweep)
+    int tf32;                 // SLAB_PREC_TF32 requested: single-pass TF32 products in the factor
+    int tf32_now;             // set while the factor runs
     size_t rsz2;              // bytes of the Stage-2 scalar
     void *Tb1, *To1;          // mixed mode: T assembled in the Stage-1 scalar (factor only)
     void *wX2, *wZ2;          // mixed mode: interface vectors in the Stage-2 scalar
     TreeDims td;
     int nt;                   // tiles per interface block (s_pad / 64)
     cudaStream_t stream;
+    int own_stream;           // the stream was created for this handle (batched factor)
     double rtol;
     int max_refine;
     int krylov;               // 0: plain refinement; m > 0: restarted GMRES(m) refinement

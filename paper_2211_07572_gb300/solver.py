@@ -15,7 +15,7 @@ import torch
 
 from . import _lib
 
-_PREC = {"fp64": _lib.PREC_FP64, "fp32": _lib.PREC_FP32}
+_PREC = {"fp64": _lib.PREC_FP64, "fp32": _lib.PREC_FP32, "tf32": _lib.PREC_TF32}
 _STAGE2 = {"auto": 0, "sweep": 1, "oddeven": 2}
 
 
@@ -38,7 +38,8 @@ class SlabSolver:
     dim, n: grid (unit square/cube, h = 1/n); b: interface spacing (b | n);
     kind: 0 Poisson, 1 diffusion -div(kappa grad u), 2 Helmholtz -Lap u - (omega/c)^2 u;
     kappa / c: node fields with (n+1)^dim entries; precision: "fp32" (FP32 factor, FP64
-    refinement) or "fp64" (plain FP64 path); stage2: "auto", "sweep" (Algorithm 1) or
+    refinement), "tf32" (as fp32 with single-pass TF32 tensor products in the factor) or
+    "fp64" (plain FP64 path); stage2: "auto", "sweep" (Algorithm 1) or
     "oddeven"; interface_precision: precision of the interface system (default: "fp64" for
     Helmholtz with an FP32 factor, else the factor precision); krylov: 0 for plain iterative
     refinement, m > 0 for restarted FP64 GMRES(m) preconditioned by the factor.
@@ -194,3 +195,111 @@ class SlabSolveFunction(torch.autograd.Function):
         lam, gk = ctx.solver.adjoint(gu.contiguous(), u, allow_noconv=True)
         ctx.solver.close()
         return gk, lam.view_as(gu), None, None, None
+
+
+class SlabBatch:
+    """Independent problems (uneven sizes allowed) factored, solved and differentiated together:
+    slab_factor_batched / slab_solve_batched / slab_adjoint_batched, each problem on a stream of
+    its own, driven by up to `workers` host threads.
+
+    problems: list of dicts with keys dim, n, b, kind and kappa / c / omega as for SlabSolver.
+    Vectors are lists of device tensors, one [k][N_i] tensor per problem.
+    """
+
+    def __init__(self, problems, precision: str = "fp32", rtol: float = 1e-10, max_refine: int = 30,
+                 stage2: str = "sweep", krylov: int = 0, workers: int = 8):
+        self.lib = _lib.load()
+        self.workers = int(workers)
+        cnt = len(problems)
+        self.count = cnt
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self._coef = []
+        grids = (_lib.SlabGrid * cnt)()
+        coeffs = (_lib.SlabCoeffs * cnt)()
+        bs = (ctypes.c_int * cnt)()
+        self.meta = []
+        for i, p in enumerate(problems):
+            kap = _dev(p.get("kappa"), self.device)
+            cc = _dev(p.get("c"), self.device)
+            self._coef.append((kap, cc))
+            grids[i] = _lib.SlabGrid(p["dim"], p["n"])
+            coeffs[i] = _lib.SlabCoeffs(p["kind"], _ptr(kap), _ptr(cc), float(p.get("omega", 0.0)))
+            bs[i] = p["b"]
+            self.meta.append((p["dim"], p["n"]))
+        opts = _lib.SlabOpts()
+        self.lib.slab_default_opts(ctypes.byref(opts))
+        opts.factor_prec = _PREC[precision]
+        opts.rtol = float(rtol)
+        opts.max_refine = int(max_refine)
+        opts.stage2 = _STAGE2[stage2]
+        opts.interface_prec = -1
+        opts.krylov = int(krylov)
+        self.h = (ctypes.c_void_p * cnt)()
+        torch.cuda.synchronize()
+        st = self.lib.slab_factor_batched(cnt, grids, coeffs, bs, ctypes.byref(opts), self.workers, self.h)
+        if st != 0:
+            self.close()
+            _lib.check(st, "slab_factor_batched")
+
+    def _ptrs(self, ts):
+        arr = (ctypes.c_void_p * self.count)()
+        for i, t in enumerate(ts):
+            arr[i] = None if t is None else t.data_ptr()
+        return arr
+
+    def solve(self, fs, allow_noconv: bool = False):
+        fs = [_dev(f, self.device).reshape(-1, (n - 1) ** d) for f, (d, n) in zip(fs, self.meta)]
+        us = [torch.empty_like(f) for f in fs]
+        ks = (ctypes.c_int * self.count)(*[f.shape[0] for f in fs])
+        rel = [np.zeros(f.shape[0]) for f in fs]
+        relp = (ctypes.c_void_p * self.count)(*[r.ctypes.data for r in rel])
+        its = (ctypes.c_int * self.count)()
+        torch.cuda.synchronize()
+        st = self.lib.slab_solve_batched(self.count, self.h, self._ptrs(fs), self._ptrs(us), ks, relp, its,
+                                         self.workers)
+        _lib.check(st, "slab_solve_batched", allow=(_lib.SLAB_ENOCONV,) if allow_noconv else ())
+        return us, rel, list(its)
+
+    def adjoint(self, dLdus, us, allow_noconv: bool = False):
+        gs = [_dev(g, self.device).reshape(-1, (n - 1) ** d) for g, (d, n) in zip(dLdus, self.meta)]
+        lams = [torch.empty_like(g) for g in gs]
+        grads = [torch.zeros((n + 1,) * d, dtype=torch.float64, device=self.device) for (d, n) in self.meta]
+        ks = (ctypes.c_int * self.count)(*[g.shape[0] for g in gs])
+        torch.cuda.synchronize()
+        st = self.lib.slab_adjoint_batched(self.count, self.h, self._ptrs(gs), self._ptrs(us), self._ptrs(lams),
+                                           self._ptrs(grads), ks, self.workers)
+        _lib.check(st, "slab_adjoint_batched", allow=(_lib.SLAB_ENOCONV,) if allow_noconv else ())
+        return lams, grads
+
+    def close(self):
+        h = getattr(self, "h", None)
+        if h is not None:
+            for i in range(self.count):
+                if h[i]:
+                    self.lib.slab_destroy(h[i])
+                    h[i] = None
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def batched_adjoint_gradients(problems, fs, u_targets, wave: int = 32, workers: int = 8,
+                              precision: str = "fp32", rtol: float = 1e-12):
+    """Loss L_i = ||u_i - u_t,i||^2 and dL_i/dkappa_i for independent diffusion problems, processed
+    in waves of `wave` problems (factor, solve, adjoint solve and gradient per wave, then free).
+    Returns (losses, gradients) as lists."""
+    losses, grads = [], []
+    for w0 in range(0, len(problems), wave):
+        sl = slice(w0, w0 + wave)
+        batch = SlabBatch(problems[sl], precision=precision, rtol=rtol, max_refine=40, workers=workers)
+        us, _, _ = batch.solve(fs[sl], allow_noconv=True)
+        uts = [_dev(t, batch.device).reshape_as(u) for t, u in zip(u_targets[sl], us)]
+        losses += [float(((u - t) ** 2).sum()) for u, t in zip(us, uts)]
+        _, g = batch.adjoint([2 * (u - t) for u, t in zip(us, uts)], us, allow_noconv=True)
+        grads += g
+        batch.close()
+    return losses, grads

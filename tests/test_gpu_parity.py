@@ -205,6 +205,20 @@ def test_gmres_refinement_matches_oracle():
     assert it <= it0 + 1, (it, it0)
 
 
+@pytest.mark.parametrize("dim,n,b", [(2, 256, 16), (3, 32, 8)])
+def test_tf32_factor_refines_to_oracle(dim, n, b):
+    """Single-pass TF32 tensor products in the factor: the refined solution still matches the oracle."""
+    from paper_2211_07572_gb300.solver import SlabSolver
+    p = inputs.diffusion(n, b, k=2, dim=dim, n_modes=8, field_seed=4, rhs_seed=106)
+    s = SlabSolver(dim, p.n, p.b, p.kind, kappa=p.kappa, precision="tf32", rtol=1e-12, max_refine=40)
+    u, rel, it = s.solve(torch.from_numpy(p.f).cuda())
+    s.close()
+    A = oracle.assemble_problem(p)
+    uo = oracle.solve(p)
+    assert oracle.relres(A, u.cpu().numpy(), p.f).max() <= 1e-11
+    assert (np.linalg.norm(u.cpu().numpy() - uo, axis=1) / np.linalg.norm(uo, axis=1)).max() <= 1e-9
+
+
 def test_many_rhs_chunks_and_empty():
     """k > 64 runs in several passes; k = 0 is a no-op."""
     p = _problem(64, 8, inputs.DIFFUSION, k=70, seed=3)
