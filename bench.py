@@ -494,6 +494,64 @@ def cpu_baseline(n_full, b, k, n_sample=512, kind="diffusion"):
                       f"k n^{2 * dim - 1}"}
 
 
+def run_adjoint_batch(args):
+    """Batched adjoint workload: 256 independent 2-D diffusion problems, n in {256, ..., 1024}, b = 16;
+    per step every problem is factored, solved, its loss ||u - u_t||^2 formed and dL/dkappa computed by
+    the adjoint solve (waves of problems, each problem on a stream of its own)."""
+    import numpy as np
+    import torch
+
+    from paper_2211_07572_gb300 import inputs
+    from paper_2211_07572_gb300.solver import batched_adjoint_gradients
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    sizes = inputs.adjoint_batch_sizes()
+    count = args.count or len(sizes)
+    sizes = sizes[:count]
+    probs, fs, uts = [], [], []
+    for i, n in enumerate(sizes):
+        d = inputs.adjoint_instance(i, int(n))
+        probs.append(dict(dim=2, n=int(n), b=16, kind=inputs.DIFFUSION, kappa=d["kappa"]))
+        fs.append(torch.from_numpy(d["f"]).to(dev))
+        uts.append(torch.from_numpy(d["u_target"]).to(dev))
+    prec = args.precision
+
+    def step(precision=prec):
+        return batched_adjoint_gradients(probs, fs, uts, wave=args.wave, workers=8, precision=precision)
+
+    for _ in range(args.warmup):
+        step()
+    sampler = ClockSampler()
+    sampler.start()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        losses, grads = step()
+    torch.cuda.synchronize()
+    sec = (time.perf_counter() - t0) / args.steps
+    sampler.stop()
+    line = {
+        "metric": "batched adjoint: factor+solve+adjoint+gradient s per batch",
+        "value": sec, "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": sec * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 factor (3xTF32 tensor products) / f64 residual+refinement" if prec == "fp32" else prec,
+        "data": "synthetic",
+        "config": {"workload": f"batched adjoint {count} x 2D diffusion n in {{256..1024}} b=16, L=||u-u_t||^2",
+                   "count": count, "wave": args.wave, "workers": 8, "precision": prec,
+                   "timing": "host clock around device-synchronised steps (problems run on their own streams)"},
+        "instances_per_s": count / sec,
+        "mean_loss": float(np.mean(losses)),
+        "clocks": sampler.summary(),
+    }
+    if args.fp64_comparator and prec != "fp64":
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step("fp64")
+        torch.cuda.synchronize()
+        line["fp64_gpu"] = {"value": time.perf_counter() - t0, "unit": "s", "path": "same batch, FP64 factor"}
+    print(json.dumps(line))
+
+
 def run_reference(args):
     n, b, k = WORKLOAD["n"], WORKLOAD["b"], WORKLOAD["k"]
     rank = int(os.environ.get("RANK", "0"))
@@ -530,7 +588,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-fp64", dest="fp64_comparator", action="store_false")
     ap.add_argument("--once", action="store_true", help="run one step only (for profilers)")
-    ap.add_argument("--workload", default="diffusion2048", choices=["diffusion2048", "helmholtz4096", "diffusion3d96"],
+    ap.add_argument("--count", type=int, default=0, help="adjoint256: number of problems (0: all 256)")
+    ap.add_argument("--wave", type=int, default=32, help="adjoint256: problems per wave")
+    ap.add_argument("--workload", default="diffusion2048",
+                    choices=["diffusion2048", "helmholtz4096", "diffusion3d96", "adjoint256"],
                     help="diffusion2048: the default bench line; helmholtz4096, diffusion3d96: the other workloads")
     ap.add_argument("--krylov", type=int, default=0, help="0: plain refinement; m: FP64 GMRES(m) refinement")
     ap.add_argument("--stage2", default="auto", choices=["auto", "sweep", "oddeven"],
@@ -541,6 +602,8 @@ def main():
         pass
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "adjoint256":
+        run_adjoint_batch(args)
     else:
         run_gpu(args)
 

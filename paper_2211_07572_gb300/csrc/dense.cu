@@ -504,12 +504,14 @@ __device__ void gj_warp_gepp(T* A, const int* rows, int nr, int* out) {
 // One launch per panel: leaves, pairwise merges (ticketed, deterministic), and at the root the
 // panel's pivot rows, their flags and perm entries, and the compacted list of remaining rows.
 template <typename T>
+// (pivot selection runs in FP32 whatever the storage type: it only chooses rows, the elimination
+// itself is done in T by the kernels below)
 __global__ void __launch_bounds__(32 * GJ_WARPS) gj_tournament_kernel(const T* __restrict__ G, int64_t ld,
                                                                        int c0, int panel, int nact, GjWork w,
                                                                        const int* act, int* act_next) {
     extern __shared__ unsigned char gj_smem[];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    T* A = reinterpret_cast<T*>(gj_smem) + (size_t)wid * GJ_LEAF * 65;
+    float* A = reinterpret_cast<float*>(gj_smem) + (size_t)wid * GJ_LEAF * 65;
     __shared__ int rows_s[GJ_WARPS][GJ_LEAF];
     int* rows = rows_s[wid];
     const int L = (nact + GJ_LEAF - 1) / GJ_LEAF;
@@ -522,11 +524,11 @@ __global__ void __launch_bounds__(32 * GJ_WARPS) gj_tournament_kernel(const T* _
         __syncwarp();
         for (int idx = lane; idx < nr * 64; idx += 32) {
             const int r = idx >> 6, c = idx & 63;
-            A[r * 65 + c] = G[(int64_t)rows[r] * ld + c0 + c];
+            A[r * 65 + c] = (float)G[(int64_t)rows[r] * ld + c0 + c];
         }
         __syncwarp();
         int* out = w.cand + (gj_level_off(L, lvl) + node) * 64;
-        gj_warp_gepp<T>(A, rows, nr, out);
+        gj_warp_gepp<float>(A, rows, nr, out);
         __syncwarp();
         if (gj_level_count(L, lvl) == 1) break;         // root
         const int parent = node >> 1;
@@ -801,7 +803,7 @@ slab_status sweep_factor_indef(slab_handle* h) {
     w.cand = (int*)wb;                   wb += (size_t)nodes * 64 * sizeof(int);
     w.tick = (unsigned*)wb;              wb += (size_t)nodes * sizeof(unsigned);
     w.piv = (int*)wb;
-    const size_t tsmem = (size_t)GJ_WARPS * GJ_LEAF * 65 * sizeof(T);
+    const size_t tsmem = (size_t)GJ_WARPS * GJ_LEAF * 65 * sizeof(float);
     const size_t ismem = (size_t)64 * 129 * sizeof(T);
     const size_t asmem = (size_t)2 * 64 * 65 * sizeof(T);
     SLAB_CK(h, cudaFuncSetAttribute(gj_tournament_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -664,11 +664,22 @@ __global__ void __launch_bounds__(TB_THREADS) tree_down_kernel(SolveArgs<T> P, i
         __syncthreads();
         if (!last) return;
         __threadfence();
-        for (int idx = tid; idx < MAXM * KMAX; idx += nth) {
-            T v = T(0);
-            for (int ch = 0; ch < nch; ++ch) v += __ldcg(wsn + (int64_t)ch * MAXM * KMAX + idx);
-            V[idx] = v;
+        // chunk order fixed (deterministic); the 16 elements of a thread are loaded together so
+        // the loads of one chunk are in flight at once
+        constexpr int PER = MAXM * KMAX / TB_THREADS;
+        T v[PER];
+#pragma unroll
+        for (int j = 0; j < PER; ++j) v[j] = T(0);
+        for (int ch = 0; ch < nch; ++ch) {
+            const T* src = wsn + (int64_t)ch * MAXM * KMAX + tid;
+            T ld[PER];
+#pragma unroll
+            for (int j = 0; j < PER; ++j) ld[j] = __ldcg(src + j * TB_THREADS);
+#pragma unroll
+            for (int j = 0; j < PER; ++j) v[j] += ld[j];
         }
+#pragma unroll
+        for (int j = 0; j < PER; ++j) V[tid + j * TB_THREADS] = v[j];
         if (tid == 0) *tk = 0;
     }
     // finish the node: V = y - V; SPD: x = Li^T V, indefinite: x = V (y already holds S^{-1} g)
