@@ -331,8 +331,12 @@ def run_gpu(args):
 
     W["krylov"] = args.krylov
 
+    iprec = None if args.interface == "default" else args.interface
+    W["interface"] = args.interface
+
     def make():
-        return solver(prec, rtol=W["rtol"], max_refine=40, stage2=stage2, krylov=args.krylov)
+        return solver(prec, rtol=W["rtol"], max_refine=40, stage2=stage2, krylov=args.krylov,
+                      interface_precision=iprec)
 
     def step(f_in, u_out, counts=None):
         s = make()
@@ -383,7 +387,8 @@ def run_gpu(args):
     t_fac = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     t_f0.record(stream)
-    s = solver(prec, rtol=W["rtol"], max_refine=40, profile=True, stage2=stage2, krylov=args.krylov)
+    s = solver(prec, rtol=W["rtol"], max_refine=40, profile=True, stage2=stage2, krylov=args.krylov,
+               interface_precision=iprec)
     t_fac.record(stream)
     _, rel1, it1 = s.solve(f, u, allow_noconv=True)
     t_end.record(stream)
@@ -414,7 +419,8 @@ def run_gpu(args):
         "vs_baseline": None,
         "dtype": {"fp32": "f32 factor (3xTF32 tensor products) / f64 residual+refinement",
                   "tf32": "f32 factor (single-pass TF32 tensor products) / f64 residual+refinement",
-                  "fp64": "f64"}[prec],
+                  "fp64": "f64"}[prec] + ("" if iprec is None else f"; interface {iprec}"
+                                            + (" (FP64-accurate tensor-core products)" if iprec == "fp64tc" else "")),
         "data": "synthetic",
         "config": dict(W, precision=prec, l2="every step streams > 10 GB (>> 129 MB L2); no explicit flush"),
         "max_relres": max(rels),
@@ -429,8 +435,8 @@ def run_gpu(args):
         "gpu_launches": int(np.mean(launches)) if launches else None,
         "clocks": clocks,
     }
-    if args.fp64_comparator and prec != "fp64":
-        line["fp64_gpu"] = fp64_comparator(lambda: solver("fp64", rtol=1.0, max_refine=0), f)
+    if args.fp64_comparator and (prec != "fp64" or iprec is not None):
+        line["fp64_gpu"] = fp64_comparator(lambda: solver("fp64", rtol=1.0, max_refine=0, interface_precision="fp64"), f)
         line["fp64_gpu"]["mixed_speedup"] = line["fp64_gpu"]["value"] / line["value"]
     if args.cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(n, b, k, kind=W["kind"], n_sample=256 if helm else (32 if dim == 3 else 512))
@@ -594,6 +600,8 @@ def main():
                     choices=["diffusion2048", "helmholtz4096", "diffusion3d96", "adjoint256"],
                     help="diffusion2048: the default bench line; helmholtz4096, diffusion3d96: the other workloads")
     ap.add_argument("--krylov", type=int, default=0, help="0: plain refinement; m: FP64 GMRES(m) refinement")
+    ap.add_argument("--interface", default="default", choices=["default", "fp32", "fp64", "fp64tc", "tf32"],
+                    help="precision of the interface system (fp64tc: FP64-accurate tensor-core products)")
     ap.add_argument("--stage2", default="auto", choices=["auto", "sweep", "oddeven"],
                     help="elimination order of T (auto: odd-even for 4 or more interfaces)")
     args = ap.parse_args()

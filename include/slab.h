@@ -60,9 +60,11 @@ typedef enum { SLAB_POISSON = 0, SLAB_DIFFUSION = 1, SLAB_HELMHOLTZ = 2 } slab_k
 typedef enum {
     SLAB_PREC_FP64 = 0,     /* factor and solves in FP64 (the plain FP64 GPU path) */
     SLAB_PREC_FP32 = 1,     /* factor and solves in FP32; FP64 residual + refinement */
-    SLAB_PREC_TF32 = 2      /* as FP32, but the factor's tensor-core products run in one TF32 pass
+    SLAB_PREC_TF32 = 2,     /* as FP32, but the factor's tensor-core products run in one TF32 pass
                                (10-bit mantissa) instead of the 3xTF32 split; the solves keep the
                                split.  Trades refinement steps for factor time. */
+    SLAB_PREC_FP64_TC = 3   /* interface_prec only: FP64 data, the interface elimination's products
+                               FP64-accurate on the tensor cores (slab_fp64_tc_gemm) */
 } slab_precision;
 
 /*
@@ -109,7 +111,8 @@ typedef struct {
     int profile;            /* 1: time every kernel launch from the start (see slab_profile) */
     int stage2;             /* slab_stage2 */
     int interface_prec;     /* slab_precision of Stage 2 (the interface elimination and sweep),
-                               or -1: FP64 for HELMHOLTZ with an FP32 factor, else factor_prec.
+                               or -1: FP64 for HELMHOLTZ with an FP32 factor, else factor_prec;
+                               SLAB_PREC_FP64_TC: FP64 with tensor-core products (see above).
                                FP32 slab trees with an FP64 interface system is the mixed mode;
                                an FP64 factor with an FP32 interface is SLAB_EINVAL */
 } slab_opts;
@@ -237,6 +240,21 @@ slab_status slab_tc_gemm(int M, int N, int K, float alpha, const float* A, int64
  * clears the record; it synchronises the stream.  Launch counts are kept even when timing
  * is off.  Timing adds an event record per launch; keep it off for timed runs.
  */
+/*
+ * FP64-accurate product on the tensor cores: C (FP64, M x N, row-major, ldc) += alpha A B^T with
+ * A (M x K, lda) and B (N x K, ldb) FP64 row-major, K <= 64 and K % 32 == 0 (SLAB_EINVAL
+ * otherwise).  Every row of A and of B is scaled by a power of two and cut into 8 exact 7-bit
+ * integer slices; the slice products run on the TF32 tensor cores without rounding and are
+ * recombined in FP64 (error ~2^-48 |A| |B| per element, like an FP64 product).  work: device
+ * scratch of slab_fp64_tc_gemm_work_bytes(M, N, K) bytes; dev_err as in slab_tc_gemm.
+ * Asynchronous on `stream`.  Used for the interface elimination with interface_prec
+ * SLAB_PREC_FP64_TC; the paper has no counterpart (its arithmetic is native FP64).
+ */
+slab_status slab_fp64_tc_gemm(int M, int N, int K, double alpha, const double* A, int64_t lda,
+                              const double* B, int64_t ldb, double* C, int64_t ldc, void* work,
+                              unsigned* dev_err, void* stream);
+size_t slab_fp64_tc_gemm_work_bytes(int M, int N, int K);
+
 #define SLAB_KERNEL_CLASSES 11
 slab_status slab_profile(slab_handle* h, int enable);
 slab_status slab_profile_read(slab_handle* h, double* ms, int64_t* launches, int n);

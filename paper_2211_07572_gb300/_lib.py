@@ -13,7 +13,7 @@ SLAB_OK, SLAB_EINVAL, SLAB_ENOMEM, SLAB_ESINGULAR, SLAB_ENOCONV, SLAB_ETIMEOUT, 
 POISSON, DIFFUSION, HELMHOLTZ = 0, 1, 2
 KERNEL_CLASSES = ("coeff", "tree_factor", "assemble_T", "panel", "trailing", "schur_update", "sweep_products",
                   "tree_up", "tree_down", "stencil", "other")
-PREC_FP64, PREC_FP32, PREC_TF32 = 0, 1, 2
+PREC_FP64, PREC_FP32, PREC_TF32, PREC_FP64_TC = 0, 1, 2, 3
 
 
 class SlabGrid(ctypes.Structure):
@@ -65,6 +65,9 @@ SIGNATURES = {
                              ctypes.c_float, c_void_p, c_int64, c_int, c_int, c_void_p, c_void_p]),
     "slab_residual_norms_noalloc": (c_int, [c_int, c_int, c_void_p, c_void_p, c_double, c_void_p, c_void_p,
                                             c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
+    "slab_fp64_tc_gemm": (c_int, [c_int, c_int, c_int, c_double, c_void_p, c_int64, c_void_p, c_int64, c_void_p,
+                                  c_int64, c_void_p, c_void_p, c_void_p]),
+    "slab_fp64_tc_gemm_work_bytes": (ctypes.c_size_t, [c_int, c_int, c_int]),
     "slab_factor_batched": (c_int, [c_int, ctypes.POINTER(SlabGrid), ctypes.POINTER(SlabCoeffs),
                                     ctypes.POINTER(c_int), ctypes.POINTER(SlabOpts), c_int, ctypes.POINTER(c_void_p)]),
     "slab_solve_batched": (c_int, [c_int, ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p),

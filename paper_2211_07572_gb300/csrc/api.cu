@@ -240,7 +240,10 @@ template <typename T>
 slab_status factor_impl(slab_handle* h) {
     if (h->prec2 == h->prec) {
         TRY(stage1_impl<T>(h));
-        return sweep_factor<T>(h);
+        h->fp64tc_now = h->fp64tc;
+        const slab_status st = sweep_factor<T>(h);
+        h->fp64tc_now = 0;
+        return st;
     }
     // mixed mode: assemble T in the Stage-1 scalar, widen it, eliminate in the Stage-2 scalar
     void* Tb2 = h->Tb;
@@ -254,7 +257,10 @@ slab_status factor_impl(slab_handle* h) {
     const int64_t blk = (int64_t)h->td.s_pad * h->td.s_pad;
     TRY(widen_to_double(h, (const float*)h->Tb1, (double*)h->Tb, h->td.NI * blk));
     TRY(widen_to_double(h, (const float*)h->To1, (double*)h->To, (h->td.NI - 1) * blk));
-    return sweep_factor<double>(h);
+    h->fp64tc_now = h->fp64tc;
+    const slab_status st2 = sweep_factor<double>(h);
+    h->fp64tc_now = 0;
+    return st2;
 }
 
 struct ProfRecord {
@@ -369,7 +375,7 @@ void slab_destroy(slab_handle* h) {
     void* p;
     p = h->AX; dfree(p); p = h->AY; dfree(p); p = h->DG; dfree(p); p = h->kappa; dfree(p);
     dfree(h->tLinv); dfree(h->tZtb); dfree(h->tRtb); dfree(h->tZI); dfree(h->tRI);
-    dfree(h->tWtb); dfree(h->tWI); dfree(h->ToT); dfree(h->dscratch); dfree(h->gjw);
+    dfree(h->tWtb); dfree(h->tWI); dfree(h->ToT); dfree(h->dscratch); dfree(h->gjw); dfree(h->ozw);
     p = h->AZ; dfree(p);
     dfree(h->t3Lin); dfree(h->t3LT); dfree(h->t3Ztb); dfree(h->t3ZtbT); dfree(h->t3ZIT); dfree(h->t3ZI);
     dfree(h->t3Rtb); dfree(h->t3RI); dfree(h->t3W);
@@ -398,6 +404,8 @@ slab_status slab_factor(const slab_grid* grid, const slab_coeffs* co, int b, con
     if (co->kind == SLAB_HELMHOLTZ && !co->c) return SLAB_EINVAL;
     if (o.factor_prec < SLAB_PREC_FP64 || o.factor_prec > SLAB_PREC_TF32) return SLAB_EINVAL;
     const int want_tf32 = o.factor_prec == SLAB_PREC_TF32 || o.interface_prec == SLAB_PREC_TF32;
+    const int want_fp64tc = o.interface_prec == SLAB_PREC_FP64_TC;
+    if (want_fp64tc) o.interface_prec = SLAB_PREC_FP64;
     if (o.factor_prec == SLAB_PREC_TF32) o.factor_prec = SLAB_PREC_FP32;
     if (o.interface_prec == SLAB_PREC_TF32) o.interface_prec = SLAB_PREC_FP32;
     if (o.stage2 < SLAB_STAGE2_AUTO || o.stage2 > SLAB_STAGE2_ODDEVEN) return SLAB_EINVAL;
@@ -417,6 +425,7 @@ slab_status slab_factor(const slab_grid* grid, const slab_coeffs* co, int b, con
     h->prec = o.factor_prec;
     h->rsz = h->prec == SLAB_PREC_FP64 ? 8 : 4;
     h->tf32 = want_tf32;
+    h->fp64tc = want_fp64tc;
     h->prec2 = prec2;
     h->rsz2 = h->prec2 == SLAB_PREC_FP64 ? 8 : 4;
     h->stream = (cudaStream_t)o.stream;
@@ -505,6 +514,7 @@ slab_status slab_factor(const slab_grid* grid, const slab_coeffs* co, int b, con
         ALLOC(h->ToT, (d.NI - 1) * blk * R2);
     }
     ALLOC(h->dscratch, 256);
+    if (h->fp64tc) ALLOC(h->ozw, ozaki_work_bytes(2 * (int64_t)d.s_pad + 128, 3 * (int64_t)d.s_pad, 64));
     ALLOC(h->Linv, d.NI * blk * R2);
     if (!h->stage2) ALLOC(h->Y, (d.NI - 1) * blk * R2);
     ALLOC(h->dstatus, sizeof(unsigned));

@@ -397,10 +397,77 @@ slab_status gemm_tn<float>(slab_handle* h, int cls, int M, int N, int K, float a
     return st;
 }
 
+template <typename T>
+__global__ void scale_matrix_kernel(T* C, int64_t ldc, int M, int N, T beta) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)M * N) return;
+    T* p = C + (e / N) * ldc + e % N;
+    *p = beta == T(0) ? T(0) : beta * *p;
+}
+
+// C = beta C + alpha A B^T for N <= 8 (right-hand sides): one warp per row of A, lanes over K
+// (coalesced), so the product streams A once at memory speed.
+template <typename T, int NB>
+__global__ void __launch_bounds__(256) gemv_rows_kernel(int M, int N, int K, T alpha, const T* __restrict__ A,
+                                                        int64_t lda, const T* __restrict__ B, int64_t ldb, T beta,
+                                                        T* C, int64_t ldc, int transC) {
+    const int row = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (row >= M) return;
+    T acc[NB];
+#pragma unroll
+    for (int r = 0; r < NB; ++r) acc[r] = T(0);
+    const T* a = A + (int64_t)row * lda;
+    for (int k = lane; k < K; k += 32) {
+        const T av = a[k];
+#pragma unroll
+        for (int r = 0; r < NB; ++r)
+            if (r < N) acc[r] += av * B[(int64_t)r * ldb + k];
+    }
+#pragma unroll
+    for (int r = 0; r < NB; ++r) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int r = 0; r < NB; ++r) {
+            if (r >= N) break;
+            T* c = transC ? C + (int64_t)r * ldc + row : C + (int64_t)row * ldc + r;
+            *c = (beta == T(0) ? T(0) : beta * *c) + alpha * acc[r];
+        }
+    }
+}
+
 template <>
 slab_status gemm_tn<double>(slab_handle* h, int cls, int M, int N, int K, double alpha, const double* A,
                             int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
                             int transC, int lower_only) {
+    if (N <= 8 && !lower_only && M > 0) {
+        SLAB_PROF(h, cls);
+        gemv_rows_kernel<double, 8><<<(M + 7) / 8, 256, 0, h->stream>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc,
+                                                                       transC);
+        SLAB_CK_LAUNCH(h);
+        return SLAB_OK;
+    }
+    if (h->fp64tc_now && !transC && K % 32 == 0 && M > 0 && N > 0) {
+        // FP64-accurate tensor-core product, K in chunks of 64
+        SLAB_PROF(h, cls);
+        if (beta != 1.0) {
+            scale_matrix_kernel<double><<<(unsigned)(((int64_t)M * N + 255) / 256), 256, 0, h->stream>>>(C, ldc, M, N,
+                                                                                                         beta);
+            SLAB_CK_LAUNCH(h);
+        }
+        for (int k0 = 0; k0 < K; k0 += 64) {
+            const int kc = std::min(64, K - k0);
+            const slab_status st = ozaki_gemm(h->stream, M, N, kc, alpha, A + k0, lda, B + k0, ldb, C, ldc, lower_only,
+                                              h->ozw, h->dstatus);
+            if (st) {
+                if (h->err == SLAB_OK) h->err = st;
+                return st;
+            }
+        }
+        return SLAB_OK;
+    }
     SLAB_PROF(h, cls);
     if (N <= 64 && !lower_only && h->wTickets) {
         int KS = K / 256;
@@ -522,9 +589,19 @@ __global__ void __launch_bounds__(32 * GJ_WARPS) gj_tournament_kernel(const T* _
     for (int i = lane; i < nr; i += 32) rows[i] = act[node * GJ_LEAF + i];
     while (true) {
         __syncwarp();
-        for (int idx = lane; idx < nr * 64; idx += 32) {
-            const int r = idx >> 6, c = idx & 63;
-            A[r * 65 + c] = (float)G[(int64_t)rows[r] * ld + c0 + c];
+        // 8 loads in flight per lane (rows are scattered over G, each 64-column row segment coalesced)
+        for (int i0 = 0; i0 < nr * 64; i0 += 32 * 8) {
+            T v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int idx = i0 + u * 32 + lane;
+                v[u] = idx < nr * 64 ? G[(int64_t)rows[idx >> 6] * ld + c0 + (idx & 63)] : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int idx = i0 + u * 32 + lane;
+                if (idx < nr * 64) A[(idx >> 6) * 65 + (idx & 63)] = (float)v[u];
+            }
         }
         __syncwarp();
         int* out = w.cand + (gj_level_off(L, lvl) + node) * 64;
@@ -573,19 +650,22 @@ __global__ void __launch_bounds__(32 * GJ_WARPS) gj_tournament_kernel(const T* _
     }
 }
 
-// A11^{-1} of the panel's pivot rows by Gauss-Jordan with partial pivoting on [A11 | I] in smem.
+// LU of the panel's pivot block A11 = G[piv, panel] with partial pivoting (row i of the
+// factored block is row perm[i] of A11): unit L below the diagonal, U on and above it, and the
+// reciprocals of U's diagonal in rdiag.  One CTA; a zero or non-finite pivot sets SLAB_DEV_NOTSPD.
 template <typename T>
-__global__ void __launch_bounds__(256) gj_a11_inverse_kernel(const T* __restrict__ G, int64_t ld, int c0,
-                                                             const int* piv, T* Ainv, unsigned* status) {
+__global__ void __launch_bounds__(256) gj_a11_lu_kernel(const T* __restrict__ G, int64_t ld, int c0, const int* piv,
+                                                        T* LU, T* rdiag, int* perm, unsigned* status) {
     extern __shared__ unsigned char gj_smem[];
-    T (*M)[129] = reinterpret_cast<T (*)[129]>(gj_smem);     // [A11 | I], 64 x 128 (+1 pad)
-    __shared__ int pr;
+    T (*M)[65] = reinterpret_cast<T (*)[65]>(gj_smem);
+    __shared__ int pr[64];
+    __shared__ int pk;
     const int tid = threadIdx.x;
     for (int idx = tid; idx < 64 * 64; idx += 256) {
         const int i = idx >> 6, j = idx & 63;
         M[i][j] = G[(int64_t)piv[i] * ld + c0 + j];
-        M[i][64 + j] = i == j ? T(1) : T(0);
     }
+    if (tid < 64) pr[tid] = tid;
     __syncthreads();
     for (int k = 0; k < 64; ++k) {
         if (tid < 32) {
@@ -606,31 +686,29 @@ __global__ void __launch_bounds__(256) gj_a11_inverse_kernel(const T* __restrict
                     atomicOr(status, SLAB_DEV_NOTSPD);
                     M[bi][k] = T(1);
                 }
-                pr = bi;
+                pk = bi;
+                if (bi != k) { const int t2 = pr[k]; pr[k] = pr[bi]; pr[bi] = t2; }
             }
         }
         __syncthreads();
-        const int p = pr;
-        if (p != k)
-            for (int j = tid; j < 128; j += 256) {
-                const T t = M[k][j];
-                M[k][j] = M[p][j];
-                M[p][j] = t;
-            }
+        const int p = pk;
+        if (p != k && tid < 64) { const T t2 = M[k][tid]; M[k][tid] = M[p][tid]; M[p][tid] = t2; }
         __syncthreads();
         const T rp = T(1) / M[k][k];
+        if (tid > k && tid < 64) M[tid][k] *= rp;                  // multipliers
         __syncthreads();
-        for (int j = tid; j < 128; j += 256) M[k][j] *= rp;
-        __syncthreads();
-        for (int idx = tid; idx < 64 * 128; idx += 256) {
-            const int i = idx >> 7, j = idx & 127;
-            if (i != k && j != k) M[i][j] -= M[i][k] * M[k][j];
+        const int r = 63 - k;
+        for (int idx = tid; idx < r * r; idx += 256) {
+            const int i = k + 1 + idx / r, j = k + 1 + idx % r;
+            M[i][j] -= M[i][k] * M[k][j];
         }
         __syncthreads();
-        if (tid < 64 && tid != k) M[tid][k] = T(0);
-        __syncthreads();
     }
-    for (int idx = tid; idx < 64 * 64; idx += 256) Ainv[idx] = M[idx >> 6][64 + (idx & 63)];
+    for (int idx = tid; idx < 64 * 64; idx += 256) LU[idx] = M[idx >> 6][idx & 63];
+    if (tid < 64) {
+        rdiag[tid] = T(1) / M[tid][tid];
+        perm[tid] = pr[tid];
+    }
 }
 
 // blockIdx.y == 0: X = A11^{-1} G[piv, col0 .. col0+63] for 64 columns of the rest (cols >= c0+64),
@@ -641,7 +719,8 @@ template <typename T>
 __global__ void __launch_bounds__(256) gj_panel_apply_kernel(T* Gt, int64_t ldt, const T* __restrict__ Gb,
                                                              int64_t ldb, int sp, int wt, int c0, int panel,
                                                              const int* piv, const int* pflag,
-                                                             const T* __restrict__ Ainv, T* XT, T* Pbuf) {
+                                                             const T* __restrict__ LU, const T* __restrict__ rdiag,
+                                                             const int* __restrict__ perm, T* XT, T* Pbuf) {
     extern __shared__ unsigned char gj_smem[];
     T (*Ai)[65] = reinterpret_cast<T (*)[65]>(gj_smem);
     T (*Bc)[65] = Ai + 64;
@@ -662,32 +741,27 @@ __global__ void __launch_bounds__(256) gj_panel_apply_kernel(T* Gt, int64_t ldt,
     const int nc = min(64, wt - cb);
     for (int idx = tid; idx < 64 * 64; idx += 256) {
         const int i = idx >> 6, j = idx & 63;
-        Ai[i][j] = Ainv[idx];
-        Bc[i][j] = j < nc ? Gt[(int64_t)piv[i] * ldt + cb + j] : T(0);
+        Ai[i][j] = LU[idx];
+        Bc[i][j] = j < nc ? Gt[(int64_t)piv[perm[i]] * ldt + cb + j] : T(0);     // P B
     }
     __syncthreads();
-    T acc[4][4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b2 = 0; b2 < 4; ++b2) acc[a][b2] = T(0);
-    for (int l = 0; l < 64; ++l) {
-        T av[4], bv[4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a) av[a] = Ai[ty + 16 * a][l];
-#pragma unroll
-        for (int b2 = 0; b2 < 4; ++b2) bv[b2] = Bc[l][tx + 16 * b2];
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b2 = 0; b2 < 4; ++b2) acc[a][b2] += av[a] * bv[b2];
+    // X = U^{-1} L^{-1} P B, 64 columns at once
+    for (int k = 0; k < 63; ++k) {                       // forward, unit L
+        for (int idx = tid; idx < (63 - k) * 64; idx += 256) {
+            const int i = k + 1 + (idx >> 6), j = idx & 63;
+            Bc[i][j] -= Ai[i][k] * Bc[k][j];
+        }
+        __syncthreads();
     }
-    __syncthreads();
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b2 = 0; b2 < 4; ++b2) Bc[ty + 16 * a][tx + 16 * b2] = acc[a][b2];
-    __syncthreads();
+    for (int k = 63; k >= 0; --k) {                      // backward
+        if (tid < 64) Bc[k][tid] *= rdiag[k];
+        __syncthreads();
+        for (int idx = tid; idx < k * 64; idx += 256) {
+            const int i = idx >> 6, j = idx & 63;
+            Bc[i][j] -= Ai[i][k] * Bc[k][j];
+        }
+        __syncthreads();
+    }
     for (int idx = tid; idx < 64 * 64; idx += 256) {
         const int i = idx >> 6, j = idx & 63;            // row of X, column in block
         if (j < nc) Gt[(int64_t)piv[i] * ldt + cb + j] = Bc[i][j];
@@ -793,7 +867,9 @@ slab_status sweep_factor_indef(slab_handle* h) {
     char* wb = (char*)h->gjw;
     T* Pbuf = (T*)wb;                    wb += (size_t)2 * sp * 64 * sizeof(T);
     T* XT = (T*)wb;                      wb += (size_t)3 * sp * 64 * sizeof(T);
-    T* Ainv = (T*)wb;                    wb += (size_t)64 * 64 * sizeof(T);
+    T* A11lu = (T*)wb;                   wb += (size_t)64 * 64 * sizeof(T);
+    T* rdiag = (T*)wb;                   wb += (size_t)64 * sizeof(T);
+    int* lperm = (int*)wb;               wb += (size_t)64 * sizeof(int);
     GjWork w;
     int* act0 = (int*)wb;                wb += (size_t)2 * sp * sizeof(int);
     w.act = act0;
@@ -804,11 +880,11 @@ slab_status sweep_factor_indef(slab_handle* h) {
     w.tick = (unsigned*)wb;              wb += (size_t)nodes * sizeof(unsigned);
     w.piv = (int*)wb;
     const size_t tsmem = (size_t)GJ_WARPS * GJ_LEAF * 65 * sizeof(float);
-    const size_t ismem = (size_t)64 * 129 * sizeof(T);
+    const size_t ismem = (size_t)64 * 65 * sizeof(T);
     const size_t asmem = (size_t)2 * 64 * 65 * sizeof(T);
     SLAB_CK(h, cudaFuncSetAttribute(gj_tournament_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)tsmem));
-    SLAB_CK(h, cudaFuncSetAttribute(gj_a11_inverse_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    SLAB_CK(h, cudaFuncSetAttribute(gj_a11_lu_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)ismem));
     SLAB_CK(h, cudaFuncSetAttribute(gj_panel_apply_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)asmem));
@@ -843,12 +919,12 @@ slab_status sweep_factor_indef(slab_handle* h) {
                 gj_tournament_kernel<T><<<(L + GJ_WARPS - 1) / GJ_WARPS, 32 * GJ_WARPS, tsmem, h->stream>>>(
                     Gt, wt, c0, kb, nact, w, act, act_next);
                 SLAB_CK_LAUNCH(h);
-                gj_a11_inverse_kernel<T><<<1, 256, ismem, h->stream>>>(Gt, wt, c0, w.piv, Ainv, h->dstatus);
+                gj_a11_lu_kernel<T><<<1, 256, ismem, h->stream>>>(Gt, wt, c0, w.piv, A11lu, rdiag, lperm, h->dstatus);
                 SLAB_CK_LAUNCH(h);
                 const int ncol = wt - c0 - 64;
                 dim3 grid((unsigned)std::max((ncol + 63) / 64, 64), 2);
                 gj_panel_apply_kernel<T><<<grid, 256, asmem, h->stream>>>(Gt, wt, Gb, 2 * sp, sp, wt, c0, kb, w.piv,
-                                                                     w.pflag, Ainv, XT, Pbuf);
+                                                                     w.pflag, A11lu, rdiag, lperm, XT, Pbuf);
                 SLAB_CK_LAUNCH(h);
             }
             // G[other, rest] -= Pbuf X : top rows over all remaining columns, bottom rows up to 2 sp
@@ -918,7 +994,8 @@ slab_status narrow_to_float(slab_handle* h, const double* src, float* dst, int64
 size_t gj_work_bytes(int sp, size_t rsz) {
     const int nodes = gj_nodes((sp + GJ_LEAF - 1) / GJ_LEAF);
     return (size_t)(2 + 3) * sp * 64 * rsz + 64 * 64 * rsz + (size_t)4 * sp * sizeof(int) +
-           (size_t)nodes * 64 * sizeof(int) + (size_t)nodes * sizeof(unsigned) + 64 * sizeof(int) + 256;
+           (size_t)nodes * 64 * sizeof(int) + (size_t)nodes * sizeof(unsigned) + 64 * sizeof(int) + 64 * rsz +
+           64 * sizeof(int) + 256;
 }
 
 // Algorithm 2 for the indefinite kind on X ([NI][kcap][s_pad]):

@@ -53,6 +53,9 @@ struct slab_handle {
     int prec2;                // slab_precision of Stage 2 (interface elimination and sweep)
     int tf32;                 // SLAB_PREC_TF32 requested: single-pass TF32 products in the factor
     int tf32_now;             // set while the factor runs
+    int fp64tc;               // SLAB_PREC_FP64_TC interface: FP64 products of Stage 2 on the tensor cores
+    int fp64tc_now;           // set while the interface elimination runs
+    void* ozw;                // work area of those products
     size_t rsz2;              // bytes of the Stage-2 scalar
     void *Tb1, *To1;          // mixed mode: T assembled in the Stage-1 scalar (factor only)
     void *wX2, *wZ2;          // mixed mode: interface vectors in the Stage-2 scalar
@@ -249,6 +252,10 @@ struct TcGemmArgs {
     int ksplit;          // > 1: K split over CTAs, partial sums in part[ksplit][M][N] (batch must be 1)
     float* part;
 };
+size_t ozaki_work_bytes(int64_t M, int64_t N, int K);
+slab_status ozaki_gemm(cudaStream_t st, int M, int N, int K, double alpha, const double* A, int64_t lda,
+                       const double* B, int64_t ldb, double* C, int64_t ldc, int lower_only, void* work,
+                       unsigned* err);
 slab_status tc_gemm(cudaStream_t st, const TcGemmArgs& g, unsigned* err);
 
 // error helper

@@ -387,6 +387,194 @@ slab_status launch_tc(cudaStream_t st, const TcGemmArgs& g, unsigned* err) {
     return SLAB_OK;
 }
 
+
+// ------------------------------------------------------------------ FP64-accurate product (integer slices)
+// C (FP64) += alpha A B^T for FP64 A (M x K) and B (N x K), K <= 64.  Every row of A (column of
+// B^T) is scaled by a power of two into (-1, 1) and cut into OZ_S slices of 7 bits:
+//   A[i][k] = 2^ea_i sum_s a_s[i][k] 2^{-7(s+1)},  |a_s| <= 127 integers (exact in TF32),
+// so every slice product a_s b_t^T is an exact TF32 tensor-core product and the sum over
+// K <= 64 (below 2^20) and over the at most OZ_S pairs of one level d = s + t (below 2^23) is
+// exact in the FP32 accumulator.  Levels d < OZ_S are kept (the neglected ones are below
+// 2^{-7 OZ_S} of |A| |B|); the epilogue adds the levels in FP32 pairs (hi + lo, ~2^-48) and
+// updates C in FP64.  Tile 128 x 64; TMEM holds the OZ_S level accumulators (64 columns each).
+constexpr int OZ_S = 8;
+constexpr int OZ_BN = 64;
+
+struct OzCfg {
+    static constexpr int A_BYTES = BM * BK * 4;
+    static constexpr int B_BYTES = OZ_BN * BK * 4;
+    static constexpr int CHUNK_BYTES = OZ_S * (A_BYTES + B_BYTES);     // every slice of one K-chunk
+    static constexpr int SMEM = CHUNK_BYTES + 1024;
+};
+
+__global__ void __launch_bounds__(256, 1)
+    ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N,
+                      int K, double alpha, const int* __restrict__ ea, const int* __restrict__ eb, double* C,
+                      int64_t ldc, int lower_only, unsigned* err) {
+    extern __shared__ __align__(1024) uint8_t oz_smem[];
+    __shared__ uint64_t full_bar[OZ_S], mma_bar;          // full_bar[s]: slice s of A and of B landed
+    __shared__ uint32_t tmem_slot;
+    __shared__ volatile int abort_flag;
+    const int bn = blockIdx.x, bm = blockIdx.y;
+    if (lower_only && bn * OZ_BN >= (bm + 1) * BM) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nk = K / BK;
+    uint8_t* base = (uint8_t*)(((uintptr_t)oz_smem + 1023) & ~(uintptr_t)1023);
+    auto a_sl = [&](int sl) { return base + sl * OzCfg::A_BYTES; };
+    auto b_sl = [&](int sl) { return base + OZ_S * OzCfg::A_BYTES + sl * OzCfg::B_BYTES; };
+    if (threadIdx.x == 0) {
+        for (int sl = 0; sl < OZ_S; ++sl) mbar_init(&full_bar[sl], 1);
+        mbar_init(&mma_bar, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) tmem_alloc(&tmem_slot, OZ_S * OZ_BN);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+    int last_issued = -1;                                                // (warp 0, lane 0)
+    // one K-chunk at a time: TMA of every slice, then every slice pair of every level
+    for (int kt = 0; kt < nk; ++kt) {
+        if (warp == 0 && lane == 0 && !abort_flag) {
+            if (kt > 0 && !mbar_wait(&mma_bar, (kt - 1) & 1)) {          // previous chunk's MMAs read the buffer
+                abort_flag = 1;
+                atomicOr(err, 2u);
+            } else {
+                for (int sl = 0; sl < OZ_S; ++sl) {                     // slice by slice: MMAs start early
+                    mbar_expect_tx(&full_bar[sl], OzCfg::A_BYTES + OzCfg::B_BYTES);
+                    tma_load_3d(a_sl(sl), &tmA, &full_bar[sl], kt * BK, bm * BM, sl);
+                    tma_load_3d(b_sl(sl), &tmB, &full_bar[sl], kt * BK, bn * OZ_BN, sl);
+                }
+                last_issued = kt;
+            }
+        }
+        if (warp == 1 && lane == 0) {
+            // when slice s has landed, issue every pair (i, s) and (s, j), i <= s, j < s, of a kept level
+            constexpr uint32_t idesc = idesc_tf32(BM, OZ_BN);
+            uint32_t started = kt > 0 ? 0xFFu : 0u;                  // levels already written this tile
+            bool ok = !abort_flag;
+            for (int sl = 0; sl < OZ_S && ok; ++sl) {
+                if (!mbar_wait(&full_bar[sl], kt & 1)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                for (int pr = 0; pr < 2 * sl + 1; ++pr) {
+                    const int sa = pr <= sl ? pr : sl, sb = pr <= sl ? sl : pr - sl - 1;   // (i, s) then (s, j)
+                    const int d = sa + sb;
+                    if (d >= OZ_S) continue;
+                    const uint64_t da = sdesc_sw128(smem_u32(a_sl(sa))), db = sdesc_sw128(smem_u32(b_sl(sb)));
+                    const uint32_t acc_col = tmem + (uint32_t)(d * OZ_BN);
+#pragma unroll
+                    for (int kk = 0; kk < BK / 8; ++kk) {
+                        const uint64_t off = (uint64_t)(kk * 2);
+                        mma_tf32(acc_col, da + off, db + off, idesc, ((started >> d) & 1u) || kk > 0 ? 1u : 0u);
+                    }
+                    started |= 1u << d;
+                }
+            }
+            if (!ok) {
+                abort_flag = 1;
+                atomicOr(err, 2u);
+            } else {
+                mma_commit(&mma_bar);
+            }
+        }
+        __syncthreads();
+    }
+    // after an abort, let the copies already issued land before the CTA's shared memory is released
+    if (warp == 0 && lane == 0 && abort_flag && last_issued >= 0)
+        for (int sl = 0; sl < OZ_S; ++sl) mbar_wait(&full_bar[sl], last_issued & 1);
+    // the last chunk's commit (parity (nk-1) & 1) marks every accumulator complete
+    if (warp >= 4) {
+        bool ok = !abort_flag && mbar_wait(&mma_bar, (nk - 1) & 1);
+        if (!ok) {
+            abort_flag = 1;
+            atomicOr(err, 2u);
+        } else {
+            tc_fence_after();
+            const int rw = warp - 4;
+            const int row = bm * BM + rw * 32 + lane;
+            const uint32_t tl = (uint32_t)(rw * 32) << 16;
+#pragma unroll 1
+            for (int cc = 0; cc < OZ_BN / 32; ++cc) {
+                float hi[32], lo[32], v[32];
+#pragma unroll
+                for (int j = 0; j < 32; ++j) { hi[j] = 0.f; lo[j] = 0.f; }
+#pragma unroll 1
+                for (int d = OZ_S - 1; d >= 0; --d) {                    // small levels first
+                    tmem_ld32(tmem + tl + (uint32_t)(d * OZ_BN + cc * 32), v);
+                    const float sc = __int_as_float((127 - 7 * d) << 23);          // 2^{-7d}, exact
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {                       // (hi, lo) += v 2^{-7d}, two-sum
+                        const float a = v[j] * sc;
+                        const float s2 = hi[j] + a;
+                        const float bb = s2 - hi[j];
+                        lo[j] += (hi[j] - (s2 - bb)) + (a - bb);
+                        hi[j] = s2;
+                    }
+                }
+                if (row < M) {
+                    // C += alpha 2^{ea + eb - 14} (hi + lo): the power of two is applied in FP32 (exact
+                    // while in range, checked), so the FP64 work per element is two conversions and
+                    // two additions
+                    const int er = ea[row] - 14;
+                    double* crow = C + (int64_t)row * ldc;
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int col = bn * OZ_BN + cc * 32 + j;
+                        if (col < N) {
+                            const int ex = er + eb[col];
+                            double c = crow[col];
+                            if (ex > -60 && ex < 60 && (alpha == 1.0 || alpha == -1.0)) {
+                                const float sc = alpha < 0 ? -__int_as_float((127 + ex) << 23)
+                                                           : __int_as_float((127 + ex) << 23);   // exact
+                                c += (double)(hi[j] * sc);
+                                c += (double)(lo[j] * sc);
+                            } else {
+                                c += alpha * ldexp((double)hi[j] + (double)lo[j], ex);
+                            }
+                            crow[col] = c;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, OZ_S * OZ_BN);
+    }
+}
+
+// slices of the rows of X (rows x K, leading dimension ldx): out[s][r][k] (FP32 integers), e[r]
+__global__ void ozaki_split_kernel(const double* __restrict__ X, int64_t ldx, int rows, int K, float* out, int* e) {
+    const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= rows) return;
+    const double* xr = X + (int64_t)r * ldx;
+    double mx = 0.0;
+    for (int k = lane; k < K; k += 32) mx = fmax(mx, fabs(xr[k]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    int ex = 0;
+    if (mx > 0.0) frexp(mx, &ex);                                    // mx < 2^ex
+    if (lane == 0) e[r] = ex;
+    for (int k = lane; k < K; k += 32) {
+        const double x = xr[k];
+        const long long q = __double2ll_rz(fabs(ldexp(x, 7 * OZ_S - ex)));   // |x| 2^{56-ex} < 2^56
+        const float sg = x < 0.0 ? -1.f : 1.f;
+#pragma unroll
+        for (int sl = 0; sl < OZ_S; ++sl) {
+            const int a = (int)((q >> (7 * (OZ_S - 1 - sl))) & 127);
+            out[((int64_t)sl * rows + r) * K + k] = sg * (float)a;
+        }
+    }
+}
+
 }  // namespace
 
 // Host entry: validates the layout constraints of the TMA path and launches.
@@ -413,3 +601,47 @@ extern "C" slab_status slab_tc_gemm(int M, int N, int K, float alpha, const floa
     g.ksplit = 1; g.part = nullptr;
     return tc_gemm((cudaStream_t)stream, g, dev_err);
 }
+
+// C (FP64, M x N, ldc) += alpha A B^T with A (M x K, lda) and B (N x K, ldb) FP64, FP64-accurate
+// on the tensor cores (integer-slice products, above).  K <= 64, K % 32 == 0.  work: float
+// slices [OZ_S][M][K] and [OZ_S][N][K] followed by the exponents (M + N ints): ozaki_work_bytes.
+size_t ozaki_work_bytes(int64_t M, int64_t N, int K) {
+    return (size_t)OZ_S * (M + N) * K * sizeof(float) + (size_t)(M + N) * sizeof(int) + 256;
+}
+
+slab_status ozaki_gemm(cudaStream_t st, int M, int N, int K, double alpha, const double* A, int64_t lda,
+                       const double* B, int64_t ldb, double* C, int64_t ldc, int lower_only, void* work,
+                       unsigned* err) {
+    if (M <= 0 || N <= 0) return SLAB_OK;
+    if (K <= 0 || K > 64 || K % BK) return SLAB_EINVAL;
+    float* As = (float*)work;
+    float* Bs = As + (int64_t)OZ_S * M * K;
+    int* ea = (int*)(Bs + (int64_t)OZ_S * N * K);
+    int* eb = ea + M;
+    ozaki_split_kernel<<<(M + 7) / 8, 256, 0, st>>>(A, lda, M, K, As, ea);
+    if (cudaGetLastError() != cudaSuccess) return SLAB_ECUDA;
+    ozaki_split_kernel<<<(N + 7) / 8, 256, 0, st>>>(B, ldb, N, K, Bs, eb);
+    if (cudaGetLastError() != cudaSuccess) return SLAB_ECUDA;
+    CUtensorMap ta, tb;
+    if (!make_map(&ta, As, M, K, K, OZ_S, (int64_t)M * K, BM)) return SLAB_ECUDA;
+    if (!make_map(&tb, Bs, N, K, K, OZ_S, (int64_t)N * K, OZ_BN)) return SLAB_ECUDA;
+    static bool attr_set = false;
+    if (!attr_set) {
+        if (cudaFuncSetAttribute(ozaki_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OzCfg::SMEM) !=
+            cudaSuccess)
+            return SLAB_ECUDA;
+        attr_set = true;
+    }
+    dim3 grid((N + OZ_BN - 1) / OZ_BN, (M + BM - 1) / BM);
+    ozaki_gemm_kernel<<<grid, 256, OzCfg::SMEM, st>>>(ta, tb, M, N, K, alpha, ea, eb, C, ldc, lower_only, err);
+    return cudaGetLastError() == cudaSuccess ? SLAB_OK : SLAB_ECUDA;
+}
+
+extern "C" slab_status slab_fp64_tc_gemm(int M, int N, int K, double alpha, const double* A, int64_t lda,
+                                         const double* B, int64_t ldb, double* C, int64_t ldc, void* work,
+                                         unsigned* dev_err, void* stream) {
+    if (!A || !B || !C || !work || !dev_err || M < 0 || N < 0) return SLAB_EINVAL;
+    return ozaki_gemm((cudaStream_t)stream, M, N, K, alpha, A, lda, B, ldb, C, ldc, 0, work, dev_err);
+}
+
+extern "C" size_t slab_fp64_tc_gemm_work_bytes(int M, int N, int K) { return ozaki_work_bytes(M, N, K); }

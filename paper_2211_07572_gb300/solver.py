@@ -15,7 +15,7 @@ import torch
 
 from . import _lib
 
-_PREC = {"fp64": _lib.PREC_FP64, "fp32": _lib.PREC_FP32, "tf32": _lib.PREC_TF32}
+_PREC = {"fp64": _lib.PREC_FP64, "fp32": _lib.PREC_FP32, "tf32": _lib.PREC_TF32, "fp64tc": _lib.PREC_FP64_TC}
 _STAGE2 = {"auto": 0, "sweep": 1, "oddeven": 2}
 
 

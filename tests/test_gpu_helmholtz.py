@@ -69,7 +69,7 @@ def _block_tridiag(Td, Tl, Tu):
     return T
 
 
-@pytest.mark.parametrize("stage_prec,eps", [("fp64", 2.2e-16), ("fp32", 6e-8)])
+@pytest.mark.parametrize("stage_prec,eps", [("fp64", 2.2e-16), ("fp32", 6e-8), ("fp64tc", 2.2e-16)])
 @pytest.mark.parametrize("n,b", [(256, 16), (512, 32)])
 def test_helmholtz_interface_solve_matches_oracle(n, b, stage_prec, eps):
     _interface_check(n, b, stage_prec, eps)
@@ -87,7 +87,7 @@ def _interface_check(n, b, stage_prec, eps):
     cond(T) times the two backward errors."""
     p = inputs.helmholtz(n, b, n_modes=8, field_seed=3)
     p.f = np.concatenate([p.f, inputs.normal_rhs(2, n, 2, 35)])
-    s = _solver(p, stage_prec, iprec=stage_prec)
+    s = _solver(p, "fp64" if stage_prec == "fp64tc" else stage_prec, iprec=stage_prec)
     A = oracle.assemble_problem(p)
     Td, Tl, Tu = oracle.reduced_system(A, 2, n, b, pivot=True)
     ft = np.concatenate(oracle.reduced_rhs(A, p.f, 2, n, b, pivot=True), axis=1)
@@ -144,11 +144,12 @@ def test_helmholtz_point_source_residual():
     assert oracle.relres(A, u.cpu().numpy(), p.f).max() <= 1e-10
 
 
-@pytest.mark.parametrize("precision,iprec,krylov", [("fp64", None, 0), ("fp64", None, 10)])
+@pytest.mark.parametrize("precision,iprec,krylov", [("fp64", None, 0), ("fp64", None, 10), ("fp64", "fp64tc", 0)])
 def test_helmholtz_solve_matches_oracle_n512(precision, iprec, krylov):
     """End to end at n = 512, b = 32 (the Helmholtz workload's b and points per wavelength; eight
     Stage-2 panels with two tournament merge levels): refined solution vs the pivoted banded LU.
-    FP64 factor, with plain refinement and with GMRES(10) refinement."""
+    FP64 factor, with plain refinement, with GMRES(10) refinement, and with the interface
+    elimination's products FP64-accurate on the tensor cores ("fp64tc")."""
     n, b = 512, 32
     p = inputs.helmholtz(n, b, n_modes=8, field_seed=3)
     s = _solver(p, precision, rtol=1e-12, max_refine=60, iprec=iprec, krylov=krylov)

@@ -168,6 +168,24 @@ def test_diffusion_solve_matches_oracle(precision, stage2):
 
 
 @pytest.mark.parametrize("stage2", ["sweep", "oddeven"])
+def test_fp64tc_interface_matches_oracle(stage2):
+    """FP64 slab trees, interface elimination with FP64-accurate tensor-core products."""
+    p = inputs.diffusion(256, 16, k=2, n_modes=16, field_seed=2, rhs_seed=107)
+    s = _solver(p, "fp64", rtol=1e-13, stage2=stage2, iprec="fp64tc")
+    A = oracle.assemble_problem(p)
+    Td, Tl, Tu = oracle.reduced_system(A, 2, p.n, p.b)
+    ft = oracle.reduced_rhs(A, p.f, 2, p.n, p.b)
+    ut_o = np.concatenate(oracle.sweep_solve(Tl, Tu, oracle.sweep_build(Td, Tl, Tu), ft), axis=1)
+    ut = s.interface_solve(torch.from_numpy(np.concatenate(ft, axis=1)).cuda()).cpu().numpy()
+    assert np.abs(ut - ut_o).max() <= 1e-10 * np.abs(ut_o).max()
+    u, rel, it = s.solve(torch.from_numpy(p.f).cuda(), allow_noconv=True)
+    uo = oracle.solve(p)
+    assert oracle.relres(A, u.cpu().numpy(), p.f).max() <= 1e-12
+    assert (np.linalg.norm(u.cpu().numpy() - uo, axis=1) / np.linalg.norm(uo, axis=1)).max() <= 1e-10
+    s.close()
+
+
+@pytest.mark.parametrize("stage2", ["sweep", "oddeven"])
 def test_mixed_precision_matches_oracle(stage2):
     """FP32 slab trees with the interface system in FP64 (both elimination orders): T blocks are
     the FP32 assembly widened, the refined solution matches the oracle."""

@@ -93,3 +93,28 @@ def test_tc_gemm_schur_shape_rate():
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / 5
     print(f"tc_gemm 2048^3 3xTF32: {ms:.3f} ms, {2 * M * N * K / ms / 1e9:.1f} TFLOP/s algorithmic")
+
+
+@pytest.mark.parametrize("M,N,K", [(200, 130, 64), (4096, 640, 64), (77, 1000, 32)])
+def test_fp64_tc_gemm_is_fp64_accurate(M, N, K):
+    """Integer-slice product: C += alpha A B^T in FP64 accuracy (normwise error near 2^-48 of
+    |A| |B|, far below FP32's 2^-24), with rows of very different magnitudes."""
+    from paper_2211_07572_gb300 import _lib
+    lib = _lib.load()
+    rng = np.random.default_rng(M + N + K)
+    A = rng.standard_normal((M, K)) * np.exp2(rng.integers(-20, 20, size=(M, 1)))
+    B = rng.standard_normal((N, K)) * np.exp2(rng.integers(-20, 20, size=(N, 1)))
+    C0 = rng.standard_normal((M, N))
+    Ad, Bd, Cd = (torch.from_numpy(x).cuda() for x in (A, B, C0.copy()))
+    work = torch.empty(int(lib.slab_fp64_tc_gemm_work_bytes(M, N, K)), dtype=torch.uint8, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    st = lib.slab_fp64_tc_gemm(M, N, K, -0.75, ctypes.c_void_p(Ad.data_ptr()), K, ctypes.c_void_p(Bd.data_ptr()), K,
+                               ctypes.c_void_p(Cd.data_ptr()), N, ctypes.c_void_p(work.data_ptr()),
+                               ctypes.c_void_p(err.data_ptr()), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == 0
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    ref = C0 - 0.75 * (A @ B.T)
+    scale = 0.75 * np.abs(A) @ np.abs(B).T + np.abs(C0)
+    rel = (np.abs(Cd.cpu().numpy() - ref) / scale).max()
+    assert rel <= 1e-13, rel
