@@ -254,6 +254,14 @@ BOUND = {"tree_factor": "alu", "assemble_T": "hbm", "panel": "alu", "trailing": 
 
 
 BOUND3 = dict(BOUND, assemble_T="tensor", tree_up="tensor", tree_down="tensor")
+
+# DRAM bytes per launch from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum), for the
+# default workload only: the n = 1024, b = 32, k = 64 case (all heights of one pass) scaled by the
+# node count (4x at n = 2048, same b, m, k) over the 11 launches of a pass at n = 2048.
+TRAFFIC = {
+    "tree_down": {"bytes": 1.682e9 * 4 / 11, "from": "ncu at n=1024 (10 launches, 1.682 GB/pass) x4 nodes / 11"},
+    "tree_up": {"bytes": 2.314e9 * 4 / 11, "from": "ncu at n=1024 (10 launches, 2.314 GB/pass) x4 nodes / 11"},
+}
 SPLIT_NOTE = "the 3xTF32 split executes 3 MMAs per flop"
 
 
@@ -403,6 +411,9 @@ def run_gpu(args):
     bmap = BOUND3 if dim == 3 else BOUND
     dom = max((c for c in cls_ms if c in bmap and work.get(c, 0) > 0), key=lambda c: cls_ms[c])
     roof = roofline_for(dom, cls_ms[dom], cls_cnt[dom], work, peaks, clocks, bmap)
+    if W["kind"] == "diffusion" and (n, b, k) == (2048, 32, 64) and dom in TRAFFIC and prec == "fp32":
+        roof["traffic"] = TRAFFIC[dom]["bytes"]
+        roof["traffic_source"] = TRAFFIC[dom]["from"]
     dense_cls = ("trailing", "schur_update", "sweep_products") + (("assemble_T", "tree_up", "tree_down") if dim == 3 else ())
     dense = {c: roofline_for(c, cls_ms[c], cls_cnt[c], work, peaks, clocks, bmap)
              for c in dense_cls if cls_ms.get(c, 0) > 0}

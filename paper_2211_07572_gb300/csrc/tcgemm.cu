@@ -452,6 +452,7 @@ __global__ void __launch_bounds__(256, 1)
         if (warp == 1 && lane == 0) {
             // when slice s has landed, issue every pair (i, s) and (s, j), i <= s, j < s, of a kept level
             constexpr uint32_t idesc = idesc_tf32(BM, OZ_BN);
+            const uint64_t da0 = sdesc_sw128(smem_u32(a_sl(0))), db0 = sdesc_sw128(smem_u32(b_sl(0)));
             uint32_t started = kt > 0 ? 0xFFu : 0u;                  // levels already written this tile
             bool ok = !abort_flag;
             for (int sl = 0; sl < OZ_S && ok; ++sl) {
@@ -464,7 +465,9 @@ __global__ void __launch_bounds__(256, 1)
                     const int sa = pr <= sl ? pr : sl, sb = pr <= sl ? sl : pr - sl - 1;   // (i, s) then (s, j)
                     const int d = sa + sb;
                     if (d >= OZ_S) continue;
-                    const uint64_t da = sdesc_sw128(smem_u32(a_sl(sa))), db = sdesc_sw128(smem_u32(b_sl(sb)));
+                    // slice tiles are OzCfg::A_BYTES / B_BYTES apart: advance the descriptors' addresses
+                    const uint64_t da = da0 + (uint64_t)(sa * (OzCfg::A_BYTES >> 4));
+                    const uint64_t db = db0 + (uint64_t)(sb * (OzCfg::B_BYTES >> 4));
                     const uint32_t acc_col = tmem + (uint32_t)(d * OZ_BN);
 #pragma unroll
                     for (int kk = 0; kk < BK / 8; ++kk) {
@@ -499,6 +502,12 @@ __global__ void __launch_bounds__(256, 1)
             const uint32_t tl = (uint32_t)(rw * 32) << 16;
 #pragma unroll 1
             for (int cc = 0; cc < OZ_BN / 32; ++cc) {
+                // the 32 old values of C first, so their loads overlap the level sums below
+                double cold[32];
+                const int col0 = bn * OZ_BN + cc * 32;
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    cold[j] = (row < M && col0 + j < N) ? C[(int64_t)row * ldc + col0 + j] : 0.0;
                 float hi[32], lo[32], v[32];
 #pragma unroll
                 for (int j = 0; j < 32; ++j) { hi[j] = 0.f; lo[j] = 0.f; }
@@ -526,7 +535,7 @@ __global__ void __launch_bounds__(256, 1)
                         const int col = bn * OZ_BN + cc * 32 + j;
                         if (col < N) {
                             const int ex = er + eb[col];
-                            double c = crow[col];
+                            double c = cold[j];
                             if (ex > -60 && ex < 60 && (alpha == 1.0 || alpha == -1.0)) {
                                 const float sc = alpha < 0 ? -__int_as_float((127 + ex) << 23)
                                                            : __int_as_float((127 + ex) << 23);   // exact
