@@ -14,9 +14,24 @@
 // waits (bounded) for the copies it issued, frees its TMEM and returns.
 #include <cuda.h>
 
+#include <atomic>
+
 #include "slab_internal.cuh"
 
 namespace {
+
+// Opt a kernel in to its dynamic shared memory once per device (idempotent, safe from several
+// host threads: the batched entry points drive problems from a worker pool).
+template <typename Kern>
+bool ensure_smem_attr(Kern kernel, int bytes, std::atomic<uint32_t>& done) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    const uint32_t bit = 1u << (dev & 31);
+    if (done.load(std::memory_order_acquire) & bit) return true;
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess) return false;
+    done.fetch_or(bit, std::memory_order_acq_rel);
+    return true;
+}
 
 constexpr int BM = 128;
 constexpr int BK = 32;                 // 32 FP32 = one 128-byte swizzle row
@@ -333,16 +348,17 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
+EncodeTiledFn lookup_encode_fn() {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+        return (EncodeTiledFn)p;
+    return nullptr;
+}
+
 EncodeTiledFn encode_fn() {
-    static EncodeTiledFn fn = nullptr;
-    if (!fn) {
-        cudaDriverEntryPointQueryResult q;
-        void* p = nullptr;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = (EncodeTiledFn)p;
-    }
+    static const EncodeTiledFn fn = lookup_encode_fn();   // thread-safe one-time initialisation
     return fn;
 }
 
@@ -366,13 +382,8 @@ slab_status launch_tc(cudaStream_t st, const TcGemmArgs& g, unsigned* err) {
     if (!make_map(&ta, g.A, g.M, g.K, g.lda, g.batch, g.sA, BM)) return SLAB_ECUDA;
     if (!make_map(&tb, g.B, g.N, g.K, g.ldb, g.batch, g.sB, BN)) return SLAB_ECUDA;
     const int smem = TcCfg<BN, SPLIT>::SMEM;
-    static bool attr_set = false;
-    if (!attr_set) {
-        if (cudaFuncSetAttribute(tc_gemm_kernel<BN, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
-            cudaSuccess)
-            return SLAB_ECUDA;
-        attr_set = true;
-    }
+    static std::atomic<uint32_t> attr_done(0);
+    if (!ensure_smem_attr(tc_gemm_kernel<BN, SPLIT>, smem, attr_done)) return SLAB_ECUDA;
     const int ks = g.ksplit > 1 ? g.ksplit : 1;
     dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, ks > 1 ? ks : g.batch);
     tc_gemm_kernel<BN, SPLIT><<<grid, 256, smem, st>>>(ta, tb, g.M, g.N, g.K, g.alpha, g.beta, g.C, g.ldc, g.sC,
@@ -634,13 +645,8 @@ slab_status ozaki_gemm(cudaStream_t st, int M, int N, int K, double alpha, const
     CUtensorMap ta, tb;
     if (!make_map(&ta, As, M, K, K, OZ_S, (int64_t)M * K, BM)) return SLAB_ECUDA;
     if (!make_map(&tb, Bs, N, K, K, OZ_S, (int64_t)N * K, OZ_BN)) return SLAB_ECUDA;
-    static bool attr_set = false;
-    if (!attr_set) {
-        if (cudaFuncSetAttribute(ozaki_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OzCfg::SMEM) !=
-            cudaSuccess)
-            return SLAB_ECUDA;
-        attr_set = true;
-    }
+    static std::atomic<uint32_t> attr_done(0);
+    if (!ensure_smem_attr(ozaki_gemm_kernel, OzCfg::SMEM, attr_done)) return SLAB_ECUDA;
     dim3 grid((N + OZ_BN - 1) / OZ_BN, (M + BM - 1) / BM);
     ozaki_gemm_kernel<<<grid, 256, OzCfg::SMEM, st>>>(ta, tb, M, N, K, alpha, ea, eb, C, ldc, lower_only, err);
     return cudaGetLastError() == cudaSuccess ? SLAB_OK : SLAB_ECUDA;
