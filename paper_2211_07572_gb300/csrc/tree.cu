@@ -345,6 +345,26 @@ struct SolveArgs {
 
 constexpr int KMAX = 64;   // right-hand sides handled per launch
 constexpr int LP = 36;     // smem row stride of the 32-row blocks read 4 at a time (16-byte aligned)
+constexpr int KP = KMAX + 4;   // smem row stride of the m x K blocks: 16-byte aligned, rows 4 banks apart
+
+// Lane -> (row i, right-hand side r) inside a warp tile of 8 rows x 4 right-hand sides, for the
+// copies between a [row][r] smem block of stride KP and global memory contiguous in the row
+// index: the smem words (KP i + r) of a warp (a half-warp for double) fall in distinct banks,
+// and the global side touches four (double: eight) 32-byte segments per warp.
+template <typename T>
+__device__ inline void lane_rows_rhs(int lane, int& i, int& r) {
+    if (sizeof(T) == 8) { i = (lane & 3) | ((lane >> 4) << 2); r = (lane >> 2) & 3; }
+    else { i = lane & 7; r = lane >> 3; }
+}
+
+// four consecutive smem values (16-byte aligned): one 128-bit store for float, two for double
+__device__ inline void sts4(float* p, const float v[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ inline void sts4(double* p, const double v[4]) {
+    reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+}
 
 // four consecutive smem values (16-byte aligned): one 128-bit load for float, two for double
 __device__ inline void lds4(const float* p, float v[4]) {
@@ -361,14 +381,15 @@ __device__ inline void lds4(const double* p, double v[4]) {
 // interface load Fi -= Z_I^T y.  grid = (node, chunk, slab).  The m x K products use 4 x 4
 // register blocks: thread (tA, tB) owns rows 4tA..4tA+3 and right-hand sides 4tB..4tB+3.
 template <typename T>
-__global__ void __launch_bounds__(TB_THREADS) tree_up_kernel(SolveArgs<T> P, int k, const double* F,
+__global__ void __launch_bounds__(TB_THREADS, sizeof(T) == 8 ? 5 : 8) tree_up_kernel(SolveArgs<T> P, int k, const double* F,
                                                              double fscale, int r0) {
-    __shared__ __align__(16) T Li[MAXM * SP];
-    __shared__ __align__(16) T Zt[MAXM * SP2];
-    __shared__ __align__(16) T y[MAXM * KMAX];
+    constexpr int ZP = 2 * MAXM + 4;   // Zt row stride: top half at 0, bottom half at MAXM
+    __shared__ __align__(16) T Li[MAXM * LP];      // Li[l][i] = (L^{-1})[i][l], zero outside m x m
+    __shared__ __align__(16) T Zt[MAXM * ZP];      // Zt[i][tb MAXM + a] = Z[i][tb m + a], zero for a >= m
+    __shared__ __align__(16) T y[MAXM * KP];
     // 32 interface columns of Z_I, staged per pass; Zt is no longer read by then
     T* const zs = Zt;
-    static_assert(SP2 >= LP, "staging area must fit in Zt");
+    static_assert(ZP >= LP, "staging area must fit in Zt");
     const TreeArgs<T>& A = P.tr;
     const int tid = threadIdx.x, nth = blockDim.x;
     const int tA = tid >> 4, tB = tid & 15;
@@ -389,23 +410,79 @@ __global__ void __launch_bounds__(TB_THREADS) tree_up_kernel(SolveArgs<T> P, int
     const int m2 = 2 * m;
     const T* Lg = A.linv(t, c);
     const T* Zg = A.ztb(t, c);
-    // rows of Li / Zt by warp (4 warps), columns by lane: no runtime division
-    for (int i = tid >> 5; i < m; i += nth >> 5) {
-        const int j = tid & 31;
-        if (j < m) Li[i * SP + j] = Lg[i * m + j];
-        if (j < m2) Zt[i * SP2 + j] = Zg[i * m2 + j];
-        if (j + 32 < m2) Zt[i * SP2 + j + 32] = Zg[i * m2 + j + 32];
+    // Zt: rows by warp, columns by lane.  Li transposed through tiles of JB columns x 32/JB rows
+    // per warp (jl fast): smem words (LP l + i) of a wavefront fall in distinct banks.  Each
+    // group of loads is issued into registers before its stores.
+    constexpr int NW = TB_THREADS / 32;
+    const int lane = tid & 31, warp = tid >> 5;
+    {
+        constexpr int JB = sizeof(T) == 8 ? 4 : 8;
+        constexpr int LIT = (MAXM / JB) * (MAXM / (32 / JB)) / NW;
+        const int jl = lane % JB, il = lane / JB;
+        T z0[MAXM / NW], z1[MAXM / NW], lr[LIT];
+#pragma unroll
+        for (int it = 0; it < MAXM / NW; ++it) {
+            const int i = warp + NW * it;
+            const bool ok = i < m && lane < m;
+            z0[it] = ok ? Zg[i * m2 + lane] : T(0);
+            z1[it] = ok ? Zg[i * m2 + m + lane] : T(0);
+        }
+#pragma unroll
+        for (int it = 0; it < LIT; ++it) {
+            const int wb = warp + NW * it;
+            const int l = JB * (wb % (MAXM / JB)) + jl, i = (32 / JB) * (wb / (MAXM / JB)) + il;
+            lr[it] = (i < m && l < m) ? Lg[i * m + l] : T(0);
+        }
+#pragma unroll
+        for (int it = 0; it < MAXM / NW; ++it) {
+            const int i = warp + NW * it;
+            Zt[i * ZP + lane] = z0[it];
+            Zt[i * ZP + MAXM + lane] = z1[it];
+        }
+#pragma unroll
+        for (int it = 0; it < LIT; ++it) {
+            const int wb = warp + NW * it;
+            const int l = JB * (wb % (MAXM / JB)) + jl, i = (32 / JB) * (wb / (MAXM / JB)) + il;
+            Li[l * LP + i] = lr[it];
+        }
     }
     const int64_t N = (int64_t)s * s;
-    for (int idx = tid; idx < MAXM * KMAX; idx += nth) {
-        const int r = idx / MAXM, i = idx % MAXM;      // consecutive threads read consecutive x
-        T g = T(0);
-        if (i < m && r < K) {
-            g = (T)F[(int64_t)(r0 + r) * N + (int64_t)(c - 1) * s + (x0 - 1 + i)] * (T)fscale;
-            if (alpha) g += P.gtb(t, alpha, 1)[i * kc + r];
-            if (beta) g += P.gtb(t, beta, 0)[i * kc + r];
+    {
+        constexpr int YIT = (MAXM / 8) * (KMAX / 4) / NW;
+        int il, rl;
+        lane_rows_rhs<T>(lane, il, rl);
+        T g[YIT];
+#pragma unroll
+        for (int it = 0; it < YIT; ++it) {
+            const int wb = warp + NW * it;
+            const int i = 8 * (wb % (MAXM / 8)) + il, r = 4 * (wb / (MAXM / 8)) + rl;
+            g[it] = (i < m && r < K)
+                        ? (T)F[(int64_t)(r0 + r) * N + (int64_t)(c - 1) * s + (x0 - 1 + i)] * (T)fscale
+                        : T(0);
         }
-        y[i * KMAX + r] = g;
+        if (alpha) {
+            const T* ga = P.gtb(t, alpha, 1);
+#pragma unroll
+            for (int it = 0; it < YIT; ++it) {
+                const int wb = warp + NW * it;
+                const int i = 8 * (wb % (MAXM / 8)) + il, r = 4 * (wb / (MAXM / 8)) + rl;
+                if (i < m && r < K) g[it] += ga[i * kc + r];
+            }
+        }
+        if (beta) {
+            const T* gb = P.gtb(t, beta, 0);
+#pragma unroll
+            for (int it = 0; it < YIT; ++it) {
+                const int wb = warp + NW * it;
+                const int i = 8 * (wb % (MAXM / 8)) + il, r = 4 * (wb / (MAXM / 8)) + rl;
+                if (i < m && r < K) g[it] += gb[i * kc + r];
+            }
+        }
+#pragma unroll
+        for (int it = 0; it < YIT; ++it) {
+            const int wb = warp + NW * it;
+            y[(8 * (wb % (MAXM / 8)) + il) * KP + 4 * (wb / (MAXM / 8)) + rl] = g[it];
+        }
     }
     __syncthreads();
     // y = Li g
@@ -417,9 +494,8 @@ __global__ void __launch_bounds__(TB_THREADS) tree_up_kernel(SolveArgs<T> P, int
             for (int p = 0; p < 4; ++p) acc[q][p] = T(0);
         for (int l = 0; l < m; ++l) {
             T gv[4], lv[4];
-            lds4(y + l * KMAX + 4 * tB, gv);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) lv[q] = (4 * tA + q < m) ? Li[(4 * tA + q) * SP + l] : T(0);
+            lds4(y + l * KP + 4 * tB, gv);
+            lds4(Li + l * LP + 4 * tA, lv);
 #pragma unroll
             for (int q = 0; q < 4; ++q)
 #pragma unroll
@@ -427,16 +503,14 @@ __global__ void __launch_bounds__(TB_THREADS) tree_up_kernel(SolveArgs<T> P, int
         }
         __syncthreads();
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-#pragma unroll
-            for (int p = 0; p < 4; ++p) y[(4 * tA + q) * KMAX + 4 * tB + p] = acc[q][p];
+        for (int q = 0; q < 4; ++q) sts4(y + (4 * tA + q) * KP + 4 * tB, acc[q]);
     }
     __syncthreads();
     if (blockIdx.y == 0) {
         T* yd = P.yv(t, c);
         for (int i = tid >> 6; i < m; i += nth >> 6) {
             const int r = tid & 63;
-            if (r < K) yd[i * kc + r] = y[i * KMAX + r];
+            if (r < K) yd[i * kc + r] = y[i * KP + r];
         }
         // condensed top / bottom loads: G_tb[a][r] = G_child[a][r] - sum_i Z[i][tb*m + a] y[i][r]
         for (int tb = 0; tb < 2; ++tb) {
@@ -448,9 +522,8 @@ __global__ void __launch_bounds__(TB_THREADS) tree_up_kernel(SolveArgs<T> P, int
                 for (int p = 0; p < 4; ++p) acc[q][p] = T(0);
             for (int i = 0; i < m; ++i) {
                 T yv[4], zv[4];
-                lds4(y + i * KMAX + 4 * tB, yv);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) zv[q] = (4 * tA + q < m) ? Zt[i * SP2 + tb * m + 4 * tA + q] : T(0);
+                lds4(y + i * KP + 4 * tB, yv);
+                lds4(Zt + i * ZP + tb * MAXM + 4 * tA, zv);
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
 #pragma unroll
@@ -482,14 +555,17 @@ __global__ void __launch_bounds__(TB_THREADS) tree_up_kernel(SolveArgs<T> P, int
             const int col = q0 + qq;
             const int sd = col / w, rr = lo + col % w - 1;
             const T* zcol = A.zi(t, k, sd) + rr;
-            T acc[8];
+            T acc[8], zv[MAXM];
 #pragma unroll
             for (int p = 0; p < 8; ++p) acc[p] = T(0);
-            for (int i = 0; i < m; ++i) {
-                const T z = zcol[(int64_t)i * A.s_pad];
+#pragma unroll
+            for (int i = 0; i < MAXM; ++i) zv[i] = i < m ? zcol[(int64_t)i * A.s_pad] : T(0);
+#pragma unroll
+            for (int i = 0; i < MAXM; ++i) {
+                if (i >= m) break;
 #pragma unroll
                 for (int p = 0; p < 8; ++p)
-                    if (p < RB) acc[p] += z * y[i * KMAX + r0b + p];
+                    if (p < RB) acc[p] += zv[i] * y[i * KP + r0b + p];
             }
             T* fo = P.fi(t, sd) + (int64_t)rr * kc;
 #pragma unroll
@@ -509,16 +585,20 @@ __global__ void __launch_bounds__(TB_THREADS) tree_up_kernel(SolveArgs<T> P, int
             rr[q] = ok[q] ? lo + qq % w - 1 : 0;
         }
         // stage Z_I[i][columns qa .. qa+31] (rows by warp, columns by lane: coalesced)
-        __syncthreads();
-        for (int i = tid >> 5; i < MAXM; i += nth >> 5) {
-            const int qq = qa + (tid & 31);
-            T z = T(0);
-            if (i < m && qq < qend) {
-                const int sdq = qq >= w, rq = lo + (sdq ? qq - w : qq) - 1;
-                z = A.zi(t, k, sdq)[(int64_t)i * A.s_pad + rq];
+        T zr[MAXM / NW];
+        {
+            const int qq = qa + lane;
+            const int sdq = qq >= w, rq = lo + (sdq ? qq - w : qq) - 1;
+            const T* zsrc = A.zi(t, k, sdq) + rq;
+#pragma unroll
+            for (int it = 0; it < MAXM / NW; ++it) {
+                const int i = warp + NW * it;
+                zr[it] = (i < m && qq < qend) ? zsrc[(int64_t)i * A.s_pad] : T(0);
             }
-            zs[i * LP + (tid & 31)] = z;
         }
+        __syncthreads();
+#pragma unroll
+        for (int it = 0; it < MAXM / NW; ++it) zs[(warp + NW * it) * LP + lane] = zr[it];
         __syncthreads();
         T acc[4][4];
 #pragma unroll
@@ -527,7 +607,7 @@ __global__ void __launch_bounds__(TB_THREADS) tree_up_kernel(SolveArgs<T> P, int
             for (int p = 0; p < 4; ++p) acc[q][p] = T(0);
         for (int i = 0; i < m; ++i) {
             T yv[4], zv[4];
-            lds4(y + i * KMAX + 4 * tB, yv);
+            lds4(y + i * KP + 4 * tB, yv);
             lds4(zs + i * LP + 4 * tA, zv);
 #pragma unroll
             for (int q = 0; q < 4; ++q)
@@ -561,17 +641,29 @@ inline int down_chunk(int nodes, int wmax) {
     return c;
 }
 template <typename T, bool INDEF>
-__global__ void __launch_bounds__(TB_THREADS) tree_down_kernel(SolveArgs<T> P, int k, double* U,
+__global__ void __launch_bounds__(TB_THREADS, sizeof(T) == 8 ? 5 : 8) tree_down_kernel(SolveArgs<T> P, int k, double* U,
                                                                int accumulate, int r0, T* ws,
                                                                unsigned* tickets, int dcw) {
     constexpr int CJ = sizeof(T) == 8 ? 16 : 32;   // columns per smem stage
+    constexpr int NW = TB_THREADS / 32;
+    // Staging tiles of 32 elements per warp: lane (jl, il) with jl fast.  zc[jj][i] and uc[jj][r]
+    // rows are LP (KP) words apart = 4 banks, so 8 columns x 4 rows (double: 4 x 8, 16 lanes
+    // per wavefront) hit distinct banks while the global side reads 32-byte segments along the
+    // column index.  Stages made only of top/bottom columns read x_top / x_bot, which are
+    // contiguous in r, with r on the lanes instead.  Each thread issues all loads of a stage
+    // into registers before the barrier that frees the smem tiles.
+    constexpr int JB = sizeof(T) == 8 ? 4 : 8;
+    constexpr int ZIT = (CJ / JB) * (MAXM / (32 / JB)) / NW;   // zc tiles per warp
+    constexpr int UIT = (CJ / JB) * (KMAX / (32 / JB)) / NW;   // uc tiles per warp
+    static_assert(UIT == (CJ / NW) * (KMAX / 32), "top/bottom staging covers the same tile count");
     __shared__ __align__(16) T Li[MAXM * LP];          // Li[l][i], zero for i >= m
-    __shared__ __align__(16) T V[MAXM * KMAX];
+    __shared__ __align__(16) T V[MAXM * KP];
     __shared__ __align__(16) T zc[CJ * LP];            // zc[jj][i]: column jj of the stage, rows i
-    __shared__ __align__(16) T uc[CJ * KMAX];
+    __shared__ __align__(16) T uc[CJ * KP];            // uc[jj][r]: column jj of the stage, rhs r
     __shared__ bool last;
     const TreeArgs<T>& A = P.tr;
-    const int tid = threadIdx.x, nth = blockDim.x;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
     const int tA = tid >> 4, tB = tid & 15;
     const int t = blockIdx.z;
     const int c = (2 * blockIdx.x + 1) << k;
@@ -585,11 +677,35 @@ __global__ void __launch_bounds__(TB_THREADS) tree_down_kernel(SolveArgs<T> P, i
     const int qa = blockIdx.y * dcw, qb = min(2 * w, qa + dcw);
     const int x0 = t * A.b + 1;
     const int m2 = 2 * m;
+    // acc accumulates -y + sum_j z_j u_j^T (y only in chunk 0), so that V = y - sum = -acc.
+    // The y loads and the Li staging are issued first and overlap the first stage.
     T acc[4][4];
+    if (blockIdx.y == 0) {
+        const T* yv = P.yv(t, c);
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
+        for (int q = 0; q < 4; ++q)
 #pragma unroll
-        for (int p = 0; p < 4; ++p) acc[q][p] = T(0);
+            for (int p = 0; p < 4; ++p) {
+                const int row = 4 * tA + q, r = 4 * tB + p;
+                acc[q][p] = (row < m && r < K) ? -yv[row * kc + r] : T(0);
+            }
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int p = 0; p < 4; ++p) acc[q][p] = T(0);
+    }
+    if (!INDEF) {
+        const T* Lg = A.linv(t, c);
+        T lr[MAXM / NW];
+#pragma unroll
+        for (int it = 0; it < MAXM / NW; ++it) {
+            const int i = warp + NW * it;
+            lr[it] = (i < m && lane < m) ? Lg[i * m + lane] : T(0);
+        }
+#pragma unroll
+        for (int it = 0; it < MAXM / NW; ++it) Li[(warp + NW * it) * LP + lane] = lr[it];
+    }
     const T* Zg = INDEF ? A.wtb(t, c) : A.ztb(t, c);    // SPD: Z; indefinite: W = S^{-1} B
     const T* xt = (lo - 1 >= 1) ? P.xs(t, lo - 1) : nullptr;
     const T* xb = (hi + 1 <= s) ? P.xs(t, hi + 1) : nullptr;
@@ -601,11 +717,14 @@ __global__ void __launch_bounds__(TB_THREADS) tree_down_kernel(SolveArgs<T> P, i
     const T* ZIr = (t < A.NS - 1) ? (INDEF ? A.wi(t, k, 1) : A.zi(t, k, 1)) + (lo - 1) : nullptr;
     const T* Ul = (t >= 1) ? P.xi(t - 1) + (lo - 1) : nullptr;
     const T* Ur = (t < A.NS - 1) ? P.xi(t) + (lo - 1) : nullptr;
+    const int jl = lane % JB, il = lane / JB;
     for (int v0 = 0; v0 < ntot; v0 += CJ) {
         const int nj = min(CJ, ntot - v0);
-        __syncthreads();
-        for (int idx = tid; idx < MAXM * CJ; idx += nth) {
-            const int i = idx / CJ, jj = idx % CJ;
+        T zr[ZIT], ur[UIT];
+#pragma unroll
+        for (int it = 0; it < ZIT; ++it) {
+            const int wb = warp + NW * it;
+            const int jj = JB * (wb % (CJ / JB)) + jl, i = (32 / JB) * (wb / (CJ / JB)) + il;
             const int col = v0 + jj;
             T z = T(0);
             if (jj < nj && i < m) {
@@ -618,45 +737,77 @@ __global__ void __launch_bounds__(TB_THREADS) tree_down_kernel(SolveArgs<T> P, i
                     if (zs) z = zs[(int64_t)i * A.s_pad + (right ? ic - w : ic)];
                 }
             }
-            zc[jj * LP + i] = z;
+            zr[it] = z;
         }
-        for (int idx = tid; idx < CJ * KMAX; idx += nth) {
-            const int jj = idx % CJ, r = idx / CJ;
-            const int col = v0 + jj;
-            T v = T(0);
-            if (jj < nj && r < K) {
-                if (col < ntb) {
-                    const T* xv = col < m ? xt : xb;
-                    if (xv) v = xv[(col < m ? col : col - m) * kc + r];
-                } else {
-                    const int ic = qa + col - ntb;
-                    const bool right = ic >= w;
-                    const T* us = right ? Ur : Ul;
-                    if (us) v = us[(int64_t)r * A.s_pad + (right ? ic - w : ic)];
-                }
+        const bool tb_only = v0 + CJ <= ntb;
+        if (tb_only) {
+#pragma unroll
+            for (int it = 0; it < UIT; ++it) {
+                const int jj = warp + NW * (it / (KMAX / 32)), r = lane + 32 * (it % (KMAX / 32));
+                const int col = v0 + jj;
+                const T* xv = col < m ? xt : xb;
+                ur[it] = (xv && r < K) ? xv[(col < m ? col : col - m) * kc + r] : T(0);
             }
-            uc[jj * KMAX + r] = v;
+        } else {
+#pragma unroll
+            for (int it = 0; it < UIT; ++it) {
+                const int wb = warp + NW * it;
+                const int jj = JB * (wb % (CJ / JB)) + jl, r = (32 / JB) * (wb / (CJ / JB)) + il;
+                const int col = v0 + jj;
+                T v = T(0);
+                if (jj < nj && r < K) {
+                    if (col < ntb) {
+                        const T* xv = col < m ? xt : xb;
+                        if (xv) v = xv[(col < m ? col : col - m) * kc + r];
+                    } else {
+                        const int ic = qa + col - ntb;
+                        const bool right = ic >= w;
+                        const T* us = right ? Ur : Ul;
+                        if (us) v = us[(int64_t)r * A.s_pad + (right ? ic - w : ic)];
+                    }
+                }
+                ur[it] = v;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int it = 0; it < ZIT; ++it) {
+            const int wb = warp + NW * it;
+            const int jj = JB * (wb % (CJ / JB)) + jl, i = (32 / JB) * (wb / (CJ / JB)) + il;
+            zc[jj * LP + i] = zr[it];
+        }
+        if (tb_only) {
+#pragma unroll
+            for (int it = 0; it < UIT; ++it)
+                uc[(warp + NW * (it / (KMAX / 32))) * KP + lane + 32 * (it % (KMAX / 32))] = ur[it];
+        } else {
+#pragma unroll
+            for (int it = 0; it < UIT; ++it) {
+                const int wb = warp + NW * it;
+                const int jj = JB * (wb % (CJ / JB)) + jl, r = (32 / JB) * (wb / (CJ / JB)) + il;
+                uc[jj * KP + r] = ur[it];
+            }
         }
         __syncthreads();
         for (int jj = 0; jj < nj; ++jj) {
             T zv[4], uv[4];
             lds4(zc + jj * LP + 4 * tA, zv);
-            lds4(uc + jj * KMAX + 4 * tB, uv);
+            lds4(uc + jj * KP + 4 * tB, uv);
 #pragma unroll
             for (int q = 0; q < 4; ++q)
 #pragma unroll
                 for (int p = 0; p < 4; ++p) acc[q][p] += zv[q] * uv[p];
         }
     }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-        for (int p = 0; p < 4; ++p) V[(4 * tA + q) * KMAX + 4 * tB + p] = acc[q][p];
-    __syncthreads();
     if (nch > 1) {
+        // partial of this chunk straight from the registers; the last CTA of the node adds the
+        // partials in chunk order (deterministic), loading a thread's 16 elements together
         T* wsn = ws + ((int64_t)(t * gridDim.x + blockIdx.x) * nch) * MAXM * KMAX;
-        for (int idx = tid; idx < MAXM * KMAX; idx += nth) wsn[(int64_t)blockIdx.y * MAXM * KMAX + idx] = V[idx];
+        T* wsc = wsn + (int64_t)blockIdx.y * MAXM * KMAX;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int p = 0; p < 4; ++p) wsc[(4 * tA + q) * KMAX + 4 * tB + p] = acc[q][p];
         __threadfence();
         __syncthreads();
         unsigned* tk = tickets + (int64_t)t * gridDim.x + blockIdx.x;
@@ -664,8 +815,6 @@ __global__ void __launch_bounds__(TB_THREADS) tree_down_kernel(SolveArgs<T> P, i
         __syncthreads();
         if (!last) return;
         __threadfence();
-        // chunk order fixed (deterministic); the 16 elements of a thread are loaded together so
-        // the loads of one chunk are in flight at once
         constexpr int PER = MAXM * KMAX / TB_THREADS;
         T v[PER];
 #pragma unroll
@@ -679,24 +828,21 @@ __global__ void __launch_bounds__(TB_THREADS) tree_down_kernel(SolveArgs<T> P, i
             for (int j = 0; j < PER; ++j) v[j] += ld[j];
         }
 #pragma unroll
-        for (int j = 0; j < PER; ++j) V[tid + j * TB_THREADS] = v[j];
+        for (int j = 0; j < PER; ++j) {
+            const int idx = tid + j * TB_THREADS;
+            V[(idx / KMAX) * KP + idx % KMAX] = -v[j];
+        }
         if (tid == 0) *tk = 0;
-    }
-    // finish the node: V = y - V; SPD: x = Li^T V, indefinite: x = V (y already holds S^{-1} g)
-    const T* yv = P.yv(t, c);
-    if (!INDEF) {
-        const T* Lg = A.linv(t, c);
-        for (int i = tid >> 5; i < MAXM; i += nth >> 5) {
-            const int j = tid & 31;
-            Li[i * LP + j] = (i < m && j < m) ? Lg[i * m + j] : T(0);
+    } else {
+        __syncthreads();   // zc / uc reads of the last stage are not affected; V is free
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const T nv[4] = {-acc[q][0], -acc[q][1], -acc[q][2], -acc[q][3]};
+            sts4(V + (4 * tA + q) * KP + 4 * tB, nv);
         }
     }
     __syncthreads();
-    for (int i = tid >> 6; i < m; i += nth >> 6) {          // r = lane pair index, no runtime division
-        const int r = tid & 63;
-        if (r < K) V[i * KMAX + r] = yv[i * kc + r] - V[i * KMAX + r];
-    }
-    __syncthreads();
+    // finish the node: V = y - sum; SPD: x = Li^T V, indefinite: x = V (y already holds S^{-1} g)
     if (!INDEF) {
 #pragma unroll
         for (int q = 0; q < 4; ++q)
@@ -705,7 +851,7 @@ __global__ void __launch_bounds__(TB_THREADS) tree_down_kernel(SolveArgs<T> P, i
         for (int l = 0; l < m; ++l) {                      // x[i] = sum_{l >= i} Li[l][i] V[l]
             T lv[4], vv[4];
             lds4(Li + l * LP + 4 * tA, lv);
-            lds4(V + l * KMAX + 4 * tB, vv);
+            lds4(V + l * KP + 4 * tB, vv);
 #pragma unroll
             for (int q = 0; q < 4; ++q)
 #pragma unroll
@@ -713,24 +859,26 @@ __global__ void __launch_bounds__(TB_THREADS) tree_down_kernel(SolveArgs<T> P, i
         }
         __syncthreads();
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-#pragma unroll
-            for (int p = 0; p < 4; ++p) V[(4 * tA + q) * KMAX + 4 * tB + p] = acc[q][p];
+        for (int q = 0; q < 4; ++q) sts4(V + (4 * tA + q) * KP + 4 * tB, acc[q]);
         __syncthreads();
     }
     T* xd = P.xs(t, c);
     const int64_t N = (int64_t)s * s;
-    for (int i = tid >> 6; i < m; i += nth >> 6) {
+    for (int i = tid >> 6; i < m; i += TB_THREADS >> 6) {
         const int r = tid & 63;
-        if (r < K) xd[i * kc + r] = V[i * KMAX + r];
+        if (r < K) xd[i * kc + r] = V[i * KP + r];
     }
-    for (int r = tid >> 5; r < K; r += nth >> 5) {      // consecutive lanes write consecutive x
-        const int i = tid & 31;
-        if (i < m) {
-            const double v = (double)V[i * KMAX + r];
-            double* up = U + (int64_t)(r0 + r) * N + (int64_t)(c - 1) * s + (x0 - 1 + i);
-            if (accumulate) *up += v;
-            else *up = v;
+    {
+        int ul, rl;
+        lane_rows_rhs<T>(lane, ul, rl);
+        for (int wb = warp; wb < (MAXM / 8) * (KMAX / 4); wb += NW) {
+            const int i = 8 * (wb % (MAXM / 8)) + ul, r = 4 * (wb / (MAXM / 8)) + rl;
+            if (i < m && r < K) {
+                const double v = (double)V[i * KP + r];
+                double* up = U + (int64_t)(r0 + r) * N + (int64_t)(c - 1) * s + (x0 - 1 + i);
+                if (accumulate) *up += v;
+                else *up = v;
+            }
         }
     }
 }
