@@ -398,21 +398,26 @@ def run_gpu(args):
     sampler.stop()
     clocks = sampler.summary()
 
-    # one instrumented step: phase split and per-kernel-class device time (events on the launch stream)
+    # phase split from one plain step (events on the launch stream only), then per-kernel-class
+    # device time from one profiled step (an event pair around every launch)
     t_f0 = torch.cuda.Event(enable_timing=True)
     t_fac = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     t_f0.record(stream)
-    s = solver(prec, rtol=W["rtol"], max_refine=40, profile=True, stage2=stage2, krylov=args.krylov,
-               interface_precision=iprec)
+    s = make()
     t_fac.record(stream)
-    _, rel1, it1 = s.solve(f, u, allow_noconv=True)
+    s.solve(f, u, allow_noconv=True)
     t_end.record(stream)
     torch.cuda.synchronize()
-    cls_ms, cls_cnt = s.profile_read()
     s.close()
     factor_ms = t_f0.elapsed_time(t_fac)
     solve_ms = t_fac.elapsed_time(t_end)
+    s = solver(prec, rtol=W["rtol"], max_refine=40, profile=True, stage2=stage2, krylov=args.krylov,
+               interface_precision=iprec)
+    _, rel1, it1 = s.solve(f, u, allow_noconv=True)
+    torch.cuda.synchronize()
+    cls_ms, cls_cnt = s.profile_read()
+    s.close()
     passes = it1 + 1
     work = work_model(n, b, k, passes, stage2, W["kind"])
     peaks = _peaks()

@@ -85,7 +85,6 @@ slab_status import_x(slab_handle* h, const double* in, int r0, int K) {
 slab_status ensure_workspace(slab_handle* h, int k) {
     const int kc = k < tree_kmax() ? k : tree_kmax();
     const TreeDims& d = h->td;
-    const int64_t N = d.N;
     static_assert(sizeof(double) == 8, "");
     if (h->kcap < kc) {
         const int64_t nodes = (int64_t)d.NS * (d.s + 1);
@@ -123,7 +122,7 @@ slab_status ensure_workspace(slab_handle* h, int k) {
         SLAB_CK(h, cudaMemsetAsync(h->wVtk, 0, nt * sizeof(unsigned), h->stream));
     }
     if (!h->wPart) {
-        TRY(dalloc(h, &h->wPart, (int64_t)(d.s_pad / SLAB_TILE) * SLAB_SPLITK * SLAB_TILE * SLAB_TILE * 8));
+        TRY(dalloc(h, &h->wPart, splitk_part_bytes(d.s_pad)));
         void* tk = nullptr;
         TRY(dalloc(h, &tk, (size_t)(d.s_pad / SLAB_TILE) * sizeof(unsigned)));
         h->wTickets = (unsigned*)tk;

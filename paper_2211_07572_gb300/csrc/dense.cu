@@ -387,8 +387,11 @@ slab_status gemm_tn<float>(slab_handle* h, int cls, int M, int N, int K, float a
     g.batch = 1; g.sA = g.sB = g.sC = 0;
     g.ksplit = 1; g.part = nullptr;
     if (N <= 64 && !lower_only && h->wPart) {     // skinny: split K over CTAs
+        const int64_t cap = (int64_t)splitk_part_bytes(h->td.s_pad) / sizeof(float);
         int ks = 1;
-        while (2 * ks <= SLAB_SPLITK && (M + 127) / 128 * ks < 148 && K % (2 * ks * 32) == 0) ks *= 2;
+        while (2 * ks <= SLAB_SPLITK && (M + 127) / 128 * ks < 148 && K % (2 * ks * 32) == 0 &&
+               (int64_t)2 * ks * M * N <= cap)
+            ks *= 2;
         g.ksplit = ks;
         g.part = (float*)h->wPart;
     }
@@ -724,7 +727,7 @@ __global__ void __launch_bounds__(256) gj_panel_apply_kernel(T* Gt, int64_t ldt,
     extern __shared__ unsigned char gj_smem[];
     T (*Ai)[65] = reinterpret_cast<T (*)[65]>(gj_smem);
     T (*Bc)[65] = Ai + 64;
-    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+    const int tid = threadIdx.x;
     if (blockIdx.y == 1) {
         const int64_t rows = 2 * (int64_t)sp;
         for (int64_t idx = (int64_t)blockIdx.x * 256 + tid; idx < rows * 64; idx += (int64_t)gridDim.x * 256) {
@@ -829,6 +832,16 @@ slab_status gemm_tn_batched<float>(slab_handle* h, int cls, int M, int N, int K,
     g.transC = transC; g.split = h->tf32_now ? 0 : 1; g.lower_only = lower_only;
     g.batch = batch; g.sA = sA; g.sB = sB; g.sC = sC;
     g.ksplit = 1; g.part = nullptr;
+    if (N <= 64 && !lower_only && h->wPart) {     // skinny batches that leave SMs idle: split K as well
+        const int64_t tiles = (int64_t)((M + 127) / 128) * ((N + 63) / 64) * batch;
+        const int64_t cap = (int64_t)splitk_part_bytes(h->td.s_pad) / sizeof(float);
+        int ks = 1;
+        while (2 * ks <= SLAB_SPLITK && tiles * ks < 148 && K % (2 * ks * 32) == 0 &&
+               (int64_t)2 * ks * batch * M * N <= cap)
+            ks *= 2;
+        g.ksplit = ks;
+        g.part = (float*)h->wPart;
+    }
     const slab_status st = tc_gemm(h->stream, g, h->dstatus);
     if (st == SLAB_ECUDA && h->err == SLAB_OK) h->err = SLAB_ECUDA;
     return st;
@@ -1036,15 +1049,13 @@ template <typename T>
 slab_status sweep_factor(slab_handle* h) {
     if (h->kind == SLAB_HELMHOLTZ) return sweep_factor_indef<T>(h);
     if (h->stage2) return cr_factor<T>(h);
-    const int NI = h->td.NI, sp = h->td.s_pad, nt = h->nt;
+    const int NI = h->td.NI, sp = h->td.s_pad;
     const int64_t blk = (int64_t)sp * sp;
     T* Tb = (T*)h->Tb;
     T* To = (T*)h->To;
     T* F = (T*)h->Fct;
     T* Lin = (T*)h->Linv;
     T* Yn = (T*)h->Y;
-    const size_t smem = 3 * TL * TLP * sizeof(T);
-    SLAB_CK(h, cudaFuncSetAttribute(panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     slab_status st;
     for (int j = 0; j < NI; ++j) {
         T* W = F + j * 3 * blk;
@@ -1064,22 +1075,7 @@ slab_status sweep_factor(slab_handle* h) {
         SLAB_CK_LAUNCH(h);
         if (hasY && (st = transpose<T>(h, To + j * blk, Yt, sp))) return st;      // T_{j+1,j}
         const int lt0 = (hasY ? 2 : 1) * sp;         // first row of the identity block
-        for (int kb = 0; kb < nt; ++kb) {
-            const int rows = lt0 + (kb + 1) * TL;      // identity rows below are still zero here
-            const int nrt = rows / TL - kb - 1;
-            {
-                SLAB_PROF(h, KC_PANEL);
-                panel_kernel<T><<<nrt, 256, smem, h->stream>>>(W, sp, kb, h->dstatus, 0);
-            }
-            SLAB_CK_LAUNCH(h);
-            const int c0 = (kb + 1) * TL;
-            if (c0 < sp) {
-                const T* P = W + (int64_t)c0 * sp + (int64_t)kb * TL;             // panel rows below the diagonal
-                if ((st = gemm_tn<T>(h, KC_TRAIL, rows - c0, sp - c0, TL, T(-1), P, sp, P, sp, T(1), W + (int64_t)c0 * sp + c0,
-                                     sp, 0, 1)))
-                    return st;
-            }
-        }
+        if ((st = dense_tall_cholesky<T>(h, W, sp, lt0, 1, 0))) return st;
         if ((st = transpose<T>(h, LT, Lin + j * blk, sp))) return st;
         if (hasY && (st = transpose<T>(h, Yt, Yn + j * blk, sp))) return st;
     }
@@ -1175,13 +1171,12 @@ __global__ void set_identity_batched_kernel(T* B, int s_pad, int64_t stride) {
 // [D ; I] in the work buffer (2 s_pad x s_pad per block).
 template <typename T>
 static slab_status cr_potrf_batch(slab_handle* h, int o0, int st_blk, int nb) {
-    const int sp = h->td.s_pad, nt = h->nt;
+    const int sp = h->td.s_pad;
     const int64_t blk = (int64_t)sp * sp;
     T* D = (T*)h->crD;
     T* W = (T*)h->crW;
     T* LT = (T*)h->crLT;
     T* Lin = (T*)h->Linv;
-    const size_t smem = 3 * TL * TLP * sizeof(T);
     const int64_t sb = (int64_t)st_blk * blk;
     for (int i = 0; i < nb; ++i)
         SLAB_CK(h, cudaMemcpyAsync(W + i * 2 * blk, D + o0 * blk + i * sb, blk * sizeof(T), cudaMemcpyDeviceToDevice,
@@ -1193,22 +1188,7 @@ static slab_status cr_potrf_batch(slab_handle* h, int o0, int st_blk, int nb) {
     }
     SLAB_CK_LAUNCH(h);
     slab_status st;
-    for (int kb = 0; kb < nt; ++kb) {
-        const int rows = sp + (kb + 1) * TL;          // identity rows below are still zero here
-        const int nrt = rows / TL - kb - 1;
-        {
-            SLAB_PROF(h, KC_PANEL);
-            panel_kernel<T><<<dim3(nrt, nb), 256, smem, h->stream>>>(W, sp, kb, h->dstatus, 2 * blk);
-        }
-        SLAB_CK_LAUNCH(h);
-        const int c0 = (kb + 1) * TL;
-        if (c0 < sp) {
-            const T* P = W + (int64_t)c0 * sp + (int64_t)kb * TL;
-            if ((st = gemm_tn_batched<T>(h, KC_TRAIL, rows - c0, sp - c0, TL, T(-1), P, sp, 2 * blk, P, sp, 2 * blk,
-                                         T(1), W + (int64_t)c0 * sp + c0, sp, 2 * blk, 0, 1, nb)))
-                return st;
-        }
-    }
+    if ((st = dense_tall_cholesky<T>(h, W, sp, sp, nb, 2 * blk))) return st;
     for (int i = 0; i < nb; ++i)
         SLAB_CK(h, cudaMemcpyAsync(LT + o0 * blk + i * sb, W + i * 2 * blk + blk, blk * sizeof(T),
                                    cudaMemcpyDeviceToDevice, h->stream));
@@ -1393,8 +1373,13 @@ slab_status dense_copy(slab_handle* h, const T* in, int64_t sin, T* out, int64_t
 // Cholesky of the leading ncols x ncols block of a batch of tall matrices (row-major, ld = ncols,
 // bstride apart) whose rows below are eliminated with it: rows [ncols, ident0) receive B^T L^{-T},
 // rows [ident0, ident0 + ncols), which must hold the identity, receive L^{-T}.
+// Right-looking with two block levels: 64-column panels (panel_kernel); after each panel, the
+// update of the remaining columns of its outer block of OB panels only; when an outer block is
+// complete, one rank-(OB 64) update of every column to its right.  The trailing matrix is thus
+// read and written once per outer block instead of once per panel.
 template <typename T>
 slab_status dense_tall_cholesky(slab_handle* h, T* W, int ncols, int ident0, int batch, int64_t bstride) {
+    constexpr int OB = 4;                              // panels per outer block
     const size_t smem = 3 * TL * TLP * sizeof(T);
     SLAB_CK(h, cudaFuncSetAttribute(panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     slab_status st;
@@ -1408,11 +1393,18 @@ slab_status dense_tall_cholesky(slab_handle* h, T* W, int ncols, int ident0, int
             panel_kernel<T><<<dim3(nrt, nb), 256, smem, h->stream>>>(W + b0 * bstride, ncols, kb, h->dstatus, bstride);
             SLAB_CK_LAUNCH(h);
         }
-        const int c0 = (kb + 1) * TL;
-        if (c0 < ncols) {
+        const int kb0 = kb - kb % OB, kend = std::min(nt, kb0 + OB);     // this outer block: panels [kb0, kend)
+        const int c0 = (kb + 1) * TL, cend = kend * TL;
+        if (c0 < cend) {                               // rest of the outer block, rank 64
             const T* P = W + (int64_t)c0 * ncols + (int64_t)kb * TL;
-            if ((st = dense_gemm<T>(h, KC_TRAIL, rows - c0, ncols - c0, TL, T(-1), P, ncols, bstride, P, ncols, bstride,
+            if ((st = dense_gemm<T>(h, KC_TRAIL, rows - c0, cend - c0, TL, T(-1), P, ncols, bstride, P, ncols, bstride,
                                     T(1), W + (int64_t)c0 * ncols + c0, ncols, bstride, 0, 1, batch)))
+                return st;
+        } else if (cend < ncols) {                     // outer block done: columns to its right, rank (kend-kb0) 64
+            const T* P = W + (int64_t)cend * ncols + (int64_t)kb0 * TL;
+            if ((st = dense_gemm<T>(h, KC_TRAIL, rows - cend, ncols - cend, (kend - kb0) * TL, T(-1), P, ncols, bstride,
+                                    P, ncols, bstride, T(1), W + (int64_t)cend * ncols + cend, ncols, bstride, 0, 1,
+                                    batch)))
                 return st;
         }
     }

@@ -25,6 +25,12 @@
 #define SLAB_MAXM 32          // largest slab interior width handled by the 2-D tree kernels
 #define SLAB_SPLITK 8         // K splits of the skinny solve products
 
+// Bytes of the split-K partial-sum buffer of a handle whose interfaces have s_pad nodes:
+// [s_pad/64][SLAB_SPLITK][64][64] FP64 tiles (FP32 products use it as a flat float array).
+inline size_t splitk_part_bytes(int s_pad) {
+    return (size_t)(s_pad / SLAB_TILE) * SLAB_SPLITK * SLAB_TILE * SLAB_TILE * 8;
+}
+
 // Device-side status word bits (set by kernels, read by the host after a phase).
 #define SLAB_DEV_NOTSPD 1u    // a Cholesky pivot was <= 0 or not finite
 #define SLAB_DEV_TIMEOUT 2u   // a bounded device-side wait gave up (tensor-core pipeline)

@@ -88,15 +88,19 @@ __global__ void __launch_bounds__(256) stencil2d_kernel(int n, int k, const doub
                     const double un = y < s ? uq[o + s] : 0.0;
                     const double uw = x > 1 ? uq[o - 1] : 0.0;
                     const double ue = x < s ? uq[o + 1] : 0.0;
-                    const double Au = dg * wc[q] - aw * uw - ae * ue - as * wu[q] - an * un;
                     if (RESID) {
+                        // r = f - A u as one chain of five FMAs (the kernel is bound by the FP64 pipe)
                         const double fv = f[(q0 + q) * N + o];
-                        const double rv = fv - Au;
+                        double rv = fma(aw, uw, fv);
+                        rv = fma(ae, ue, rv);
+                        rv = fma(as, wu[q], rv);
+                        rv = fma(an, un, rv);
+                        rv = fma(-dg, wc[q], rv);
                         r[(q0 + q) * N + o] = rv;
                         rr2[q] += rv * rv;
                         if (NORMF) ff2[q] += fv * fv;
                     } else {
-                        r[(q0 + q) * N + o] = Au;
+                        r[(q0 + q) * N + o] = dg * wc[q] - aw * uw - ae * ue - as * wu[q] - an * un;
                     }
                     wu[q] = wc[q];
                     wc[q] = un;

@@ -141,10 +141,10 @@ __global__ void __launch_bounds__(256, 1)
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int abort_flag;
 
-    // with ksplit > 1 (single product), blockIdx.z is the K split: K range [zs K/ksplit, (zs+1) K/ksplit)
+    // blockIdx.z = batch index * ksplit + K split; split zs covers K range [zs K/ksplit, (zs+1) K/ksplit)
     const int bn = blockIdx.x, bm = blockIdx.y;
-    const int zs = ksplit > 1 ? (int)blockIdx.z : 0;
-    const int bz = ksplit > 1 ? 0 : (int)blockIdx.z;
+    const int zs = (int)blockIdx.z % ksplit;
+    const int bz = (int)blockIdx.z / ksplit;
     if (lower_only && bn * BN >= (bm + 1) * BM) return;        // tile strictly above the diagonal
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nk = K / ksplit / BK;
@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(256, 1)
                 }
                 if (row < M) {
                     if (ksplit > 1) {                            // raw partial sums, reduced later
-                        float* pb = part + (int64_t)zs * M * N;
+                        float* pb = part + (int64_t)blockIdx.z * M * N;   // [batch][ksplit][M N]
 #pragma unroll
                         for (int j = 0; j < 32; ++j) {
                             const int col = bn * BN + cc * 32 + j;
@@ -330,18 +330,22 @@ __global__ void __launch_bounds__(256, 1)
     }
 }
 
-// C = alpha sum_s part[s] + beta C, part laid out like C (transC: [N][M], else [M][N]), fixed order.
+// C_b = alpha sum_s part[b][s] + beta C_b for the batch matrices b (sC apart); part laid out like C
+// (transC: [N][M], else [M][N]); the splits are added in a fixed order.
 __global__ void splitk_reduce_kernel(int M, int N, int ks, const float* __restrict__ part, float alpha, float beta,
-                                     float* C, int64_t ldc, int transC) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+                                     float* C, int64_t ldc, int transC, int64_t sC, int batch) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t tot = (int64_t)M * N;
-    if (e >= tot) return;
+    if (g >= tot * batch) return;
+    const int64_t b = g / tot, e = g % tot;
+    const float* pb = part + b * ks * tot + e;
     float v = 0.f;
-    for (int s = 0; s < ks; ++s) v += part[(int64_t)s * tot + e];
+    for (int s = 0; s < ks; ++s) v += pb[(int64_t)s * tot];
     int64_t idx;
     if (transC) idx = (e / M) * ldc + (e % M);          // e = col * M + row
     else idx = (e / N) * ldc + (e % N);                 // e = row * N + col
-    C[idx] = alpha * v + (beta != 0.f ? beta * C[idx] : 0.f);
+    float* Cb = C + b * sC;
+    Cb[idx] = alpha * v + (beta != 0.f ? beta * Cb[idx] : 0.f);
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -385,14 +389,14 @@ slab_status launch_tc(cudaStream_t st, const TcGemmArgs& g, unsigned* err) {
     static std::atomic<uint32_t> attr_done(0);
     if (!ensure_smem_attr(tc_gemm_kernel<BN, SPLIT>, smem, attr_done)) return SLAB_ECUDA;
     const int ks = g.ksplit > 1 ? g.ksplit : 1;
-    dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, ks > 1 ? ks : g.batch);
+    dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, ks * g.batch);
     tc_gemm_kernel<BN, SPLIT><<<grid, 256, smem, st>>>(ta, tb, g.M, g.N, g.K, g.alpha, g.beta, g.C, g.ldc, g.sC,
                                                        g.transC, g.lower_only, ks, g.part, err);
     if (cudaGetLastError() != cudaSuccess) return SLAB_ECUDA;
     if (ks > 1) {
-        const int64_t tot = (int64_t)g.M * g.N;
+        const int64_t tot = (int64_t)g.M * g.N * g.batch;
         splitk_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(g.M, g.N, ks, g.part, g.alpha, g.beta,
-                                                                           g.C, g.ldc, g.transC);
+                                                                           g.C, g.ldc, g.transC, g.sC, g.batch);
         if (cudaGetLastError() != cudaSuccess) return SLAB_ECUDA;
     }
     return SLAB_OK;
@@ -601,7 +605,7 @@ __global__ void ozaki_split_kernel(const double* __restrict__ X, int64_t ldx, in
 slab_status tc_gemm(cudaStream_t st, const TcGemmArgs& g, unsigned* err) {
     if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return SLAB_OK;
     if (g.K <= 0 || g.K % BK) return SLAB_EINVAL;
-    if (g.ksplit > 1 && (g.batch != 1 || g.K % (g.ksplit * BK) || !g.part)) return SLAB_EINVAL;
+    if (g.ksplit > 1 && (g.K % (g.ksplit * BK) || !g.part || g.lower_only)) return SLAB_EINVAL;
     if (g.lda % 4 || g.ldb % 4 || g.sA % 4 || g.sB % 4) return SLAB_EINVAL;       // 16-byte strides
     if (((uintptr_t)g.A & 15) || ((uintptr_t)g.B & 15)) return SLAB_EINVAL;      // 16-byte base
     const bool narrow = g.N <= 64;

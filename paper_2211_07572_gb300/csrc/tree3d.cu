@@ -653,7 +653,7 @@ slab_status tree3d_up_gather(slab_handle* h, const double* F, double fscale, int
 template <typename T>
 slab_status tree3d_down_scatter(slab_handle* h, double* U, int accumulate, int r0, int K) {
     const Tree3Plan& P = *h->t3plan;
-    const int Mp = P.Mp, NS = h->td.NS, NI = h->td.NI, sp = h->td.s_pad, s = h->td.s, kc = h->kcap;
+    const int Mp = P.Mp, NS = h->td.NS, NI = h->td.NI, s = h->td.s, kc = h->kcap;
     const int64_t mm = (int64_t)Mp * Mp;
     T* y = (T*)h->t3y;
     T* X = (T*)h->t3x;
