@@ -218,10 +218,14 @@ slab_status slab_get_T_block(slab_handle* h, int which, int q, double* out);
  * tensor memory).  A: M x K, B: N x K, C: M x N, all FP32 row-major on the device with
  * leading dimensions lda, ldb, ldc (elements); trans_c = 1 writes C^T instead (C is then
  * N x M with leading dimension ldc).  split = 1 multiplies with three TF32 products
- * (hi*hi + hi*lo + lo*hi), which keeps FP32 accuracy; split = 0 uses one TF32 product.
- * Requires K % 32 == 0, lda, ldb multiples of 4 and 16-byte aligned A and B (SLAB_EINVAL
- * otherwise).  dev_err: device word, bit 2 is set if a bounded device wait gave up.
- * Asynchronous on stream.  Used in the paper's sense by Algorithm 1 (Sec. 4) products.
+ * (hi*hi + hi*lo + lo*hi), which keeps FP32 accuracy; split = 0 uses one TF32 product;
+ * split = 2 scales every row of A and B by a power of two into (-1, 1), splits it into FP16
+ * hi + lo and multiplies with three FP16 products (FP32 accuracy at twice the TF32 rate; needs
+ * K % 64 == 0; scratch of about 4 (M + N) K bytes comes from the stream-ordered allocator,
+ * SLAB_ENOMEM if it cannot).  The factorization uses split 2 for its Schur and trailing
+ * products.  Requires K % 32 == 0, lda, ldb multiples of 4 and 16-byte aligned A and B
+ * (SLAB_EINVAL otherwise).  dev_err: device word, bit 2 is set if a bounded device wait gave
+ * up.  Asynchronous on stream.  Used in the paper's sense by Algorithm 1 (Sec. 4) products.
  */
 slab_status slab_tc_gemm(int M, int N, int K, float alpha, const float* A, int64_t lda, const float* B,
                          int64_t ldb, float beta, float* C, int64_t ldc, int trans_c, int split,

@@ -374,7 +374,7 @@ void slab_destroy(slab_handle* h) {
     void* p;
     p = h->AX; dfree(p); p = h->AY; dfree(p); p = h->DG; dfree(p); p = h->kappa; dfree(p);
     dfree(h->tLinv); dfree(h->tZtb); dfree(h->tRtb); dfree(h->tZI); dfree(h->tRI);
-    dfree(h->tWtb); dfree(h->tWI); dfree(h->ToT); dfree(h->dscratch); dfree(h->gjw); dfree(h->ozw);
+    dfree(h->tWtb); dfree(h->tWI); dfree(h->ToT); dfree(h->dscratch); dfree(h->gjw); dfree(h->ozw); dfree(h->w16);
     p = h->AZ; dfree(p);
     dfree(h->t3Lin); dfree(h->t3LT); dfree(h->t3Ztb); dfree(h->t3ZtbT); dfree(h->t3ZIT); dfree(h->t3ZI);
     dfree(h->t3Rtb); dfree(h->t3RI); dfree(h->t3W);
@@ -514,6 +514,12 @@ slab_status slab_factor(const slab_grid* grid, const slab_coeffs* co, int b, con
     }
     ALLOC(h->dscratch, 256);
     if (h->fp64tc) ALLOC(h->ozw, ozaki_work_bytes(2 * (int64_t)d.s_pad + 128, 3 * (int64_t)d.s_pad, 64));
+    if (!h->tf32 && co->kind != SLAB_HELMHOLTZ &&
+        (h->prec2 == SLAB_PREC_FP32 || (h->dim == 3 && h->prec == SLAB_PREC_FP32))) {
+        // largest FP16 three-product of the factor: the batched Stage-2 Schur products (s_pad^3)
+        h->w16_bytes = f16x3_work_bytes(d.s_pad, d.s_pad, d.s_pad, h->stage2 ? cr_max_batch(d.NI) : 1, false);
+        ALLOC(h->w16, h->w16_bytes);
+    }
     ALLOC(h->Linv, d.NI * blk * R2);
     if (!h->stage2) ALLOC(h->Y, (d.NI - 1) * blk * R2);
     ALLOC(h->dstatus, sizeof(unsigned));
@@ -541,6 +547,9 @@ slab_status slab_factor(const slab_grid* grid, const slab_coeffs* co, int b, con
     dfree(h->Tb1);                                     // mixed-mode assembly buffers
     dfree(h->To1);
     h->Tb1 = h->To1 = nullptr;
+    dfree(h->w16);                                     // factor-only product work
+    h->w16 = nullptr;
+    h->w16_bytes = 0;
     dfree(h->t3Rtb);                                   // 3-D factor-only arrays
     dfree(h->t3RI);
     dfree(h->t3W);

@@ -370,6 +370,17 @@ slab_status transpose(slab_handle* h, const T* in, T* out, int n) {
     return transpose_batched<T>(h, in, 0, out, 0, n, 1);
 }
 
+// The factor's Schur and trailing products (FP32, 3xTF32 accuracy requested) run as three FP16
+// products of row-scaled hi/lo splits when the handle holds a large enough work buffer.
+inline bool use_f16x3(slab_handle* h, int cls, TcGemmArgs& g) {
+    if (!h->w16 || g.split != 1 || (cls != KC_SYRK && cls != KC_TRAIL) || g.K % 64) return false;
+    if (f16x3_work_bytes(g.M, g.N, g.K, g.batch, f16x3_shared(g)) > h->w16_bytes) return false;
+    g.split = 2;
+    g.w16 = h->w16;
+    g.w16_bytes = h->w16_bytes;
+    return true;
+}
+
 // C = beta C + alpha A B^T on the unit of this precision: tensor cores for FP32, SIMT for FP64.
 template <typename T>
 slab_status gemm_tn(slab_handle* h, int cls, int M, int N, int K, T alpha, const T* A, int64_t lda, const T* B,
@@ -386,7 +397,10 @@ slab_status gemm_tn<float>(slab_handle* h, int cls, int M, int N, int K, float a
     g.transC = transC; g.split = h->tf32_now ? 0 : 1; g.lower_only = lower_only;
     g.batch = 1; g.sA = g.sB = g.sC = 0;
     g.ksplit = 1; g.part = nullptr;
-    if (N <= 64 && !lower_only && h->wPart) {     // skinny: split K over CTAs
+    g.w16 = nullptr; g.w16_bytes = 0;
+    if (use_f16x3(h, cls, g)) {
+        // FP16 three-product path (factor products)
+    } else if (N <= 64 && !lower_only && h->wPart) {     // skinny: split K over CTAs
         const int64_t cap = (int64_t)splitk_part_bytes(h->td.s_pad) / sizeof(float);
         int ks = 1;
         while (2 * ks <= SLAB_SPLITK && (M + 127) / 128 * ks < 148 && K % (2 * ks * 32) == 0 &&
@@ -832,7 +846,10 @@ slab_status gemm_tn_batched<float>(slab_handle* h, int cls, int M, int N, int K,
     g.transC = transC; g.split = h->tf32_now ? 0 : 1; g.lower_only = lower_only;
     g.batch = batch; g.sA = sA; g.sB = sB; g.sC = sC;
     g.ksplit = 1; g.part = nullptr;
-    if (N <= 64 && !lower_only && h->wPart) {     // skinny batches that leave SMs idle: split K as well
+    g.w16 = nullptr; g.w16_bytes = 0;
+    if (use_f16x3(h, cls, g)) {
+        // FP16 three-product path (factor products)
+    } else if (N <= 64 && !lower_only && h->wPart) {     // skinny batches that leave SMs idle: split K as well
         const int64_t tiles = (int64_t)((M + 127) / 128) * ((N + 63) / 64) * batch;
         const int64_t cap = (int64_t)splitk_part_bytes(h->td.s_pad) / sizeof(float);
         int ks = 1;

@@ -62,6 +62,8 @@ struct slab_handle {
     int fp64tc;               // SLAB_PREC_FP64_TC interface: FP64 products of Stage 2 on the tensor cores
     int fp64tc_now;           // set while the interface elimination runs
     void* ozw;                // work area of those products
+    void* w16;                // FP32 factor: operand splits of the FP16 three-product path (factor only)
+    size_t w16_bytes;
     size_t rsz2;              // bytes of the Stage-2 scalar
     void *Tb1, *To1;          // mixed mode: T assembled in the Stage-1 scalar (factor only)
     void *wX2, *wZ2;          // mixed mode: interface vectors in the Stage-2 scalar
@@ -251,13 +253,22 @@ struct TcGemmArgs {
     const float* B; int64_t ldb;
     float* C; int64_t ldc;
     int transC;          // 1: write C^T, i.e. C[col * ldc + row]
-    int split;           // 1: 3xTF32 (FP32 accuracy), 0: plain TF32
+    int split;           // 0: plain TF32; 1: 3xTF32; 2: three FP16 products of row-scaled hi/lo splits
+                         // (both FP32-level accuracy; 2 needs K % 64 == 0 and the work buffer w16)
     int lower_only;      // skip 128 x BN tiles strictly above the diagonal
     int batch;           // independent products, A/B/C batch strides sA/sB/sC (elements)
     int64_t sA, sB, sC;
-    int ksplit;          // > 1: K split over CTAs, partial sums in part[ksplit][M][N] (batch must be 1)
+    int ksplit;          // > 1: K split over CTAs, partial sums in part[batch][ksplit][M][N] (split 0 / 1)
     float* part;
+    void* w16;           // split 2: operand splits and exponents, f16x3_work_bytes(M, N, K, batch, shared)
+    size_t w16_bytes;
 };
+// Work bytes of the split-2 product; shared: B is the first N rows of A (one split serves both).
+size_t f16x3_work_bytes(int64_t M, int64_t N, int64_t K, int batch, bool shared);
+// True when B can reuse the split of A: same array, strides and batch stride, N <= M.
+inline bool f16x3_shared(const TcGemmArgs& g) {
+    return g.A == g.B && g.lda == g.ldb && g.sA == g.sB && g.N <= g.M;
+}
 size_t ozaki_work_bytes(int64_t M, int64_t N, int K);
 slab_status ozaki_gemm(cudaStream_t st, int M, int N, int K, double alpha, const double* A, int64_t lda,
                        const double* B, int64_t ldb, double* C, int64_t ldc, int lower_only, void* work,

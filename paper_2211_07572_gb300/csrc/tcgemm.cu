@@ -13,6 +13,7 @@
 // Every wait is bounded; a wait that runs out sets bit 2 of *err, the CTA stops issuing work,
 // waits (bounded) for the copies it issued, frees its TMEM and returns.
 #include <cuda.h>
+#include <cuda_fp16.h>
 
 #include <atomic>
 
@@ -599,18 +600,298 @@ __global__ void ozaki_split_kernel(const double* __restrict__ X, int64_t ldx, in
     }
 }
 
+// ------------------------------------------------------------------ FP32-accurate product on FP16 MMAs
+// C = alpha A B^T + beta C for FP32 A (M x K) and B (N x K) with K % 64 == 0.  A pre-pass scales
+// every row of A and B by a power of two, x = 2^e_r x', |x'| < 1 (e_r from the row's largest
+// magnitude), and splits x' = hi + lo with hi = fp16(x') and lo = fp16(x' - hi): FP16 keeps 11
+// significant bits, as TF32 does, so hi + lo carries x' to about 2^-22 (below 2^-24 of the row's
+// largest magnitude where lo is subnormal).  The kernel accumulates A_hi B_hi + A_hi B_lo +
+// A_lo B_hi in FP32 (TMEM) on tcgen05.mma.kind::f16, twice the TF32 rate and half the shared-memory
+// bytes per multiply-add, with no conversion work inside the kernel; the epilogue applies
+// alpha 2^(ea_i + eb_j).  Same warp roles and bounded waits as tc_gemm_kernel, minus the split warps.
+constexpr int BK16 = 64;               // 64 FP16 = one 128-byte swizzle row
+
+__device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+        ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+// Instruction descriptor, kind::f16: D = F32, A = B = F16, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+    return (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+template <int BN>
+struct F16Cfg {
+    static constexpr int A_BYTES = BM * BK16 * 2;
+    static constexpr int B_BYTES = BN * BK16 * 2;
+    static constexpr int STAGE_BYTES = 2 * (A_BYTES + B_BYTES);   // hi and lo of A and B
+    static constexpr int STAGES = BN == 128 ? 3 : 4;
+    static constexpr int EPI_BYTES = 4 * 32 * 33 * 4;
+    static constexpr int SMEM = STAGES * STAGE_BYTES + EPI_BYTES + 1024;
+};
+
+// One warp per row: e_r, then hi / lo (FP16, [rows][K] per batch matrix, rows * K apart).
+__global__ void split16_kernel(const float* __restrict__ X, int64_t ldx, int64_t sx, int rows, int K, __half* hi,
+                               __half* lo, int* ex) {
+    const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= rows) return;
+    const int64_t bz = blockIdx.y;
+    const float* xr = X + bz * sx + (int64_t)r * ldx;
+    float mx = 0.f;
+    for (int k = 4 * lane; k < K; k += 128) {
+        const float4 v = *reinterpret_cast<const float4*>(xr + k);
+        mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    int e = 0;
+    if (mx > 0.f && isfinite(mx)) frexpf(mx, &e);                  // mx < 2^e
+    if (lane == 0) ex[bz * rows + r] = e;
+    __half* hr = hi + (bz * rows + r) * (int64_t)K;
+    __half* lr = lo + (bz * rows + r) * (int64_t)K;
+    for (int k = 4 * lane; k < K; k += 128) {
+        const float4 v = *reinterpret_cast<const float4*>(xr + k);
+        const float x[4] = {ldexpf(v.x, -e), ldexpf(v.y, -e), ldexpf(v.z, -e), ldexpf(v.w, -e)};
+        __half h[4], l[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            h[q] = __float2half_rn(x[q]);
+            l[q] = __float2half_rn(x[q] - __half2float(h[q]));
+        }
+        *reinterpret_cast<__half2*>(hr + k) = __halves2half2(h[0], h[1]);
+        *reinterpret_cast<__half2*>(hr + k + 2) = __halves2half2(h[2], h[3]);
+        *reinterpret_cast<__half2*>(lr + k) = __halves2half2(l[0], l[1]);
+        *reinterpret_cast<__half2*>(lr + k + 2) = __halves2half2(l[2], l[3]);
+    }
+}
+
+template <int BN>
+__global__ void __launch_bounds__(256, 1)
+    tc_f16x3_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
+                    const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl, int M, int N,
+                    int K, float alpha, float beta, float* C, int64_t ldc, int64_t c_bstride, const int* __restrict__ ea,
+                    const int* __restrict__ eb, int64_t eb_bstride, int transC, int lower_only, unsigned* err) {
+    using Cfg = F16Cfg<BN>;
+    constexpr int STAGES = Cfg::STAGES;
+    extern __shared__ __align__(1024) uint8_t tc_smem[];
+    __shared__ uint64_t full_bar[STAGES], empty_bar[STAGES], done_bar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ volatile int abort_flag;
+
+    const int bn = blockIdx.x, bm = blockIdx.y, bz = blockIdx.z;
+    if (lower_only && bn * BN >= (bm + 1) * BM) return;        // tile strictly above the diagonal
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nk = K / BK16;
+    uint8_t* base = (uint8_t*)(((uintptr_t)tc_smem + 1023) & ~(uintptr_t)1023);
+    auto a_hi = [&](int s) { return base + s * Cfg::STAGE_BYTES; };
+    auto b_hi = [&](int s) { return base + s * Cfg::STAGE_BYTES + Cfg::A_BYTES; };
+    auto a_lo = [&](int s) { return base + s * Cfg::STAGE_BYTES + Cfg::A_BYTES + Cfg::B_BYTES; };
+    auto b_lo = [&](int s) { return base + s * Cfg::STAGE_BYTES + 2 * Cfg::A_BYTES + Cfg::B_BYTES; };
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full_bar[s], 1);
+            mbar_init(&empty_bar[s], 1);
+        }
+        mbar_init(&done_bar, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) tmem_alloc(&tmem_slot, BN);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {                                         // TMA producer
+            int issued = 0;
+            for (int kt = 0; kt < nk && !abort_flag; ++kt) {
+                const int s = kt % STAGES;
+                if (kt >= STAGES && !mbar_wait(&empty_bar[s], ((kt / STAGES) - 1) & 1)) {
+                    abort_flag = 1;
+                    atomicOr(err, 2u);
+                    break;
+                }
+                mbar_expect_tx(&full_bar[s], Cfg::STAGE_BYTES);
+                tma_load_3d(a_hi(s), &tmAh, &full_bar[s], kt * BK16, bm * BM, bz);
+                tma_load_3d(a_lo(s), &tmAl, &full_bar[s], kt * BK16, bm * BM, bz);
+                tma_load_3d(b_hi(s), &tmBh, &full_bar[s], kt * BK16, bn * BN, bz);
+                tma_load_3d(b_lo(s), &tmBl, &full_bar[s], kt * BK16, bn * BN, bz);
+                issued = kt + 1;
+            }
+            if (abort_flag)                                     // let the copies already issued land
+                for (int kt = (issued > STAGES ? issued - STAGES : 0); kt < issued; ++kt)
+                    mbar_wait(&full_bar[kt % STAGES], (kt / STAGES) & 1);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {                                         // MMA issuer
+            constexpr uint32_t idesc = idesc_f16(BM, BN);
+            bool ok = true;
+            for (int kt = 0; kt < nk; ++kt) {
+                const int s = kt % STAGES;
+                if (abort_flag || !mbar_wait(&full_bar[s], (kt / STAGES) & 1)) {
+                    abort_flag = 1;
+                    atomicOr(err, 2u);
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint64_t dah = sdesc_sw128(smem_u32(a_hi(s))), dbh = sdesc_sw128(smem_u32(b_hi(s)));
+                const uint64_t dal = sdesc_sw128(smem_u32(a_lo(s))), dbl = sdesc_sw128(smem_u32(b_lo(s)));
+#pragma unroll
+                for (int kk = 0; kk < BK16 / 16; ++kk) {         // 16 FP16 = 32 bytes per MMA
+                    const uint64_t off = (uint64_t)(kk * 2);
+                    mma_f16(tmem, dah + off, dbh + off, idesc, (kt | kk) != 0);
+                    mma_f16(tmem, dah + off, dbl + off, idesc, 1);
+                    mma_f16(tmem, dal + off, dbh + off, idesc, 1);
+                }
+                mma_commit(&empty_bar[s]);
+            }
+            if (ok) mma_commit(&done_bar);
+        }
+    } else if (warp >= 4) {
+        // epilogue: TMEM lanes 32*(warp-4) .. +31 are rows of the tile
+        const bool ok = !abort_flag && mbar_wait(&done_bar, 0);
+        if (!ok) {
+            abort_flag = 1;
+            atomicOr(err, 2u);
+        } else {
+            tc_fence_after();
+            const int rw = warp - 4;
+            const int row = bm * BM + rw * 32 + lane;
+            const int row0 = bm * BM + rw * 32;
+            float* Cb = C + (int64_t)bz * c_bstride;
+            const int* ebz = eb + (int64_t)bz * eb_bstride;
+            const float sa = row < M ? ldexpf(alpha, ea[(int64_t)bz * M + row]) : 0.f;   // this lane's row
+            float* stg = reinterpret_cast<float*>(base + STAGES * Cfg::STAGE_BYTES) + rw * 32 * 33;
+#pragma unroll 1
+            for (int cc = 0; cc < BN / 32; ++cc) {
+                float v[32];
+                tmem_ld32(tmem + ((uint32_t)(rw * 32) << 16) + (uint32_t)(cc * 32), v);
+                if (!transC) {
+                    // row-major C: stage the 32 x 32 block (row scale applied), then each lane
+                    // walks a column of it (column scale applied); old values loaded before stores
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) stg[lane * 33 + j] = v[j] * sa;
+                    __syncwarp();
+                    const int col = bn * BN + cc * 32 + lane;
+                    const float sb = col < N ? ldexpf(1.f, ebz[col]) : 0.f;
+                    float old[32];
+#pragma unroll
+                    for (int r = 0; r < 32; ++r)
+                        old[r] = (beta != 0.f && row0 + r < M && col < N) ? Cb[(int64_t)(row0 + r) * ldc + col] : 0.f;
+#pragma unroll
+                    for (int r = 0; r < 32; ++r)
+                        if (row0 + r < M && col < N)
+                            Cb[(int64_t)(row0 + r) * ldc + col] = stg[r * 33 + lane] * sb + beta * old[r];
+                    __syncwarp();
+                    continue;
+                }
+                if (row < M) {                                   // C^T: lanes write consecutive rows
+                    float old[32];
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int col = bn * BN + cc * 32 + j;
+                        old[j] = (beta != 0.f && col < N) ? Cb[(int64_t)col * ldc + row] : 0.f;
+                    }
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int col = bn * BN + cc * 32 + j;
+                        if (col < N) Cb[(int64_t)col * ldc + row] = v[j] * sa * ldexpf(1.f, ebz[col]) + beta * old[j];
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, BN);
+    }
+}
+
+// rows x cols row-major FP16 matrices, batch of them rows * cols apart
+bool make_map16(CUtensorMap* m, const __half* ptr, int64_t rows, int64_t cols, int batch, int box_rows) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)batch};
+    cuuint64_t strides[2] = {(cuuint64_t)cols * 2, (cuuint64_t)(rows * cols) * 2};
+    cuuint32_t box[3] = {(cuuint32_t)BK16, (cuuint32_t)box_rows, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, (void*)ptr, dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+template <int BN>
+slab_status launch_f16x3(cudaStream_t st, const TcGemmArgs& g, unsigned* err) {
+    const bool shared = f16x3_shared(g);
+    const int64_t b = g.batch, K = g.K;
+    const int64_t rB = shared ? g.M : g.N;                 // rows of the split that serves B
+    uint8_t* w = (uint8_t*)g.w16;
+    __half* Ah = (__half*)w;                 w += align256((size_t)b * g.M * K * 2);
+    __half* Al = (__half*)w;                 w += align256((size_t)b * g.M * K * 2);
+    __half* Bh = Ah;
+    __half* Bl = Al;
+    if (!shared) {
+        Bh = (__half*)w;                     w += align256((size_t)b * g.N * K * 2);
+        Bl = (__half*)w;                     w += align256((size_t)b * g.N * K * 2);
+    }
+    int* ea = (int*)w;                       w += align256((size_t)b * g.M * 4);
+    int* eb = shared ? ea : (int*)w;
+    split16_kernel<<<dim3((unsigned)((g.M + 7) / 8), (unsigned)b), 256, 0, st>>>(g.A, g.lda, g.sA, g.M, g.K, Ah, Al,
+                                                                                  ea);
+    if (cudaGetLastError() != cudaSuccess) return SLAB_ECUDA;
+    if (!shared) {
+        split16_kernel<<<dim3((unsigned)((g.N + 7) / 8), (unsigned)b), 256, 0, st>>>(g.B, g.ldb, g.sB, g.N, g.K, Bh,
+                                                                                      Bl, eb);
+        if (cudaGetLastError() != cudaSuccess) return SLAB_ECUDA;
+    }
+    CUtensorMap tah, tal, tbh, tbl;
+    if (!make_map16(&tah, Ah, g.M, K, g.batch, BM) || !make_map16(&tal, Al, g.M, K, g.batch, BM) ||
+        !make_map16(&tbh, Bh, rB, K, g.batch, BN) || !make_map16(&tbl, Bl, rB, K, g.batch, BN))
+        return SLAB_ECUDA;
+    const int smem = F16Cfg<BN>::SMEM;
+    static std::atomic<uint32_t> attr_done(0);
+    if (!ensure_smem_attr(tc_f16x3_kernel<BN>, smem, attr_done)) return SLAB_ECUDA;
+    dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, g.batch);
+    tc_f16x3_kernel<BN><<<grid, 256, smem, st>>>(tah, tal, tbh, tbl, g.M, g.N, g.K, g.alpha, g.beta, g.C, g.ldc, g.sC,
+                                                 ea, eb, rB, g.transC, g.lower_only, err);
+    return cudaGetLastError() == cudaSuccess ? SLAB_OK : SLAB_ECUDA;
+}
+
 }  // namespace
 
 // Host entry: validates the layout constraints of the TMA path and launches.
 slab_status tc_gemm(cudaStream_t st, const TcGemmArgs& g, unsigned* err) {
     if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return SLAB_OK;
     if (g.K <= 0 || g.K % BK) return SLAB_EINVAL;
-    if (g.ksplit > 1 && (g.K % (g.ksplit * BK) || !g.part || g.lower_only)) return SLAB_EINVAL;
+    if (g.ksplit > 1 && (g.K % (g.ksplit * BK) || !g.part || g.lower_only || g.split == 2)) return SLAB_EINVAL;
     if (g.lda % 4 || g.ldb % 4 || g.sA % 4 || g.sB % 4) return SLAB_EINVAL;       // 16-byte strides
     if (((uintptr_t)g.A & 15) || ((uintptr_t)g.B & 15)) return SLAB_EINVAL;      // 16-byte base
     const bool narrow = g.N <= 64;
+    if (g.split == 2) {
+        if (g.K % BK16 || !g.w16 || g.w16_bytes < f16x3_work_bytes(g.M, g.N, g.K, g.batch, f16x3_shared(g)) ||
+            ((uintptr_t)g.w16 & 255) || g.batch > 65535)
+            return SLAB_EINVAL;
+        return narrow ? launch_f16x3<64>(st, g, err) : launch_f16x3<128>(st, g, err);
+    }
     if (g.split) return narrow ? launch_tc<64, true>(st, g, err) : launch_tc<128, true>(st, g, err);
     return narrow ? launch_tc<64, false>(st, g, err) : launch_tc<128, false>(st, g, err);
+}
+
+size_t f16x3_work_bytes(int64_t M, int64_t N, int64_t K, int batch, bool shared) {
+    const size_t b = (size_t)(batch > 0 ? batch : 1);
+    size_t w = 2 * align256(b * M * K * 2) + align256(b * M * 4);
+    if (!shared) w += 2 * align256(b * N * K * 2) + align256(b * N * 4);
+    return w;
 }
 
 extern "C" slab_status slab_tc_gemm(int M, int N, int K, float alpha, const float* A, int64_t lda, const float* B,
@@ -623,7 +904,19 @@ extern "C" slab_status slab_tc_gemm(int M, int N, int K, float alpha, const floa
     g.transC = trans_c; g.split = split; g.lower_only = 0;
     g.batch = 1; g.sA = g.sB = g.sC = 0;
     g.ksplit = 1; g.part = nullptr;
-    return tc_gemm((cudaStream_t)stream, g, dev_err);
+    g.w16 = nullptr; g.w16_bytes = 0;
+    if (split != 2) return tc_gemm((cudaStream_t)stream, g, dev_err);
+    // FP16 three-product: scratch for the operand splits from the stream-ordered allocator
+    if (K <= 0 || K % 64) return SLAB_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    g.w16_bytes = f16x3_work_bytes(M, N, K, 1, f16x3_shared(g));
+    if (cudaMallocAsync(&g.w16, g.w16_bytes, st) != cudaSuccess) {
+        cudaGetLastError();
+        return SLAB_ENOMEM;
+    }
+    const slab_status s = tc_gemm(st, g, dev_err);
+    if (cudaFreeAsync(g.w16, st) != cudaSuccess) return SLAB_ECUDA;
+    return s;
 }
 
 // C (FP64, M x N, ldc) += alpha A B^T with A (M x K, lda) and B (N x K, ldb) FP64, FP64-accurate

@@ -862,11 +862,13 @@ __global__ void __launch_bounds__(TB_THREADS, sizeof(T) == 8 ? 5 : 8) tree_down_
         for (int q = 0; q < 4; ++q) sts4(V + (4 * tA + q) * KP + 4 * tB, acc[q]);
         __syncthreads();
     }
-    T* xd = P.xs(t, c);
     const int64_t N = (int64_t)s * s;
-    for (int i = tid >> 6; i < m; i += TB_THREADS >> 6) {
-        const int r = tid & 63;
-        if (r < K) xd[i * kc + r] = V[i * KP + r];
+    if (k > 0) {                       // x of a height-0 row is read by no lower node
+        T* xd = P.xs(t, c);
+        for (int i = tid >> 6; i < m; i += TB_THREADS >> 6) {
+            const int r = tid & 63;
+            if (r < K) xd[i * kc + r] = V[i * KP + r];
+        }
     }
     {
         int ul, rl;

@@ -1,8 +1,9 @@
 """Tensor-core product (tcgen05 + TMA) against an FP64 reference of the same op.
 
-The 3xTF32 mode is required to stay within 16x of the error of the same product done in
-plain FP32: the three TF32 products are each exact, but the tensor core accumulates them in
-FP32 inside the MMA, which at K = 2048 costs about one decimal digit against a CPU FP32 dot.
+The 3xTF32 mode (split 1) and the three-FP16-product mode (split 2) are required to stay within
+16x of the error of the same product done in plain FP32: the split products are each exact, but
+the tensor core accumulates them in FP32 inside the MMA, which at K = 2048 costs about one decimal
+digit against a CPU FP32 dot.
 """
 import ctypes
 
@@ -56,9 +57,61 @@ def test_tc_gemm_transposed_output():
     assert rel < max(16 * rel32, 1e-6), (rel, rel32)
 
 
-def test_tc_gemm_schur_shape_rate():
-    """The odd-even Schur update shape of the n = 2048 workload (2048^3, C -= A B^T) in 3xTF32:
-    sampled rows against FP64, and the event-timed rate reported for the record."""
+@pytest.mark.parametrize("M,N,K", [(128, 128, 64), (300, 200, 256), (512, 64, 2048), (1000, 130, 192)])
+def test_tc_gemm_f16x3_is_fp32_accurate(M, N, K):
+    """Three FP16 products of row-scaled hi/lo splits: FP32-level accuracy like 3xTF32."""
+    rel, rel32 = _run(M, N, K, -1.0, 1.0, split=2, trans_c=0)
+    assert rel < max(16 * rel32, 1e-6), (rel, rel32)
+
+
+def test_tc_gemm_f16x3_transposed_output():
+    rel, rel32 = _run(200, 64, 128, 0.5, 2.0, split=2, trans_c=1)
+    assert rel < max(16 * rel32, 1e-6), (rel, rel32)
+
+
+def test_tc_gemm_f16x3_row_scales():
+    """Rows of A and B spread over 2^-30 .. 2^30: the per-row power-of-two scales keep the FP16
+    splits in range, so every entry keeps FP32-level accuracy relative to |A| |B|."""
+    from paper_2211_07572_gb300 import _lib
+    lib = _lib.load()
+    M, N, K = 256, 192, 320
+    rng = np.random.default_rng(11)
+    A = (rng.standard_normal((M, K)) * np.exp2(rng.integers(-30, 30, size=(M, 1)))).astype(np.float32)
+    B = (rng.standard_normal((N, K)) * np.exp2(rng.integers(-30, 30, size=(N, 1)))).astype(np.float32)
+    Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    Cd = torch.zeros(M, N, dtype=torch.float32, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    st = lib.slab_tc_gemm(M, N, K, 1.0, ctypes.c_void_p(Ad.data_ptr()), K, ctypes.c_void_p(Bd.data_ptr()), K, 0.0,
+                          ctypes.c_void_p(Cd.data_ptr()), N, 0, 2, ctypes.c_void_p(err.data_ptr()),
+                          ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == 0
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    A64, B64 = A.astype(np.float64), B.astype(np.float64)
+    ref = A64 @ B64.T
+    scale = np.abs(A64) @ np.abs(B64).T
+    rel = (np.abs(Cd.cpu().numpy().astype(np.float64) - ref) / scale).max()
+    assert rel <= 2e-6, rel
+
+
+def test_tc_gemm_f16x3_rejects_ragged_k():
+    """K must be a multiple of 64 for the FP16 path: rejected on the host, nothing launched."""
+    from paper_2211_07572_gb300 import _lib
+    lib = _lib.load()
+    A = torch.zeros(128, 96, device="cuda")
+    C = torch.zeros(128, 128, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    st = lib.slab_tc_gemm(128, 128, 96, 1.0, ctypes.c_void_p(A.data_ptr()), 96, ctypes.c_void_p(A.data_ptr()), 96,
+                          0.0, ctypes.c_void_p(C.data_ptr()), 128, 0, 2, ctypes.c_void_p(err.data_ptr()),
+                          ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == 1
+
+
+@pytest.mark.parametrize("split", [1, 2])
+def test_tc_gemm_schur_shape_rate(split):
+    """The odd-even Schur update shape of the n = 2048 workload (2048^3, C -= A B^T) in 3xTF32
+    (split 1) and in three FP16 products (split 2): sampled rows against FP64, and the
+    event-timed rate reported for the record."""
     from paper_2211_07572_gb300 import _lib
     lib = _lib.load()
     M = N = K = 2048
@@ -72,7 +125,7 @@ def test_tc_gemm_schur_shape_rate():
 
     def run():
         st = lib.slab_tc_gemm(M, N, K, -1.0, ctypes.c_void_p(A.data_ptr()), K, ctypes.c_void_p(B.data_ptr()), K,
-                              1.0, ctypes.c_void_p(C.data_ptr()), N, 0, 1, ctypes.c_void_p(err.data_ptr()),
+                              1.0, ctypes.c_void_p(C.data_ptr()), N, 0, split, ctypes.c_void_p(err.data_ptr()),
                               ctypes.c_void_p(stream.cuda_stream))
         assert st == 0
 
@@ -92,7 +145,8 @@ def test_tc_gemm_schur_shape_rate():
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / 5
-    print(f"tc_gemm 2048^3 3xTF32: {ms:.3f} ms, {2 * M * N * K / ms / 1e9:.1f} TFLOP/s algorithmic")
+    mode = "3xTF32" if split == 1 else "3xFP16 (row-scaled splits)"
+    print(f"tc_gemm 2048^3 {mode}: {ms:.3f} ms, {2 * M * N * K / ms / 1e9:.1f} TFLOP/s algorithmic")
 
 
 @pytest.mark.parametrize("M,N,K", [(200, 130, 64), (4096, 640, 64), (77, 1000, 32)])
