@@ -259,10 +259,13 @@ BOUND3 = dict(BOUND, assemble_T="tensor", tree_up="tensor", tree_down="tensor")
 # default workload only: the n = 1024, b = 32, k = 64 case (all heights of one pass) scaled by the
 # node count (4x at n = 2048, same b, m, k) over the 11 launches of a pass at n = 2048.
 TRAFFIC = {
-    "tree_down": {"bytes": 1.682e9 * 4 / 11, "from": "ncu at n=1024 (10 launches, 1.682 GB/pass) x4 nodes / 11"},
-    "tree_up": {"bytes": 2.314e9 * 4 / 11, "from": "ncu at n=1024 (10 launches, 2.314 GB/pass) x4 nodes / 11"},
+    "tree_down": {"bytes": 1.560e9 * 4 / 11, "from": "ncu at n=1024 (10 launches, 1.560 GB/pass) x4 nodes / 11"},
+    "tree_up": {"bytes": 2.340e9 * 4 / 11, "from": "ncu at n=1024 (10 launches, 2.340 GB/pass) x4 nodes / 11"},
 }
-SPLIT_NOTE = "the 3xTF32 split executes 3 MMAs per flop"
+# How each tensor-core class multiplies (set per run in run_gpu): "f16x3" three FP16 MMAs of
+# row-scaled hi/lo splits per algorithmic FP32 flop (the FP32 factor's Schur and trailing
+# products), "tf32x3" three TF32 MMAs (3xTF32), "tf32" one TF32 MMA.
+MMA_MODE = {}
 
 
 def roofline_for(cls, ms, count, work, peaks, clocks, bounds=None):
@@ -275,9 +278,16 @@ def roofline_for(cls, ms, count, work, peaks, clocks, bounds=None):
     elif bound == "tensor":
         achieved = work[cls] / t / 1e12
         bf16 = peaks.get("bf16_tflops", 1891.8)
-        peak = bf16 * 1.1 / 2.25
-        unit, src = "TFLOP/s", ("measured bf16 dense x 1.1/2.25 (tf32 nominal ratio); algorithmic FP32 flops, "
-                                + SPLIT_NOTE)
+        mode = MMA_MODE.get(cls, "tf32x3")
+        if mode == "f16x3":
+            peak = bf16
+            src = ("measured bf16 dense (= fp16 dense rate); algorithmic FP32 flops, three FP16 MMAs of "
+                   "row-scaled hi/lo splits per flop")
+        else:
+            peak = bf16 * 1.1 / 2.25
+            src = ("measured bf16 dense x 1.1/2.25 (tf32 nominal ratio); algorithmic FP32 flops, "
+                   + ("three TF32 MMAs per flop (3xTF32)" if mode == "tf32x3" else "one TF32 MMA per flop"))
+        unit = "TFLOP/s"
     else:
         mhz = peaks.get("sm_max_mhz", 2070.0)
         achieved = work[cls] / t / 1e12
@@ -323,9 +333,11 @@ def run_gpu(args):
     prec = args.precision
 
     NI = n // b - 1
-    global SPLIT_NOTE
+    MMA_MODE.clear()
     if prec == "tf32":
-        SPLIT_NOTE = "factor products in one TF32 pass (1 MMA per flop), solve products 3xTF32"
+        MMA_MODE.update(schur_update="tf32", trailing="tf32", assemble_T="tf32")   # factor products
+    elif prec == "fp32" and not helm:
+        MMA_MODE.update(schur_update="f16x3", trailing="f16x3")
     if helm:
         stage2 = "sweep"
     else:
@@ -355,9 +367,11 @@ def run_gpu(args):
         return rel, it
 
     if args.once:
-        rel, it = step(f, u)
+        cnt = []
+        rel, it = step(f, u, cnt)
         torch.cuda.synchronize()
-        print(json.dumps({"once": True, "config": W, "max_relres": float(np.max(rel)), "refine_steps": it}))
+        print(json.dumps({"once": True, "config": W, "max_relres": float(np.max(rel)), "refine_steps": it,
+                          "gpu_launches": cnt[0]}))
         return
     for _ in range(args.warmup):
         rel, it = step(f, u)

@@ -411,6 +411,7 @@ slab_status gemm_tn<float>(slab_handle* h, int cls, int M, int N, int K, float a
     }
     const slab_status st = tc_gemm(h->stream, g, h->dstatus);
     if (st == SLAB_ECUDA && h->err == SLAB_OK) h->err = SLAB_ECUDA;
+    prof_extra(h, cls, tc_gemm_extra_launches(g));
     return st;
 }
 
@@ -483,6 +484,8 @@ slab_status gemm_tn<double>(slab_handle* h, int cls, int M, int N, int K, double
                 return st;
             }
         }
+        // launches beyond the one counted: the scaling of C and three per K chunk (two splits, product)
+        prof_extra(h, cls, (beta != 1.0 ? 1 : 0) + 3 * ((K + 63) / 64) - 1);
         return SLAB_OK;
     }
     SLAB_PROF(h, cls);
@@ -861,6 +864,7 @@ slab_status gemm_tn_batched<float>(slab_handle* h, int cls, int M, int N, int K,
     }
     const slab_status st = tc_gemm(h->stream, g, h->dstatus);
     if (st == SLAB_ECUDA && h->err == SLAB_OK) h->err = SLAB_ECUDA;
+    prof_extra(h, cls, tc_gemm_extra_launches(g));
     return st;
 }
 

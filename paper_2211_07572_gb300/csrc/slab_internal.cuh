@@ -160,6 +160,8 @@ struct ProfScope {
     ~ProfScope() { prof_end(h, cls); }
 };
 #define SLAB_PROF(h, cls) ProfScope _prof_scope_((h), (cls))
+// Further kernel launches made inside one SLAB_PROF scope (split pre-passes, split-K reductions).
+inline void prof_extra(slab_handle* h, int cls, int n) { h->launches[cls] += n; }
 
 // ---------------------------------------------------------------- tree helpers (host+device)
 __host__ __device__ inline int tree_height_count(int s) {
@@ -274,6 +276,11 @@ slab_status ozaki_gemm(cudaStream_t st, int M, int N, int K, double alpha, const
                        const double* B, int64_t ldb, double* C, int64_t ldc, int lower_only, void* work,
                        unsigned* err);
 slab_status tc_gemm(cudaStream_t st, const TcGemmArgs& g, unsigned* err);
+// Kernels tc_gemm launches besides the product itself: the split-K reduction, the operand splits.
+inline int tc_gemm_extra_launches(const TcGemmArgs& g) {
+    if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return -1;                 // nothing launched
+    return (g.ksplit > 1 ? 1 : 0) + (g.split == 2 ? (f16x3_shared(g) ? 1 : 2) : 0);
+}
 
 // error helper
 slab_status slab_cuda_check(slab_handle* h, cudaError_t e);
