@@ -15,6 +15,7 @@
 #include <cuda.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
 #include <atomic>
 
 #include "slab_internal.cuh"
@@ -32,6 +33,19 @@ bool ensure_smem_attr(Kern kernel, int bytes, std::atomic<uint32_t>& done) {
     if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess) return false;
     done.fetch_or(bit, std::memory_order_acq_rel);
     return true;
+}
+
+// Streaming multiprocessors of the current device (cached per device).
+int num_sms() {
+    static std::atomic<int> cache[32];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 148;
+    std::atomic<int>& c = cache[dev & 31];
+    int v = c.load(std::memory_order_relaxed);
+    if (v > 0) return v;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) return 148;
+    c.store(v, std::memory_order_relaxed);
+    return v;
 }
 
 constexpr int BM = 128;
@@ -668,23 +682,40 @@ __global__ void split16_kernel(const float* __restrict__ X, int64_t ldx, int64_t
     }
 }
 
+// Persistent: grid = min(tiles, SMs), CTA c takes tiles c, c + grid, ... (row-major over
+// (batch, tile row, tile column); with lower_only the tiles strictly above the diagonal are left
+// out of the sequence by every role alike).  The smem ring runs on across tiles (stage counter
+// it), the accumulator alternates between two TMEM buffers of BN columns (tile counter tl):
+// the MMA warp fills buffer tl & 1 while the epilogue warps drain the other one.
+//   full[s] / empty[s]: TMA landed / MMAs done reading stage s  (phase (it / STAGES) & 1)
+//   acc_full[b]: MMAs of the tile in buffer b done (commit); acc_empty[b]: its epilogue done
+//   (128 arrivals), both in phase (tl / 2) & 1.
 template <int BN>
 __global__ void __launch_bounds__(256, 1)
     tc_f16x3_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
                     const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl, int M, int N,
-                    int K, float alpha, float beta, float* C, int64_t ldc, int64_t c_bstride, const int* __restrict__ ea,
-                    const int* __restrict__ eb, int64_t eb_bstride, int transC, int lower_only, unsigned* err) {
+                    int K, int batch, float alpha, float beta, float* C, int64_t ldc, int64_t c_bstride,
+                    const int* __restrict__ ea, const int* __restrict__ eb, int64_t eb_bstride, int transC,
+                    int lower_only, unsigned* err) {
     using Cfg = F16Cfg<BN>;
     constexpr int STAGES = Cfg::STAGES;
     extern __shared__ __align__(1024) uint8_t tc_smem[];
-    __shared__ uint64_t full_bar[STAGES], empty_bar[STAGES], done_bar;
+    __shared__ uint64_t full_bar[STAGES], empty_bar[STAGES], accf_bar[2], acce_bar[2];
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int abort_flag;
 
-    const int bn = blockIdx.x, bm = blockIdx.y, bz = blockIdx.z;
-    if (lower_only && bn * BN >= (bm + 1) * BM) return;        // tile strictly above the diagonal
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nk = K / BK16;
+    const int tn = (N + BN - 1) / BN, tm = (M + BM - 1) / BM;
+    const int64_t ntiles = (int64_t)batch * tm * tn;
+    // tile id -> (bz, bm, bn); false for a tile strictly above the diagonal when lower_only
+    auto tile_of = [&](int64_t id, int& bz, int& bm, int& bn) {
+        bn = (int)(id % tn);
+        const int64_t r = id / tn;
+        bm = (int)(r % tm);
+        bz = (int)(r / tm);
+        return !(lower_only && bn * BN >= (bm + 1) * BM);
+    };
     uint8_t* base = (uint8_t*)(((uintptr_t)tc_smem + 1023) & ~(uintptr_t)1023);
     auto a_hi = [&](int s) { return base + s * Cfg::STAGE_BYTES; };
     auto b_hi = [&](int s) { return base + s * Cfg::STAGE_BYTES + Cfg::A_BYTES; };
@@ -696,11 +727,14 @@ __global__ void __launch_bounds__(256, 1)
             mbar_init(&full_bar[s], 1);
             mbar_init(&empty_bar[s], 1);
         }
-        mbar_init(&done_bar, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accf_bar[b], 1);
+            mbar_init(&acce_bar[b], 128);
+        }
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 1) tmem_alloc(&tmem_slot, BN);
+    if (warp == 1) tmem_alloc(&tmem_slot, 2 * BN);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -708,70 +742,95 @@ __global__ void __launch_bounds__(256, 1)
 
     if (warp == 0) {
         if (lane == 0) {                                         // TMA producer
-            int issued = 0;
-            for (int kt = 0; kt < nk && !abort_flag; ++kt) {
-                const int s = kt % STAGES;
-                if (kt >= STAGES && !mbar_wait(&empty_bar[s], ((kt / STAGES) - 1) & 1)) {
-                    abort_flag = 1;
-                    atomicOr(err, 2u);
-                    break;
+            int64_t it = 0, issued = 0;
+            for (int64_t id = blockIdx.x; id < ntiles && !abort_flag; id += gridDim.x) {
+                int bz, bm, bn;
+                if (!tile_of(id, bz, bm, bn)) continue;
+                for (int kt = 0; kt < nk; ++kt, ++it) {
+                    const int s = (int)(it % STAGES);
+                    if (it >= STAGES && !mbar_wait(&empty_bar[s], (uint32_t)((it / STAGES) - 1) & 1)) {
+                        abort_flag = 1;
+                        atomicOr(err, 2u);
+                        break;
+                    }
+                    mbar_expect_tx(&full_bar[s], Cfg::STAGE_BYTES);
+                    tma_load_3d(a_hi(s), &tmAh, &full_bar[s], kt * BK16, bm * BM, bz);
+                    tma_load_3d(a_lo(s), &tmAl, &full_bar[s], kt * BK16, bm * BM, bz);
+                    tma_load_3d(b_hi(s), &tmBh, &full_bar[s], kt * BK16, bn * BN, bz);
+                    tma_load_3d(b_lo(s), &tmBl, &full_bar[s], kt * BK16, bn * BN, bz);
+                    issued = it + 1;
                 }
-                mbar_expect_tx(&full_bar[s], Cfg::STAGE_BYTES);
-                tma_load_3d(a_hi(s), &tmAh, &full_bar[s], kt * BK16, bm * BM, bz);
-                tma_load_3d(a_lo(s), &tmAl, &full_bar[s], kt * BK16, bm * BM, bz);
-                tma_load_3d(b_hi(s), &tmBh, &full_bar[s], kt * BK16, bn * BN, bz);
-                tma_load_3d(b_lo(s), &tmBl, &full_bar[s], kt * BK16, bn * BN, bz);
-                issued = kt + 1;
             }
             if (abort_flag)                                     // let the copies already issued land
-                for (int kt = (issued > STAGES ? issued - STAGES : 0); kt < issued; ++kt)
-                    mbar_wait(&full_bar[kt % STAGES], (kt / STAGES) & 1);
+                for (int64_t q = (issued > STAGES ? issued - STAGES : 0); q < issued; ++q)
+                    mbar_wait(&full_bar[q % STAGES], (uint32_t)(q / STAGES) & 1);
         }
     } else if (warp == 1) {
         if (lane == 0) {                                         // MMA issuer
             constexpr uint32_t idesc = idesc_f16(BM, BN);
-            bool ok = true;
-            for (int kt = 0; kt < nk; ++kt) {
-                const int s = kt % STAGES;
-                if (abort_flag || !mbar_wait(&full_bar[s], (kt / STAGES) & 1)) {
+            int64_t it = 0, tl = 0;
+            for (int64_t id = blockIdx.x; id < ntiles; id += gridDim.x) {
+                int bz, bm, bn;
+                if (!tile_of(id, bz, bm, bn)) continue;
+                const int buf = (int)(tl & 1);
+                if (abort_flag ||
+                    (tl >= 2 && !mbar_wait(&acce_bar[buf], (uint32_t)((tl / 2) - 1) & 1))) {
                     abort_flag = 1;
                     atomicOr(err, 2u);
-                    ok = false;
                     break;
                 }
                 tc_fence_after();
-                const uint64_t dah = sdesc_sw128(smem_u32(a_hi(s))), dbh = sdesc_sw128(smem_u32(b_hi(s)));
-                const uint64_t dal = sdesc_sw128(smem_u32(a_lo(s))), dbl = sdesc_sw128(smem_u32(b_lo(s)));
+                const uint32_t acc = tmem + (uint32_t)(buf * BN);
+                bool ok = true;
+                for (int kt = 0; kt < nk; ++kt, ++it) {
+                    const int s = (int)(it % STAGES);
+                    if (abort_flag || !mbar_wait(&full_bar[s], (uint32_t)(it / STAGES) & 1)) {
+                        abort_flag = 1;
+                        atomicOr(err, 2u);
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint64_t dah = sdesc_sw128(smem_u32(a_hi(s))), dbh = sdesc_sw128(smem_u32(b_hi(s)));
+                    const uint64_t dal = sdesc_sw128(smem_u32(a_lo(s))), dbl = sdesc_sw128(smem_u32(b_lo(s)));
 #pragma unroll
-                for (int kk = 0; kk < BK16 / 16; ++kk) {         // 16 FP16 = 32 bytes per MMA
-                    const uint64_t off = (uint64_t)(kk * 2);
-                    mma_f16(tmem, dah + off, dbh + off, idesc, (kt | kk) != 0);
-                    mma_f16(tmem, dah + off, dbl + off, idesc, 1);
-                    mma_f16(tmem, dal + off, dbh + off, idesc, 1);
+                    for (int kk = 0; kk < BK16 / 16; ++kk) {     // 16 FP16 = 32 bytes per MMA
+                        const uint64_t off = (uint64_t)(kk * 2);
+                        mma_f16(acc, dah + off, dbh + off, idesc, (kt | kk) != 0);
+                        mma_f16(acc, dah + off, dbl + off, idesc, 1);
+                        mma_f16(acc, dal + off, dbh + off, idesc, 1);
+                    }
+                    mma_commit(&empty_bar[s]);
                 }
-                mma_commit(&empty_bar[s]);
+                if (!ok) break;
+                mma_commit(&accf_bar[buf]);
+                ++tl;
             }
-            if (ok) mma_commit(&done_bar);
         }
     } else if (warp >= 4) {
         // epilogue: TMEM lanes 32*(warp-4) .. +31 are rows of the tile
-        const bool ok = !abort_flag && mbar_wait(&done_bar, 0);
-        if (!ok) {
-            abort_flag = 1;
-            atomicOr(err, 2u);
-        } else {
+        const int rw = warp - 4;
+        float* stg = reinterpret_cast<float*>(base + STAGES * Cfg::STAGE_BYTES) + rw * 32 * 33;
+        int64_t tl = 0;
+        for (int64_t id = blockIdx.x; id < ntiles; id += gridDim.x) {
+            int bz, bm, bn;
+            if (!tile_of(id, bz, bm, bn)) continue;
+            const int buf = (int)(tl & 1);
+            if (abort_flag || !mbar_wait(&accf_bar[buf], (uint32_t)(tl / 2) & 1)) {
+                abort_flag = 1;
+                atomicOr(err, 2u);
+                break;
+            }
             tc_fence_after();
-            const int rw = warp - 4;
             const int row = bm * BM + rw * 32 + lane;
             const int row0 = bm * BM + rw * 32;
             float* Cb = C + (int64_t)bz * c_bstride;
             const int* ebz = eb + (int64_t)bz * eb_bstride;
             const float sa = row < M ? ldexpf(alpha, ea[(int64_t)bz * M + row]) : 0.f;   // this lane's row
-            float* stg = reinterpret_cast<float*>(base + STAGES * Cfg::STAGE_BYTES) + rw * 32 * 33;
 #pragma unroll 1
             for (int cc = 0; cc < BN / 32; ++cc) {
                 float v[32];
-                tmem_ld32(tmem + ((uint32_t)(rw * 32) << 16) + (uint32_t)(cc * 32), v);
+                tmem_ld32(tmem + ((uint32_t)(rw * 32) << 16) + (uint32_t)(buf * BN + cc * 32), v);
                 if (!transC) {
                     // row-major C: stage the 32 x 32 block (row scale applied), then each lane
                     // walks a column of it (column scale applied); old values loaded before stores
@@ -805,13 +864,16 @@ __global__ void __launch_bounds__(256, 1)
                     }
                 }
             }
+            tc_fence_before();
+            mbar_arrive(&acce_bar[buf]);                          // this thread's reads of the buffer are done
+            ++tl;
         }
     }
     tc_fence_before();
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc(tmem, BN);
+        tmem_dealloc(tmem, 2 * BN);
     }
 }
 
@@ -861,9 +923,10 @@ slab_status launch_f16x3(cudaStream_t st, const TcGemmArgs& g, unsigned* err) {
     const int smem = F16Cfg<BN>::SMEM;
     static std::atomic<uint32_t> attr_done(0);
     if (!ensure_smem_attr(tc_f16x3_kernel<BN>, smem, attr_done)) return SLAB_ECUDA;
-    dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, g.batch);
-    tc_f16x3_kernel<BN><<<grid, 256, smem, st>>>(tah, tal, tbh, tbl, g.M, g.N, g.K, g.alpha, g.beta, g.C, g.ldc, g.sC,
-                                                 ea, eb, rB, g.transC, g.lower_only, err);
+    const int64_t tiles = (int64_t)g.batch * ((g.M + BM - 1) / BM) * ((g.N + BN - 1) / BN);
+    const int grid = (int)std::min<int64_t>(tiles, num_sms());
+    tc_f16x3_kernel<BN><<<grid, 256, smem, st>>>(tah, tal, tbh, tbl, g.M, g.N, g.K, g.batch, g.alpha, g.beta, g.C,
+                                                 g.ldc, g.sC, ea, eb, rB, g.transC, g.lower_only, err);
     return cudaGetLastError() == cudaSuccess ? SLAB_OK : SLAB_ECUDA;
 }
 
