@@ -374,7 +374,7 @@ void slab_destroy(slab_handle* h) {
     void* p;
     p = h->AX; dfree(p); p = h->AY; dfree(p); p = h->DG; dfree(p); p = h->kappa; dfree(p);
     dfree(h->tLinv); dfree(h->tZtb); dfree(h->tRtb); dfree(h->tZI); dfree(h->tRI);
-    dfree(h->tWtb); dfree(h->tWI); dfree(h->ToT); dfree(h->dscratch); dfree(h->gjw); dfree(h->ozw); dfree(h->w16);
+    dfree(h->tWtb); dfree(h->tWI); dfree(h->ToT); dfree(h->dscratch); dfree(h->gjw); dfree(h->ozw); dfree(h->w16); dfree(h->pnl);
     p = h->AZ; dfree(p);
     dfree(h->t3Lin); dfree(h->t3LT); dfree(h->t3Ztb); dfree(h->t3ZtbT); dfree(h->t3ZIT); dfree(h->t3ZI);
     dfree(h->t3Rtb); dfree(h->t3RI); dfree(h->t3W);
@@ -550,6 +550,9 @@ slab_status slab_factor(const slab_grid* grid, const slab_coeffs* co, int b, con
     dfree(h->w16);                                     // factor-only product work
     h->w16 = nullptr;
     h->w16_bytes = 0;
+    dfree(h->pnl);
+    h->pnl = nullptr;
+    h->pnl_bytes = 0;
     dfree(h->t3Rtb);                                   // 3-D factor-only arrays
     dfree(h->t3RI);
     dfree(h->t3W);

@@ -288,25 +288,42 @@ __device__ void chol_inv_tile(const T* S, T* Li, unsigned* status) {
     __syncthreads();
 }
 
-// Panel of tile column kb of the tall matrix Wt (leading dimension ld): every CTA factors the
-// diagonal tile Wt[kb][kb] and CTA x replaces the tile Wt[kb+1+x][kb] by itself times L_kk^{-T}.
+// Panel of tile column kb of the tall matrix Wt (leading dimension ld), in two launches.
+// panel_diag_kernel (one CTA per matrix of the batch): Cholesky of the diagonal tile
+// Wt[kb][kb] = L L^T and Linv = L^{-1} to Lw (64 x 64 per matrix, row-major).
 template <typename T>
-__global__ void __launch_bounds__(256) panel_kernel(T* Wt, int64_t ld, int kb, unsigned* status, int64_t bstride) {
+__global__ void __launch_bounds__(256) panel_diag_kernel(const T* Wt, int64_t ld, int kb, unsigned* status,
+                                                         int64_t bstride, T* Lw) {
     extern __shared__ unsigned char smem_raw[];
     T* S = reinterpret_cast<T*>(smem_raw);
     T* Li = S + TL * TLP;
+    const int tid = threadIdx.x;
+    Wt += (int64_t)blockIdx.y * bstride;
+    const T* D = Wt + (int64_t)kb * TL * ld + (int64_t)kb * TL;
+    for (int i = tid; i < TL * TL; i += 256) S[(i / TL) * TLP + i % TL] = D[(int64_t)(i / TL) * ld + i % TL];
+    __syncthreads();
+    chol_inv_tile<T>(S, Li, status);
+    T* out = Lw + (int64_t)blockIdx.y * TL * TL;
+    for (int i = tid; i < TL * TL; i += 256) out[i] = Li[(i / TL) * TLP + i % TL];
+}
+
+// panel_apply_kernel: CTA x replaces the tile Wt[kb+1+x][kb] by itself times L^{-T}.
+template <typename T>
+__global__ void __launch_bounds__(256) panel_apply_kernel(T* Wt, int64_t ld, int kb, int64_t bstride,
+                                                          const T* Lw) {
+    extern __shared__ unsigned char smem_raw[];
+    T* Li = reinterpret_cast<T*>(smem_raw);
     T* X = Li + TL * TLP;
     const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
     const int r = kb + 1 + blockIdx.x;
-    Wt += (int64_t)blockIdx.y * bstride;                 // batch of independent tall matrices
-    const T* D = Wt + (int64_t)kb * TL * ld + (int64_t)kb * TL;
+    Wt += (int64_t)blockIdx.y * bstride;
     T* src = Wt + (int64_t)r * TL * ld + (int64_t)kb * TL;
+    const T* lin = Lw + (int64_t)blockIdx.y * TL * TL;
     for (int i = tid; i < TL * TL; i += 256) {
-        S[(i / TL) * TLP + i % TL] = D[(int64_t)(i / TL) * ld + i % TL];
+        Li[(i / TL) * TLP + i % TL] = lin[i];
         X[(i / TL) * TLP + i % TL] = src[(int64_t)(i / TL) * ld + i % TL];
     }
     __syncthreads();
-    chol_inv_tile<T>(S, Li, status);
     T acc[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -1228,8 +1245,6 @@ slab_status cr_factor(slab_handle* h) {
     T* P = (T*)h->crP;
     T* Qt = (T*)h->crQt;
     T* Q = (T*)h->crQ;
-    const size_t smem = 3 * TL * TLP * sizeof(T);
-    SLAB_CK(h, cudaFuncSetAttribute(panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     SLAB_CK(h, cudaMemcpyAsync(D, h->Tb, NI * blk * sizeof(T), cudaMemcpyDeviceToDevice, h->stream));
     if (NI > 1)
         SLAB_CK(h, cudaMemcpyAsync(E, h->To, (NI - 1) * blk * sizeof(T), cudaMemcpyDeviceToDevice, h->stream));
@@ -1353,6 +1368,20 @@ __global__ void copy_batched_kernel(const T* __restrict__ in, int64_t sin, T* __
 }
 }  // namespace
 
+// Panel workspace (one 64 x 64 inverse per matrix of a batch); grown on demand during the factor.
+static slab_status ensure_panel_work(slab_handle* h, size_t bytes) {
+    if (h->pnl_bytes >= bytes) return SLAB_OK;
+    if (h->pnl) cudaFree(h->pnl);                      // waits for the work that may still read it
+    h->pnl = nullptr;
+    h->pnl_bytes = 0;
+    if (cudaMalloc(&h->pnl, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return SLAB_ENOMEM;
+    }
+    h->pnl_bytes = bytes;
+    return SLAB_OK;
+}
+
 template <typename T>
 slab_status dense_gemm(slab_handle* h, int cls, int M, int N, int K, T alpha, const T* A, int64_t lda, int64_t sA,
                        const T* B, int64_t ldb, int64_t sB, T beta, T* C, int64_t ldc, int64_t sC, int transC,
@@ -1401,18 +1430,31 @@ slab_status dense_copy(slab_handle* h, const T* in, int64_t sin, T* out, int64_t
 template <typename T>
 slab_status dense_tall_cholesky(slab_handle* h, T* W, int ncols, int ident0, int batch, int64_t bstride) {
     constexpr int OB = 4;                              // panels per outer block
-    const size_t smem = 3 * TL * TLP * sizeof(T);
-    SLAB_CK(h, cudaFuncSetAttribute(panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const size_t smem = 2 * TL * TLP * sizeof(T);
+    SLAB_CK(h, cudaFuncSetAttribute(panel_diag_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SLAB_CK(h, cudaFuncSetAttribute(panel_apply_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int bchunk = std::min(batch, 65535);
     slab_status st;
+    if ((st = ensure_panel_work(h, (size_t)bchunk * TL * TL * sizeof(T)))) return st;
+    T* Lw = (T*)h->pnl;
     const int nt = ncols / TL;
     for (int kb = 0; kb < nt; ++kb) {
         const int rows = ident0 + (kb + 1) * TL;      // identity rows below are still zero in these columns
         const int nrt = rows / TL - kb - 1;
         for (int b0 = 0; b0 < batch; b0 += 65535) {
             const int nb = std::min(65535, batch - b0);
-            SLAB_PROF(h, KC_PANEL);
-            panel_kernel<T><<<dim3(nrt, nb), 256, smem, h->stream>>>(W + b0 * bstride, ncols, kb, h->dstatus, bstride);
-            SLAB_CK_LAUNCH(h);
+            {
+                SLAB_PROF(h, KC_PANEL);
+                panel_diag_kernel<T><<<dim3(1, nb), 256, smem, h->stream>>>(W + b0 * bstride, ncols, kb, h->dstatus,
+                                                                             bstride, Lw);
+                SLAB_CK_LAUNCH(h);
+            }
+            if (nrt > 0) {
+                SLAB_PROF(h, KC_PANEL);
+                panel_apply_kernel<T><<<dim3(nrt, nb), 256, smem, h->stream>>>(W + b0 * bstride, ncols, kb, bstride,
+                                                                               Lw);
+                SLAB_CK_LAUNCH(h);
+            }
         }
         const int kb0 = kb - kb % OB, kend = std::min(nt, kb0 + OB);     // this outer block: panels [kb0, kend)
         const int c0 = (kb + 1) * TL, cend = kend * TL;

@@ -64,6 +64,8 @@ struct slab_handle {
     void* ozw;                // work area of those products
     void* w16;                // FP32 factor: operand splits of the FP16 three-product path (factor only)
     size_t w16_bytes;
+    void* pnl;                // panel inverses of the tall Cholesky (factor only)
+    size_t pnl_bytes;
     size_t rsz2;              // bytes of the Stage-2 scalar
     void *Tb1, *To1;          // mixed mode: T assembled in the Stage-1 scalar (factor only)
     void *wX2, *wZ2;          // mixed mode: interface vectors in the Stage-2 scalar
