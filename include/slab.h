@@ -185,6 +185,19 @@ slab_status slab_apply_residual(slab_handle* h, const double* u, const double* f
 slab_status slab_apply(slab_handle* h, const double* x, double* y, int k);
 
 /*
+ * Non-zero Dirichlet data (Sec. 1.1 with u = g on the boundary instead of 0).  Eliminating the
+ * boundary unknowns from the interior rows gives A u = f + lift(g) with
+ *   lift(g)_P = h^-2 sum over the boundary neighbours Q of P of k_PQ g_Q,
+ * k_PQ the operator's face coefficients; this writes f_out = f + lift(g), so that
+ * slab_solve(h, f_out, u, k) returns the interior values of the solution.
+ * g: device, k x (n+1)^d FP64 over all nodes (C order [z][y][x], only boundary entries are
+ * read); f: device, k x (n-1)^d interior load, or NULL for zero; f_out: device, same layout as f,
+ * may be f itself.  Caller owns all buffers.  SLAB_EINVAL for a null handle, g or f_out, or
+ * k < 0.  Asynchronous on the handle's stream.
+ */
+slab_status slab_boundary_lift(slab_handle* h, const double* g, const double* f, double* f_out, int k);
+
+/*
  * Adjoint solve and coefficient gradient (DIFFUSION).  Given dL/du (device,
  * [k][(n-1)^d]) and the state u, solves A^T lambda = dL/du with the stored
  * factors (A is symmetric here) and, if dLdkappa != NULL, accumulates into it

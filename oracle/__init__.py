@@ -21,6 +21,7 @@ Contents
   * ``schur_dense``: the exact Schur complement A_II - A_IJ A_JJ^-1 A_JI of the
     dense matrix, the invariant the assembled T must equal.
   * ``kappa_gradient``: dL/dkappa = -lam^T (dA/dkappa) u for the diffusion kind.
+  * ``boundary_lift``: non-zero Dirichlet data moved into the load of the interior system.
 
 Readings of the paper used here (the paper is silent or garbled on these):
   b is the interface spacing (interfaces at x = q b, slab interiors b-1 wide);
@@ -88,6 +89,9 @@ def lib():
             L.orc_dense_solve.argtypes = [_i64, _dp, ctypes.c_int, _dp]
             L.orc_kappa_gradient.restype = None
             L.orc_kappa_gradient.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp]
+            L.orc_boundary_lift.restype = None
+            L.orc_boundary_lift.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int, _dp,
+                                            ctypes.c_void_p, _dp]
             L.orc_threads.restype = ctypes.c_int
             _lib = L
     return _lib
@@ -171,6 +175,20 @@ def assemble(dim: int, n: int, kind: int, kappa=None, c=None, omega: float = 0.0
     nnz = lib().orc_assemble(dim, n, kind, _p(kap), _p(cc), float(omega), _p(rowptr, _lp),
                              _p(col, _lp), _p(val))
     return CSR(N, rowptr, col[:nnz].copy(), val[:nnz].copy())
+
+
+def boundary_lift(dim: int, n: int, kind: int, g: np.ndarray, f=None, kappa=None) -> np.ndarray:
+    """Load of the interior system for Dirichlet data g (rows = right-hand sides, all (n+1)^d
+    nodes): f + h^-2 sum over boundary neighbours Q of k_PQ g_Q (Sec. 1.1 with u = g on the
+    boundary, the boundary unknowns eliminated from the interior rows)."""
+    kap, _ = _node_arrays(dim, n, kind, kappa, None)
+    G = np.ascontiguousarray(np.atleast_2d(g), dtype=np.float64)
+    k = G.shape[0]
+    assert G.shape[1] == (n + 1) ** dim
+    out = np.empty((k, (n - 1) ** dim))
+    F = None if f is None else np.ascontiguousarray(np.atleast_2d(f), dtype=np.float64)
+    lib().orc_boundary_lift(dim, n, kind, _p(kap), k, _p(G), None if F is None else F.ctypes.data, _p(out))
+    return out
 
 
 def assemble_problem(p) -> CSR:

@@ -120,6 +120,50 @@ int64_t orc_assemble(int dim, int n, int kind, const double* kappa, const double
     return nnz;
 }
 
+/*
+ * Dirichlet data moved into the load (the problem of Sec. 1.1 with u = g on the boundary):
+ * eliminating the boundary unknowns from the interior rows of the full operator gives
+ *   A u_I = f_I + h^-2 sum_{faces P~Q, Q on the boundary} k_PQ g_Q,
+ * so f_out[r][P] = f[r][P] + that sum (f may be NULL: zero).  g is [k][(n+1)^d] over all nodes
+ * (interior entries unused), f and f_out are [k][(n-1)^d] in the natural interior order.
+ */
+void orc_boundary_lift(int dim, int n, int kind, const double* kappa, int k, const double* g,
+                       const double* f, double* f_out) {
+    const int m = n - 1;
+    const double ih2 = (double)n * (double)n;
+    const int zmax = dim == 3 ? m : 1;
+    const int64_t N = ipow(m, dim), nodes = ipow(n + 1, dim);
+    for (int r = 0; r < k; ++r) {
+        const double* gr = g + (int64_t)r * nodes;
+        int64_t row = 0;
+        for (int z = 1; z <= zmax; ++z)
+            for (int y = 1; y <= m; ++y)
+                for (int x = 1; x <= m; ++x, ++row) {
+                    const int zz = dim == 3 ? z : 0;
+                    const int64_t P = node_id(dim, n, x, y, zz);
+                    int nx[6], ny[6], nz[6], cnt = 0;
+                    nx[cnt] = x - 1; ny[cnt] = y; nz[cnt] = zz; ++cnt;
+                    nx[cnt] = x + 1; ny[cnt] = y; nz[cnt] = zz; ++cnt;
+                    nx[cnt] = x; ny[cnt] = y - 1; nz[cnt] = zz; ++cnt;
+                    nx[cnt] = x; ny[cnt] = y + 1; nz[cnt] = zz; ++cnt;
+                    if (dim == 3) {
+                        nx[cnt] = x; ny[cnt] = y; nz[cnt] = zz - 1; ++cnt;
+                        nx[cnt] = x; ny[cnt] = y; nz[cnt] = zz + 1; ++cnt;
+                    }
+                    double v = f ? f[(int64_t)r * N + row] : 0.0;
+                    for (int t = 0; t < cnt; ++t) {
+                        const int bx = nx[t], by = ny[t], bz = nz[t];
+                        const int interior = bx >= 1 && bx <= m && by >= 1 && by <= m &&
+                                             (dim == 2 || (bz >= 1 && bz <= m));
+                        if (interior) continue;
+                        const int64_t Q = node_id(dim, n, bx, by, bz);
+                        v += ih2 * face_coef(kind, kappa, P, Q) * gr[Q];
+                    }
+                    f_out[(int64_t)r * N + row] = v;
+                }
+    }
+}
+
 /* y = A x for k vectors (x, y laid out [k][N]). */
 void orc_csr_matvec(int64_t N, const int64_t* rowptr, const int64_t* col, const double* val,
                     int k, const double* x, double* y) {

@@ -49,6 +49,7 @@ SIGNATURES = {
                            ctypes.POINTER(c_int)]),
     "slab_apply_residual": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int]),
     "slab_apply": (c_int, [c_void_p, c_void_p, c_void_p, c_int]),
+    "slab_boundary_lift": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int]),
     "slab_adjoint": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int]),
     "slab_reduced_rhs": (c_int, [c_void_p, c_void_p, c_void_p, c_int]),
     "slab_interface_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_int]),

@@ -567,6 +567,13 @@ slab_status slab_apply_residual(slab_handle* h, const double* u, const double* f
     return launch_residual(h, u, f, r, k, nullptr, nullptr);
 }
 
+slab_status slab_boundary_lift(slab_handle* h, const double* g, const double* f, double* f_out, int k) {
+    if (!h || k < 0) return SLAB_EINVAL;
+    if (k == 0) return SLAB_OK;
+    if (!g || !f_out) return SLAB_EINVAL;
+    return launch_boundary_lift(h, g, f, f_out, k);
+}
+
 slab_status slab_apply(slab_handle* h, const double* x, double* y, int k) {
     if (!h || k < 0) return SLAB_EINVAL;
     if (k == 0) return SLAB_OK;

@@ -189,6 +189,7 @@ slab_status launch_coefficients(slab_handle* h, const double* kappa, const doubl
 slab_status launch_residual(slab_handle* h, const double* u, const double* f, double* r, int k,
                             double* nrm_r, double* nrm_f);   // nrm_* may be NULL (device, k each)
 slab_status launch_apply(slab_handle* h, const double* x, double* y, int k);
+slab_status launch_boundary_lift(slab_handle* h, const double* g, const double* f, double* fo, int k);
 slab_status launch_kappa_gradient(slab_handle* h, const double* u, const double* lam, double* g, int k);
 // FP64 vector kernels for the Krylov refinement (batched over k vectors of length N)
 slab_status vec_dot(slab_handle* h, const double* x, const double* y, int64_t N, int k, double* part, double* out);

@@ -237,6 +237,36 @@ __global__ void __launch_bounds__(128) stencil3d_kernel(int n, int k, const doub
     else r[(int64_t)q * N + o] = Au;
 }
 
+// Dirichlet data into the load: f_out = f + h^-2 sum over the boundary neighbours Q of each
+// interior node P of k_PQ g_Q (g over all (n+1)^d nodes per right-hand side, f may be null).
+// One thread per interior unknown and right-hand side, x fastest.
+__global__ void boundary_lift_kernel(int dim, int n, int k, const double* __restrict__ AX,
+                                     const double* __restrict__ AY, const double* __restrict__ AZ,
+                                     const double* __restrict__ g, const double* __restrict__ f, double* fo) {
+    const int s = n - 1, np1 = n + 1;
+    const int64_t N = dim == 3 ? (int64_t)s * s * s : (int64_t)s * s;
+    const int64_t nodes = dim == 3 ? (int64_t)np1 * np1 * np1 : (int64_t)np1 * np1;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= N * k) return;
+    const int64_t q = idx / N, o = idx % N;
+    const int x = (int)(o % s) + 1;
+    const int y = (int)((o / s) % s) + 1;
+    const int z = dim == 3 ? (int)(o / ((int64_t)s * s)) + 1 : 0;
+    const int64_t P = ((int64_t)z * np1 + y) * np1 + x;
+    const int64_t sy = np1, sz = (int64_t)np1 * np1;
+    const double* gq = g + q * nodes;
+    double v = 0.0;
+    if (x == 1) v += AX[P - 1] * gq[P - 1];
+    if (x == s) v += AX[P] * gq[P + 1];
+    if (y == 1) v += AY[P - sy] * gq[P - sy];
+    if (y == s) v += AY[P] * gq[P + sy];
+    if (dim == 3) {
+        if (z == 1) v += AZ[P - sz] * gq[P - sz];
+        if (z == s) v += AZ[P] * gq[P + sz];
+    }
+    fo[idx] = (f ? f[idx] : 0.0) + (double)n * (double)n * v;
+}
+
 // ---------------------------------------------------------------- FP64 vector kernels (Krylov)
 // Batched over k vectors of length N, vector q at x + q * N.  Dot products are reduced in a
 // fixed order (per-block partials, then one block per vector), so they are deterministic.
@@ -372,6 +402,17 @@ slab_status launch_residual(slab_handle* h, const double* u, const double* f, do
     else
         stencil2d_kernel<true, false><<<grid, 256, 0, h->stream>>>(n, k, h->AX, h->AY, h->DG, u, f, r, nrm_r,
                                                                    nullptr, part, tickets);
+    SLAB_CK_LAUNCH(h);
+    return SLAB_OK;
+}
+
+slab_status launch_boundary_lift(slab_handle* h, const double* g, const double* f, double* fo, int k) {
+    const int s = h->n - 1;
+    const int64_t tot = (h->dim == 3 ? (int64_t)s * s * s : (int64_t)s * s) * k;
+    if (tot <= 0) return SLAB_OK;
+    SLAB_PROF(h, KC_OTHER);
+    boundary_lift_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>(h->dim, h->n, k, h->AX, h->AY, h->AZ,
+                                                                               g, f, fo);
     SLAB_CK_LAUNCH(h);
     return SLAB_OK;
 }

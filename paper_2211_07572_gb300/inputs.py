@@ -145,6 +145,21 @@ def constant_helmholtz(n: int, b: int, omega: float, rhs_seed: int = 7, k: int =
                    c=np.ones((n + 1, n + 1)), omega=omega, f=normal_rhs(2, n, k, rhs_seed))
 
 
+def bessel_j0(n: int, b: int, wavenumber: float = 27.1, source=(-0.1, 0.5)) -> dict:
+    """Constant-coefficient Helmholtz -Lap u - k^2 u = 0 on the unit square with Dirichlet data
+    u = J_0(k |x - x_s|), x_s outside the domain (the paper's low-order benchmark PDE, Sec. 6.1,
+    eq. "constant_coeff_helm").  Returns the problem (zero load), the data g on all (n+1)^2
+    nodes (C order [y][x]) and the true solution at the interior nodes."""
+    from scipy.special import j0
+    t = np.arange(n + 1) / n
+    Y, X = np.meshgrid(t, t, indexing="ij")
+    u_nodes = j0(wavenumber * np.hypot(X - source[0], Y - source[1]))
+    prob = Problem(name=f"helmholtz_j0_n{n}_b{b}", dim=2, n=n, b=b, kind=HELMHOLTZ, c=np.ones((n + 1, n + 1)),
+                   omega=float(wavenumber), f=np.zeros((1, (n - 1) ** 2)),
+                   meta=dict(wavenumber=wavenumber, source=tuple(source)))
+    return dict(problem=prob, g=u_nodes.reshape(1, -1), u_true=u_nodes[1:n, 1:n].reshape(1, -1))
+
+
 # The workloads, named by what they are (sizes and seeds fixed here).
 def poisson_sine_128() -> Problem:
     """Poisson, n = 128, b = 16, manufactured sine solution."""

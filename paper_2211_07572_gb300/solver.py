@@ -138,6 +138,19 @@ class SlabSolver:
         _lib.check(self.lib.slab_apply(self.h, _ptr(x), _ptr(y), x.shape[0]), "apply")
         return y
 
+    def boundary_lift(self, g, f=None) -> torch.Tensor:
+        """f + lift(g): the load of the interior system for Dirichlet data g given on all
+        (n+1)^dim nodes (rows = right-hand sides); solve() with it gives the interior solution."""
+        g = _dev(g, self.device)
+        g = g.reshape(-1, (self.n + 1) ** self.dim)
+        k = g.shape[0]
+        fo = torch.empty((k, self.N), dtype=torch.float64, device=self.device)
+        fi = None if f is None else self._vec(f)
+        if fi is not None and fi.shape[0] != k:
+            raise ValueError("f and g need the same number of right-hand sides")
+        _lib.check(self.lib.slab_boundary_lift(self.h, _ptr(g), _ptr(fi), _ptr(fo), k), "boundary_lift")
+        return fo
+
     def adjoint(self, dLdu, u=None, allow_noconv: bool = False) -> Tuple[torch.Tensor, Optional[torch.Tensor]]:
         g = self._vec(dLdu)
         lam = torch.empty_like(g)

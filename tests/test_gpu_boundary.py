@@ -1,0 +1,92 @@
+"""Non-zero Dirichlet data (slab_boundary_lift) and the paper's J_0 benchmark.
+
+The lift moves boundary values into the load of the interior system (Sec. 1.1 with u = g on
+the boundary); the J_0 benchmark (Sec. 6.1, eq. "constant_coeff_helm") is constant-coefficient
+Helmholtz with Dirichlet data u_true = J_0(kappa |x - (-0.1, 0.5)|).  Checked: the lift
+against the oracle's, the solution against the oracle's banded LU at n = 256, and the error
+against u_true at n = 1024 against the value the paper prints (tests/golden).
+"""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2211_07572_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "helmholtz_j0_fd_table.txt")
+
+
+def _golden_row():
+    rows = [l.split() for l in open(GOLD) if l.strip() and not l.startswith("#")]
+    N, b, kappa, rres, rtrue = (float(v) for v in rows[0])
+    return dict(N=N, b=b, kappa=kappa, relerr_res=rres, relerr_true=rtrue)
+
+
+@pytest.mark.parametrize("dim,n,b", [(2, 40, 8), (2, 33, 11), (3, 12, 4)])
+def test_boundary_lift_matches_oracle(dim, n, b):
+    from paper_2211_07572_gb300.solver import SlabSolver
+    p = inputs.diffusion(n, b, k=2, dim=dim, n_modes=8, field_seed=6, rhs_seed=106)
+    rng = np.random.default_rng(n)
+    g = rng.standard_normal((2, (n + 1) ** dim))
+    s = SlabSolver(dim, n, b, p.kind, kappa=p.kappa, precision="fp64")
+    got = s.boundary_lift(torch.from_numpy(g).cuda(), torch.from_numpy(p.f).cuda()).cpu().numpy()
+    got0 = s.boundary_lift(torch.from_numpy(g).cuda()).cpu().numpy()
+    s.close()
+    want = oracle.boundary_lift(dim, n, p.kind, g, f=p.f, kappa=p.kappa)
+    want0 = oracle.boundary_lift(dim, n, p.kind, g, kappa=p.kappa)
+    assert np.abs(got - want).max() <= 1e-13 * np.abs(want).max()
+    assert np.abs(got0 - want0).max() <= 1e-13 * np.abs(want0).max()
+
+
+def test_boundary_lift_rejects_null_data():
+    from paper_2211_07572_gb300 import _lib
+    from paper_2211_07572_gb300.solver import SlabSolver
+    s = SlabSolver(2, 16, 4, inputs.POISSON, precision="fp64")
+    out = torch.empty(1, 15 * 15, dtype=torch.float64, device="cuda")
+    st = s.lib.slab_boundary_lift(s.h, None, None, out.data_ptr(), 1)
+    s.close()
+    assert st == _lib.SLAB_EINVAL
+
+
+def test_bessel_j0_n256_matches_oracle():
+    """Default FP32 factor (FP64 interface for Helmholtz) with refinement: the solution of the
+    lifted system equals the oracle's banded LU solution."""
+    from paper_2211_07572_gb300.solver import SlabSolver
+    n, b = 256, 16
+    d = inputs.bessel_j0(n, b)
+    p = d["problem"]
+    s = SlabSolver(2, n, b, p.kind, c=p.c, omega=p.omega, rtol=1e-12, max_refine=40)
+    f = s.boundary_lift(torch.from_numpy(d["g"]).cuda())
+    u, rel, _ = s.solve(f)
+    s.close()
+    u = u.cpu().numpy()
+    fo = oracle.boundary_lift(2, n, p.kind, d["g"])
+    uo = oracle.solve(p, fo)
+    A = oracle.assemble_problem(p)
+    assert oracle.relres(A, u, fo).max() <= 1e-10
+    assert np.linalg.norm(u - uo) / np.linalg.norm(uo) <= 1e-8
+
+
+def test_bessel_j0_n1024_error_matches_the_paper():
+    """N = 1.0M, kappa = 27.1 (the first row of the paper's second-order FD Helmholtz table): the
+    discrete solution's error against J_0 is a property of the discretization; the paper prints
+    1.8e-3 for its N = 1.0M grid, here n = 1024 (N = 1.05M, slightly finer), so the value agrees
+    to within the grid difference (35 %)."""
+    from paper_2211_07572_gb300.solver import SlabSolver
+    row = _golden_row()
+    n, b = 1024, 32
+    d = inputs.bessel_j0(n, b, wavenumber=row["kappa"])
+    p = d["problem"]
+    s = SlabSolver(2, n, b, p.kind, c=p.c, omega=p.omega, precision="fp64", rtol=1e-11)
+    f = s.boundary_lift(torch.from_numpy(d["g"]).cuda())
+    u, rel, _ = s.solve(f)
+    r = s.residual(u, f)
+    s.close()
+    relres = float(torch.linalg.norm(r) / torch.linalg.norm(f))
+    err = float(np.linalg.norm(u.cpu().numpy() - d["u_true"]) / np.linalg.norm(d["u_true"]))
+    assert relres <= 1e-10
+    assert abs(err - row["relerr_true"]) <= 0.35 * row["relerr_true"], err
