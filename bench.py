@@ -391,19 +391,20 @@ def run_gpu(args):
     ms = e0.elapsed_time(e1) / args.steps
     # end to end through the public API with host buffers: H2D of f and D2H of u inside the region.
     # The load's copy runs on a copy stream while the factor (which does not need f) runs.
+    # Device staging buffers for the load and the solution are allocated once, outside the region.
     u_host = torch.empty_like(f_host).pin_memory()
     copy_stream = torch.cuda.Stream(device=dev)
+    fd = torch.empty_like(f)
+    ud = torch.empty_like(f)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    ne2e = max(1, args.steps // 2)
+    ne2e = max(1, args.steps)
     for _ in range(ne2e):
         with torch.cuda.stream(copy_stream):
-            fd = f_host.to(dev, non_blocking=True)
+            fd.copy_(f_host, non_blocking=True)
             ready = copy_stream.record_event()
-        ud = torch.empty_like(f)
         s_e2e = make()                                   # factor on `stream`, overlapping the copy
         stream.wait_event(ready)
-        fd.record_stream(stream)
         s_e2e.solve(fd, ud, allow_noconv=True)
         s_e2e.close()
         u_host.copy_(ud, non_blocking=True)

@@ -39,6 +39,7 @@ def test_argument_validation_needs_no_gpu():
     g4 = _lib.SlabGrid(4, 64)
     assert lib.slab_factor(ctypes.byref(g4), ctypes.byref(co), 8, None, ctypes.byref(h)) == _lib.SLAB_EINVAL
     assert lib.slab_solve(None, None, None, 1, None, None) == _lib.SLAB_EINVAL
+    assert lib.slab_boundary_lift(None, None, None, None, 1) == _lib.SLAB_EINVAL
     assert lib.slab_strerror(_lib.SLAB_ENOCONV).decode().startswith("iterative refinement")
     o = _lib.SlabOpts()
     lib.slab_default_opts(ctypes.byref(o))
