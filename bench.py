@@ -597,6 +597,81 @@ def run_adjoint_batch(args):
     print(json.dumps(line))
 
 
+def run_j0(args):
+    """Second workload: constant-coefficient Helmholtz with Dirichlet data J_0(k |x - (-0.1, 0.5)|),
+    n = 1024, b = 32, k = 27.1 (the first row of the paper's second-order FD table, Sec. 6.2).  A step
+    is: factor, move the boundary data into the load (slab_boundary_lift), solve with refinement."""
+    import numpy as np
+    import torch
+
+    from paper_2211_07572_gb300 import inputs
+    from paper_2211_07572_gb300.solver import SlabSolver
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    n, b = args.n or 1024, args.b or 32
+    d = inputs.bessel_j0(n, b)
+    p = d["problem"]
+    c = torch.from_numpy(p.c).to(dev)
+    g_host = torch.from_numpy(d["g"]).pin_memory()
+    g = g_host.to(dev)
+    prec = args.precision
+    stream = torch.cuda.current_stream(dev)
+
+    def step(gd, counts=None):
+        s = SlabSolver(2, n, b, p.kind, c=c, omega=p.omega, precision=prec, rtol=1e-10, max_refine=40,
+                       stream=stream, device=dev)
+        fd = s.boundary_lift(gd)
+        u, rel, it = s.solve(fd, allow_noconv=True)
+        if counts is not None:
+            counts.append(sum(s.profile_read()[1].values()))
+        s.close()
+        return u, rel, it
+
+    for _ in range(args.warmup):
+        step(g)
+    sampler = ClockSampler()
+    sampler.start()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    launches, its, rels = [], [], []
+    for _ in range(args.steps):
+        u, rel, it = step(g, launches)
+        its.append(it)
+        rels.append(float(np.max(rel)))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    # end to end: boundary data from pinned host memory, solution back to pinned host memory
+    u_host = torch.empty((1, (n - 1) ** 2), dtype=torch.float64).pin_memory()
+    gd = torch.empty_like(g)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        gd.copy_(g_host, non_blocking=True)
+        u, _, _ = step(gd)
+        u_host.copy_(u, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e = (time.perf_counter() - t0) / args.steps
+    sampler.stop()
+    err = float(np.linalg.norm(u_host.numpy() - d["u_true"]) / np.linalg.norm(d["u_true"]))
+    print(json.dumps({
+        "metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"fp32": "f32 slab trees, f64 interface, f64 refinement"}.get(prec, prec),
+        "data": "synthetic",
+        "config": {"workload": f"2D constant-coefficient Helmholtz n={n} b={b} wavenumber 27.1, Dirichlet data "
+                               "J_0(k|x-(-0.1,0.5)|), zero load", "n": n, "b": b, "precision": prec,
+                   "l2": "every step streams > 1 GB (>> 129 MB L2); no explicit flush"},
+        "max_relres": max(rels), "refine_steps": its, "relerr_true": err,
+        "paper_relerr_true_N1M": 1.8e-3,
+        "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": int(g_host.numel() * 8),
+                "d2h_bytes_per_step": int(u_host.numel() * 8)},
+        "gpu_launches": launches[-1] if launches else None,
+        "clocks": sampler.summary(),
+    }))
+
+
 def run_reference(args):
     n, b, k = WORKLOAD["n"], WORKLOAD["b"], WORKLOAD["k"]
     rank = int(os.environ.get("RANK", "0"))
@@ -636,8 +711,8 @@ def main():
     ap.add_argument("--count", type=int, default=0, help="adjoint256: number of problems (0: all 256)")
     ap.add_argument("--wave", type=int, default=32, help="adjoint256: problems per wave")
     ap.add_argument("--workload", default="diffusion2048",
-                    choices=["diffusion2048", "helmholtz4096", "diffusion3d96", "adjoint256"],
-                    help="diffusion2048: the default bench line; helmholtz4096, diffusion3d96: the other workloads")
+                    choices=["diffusion2048", "helmholtz4096", "diffusion3d96", "adjoint256", "helmholtzj0"],
+                    help="diffusion2048: the default bench line; helmholtz4096, diffusion3d96, adjoint256, helmholtzj0: the other workloads")
     ap.add_argument("--krylov", type=int, default=0, help="0: plain refinement; m: FP64 GMRES(m) refinement")
     ap.add_argument("--interface", default="default", choices=["default", "fp32", "fp64", "fp64tc", "tf32"],
                     help="precision of the interface system (fp64tc: FP64-accurate tensor-core products)")
@@ -651,6 +726,8 @@ def main():
         run_reference(args)
     elif args.workload == "adjoint256":
         run_adjoint_batch(args)
+    elif args.workload == "helmholtzj0":
+        run_j0(args)
     else:
         run_gpu(args)
 
