@@ -1423,7 +1423,8 @@ slab_status dense_copy(slab_handle* h, const T* in, int64_t sin, T* out, int64_t
 // Cholesky of the leading ncols x ncols block of a batch of tall matrices (row-major, ld = ncols,
 // bstride apart) whose rows below are eliminated with it: rows [ncols, ident0) receive B^T L^{-T},
 // rows [ident0, ident0 + ncols), which must hold the identity, receive L^{-T}.
-// Right-looking with two block levels: 64-column panels (panel_kernel); after each panel, the
+// Right-looking with two block levels: 64-column panels (panel_diag_kernel factors the diagonal
+// tile once, panel_apply_kernel scales the tiles below by its inverse); after each panel, the
 // update of the remaining columns of its outer block of OB panels only; when an outer block is
 // complete, one rank-(OB 64) update of every column to its right.  The trailing matrix is thus
 // read and written once per outer block instead of once per panel.
