@@ -338,6 +338,8 @@ def run_gpu(args):
         MMA_MODE.update(schur_update="tf32", trailing="tf32", assemble_T="tf32")   # factor products
     elif prec == "fp32" and not helm:
         MMA_MODE.update(schur_update="f16x3", trailing="f16x3")
+        if dim == 3:
+            MMA_MODE["assemble_T"] = "f16x3"                    # 3-D T assembly products
     if helm:
         stage2 = "sweep"
     else:

@@ -387,10 +387,12 @@ slab_status transpose(slab_handle* h, const T* in, T* out, int n) {
     return transpose_batched<T>(h, in, 0, out, 0, n, 1);
 }
 
-// The factor's Schur and trailing products (FP32, 3xTF32 accuracy requested) run as three FP16
-// products of row-scaled hi/lo splits when the handle holds a large enough work buffer.
+// The factor's Schur, trailing and (3-D) T-assembly products (FP32, 3xTF32 accuracy requested)
+// run as three FP16 products of row-scaled hi/lo splits when the handle holds a large enough
+// work buffer (it exists only while the factor runs).
 inline bool use_f16x3(slab_handle* h, int cls, TcGemmArgs& g) {
-    if (!h->w16 || g.split != 1 || (cls != KC_SYRK && cls != KC_TRAIL) || g.K % 64) return false;
+    if (!h->w16 || g.split != 1 || (cls != KC_SYRK && cls != KC_TRAIL && cls != KC_ASSEMBLE) || g.K % 64)
+        return false;
     if (f16x3_work_bytes(g.M, g.N, g.K, g.batch, f16x3_shared(g)) > h->w16_bytes) return false;
     g.split = 2;
     g.w16 = h->w16;
