@@ -25,6 +25,55 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "factor+solve s at 1e-10 rel. residual vs plain FP64 GPU; dense TFLOP/s % of peak"
+
+
+# ---------------------------------------------------------------- replicas (one process per GPU)
+# The method's multi-GPU form here is replicas: under torchrun every rank factors and solves its
+# own copy of the workload on its own GPU (no exchange on the data path); the timed region is
+# bracketed by barriers and the slowest rank's time is reported, by rank 0 alone.
+def dist_env():
+    """(rank, local_rank, world_size) from the launcher's environment; (0, 0, 1) without one."""
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+def dist_init(backend: str) -> None:
+    """Join the process group when more than one rank runs (env:// rendezvous)."""
+    import torch.distributed as dist
+    if dist_env()[2] > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend, init_method="env://")
+
+
+def _dist_on() -> bool:
+    import torch.distributed as dist
+    return dist.is_available() and dist.is_initialized()
+
+
+def dist_barrier() -> None:
+    if _dist_on():
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def dist_max(x: float) -> float:
+    """Largest value of x over the ranks (x itself with one rank)."""
+    if not _dist_on():
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_device():
+    """This rank's GPU (cuda:LOCAL_RANK), made current, with the process group joined."""
+    import torch
+    dev = torch.device("cuda", dist_env()[1])
+    torch.cuda.set_device(dev)
+    dist_init("nccl")
+    return dev
 WORKLOAD = dict(workload="2D var-coef diffusion n=2048 b=32 k=64 (kappa=exp(16-mode field), f~N(0,1)), "
                          "FP32 factor + FP64 refinement to 1e-10",
                 n=2048, b=32, k=64, rtol=1e-10, kind="diffusion")
@@ -313,8 +362,8 @@ def run_gpu(args):
         W["workload"] = (f"2D Helmholtz n={W['n']} b={W['b']} point source" if helm else
                          f"2D var-coef diffusion n={W['n']} b={W['b']} k={W['k']}")
     n, b, k = W["n"], W["b"], W["k"]
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
+    dev = rank_device()
+    rank, _, world = dist_env()
     if helm:
         p = inputs.helmholtz(n, b, dim=2, n_modes=8, field_seed=3)
         coeff = dict(kind=inputs.HELMHOLTZ, c=torch.from_numpy(p.c).to(dev), omega=p.omega)
@@ -372,13 +421,15 @@ def run_gpu(args):
         cnt = []
         rel, it = step(f, u, cnt)
         torch.cuda.synchronize()
-        print(json.dumps({"once": True, "config": W, "max_relres": float(np.max(rel)), "refine_steps": it,
-                          "gpu_launches": cnt[0]}))
+        if rank == 0:
+            print(json.dumps({"once": True, "config": W, "max_relres": float(np.max(rel)), "refine_steps": it,
+                              "gpu_launches": cnt[0]}))
         return
     for _ in range(args.warmup):
         rel, it = step(f, u)
     sampler = ClockSampler()
     sampler.start()
+    dist_barrier()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -390,7 +441,8 @@ def run_gpu(args):
         its.append(it)
     e1.record(stream)
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
+    dist_barrier()
+    ms = dist_max(e0.elapsed_time(e1) / args.steps)
     # end to end through the public API with host buffers: H2D of f and D2H of u inside the region.
     # The load's copy runs on a copy stream while the factor (which does not need f) runs.
     # Device staging buffers for the load and the solution are allocated once, outside the region.
@@ -411,7 +463,7 @@ def run_gpu(args):
         s_e2e.close()
         u_host.copy_(ud, non_blocking=True)
         torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / ne2e
+    e2e_s = dist_max((time.perf_counter() - t0) / ne2e)
     sampler.stop()
     clocks = sampler.summary()
 
@@ -451,7 +503,7 @@ def run_gpu(args):
         "metric": METRIC,
         "value": ms / 1e3,
         "unit": "s",
-        "n_gpus": 1,
+        "n_gpus": world,
         "steps": args.steps,
         "warmup": args.warmup,
         "ms_per_step": ms,
@@ -479,7 +531,11 @@ def run_gpu(args):
     if args.fp64_comparator and (prec != "fp64" or iprec is not None):
         line["fp64_gpu"] = fp64_comparator(lambda: solver("fp64", rtol=1.0, max_refine=0, interface_precision="fp64"), f)
         line["fp64_gpu"]["mixed_speedup"] = line["fp64_gpu"]["value"] / line["value"]
-    if args.cpu_baseline:
+    if world > 1:
+        line["config"]["parallelism"] = f"replicas{world}"     # one problem per GPU, no data exchange
+    if rank != 0:
+        return
+    if args.cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(n, b, k, kind=W["kind"], n_sample=256 if helm else (32 if dim == 3 else 512))
     print(json.dumps(line))
 
@@ -550,8 +606,8 @@ def run_adjoint_batch(args):
 
     from paper_2211_07572_gb300 import inputs
     from paper_2211_07572_gb300.solver import batched_adjoint_gradients
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
+    dev = rank_device()
+    rank, _, world = dist_env()
     sizes = inputs.adjoint_batch_sizes()
     count = args.count or len(sizes)
     sizes = sizes[:count]
@@ -570,16 +626,18 @@ def run_adjoint_batch(args):
         step()
     sampler = ClockSampler()
     sampler.start()
+    dist_barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         losses, grads = step()
     torch.cuda.synchronize()
-    sec = (time.perf_counter() - t0) / args.steps
+    dist_barrier()
+    sec = dist_max((time.perf_counter() - t0) / args.steps)
     sampler.stop()
     line = {
         "metric": "batched adjoint: factor+solve+adjoint+gradient s per batch",
-        "value": sec, "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "value": sec, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": sec * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 factor (3xTF32 tensor products) / f64 residual+refinement" if prec == "fp32" else prec,
         "data": "synthetic",
@@ -596,7 +654,10 @@ def run_adjoint_batch(args):
         step("fp64")
         torch.cuda.synchronize()
         line["fp64_gpu"] = {"value": time.perf_counter() - t0, "unit": "s", "path": "same batch, FP64 factor"}
-    print(json.dumps(line))
+    if world > 1:
+        line["config"]["parallelism"] = f"replicas{world}"
+    if rank == 0:
+        print(json.dumps(line))
 
 
 def run_j0(args):
@@ -608,8 +669,8 @@ def run_j0(args):
 
     from paper_2211_07572_gb300 import inputs
     from paper_2211_07572_gb300.solver import SlabSolver
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
+    dev = rank_device()
+    rank, _, world = dist_env()
     n, b = args.n or 1024, args.b or 32
     d = inputs.bessel_j0(n, b)
     p = d["problem"]
@@ -633,6 +694,7 @@ def run_j0(args):
         step(g)
     sampler = ClockSampler()
     sampler.start()
+    dist_barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -643,7 +705,8 @@ def run_j0(args):
         rels.append(float(np.max(rel)))
     e1.record(stream)
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
+    dist_barrier()
+    ms = dist_max(e0.elapsed_time(e1) / args.steps)
     # end to end: boundary data from pinned host memory, solution back to pinned host memory
     u_host = torch.empty((1, (n - 1) ** 2), dtype=torch.float64).pin_memory()
     gd = torch.empty_like(g)
@@ -654,11 +717,13 @@ def run_j0(args):
         u, _, _ = step(gd)
         u_host.copy_(u, non_blocking=True)
         torch.cuda.synchronize()
-    e2e = (time.perf_counter() - t0) / args.steps
+    e2e = dist_max((time.perf_counter() - t0) / args.steps)
     sampler.stop()
     err = float(np.linalg.norm(u_host.numpy() - d["u_true"]) / np.linalg.norm(d["u_true"]))
+    if rank != 0:
+        return
     print(json.dumps({
-        "metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": 1, "steps": args.steps,
+        "metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": {"fp32": "f32 slab trees, f64 interface, f64 refinement"}.get(prec, prec),
         "data": "synthetic",
@@ -721,9 +786,8 @@ def main():
     ap.add_argument("--stage2", default="auto", choices=["auto", "sweep", "oddeven"],
                     help="elimination order of T (auto: odd-even for 4 or more interfaces)")
     args = ap.parse_args()
-    if args.gpus != 1:
-        # one GPU per run here: the method's multi-GPU form is replicas of independent problems
-        pass
+    if args.gpus != dist_env()[2] and dist_env()[2] > 1:
+        raise SystemExit(f"--gpus {args.gpus} but the launcher started {dist_env()[2]} ranks")
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "adjoint256":
