@@ -171,7 +171,10 @@ def oddeven_levels(NI):
 
 
 def work_model_3d(n, b, k, passes, stage2):
-    """Algorithmic flops per kernel class for the 3-D path (dense per-node tree along z)."""
+    """Algorithmic flops per kernel class for the 3-D path (dense per-node tree along z).
+
+    Stage 1 (the slab elimination, slab_* classes and assemble_T) and Stage 2 (panel, trailing,
+    schur_update) are counted apart, as the library times them apart."""
     s = n - 1
     m = b - 1
     M = m * s
@@ -180,7 +183,7 @@ def work_model_3d(n, b, k, passes, stage2):
     sp = (si + 63) // 64 * 64
     NS, NI = n // b, n // b - 1
     W = {k_: 0.0 for k_ in ("tree_factor", "assemble_T", "panel", "trailing", "schur_update", "sweep_products",
-                            "tree_up", "tree_down", "stencil")}
+                            "tree_up", "tree_down", "stencil", "slab_panel", "slab_trailing", "slab_schur")}
     for (c, kk, w) in tree_nodes(s):
         wl = w * s
         wmax = min(s, (1 << (kk + 1)) - 1)
@@ -188,12 +191,12 @@ def work_model_3d(n, b, k, passes, stage2):
         ident0 = 3 * Mp + 2 * wsp
         for kb in range(Mp // 64):                     # batched tall Cholesky of [S; B^T; I]
             rows = ident0 + (kb + 1) * 64
-            W["panel"] += NS * (rows // 64 - kb - 1) * (2 * 64 ** 3 + 2 * 64 ** 3 / 3)
+            W["slab_panel"] += NS * (rows // 64 - kb - 1) * (2 * 64 ** 3 + 2 * 64 ** 3 / 3)
             c0 = (kb + 1) * 64
             if c0 < Mp:
                 nn = Mp - c0
-                W["trailing"] += NS * 2 * 64 * (nn * (nn + 1) / 2 + (rows - Mp) * nn)
-        W["schur_update"] += NS * (2.0 * (2 * Mp) ** 2 * Mp + 2 * 2.0 * 2 * Mp * wl * Mp)
+                W["slab_trailing"] += NS * 2 * 64 * (nn * (nn + 1) / 2 + (rows - Mp) * nn)
+        W["slab_schur"] += NS * (2.0 * (2 * Mp) ** 2 * Mp + 2 * 2.0 * 2 * Mp * wl * Mp)
         W["assemble_T"] += NS * 3 * 2.0 * wl * wl * Mp
         W["tree_up"] += passes * NS * k * (2.0 * Mp * Mp + 2.0 * 2 * Mp * Mp + 2.0 * 2 * wsp * Mp)
         W["tree_down"] += passes * NS * k * (2.0 * Mp * 2 * Mp + 2.0 * Mp * 2 * wsp + 2.0 * Mp * Mp)
@@ -202,6 +205,13 @@ def work_model_3d(n, b, k, passes, stage2):
         W[key] += W2[key]
     W["stencil"] = passes * 24.0 * s ** 3 * k
     return W
+
+
+def alg1_cholesky_flops(si, NI):
+    """Algorithm 1 in Cholesky form on the unpadded interface blocks (s = si): per interface the
+    Cholesky of S_j (s^3/3), Y_j = L_j^-1 T_{j,j+1} (s^3) and S_{j+1} = T_{j+1,j+1} - Y_j^T Y_j (s^3):
+    N_I s^3/3 + (N_I - 1) 2 s^3.  The odd-even order performs about 4x these flops."""
+    return NI * si ** 3 / 3.0 + (NI - 1) * 2.0 * si ** 3
 
 
 def work_model_stage2(sp, NI, k, passes, stage2):
@@ -302,7 +312,8 @@ BOUND = {"tree_factor": "alu", "assemble_T": "hbm", "panel": "alu", "trailing": 
          "stencil": "hbm"}
 
 
-BOUND3 = dict(BOUND, assemble_T="tensor", tree_up="tensor", tree_down="tensor")
+BOUND3 = dict(BOUND, assemble_T="tensor", tree_up="tensor", tree_down="tensor", slab_panel="alu",
+              slab_trailing="tensor", slab_schur="tensor")
 
 # DRAM bytes per launch from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum), for the
 # default workload only: the n = 1024, b = 32, k = 64 case (all heights of one pass) scaled by the
@@ -354,7 +365,7 @@ def run_gpu(args):
     from paper_2211_07572_gb300 import inputs
     from paper_2211_07572_gb300.solver import SlabSolver
 
-    W = dict({"helmholtz4096": HELMHOLTZ, "diffusion3d96": DIFFUSION3D}.get(args.workload, WORKLOAD))
+    W = dict({"helmholtz4096": HELMHOLTZ, "diffusion2048": WORKLOAD}.get(args.workload, DIFFUSION3D))
     helm = W["kind"] == "helmholtz"
     dim = 3 if W["kind"] == "diffusion3d" else 2
     if args.n:
@@ -384,9 +395,10 @@ def run_gpu(args):
     NI = n // b - 1
     MMA_MODE.clear()
     if prec == "tf32":
-        MMA_MODE.update(schur_update="tf32", trailing="tf32", assemble_T="tf32")   # factor products
+        MMA_MODE.update(schur_update="tf32", trailing="tf32", assemble_T="tf32", slab_trailing="tf32",
+                        slab_schur="tf32")                     # factor products
     elif prec == "fp32" and not helm:
-        MMA_MODE.update(schur_update="f16x3", trailing="f16x3")
+        MMA_MODE.update(schur_update="f16x3", trailing="f16x3", slab_trailing="f16x3", slab_schur="f16x3")
         if dim == 3:
             MMA_MODE["assemble_T"] = "f16x3"                    # 3-D T assembly products
     if helm:
@@ -496,9 +508,24 @@ def run_gpu(args):
     if W["kind"] == "diffusion" and (n, b, k) == (2048, 32, 64) and dom in TRAFFIC and prec == "fp32":
         roof["traffic"] = TRAFFIC[dom]["bytes"]
         roof["traffic_source"] = TRAFFIC[dom]["from"]
-    dense_cls = ("trailing", "schur_update", "sweep_products") + (("assemble_T", "tree_up", "tree_down") if dim == 3 else ())
+    dense_cls = ("trailing", "schur_update", "sweep_products") + (
+        ("assemble_T", "tree_up", "tree_down", "slab_trailing", "slab_schur") if dim == 3 else ())
     dense = {c: roofline_for(c, cls_ms[c], cls_cnt[c], work, peaks, clocks, bmap)
              for c in dense_cls if cls_ms.get(c, 0) > 0}
+    # Stage 2 against the survey's count: Algorithm 1 in Cholesky form on the unpadded blocks, over
+    # the measured time of every Stage-2 factor class (panels, trailing and Schur updates)
+    si = (n - 1) ** (dim - 1)
+    s2_ms = sum(cls_ms.get(c, 0.0) for c in ("panel", "trailing", "schur_update"))
+    if s2_ms > 0 and not helm:
+        a1 = alg1_cholesky_flops(si, NI)
+        pk = peaks.get("bf16_tflops", 1891.8) * (1.0 if MMA_MODE.get("schur_update") == "f16x3" else 1.1 / 2.25)
+        dense["stage2_alg1"] = {
+            "bound": "tensor", "achieved": a1 / (s2_ms * 1e-3) / 1e12, "peak": pk, "unit": "TFLOP/s",
+            "frac": a1 / (s2_ms * 1e-3) / 1e12 / pk, "traffic": None, "ms": s2_ms, "flops": a1,
+            "count": "Algorithm 1 in Cholesky form, unpadded s = (n-1)^(d-1): N_I s^3/3 + (N_I-1) 2 s^3",
+            "order": stage2, "order_flops": work["panel"] + work["trailing"] + work["schur_update"],
+            "peak_source": "measured bf16 dense (= fp16 dense rate)" if pk == peaks.get("bf16_tflops", 1891.8)
+                           else "measured bf16 dense x 1.1/2.25 (tf32 nominal ratio)"}
     line = {
         "metric": METRIC,
         "value": ms / 1e3,
@@ -510,7 +537,8 @@ def run_gpu(args):
         "higher_is_better": False,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": {"fp32": "f32 factor (3xTF32 tensor products) / f64 residual+refinement",
+        "dtype": {"fp32": "f32 factor (FP32-accurate tensor products: three FP16 products of row-scaled hi/lo "
+                          "splits in the factor, 3xTF32 in the solve) / f64 residual+refinement",
                   "tf32": "f32 factor (single-pass TF32 tensor products) / f64 residual+refinement",
                   "fp64": "f64"}[prec] + ("" if iprec is None else f"; interface {iprec}"
                                             + (" (FP64-accurate tensor-core products)" if iprec == "fp64tc" else "")),
@@ -536,7 +564,8 @@ def run_gpu(args):
     if rank != 0:
         return
     if args.cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline(n, b, k, kind=W["kind"], n_sample=256 if helm else (32 if dim == 3 else 512))
+        rungs = ((256, 1),) if helm else (((32, 3), (48, 1)) if dim == 3 else ((512, 3),))
+        line["cpu_baseline"] = cpu_baseline(n, b, k, kind=W["kind"], rungs=rungs)
     print(json.dumps(line))
 
 
@@ -565,12 +594,10 @@ def fp64_comparator(make64, f):
             "path": "FP64 factor and solve on the same kernels (SIMT FP64), single pass"}
 
 
-def cpu_baseline(n_full, b, k, n_sample=512, kind="diffusion"):
-    """Oracle (banded LU, FP64) on a bounded sample of the workload: n = n_sample, same b, k rhs.
-
-    Extrapolated to the full size by the banded-LU cost model: factor ~ n^4, solve ~ k n^3.
-    The Helmholtz sample keeps 10 points per wavelength and pivots (partial pivoting).
-    """
+def cpu_sample(n_full, b, k, n_sample, kind="diffusion"):
+    """One oracle run (banded LU, FP64) on a bounded sample of the workload: n = n_sample, same b and
+    k loads, extrapolated to n_full by the banded-LU cost model (factor ~ N w^2, solve ~ k N w with
+    N = n^d, w = n^(d-1)).  The Helmholtz sample keeps 10 points per wavelength and pivots."""
     import oracle
     from paper_2211_07572_gb300 import inputs
     oracle.build()
@@ -588,13 +615,40 @@ def cpu_baseline(n_full, b, k, n_sample=512, kind="diffusion"):
     u = lu.solve(p.f)
     t2 = time.perf_counter()
     rr = float(oracle.relres(A, u, p.f).max())
-    scale = (n_full / n_sample)
-    # banded LU: factor ~ N w^2, solve ~ k N w (N = n^d, w = n^(d-1))
+    scale = n_full / n_sample
     est = (t1 - t0) * scale ** (3 * dim - 2) + (t2 - t1) * scale ** (2 * dim - 1)
-    return {"value": est, "unit": "s", "cores": oracle.threads(), "kind": "oracle",
-            "sample": f"banded LU FP64 at n={n_sample} (b={b}, k={k}): factor {t1 - t0:.2f} s, "
-                      f"solve {t2 - t1:.2f} s, relres {rr:.1e}; extrapolated to n={n_full} by n^{3 * dim - 2} / "
-                      f"k n^{2 * dim - 1}"}
+    return {"n": n_sample, "factor_s": t1 - t0, "solve_s": t2 - t1, "relres": rr, "est": est, "dim": dim,
+            "cores": oracle.threads()}
+
+
+def cpu_baseline(n_full, b, k, kind="diffusion", rungs=((512, 3),)):
+    """The oracle timed on a ladder of bounded samples (n, repeats); the value is the median
+    extrapolation of the largest rung, the spread of its repeats and the exponent the rungs show
+    between them are reported beside it."""
+    import statistics
+    res = {}
+    for n_s, rep in rungs:
+        res[n_s] = [cpu_sample(n_full, b, k, n_s, kind) for _ in range(rep)]
+    top = max(res)
+    ests = [r["est"] for r in res[top]]
+    dim = res[top][0]["dim"]
+    parts = []
+    for n_s in sorted(res):
+        rs = res[n_s]
+        parts.append(f"n={n_s}: factor {', '.join(f'{r['factor_s']:.2f}' for r in rs)} s, solve "
+                     f"{statistics.median(r['solve_s'] for r in rs):.2f} s, relres {max(r['relres'] for r in rs):.1e}")
+    lo = min(res)
+    expo = ""
+    if lo != top:
+        f_lo = statistics.median(r["factor_s"] for r in res[lo])
+        f_hi = statistics.median(r["factor_s"] for r in res[top])
+        import math
+        expo = f"; measured factor exponent n={lo}->{top}: {math.log(f_hi / f_lo) / math.log(top / lo):.2f}"
+    return {"value": statistics.median(ests), "unit": "s", "cores": res[top][0]["cores"], "kind": "oracle",
+            "spread": [min(ests), max(ests)],
+            "sample": f"banded LU FP64 (b={b}, k={k}) on a ladder -- " + "; ".join(parts) +
+                      f"; value = median over the n={top} repeats extrapolated to n={n_full} by n^{3 * dim - 2} "
+                      f"(factor) and k n^{2 * dim - 1} (solve), spread {min(ests):.0f}-{max(ests):.0f} s" + expo}
 
 
 def run_adjoint_batch(args):
@@ -740,23 +794,31 @@ def run_j0(args):
 
 
 def run_reference(args):
-    n, b, k = WORKLOAD["n"], WORKLOAD["b"], WORKLOAD["k"]
+    """The reference arm: the oracle (banded LU) timed as it stands on the host cores, each step one
+    bounded sample of the default workload (3-D diffusion, n = ref_n) extrapolated to n = 96."""
+    W = DIFFUSION3D
+    n, b, k = W["n"], W["b"], W["k"]
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     vals = []
     t0 = time.perf_counter()
     for _ in range(args.warmup):
-        cpu_baseline(n, b, k, n_sample=128)
+        cpu_sample(n, b, k, 16, kind=W["kind"])
     for _ in range(args.steps):
-        vals.append(cpu_baseline(n, b, k, n_sample=args.ref_n))
-    v = sum(x["value"] for x in vals) / len(vals)
-    cb = dict(vals[-1])
+        vals.append(cpu_sample(n, b, k, args.ref_n, kind=W["kind"]))
+    import statistics
+    ests = [x["est"] for x in vals]
+    v = statistics.mean(ests)
+    cb = {"value": v, "unit": "s", "cores": vals[0]["cores"], "kind": "oracle", "spread": [min(ests), max(ests)],
+          "sample": f"banded LU FP64 at n={args.ref_n} (b={b}, k={k}) per step, factor "
+                    f"{statistics.median(x['factor_s'] for x in vals):.2f} s median; extrapolated to n={n} by n^7 "
+                    f"(factor) and k n^5 (solve)"}
     print(json.dumps({
         "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-        "config": dict(WORKLOAD, impl="CPU oracle banded LU, extrapolated from a bounded sample"),
+        "config": dict(W, impl="CPU oracle banded LU, extrapolated from a bounded sample"),
         "cpu_baseline": cb, "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "wall_s": time.perf_counter() - t0}))
 
@@ -771,15 +833,16 @@ def main():
     ap.add_argument("--n", type=int, default=0)
     ap.add_argument("--b", type=int, default=0)
     ap.add_argument("--k", type=int, default=0)
-    ap.add_argument("--ref-n", type=int, default=512)
+    ap.add_argument("--ref-n", type=int, default=32, help="reference arm: oracle sample size (3-D)")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-fp64", dest="fp64_comparator", action="store_false")
     ap.add_argument("--once", action="store_true", help="run one step only (for profilers)")
     ap.add_argument("--count", type=int, default=0, help="adjoint256: number of problems (0: all 256)")
     ap.add_argument("--wave", type=int, default=32, help="adjoint256: problems per wave")
-    ap.add_argument("--workload", default="diffusion2048",
+    ap.add_argument("--workload", default="diffusion3d96",
                     choices=["diffusion2048", "helmholtz4096", "diffusion3d96", "adjoint256", "helmholtzj0"],
-                    help="diffusion2048: the default bench line; helmholtz4096, diffusion3d96, adjoint256, helmholtzj0: the other workloads")
+                    help="diffusion3d96: the default bench line (3-D diffusion n=96, b=8, k=16); diffusion2048, "
+                         "helmholtz4096, adjoint256, helmholtzj0: the other workloads")
     ap.add_argument("--krylov", type=int, default=0, help="0: plain refinement; m: FP64 GMRES(m) refinement")
     ap.add_argument("--interface", default="default", choices=["default", "fp32", "fp64", "fp64tc", "tf32"],
                     help="precision of the interface system (fp64tc: FP64-accurate tensor-core products)")

@@ -119,16 +119,18 @@ typedef struct {
 
 typedef struct slab_handle slab_handle;
 
-/* Fill opts with the defaults: FP32 factor, rtol 1e-10, max_refine 30, default stream,
- * SLAB_STAGE2_AUTO, interface_prec -1. */
+/* Fill every field of opts with the defaults: FP32 factor, pivot 0, rtol 1e-10, max_refine 30,
+ * krylov 0, default stream (NULL), profile 0, SLAB_STAGE2_AUTO, interface_prec -1.
+ * slab_factor with opts == NULL uses exactly these. */
 void slab_default_opts(slab_opts* opts);
 
 /*
  * Factor A (Algorithm 3): Stage 1 for every slab in parallel, assembly of the
  * reduced matrix T, Stage 2 (Algorithm 1's sweep or the odd-even order, opts.stage2).  b is the interface spacing:
  * interfaces at x = q b, q = 1..n/b-1, slab interiors b-1 nodes wide.
- * Requires b >= 2 and n % b == 0, 2 <= b <= 33, n/b >= 2 (SLAB_EINVAL otherwise);
- * dim == 2 (SLAB_EUNSUPPORTED otherwise).  POISSON and DIFFUSION are factored by
+ * Requires dim 2 or 3, b >= 2, n % b == 0 and n/b >= 2 (SLAB_EINVAL otherwise).  In 2-D the slab
+ * interior width b - 1 is at most 32 (SLAB_EUNSUPPORTED otherwise); HELMHOLTZ in 3-D, and
+ * SLAB_STAGE2_ODDEVEN with HELMHOLTZ, are SLAB_EUNSUPPORTED.  POISSON and DIFFUSION are factored by
  * Cholesky (slab separators and Stage 2); HELMHOLTZ (indefinite) by Gauss-Jordan
  * with partial pivoting in the slab separators, and in Stage 2 (Algorithm 1 as printed) by a
  * blocked Gauss-Jordan elimination of [S_j | T_{j,j+1} | I] with tournament pivoting
@@ -250,7 +252,9 @@ slab_status slab_tc_gemm(int M, int N, int K, float alpha, const float* A, int64
  *   3 panel factor of Stage 2 (A4), 4 Stage-2 trailing update (A4, tensor cores in FP32),
  *   5 Stage-2 Schur update S_{j+1} = T - Y^T Y (A4), 6 interface sweep products (A6),
  *   7 tree up pass + reduced load (A5), 8 tree down pass (A7), 9 FP64 stencil residual (A8),
- *   10 other (transposes, reductions, scatter/gather, gradient).
+ *   10 other (transposes, reductions, scatter/gather, gradient),
+ *   11-13 the panel, trailing-update and Schur-update products of the 3-D slab elimination
+ *   (Stage 1 in 3-D runs the same dense kernels as Stage 2; these classes keep them apart).
  * slab_profile(h, 1) starts recording a CUDA event pair around every launch on the handle's
  * stream; slab_profile_read fills ms[c] (summed device time) and launches[c] (HOST arrays
  * of n <= SLAB_KERNEL_CLASSES entries) for the launches since the previous read, then
@@ -272,7 +276,7 @@ slab_status slab_fp64_tc_gemm(int M, int N, int K, double alpha, const double* A
                               unsigned* dev_err, void* stream);
 size_t slab_fp64_tc_gemm_work_bytes(int M, int N, int K);
 
-#define SLAB_KERNEL_CLASSES 11
+#define SLAB_KERNEL_CLASSES 14
 slab_status slab_profile(slab_handle* h, int enable);
 slab_status slab_profile_read(slab_handle* h, double* ms, int64_t* launches, int n);
 

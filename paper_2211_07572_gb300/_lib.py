@@ -12,7 +12,7 @@ c_int, c_double, c_void_p, c_int64 = ctypes.c_int, ctypes.c_double, ctypes.c_voi
 SLAB_OK, SLAB_EINVAL, SLAB_ENOMEM, SLAB_ESINGULAR, SLAB_ENOCONV, SLAB_ETIMEOUT, SLAB_ECUDA, SLAB_EUNSUPPORTED = range(8)
 POISSON, DIFFUSION, HELMHOLTZ = 0, 1, 2
 KERNEL_CLASSES = ("coeff", "tree_factor", "assemble_T", "panel", "trailing", "schur_update", "sweep_products",
-                  "tree_up", "tree_down", "stencil", "other")
+                  "tree_up", "tree_down", "stencil", "other", "slab_panel", "slab_trailing", "slab_schur")
 PREC_FP64, PREC_FP32, PREC_TF32, PREC_FP64_TC = 0, 1, 2, 3
 
 

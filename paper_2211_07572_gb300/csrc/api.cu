@@ -230,7 +230,12 @@ slab_status sync_status(slab_handle* h) {
 // Stage 1 and the assembly of T (into h->Tb / h->To in the Stage-1 scalar)
 template <typename T>
 slab_status stage1_impl(slab_handle* h) {
-    if (h->dim == 3) return tree3d_factor<T>(h);
+    if (h->dim == 3) {
+        h->stage1_dense = 1;
+        const slab_status st = tree3d_factor<T>(h);
+        h->stage1_dense = 0;
+        return st;
+    }
     TRY(tree_factor<T>(h));
     return assemble_T<T>(h);
 }
@@ -273,6 +278,7 @@ struct ProfRecord {
 
 void prof_begin(slab_handle* h, int cls) {
     if (!h) return;
+    cls = prof_class(h, cls);
     h->launches[cls] += 1;
     if (!h->prof_on || !h->prof) return;
     ProfRecord* R = (ProfRecord*)h->prof;
@@ -346,6 +352,7 @@ void slab_default_opts(slab_opts* o) {
     o->stream = nullptr;
     o->profile = 0;
     o->stage2 = SLAB_STAGE2_AUTO;
+    o->interface_prec = -1;
 }
 
 const char* slab_strerror(slab_status s) {

@@ -143,14 +143,24 @@ struct slab_handle {
 
     // measurement: launch counts per kernel class, optional event timing
     int64_t launches[SLAB_KERNEL_CLASSES];
+    int stage1_dense;         // set while the 3-D slab elimination runs (see prof_class)
     int prof_on;
     void* prof;               // ProfRecord (api.cu) while timing is on
 };
 
 enum SlabKernelClass {
     KC_COEFF = 0, KC_TREE_FACTOR, KC_ASSEMBLE, KC_PANEL, KC_TRAIL, KC_SYRK, KC_SOLVE_PROD,
-    KC_TREE_UP, KC_TREE_DOWN, KC_STENCIL, KC_OTHER
+    KC_TREE_UP, KC_TREE_DOWN, KC_STENCIL, KC_OTHER,
+    KC_SLAB_PANEL, KC_SLAB_TRAIL, KC_SLAB_SYRK      // the same dense kernels inside the 3-D slab elimination
 };
+
+// While h->stage1_dense is set (the 3-D slab elimination runs), the dense classes are counted
+// under their Stage-1 names, so that the Stage-2 classes time Algorithm 1 alone.
+inline int prof_class(const slab_handle* h, int cls) {
+    return (h->stage1_dense && (cls == KC_PANEL || cls == KC_TRAIL || cls == KC_SYRK))
+               ? cls - KC_PANEL + KC_SLAB_PANEL
+               : cls;
+}
 
 // Records one launch of class cls on h->stream; with timing on, brackets it by events.
 void prof_begin(slab_handle* h, int cls);
@@ -163,7 +173,7 @@ struct ProfScope {
 };
 #define SLAB_PROF(h, cls) ProfScope _prof_scope_((h), (cls))
 // Further kernel launches made inside one SLAB_PROF scope (split pre-passes, split-K reductions).
-inline void prof_extra(slab_handle* h, int cls, int n) { h->launches[cls] += n; }
+inline void prof_extra(slab_handle* h, int cls, int n) { h->launches[prof_class(h, cls)] += n; }
 
 // ---------------------------------------------------------------- tree helpers (host+device)
 __host__ __device__ inline int tree_height_count(int s) {

@@ -5,6 +5,8 @@
 // + q_P u_P.  These kernels are bound by HBM bandwidth: one coalesced pass over
 // u, f and r per right-hand side (the coefficient arrays stay in L2 across
 // right-hand sides).
+#include <algorithm>
+
 #include "slab_internal.cuh"
 
 namespace {
@@ -214,11 +216,11 @@ template <bool RESID>
 __global__ void __launch_bounds__(128) stencil3d_kernel(int n, int k, const double* __restrict__ AX,
                                                         const double* __restrict__ AY, const double* __restrict__ AZ,
                                                         const double* __restrict__ DG, const double* __restrict__ u,
-                                                        const double* __restrict__ f, double* r) {
+                                                        const double* __restrict__ f, double* r, int q0) {
     const int s = n - 1, np1 = n + 1;
     const int x = blockIdx.x * blockDim.x + threadIdx.x + 1;
     const int y = blockIdx.y + 1;
-    const int z = blockIdx.z % s + 1, q = blockIdx.z / s;
+    const int z = blockIdx.z % s + 1, q = q0 + (int)(blockIdx.z / s);
     if (x > s || q >= k) return;
     const double n2 = (double)n * (double)n;
     const int64_t N = (int64_t)s * s * s;
@@ -362,9 +364,15 @@ slab_status launch_residual(slab_handle* h, const double* u, const double* f, do
     if (h->dim == 3) {
         {
             SLAB_PROF(h, KC_STENCIL);
-            stencil3d_kernel<true><<<dim3((s + 127) / 128, s, s * k), 128, 0, h->stream>>>(n, k, h->AX, h->AY, h->AZ,
-                                                                                           h->DG, u, f, r);
-            SLAB_CK_LAUNCH(h);
+            // gridDim.z = s x (right-hand sides of one launch) stays within 65535
+            const int qc = 65535 / s;
+            for (int q0 = 0; q0 < k; q0 += qc) {
+                const int kq = std::min(qc, k - q0);
+                stencil3d_kernel<true><<<dim3((s + 127) / 128, s, s * kq), 128, 0, h->stream>>>(
+                    n, q0 + kq, h->AX, h->AY, h->AZ, h->DG, u, f, r, q0);
+                SLAB_CK_LAUNCH(h);
+            }
+            prof_extra(h, KC_STENCIL, (k - 1) / qc);
         }
         if (!nrm_r) return SLAB_OK;
         const size_t need = vec_dot_part_elems(k);
@@ -422,9 +430,14 @@ slab_status launch_apply(slab_handle* h, const double* x, double* y, int k) {
     if (k <= 0) return SLAB_OK;
     if (h->dim == 3) {
         SLAB_PROF(h, KC_STENCIL);
-        stencil3d_kernel<false><<<dim3((s + 127) / 128, s, s * k), 128, 0, h->stream>>>(n, k, h->AX, h->AY, h->AZ,
-                                                                                        h->DG, x, nullptr, y);
-        SLAB_CK_LAUNCH(h);
+        const int qc = 65535 / s;
+        for (int q0 = 0; q0 < k; q0 += qc) {
+            const int kq = std::min(qc, k - q0);
+            stencil3d_kernel<false><<<dim3((s + 127) / 128, s, s * kq), 128, 0, h->stream>>>(
+                n, q0 + kq, h->AX, h->AY, h->AZ, h->DG, x, nullptr, y, q0);
+            SLAB_CK_LAUNCH(h);
+        }
+        prof_extra(h, KC_STENCIL, (k - 1) / qc);
         return SLAB_OK;
     }
     dim3 grid((s + 255) / 256, (s + ST_ROWS - 1) / ST_ROWS, (k + ST_Q - 1) / ST_Q);

@@ -15,7 +15,7 @@ def _run(extra_env, *args):
 
 
 def test_reference_arm_prints_the_contract_line():
-    r = _run({}, "--steps", "1", "--warmup", "0", "--ref-n", "128")
+    r = _run({}, "--steps", "1", "--warmup", "0", "--ref-n", "16")
     assert r.returncode == 0, r.stderr[-2000:]
     line = json.loads(r.stdout.strip().splitlines()[-1])
     for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
@@ -30,6 +30,6 @@ def test_reference_arm_prints_the_contract_line():
 
 def test_reference_arm_other_ranks_stay_silent():
     env = dict(RANK="1", LOCAL_RANK="1", WORLD_SIZE="2", MASTER_ADDR="127.0.0.1", MASTER_PORT="29731")
-    r = _run(env, "--gpus", "2", "--steps", "1", "--warmup", "0", "--ref-n", "128")
+    r = _run(env, "--gpus", "2", "--steps", "1", "--warmup", "0", "--ref-n", "16")
     assert r.returncode == 0, r.stderr[-2000:]
     assert r.stdout.strip() == ""
