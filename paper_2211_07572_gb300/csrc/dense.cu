@@ -1425,56 +1425,94 @@ slab_status dense_copy(slab_handle* h, const T* in, int64_t sin, T* out, int64_t
 // Cholesky of the leading ncols x ncols block of a batch of tall matrices (row-major, ld = ncols,
 // bstride apart) whose rows below are eliminated with it: rows [ncols, ident0) receive B^T L^{-T},
 // rows [ident0, ident0 + ncols), which must hold the identity, receive L^{-T}.
-// Right-looking with two block levels: 64-column panels (panel_diag_kernel factors the diagonal
-// tile once, panel_apply_kernel scales the tiles below by its inverse); after each panel, the
-// update of the remaining columns of its outer block of OB panels only; when an outer block is
-// complete, one rank-(OB 64) update of every column to its right.  The trailing matrix is thus
-// read and written once per outer block instead of once per panel.
+// Identity row ident0 + r is zero in the columns left of r until column r is eliminated, so the
+// columns [0, c) only ever touch rows [0, ident0 + c).
+//
+// Recursive column bisection (right-looking at every level): factor the left half of a column
+// range, apply its one update to the right half -- C[c0:, c0:c1] -= P P[:c1-c0]^T with P the left
+// half's columns and K = the left half's width -- then factor the right half.  64-column panels
+// are the leaves (panel_diag_kernel factors the diagonal tile once, panel_apply_kernel scales the
+// tiles below by its inverse).  Each level reads and writes the trailing matrix once, so the
+// trailing updates stream it about log2(ncols / 64) times in all, and most of their flops fall in
+// products with a large K.
+namespace {
+
+// C[c0 : rows, c0 : c1] -= W[c0 : rows, k0 : k1] W[c0 : c1, k0 : k1]^T (lower tiles of the square
+// part), for every matrix of the batch.  Where the FP16 three-product work buffer of the factor is
+// too small for the whole batch, the product runs on slices of the batch, or of K for one matrix.
+template <typename T>
+slab_status tall_update(slab_handle* h, T* W, int ncols, int rows, int c0, int c1, int k0, int k1, int batch,
+                        int64_t bstride) {
+    const int M = rows - c0, N = c1 - c0;
+    int bchunk = batch, kchunk = k1 - k0;
+    if (sizeof(T) == 4 && h->w16 && !h->tf32_now) {
+        while (bchunk > 1 && f16x3_work_bytes(M, N, kchunk, bchunk, true) > h->w16_bytes) bchunk = (bchunk + 1) / 2;
+        while (kchunk > TL && f16x3_work_bytes(M, N, kchunk, bchunk, true) > h->w16_bytes)
+            kchunk = (kchunk / TL + 1) / 2 * TL;
+    }
+    slab_status st;
+    for (int b0 = 0; b0 < batch; b0 += bchunk) {
+        const int nb = std::min(bchunk, batch - b0);
+        T* Wb = W + (int64_t)b0 * bstride;
+        for (int ka = k0; ka < k1; ka += kchunk) {
+            const int kw = std::min(kchunk, k1 - ka);
+            const T* P = Wb + (int64_t)c0 * ncols + ka;
+            if ((st = dense_gemm<T>(h, KC_TRAIL, M, N, kw, T(-1), P, ncols, bstride, P, ncols, bstride, T(1),
+                                    Wb + (int64_t)c0 * ncols + c0, ncols, bstride, 0, 1, nb)))
+                return st;
+        }
+    }
+    return SLAB_OK;
+}
+
+template <typename T>
+slab_status tall_panel(slab_handle* h, T* W, int ncols, int ident0, int kb, int batch, int64_t bstride, size_t smem) {
+    const int rows = ident0 + (kb + 1) * TL;
+    const int nrt = rows / TL - kb - 1;
+    T* Lw = (T*)h->pnl;
+    for (int b0 = 0; b0 < batch; b0 += 65535) {
+        const int nb = std::min(65535, batch - b0);
+        {
+            SLAB_PROF(h, KC_PANEL);
+            panel_diag_kernel<T><<<dim3(1, nb), 256, smem, h->stream>>>(W + b0 * bstride, ncols, kb, h->dstatus,
+                                                                         bstride, Lw);
+            SLAB_CK_LAUNCH(h);
+        }
+        if (nrt > 0) {
+            SLAB_PROF(h, KC_PANEL);
+            panel_apply_kernel<T><<<dim3(nrt, nb), 256, smem, h->stream>>>(W + b0 * bstride, ncols, kb, bstride, Lw);
+            SLAB_CK_LAUNCH(h);
+        }
+    }
+    return SLAB_OK;
+}
+
+// Panels [kb0, kb1), all updates from the columns left of kb0 already applied.
+template <typename T>
+slab_status tall_chol_range(slab_handle* h, T* W, int ncols, int ident0, int kb0, int kb1, int batch,
+                            int64_t bstride, size_t smem) {
+    if (kb1 - kb0 == 1) return tall_panel<T>(h, W, ncols, ident0, kb0, batch, bstride, smem);
+    const int kbm = kb0 + (kb1 - kb0) / 2;
+    slab_status st;
+    if ((st = tall_chol_range<T>(h, W, ncols, ident0, kb0, kbm, batch, bstride, smem))) return st;
+    if ((st = tall_update<T>(h, W, ncols, ident0 + kbm * TL, kbm * TL, kb1 * TL, kb0 * TL, kbm * TL, batch, bstride)))
+        return st;
+    return tall_chol_range<T>(h, W, ncols, ident0, kbm, kb1, batch, bstride, smem);
+}
+
+}  // namespace
+
 template <typename T>
 slab_status dense_tall_cholesky(slab_handle* h, T* W, int ncols, int ident0, int batch, int64_t bstride) {
-    constexpr int OB = 4;                              // panels per outer block
     const size_t smem = 2 * TL * TLP * sizeof(T);
     SLAB_CK(h, cudaFuncSetAttribute(panel_diag_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     SLAB_CK(h, cudaFuncSetAttribute(panel_apply_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int bchunk = std::min(batch, 65535);
     slab_status st;
     if ((st = ensure_panel_work(h, (size_t)bchunk * TL * TL * sizeof(T)))) return st;
-    T* Lw = (T*)h->pnl;
     const int nt = ncols / TL;
-    for (int kb = 0; kb < nt; ++kb) {
-        const int rows = ident0 + (kb + 1) * TL;      // identity rows below are still zero in these columns
-        const int nrt = rows / TL - kb - 1;
-        for (int b0 = 0; b0 < batch; b0 += 65535) {
-            const int nb = std::min(65535, batch - b0);
-            {
-                SLAB_PROF(h, KC_PANEL);
-                panel_diag_kernel<T><<<dim3(1, nb), 256, smem, h->stream>>>(W + b0 * bstride, ncols, kb, h->dstatus,
-                                                                             bstride, Lw);
-                SLAB_CK_LAUNCH(h);
-            }
-            if (nrt > 0) {
-                SLAB_PROF(h, KC_PANEL);
-                panel_apply_kernel<T><<<dim3(nrt, nb), 256, smem, h->stream>>>(W + b0 * bstride, ncols, kb, bstride,
-                                                                               Lw);
-                SLAB_CK_LAUNCH(h);
-            }
-        }
-        const int kb0 = kb - kb % OB, kend = std::min(nt, kb0 + OB);     // this outer block: panels [kb0, kend)
-        const int c0 = (kb + 1) * TL, cend = kend * TL;
-        if (c0 < cend) {                               // rest of the outer block, rank 64
-            const T* P = W + (int64_t)c0 * ncols + (int64_t)kb * TL;
-            if ((st = dense_gemm<T>(h, KC_TRAIL, rows - c0, cend - c0, TL, T(-1), P, ncols, bstride, P, ncols, bstride,
-                                    T(1), W + (int64_t)c0 * ncols + c0, ncols, bstride, 0, 1, batch)))
-                return st;
-        } else if (cend < ncols) {                     // outer block done: columns to its right, rank (kend-kb0) 64
-            const T* P = W + (int64_t)cend * ncols + (int64_t)kb0 * TL;
-            if ((st = dense_gemm<T>(h, KC_TRAIL, rows - cend, ncols - cend, (kend - kb0) * TL, T(-1), P, ncols, bstride,
-                                    P, ncols, bstride, T(1), W + (int64_t)cend * ncols + cend, ncols, bstride, 0, 1,
-                                    batch)))
-                return st;
-        }
-    }
-    return SLAB_OK;
+    if (nt <= 0) return SLAB_OK;
+    return tall_chol_range<T>(h, W, ncols, ident0, 0, nt, batch, bstride, smem);
 }
 
 template slab_status dense_gemm<float>(slab_handle*, int, int, int, int, float, const float*, int64_t, int64_t,

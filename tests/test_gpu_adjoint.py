@@ -12,6 +12,7 @@ import pytest
 import torch
 
 import oracle
+from fdcheck import fd_operator_difference
 from paper_2211_07572_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -23,13 +24,12 @@ def _solver(n, b, kappa):
 
 
 # Central differences L(k+d) - L(k-d) with the difference of the two forward solutions formed
-# without cancellation:  u+ - u- = -A(k+d)^{-1} (A(k+d) - A(k-d)) u-.  Both products come from
-# the solver's own FP64 operator apply; every row away from the perturbed node is bit-identical
-# in the two and cancels exactly, so the right-hand side carries no O(eps ||A|| ||u||) rounding
-# noise, and the loss difference sum (u+ - u-)(u+ + u- - 2 u_t) has no cancellation either.
-# (u- is the exact solution for the load f - r-, r- its residual of relative size <= 1e-14; the
-# gradient at that load differs from the one at f by that relative amount.)  The remaining FD
-# error is the O(d^2) truncation, below 1e-8 relative at both steps for kappa >= 0.03.
+# without cancellation:  u+ - u- = -A(k+d)^{-1} (A(k+d) - A(k-d)) u-, the operator difference
+# applied in closed form (fd_operator_difference), and the loss difference
+# sum (u+ - u-)(u+ + u- - 2 u_t), which has no cancellation either.  (u- is the exact solution for
+# the load f - r-, r- its residual of relative size <= 1e-13; the gradient at that load differs
+# from the one at f by that relative amount.)  The remaining FD error is the O(d^2) truncation,
+# below 1e-8 relative at both steps for kappa >= 0.03.
 @pytest.mark.parametrize("inst,delta,tol", [(0, 1e-4, 1e-6), (1, 1e-4, 1e-6), (0, 1e-6, 1e-6)])
 def test_adjoint_gradient_vs_central_differences(inst, delta, tol):
     assert torch.cuda.is_available()
@@ -50,9 +50,9 @@ def test_adjoint_gradient_vs_central_differences(inst, delta, tol):
         km = kappa.copy(); km[y, x] -= delta
         sm = _solver(n, d["b"], km)
         um, _, _ = sm.solve(f, allow_noconv=True)
-        sp = _solver(n, d["b"], kp)
-        dAu = sp.apply(um) - sm.apply(um)
         sm.close()
+        sp = _solver(n, d["b"], kp)
+        dAu = torch.from_numpy(fd_operator_difference(um.cpu().numpy(), kp, km, x, y, n)).cuda()
         du, _, _ = sp.solve(-dAu, allow_noconv=True)
         sp.close()
         fd.append(float((du * (2 * um + du - 2 * ut)).sum()) / (2 * delta))

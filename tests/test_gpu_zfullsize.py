@@ -118,7 +118,9 @@ def test_adjoint_gradient_central_differences_32_probes(inst):
     n = 256): dL/dkappa from the adjoint solve against central differences with absolute step
     1e-6 on the instance's 32 seeded interior probe nodes, ||g_adj - g_fd|| / ||g_fd|| <= 1e-6.
     The loss difference is formed without cancellation as in the smaller adjoint tests:
-    u+ - u- = -A(k+d)^-1 (A(k+d) - A(k-d)) u-, L+ - L- = sum (u+ - u-)(u+ + u- - 2 u_t)."""
+    u+ - u- = -A(k+d)^-1 (A(k+d) - A(k-d)) u-, L+ - L- = sum (u+ - u-)(u+ + u- - 2 u_t), with the
+    operator difference applied in its closed form (fd_operator_difference)."""
+    from fdcheck import fd_operator_difference
     from paper_2211_07572_gb300.solver import SlabSolver
     n = int(inputs.adjoint_batch_sizes()[inst])
     d = inputs.adjoint_instance(inst, n)
@@ -141,9 +143,9 @@ def test_adjoint_gradient_central_differences_32_probes(inst):
         km = kappa.copy(); km[y, x] -= delta
         sm = solver(km)
         um, _, _ = sm.solve(f, allow_noconv=True)
-        sp = solver(kp)
-        dAu = sp.apply(um) - sm.apply(um)
         sm.close()
+        sp = solver(kp)
+        dAu = torch.from_numpy(fd_operator_difference(um.cpu().numpy(), kp, km, x, y, n)).cuda()
         du, _, _ = sp.solve(-dAu, allow_noconv=True)
         sp.close()
         fd.append(float((du * (2 * um + du - 2 * ut)).sum()) / (2 * delta))
