@@ -401,11 +401,7 @@ def run_gpu(args):
         MMA_MODE.update(schur_update="f16x3", trailing="f16x3", slab_trailing="f16x3", slab_schur="f16x3")
         if dim == 3:
             MMA_MODE["assemble_T"] = "f16x3"                    # 3-D T assembly products
-    if helm:
-        stage2 = "sweep"
-    else:
-        stage2 = args.stage2 if args.stage2 != "auto" else ("oddeven" if NI >= 4 and prec != "fp64" else "sweep")
-    W["stage2"] = stage2
+    stage2 = "sweep" if helm else args.stage2          # "auto": the library's own choice (read back below)
 
     def solver(precision, **kw):
         kk = dict(coeff)
@@ -421,24 +417,30 @@ def run_gpu(args):
         return solver(prec, rtol=W["rtol"], max_refine=40, stage2=stage2, krylov=args.krylov,
                       interface_precision=iprec)
 
-    def step(f_in, u_out, counts=None):
+    def step(f_in, u_out, counts=None, orders=None):
         s = make()
+        if orders is not None:
+            orders.append(s.stage2_order)               # the order the factor used ("auto" resolved)
         _, rel, it = s.solve(f_in, u_out, allow_noconv=True)
         if counts is not None:
             counts.append(sum(s.profile_read()[1].values()))
         s.close()
         return rel, it
 
+    orders = []
     if args.once:
         cnt = []
-        rel, it = step(f, u, cnt)
+        rel, it = step(f, u, cnt, orders)
         torch.cuda.synchronize()
+        W["stage2"] = orders[0]
         if rank == 0:
             print(json.dumps({"once": True, "config": W, "max_relres": float(np.max(rel)), "refine_steps": it,
                               "gpu_launches": cnt[0]}))
         return
-    for _ in range(args.warmup):
-        rel, it = step(f, u)
+    for _ in range(max(args.warmup, 1)):
+        rel, it = step(f, u, orders=orders)
+    stage2 = orders[0]
+    W["stage2"] = stage2
     sampler = ClockSampler()
     sampler.start()
     dist_barrier()
@@ -465,17 +467,36 @@ def run_gpu(args):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     ne2e = max(1, args.steps)
+    parts = {"h2d_ms": [], "device_ms": [], "d2h_ms": [], "step_ms": []}
     for _ in range(ne2e):
+        ts = time.perf_counter()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
         with torch.cuda.stream(copy_stream):
+            ev[0].record(copy_stream)
             fd.copy_(f_host, non_blocking=True)
+            ev[1].record(copy_stream)
             ready = copy_stream.record_event()
+        ev[2].record(stream)
         s_e2e = make()                                   # factor on `stream`, overlapping the copy
         stream.wait_event(ready)
         s_e2e.solve(fd, ud, allow_noconv=True)
         s_e2e.close()
+        ev[3].record(stream)
+        ev[4].record(stream)
         u_host.copy_(ud, non_blocking=True)
+        ev[5].record(stream)
         torch.cuda.synchronize()
+        parts["step_ms"].append((time.perf_counter() - ts) * 1e3)
+        parts["h2d_ms"].append(ev[0].elapsed_time(ev[1]))
+        parts["device_ms"].append(ev[2].elapsed_time(ev[3]))
+        parts["d2h_ms"].append(ev[4].elapsed_time(ev[5]))
     e2e_s = dist_max((time.perf_counter() - t0) / ne2e)
+    e2e_parts = {k: float(np.median(v)) for k, v in parts.items()}
+    e2e_parts["host_ms"] = e2e_parts["step_ms"] - e2e_parts["device_ms"] - e2e_parts["d2h_ms"]
+    e2e_parts["step_ms_spread"] = [float(min(parts["step_ms"])), float(max(parts["step_ms"]))]
+    e2e_parts["note"] = ("medians per step: H2D on a copy stream overlapping the factor; device = factor + solve "
+                         "on the compute stream (handle setup and the refinement's host decisions included); "
+                         "host = the rest of the wall time")
     sampler.stop()
     clocks = sampler.summary()
 
@@ -543,7 +564,8 @@ def run_gpu(args):
                   "fp64": "f64"}[prec] + ("" if iprec is None else f"; interface {iprec}"
                                             + (" (FP64-accurate tensor-core products)" if iprec == "fp64tc" else "")),
         "data": "synthetic",
-        "config": dict(W, precision=prec, l2="every step streams > 10 GB (>> 129 MB L2); no explicit flush"),
+        "config": dict(W, precision=prec, autotune=bool(args.autotune),
+                       l2="every step streams > 10 GB (>> 129 MB L2); no explicit flush"),
         "max_relres": max(rels),
         "refine_steps": its,
         "phase_ms": {"factor": factor_ms, "solve_refine": solve_ms},
@@ -552,7 +574,7 @@ def run_gpu(args):
         "roofline": roof,
         "dense_rooflines": dense,
         "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(f_host.numel() * 8),
-                "d2h_bytes_per_step": int(u_host.numel() * 8)},
+                "d2h_bytes_per_step": int(u_host.numel() * 8), "breakdown": e2e_parts},
         "gpu_launches": int(np.mean(launches)) if launches else None,
         "clocks": clocks,
     }
@@ -654,55 +676,122 @@ def cpu_baseline(n_full, b, k, kind="diffusion", rungs=((512, 3),)):
 def run_adjoint_batch(args):
     """Batched adjoint workload: 256 independent 2-D diffusion problems, n in {256, ..., 1024}, b = 16;
     per step every problem is factored, solved, its loss ||u - u_t||^2 formed and dL/dkappa computed by
-    the adjoint solve (waves of problems, each problem on a stream of its own)."""
+    the adjoint solve.  Default: the CUDA-graph batch (slab_batch: everything allocated once, one graph
+    launch per wave of problems); --no-graph: the stream-per-problem path (slab_factor_batched ...)."""
     import numpy as np
     import torch
 
     from paper_2211_07572_gb300 import inputs
-    from paper_2211_07572_gb300.solver import batched_adjoint_gradients
+    from paper_2211_07572_gb300.solver import GraphBatch, batched_adjoint_gradients
     dev = rank_device()
     rank, _, world = dist_env()
     sizes = inputs.adjoint_batch_sizes()
     count = args.count or len(sizes)
-    sizes = sizes[:count]
-    probs, fs, uts = [], [], []
-    for i, n in enumerate(sizes):
-        d = inputs.adjoint_instance(i, int(n))
-        probs.append(dict(dim=2, n=int(n), b=16, kind=inputs.DIFFUSION, kappa=d["kappa"]))
-        fs.append(torch.from_numpy(d["f"]).to(dev))
-        uts.append(torch.from_numpy(d["u_target"]).to(dev))
+    sizes = [int(n) for n in sizes[:count]]
+    data = [inputs.adjoint_instance(i, n) for i, n in enumerate(sizes)]
     prec = args.precision
+    stream = torch.cuda.current_stream(dev)
+    line_extra = {}
+    if args.graph:
+        t0 = time.perf_counter()
+        gb = GraphBatch(sizes, b=16, precision=prec, rtol=1e-12, steps=args.graph_steps, wave=args.wave,
+                        branches=args.branches)
+        t_create = time.perf_counter() - t0
+        host = []                                      # pinned host copies of every input
+        for i, d in enumerate(data):
+            hk = torch.from_numpy(d["kappa"]).pin_memory()
+            hf = torch.from_numpy(d["f"]).pin_memory()
+            ht = torch.from_numpy(d["u_target"]).pin_memory()
+            host.append((hk, hf, ht))
+            gb.set_inputs(i, hk.to(dev), hf.to(dev), ht.to(dev))
+        torch.cuda.synchronize()
 
-    def step(precision=prec):
-        return batched_adjoint_gradients(probs, fs, uts, wave=args.wave, workers=8, precision=precision)
+        def step():
+            gb.run(stream)
+            return gb.results()
 
-    for _ in range(args.warmup):
-        step()
-    sampler = ClockSampler()
-    sampler.start()
-    dist_barrier()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        losses, grads = step()
-    torch.cuda.synchronize()
-    dist_barrier()
-    sec = dist_max((time.perf_counter() - t0) / args.steps)
-    sampler.stop()
+        for _ in range(args.warmup):
+            L, ru, rl = step()
+        sampler = ClockSampler()
+        sampler.start()
+        dist_barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        worst = 0.0
+        for _ in range(args.steps):
+            L, ru, rl = step()
+            worst = max(worst, float(ru.max()), float(rl.max()))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        dist_barrier()
+        sec = dist_max(e0.elapsed_time(e1) / 1e3 / args.steps)
+        # end to end: inputs from pinned host memory into the batch's buffers, every gradient back
+        grads_host = [torch.empty((n + 1, n + 1), dtype=torch.float64).pin_memory() for n in sizes]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            for i, (hk, hf, ht) in enumerate(host):
+                k_, f_, t_ = gb.inputs(i)
+                k_.copy_(hk.view_as(k_), non_blocking=True)
+                f_.copy_(hf.view_as(f_), non_blocking=True)
+                t_.copy_(ht.view_as(t_), non_blocking=True)
+            gb.run(stream)
+            for i in range(count):
+                grads_host[i].copy_(gb.outputs(i)[2], non_blocking=True)
+            gb.results()
+            torch.cuda.synchronize()
+        e2e = dist_max((time.perf_counter() - t0) / args.steps)
+        sampler.stop()
+        h2d = sum(int(a.numel() + b_.numel() + c.numel()) * 8 for a, b_, c in host)
+        d2h = sum(int(g.numel()) * 8 for g in grads_host)
+        line_extra = {"e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                      "max_relres": worst, "graph": {"create_s": t_create, "device_bytes": gb.device_bytes,
+                                                     "waves": (count + (args.wave or count) - 1) // (args.wave or count),
+                                                     "branches": args.branches, "refine_steps": args.graph_steps}}
+        losses = L
+        gb.close()
+        timing = "CUDA events around the graph launches and the results read (device-resident inputs)"
+    else:
+        probs, fs, uts = [], [], []
+        for d, n in zip(data, sizes):
+            probs.append(dict(dim=2, n=int(n), b=16, kind=inputs.DIFFUSION, kappa=d["kappa"]))
+            fs.append(torch.from_numpy(d["f"]).to(dev))
+            uts.append(torch.from_numpy(d["u_target"]).to(dev))
+
+        def step(precision=prec):
+            return batched_adjoint_gradients(probs, fs, uts, wave=args.wave or 32, workers=8, precision=precision)
+
+        for _ in range(args.warmup):
+            step()
+        sampler = ClockSampler()
+        sampler.start()
+        dist_barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            losses, grads = step()
+        torch.cuda.synchronize()
+        dist_barrier()
+        sec = dist_max((time.perf_counter() - t0) / args.steps)
+        sampler.stop()
+        timing = "host clock around device-synchronised steps (problems run on their own streams)"
     line = {
         "metric": "batched adjoint: factor+solve+adjoint+gradient s per batch",
         "value": sec, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": sec * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 factor (3xTF32 tensor products) / f64 residual+refinement" if prec == "fp32" else prec,
+        "dtype": ("f32 factor (FP32-accurate tensor products) / f64 residual+refinement" if prec == "fp32"
+                  else prec),
         "data": "synthetic",
         "config": {"workload": f"batched adjoint {count} x 2D diffusion n in {{256..1024}} b=16, L=||u-u_t||^2",
-                   "count": count, "wave": args.wave, "workers": 8, "precision": prec,
-                   "timing": "host clock around device-synchronised steps (problems run on their own streams)"},
+                   "count": count, "wave": args.wave, "precision": prec, "graph": bool(args.graph),
+                   "timing": timing},
         "instances_per_s": count / sec,
         "mean_loss": float(np.mean(losses)),
         "clocks": sampler.summary(),
     }
-    if args.fp64_comparator and prec != "fp64":
+    line.update(line_extra)
+    if args.fp64_comparator and prec != "fp64" and not args.graph:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         step("fp64")
@@ -838,12 +927,19 @@ def main():
     ap.add_argument("--no-fp64", dest="fp64_comparator", action="store_false")
     ap.add_argument("--once", action="store_true", help="run one step only (for profilers)")
     ap.add_argument("--count", type=int, default=0, help="adjoint256: number of problems (0: all 256)")
-    ap.add_argument("--wave", type=int, default=32, help="adjoint256: problems per wave")
+    ap.add_argument("--wave", type=int, default=64, help="adjoint256: problems per wave (graph: per graph)")
+    ap.add_argument("--no-graph", dest="graph", action="store_false",
+                    help="adjoint256: stream-per-problem path instead of the CUDA-graph batch")
+    ap.add_argument("--graph-steps", type=int, default=4, help="adjoint256 graph: refinement passes per solve")
+    ap.add_argument("--branches", type=int, default=16, help="adjoint256 graph: parallel branches per wave")
     ap.add_argument("--workload", default="diffusion3d96",
                     choices=["diffusion2048", "helmholtz4096", "diffusion3d96", "adjoint256", "helmholtzj0"],
                     help="diffusion3d96: the default bench line (3-D diffusion n=96, b=8, k=16); diffusion2048, "
                          "helmholtz4096, adjoint256, helmholtzj0: the other workloads")
     ap.add_argument("--krylov", type=int, default=0, help="0: plain refinement; m: FP64 GMRES(m) refinement")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="keep the fixed size heuristic for the factor products instead of the online tuner "
+                         "(which decides during the warm-up steps)")
     ap.add_argument("--interface", default="default", choices=["default", "fp32", "fp64", "fp64tc", "tf32"],
                     help="precision of the interface system (fp64tc: FP64-accurate tensor-core products)")
     ap.add_argument("--stage2", default="auto", choices=["auto", "sweep", "oddeven"],
@@ -851,6 +947,9 @@ def main():
     args = ap.parse_args()
     if args.gpus != dist_env()[2] and dist_env()[2] > 1:
         raise SystemExit(f"--gpus {args.gpus} but the launcher started {dist_env()[2]} ranks")
+    if args.impl != "reference":
+        from paper_2211_07572_gb300 import _lib
+        _lib.load().slab_autotune(1 if args.autotune else 0)
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "adjoint256":

@@ -77,7 +77,10 @@ typedef enum {
  * numbers per interface in the factor versus about 5 for SWEEP.
  * ODDEVEN does about 4x the dense flops of SWEEP but in log2(N_I) batched levels, which pays
  * on the tensor-core (FP32) path; on the SIMT FP64 path SWEEP is faster.
- * AUTO: ODDEVEN for POISSON / DIFFUSION with N_I >= 4 and an FP32 factor, SWEEP otherwise.
+ * AUTO: for POISSON / DIFFUSION with N_I >= 4 and an FP32 interface system, whichever order a cost
+ * model (latency of the s_pad / 64 panel steps on the critical path plus the dense flops) predicts
+ * faster -- ODDEVEN for many small interface blocks (e.g. 2-D n = 2048, b = 32), SWEEP for few
+ * large ones (e.g. 3-D n = 96, b = 8); SWEEP otherwise.
  */
 typedef enum {
     SLAB_STAGE2_AUTO = 0,
@@ -276,12 +279,71 @@ slab_status slab_fp64_tc_gemm(int M, int N, int K, double alpha, const double* A
                               unsigned* dev_err, void* stream);
 size_t slab_fp64_tc_gemm_work_bytes(int M, int N, int K);
 
+/*
+ * Batches of independent problems as CUDA graphs (the batched adjoint workload).  count 2-D
+ * DIFFUSION problems, problem i on the n[i] x n[i] grid with interface spacing b[i] (uneven sizes
+ * allowed), each with one load f_i and one target t_i and the least-squares objective
+ *   L_i = ||u_i - t_i||^2,  u_i = A_i^-1 f_i.
+ * One run computes, for every problem: the factor (Algorithm 3), u_i with one solve pass and
+ * `steps` refinement passes (Algorithm 4), L_i, lambda_i = A_i^-T dL_i/du_i with the same factors
+ * (A_i is symmetric) and steps refinement passes, and grad_i = dL_i/dkappa_i at the (n[i]+1)^2 nodes.
+ * slab_batch_create allocates every device buffer once (one region: the inputs and outputs of all
+ * problems plus the factor memory of the largest wave) and records all launches of each wave of
+ * `wave` problems (0: all) into one CUDA graph, the wave's problems spread over `branches` parallel
+ * graph branches (0: 16); waves run one after another and reuse the factor memory.  A run is then
+ * one graph launch per wave with no allocation, no host synchronisation and no host decision.
+ * opts: as for slab_factor (factor_prec, interface_prec, stage2, rtol; krylov must be 0; stream
+ * and profile are ignored); steps in 0..100.  SLAB_EINVAL for bad sizes, SLAB_ENOMEM when the region
+ * does not fit, SLAB_EUNSUPPORTED for krylov > 0.  Synchronises before returning.
+ */
+typedef struct slab_batch slab_batch;
+slab_status slab_batch_create(int count, const int* n, const int* b, const slab_opts* opts, int steps, int wave,
+                              int branches, slab_batch** out);
+/* Device buffers of problem i, owned by the batch (valid until slab_batch_destroy): inputs kappa
+ * ((n+1)^2 nodes), f and target ((n-1)^2 interior nodes); outputs u, lambda ((n-1)^2) and grad
+ * ((n+1)^2).  Write the inputs before slab_batch_run (any stream ordered before it); any pointer
+ * argument may be NULL. */
+slab_status slab_batch_buffers(slab_batch* B, int i, double** kappa, double** f, double** target, double** u,
+                               double** lambda, double** grad);
+/* Enqueue one run of every wave's graph on `stream` (a cudaStream_t, NULL = legacy default).
+ * Runs of one batch must not overlap (they share the factor memory). */
+slab_status slab_batch_run(slab_batch* B, void* stream);
+/* Wait for the last run and read per problem (HOST arrays of count entries, each may be NULL) the
+ * loss L_i and the relative residuals ||f - A u|| / ||f|| and ||g - A lambda|| / ||g|| it reached.
+ * Returns SLAB_ESINGULAR / SLAB_ETIMEOUT if a factor reported one, else SLAB_ENOCONV if a residual
+ * is above opts->rtol (raise `steps`), else SLAB_OK. */
+slab_status slab_batch_results(slab_batch* B, double* loss, double* relres_u, double* relres_lambda);
+/* Bytes of the batch's device region. */
+int64_t slab_batch_device_bytes(const slab_batch* B);
+void slab_batch_destroy(slab_batch* B);
+
+/*
+ * Online tuning of the factor's tensor-core products (process-wide, all devices).  The FP32-accurate
+ * factor products have three implementations: three FP16 products of row-scaled hi/lo splits on
+ * 128 x 128 or 128 x 256 tiles (a pre-pass makes the splits), or 3xTF32 with the split inside the
+ * kernel (no pre-pass, half the MMA rate).  mode 1: the first calls of each shape class (log2
+ * buckets of M, N, K and the batch) run every candidate twice, timed by CUDA events on the
+ * launching stream, and the class then keeps the fastest per flop; mode 0: a fixed size heuristic
+ * (the default; also set by the environment variable SLAB_AUTOTUNE=1 / 0 before the first call);
+ * mode 2: forget every decision (mode unchanged).  Returns the previous mode.  Results of the
+ * candidates agree to FP32 rounding, so tuning changes only the last bits and the time.  Launches
+ * on a stream under CUDA graph capture are never timed: they use the decided candidate, or the
+ * heuristic one while the class is undecided.
+ */
+int slab_autotune(int mode);
+/* Shape classes seen, decided, decided for 3xTF32, decided for the other tile width (each may be NULL). */
+slab_status slab_autotune_stats(int* classes, int* decided, int* tf32x3, int* alt_width);
+
 #define SLAB_KERNEL_CLASSES 14
 slab_status slab_profile(slab_handle* h, int enable);
 slab_status slab_profile_read(slab_handle* h, double* ms, int64_t* launches, int n);
 
 /* Sizes: unknowns (n-1)^d, interface size (n-1)^(d-1), number of interfaces N_I. */
 slab_status slab_sizes(const slab_handle* h, int64_t* unknowns, int64_t* iface_size, int* n_ifaces);
+
+/* Elimination order Stage 2 used for this handle: SLAB_STAGE2_SWEEP or SLAB_STAGE2_ODDEVEN (what
+ * SLAB_STAGE2_AUTO resolved to); 0 for a NULL handle. */
+int slab_stage2_order(const slab_handle* h);
 
 /* Bytes of device memory the handle holds. */
 int64_t slab_device_bytes(const slab_handle* h);

@@ -57,6 +57,7 @@ SIGNATURES = {
     "slab_get_T_block": (c_int, [c_void_p, c_int, c_int, c_void_p]),
     "slab_sizes": (c_int, [c_void_p, ctypes.POINTER(c_int64), ctypes.POINTER(c_int64), ctypes.POINTER(c_int)]),
     "slab_device_bytes": (c_int64, [c_void_p]),
+    "slab_stage2_order": (c_int, [c_void_p]),
     "slab_last_error": (c_int, [c_void_p]),
     "slab_destroy": (None, [c_void_p]),
     "slab_strerror": (ctypes.c_char_p, [c_int]),
@@ -69,6 +70,15 @@ SIGNATURES = {
     "slab_fp64_tc_gemm": (c_int, [c_int, c_int, c_int, c_double, c_void_p, c_int64, c_void_p, c_int64, c_void_p,
                                   c_int64, c_void_p, c_void_p, c_void_p]),
     "slab_fp64_tc_gemm_work_bytes": (ctypes.c_size_t, [c_int, c_int, c_int]),
+    "slab_batch_create": (c_int, [c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(SlabOpts),
+                                  c_int, c_int, c_int, ctypes.POINTER(c_void_p)]),
+    "slab_batch_buffers": (c_int, [c_void_p, c_int] + [ctypes.POINTER(c_void_p)] * 6),
+    "slab_batch_run": (c_int, [c_void_p, c_void_p]),
+    "slab_batch_results": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "slab_batch_device_bytes": (c_int64, [c_void_p]),
+    "slab_batch_destroy": (None, [c_void_p]),
+    "slab_autotune": (c_int, [c_int]),
+    "slab_autotune_stats": (c_int, [ctypes.POINTER(c_int)] * 4),
     "slab_factor_batched": (c_int, [c_int, ctypes.POINTER(SlabGrid), ctypes.POINTER(SlabCoeffs),
                                     ctypes.POINTER(c_int), ctypes.POINTER(SlabOpts), c_int, ctypes.POINTER(c_void_p)]),
     "slab_solve_batched": (c_int, [c_int, ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p),

@@ -26,6 +26,15 @@ namespace {
 slab_status dalloc(slab_handle* h, void** p, size_t bytes) {
     *p = nullptr;
     if (bytes == 0) return SLAB_OK;
+    if (h->arena) {
+        SlabArena* A = h->arena;
+        const size_t off = (A->off + 255) & ~(size_t)255;
+        if (A->base && off + bytes > A->cap) return SLAB_ENOMEM;
+        *p = A->base + off;                            // sizing pass: an offset, never dereferenced
+        A->off = off + bytes;
+        h->dev_bytes += (int64_t)bytes;
+        return SLAB_OK;
+    }
     cudaError_t e = cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -119,14 +128,15 @@ slab_status ensure_workspace(slab_handle* h, int k) {
         TRY(dalloc(h, &h->wVp, (e ? e : 1) * h->rsz));
         const size_t nt = tree_down_tickets(d.s, d.NS);
         TRY(dalloc(h, &h->wVtk, nt * sizeof(unsigned)));
-        SLAB_CK(h, cudaMemsetAsync(h->wVtk, 0, nt * sizeof(unsigned), h->stream));
+        if (!sizing_pass(h)) SLAB_CK(h, cudaMemsetAsync(h->wVtk, 0, nt * sizeof(unsigned), h->stream));
     }
     if (!h->wPart) {
         TRY(dalloc(h, &h->wPart, splitk_part_bytes(d.s_pad)));
         void* tk = nullptr;
         TRY(dalloc(h, &tk, (size_t)(d.s_pad / SLAB_TILE) * sizeof(unsigned)));
         h->wTickets = (unsigned*)tk;
-        SLAB_CK(h, cudaMemsetAsync(h->wTickets, 0, (size_t)(d.s_pad / SLAB_TILE) * sizeof(unsigned), h->stream));
+        if (!sizing_pass(h))
+            SLAB_CK(h, cudaMemsetAsync(h->wTickets, 0, (size_t)(d.s_pad / SLAB_TILE) * sizeof(unsigned), h->stream));
     }
     return SLAB_OK;
 }
@@ -197,6 +207,34 @@ slab_status pass(slab_handle* h, const double* F, double fscale, double* U, int 
 
 }  // namespace
 
+slab_status slab_dalloc(slab_handle* h, void** p, size_t bytes) { return dalloc(h, p, bytes); }
+
+slab_status solve_prepare(slab_handle* h, int k) {
+    TRY(ensure_workspace(h, k));
+    TRY(ensure_resid(h, k));
+    return ensure_red(h, k);
+}
+
+slab_status reset_scratch(slab_handle* h) {
+    if (h->wVtk && h->dim == 2)
+        SLAB_CK(h, cudaMemsetAsync(h->wVtk, 0, tree_down_tickets(h->td.s, h->td.NS) * sizeof(unsigned), h->stream));
+    if (h->wTickets)
+        SLAB_CK(h, cudaMemsetAsync(h->wTickets, 0, (size_t)(h->td.s_pad / SLAB_TILE) * sizeof(unsigned), h->stream));
+    if (h->red_tickets) SLAB_CK(h, cudaMemsetAsync(h->red_tickets, 0, h->ticket_cap * sizeof(unsigned), h->stream));
+    return SLAB_OK;
+}
+
+slab_status solve_fixed(slab_handle* h, const double* f, double* u, int k, int steps, double* nrm) {
+    const double h2 = 1.0 / ((double)h->n * (double)h->n);
+    TRY(pass(h, f, h2, u, 0, k));
+    for (int it = 0; it < steps; ++it) {
+        TRY(launch_residual(h, u, f, h->wR, k, nullptr, nullptr));
+        TRY(pass(h, h->wR, h2, u, 1, k));
+    }
+    SLAB_CK(h, cudaMemsetAsync(nrm, 0, 2 * (size_t)k * sizeof(double), h->stream));
+    return launch_residual(h, u, f, h->wR, k, nrm, nrm + k);
+}
+
 bool slab_debug() {
     static const bool on = std::getenv("SLAB_DEBUG") != nullptr;
     return on;
@@ -266,6 +304,12 @@ slab_status factor_impl(slab_handle* h) {
     h->fp64tc_now = 0;
     return st2;
 }
+
+}  // namespace
+
+slab_status factor_status(slab_handle* h) { return sync_status(h); }
+
+namespace {
 
 struct ProfRecord {
     std::vector<cudaEvent_t> pool;     // event pairs, reused
@@ -373,6 +417,13 @@ void slab_destroy(slab_handle* h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
     const cudaStream_t own = h->own_stream ? h->stream : nullptr;
+    if (h->arena) {                                    // buffers belong to the arena's owner
+        if (h->t3plan) tree3d_plan_free(h->t3plan);
+        if (own) cudaStreamDestroy(own);
+        prof_free(h);
+        delete h;
+        return;
+    }
     free_workspace(h);
     dfree(h->wX2); dfree(h->wZ2);
     {
@@ -395,8 +446,41 @@ void slab_destroy(slab_handle* h) {
     delete h;
 }
 
-slab_status slab_factor(const slab_grid* grid, const slab_coeffs* co, int b, const slab_opts* opts,
-                        slab_handle** out) {
+}  // extern "C"
+
+namespace {
+
+// Elimination order of an FP32 Stage 2 when the caller leaves it open.  Both orders run one
+// tall Cholesky per eliminated block, whose s_pad / 64 panel steps are latency-bound (about
+// 35 us each: two small launches and a thin update, measured on GB300), while the products run
+// at a few hundred TFLOP/s.  The sweep eliminates N_I blocks one after another with about
+// 2.7 s_pad^3 flops each; the odd-even order eliminates a whole level per batch (so only the
+// levels count towards the panel latency) but does about 3 s_pad^3 per eliminated block plus
+// 5 s_pad^3 per block with a right neighbour.  Pick the smaller modelled time.
+bool oddeven_is_faster(int NI, int s_pad) {
+    const double panel_s = 35e-6, rate = 3e14;
+    const double P = s_pad / 64.0, s3 = (double)s_pad * s_pad * s_pad;
+    int levels = 0, nb = 0, nc = 0;
+    for (int step = 1; step < NI; step *= 2) {
+        const int nrem = (NI - 1) / step + 1;
+        if (nrem < 2) break;
+        ++levels;
+        nb += nrem / 2;
+        nc += (nrem - 1) / 2;
+    }
+    const double t_sweep = NI * P * panel_s + NI * 2.7 * s3 / rate;
+    const double t_oe = (levels + 1) * P * panel_s + (nb * 3.0 + nc * 5.0 + 1.0) * s3 / rate;
+    return t_oe < t_sweep;
+}
+
+}  // namespace
+
+// slab_factor in three steps, so that a batch can allocate everything first and record only
+// launches in a CUDA graph: factor_create validates and allocates (no kernel runs), factor_launch
+// enqueues the factor on h->stream (no allocation, no host synchronisation), factor_finish waits,
+// reads the device status word and frees the factor-only buffers.
+slab_status factor_create(const slab_grid* grid, const slab_coeffs* co, int b, const slab_opts* opts,
+                          slab_handle** out, SlabArena* arena) {
     if (!grid || !co || !out) return SLAB_EINVAL;
     *out = nullptr;
     slab_opts o;
@@ -427,6 +511,7 @@ slab_status slab_factor(const slab_grid* grid, const slab_coeffs* co, int b, con
     slab_handle* h = new (std::nothrow) slab_handle();
     if (!h) return SLAB_ENOMEM;
     std::memset(h, 0, sizeof(*h));
+    h->arena = arena;
     h->dim = grid->dim; h->n = n; h->b = b; h->kind = co->kind; h->omega = co->omega;
     h->prec = o.factor_prec;
     h->rsz = h->prec == SLAB_PREC_FP64 ? 8 : 4;
@@ -498,7 +583,7 @@ slab_status slab_factor(const slab_grid* grid, const slab_coeffs* co, int b, con
     }
     h->stage2 = o.stage2 == SLAB_STAGE2_ODDEVEN ||
                 (o.stage2 == SLAB_STAGE2_AUTO && co->kind != SLAB_HELMHOLTZ && d.NI >= 4 &&
-                 h->prec2 == SLAB_PREC_FP32);
+                 h->prec2 == SLAB_PREC_FP32 && oddeven_is_faster(d.NI, d.s_pad));
     if (h->stage2) {
         ALLOC(h->crD, d.NI * blk * R2);
         ALLOC(h->crE, (d.NI > 1 ? d.NI - 1 : 1) * blk * R2);
@@ -530,27 +615,37 @@ slab_status slab_factor(const slab_grid* grid, const slab_coeffs* co, int b, con
     ALLOC(h->Linv, d.NI * blk * R2);
     if (!h->stage2) ALLOC(h->Y, (d.NI - 1) * blk * R2);
     ALLOC(h->dstatus, sizeof(unsigned));
+    {
+        // panel inverses of the tall Cholesky: one 64 x 64 block per matrix of its largest batch
+        int pb = h->stage2 ? cr_max_batch(d.NI) : 1;
+        if (grid->dim == 3) pb = std::max(pb, d.NS * tree_nodes_at(d.s, 0));
+        h->pnl_bytes = (size_t)std::min(pb, 65535) * SLAB_TILE * SLAB_TILE * std::max(R, R2);
+        ALLOC(h->pnl, h->pnl_bytes);
+    }
 #undef ALLOC
-#define CK(call)                                                               \
-    do {                                                                       \
-        if ((call) != cudaSuccess) { cudaGetLastError(); slab_destroy(h); return SLAB_ECUDA; } \
-    } while (0)
-    CK(cudaMemsetAsync(h->dstatus, 0, sizeof(unsigned), h->stream));
-    if (h->tZI) CK(cudaMemsetAsync(h->tZI, 0, (size_t)d.NS * d.H * 2 * d.m * d.s_pad * R, h->stream));
-    if (h->tRI) CK(cudaMemsetAsync(h->tRI, 0, (size_t)d.NS * d.H * 4 * d.m * d.s_pad * R, h->stream));
-    if (h->tWI) CK(cudaMemsetAsync(h->tWI, 0, (size_t)d.NS * d.H * 2 * d.m * d.s_pad * R, h->stream));
-    if (h->kappa)
-        CK(cudaMemcpyAsync(h->kappa, co->kappa, nodes2 * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
-#undef CK
-    st = launch_coefficients(h, co->kappa, co->c);
+    *out = h;
+    return SLAB_OK;
+}
+
+// Enqueue the factor of a created handle for the coefficients co (read during the launches).
+slab_status factor_launch(slab_handle* h, const double* kappa, const double* c) {
+    const TreeDims& d = h->td;
+    const size_t R = h->rsz;
+    const size_t nodes2 = (size_t)(h->n + 1) * (h->n + 1) * (h->dim == 3 ? (size_t)(h->n + 1) : 1);
+    SLAB_CK(h, cudaMemsetAsync(h->dstatus, 0, sizeof(unsigned), h->stream));
+    if (h->tZI) SLAB_CK(h, cudaMemsetAsync(h->tZI, 0, (size_t)d.NS * d.H * 2 * d.m * d.s_pad * R, h->stream));
+    if (h->tRI) SLAB_CK(h, cudaMemsetAsync(h->tRI, 0, (size_t)d.NS * d.H * 4 * d.m * d.s_pad * R, h->stream));
+    if (h->tWI) SLAB_CK(h, cudaMemsetAsync(h->tWI, 0, (size_t)d.NS * d.H * 2 * d.m * d.s_pad * R, h->stream));
+    if (h->kappa && kappa != h->kappa)
+        SLAB_CK(h, cudaMemcpyAsync(h->kappa, kappa, nodes2 * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    slab_status st = launch_coefficients(h, kappa, c);
     h->tf32_now = h->tf32;
     if (!st) st = h->prec == SLAB_PREC_FP64 ? factor_impl<double>(h) : factor_impl<float>(h);
     h->tf32_now = 0;
-    if (!st) st = sync_status(h);
-    if (st) {
-        slab_destroy(h);
-        return st;
-    }
+    return st;
+}
+
+static void free_factor_only(slab_handle* h) {
     dfree(h->Tb1);                                     // mixed-mode assembly buffers
     dfree(h->To1);
     h->Tb1 = h->To1 = nullptr;
@@ -563,6 +658,24 @@ slab_status slab_factor(const slab_grid* grid, const slab_coeffs* co, int b, con
     dfree(h->t3Rtb);                                   // 3-D factor-only arrays
     dfree(h->t3RI);
     dfree(h->t3W);
+}
+
+extern "C" {
+
+slab_status slab_factor(const slab_grid* grid, const slab_coeffs* co, int b, const slab_opts* opts,
+                        slab_handle** out) {
+    if (!out) return SLAB_EINVAL;
+    *out = nullptr;
+    slab_handle* h = nullptr;
+    slab_status st = factor_create(grid, co, b, opts, &h, nullptr);
+    if (st) return st;
+    st = factor_launch(h, co->kappa, co->c);
+    if (!st) st = sync_status(h);
+    if (st) {
+        slab_destroy(h);
+        return st;
+    }
+    free_factor_only(h);
     *out = h;
     return SLAB_OK;
 }
@@ -897,6 +1010,11 @@ slab_status slab_sizes(const slab_handle* h, int64_t* unknowns, int64_t* iface_s
 }
 
 int64_t slab_device_bytes(const slab_handle* h) { return h ? h->dev_bytes : 0; }
+
+int slab_stage2_order(const slab_handle* h) {
+    if (!h) return 0;
+    return h->stage2 ? SLAB_STAGE2_ODDEVEN : SLAB_STAGE2_SWEEP;
+}
 
 slab_status slab_last_error(const slab_handle* h) { return h ? h->err : SLAB_EINVAL; }
 

@@ -861,6 +861,26 @@ template <>
 slab_status gemm_tn_batched<float>(slab_handle* h, int cls, int M, int N, int K, float alpha, const float* A,
                                    int64_t lda, int64_t sA, const float* B, int64_t ldb, int64_t sB, float beta,
                                    float* C, int64_t ldc, int64_t sC, int transC, int lower_only, int batch) {
+    // a factor product whose operand splits do not fit the FP16 work buffer runs on slices of the
+    // batch that do, rather than falling back to the slower 3xTF32 product
+    if (batch > 1 && h->w16 && !h->tf32_now && K % 64 == 0 &&
+        (cls == KC_SYRK || cls == KC_TRAIL || cls == KC_ASSEMBLE)) {
+        const bool shared = A == B && lda == ldb && sA == sB && N <= M;
+        if (f16x3_work_bytes(M, N, K, batch, shared) > h->w16_bytes) {
+            int bc = batch;
+            while (bc > 1 && f16x3_work_bytes(M, N, K, bc, shared) > h->w16_bytes) bc = (bc + 1) / 2;
+            if (f16x3_work_bytes(M, N, K, bc, shared) <= h->w16_bytes) {
+                for (int b0 = 0; b0 < batch; b0 += bc) {
+                    const int nb = std::min(bc, batch - b0);
+                    const slab_status st = gemm_tn_batched<float>(h, cls, M, N, K, alpha, A + b0 * sA, lda, sA,
+                                                                  B + b0 * sB, ldb, sB, beta, C + b0 * sC, ldc, sC,
+                                                                  transC, lower_only, nb);
+                    if (st) return st;
+                }
+                return SLAB_OK;
+            }
+        }
+    }
     SLAB_PROF(h, cls);
     TcGemmArgs g;
     g.M = M; g.N = N; g.K = K; g.alpha = alpha; g.beta = beta;
@@ -1371,15 +1391,15 @@ __global__ void copy_batched_kernel(const T* __restrict__ in, int64_t sin, T* __
 }  // namespace
 
 // Panel workspace (one 64 x 64 inverse per matrix of a batch); grown on demand during the factor.
+// The factor allocates the panel inverses for its largest batch up front (factor_create); a
+// larger request (direct use of the tall Cholesky) grows them.
 static slab_status ensure_panel_work(slab_handle* h, size_t bytes) {
     if (h->pnl_bytes >= bytes) return SLAB_OK;
-    if (h->pnl) cudaFree(h->pnl);                      // waits for the work that may still read it
+    if (h->pnl && !h->arena) cudaFree(h->pnl);         // waits for the work that may still read it
     h->pnl = nullptr;
     h->pnl_bytes = 0;
-    if (cudaMalloc(&h->pnl, bytes) != cudaSuccess) {
-        cudaGetLastError();
-        return SLAB_ENOMEM;
-    }
+    const slab_status st = slab_dalloc(h, &h->pnl, bytes);
+    if (st) return st;
     h->pnl_bytes = bytes;
     return SLAB_OK;
 }

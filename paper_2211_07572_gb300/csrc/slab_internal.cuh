@@ -51,8 +51,16 @@ struct TreeDims {
     int b, n;
 };
 
+// Bump allocator over one device region; handles created in it never free their buffers (the
+// region's owner frees it).  With base == nullptr it only adds up the bytes (a sizing pass).
+struct SlabArena {
+    char* base;
+    size_t off, cap;
+};
+
 struct slab_handle {
     int dim, n, b, kind;
+    SlabArena* arena;         // non-null: every device buffer comes from this arena
     double omega;
     int prec;                 // slab_precision of Stage 1 (slab trees, T assembly, tree solves)
     size_t rsz;               // bytes of the Stage-1 scalar
@@ -193,6 +201,27 @@ __host__ __device__ inline int tree_right_height(int s, int c, int k) {
     return -1;
 }
 
+// A sizing pass over an arena without memory: buffers are offsets only, so nothing may touch them.
+inline bool sizing_pass(const slab_handle* h) { return h->arena && !h->arena->base; }
+
+// ---------------------------------------------------------------- building blocks (api.cu)
+// Device allocation of a handle's buffer (from its arena if it has one; counted in dev_bytes).
+slab_status slab_dalloc(slab_handle* h, void** p, size_t bytes);
+// slab_factor in steps: create validates and allocates every buffer the factor needs (no kernel
+// runs); launch enqueues the factor on h->stream with no allocation and no host synchronisation;
+// factor_status synchronises the stream and maps the device status word to a slab_status.
+slab_status factor_create(const slab_grid* grid, const slab_coeffs* co, int b, const slab_opts* opts,
+                          slab_handle** out, SlabArena* arena);
+slab_status factor_launch(slab_handle* h, const double* kappa, const double* c);
+slab_status factor_status(slab_handle* h);
+// Every buffer a solve of k loads needs (solve workspace, FP64 residual, norm reduction).
+slab_status solve_prepare(slab_handle* h, int k);
+// Zero the self-resetting ticket counters of a handle whose memory may hold another's old data.
+slab_status reset_scratch(slab_handle* h);
+// u = A^-1 f by one solve pass and `steps` refinement passes, then nrm[q] = ||f_q - A u_q||^2 and
+// nrm[k + q] = ||f_q||^2 on the device: enqueued on h->stream, no allocation, no host sync.
+slab_status solve_fixed(slab_handle* h, const double* f, double* u, int k, int steps, double* nrm);
+
 // ---------------------------------------------------------------- launchers (defined in .cu files)
 // coefficients / stencil (stencil.cu)
 slab_status launch_coefficients(slab_handle* h, const double* kappa, const double* c);
@@ -201,6 +230,8 @@ slab_status launch_residual(slab_handle* h, const double* u, const double* f, do
 slab_status launch_apply(slab_handle* h, const double* x, double* y, int k);
 slab_status launch_boundary_lift(slab_handle* h, const double* g, const double* f, double* fo, int k);
 slab_status launch_kappa_gradient(slab_handle* h, const double* u, const double* lam, double* g, int k);
+// Sizes the norm-reduction scratch of launch_residual for k right-hand sides.
+slab_status ensure_red(slab_handle* h, int k);
 // FP64 vector kernels for the Krylov refinement (batched over k vectors of length N)
 slab_status vec_dot(slab_handle* h, const double* x, const double* y, int64_t N, int k, double* part, double* out);
 slab_status vec_axpy(slab_handle* h, double* y, const double* x, const double* c, double sign, int64_t N, int k);
@@ -288,7 +319,8 @@ size_t ozaki_work_bytes(int64_t M, int64_t N, int K);
 slab_status ozaki_gemm(cudaStream_t st, int M, int N, int K, double alpha, const double* A, int64_t lda,
                        const double* B, int64_t ldb, double* C, int64_t ldc, int lower_only, void* work,
                        unsigned* err);
-slab_status tc_gemm(cudaStream_t st, const TcGemmArgs& g, unsigned* err);
+// g.split may come back changed (the tuner can run a split-2 request as 3xTF32, split 1).
+slab_status tc_gemm(cudaStream_t st, TcGemmArgs& g, unsigned* err);
 // Kernels tc_gemm launches besides the product itself: the split-K reduction, the operand splits.
 inline int tc_gemm_extra_launches(const TcGemmArgs& g) {
     if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return -1;                 // nothing launched

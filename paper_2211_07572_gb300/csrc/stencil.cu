@@ -357,6 +357,32 @@ slab_status launch_coefficients(slab_handle* h, const double* kappa, const doubl
     return SLAB_OK;
 }
 
+slab_status ensure_red(slab_handle* h, int k) {
+    const int s = h->n - 1;
+    const size_t need = h->dim == 3 ? vec_dot_part_elems(k)
+                                    : (size_t)k * ((s + 255) / 256) * ((s + ST_ROWS - 1) / ST_ROWS) * 2;
+    const size_t tk = h->dim == 3 ? 0 : (size_t)k;
+    if (h->red_cap >= need && h->ticket_cap >= tk) return SLAB_OK;
+    if (!h->arena) {
+        if (h->red_part) cudaFree(h->red_part);
+        if (h->red_tickets) cudaFree(h->red_tickets);
+    }
+    h->red_part = nullptr; h->red_tickets = nullptr; h->red_cap = h->ticket_cap = 0;
+    void* p = nullptr;
+    slab_status st = slab_dalloc(h, &p, need * sizeof(double));
+    if (st) return st;
+    h->red_part = (double*)p;
+    h->red_cap = need;
+    if (tk) {
+        st = slab_dalloc(h, &p, tk * sizeof(unsigned));
+        if (st) return st;
+        h->red_tickets = (unsigned*)p;
+        if (!sizing_pass(h)) SLAB_CK(h, cudaMemsetAsync(h->red_tickets, 0, tk * sizeof(unsigned), h->stream));
+        h->ticket_cap = tk;
+    }
+    return SLAB_OK;
+}
+
 slab_status launch_residual(slab_handle* h, const double* u, const double* f, double* r, int k,
                             double* nrm_r, double* nrm_f) {
     const int n = h->n, s = n - 1;
@@ -375,13 +401,8 @@ slab_status launch_residual(slab_handle* h, const double* u, const double* f, do
             prof_extra(h, KC_STENCIL, (k - 1) / qc);
         }
         if (!nrm_r) return SLAB_OK;
-        const size_t need = vec_dot_part_elems(k);
-        if (h->red_cap < need) {
-            if (h->red_part) cudaFree(h->red_part);
-            h->red_part = nullptr; h->red_cap = 0;
-            SLAB_CK(h, cudaMalloc((void**)&h->red_part, need * sizeof(double)));
-            h->red_cap = need;
-        }
+        const slab_status sr = ensure_red(h, k);
+        if (sr) return sr;
         const int64_t N = (int64_t)s * s * s;
         slab_status st = vec_dot(h, r, r, N, k, h->red_part, nrm_r);
         if (!st && nrm_f) st = vec_dot(h, f, f, N, k, h->red_part, nrm_f);
@@ -391,16 +412,8 @@ slab_status launch_residual(slab_handle* h, const double* u, const double* f, do
     double* part = nullptr;
     unsigned* tickets = nullptr;
     if (nrm_r) {
-        const size_t need = (size_t)k * grid.x * grid.y * 2;
-        if (h->red_cap < need || h->ticket_cap < (size_t)k) {
-            if (h->red_part) cudaFree(h->red_part);
-            if (h->red_tickets) cudaFree(h->red_tickets);
-            h->red_part = nullptr; h->red_tickets = nullptr; h->red_cap = h->ticket_cap = 0;
-            SLAB_CK(h, cudaMalloc((void**)&h->red_part, need * sizeof(double)));
-            SLAB_CK(h, cudaMalloc((void**)&h->red_tickets, (size_t)k * sizeof(unsigned)));
-            SLAB_CK(h, cudaMemsetAsync(h->red_tickets, 0, (size_t)k * sizeof(unsigned), h->stream));
-            h->red_cap = need; h->ticket_cap = k;
-        }
+        const slab_status sr = ensure_red(h, k);
+        if (sr) return sr;
         part = h->red_part; tickets = h->red_tickets;
     }
     SLAB_PROF(h, KC_STENCIL);

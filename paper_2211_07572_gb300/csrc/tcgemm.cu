@@ -17,6 +17,10 @@
 
 #include <algorithm>
 #include <atomic>
+#include <cstdlib>
+#include <mutex>
+#include <unordered_map>
+#include <vector>
 
 #include "slab_internal.cuh"
 
@@ -641,7 +645,8 @@ struct F16Cfg {
     static constexpr int A_BYTES = BM * BK16 * 2;
     static constexpr int B_BYTES = BN * BK16 * 2;
     static constexpr int STAGE_BYTES = 2 * (A_BYTES + B_BYTES);   // hi and lo of A and B
-    static constexpr int STAGES = BN == 128 ? 3 : 4;
+    // ring depth: 192 KB of operands in flight for BN = 128 and 256 (3 x 64 KB, 2 x 96 KB)
+    static constexpr int STAGES = BN == 256 ? 2 : (BN == 128 ? 3 : 4);
     static constexpr int EPI_BYTES = 4 * 32 * 33 * 4;
     static constexpr int SMEM = STAGES * STAGE_BYTES + EPI_BYTES + 1024;
 };
@@ -932,8 +937,144 @@ slab_status launch_f16x3(cudaStream_t st, const TcGemmArgs& g, unsigned* err) {
 
 }  // namespace
 
+// 128 x 256 tiles halve the B-operand traffic per flop against 128 x 128; taken for wide products
+// that still fill every SM with them (otherwise the narrower tile keeps more SMs busy).
+bool f16x3_use_wide(const TcGemmArgs& g) {
+    if (g.N <= 192) return false;
+    const int64_t tiles256 = (int64_t)g.batch * ((g.M + BM - 1) / BM) * ((g.N + 255) / 256);
+    return tiles256 >= num_sms();
+}
+
+namespace {
+
+// ------------------------------------------------------------------ online tuning of the variant
+// The factor's FP32-accurate products have three implementations: the FP16 three-product kernel on
+// the tile width the heuristic above picks (V_F16), on the other width of {128, 256} (V_F16_ALT,
+// for N > 128), and the 3xTF32 kernel with the split done inside the kernel (V_TF32X3: no
+// pre-pass launch, half the MMA rate).  With tuning on (slab_autotune(1) or SLAB_AUTOTUNE=1), the
+// first calls of each shape class -- log2 buckets of M, N, K and the batch, plus the triangle,
+// transposition and shared-operand flags -- run every candidate TUNE_SAMPLES times, timed by an
+// event pair on the launching stream, and the class then keeps the candidate with the lowest
+// time per flop.  All candidates compute the same product to FP32-level accuracy (the last bits
+// differ), so exploring costs nothing but time.  Streams under capture are never timed: they take
+// the decided candidate, or V_F16 while a class is still undecided.
+enum TuneVariant { V_F16 = 0, V_F16_ALT = 1, V_TF32X3 = 2, NV = 3 };
+constexpr int TUNE_SAMPLES = 2;
+
+struct TuneStat {
+    double ms_per_gflop[NV] = {0, 0, 0};
+    int done[NV] = {0, 0, 0};         // timed samples harvested
+    int issued[NV] = {0, 0, 0};       // timed samples launched
+    int choice = -1;
+};
+struct TunePending {
+    uint64_t key;
+    int v;
+    double gflop;
+    cudaEvent_t e0, e1;
+};
+struct Tuner {
+    std::mutex mu;
+    std::atomic<int> mode{-1};
+    std::unordered_map<uint64_t, TuneStat> table;
+    std::vector<TunePending> pending;
+    std::vector<cudaEvent_t> spare;
+};
+Tuner& tuner() {
+    static Tuner t;
+    return t;
+}
+
+int tune_mode() {
+    Tuner& T = tuner();
+    int m = T.mode.load();
+    if (m < 0) {
+        const char* e = std::getenv("SLAB_AUTOTUNE");
+        int want = (e && *e && *e != '0') ? 1 : 0, expect = -1;
+        T.mode.compare_exchange_strong(expect, want);
+        m = T.mode.load();
+    }
+    return m;
+}
+
+int ceil_log2(int64_t x) {
+    int r = 0;
+    while ((int64_t(1) << r) < x) ++r;
+    return r;
+}
+uint64_t tune_key(const TcGemmArgs& g) {
+    return (uint64_t)ceil_log2(g.M) | (uint64_t)ceil_log2(g.N) << 6 | (uint64_t)ceil_log2(g.K) << 12 |
+           (uint64_t)ceil_log2(g.batch) << 18 | (uint64_t)(g.lower_only != 0) << 24 | (uint64_t)(g.transC != 0) << 25 |
+           (uint64_t)f16x3_shared(g) << 26;
+}
+bool tune_allowed(const TcGemmArgs& g, int v) { return v != V_F16_ALT || g.N > 128; }
+
+// Decide a class once every candidate has its samples: the lowest mean time per flop.
+void tune_decide(TuneStat& s, bool alt_ok) {
+    int best = -1;
+    for (int v = 0; v < NV; ++v) {
+        if (v == V_F16_ALT && !alt_ok) continue;
+        if (s.done[v] < TUNE_SAMPLES) return;
+        if (best < 0 || s.ms_per_gflop[v] / s.done[v] < s.ms_per_gflop[best] / s.done[best]) best = v;
+    }
+    s.choice = best;
+}
+
+// Fold finished timings into the table (caller holds the lock).
+void tune_harvest(Tuner& T) {
+    for (size_t i = 0; i < T.pending.size();) {
+        TunePending& p = T.pending[i];
+        const cudaError_t q = cudaEventQuery(p.e1);
+        if (q == cudaErrorNotReady) {
+            ++i;
+            continue;
+        }
+        float ms = 0.f;
+        if (q == cudaSuccess && cudaEventElapsedTime(&ms, p.e0, p.e1) == cudaSuccess && p.gflop > 0) {
+            TuneStat& s = T.table[p.key];
+            s.ms_per_gflop[p.v] += ms / p.gflop;
+            s.done[p.v] += 1;
+            const bool alt_ok = ((p.key >> 6) & 63) > 7;            // N > 128
+            if (s.choice < 0) tune_decide(s, alt_ok);
+        } else {
+            cudaGetLastError();
+        }
+        T.spare.push_back(p.e0);
+        T.spare.push_back(p.e1);
+        T.pending[i] = T.pending.back();
+        T.pending.pop_back();
+    }
+}
+
+cudaEvent_t tune_event(Tuner& T) {
+    if (!T.spare.empty()) {
+        cudaEvent_t e = T.spare.back();
+        T.spare.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+slab_status launch_variant(cudaStream_t st, TcGemmArgs& g, unsigned* err, int v) {
+    const bool narrow = g.N <= 64;
+    if (v == V_TF32X3) {
+        g.split = 1;
+        return narrow ? launch_tc<64, true>(st, g, err) : launch_tc<128, true>(st, g, err);
+    }
+    if (narrow) return launch_f16x3<64>(st, g, err);
+    const bool wide = f16x3_use_wide(g) != (v == V_F16_ALT && g.N > 128);
+    return wide ? launch_f16x3<256>(st, g, err) : launch_f16x3<128>(st, g, err);
+}
+
+}  // namespace
+
 // Host entry: validates the layout constraints of the TMA path and launches.
-slab_status tc_gemm(cudaStream_t st, const TcGemmArgs& g, unsigned* err) {
+slab_status tc_gemm(cudaStream_t st, TcGemmArgs& g, unsigned* err) {
     if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return SLAB_OK;
     if (g.K <= 0 || g.K % BK) return SLAB_EINVAL;
     if (g.ksplit > 1 && (g.K % (g.ksplit * BK) || !g.part || g.lower_only || g.split == 2)) return SLAB_EINVAL;
@@ -944,10 +1085,80 @@ slab_status tc_gemm(cudaStream_t st, const TcGemmArgs& g, unsigned* err) {
         if (g.K % BK16 || !g.w16 || g.w16_bytes < f16x3_work_bytes(g.M, g.N, g.K, g.batch, f16x3_shared(g)) ||
             ((uintptr_t)g.w16 & 255) || g.batch > 65535)
             return SLAB_EINVAL;
-        return narrow ? launch_f16x3<64>(st, g, err) : launch_f16x3<128>(st, g, err);
+        if (tune_mode() == 1) {
+            Tuner& T = tuner();
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            const bool capturing = cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone;
+            const uint64_t key = tune_key(g);
+            int v = V_F16;
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            {
+                std::lock_guard<std::mutex> lock(T.mu);
+                if (!capturing) tune_harvest(T);
+                TuneStat& s = T.table[key];
+                if (s.choice >= 0) {
+                    v = s.choice;
+                } else if (!capturing) {
+                    int best = -1;                      // the least-sampled candidate still short of samples
+                    for (int c = 0; c < NV; ++c)
+                        if (tune_allowed(g, c) && s.issued[c] < TUNE_SAMPLES && (best < 0 || s.issued[c] < s.issued[best]))
+                            best = c;
+                    if (best >= 0) {
+                        e0 = tune_event(T);
+                        e1 = e0 ? tune_event(T) : nullptr;
+                        if (e1) {
+                            v = best;
+                            s.issued[v] += 1;
+                        } else if (e0) {
+                            T.spare.push_back(e0);
+                            e0 = nullptr;
+                        }
+                    }
+                }
+            }
+            if (e0) cudaEventRecord(e0, st);
+            const slab_status r = launch_variant(st, g, err, v);
+            if (e0) {
+                cudaEventRecord(e1, st);
+                std::lock_guard<std::mutex> lock(T.mu);
+                T.pending.push_back(TunePending{key, v, 2e-9 * g.M * g.N * g.K * g.batch, e0, e1});
+            }
+            return r;
+        }
+        if (narrow) return launch_f16x3<64>(st, g, err);
+        return f16x3_use_wide(g) ? launch_f16x3<256>(st, g, err) : launch_f16x3<128>(st, g, err);
     }
     if (g.split) return narrow ? launch_tc<64, true>(st, g, err) : launch_tc<128, true>(st, g, err);
     return narrow ? launch_tc<64, false>(st, g, err) : launch_tc<128, false>(st, g, err);
+}
+
+extern "C" int slab_autotune(int mode) {
+    Tuner& T = tuner();
+    const int prev = tune_mode();
+    if (mode == 0 || mode == 1) T.mode.store(mode);
+    if (mode == 2) {                                   // forget every decision
+        std::lock_guard<std::mutex> lock(T.mu);
+        T.table.clear();
+    }
+    return prev;
+}
+
+extern "C" slab_status slab_autotune_stats(int* classes, int* decided, int* tf32x3, int* alt_width) {
+    Tuner& T = tuner();
+    std::lock_guard<std::mutex> lock(T.mu);
+    tune_harvest(T);
+    int c = 0, d = 0, t = 0, a = 0;
+    for (auto& kv : T.table) {
+        ++c;
+        if (kv.second.choice >= 0) ++d;
+        if (kv.second.choice == V_TF32X3) ++t;
+        if (kv.second.choice == V_F16_ALT) ++a;
+    }
+    if (classes) *classes = c;
+    if (decided) *decided = d;
+    if (tf32x3) *tf32x3 = t;
+    if (alt_width) *alt_width = a;
+    return SLAB_OK;
 }
 
 size_t f16x3_work_bytes(int64_t M, int64_t N, int64_t K, int batch, bool shared) {

@@ -112,6 +112,11 @@ class SlabSolver:
     def device_bytes(self) -> int:
         return int(self.lib.slab_device_bytes(self.h))
 
+    @property
+    def stage2_order(self) -> str:
+        """"sweep" or "oddeven": the Stage-2 elimination order the factor used."""
+        return {1: "sweep", 2: "oddeven"}.get(int(self.lib.slab_stage2_order(self.h)), "?")
+
     # ------------------------------------------------------------------ API
     def solve(self, f, u: Optional[torch.Tensor] = None, allow_noconv: bool = False
               ) -> Tuple[torch.Tensor, np.ndarray, int]:
@@ -292,6 +297,102 @@ class SlabBatch:
                     self.lib.slab_destroy(h[i])
                     h[i] = None
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _DeviceArray:
+    """A raw device buffer of the library, presented to torch through __cuda_array_interface__
+    (zero-copy: torch.as_tensor aliases it)."""
+
+    def __init__(self, ptr: int, shape):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": "<f8", "data": (int(ptr), False),
+                                         "version": 3, "strides": None}
+
+
+class GraphBatch:
+    """Independent 2-D diffusion problems with the least-squares objective L_i = ||u_i - t_i||^2,
+    run as CUDA graphs (slab_batch_create / slab_batch_run / slab_batch_results).
+
+    Every run computes, per problem, the factor, u_i = A_i^-1 f_i (one solve pass and `steps`
+    refinement passes), L_i, lambda_i = A_i^-T dL_i/du_i and grad_i = dL_i/dkappa_i.  All device
+    memory is allocated once at construction; the per-problem inputs (kappa, f, target) and outputs
+    (u, lam, grad) are tensors aliasing the batch's own buffers (``inputs(i)`` / ``outputs(i)``).
+    sizes: grid sizes n_i; b: interface spacing (int or one per problem); wave: problems per graph
+    (0: all in one); branches: parallel graph branches per wave.
+    """
+
+    def __init__(self, sizes, b=16, precision: str = "fp32", rtol: float = 1e-10, steps: int = 4,
+                 wave: int = 0, branches: int = 16, stage2: str = "auto"):
+        self.lib = _lib.load()
+        self.sizes = [int(n) for n in sizes]
+        cnt = len(self.sizes)
+        bs = [int(b)] * cnt if np.isscalar(b) else [int(x) for x in b]
+        opts = _lib.SlabOpts()
+        self.lib.slab_default_opts(ctypes.byref(opts))
+        opts.factor_prec = _PREC[precision]
+        opts.rtol = float(rtol)
+        opts.stage2 = _STAGE2[stage2]
+        self.h = ctypes.c_void_p()
+        narr = (ctypes.c_int * cnt)(*self.sizes)
+        barr = (ctypes.c_int * cnt)(*bs)
+        torch.cuda.synchronize()
+        _lib.check(self.lib.slab_batch_create(cnt, narr, barr, ctypes.byref(opts), int(steps), int(wave),
+                                              int(branches), ctypes.byref(self.h)), "slab_batch_create")
+        self.count = cnt
+        self._bufs = []
+        for i, n in enumerate(self.sizes):
+            ptrs = [ctypes.c_void_p() for _ in range(6)]
+            _lib.check(self.lib.slab_batch_buffers(self.h, i, *[ctypes.byref(p) for p in ptrs]), "slab_batch_buffers")
+            shapes = [(n + 1, n + 1), (1, (n - 1) ** 2), (1, (n - 1) ** 2), (1, (n - 1) ** 2), (1, (n - 1) ** 2),
+                      (n + 1, n + 1)]
+            t = [torch.as_tensor(_DeviceArray(p.value, sh), device="cuda") for p, sh in zip(ptrs, shapes)]
+            self._bufs.append(dict(zip(("kappa", "f", "target", "u", "lam", "grad"), t)))
+
+    @property
+    def device_bytes(self) -> int:
+        return int(self.lib.slab_batch_device_bytes(self.h))
+
+    def inputs(self, i: int):
+        """(kappa, f, target) of problem i: tensors aliasing the batch's input buffers."""
+        d = self._bufs[i]
+        return d["kappa"], d["f"], d["target"]
+
+    def outputs(self, i: int):
+        """(u, lam, grad) of problem i after a run: tensors aliasing the batch's output buffers."""
+        d = self._bufs[i]
+        return d["u"], d["lam"], d["grad"]
+
+    def set_inputs(self, i: int, kappa, f, target):
+        k, ff, t = self.inputs(i)
+        k.copy_(torch.as_tensor(kappa, dtype=torch.float64).reshape(k.shape), non_blocking=True)
+        ff.copy_(torch.as_tensor(f, dtype=torch.float64).reshape(ff.shape), non_blocking=True)
+        t.copy_(torch.as_tensor(target, dtype=torch.float64).reshape(t.shape), non_blocking=True)
+
+    def run(self, stream: Optional[torch.cuda.Stream] = None):
+        """Enqueue one run (one graph launch per wave) on `stream` (default: the current stream)."""
+        s = stream if stream is not None else torch.cuda.current_stream()
+        _lib.check(self.lib.slab_batch_run(self.h, ctypes.c_void_p(s.cuda_stream)), "slab_batch_run")
+
+    def results(self, allow_noconv: bool = False):
+        """Wait for the last run: (losses, relres of u, relres of lambda) as numpy arrays."""
+        L = np.zeros(self.count)
+        ru = np.zeros(self.count)
+        rl = np.zeros(self.count)
+        st = self.lib.slab_batch_results(self.h, L.ctypes.data_as(ctypes.c_void_p), ru.ctypes.data_as(ctypes.c_void_p),
+                                         rl.ctypes.data_as(ctypes.c_void_p))
+        _lib.check(st, "slab_batch_results", allow=(_lib.SLAB_ENOCONV,) if allow_noconv else ())
+        return L, ru, rl
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self._bufs = []
+            self.lib.slab_batch_destroy(self.h)
+            self.h = ctypes.c_void_p()
 
     def __del__(self):
         try:

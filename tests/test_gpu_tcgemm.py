@@ -64,6 +64,14 @@ def test_tc_gemm_f16x3_is_fp32_accurate(M, N, K):
     assert rel < max(16 * rel32, 1e-6), (rel, rel32)
 
 
+@pytest.mark.parametrize("M,N,K,trans_c", [(2600, 4000, 192, 0), (2600, 4000, 128, 1), (1200, 8200, 64, 0)])
+def test_tc_gemm_f16x3_wide_tiles(M, N, K, trans_c):
+    """Wide products (enough 128 x 256 tiles for every SM) run on the 128 x 256 tile; ragged M and
+    N cover partial tiles in both directions."""
+    rel, rel32 = _run(M, N, K, -1.0, 1.0, split=2, trans_c=trans_c)
+    assert rel < max(16 * rel32, 1e-6), (rel, rel32)
+
+
 def test_tc_gemm_f16x3_transposed_output():
     rel, rel32 = _run(200, 64, 128, 0.5, 2.0, split=2, trans_c=1)
     assert rel < max(16 * rel32, 1e-6), (rel, rel32)
@@ -172,3 +180,38 @@ def test_fp64_tc_gemm_is_fp64_accurate(M, N, K):
     scale = 0.75 * np.abs(A) @ np.abs(B).T + np.abs(C0)
     rel = (np.abs(Cd.cpu().numpy() - ref) / scale).max()
     assert rel <= 1e-13, rel
+
+
+def test_autotuner_decides_and_keeps_results():
+    """Online tuning of the factor products: repeated factors of one problem let every shape class
+    try each candidate and decide; the refined solutions match the untuned ones to the refinement
+    tolerance, and mode 0 restores the fixed heuristic."""
+    import ctypes as C
+
+    from paper_2211_07572_gb300 import _lib, inputs
+    from paper_2211_07572_gb300.solver import SlabSolver
+    lib = _lib.load()
+    p = inputs.diffusion(512, 16, k=2, n_modes=8, field_seed=31, rhs_seed=32)
+    f = torch.from_numpy(p.f).cuda()
+
+    def solve():
+        s = SlabSolver(2, p.n, p.b, inputs.DIFFUSION, kappa=p.kappa, precision="fp32", rtol=1e-12, max_refine=40)
+        u, rel, _ = s.solve(f)
+        s.close()
+        return u, rel
+
+    prev = lib.slab_autotune(0)
+    u0, _ = solve()
+    lib.slab_autotune(2)                           # forget earlier decisions
+    lib.slab_autotune(1)
+    try:
+        for _ in range(6):
+            u1, rel = solve()
+            assert rel.max() <= 1e-12
+            assert float((u1 - u0).abs().max()) <= 1e-9 * float(u0.abs().max())
+        torch.cuda.synchronize()
+        c, d, t, a = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        assert lib.slab_autotune_stats(C.byref(c), C.byref(d), C.byref(t), C.byref(a)) == 0
+        assert c.value > 0 and d.value > 0, (c.value, d.value)
+    finally:
+        lib.slab_autotune(prev if prev in (0, 1) else 0)
