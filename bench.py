@@ -298,11 +298,17 @@ def work_model(n, b, k, passes, stage2="sweep", kind="diffusion"):
     else:
         W["schur_update"] = (NI - 1) * sp * sp * (sp + 1.0)
         W["sweep_products"] = passes * (4 * NI - 2) * 2.0 * sp * sp * k
-    # tree passes: algorithmic HBM bytes per node (factor blocks once, vectors once, FP64 f read / u update)
-    W["tree_up"] = passes * NS * sum(4 * 3 * m * m + 8 * m * k + (8 * m * k if kk > 0 else 0) + 4 * 2 * w * m
-                                     + 16 * w * k + 4 * m * k + 8 * m * k for (_, kk, w) in nodes)
-    W["tree_down"] = passes * NS * sum(4 * 3 * m * m + 4 * m * k + 8 * m * k + 8 * w * m + 8 * w * k + 4 * m * k
-                                       + 16 * m * k for (_, _, w) in nodes)
+    # tree passes: compulsory HBM bytes only (a lower bound of the traffic): per node the FP32 factor
+    # blocks L^-1 and Z_tb (3 m^2) and the interface columns Z_I (2 w m) once; per pass the up pass reads
+    # the FP64 load of the slab interiors and writes y (m k FP32 per node), the down pass reads y and
+    # writes the FP64 solution of the slab interiors -- and reads it too in the refinement passes, which
+    # accumulate.  Intermediate condensed vectors and the interface values are left out (they may stay
+    # in L2).
+    nn = NS * len(nodes)
+    fac = NS * sum(4 * 3 * m * m + 4 * 2 * w * m for (_, _, w) in nodes)
+    uint = 8.0 * NS * s * m * k                                          # FP64 interior vector, one pass
+    W["tree_up"] = passes * (fac + uint + 4.0 * nn * m * k)
+    W["tree_down"] = passes * (fac + 4.0 * nn * m * k + uint) + (passes - 1) * uint
     W["stencil"] = passes * 24.0 * s * s * k                            # bytes: read u, f; write r (FP64)
     return W
 
@@ -315,12 +321,15 @@ BOUND = {"tree_factor": "alu", "assemble_T": "hbm", "panel": "alu", "trailing": 
 BOUND3 = dict(BOUND, assemble_T="tensor", tree_up="tensor", tree_down="tensor", slab_panel="alu",
               slab_trailing="tensor", slab_schur="tensor")
 
-# DRAM bytes per launch from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum), for the
-# default workload only: the n = 1024, b = 32, k = 64 case (all heights of one pass) scaled by the
-# node count (4x at n = 2048, same b, m, k) over the 11 launches of a pass at n = 2048.
+# Measured DRAM bytes per pass (dram__bytes_read.sum + dram__bytes_write.sum summed over the 11
+# height launches of one pass; one ncu capture of the 2-D diffusion workload, n = 2048, b = 32, k = 64,
+# NVTX range profiled_step): the down pass moves more in the refinement passes, which read the FP64
+# solution they accumulate into.  Other n at the same b and k scale with the node count, (n / 2048)^2.
 TRAFFIC = {
-    "tree_down": {"bytes": 1.560e9 * 4 / 11, "from": "ncu at n=1024 (10 launches, 1.560 GB/pass) x4 nodes / 11"},
-    "tree_up": {"bytes": 2.340e9 * 4 / 11, "from": "ncu at n=1024 (10 launches, 2.340 GB/pass) x4 nodes / 11"},
+    "tree_down": {"first": 6.997e9, "refine": 8.872e9, "n": 2048, "launches": 11,
+                  "from": "ncu, n=2048: 6.997 GB first pass, 8.872 GB refinement pass, 11 launches each"},
+    "tree_up": {"first": 10.246e9, "refine": 10.242e9, "n": 2048, "launches": 11,
+                "from": "ncu, n=2048: 10.246 GB first pass, 10.242 GB refinement pass, 11 launches each"},
 }
 # How each tensor-core class multiplies (set per run in run_gpu): "f16x3" three FP16 MMAs of
 # row-scaled hi/lo splits per algorithmic FP32 flop (the FP32 factor's Schur and trailing
@@ -429,9 +438,16 @@ def run_gpu(args):
 
     orders = []
     if args.once:
+        # warm-up steps first (the tuner decides during them), then the step a profiler looks at, inside
+        # the NVTX range "profiled_step" (ncu --nvtx --nvtx-include "profiled_step/")
+        for _ in range(args.once_warmup):
+            step(f, u)
+        torch.cuda.synchronize()
         cnt = []
+        torch.cuda.nvtx.range_push("profiled_step")
         rel, it = step(f, u, cnt, orders)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         W["stage2"] = orders[0]
         if rank == 0:
             print(json.dumps({"once": True, "config": W, "max_relres": float(np.max(rel)), "refine_steps": it,
@@ -526,9 +542,16 @@ def run_gpu(args):
     bmap = BOUND3 if dim == 3 else BOUND
     dom = max((c for c in cls_ms if c in bmap and work.get(c, 0) > 0), key=lambda c: cls_ms[c])
     roof = roofline_for(dom, cls_ms[dom], cls_cnt[dom], work, peaks, clocks, bmap)
-    if W["kind"] == "diffusion" and (n, b, k) == (2048, 32, 64) and dom in TRAFFIC and prec == "fp32":
-        roof["traffic"] = TRAFFIC[dom]["bytes"]
-        roof["traffic_source"] = TRAFFIC[dom]["from"]
+    if W["kind"] == "diffusion" and (b, k) == (32, 64) and dom in TRAFFIC and prec == "fp32":
+        tr = TRAFFIC[dom]
+        scale = (n / tr["n"]) ** 2                                      # nodes of the tree at fixed b
+        per_pass = (tr["first"] + (passes - 1) * tr["refine"]) / passes * scale
+        roof["traffic"] = per_pass / tr["launches"]
+        roof["traffic_source"] = (tr["from"] + f"; mean over {passes} passes" +
+                                  (f", x{scale:.2f} nodes at n={n}" if n != tr["n"] else "") +
+                                  f", per tree launch ({tr['launches']} a pass)")
+        roof["traffic_achieved"] = per_pass * passes / (cls_ms[dom] * 1e-3) / 1e9
+        roof["traffic_frac"] = roof["traffic_achieved"] / roof["peak"]
     dense_cls = ("trailing", "schur_update", "sweep_products") + (
         ("assemble_T", "tree_up", "tree_down", "slab_trailing", "slab_schur") if dim == 3 else ())
     dense = {c: roofline_for(c, cls_ms[c], cls_cnt[c], work, peaks, clocks, bmap)
@@ -925,7 +948,9 @@ def main():
     ap.add_argument("--ref-n", type=int, default=32, help="reference arm: oracle sample size (3-D)")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-fp64", dest="fp64_comparator", action="store_false")
-    ap.add_argument("--once", action="store_true", help="run one step only (for profilers)")
+    ap.add_argument("--once", action="store_true",
+                    help="warm-up steps, then one step in the NVTX range profiled_step (for profilers)")
+    ap.add_argument("--once-warmup", type=int, default=3, help="--once: warm-up steps before the profiled one")
     ap.add_argument("--count", type=int, default=0, help="adjoint256: number of problems (0: all 256)")
     ap.add_argument("--wave", type=int, default=64, help="adjoint256: problems per wave (graph: per graph)")
     ap.add_argument("--no-graph", dest="graph", action="store_false",

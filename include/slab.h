@@ -224,6 +224,18 @@ slab_status slab_interior_solve(slab_handle* h, const double* f, const double* u
                                 int k);
 
 /*
+ * Y = T X without forming T, the operation the randomized recovery of T in Sec. 3.3 is built on
+ * (T is only ever applied to a sketch matrix there).  With the interface values u_I = X, the slab
+ * interiors u_J = -A_JJ^-1 A_JI X come from one interior solve with zero load (eq. usol_even, the
+ * stored Stage-1 factors), and T X = A_II X + A_IJ u_J = (A u)_I is read off the stencil rows of the
+ * interface nodes.  X, Y: device, k interface vectors ([k][N_I (n-1)^(d-1)], the interface layout
+ * above); work: device scratch of 2 k (n-1)^d doubles owned by the caller.  Accuracy: that of the
+ * Stage-1 factor (FP32 or FP64).  SLAB_EINVAL for a null handle or pointer, k < 0.  Asynchronous on
+ * the handle's stream.
+ */
+slab_status slab_apply_T(slab_handle* h, const double* X, double* Y, int k, double* work);
+
+/*
  * Copy one (n-1)^(d-1) square block of the reduced matrix T (as assembled,
  * before Stage 2) to out (HOST, row-major, FP64): which = 0 gives T_qq, which
  * = 1 gives T_{q,q+1} (q = 0..N_I-2).  Synchronises the stream.

@@ -55,6 +55,7 @@ SIGNATURES = {
     "slab_interface_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_int]),
     "slab_interior_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int]),
     "slab_get_T_block": (c_int, [c_void_p, c_int, c_int, c_void_p]),
+    "slab_apply_T": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
     "slab_sizes": (c_int, [c_void_p, ctypes.POINTER(c_int64), ctypes.POINTER(c_int64), ctypes.POINTER(c_int)]),
     "slab_device_bytes": (c_int64, [c_void_p]),
     "slab_stage2_order": (c_int, [c_void_p]),

@@ -616,10 +616,10 @@ slab_status factor_create(const slab_grid* grid, const slab_coeffs* co, int b, c
     if (!h->stage2) ALLOC(h->Y, (d.NI - 1) * blk * R2);
     ALLOC(h->dstatus, sizeof(unsigned));
     {
-        // panel inverses of the tall Cholesky: one 64 x 64 block per matrix of its largest batch
+        // panel inverses of the tall Cholesky: two 64 x 64 blocks per matrix of its largest batch
         int pb = h->stage2 ? cr_max_batch(d.NI) : 1;
         if (grid->dim == 3) pb = std::max(pb, d.NS * tree_nodes_at(d.s, 0));
-        h->pnl_bytes = (size_t)std::min(pb, 65535) * SLAB_TILE * SLAB_TILE * std::max(R, R2);
+        h->pnl_bytes = 2 * (size_t)std::min(pb, 65535) * SLAB_TILE * SLAB_TILE * std::max(R, R2);
         ALLOC(h->pnl, h->pnl_bytes);
     }
 #undef ALLOC
@@ -978,6 +978,20 @@ slab_status slab_interior_solve(slab_handle* h, const double* f, const double* u
         }
     }
     return SLAB_OK;
+}
+
+slab_status slab_apply_T(slab_handle* h, const double* X, double* Y, int k, double* work) {
+    if (!h || k < 0) return SLAB_EINVAL;
+    if (k == 0) return SLAB_OK;
+    if (!X || !Y || !work) return SLAB_EINVAL;
+    // u_I = X and u_J = -A_JJ^-1 A_JI X (interior solve with zero load), then (A u)_I = T X
+    const int64_t N = h->td.N;
+    double* f0 = work;
+    double* u = work + (int64_t)k * N;
+    SLAB_CK(h, cudaMemsetAsync(f0, 0, (size_t)k * N * sizeof(double), h->stream));
+    TRY(slab_interior_solve(h, f0, X, u, k));
+    TRY(launch_apply(h, u, f0, k));
+    return launch_gather_interface(h, f0, Y, k);
 }
 
 slab_status slab_get_T_block(slab_handle* h, int which, int q, double* out) {

@@ -346,6 +346,105 @@ __global__ void __launch_bounds__(256) panel_apply_kernel(T* Wt, int64_t ld, int
         for (int b = 0; b < 4; ++b) src[(int64_t)(ty + 16 * a) * ld + tx + 16 * b] = acc[a][b];
 }
 
+// acc[a][b] += sum_l X[ty + 16 a][l] Y[tx + 16 b][l] for 64 x 64 tiles X, Y in shared memory (stride TLP).
+template <typename T>
+__device__ __forceinline__ void tile_nt(const T* X, const T* Y, T acc[4][4], int ty, int tx) {
+    for (int l = 0; l < TL; ++l) {
+        T av[4], bv[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) av[a] = X[(ty + 16 * a) * TLP + l];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) bv[b] = Y[(tx + 16 * b) * TLP + l];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
+    }
+}
+
+// Two panels kb, kb+1 of the tall Cholesky in one launch after panel_diag_kernel(kb): CTA x owns
+// row tile r = kb+1+x and
+//   scales its tile of panel kb, P_r = W[r][kb] L^{-T} (written back, except for r = kb+1),
+//   recomputes P_{kb+1} = W[kb+1][kb] L^{-T} from the unscaled tile (every CTA reads it; its scaled
+//   value is used only here, so it is never written),
+//   applies panel kb to panel kb+1: W[r][kb+1] -= P_r P_{kb+1}^T,
+// and the CTA of r = kb+1 then factors the updated diagonal tile of panel kb+1 (Cholesky and
+// inverse, as panel_diag_kernel) into Lw2.  Panel kb+1 is finished by panel_apply_kernel(kb+1, Lw2).
+template <typename T>
+__global__ void __launch_bounds__(256) panel_pair_kernel(T* Wt, int64_t ld, int kb, int64_t bstride, const T* Lw,
+                                                         T* Lw2, unsigned* status) {
+    extern __shared__ unsigned char smem_raw[];
+    T* Li = reinterpret_cast<T*>(smem_raw);
+    T* X = Li + TL * TLP;
+    T* Y = X + TL * TLP;
+    T* C = Y + TL * TLP;
+    const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
+    const int r = kb + 1 + blockIdx.x;
+    Wt += (int64_t)blockIdx.y * bstride;
+    T* src = Wt + (int64_t)r * TL * ld + (int64_t)kb * TL;
+    const T* src1 = Wt + (int64_t)(kb + 1) * TL * ld + (int64_t)kb * TL;
+    T* dst = Wt + (int64_t)r * TL * ld + (int64_t)(kb + 1) * TL;
+    const T* lin = Lw + (int64_t)blockIdx.y * TL * TL;
+    for (int i = tid; i < TL * TL; i += 256) {
+        const int a = i / TL, b = i % TL;
+        Li[a * TLP + b] = lin[i];
+        X[a * TLP + b] = src[(int64_t)a * ld + b];
+        Y[a * TLP + b] = src1[(int64_t)a * ld + b];
+        C[a * TLP + b] = dst[(int64_t)a * ld + b];
+    }
+    __syncthreads();
+    T p[4][4], q[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) p[a][b] = q[a][b] = T(0);
+    tile_nt<T>(X, Li, p, ty, tx);                  // P_r
+    tile_nt<T>(Y, Li, q, ty, tx);                  // P_{kb+1}
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            X[(ty + 16 * a) * TLP + tx + 16 * b] = p[a][b];
+            Y[(ty + 16 * a) * TLP + tx + 16 * b] = q[a][b];
+            if (r != kb + 1) src[(int64_t)(ty + 16 * a) * ld + tx + 16 * b] = p[a][b];
+        }
+    __syncthreads();
+    T u[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) u[a][b] = C[(ty + 16 * a) * TLP + tx + 16 * b];
+    {
+        T pq[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) pq[a][b] = T(0);
+        tile_nt<T>(X, Y, pq, ty, tx);              // P_r P_{kb+1}^T
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) u[a][b] -= pq[a][b];
+    }
+    if (r != kb + 1) {
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) dst[(int64_t)(ty + 16 * a) * ld + tx + 16 * b] = u[a][b];
+        return;
+    }
+    __syncthreads();                               // (uniform: this CTA alone) all reads of C done
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) C[(ty + 16 * a) * TLP + tx + 16 * b] = u[a][b];
+    __syncthreads();
+    chol_inv_tile<T>(C, X, status);                // X := L^{-1} of panel kb+1's diagonal tile
+    T* out = Lw2 + (int64_t)blockIdx.y * TL * TL;
+    for (int i = tid; i < TL * TL; i += 256) out[i] = X[(i / TL) * TLP + i % TL];
+}
+
 template <typename T>
 __global__ void set_identity_kernel(T* B, int s_pad) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -400,6 +499,105 @@ inline bool use_f16x3(slab_handle* h, int cls, TcGemmArgs& g) {
     return true;
 }
 
+// FP32 C = beta C + alpha A B^T for N <= NB right-hand sides (the single-load solves' products): the product
+// streams A once.  A block owns 32 rows (a warp four of them); per 128-wide K chunk the block stages
+// the N x 128 slice of B in shared memory once (so B is read once per block, not once per warp), and
+// every lane multiplies its float4 of the four rows with it, the next chunk of A already loaded
+// into registers.  Exact FP32 FMAs; one warp reduction per output at the end.  blockIdx.y is the
+// batch index (sA, sB, sC element strides).  Needs K, lda and ldb multiples of 4 and 16-byte
+// aligned A and B.
+constexpr int SK_ROWS = 32;                          // rows per block (four per warp)
+template <int NB>
+__global__ void __launch_bounds__(256, 2) skinny_nt_kernel(int M, int N, int K, float alpha, const float* __restrict__ A,
+                                                           int64_t lda, int64_t sA, const float* __restrict__ B,
+                                                           int64_t ldb, int64_t sB, float beta, float* C, int64_t ldc,
+                                                           int64_t sC, int transC) {
+    __shared__ float4 bs[NB][32];                     // B[n][k0 .. k0 + 127]
+    __shared__ float red[8][4 * NB];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row0 = (blockIdx.x * 8 + warp) * 4;
+    A += (int64_t)blockIdx.y * sA;
+    B += (int64_t)blockIdx.y * sB;
+    C += (int64_t)blockIdx.y * sC;
+    float acc[4][NB];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int n = 0; n < NB; ++n) acc[r][n] = 0.f;
+    const float* ar[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) ar[r] = A + (int64_t)min(row0 + r, M - 1) * lda;
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 a[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+        a[r] = (4 * lane < K) ? __ldg(reinterpret_cast<const float4*>(ar[r] + 4 * lane)) : zero;
+    for (int k0 = 0; k0 < K; k0 += 128) {
+        __syncthreads();                              // the previous chunk of bs is consumed
+        for (int e = threadIdx.x; e < NB * 32; e += 256) {
+            const int n = e >> 5, kk = k0 + 4 * (e & 31);
+            bs[n][e & 31] = (n < N && kk < K) ? __ldg(reinterpret_cast<const float4*>(B + (int64_t)n * ldb + kk)) : zero;
+        }
+        __syncthreads();
+        float4 an[4];                                 // next chunk of A
+        const int kn = k0 + 128 + 4 * lane;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) an[r] = (kn < K) ? __ldg(reinterpret_cast<const float4*>(ar[r] + kn)) : zero;
+#pragma unroll
+        for (int n = 0; n < NB; ++n) {
+            const float4 b = bs[n][lane];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+                acc[r][n] = fmaf(a[r].x, b.x, fmaf(a[r].y, b.y, fmaf(a[r].z, b.z, fmaf(a[r].w, b.w, acc[r][n]))));
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) a[r] = an[r];
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int n = 0; n < NB; ++n) {
+            float v = acc[r][n];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) red[warp][r * NB + n] = v;
+        }
+    __syncwarp();
+    // lane j writes output j, j + 32, ... of the warp's 4 x N block
+    for (int e = lane; e < 4 * N; e += 32) {
+        const int r = e / N, n = e % N, row = row0 + r;
+        if (row < M) {
+            float* c = transC ? C + (int64_t)n * ldc + row : C + (int64_t)row * ldc + n;
+            *c = (beta == 0.f ? 0.f : beta * *c) + alpha * red[warp][r * NB + n];
+        }
+    }
+}
+
+// The skinny kernel serves a product when N is small and the layout allows 16-byte loads.
+inline bool skinny_ok(int N, int K, const float* A, int64_t lda, int64_t sA, const float* B, int64_t ldb,
+                      int64_t sB, int lower_only) {
+    // N <= 4 (single loads, as in the batched problems): the tensor-core path would pad N to 64.  From
+    // 5 to 16 loads the 3xTF32 tensor-core kernel streams A at least as fast (measured on GB300).
+    return N >= 1 && N <= 4 && !lower_only && K % 4 == 0 && lda % 4 == 0 && ldb % 4 == 0 && sA % 4 == 0 &&
+           sB % 4 == 0 && ((uintptr_t)A & 15) == 0 && ((uintptr_t)B & 15) == 0;
+}
+
+slab_status launch_skinny(slab_handle* h, int M, int N, int K, float alpha, const float* A, int64_t lda, int64_t sA,
+                          const float* B, int64_t ldb, int64_t sB, float beta, float* C, int64_t ldc, int64_t sC,
+                          int transC, int batch) {
+    for (int b0 = 0; b0 < batch; b0 += 65535) {
+        const int nb = std::min(65535, batch - b0);
+        dim3 grid((unsigned)((M + SK_ROWS - 1) / SK_ROWS), (unsigned)nb);
+        const float* Ab = A + (int64_t)b0 * sA;
+        const float* Bb = B + (int64_t)b0 * sB;
+        float* Cb = C + (int64_t)b0 * sC;
+        skinny_nt_kernel<4><<<grid, 256, 0, h->stream>>>(M, N, K, alpha, Ab, lda, sA, Bb, ldb, sB, beta, Cb, ldc, sC,
+                                                         transC);
+        SLAB_CK_LAUNCH(h);
+    }
+    return SLAB_OK;
+}
+
 // C = beta C + alpha A B^T on the unit of this precision: tensor cores for FP32, SIMT for FP64.
 template <typename T>
 slab_status gemm_tn(slab_handle* h, int cls, int M, int N, int K, T alpha, const T* A, int64_t lda, const T* B,
@@ -410,6 +608,8 @@ slab_status gemm_tn<float>(slab_handle* h, int cls, int M, int N, int K, float a
                            const float* B, int64_t ldb, float beta, float* C, int64_t ldc, int transC,
                            int lower_only) {
     SLAB_PROF(h, cls);
+    if (skinny_ok(N, K, A, lda, 0, B, ldb, 0, lower_only))
+        return launch_skinny(h, M, N, K, alpha, A, lda, 0, B, ldb, 0, beta, C, ldc, 0, transC, 1);
     TcGemmArgs g;
     g.M = M; g.N = N; g.K = K; g.alpha = alpha; g.beta = beta;
     g.A = A; g.lda = lda; g.B = B; g.ldb = ldb; g.C = C; g.ldc = ldc;
@@ -882,6 +1082,8 @@ slab_status gemm_tn_batched<float>(slab_handle* h, int cls, int M, int N, int K,
         }
     }
     SLAB_PROF(h, cls);
+    if (skinny_ok(N, K, A, lda, sA, B, ldb, sB, lower_only))
+        return launch_skinny(h, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, transC, batch);
     TcGemmArgs g;
     g.M = M; g.N = N; g.K = K; g.alpha = alpha; g.beta = beta;
     g.A = A; g.lda = lda; g.B = B; g.ldb = ldb; g.C = C; g.ldc = ldc;
@@ -1507,11 +1709,45 @@ slab_status tall_panel(slab_handle* h, T* W, int ncols, int ident0, int kb, int 
     return SLAB_OK;
 }
 
+// Panels kb and kb+1 (kb+1 < ncols / 64), all updates from the columns left of kb applied: three
+// launches -- panel_diag_kernel(kb), panel_pair_kernel(kb) (panel kb scaled, its update of panel
+// kb+1, panel kb+1's diagonal factored), panel_apply_kernel(kb+1) -- instead of a panel, a product
+// and a panel.
+template <typename T>
+slab_status tall_pair(slab_handle* h, T* W, int ncols, int ident0, int kb, int batch, int64_t bstride, size_t smem) {
+    const int nrt0 = (ident0 + (kb + 1) * TL) / TL - kb - 1;      // row tiles below the diagonal, panel kb
+    const int nrt1 = (ident0 + (kb + 2) * TL) / TL - kb - 2;      // and panel kb+1
+    const size_t psmem = 4 * TL * TLP * sizeof(T);
+    T* Lw = (T*)h->pnl;
+    for (int b0 = 0; b0 < batch; b0 += 65535) {
+        const int nb = std::min(65535, batch - b0);
+        T* Lw2 = Lw + (int64_t)nb * TL * TL;
+        SLAB_PROF(h, KC_PANEL);
+        panel_diag_kernel<T><<<dim3(1, nb), 256, smem, h->stream>>>(W + b0 * bstride, ncols, kb, h->dstatus, bstride,
+                                                                     Lw);
+        SLAB_CK_LAUNCH(h);
+        panel_pair_kernel<T><<<dim3(nrt0, nb), 256, psmem, h->stream>>>(W + b0 * bstride, ncols, kb, bstride, Lw, Lw2,
+                                                                       h->dstatus);
+        SLAB_CK_LAUNCH(h);
+        if (nrt1 > 0) {
+            panel_apply_kernel<T><<<dim3(nrt1, nb), 256, smem, h->stream>>>(W + b0 * bstride, ncols, kb + 1, bstride,
+                                                                           Lw2);
+            SLAB_CK_LAUNCH(h);
+        }
+        prof_extra(h, KC_PANEL, nrt1 > 0 ? 2 : 1);
+    }
+    return SLAB_OK;
+}
+
 // Panels [kb0, kb1), all updates from the columns left of kb0 already applied.
 template <typename T>
 slab_status tall_chol_range(slab_handle* h, T* W, int ncols, int ident0, int kb0, int kb1, int batch,
                             int64_t bstride, size_t smem) {
     if (kb1 - kb0 == 1) return tall_panel<T>(h, W, ncols, ident0, kb0, batch, bstride, smem);
+    // the fused pair saves launches on the latency-bound critical path of small batches; large batches
+    // fill the GPU anyway, and there its redundant tile products cost more than the launches it saves
+    const int64_t tiles = (int64_t)batch * ((ident0 + (kb0 + 1) * TL) / TL - kb0 - 1);
+    if (kb1 - kb0 == 2 && tiles <= 8 * 152) return tall_pair<T>(h, W, ncols, ident0, kb0, batch, bstride, smem);
     const int kbm = kb0 + (kb1 - kb0) / 2;
     slab_status st;
     if ((st = tall_chol_range<T>(h, W, ncols, ident0, kb0, kbm, batch, bstride, smem))) return st;
@@ -1527,9 +1763,11 @@ slab_status dense_tall_cholesky(slab_handle* h, T* W, int ncols, int ident0, int
     const size_t smem = 2 * TL * TLP * sizeof(T);
     SLAB_CK(h, cudaFuncSetAttribute(panel_diag_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     SLAB_CK(h, cudaFuncSetAttribute(panel_apply_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SLAB_CK(h, cudaFuncSetAttribute(panel_pair_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)(4 * TL * TLP * sizeof(T))));
     const int bchunk = std::min(batch, 65535);
     slab_status st;
-    if ((st = ensure_panel_work(h, (size_t)bchunk * TL * TL * sizeof(T)))) return st;
+    if ((st = ensure_panel_work(h, 2 * (size_t)bchunk * TL * TL * sizeof(T)))) return st;   // L^-1 of two panels
     const int nt = ncols / TL;
     if (nt <= 0) return SLAB_OK;
     return tall_chol_range<T>(h, W, ncols, ident0, 0, nt, batch, bstride, smem);

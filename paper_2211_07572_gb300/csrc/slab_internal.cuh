@@ -230,6 +230,8 @@ slab_status launch_residual(slab_handle* h, const double* u, const double* f, do
 slab_status launch_apply(slab_handle* h, const double* x, double* y, int k);
 slab_status launch_boundary_lift(slab_handle* h, const double* g, const double* f, double* fo, int k);
 slab_status launch_kappa_gradient(slab_handle* h, const double* u, const double* lam, double* g, int k);
+// out = the interface entries of v ([k][N] -> [k][N_I][si], the ABI's interface layout).
+slab_status launch_gather_interface(slab_handle* h, const double* v, double* out, int k);
 // Sizes the norm-reduction scratch of launch_residual for k right-hand sides.
 slab_status ensure_red(slab_handle* h, int k);
 // FP64 vector kernels for the Krylov refinement (batched over k vectors of length N)

@@ -461,6 +461,30 @@ slab_status launch_apply(slab_handle* h, const double* x, double* y, int k) {
     return SLAB_OK;
 }
 
+// out[r][q][j] = v[r][interface node (q, j)]: interface q is the plane x = (q + 1) b, its nodes j
+// ordered by y (then z), y fastest (the interface-vector layout of the ABI).
+__global__ void gather_interface_kernel(int dim, int n, int b, int NI, int k, const double* __restrict__ v,
+                                        double* __restrict__ out) {
+    const int64_t s = n - 1, si = dim == 3 ? s * s : s, N = dim == 3 ? s * s * s : s * s;
+    const int64_t tot = (int64_t)k * NI * si;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = e % si, q = (e / si) % NI, r = e / (si * NI);
+        const int64_t x = (q + 1) * b;
+        const int64_t idx = dim == 3 ? ((j / s) * s + (j % s)) * s + (x - 1) : j * s + (x - 1);
+        out[e] = v[r * N + idx];
+    }
+}
+
+slab_status launch_gather_interface(slab_handle* h, const double* v, double* out, int k) {
+    const int64_t tot = (int64_t)k * h->td.NI * h->td.si;
+    if (tot <= 0) return SLAB_OK;
+    SLAB_PROF(h, KC_OTHER);
+    gather_interface_kernel<<<(unsigned)std::min<int64_t>((tot + 255) / 256, 152 * 32), 256, 0, h->stream>>>(
+        h->dim, h->n, h->b, h->td.NI, k, v, out);
+    SLAB_CK_LAUNCH(h);
+    return SLAB_OK;
+}
+
 slab_status launch_kappa_gradient(slab_handle* h, const double* u, const double* lam, double* g, int k) {
     const int n = h->n;
     dim3 grid((n + 1 + 127) / 128, n + 1);

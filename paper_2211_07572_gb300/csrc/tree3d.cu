@@ -196,6 +196,18 @@ __global__ void t3_init_T_kernel(T3Args A, T* Tb) {
     }
 }
 
+// Upper triangle of every diagonal block T_qq from its lower triangle (the interface products
+// that add into T_qq are symmetric and computed on the lower tiles only).
+template <typename T>
+__global__ void t3_mirror_lower_kernel(T* Tb, int sp) {
+    T* Tq = Tb + (int64_t)blockIdx.y * sp * sp;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)sp * sp;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int I = (int)(e / sp), J = (int)(e % sp);
+        if (J > I) Tq[e] = Tq[(int64_t)J * sp + I];
+    }
+}
+
 // ------------------------------------------------------------------ solve kernels
 struct T3Vec {
     int kcap, K, r0;
@@ -575,12 +587,18 @@ slab_status tree3d_factor(slab_handle* h) {
                     const T* zb = zit + ((int64_t)(t * cnt + i0) * 2 + sb) * wsp * Mp;
                     const int64_t off = (int64_t)(lo - 1) * s;
                     const int64_t step = (int64_t)(2 << k) * s;
+                    // pairs 0 and 1 add a symmetric product into a diagonal block: lower tiles only
                     if ((st = dense_gemm<T>(h, KC_ASSEMBLE, wl, wl, Mp, T(-1), za, Mp, zs, zb, Mp, zs, T(1),
-                                            Tq + off * sp + off, sp, step * sp + step, 0, 0, nb)))
+                                            Tq + off * sp + off, sp, step * sp + step, 0, pair < 2, nb)))
                         return st;
                 }
             }
         }
+    }
+    {
+        SLAB_PROF(h, KC_ASSEMBLE);
+        t3_mirror_lower_kernel<T><<<dim3(grid1(blk) < 256 ? grid1(blk) : 256, NI), 256, 0, h->stream>>>(Tb, sp);
+        SLAB_CK_LAUNCH(h);
     }
     return SLAB_OK;
 }

@@ -187,6 +187,16 @@ class SlabSolver:
                    "interior_solve")
         return u
 
+    def apply_T(self, X) -> torch.Tensor:
+        """Y = T X for k interface vectors ([k][N_I s] rows) without forming T (the sketch operation
+        of Sec. 3.3): one interior solve with zero load, then the interface rows of A u."""
+        X = _dev(X, self.device).reshape(-1, self.NI * self.s)
+        k = X.shape[0]
+        Y = torch.empty_like(X)
+        work = torch.empty((2 * k, self.N), dtype=torch.float64, device=self.device)
+        _lib.check(self.lib.slab_apply_T(self.h, _ptr(X), _ptr(Y), k, _ptr(work)), "apply_T")
+        return Y
+
     def T_block(self, which: int, q: int) -> np.ndarray:
         out = np.empty((self.s, self.s), dtype=np.float64)
         _lib.check(self.lib.slab_get_T_block(self.h, which, q, out.ctypes.data_as(ctypes.c_void_p)), "T_block")

@@ -284,3 +284,30 @@ def test_invalid_arguments_are_rejected():
     with pytest.raises(SlabError) as ei:
         _solver(hp, stage2="oddeven")
     assert ei.value.status == 7
+
+
+@pytest.mark.parametrize("dim,n,b,precision,tol", [(2, 64, 8, "fp64", 1e-11), (2, 64, 8, "fp32", 2e-5),
+                                                   (3, 16, 4, "fp64", 1e-11)])
+def test_matrix_free_T_sketch_matches_oracle(dim, n, b, precision, tol):
+    """Y = T Omega for a Gaussian sketch Omega of 6 b columns (the sketch size the paper's recovery
+    draws, Sec. 3.3), applied without forming T, against the oracle's reduced blocks (eqs. T11-T35)
+    multiplied out block-tridiagonally."""
+    from paper_2211_07572_gb300.solver import SlabSolver
+    p = inputs.diffusion(n, b, k=0, dim=dim, n_modes=8, field_seed=51)
+    s = SlabSolver(dim, n, b, inputs.DIFFUSION, kappa=p.kappa, precision=precision)
+    si, NI = s.s, s.NI
+    k = 6 * b
+    Om = np.random.default_rng(52).standard_normal((k, NI * si))
+    Y = s.apply_T(torch.from_numpy(Om).cuda()).cpu().numpy()
+    s.close()
+    A = oracle.assemble_problem(p)
+    Td, Tl, Tu = oracle.reduced_system(A, dim, n, b)
+    Yo = np.zeros_like(Om)
+    for q in range(NI):
+        acc = Om[:, q * si:(q + 1) * si] @ Td[q].T
+        if q + 1 < NI:
+            acc += Om[:, (q + 1) * si:(q + 2) * si] @ Tu[q].T
+        if q > 0:
+            acc += Om[:, (q - 1) * si:q * si] @ Tl[q - 1].T
+        Yo[:, q * si:(q + 1) * si] = acc
+    assert np.linalg.norm(Y - Yo) <= tol * np.linalg.norm(Yo)

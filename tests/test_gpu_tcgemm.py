@@ -115,14 +115,14 @@ def test_tc_gemm_f16x3_rejects_ragged_k():
     assert st == 1
 
 
-@pytest.mark.parametrize("split", [1, 2])
-def test_tc_gemm_schur_shape_rate(split):
-    """The odd-even Schur update shape of the n = 2048 workload (2048^3, C -= A B^T) in 3xTF32
-    (split 1) and in three FP16 products (split 2): sampled rows against FP64, and the
-    event-timed rate reported for the record."""
+@pytest.mark.parametrize("split,M,N,K", [(1, 2048, 2048, 2048), (2, 2048, 2048, 2048), (2, 4096, 4096, 2048)])
+def test_tc_gemm_schur_shape_rate(split, M, N, K):
+    """Schur-update shapes, C -= A B^T: the odd-even update of the n = 2048 workload (2048^3) in
+    3xTF32 (split 1) and in three FP16 products (split 2), and a 4096 x 4096 x 2048 product that runs
+    on the 128 x 256 tiles: sampled rows against FP64, and the event-timed rate reported for the
+    record."""
     from paper_2211_07572_gb300 import _lib
     lib = _lib.load()
-    M = N = K = 2048
     g = torch.Generator(device="cuda").manual_seed(5)
     A = torch.randn(M, K, generator=g, device="cuda")
     B = torch.randn(N, K, generator=g, device="cuda")
@@ -154,7 +154,7 @@ def test_tc_gemm_schur_shape_rate(split):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / 5
     mode = "3xTF32" if split == 1 else "3xFP16 (row-scaled splits)"
-    print(f"tc_gemm 2048^3 {mode}: {ms:.3f} ms, {2 * M * N * K / ms / 1e9:.1f} TFLOP/s algorithmic")
+    print(f"tc_gemm {M}x{N}x{K} {mode}: {ms:.3f} ms, {2 * M * N * K / ms / 1e9:.1f} TFLOP/s algorithmic")
 
 
 @pytest.mark.parametrize("M,N,K", [(200, 130, 64), (4096, 640, 64), (77, 1000, 32)])
