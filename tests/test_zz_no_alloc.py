@@ -56,11 +56,15 @@ def test_noalloc_residual_matches_handle_path_twice(kind):
         r_ref = s.residual(uu, f)
         torch.cuda.synchronize()
         scale = float(s.apply(uu).abs().max())
+        # the two residual kernels round differently, by up to about eps |A u| per entry
         assert float((r - r_ref).abs().max()) <= 1e-13 * scale
         rel = np.sqrt(nr.cpu().numpy() / nf.cpu().numpy())
         if call == 0:
-            np.testing.assert_allclose(rel, relres, rtol=1e-10)
-        np.testing.assert_allclose(nr.cpu().numpy(), (r_ref * r_ref).sum(dim=1).cpu().numpy(), rtol=1e-10)
+            # per entry the residuals differ by up to 1e-13 |A u| while |r| ~ 1e-6 |A u| after one FP32
+            # pass, so the two relative residuals agree to about 1e-7
+            np.testing.assert_allclose(rel, relres, rtol=1e-7)
+        # the reduction itself: the squared norms of the kernel's own residual and load
+        np.testing.assert_allclose(nr.cpu().numpy(), (r * r).sum(dim=1).cpu().numpy(), rtol=1e-12)
         np.testing.assert_allclose(nf.cpu().numpy(), (f * f).sum(dim=1).cpu().numpy(), rtol=1e-12)
     # requests beyond the fixed scratch are rejected before any launch
     big = lib.slab_residual_norms_noalloc(4097, inputs.POISSON, None, None, 0.0, _p(u), _p(f), _p(r), 100000,
