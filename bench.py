@@ -953,7 +953,7 @@ def main():
     ap.add_argument("--no-graph", dest="graph", action="store_false",
                     help="adjoint256: stream-per-problem path instead of the CUDA-graph batch")
     ap.add_argument("--graph-steps", type=int, default=4, help="adjoint256 graph: refinement passes per solve")
-    ap.add_argument("--branches", type=int, default=16, help="adjoint256 graph: parallel branches per wave")
+    ap.add_argument("--branches", type=int, default=32, help="adjoint256 graph: parallel branches per wave")
     ap.add_argument("--workload", default="diffusion3d96",
                     choices=["diffusion2048", "helmholtz4096", "diffusion3d96", "adjoint256", "helmholtzj0"],
                     help="diffusion3d96: the default bench line (3-D diffusion n=96, b=8, k=16); diffusion2048, "
