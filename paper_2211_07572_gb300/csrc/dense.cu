@@ -294,6 +294,8 @@ __device__ void chol_inv_tile(const T* S, T* Li, unsigned* status) {
 template <typename T>
 __global__ void __launch_bounds__(256) panel_diag_kernel(const T* Wt, int64_t ld, int kb, unsigned* status,
                                                          int64_t bstride, T* Lw) {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ unsigned char smem_raw[];
     T* S = reinterpret_cast<T*>(smem_raw);
     T* Li = S + TL * TLP;
@@ -311,6 +313,8 @@ __global__ void __launch_bounds__(256) panel_diag_kernel(const T* Wt, int64_t ld
 template <typename T>
 __global__ void __launch_bounds__(256) panel_apply_kernel(T* Wt, int64_t ld, int kb, int64_t bstride,
                                                           const T* Lw) {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ unsigned char smem_raw[];
     T* Li = reinterpret_cast<T*>(smem_raw);
     T* X = Li + TL * TLP;
@@ -373,6 +377,8 @@ __device__ __forceinline__ void tile_nt(const T* X, const T* Y, T acc[4][4], int
 template <typename T>
 __global__ void __launch_bounds__(256) panel_pair_kernel(T* Wt, int64_t ld, int kb, int64_t bstride, const T* Lw,
                                                          T* Lw2, unsigned* status) {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ unsigned char smem_raw[];
     T* Li = reinterpret_cast<T*>(smem_raw);
     T* X = Li + TL * TLP;
@@ -1696,13 +1702,14 @@ slab_status tall_panel(slab_handle* h, T* W, int ncols, int ident0, int kb, int 
         const int nb = std::min(65535, batch - b0);
         {
             SLAB_PROF(h, KC_PANEL);
-            panel_diag_kernel<T><<<dim3(1, nb), 256, smem, h->stream>>>(W + b0 * bstride, ncols, kb, h->dstatus,
-                                                                         bstride, Lw);
+            SLAB_CK(h, launch_pdl(panel_diag_kernel<T>, dim3(1, nb), dim3(256), smem, h->stream, W + b0 * bstride,
+                                  (int64_t)ncols, kb, h->dstatus, bstride, Lw));
             SLAB_CK_LAUNCH(h);
         }
         if (nrt > 0) {
             SLAB_PROF(h, KC_PANEL);
-            panel_apply_kernel<T><<<dim3(nrt, nb), 256, smem, h->stream>>>(W + b0 * bstride, ncols, kb, bstride, Lw);
+            SLAB_CK(h, launch_pdl(panel_apply_kernel<T>, dim3(nrt, nb), dim3(256), smem, h->stream, W + b0 * bstride,
+                                  (int64_t)ncols, kb, bstride, (const T*)Lw));
             SLAB_CK_LAUNCH(h);
         }
     }
@@ -1723,15 +1730,15 @@ slab_status tall_pair(slab_handle* h, T* W, int ncols, int ident0, int kb, int b
         const int nb = std::min(65535, batch - b0);
         T* Lw2 = Lw + (int64_t)nb * TL * TL;
         SLAB_PROF(h, KC_PANEL);
-        panel_diag_kernel<T><<<dim3(1, nb), 256, smem, h->stream>>>(W + b0 * bstride, ncols, kb, h->dstatus, bstride,
-                                                                     Lw);
+        SLAB_CK(h, launch_pdl(panel_diag_kernel<T>, dim3(1, nb), dim3(256), smem, h->stream, W + b0 * bstride,
+                              (int64_t)ncols, kb, h->dstatus, bstride, Lw));
         SLAB_CK_LAUNCH(h);
-        panel_pair_kernel<T><<<dim3(nrt0, nb), 256, psmem, h->stream>>>(W + b0 * bstride, ncols, kb, bstride, Lw, Lw2,
-                                                                       h->dstatus);
+        SLAB_CK(h, launch_pdl(panel_pair_kernel<T>, dim3(nrt0, nb), dim3(256), psmem, h->stream, W + b0 * bstride,
+                              (int64_t)ncols, kb, bstride, (const T*)Lw, Lw2, h->dstatus));
         SLAB_CK_LAUNCH(h);
         if (nrt1 > 0) {
-            panel_apply_kernel<T><<<dim3(nrt1, nb), 256, smem, h->stream>>>(W + b0 * bstride, ncols, kb + 1, bstride,
-                                                                           Lw2);
+            SLAB_CK(h, launch_pdl(panel_apply_kernel<T>, dim3(nrt1, nb), dim3(256), smem, h->stream,
+                                  W + b0 * bstride, (int64_t)ncols, kb + 1, bstride, (const T*)Lw2));
             SLAB_CK_LAUNCH(h);
         }
         prof_extra(h, KC_PANEL, nrt1 > 0 ? 2 : 1);

@@ -329,6 +329,30 @@ inline int tc_gemm_extra_launches(const TcGemmArgs& g) {
     return (g.ksplit > 1 ? 1 : 0) + (g.split == 2 ? (f16x3_shared(g) ? 1 : 2) : 0);
 }
 
+// Programmatic dependent launch for the chains of short dependent kernels (tall-Cholesky panels,
+// their products and pre-passes): a kernel launched with launch_pdl may start while its
+// predecessor in the stream is still running; it must call pdl_wait() before it touches anything
+// the predecessor writes (the wait returns once the predecessor has completed and its memory is
+// visible), and it lets its own dependents start early with pdl_trigger().  Both are no-ops for a
+// kernel launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, ((KArgs)args)...);
+}
+
 // error helper
 slab_status slab_cuda_check(slab_handle* h, cudaError_t e);
 #define SLAB_CK(h, call)                                             \

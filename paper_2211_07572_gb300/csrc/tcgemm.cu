@@ -155,6 +155,8 @@ __global__ void __launch_bounds__(256, 1)
                    int lower_only, int ksplit, float* part, unsigned* err) {
     using Cfg = TcCfg<BN, SPLIT>;
     constexpr int STAGES = Cfg::STAGES;
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ __align__(1024) uint8_t tc_smem[];
     __shared__ uint64_t full_bar[STAGES], conv_bar[STAGES], empty_bar[STAGES], done_bar;
     __shared__ uint32_t tmem_slot;
@@ -353,6 +355,8 @@ __global__ void __launch_bounds__(256, 1)
 // (transC: [N][M], else [M][N]); the splits are added in a fixed order.
 __global__ void splitk_reduce_kernel(int M, int N, int ks, const float* __restrict__ part, float alpha, float beta,
                                      float* C, int64_t ldc, int transC, int64_t sC, int batch) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t tot = (int64_t)M * N;
     if (g >= tot * batch) return;
@@ -409,14 +413,18 @@ slab_status launch_tc(cudaStream_t st, const TcGemmArgs& g, unsigned* err) {
     if (!ensure_smem_attr(tc_gemm_kernel<BN, SPLIT>, smem, attr_done)) return SLAB_ECUDA;
     const int ks = g.ksplit > 1 ? g.ksplit : 1;
     dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, ks * g.batch);
-    tc_gemm_kernel<BN, SPLIT><<<grid, 256, smem, st>>>(ta, tb, g.M, g.N, g.K, g.alpha, g.beta, g.C, g.ldc, g.sC,
-                                                       g.transC, g.lower_only, ks, g.part, err);
-    if (cudaGetLastError() != cudaSuccess) return SLAB_ECUDA;
+    if (launch_pdl(tc_gemm_kernel<BN, SPLIT>, grid, dim3(256), (size_t)smem, st, ta, tb, g.M, g.N, g.K, g.alpha, g.beta,
+                   g.C, g.ldc, g.sC, g.transC, g.lower_only, ks, g.part, err) != cudaSuccess) {
+        cudaGetLastError();
+        return SLAB_ECUDA;
+    }
     if (ks > 1) {
         const int64_t tot = (int64_t)g.M * g.N * g.batch;
-        splitk_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(g.M, g.N, ks, g.part, g.alpha, g.beta,
-                                                                           g.C, g.ldc, g.transC, g.sC, g.batch);
-        if (cudaGetLastError() != cudaSuccess) return SLAB_ECUDA;
+        if (launch_pdl(splitk_reduce_kernel, dim3((unsigned)((tot + 255) / 256)), dim3(256), 0, st, g.M, g.N, ks,
+                       (const float*)g.part, g.alpha, g.beta, g.C, g.ldc, g.transC, g.sC, g.batch) != cudaSuccess) {
+            cudaGetLastError();
+            return SLAB_ECUDA;
+        }
     }
     return SLAB_OK;
 }
@@ -654,6 +662,8 @@ struct F16Cfg {
 // One warp per row: e_r, then hi / lo (FP16, [rows][K] per batch matrix, rows * K apart).
 __global__ void split16_kernel(const float* __restrict__ X, int64_t ldx, int64_t sx, int rows, int K, __half* hi,
                                __half* lo, int* ex) {
+    pdl_wait();
+    pdl_trigger();
     const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (r >= rows) return;
@@ -704,6 +714,8 @@ __global__ void __launch_bounds__(256, 1)
                     int lower_only, unsigned* err) {
     using Cfg = F16Cfg<BN>;
     constexpr int STAGES = Cfg::STAGES;
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ __align__(1024) uint8_t tc_smem[];
     __shared__ uint64_t full_bar[STAGES], empty_bar[STAGES], accf_bar[2], acce_bar[2];
     __shared__ uint32_t tmem_slot;
@@ -913,13 +925,16 @@ slab_status launch_f16x3(cudaStream_t st, const TcGemmArgs& g, unsigned* err) {
     }
     int* ea = (int*)w;                       w += align256((size_t)b * g.M * 4);
     int* eb = shared ? ea : (int*)w;
-    split16_kernel<<<dim3((unsigned)((g.M + 7) / 8), (unsigned)b), 256, 0, st>>>(g.A, g.lda, g.sA, g.M, g.K, Ah, Al,
-                                                                                  ea);
-    if (cudaGetLastError() != cudaSuccess) return SLAB_ECUDA;
-    if (!shared) {
-        split16_kernel<<<dim3((unsigned)((g.N + 7) / 8), (unsigned)b), 256, 0, st>>>(g.B, g.ldb, g.sB, g.N, g.K, Bh,
-                                                                                      Bl, eb);
-        if (cudaGetLastError() != cudaSuccess) return SLAB_ECUDA;
+    if (launch_pdl(split16_kernel, dim3((unsigned)((g.M + 7) / 8), (unsigned)b), dim3(256), 0, st, g.A, g.lda, g.sA,
+                   g.M, g.K, Ah, Al, ea) != cudaSuccess) {
+        cudaGetLastError();
+        return SLAB_ECUDA;
+    }
+    if (!shared &&
+        launch_pdl(split16_kernel, dim3((unsigned)((g.N + 7) / 8), (unsigned)b), dim3(256), 0, st, g.B, g.ldb, g.sB,
+                   g.N, g.K, Bh, Bl, eb) != cudaSuccess) {
+        cudaGetLastError();
+        return SLAB_ECUDA;
     }
     CUtensorMap tah, tal, tbh, tbl;
     if (!make_map16(&tah, Ah, g.M, K, g.batch, BM) || !make_map16(&tal, Al, g.M, K, g.batch, BM) ||
@@ -930,9 +945,13 @@ slab_status launch_f16x3(cudaStream_t st, const TcGemmArgs& g, unsigned* err) {
     if (!ensure_smem_attr(tc_f16x3_kernel<BN>, smem, attr_done)) return SLAB_ECUDA;
     const int64_t tiles = (int64_t)g.batch * ((g.M + BM - 1) / BM) * ((g.N + BN - 1) / BN);
     const int grid = (int)std::min<int64_t>(tiles, num_sms());
-    tc_f16x3_kernel<BN><<<grid, 256, smem, st>>>(tah, tal, tbh, tbl, g.M, g.N, g.K, g.batch, g.alpha, g.beta, g.C,
-                                                 g.ldc, g.sC, ea, eb, rB, g.transC, g.lower_only, err);
-    return cudaGetLastError() == cudaSuccess ? SLAB_OK : SLAB_ECUDA;
+    if (launch_pdl(tc_f16x3_kernel<BN>, dim3(grid), dim3(256), (size_t)smem, st, tah, tal, tbh, tbl, g.M, g.N, g.K,
+                   g.batch, g.alpha, g.beta, g.C, g.ldc, g.sC, (const int*)ea, (const int*)eb, rB, g.transC,
+                   g.lower_only, err) != cudaSuccess) {
+        cudaGetLastError();
+        return SLAB_ECUDA;
+    }
+    return SLAB_OK;
 }
 
 }  // namespace
