@@ -146,14 +146,20 @@ __global__ void __launch_bounds__(256) gemm_tn_skinny_kernel(int M, int N, int K
 }
 
 // Cholesky L L^T = S of the 64 x 64 tile S (smem, stride TLP; lower triangle read) and
-// Li = L^{-1} (written to smem, stride TLP), by 256 threads in 4 x 4 register blocks: thread
-// (ti, tj) keeps block (ti, tj) of the matrix under elimination and of X, which starts as I and
-// ends as L^{-1}.  Block step kt: the diagonal thread factors and inverts its 4 x 4 block
-// (reciprocal square roots refined by one Newton step); the owners of block column kt form
-// L_ik = A_ik L_kk^{-T}, the owners of block row kt of X apply L_kk^{-1}; then every thread
-// applies the rank-4 updates to its blocks (right-looking Cholesky and forward elimination of
-// [S | I] in one sweep, 16 steps with two barriers each).  A non-positive or non-finite pivot
-// sets SLAB_DEV_NOTSPD and continues with 1.
+// Li = L^{-1} (written to smem, stride TLP), by 256 threads in 4 x 4 register blocks, as one sweep
+// of right-looking elimination over [S | I] (16 block steps of 4 columns, two barriers each).
+// Thread (ti, tj), tj <= ti, holds one block: A_ij while column block tj is not yet eliminated,
+// then X_ij, the block of X = L^{-1} under construction (X starts as I).  Block step kt:
+//   the diagonal thread factors its 4 x 4 block, L_kk L_kk^T = A_kk, inverts L_kk (reciprocal
+//   square roots refined by one Newton step) and continues with X_kk = I;
+//   the owners of block column kt publish L_ik = A_ik L_kk^{-T} and continue with X_ik = 0, the
+//   owners of block row kt of X apply X_kj := L_kk^{-1} X_kj and publish it;
+//   every thread below row kt applies B_ij -= L_ik R_j with R_j = L_jk^T (j > kt, its A block) or
+//   R_j = X_kj (j <= kt, its X block).
+// L's column block and X's row block share one staging buffer pb[p][4 j + c] (rows of L for
+// j > kt, columns of X for j <= kt), so both updates are one product with no divergence, and the
+// 16 column owners of a warp read 16 consecutive words per load.  A non-positive or non-finite
+// pivot sets SLAB_DEV_NOTSPD and continues with 1.
 template <typename T> __device__ __forceinline__ T rsqrt_nr(T a);
 template <> __device__ __forceinline__ float rsqrt_nr<float>(float a) {
     float r = rsqrtf(a);
@@ -163,20 +169,20 @@ template <> __device__ __forceinline__ double rsqrt_nr<double>(double a) {
     double r = rsqrt(a);
     return r * (1.5 - 0.5 * a * r * r);
 }
+// A usable Cholesky pivot: positive and finite (NaN fails both comparisons), in T's own arithmetic.
+__device__ __forceinline__ bool pivot_ok(float d) { return d > 0.0f && d <= 3.402823466e38f; }
+__device__ __forceinline__ bool pivot_ok(double d) { return d > 0.0 && d <= 1.7976931348623157e308; }
+
 template <typename T>
-__device__ void chol_inv_tile(const T* S, T* Li, unsigned* status) {
+__device__ __forceinline__ void chol_inv_tile(const T* S, T* Li, unsigned* status) {
     __shared__ T dinv[16];          // L_kk^{-1} (4x4 lower, row-major)
-    __shared__ T colb[64 * 4];      // column block kt of L: rows x 4
-    __shared__ T xrow[4 * 64];      // row block kt of X: 4 x cols
+    __shared__ T pb[4 * 64];        // column block kt of L / row block kt of X: [p][4 j + c]
     const int t = threadIdx.x, ti = t >> 4, tj = t & 15;
-    T a[4][4], x[4][4];
+    T blk[4][4];
 #pragma unroll
     for (int r = 0; r < 4; ++r)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            a[r][c] = S[(4 * ti + r) * TLP + 4 * tj + c];
-            x[r][c] = (ti == tj && r == c) ? T(1) : T(0);
-        }
+        for (int c = 0; c < 4; ++c) blk[r][c] = S[(4 * ti + r) * TLP + 4 * tj + c];
     for (int kt = 0; kt < 16; ++kt) {
         if (ti == kt && tj == kt) {               // 4x4 Cholesky and inverse in registers
             T l[4][4], li[4][4];
@@ -186,15 +192,15 @@ __device__ void chol_inv_tile(const T* S, T* Li, unsigned* status) {
                 for (int c = 0; c < 4; ++c) { l[r][c] = T(0); li[r][c] = T(0); }
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-                T d = a[c][c];
+                T d = blk[c][c];
 #pragma unroll
                 for (int p = 0; p < c; ++p) d -= l[c][p] * l[c][p];
-                if (!(d > T(0)) || !isfinite((double)d)) { atomicOr(status, SLAB_DEV_NOTSPD); d = T(1); }
+                if (!pivot_ok(d)) { atomicOr(status, SLAB_DEV_NOTSPD); d = T(1); }
                 const T rd = rsqrt_nr<T>(d);
                 l[c][c] = d * rd;
 #pragma unroll
                 for (int r = c + 1; r < 4; ++r) {
-                    T v = a[r][c];
+                    T v = blk[r][c];
 #pragma unroll
                     for (int p = 0; p < c; ++p) v -= l[r][p] * l[c][p];
                     l[r][c] = v * rd;
@@ -213,10 +219,28 @@ __device__ void chol_inv_tile(const T* S, T* Li, unsigned* status) {
 #pragma unroll
             for (int r = 0; r < 4; ++r)
 #pragma unroll
-                for (int c = 0; c < 4; ++c) dinv[r * 4 + c] = li[r][c];
+                for (int c = 0; c < 4; ++c) {
+                    dinv[r * 4 + c] = li[r][c];
+                    blk[r][c] = (r == c) ? T(1) : T(0);   // X_kk starts as I
+                }
         }
         __syncthreads();
-        if (tj == kt && ti > kt) {                // L_ik = A_ik L_kk^{-T}
+        if (tj == kt && ti > kt) {                // publish L_ik = A_ik L_kk^{-T}; continue with X_ik = 0
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    T v = T(0);
+#pragma unroll
+                    for (int p = 0; p <= c; ++p) v += blk[r][p] * dinv[c * 4 + p];
+                    pb[c * 64 + 4 * ti + r] = v;
+                }
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) blk[r][c] = T(0);
+        }
+        if (ti == kt && tj <= kt) {               // X_kt,j = L_kk^{-1} X_kt,j, published
             T o[4][4];
 #pragma unroll
             for (int r = 0; r < 4; ++r)
@@ -224,68 +248,59 @@ __device__ void chol_inv_tile(const T* S, T* Li, unsigned* status) {
                 for (int c = 0; c < 4; ++c) {
                     T v = T(0);
 #pragma unroll
-                    for (int p = 0; p <= c; ++p) v += a[r][p] * dinv[c * 4 + p];
+                    for (int p = 0; p <= r; ++p) v += dinv[r * 4 + p] * blk[p][c];
                     o[r][c] = v;
                 }
 #pragma unroll
             for (int r = 0; r < 4; ++r)
 #pragma unroll
-                for (int c = 0; c < 4; ++c) colb[(4 * ti + r) * 4 + c] = o[r][c];
-        }
-        if (ti == kt && tj <= kt) {               // X_kt,j = L_kk^{-1} X_kt,j
-            T o[4][4];
-#pragma unroll
-            for (int r = 0; r < 4; ++r)
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    T v = T(0);
-#pragma unroll
-                    for (int p = 0; p <= r; ++p) v += dinv[r * 4 + p] * x[p][c];
-                    o[r][c] = v;
-                }
-#pragma unroll
-            for (int r = 0; r < 4; ++r)
-#pragma unroll
-                for (int c = 0; c < 4; ++c) { x[r][c] = o[r][c]; xrow[r * 64 + 4 * tj + c] = o[r][c]; }
+                for (int c = 0; c < 4; ++c) { blk[r][c] = o[r][c]; pb[r * 64 + 4 * tj + c] = o[r][c]; }
         }
         __syncthreads();
-        if (ti > kt) {
-            T li_[4][4];
+        if (ti > kt && tj <= ti) {                // B_ij -= L_ik R_j
+            T lk[4][4];
 #pragma unroll
             for (int r = 0; r < 4; ++r)
 #pragma unroll
-                for (int p = 0; p < 4; ++p) li_[r][p] = colb[(4 * ti + r) * 4 + p];
-            if (tj > kt && tj <= ti) {            // A_ij -= L_ik L_jk^T
+                for (int p = 0; p < 4; ++p) lk[r][p] = pb[p * 64 + 4 * ti + r];
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    T lj[4];
+            for (int c = 0; c < 4; ++c) {
+                T rj[4];
 #pragma unroll
-                    for (int p = 0; p < 4; ++p) lj[p] = colb[(4 * tj + c) * 4 + p];
+                for (int p = 0; p < 4; ++p) rj[p] = pb[p * 64 + 4 * tj + c];
 #pragma unroll
-                    for (int r = 0; r < 4; ++r)
+                for (int r = 0; r < 4; ++r)
 #pragma unroll
-                        for (int p = 0; p < 4; ++p) a[r][c] -= li_[r][p] * lj[p];
-                }
-            }
-            if (tj <= kt) {                       // X_ij -= L_ik X_kt,j
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    T xk[4];
-#pragma unroll
-                    for (int p = 0; p < 4; ++p) xk[p] = xrow[p * 64 + 4 * tj + c];
-#pragma unroll
-                    for (int r = 0; r < 4; ++r)
-#pragma unroll
-                        for (int p = 0; p < 4; ++p) x[r][c] -= li_[r][p] * xk[p];
-                }
+                    for (int p = 0; p < 4; ++p) blk[r][c] -= lk[r][p] * rj[p];
             }
         }
     }
 #pragma unroll
     for (int r = 0; r < 4; ++r)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) Li[(4 * ti + r) * TLP + 4 * tj + c] = (tj <= ti) ? x[r][c] : T(0);
+        for (int c = 0; c < 4; ++c) Li[(4 * ti + r) * TLP + 4 * tj + c] = (tj <= ti) ? blk[r][c] : T(0);
     __syncthreads();
+}
+
+// Stage a 64 x 64 tile (row stride ld) in registers, then in shared memory (row stride TLP); 256
+// threads.  Every global load of a thread is issued before its first shared store, so a tile costs
+// one memory round trip instead of one per element the thread copies.
+constexpr int TPT = TL * TL / 256;     // elements of a tile per thread
+template <typename T>
+__device__ __forceinline__ void tile_fetch(const T* src, int64_t ld, T (&v)[TPT]) {
+#pragma unroll
+    for (int q = 0; q < TPT; ++q) {
+        const int i = threadIdx.x + 256 * q;
+        v[q] = src[(int64_t)(i / TL) * ld + i % TL];
+    }
+}
+template <typename T>
+__device__ __forceinline__ void tile_stash(const T (&v)[TPT], T* dst) {
+#pragma unroll
+    for (int q = 0; q < TPT; ++q) {
+        const int i = threadIdx.x + 256 * q;
+        dst[(i / TL) * TLP + i % TL] = v[q];
+    }
 }
 
 // Panel of tile column kb of the tall matrix Wt (leading dimension ld), in two launches.
@@ -302,32 +317,44 @@ __global__ void __launch_bounds__(256) panel_diag_kernel(const T* Wt, int64_t ld
     const int tid = threadIdx.x;
     Wt += (int64_t)blockIdx.y * bstride;
     const T* D = Wt + (int64_t)kb * TL * ld + (int64_t)kb * TL;
-    for (int i = tid; i < TL * TL; i += 256) S[(i / TL) * TLP + i % TL] = D[(int64_t)(i / TL) * ld + i % TL];
+    {
+        T v[TPT];
+        tile_fetch<T>(D, ld, v);
+        tile_stash<T>(v, S);
+    }
     __syncthreads();
     chol_inv_tile<T>(S, Li, status);
     T* out = Lw + (int64_t)blockIdx.y * TL * TL;
     for (int i = tid; i < TL * TL; i += 256) out[i] = Li[(i / TL) * TLP + i % TL];
 }
 
-// panel_apply_kernel: CTA x replaces the tile Wt[kb+1+x][kb] by itself times L^{-T}.
-template <typename T>
+// panel_apply_kernel: CTA x replaces the tile Wt[kb+1+x][kb] by itself times L^{-T}.  DIAG: every
+// CTA factors the diagonal tile itself (the same arithmetic as panel_diag_kernel, so every CTA
+// obtains the same L^{-1}) instead of reading Lw -- one launch per panel where the row tiles of the
+// batch fit in one wave, so the redundant 64 x 64 factorisations cost no extra time.
+template <typename T, bool DIAG>
 __global__ void __launch_bounds__(256) panel_apply_kernel(T* Wt, int64_t ld, int kb, int64_t bstride,
-                                                          const T* Lw) {
+                                                          const T* Lw, unsigned* status) {
     pdl_wait();
     pdl_trigger();
     extern __shared__ unsigned char smem_raw[];
     T* Li = reinterpret_cast<T*>(smem_raw);
     T* X = Li + TL * TLP;
+    T* S = X + TL * TLP;                          // DIAG only: the diagonal tile
     const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
     const int r = kb + 1 + blockIdx.x;
     Wt += (int64_t)blockIdx.y * bstride;
     T* src = Wt + (int64_t)r * TL * ld + (int64_t)kb * TL;
-    const T* lin = Lw + (int64_t)blockIdx.y * TL * TL;
-    for (int i = tid; i < TL * TL; i += 256) {
-        Li[(i / TL) * TLP + i % TL] = lin[i];
-        X[(i / TL) * TLP + i % TL] = src[(int64_t)(i / TL) * ld + i % TL];
+    {
+        T vl[TPT], vx[TPT];
+        if (DIAG) tile_fetch<T>(Wt + (int64_t)kb * TL * ld + (int64_t)kb * TL, ld, vl);
+        else tile_fetch<T>(Lw + (int64_t)blockIdx.y * TL * TL, TL, vl);
+        tile_fetch<T>(src, ld, vx);
+        tile_stash<T>(vl, DIAG ? S : Li);
+        tile_stash<T>(vx, X);
     }
     __syncthreads();
+    if (DIAG) chol_inv_tile<T>(S, Li, status);
     T acc[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -374,7 +401,8 @@ __device__ __forceinline__ void tile_nt(const T* X, const T* Y, T acc[4][4], int
 //   applies panel kb to panel kb+1: W[r][kb+1] -= P_r P_{kb+1}^T,
 // and the CTA of r = kb+1 then factors the updated diagonal tile of panel kb+1 (Cholesky and
 // inverse, as panel_diag_kernel) into Lw2.  Panel kb+1 is finished by panel_apply_kernel(kb+1, Lw2).
-template <typename T>
+// DIAG: every CTA factors panel kb's diagonal tile itself, as panel_apply_kernel<T, true>.
+template <typename T, bool DIAG>
 __global__ void __launch_bounds__(256) panel_pair_kernel(T* Wt, int64_t ld, int kb, int64_t bstride, const T* Lw,
                                                          T* Lw2, unsigned* status) {
     pdl_wait();
@@ -384,21 +412,27 @@ __global__ void __launch_bounds__(256) panel_pair_kernel(T* Wt, int64_t ld, int 
     T* X = Li + TL * TLP;
     T* Y = X + TL * TLP;
     T* C = Y + TL * TLP;
+    T* S = C + TL * TLP;                          // DIAG only: panel kb's diagonal tile
     const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
     const int r = kb + 1 + blockIdx.x;
     Wt += (int64_t)blockIdx.y * bstride;
     T* src = Wt + (int64_t)r * TL * ld + (int64_t)kb * TL;
     const T* src1 = Wt + (int64_t)(kb + 1) * TL * ld + (int64_t)kb * TL;
     T* dst = Wt + (int64_t)r * TL * ld + (int64_t)(kb + 1) * TL;
-    const T* lin = Lw + (int64_t)blockIdx.y * TL * TL;
-    for (int i = tid; i < TL * TL; i += 256) {
-        const int a = i / TL, b = i % TL;
-        Li[a * TLP + b] = lin[i];
-        X[a * TLP + b] = src[(int64_t)a * ld + b];
-        Y[a * TLP + b] = src1[(int64_t)a * ld + b];
-        C[a * TLP + b] = dst[(int64_t)a * ld + b];
+    {
+        T vl[TPT], vx[TPT], vy[TPT], vc[TPT];
+        if (DIAG) tile_fetch<T>(Wt + (int64_t)kb * TL * ld + (int64_t)kb * TL, ld, vl);
+        else tile_fetch<T>(Lw + (int64_t)blockIdx.y * TL * TL, TL, vl);
+        tile_fetch<T>(src, ld, vx);
+        tile_fetch<T>(src1, ld, vy);
+        tile_fetch<T>(dst, ld, vc);
+        tile_stash<T>(vl, DIAG ? S : Li);
+        tile_stash<T>(vx, X);
+        tile_stash<T>(vy, Y);
+        tile_stash<T>(vc, C);
     }
     __syncthreads();
+    if (DIAG) chol_inv_tile<T>(S, Li, status);
     T p[4][4], q[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -1693,6 +1727,11 @@ slab_status tall_update(slab_handle* h, T* W, int ncols, int rows, int c0, int c
     return SLAB_OK;
 }
 
+// Whether a panel launch of `ctas` CTAs with one extra 64 x 64 tile of shared memory runs in one wave
+// on the 152 SMs (two CTAs per SM in FP32, one in FP64): then every CTA can factor the diagonal
+// tile itself and the separate diagonal launch is saved.
+inline bool one_wave(int64_t ctas, size_t elem) { return ctas <= (elem == 4 ? 2 : 1) * 152; }
+
 template <typename T>
 slab_status tall_panel(slab_handle* h, T* W, int ncols, int ident0, int kb, int batch, int64_t bstride, size_t smem) {
     const int rows = ident0 + (kb + 1) * TL;
@@ -1700,6 +1739,14 @@ slab_status tall_panel(slab_handle* h, T* W, int ncols, int ident0, int kb, int 
     T* Lw = (T*)h->pnl;
     for (int b0 = 0; b0 < batch; b0 += 65535) {
         const int nb = std::min(65535, batch - b0);
+        if (nrt > 0 && one_wave((int64_t)nrt * nb, sizeof(T))) {
+            SLAB_PROF(h, KC_PANEL);
+            SLAB_CK(h, launch_pdl(panel_apply_kernel<T, true>, dim3(nrt, nb), dim3(256), smem + TL * TLP * sizeof(T),
+                                  h->stream, W + b0 * bstride, (int64_t)ncols, kb, bstride, (const T*)Lw,
+                                  h->dstatus));
+            SLAB_CK_LAUNCH(h);
+            continue;
+        }
         {
             SLAB_PROF(h, KC_PANEL);
             SLAB_CK(h, launch_pdl(panel_diag_kernel<T>, dim3(1, nb), dim3(256), smem, h->stream, W + b0 * bstride,
@@ -1708,8 +1755,8 @@ slab_status tall_panel(slab_handle* h, T* W, int ncols, int ident0, int kb, int 
         }
         if (nrt > 0) {
             SLAB_PROF(h, KC_PANEL);
-            SLAB_CK(h, launch_pdl(panel_apply_kernel<T>, dim3(nrt, nb), dim3(256), smem, h->stream, W + b0 * bstride,
-                                  (int64_t)ncols, kb, bstride, (const T*)Lw));
+            SLAB_CK(h, launch_pdl(panel_apply_kernel<T, false>, dim3(nrt, nb), dim3(256), smem, h->stream,
+                                  W + b0 * bstride, (int64_t)ncols, kb, bstride, (const T*)Lw, h->dstatus));
             SLAB_CK_LAUNCH(h);
         }
     }
@@ -1719,7 +1766,8 @@ slab_status tall_panel(slab_handle* h, T* W, int ncols, int ident0, int kb, int 
 // Panels kb and kb+1 (kb+1 < ncols / 64), all updates from the columns left of kb applied: three
 // launches -- panel_diag_kernel(kb), panel_pair_kernel(kb) (panel kb scaled, its update of panel
 // kb+1, panel kb+1's diagonal factored), panel_apply_kernel(kb+1) -- instead of a panel, a product
-// and a panel.
+// and a panel; two where panel kb's row tiles fit in one wave (the pair kernel then factors panel
+// kb's diagonal tile in every CTA).
 template <typename T>
 slab_status tall_pair(slab_handle* h, T* W, int ncols, int ident0, int kb, int batch, int64_t bstride, size_t smem) {
     const int nrt0 = (ident0 + (kb + 1) * TL) / TL - kb - 1;      // row tiles below the diagonal, panel kb
@@ -1730,18 +1778,26 @@ slab_status tall_pair(slab_handle* h, T* W, int ncols, int ident0, int kb, int b
         const int nb = std::min(65535, batch - b0);
         T* Lw2 = Lw + (int64_t)nb * TL * TL;
         SLAB_PROF(h, KC_PANEL);
-        SLAB_CK(h, launch_pdl(panel_diag_kernel<T>, dim3(1, nb), dim3(256), smem, h->stream, W + b0 * bstride,
-                              (int64_t)ncols, kb, h->dstatus, bstride, Lw));
-        SLAB_CK_LAUNCH(h);
-        SLAB_CK(h, launch_pdl(panel_pair_kernel<T>, dim3(nrt0, nb), dim3(256), psmem, h->stream, W + b0 * bstride,
-                              (int64_t)ncols, kb, bstride, (const T*)Lw, Lw2, h->dstatus));
-        SLAB_CK_LAUNCH(h);
-        if (nrt1 > 0) {
-            SLAB_CK(h, launch_pdl(panel_apply_kernel<T>, dim3(nrt1, nb), dim3(256), smem, h->stream,
-                                  W + b0 * bstride, (int64_t)ncols, kb + 1, bstride, (const T*)Lw2));
+        if (one_wave((int64_t)nrt0 * nb, sizeof(T))) {
+            SLAB_CK(h, launch_pdl(panel_pair_kernel<T, true>, dim3(nrt0, nb), dim3(256), psmem + TL * TLP * sizeof(T),
+                                  h->stream, W + b0 * bstride, (int64_t)ncols, kb, bstride, (const T*)Lw, Lw2,
+                                  h->dstatus));
             SLAB_CK_LAUNCH(h);
+        } else {
+            SLAB_CK(h, launch_pdl(panel_diag_kernel<T>, dim3(1, nb), dim3(256), smem, h->stream, W + b0 * bstride,
+                                  (int64_t)ncols, kb, h->dstatus, bstride, Lw));
+            SLAB_CK_LAUNCH(h);
+            SLAB_CK(h, launch_pdl(panel_pair_kernel<T, false>, dim3(nrt0, nb), dim3(256), psmem, h->stream,
+                                  W + b0 * bstride, (int64_t)ncols, kb, bstride, (const T*)Lw, Lw2, h->dstatus));
+            SLAB_CK_LAUNCH(h);
+            prof_extra(h, KC_PANEL, 1);
         }
-        prof_extra(h, KC_PANEL, nrt1 > 0 ? 2 : 1);
+        if (nrt1 > 0) {
+            SLAB_CK(h, launch_pdl(panel_apply_kernel<T, false>, dim3(nrt1, nb), dim3(256), smem, h->stream,
+                                  W + b0 * bstride, (int64_t)ncols, kb + 1, bstride, (const T*)Lw2, h->dstatus));
+            SLAB_CK_LAUNCH(h);
+            prof_extra(h, KC_PANEL, 1);
+        }
     }
     return SLAB_OK;
 }
@@ -1769,9 +1825,15 @@ template <typename T>
 slab_status dense_tall_cholesky(slab_handle* h, T* W, int ncols, int ident0, int batch, int64_t bstride) {
     const size_t smem = 2 * TL * TLP * sizeof(T);
     SLAB_CK(h, cudaFuncSetAttribute(panel_diag_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    SLAB_CK(h, cudaFuncSetAttribute(panel_apply_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    SLAB_CK(h, cudaFuncSetAttribute(panel_pair_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)(4 * TL * TLP * sizeof(T))));
+    const int tile = (int)(TL * TLP * sizeof(T));
+    SLAB_CK(h, cudaFuncSetAttribute(panel_apply_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+    SLAB_CK(h, cudaFuncSetAttribute(panel_apply_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem + tile));
+    SLAB_CK(h, cudaFuncSetAttribute(panel_pair_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    4 * tile));
+    SLAB_CK(h, cudaFuncSetAttribute(panel_pair_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    5 * tile));
     const int bchunk = std::min(batch, 65535);
     slab_status st;
     if ((st = ensure_panel_work(h, 2 * (size_t)bchunk * TL * TL * sizeof(T)))) return st;   // L^-1 of two panels
