@@ -485,6 +485,101 @@ __global__ void __launch_bounds__(256) panel_pair_kernel(T* Wt, int64_t ld, int 
     for (int i = tid; i < TL * TL; i += 256) out[i] = X[(i / TL) * TLP + i % TL];
 }
 
+// Panels kb and kb+1 complete in one launch (every CTA factors both diagonal tiles itself): CTA x
+// owns row tile r = kb+1+x, x = 0 .. nrt (one more than panel kb's row tiles: with the identity
+// block starting on a tile boundary, the last one enters with panel kb+1, and its tile of panel kb
+// is zero), and
+//   factors W[kb][kb] = L L^T,  P_r = W[r][kb] L^{-T} (written back, except for r = kb+1),
+//   P_{kb+1} = W[kb+1][kb] L^{-T} (recomputed from the unscaled tile, never written),
+//   W[r][kb+1] -= P_r P_{kb+1}^T and the updated diagonal tile D = W[kb+1][kb+1] - P_{kb+1} P_{kb+1}^T,
+//   factors D = L' L'^T and writes W[r][kb+1] L'^{-T} (except for r = kb+1, the diagonal tile).
+// The same arithmetic in every CTA gives every CTA the same L^{-1} and L'^{-1}.
+template <typename T>
+__global__ void __launch_bounds__(256) panel_pair_full_kernel(T* Wt, int64_t ld, int kb, int64_t bstride,
+                                                              unsigned* status) {
+    pdl_wait();
+    pdl_trigger();
+    extern __shared__ unsigned char smem_raw[];
+    T* Li = reinterpret_cast<T*>(smem_raw);
+    T* X = Li + TL * TLP;
+    T* Y = X + TL * TLP;
+    T* C = Y + TL * TLP;
+    T* S = C + TL * TLP;
+    const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
+    const int r = kb + 1 + blockIdx.x;
+    Wt += (int64_t)blockIdx.y * bstride;
+    T* src = Wt + (int64_t)r * TL * ld + (int64_t)kb * TL;
+    const T* src1 = Wt + (int64_t)(kb + 1) * TL * ld + (int64_t)kb * TL;
+    T* dst = Wt + (int64_t)r * TL * ld + (int64_t)(kb + 1) * TL;
+    T vd[TPT];
+    {
+        T vs[TPT], vx[TPT], vy[TPT], vc[TPT];
+        tile_fetch<T>(Wt + (int64_t)kb * TL * ld + (int64_t)kb * TL, ld, vs);
+        tile_fetch<T>(src, ld, vx);
+        tile_fetch<T>(src1, ld, vy);
+        tile_fetch<T>(dst, ld, vc);
+        tile_fetch<T>(Wt + (int64_t)(kb + 1) * TL * ld + (int64_t)(kb + 1) * TL, ld, vd);
+        tile_stash<T>(vs, S);
+        tile_stash<T>(vx, X);
+        tile_stash<T>(vy, Y);
+        tile_stash<T>(vc, C);
+    }
+    __syncthreads();
+    chol_inv_tile<T>(S, Li, status);               // ends with a barrier: S is free
+    tile_stash<T>(vd, S);
+    T p[4][4], q[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) p[a][b] = q[a][b] = T(0);
+    tile_nt<T>(X, Li, p, ty, tx);                  // P_r
+    tile_nt<T>(Y, Li, q, ty, tx);                  // P_{kb+1}
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            X[(ty + 16 * a) * TLP + tx + 16 * b] = p[a][b];
+            Y[(ty + 16 * a) * TLP + tx + 16 * b] = q[a][b];
+            if (r != kb + 1) src[(int64_t)(ty + 16 * a) * ld + tx + 16 * b] = p[a][b];
+        }
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) p[a][b] = q[a][b] = T(0);
+    tile_nt<T>(X, Y, p, ty, tx);                   // P_r P_{kb+1}^T
+    tile_nt<T>(Y, Y, q, ty, tx);                   // P_{kb+1} P_{kb+1}^T
+    T u[4][4], d[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            u[a][b] = C[(ty + 16 * a) * TLP + tx + 16 * b] - p[a][b];
+            d[a][b] = S[(ty + 16 * a) * TLP + tx + 16 * b] - q[a][b];
+        }
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            C[(ty + 16 * a) * TLP + tx + 16 * b] = u[a][b];
+            S[(ty + 16 * a) * TLP + tx + 16 * b] = d[a][b];
+        }
+    __syncthreads();
+    chol_inv_tile<T>(S, Li, status);               // L'^{-1}
+    if (r == kb + 1) return;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) p[a][b] = T(0);
+    tile_nt<T>(C, Li, p, ty, tx);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) dst[(int64_t)(ty + 16 * a) * ld + tx + 16 * b] = p[a][b];
+}
+
 template <typename T>
 __global__ void set_identity_kernel(T* B, int s_pad) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1766,8 +1861,7 @@ slab_status tall_panel(slab_handle* h, T* W, int ncols, int ident0, int kb, int 
 // Panels kb and kb+1 (kb+1 < ncols / 64), all updates from the columns left of kb applied: three
 // launches -- panel_diag_kernel(kb), panel_pair_kernel(kb) (panel kb scaled, its update of panel
 // kb+1, panel kb+1's diagonal factored), panel_apply_kernel(kb+1) -- instead of a panel, a product
-// and a panel; two where panel kb's row tiles fit in one wave (the pair kernel then factors panel
-// kb's diagonal tile in every CTA).
+// and a panel; one (panel_pair_full_kernel) where the row tiles fit in one wave.
 template <typename T>
 slab_status tall_pair(slab_handle* h, T* W, int ncols, int ident0, int kb, int batch, int64_t bstride, size_t smem) {
     const int nrt0 = (ident0 + (kb + 1) * TL) / TL - kb - 1;      // row tiles below the diagonal, panel kb
@@ -1778,6 +1872,12 @@ slab_status tall_pair(slab_handle* h, T* W, int ncols, int ident0, int kb, int b
         const int nb = std::min(65535, batch - b0);
         T* Lw2 = Lw + (int64_t)nb * TL * TL;
         SLAB_PROF(h, KC_PANEL);
+        if (ident0 % TL == 0 && nrt1 == nrt0 && one_wave((int64_t)(nrt0 + 1) * nb, sizeof(T))) {
+            SLAB_CK(h, launch_pdl(panel_pair_full_kernel<T>, dim3(nrt0 + 1, nb), dim3(256), psmem + TL * TLP * sizeof(T),
+                                  h->stream, W + b0 * bstride, (int64_t)ncols, kb, bstride, h->dstatus));
+            SLAB_CK_LAUNCH(h);
+            continue;
+        }
         if (one_wave((int64_t)nrt0 * nb, sizeof(T))) {
             SLAB_CK(h, launch_pdl(panel_pair_kernel<T, true>, dim3(nrt0, nb), dim3(256), psmem + TL * TLP * sizeof(T),
                                   h->stream, W + b0 * bstride, (int64_t)ncols, kb, bstride, (const T*)Lw, Lw2,
@@ -1834,6 +1934,7 @@ slab_status dense_tall_cholesky(slab_handle* h, T* W, int ncols, int ident0, int
                                     4 * tile));
     SLAB_CK(h, cudaFuncSetAttribute(panel_pair_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     5 * tile));
+    SLAB_CK(h, cudaFuncSetAttribute(panel_pair_full_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 5 * tile));
     const int bchunk = std::min(batch, 65535);
     slab_status st;
     if ((st = ensure_panel_work(h, 2 * (size_t)bchunk * TL * TL * sizeof(T)))) return st;   // L^-1 of two panels
