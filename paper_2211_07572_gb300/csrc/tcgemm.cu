@@ -140,7 +140,7 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
 
 template <int BN, bool SPLIT>
 struct TcCfg {
-    static constexpr int STAGES = SPLIT ? 3 : 5;
+    static constexpr int STAGES = SPLIT ? (BN <= 32 ? 5 : (BN <= 64 ? 4 : 3)) : 5;   // as many as fit in 227 KB
     static constexpr int A_BYTES = BM * BK * 4;
     static constexpr int B_BYTES = BN * BK * 4;
     static constexpr int STAGE_BYTES = (SPLIT ? 2 : 1) * (A_BYTES + B_BYTES);
@@ -1147,6 +1147,8 @@ slab_status tc_gemm(cudaStream_t st, TcGemmArgs& g, unsigned* err) {
         if (narrow) return launch_f16x3<64>(st, g, err);
         return f16x3_use_wide(g) ? launch_f16x3<256>(st, g, err) : launch_f16x3<128>(st, g, err);
     }
+    // few right-hand sides (the solve products): 32-wide tiles leave room for a fifth stage in flight
+    if (g.split && g.N <= 32) return launch_tc<32, true>(st, g, err);
     if (g.split) return narrow ? launch_tc<64, true>(st, g, err) : launch_tc<128, true>(st, g, err);
     return narrow ? launch_tc<64, false>(st, g, err) : launch_tc<128, false>(st, g, err);
 }
