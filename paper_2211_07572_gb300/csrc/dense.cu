@@ -736,12 +736,12 @@ slab_status launch_skinny(slab_handle* h, int M, int N, int K, float alpha, cons
 // C = beta C + alpha A B^T on the unit of this precision: tensor cores for FP32, SIMT for FP64.
 template <typename T>
 slab_status gemm_tn(slab_handle* h, int cls, int M, int N, int K, T alpha, const T* A, int64_t lda, const T* B,
-                    int64_t ldb, T beta, T* C, int64_t ldc, int transC, int lower_only);
+                    int64_t ldb, T beta, T* C, int64_t ldc, int transC, int lower_only, int triA = 0);
 
 template <>
 slab_status gemm_tn<float>(slab_handle* h, int cls, int M, int N, int K, float alpha, const float* A, int64_t lda,
                            const float* B, int64_t ldb, float beta, float* C, int64_t ldc, int transC,
-                           int lower_only) {
+                           int lower_only, int triA) {
     SLAB_PROF(h, cls);
     if (skinny_ok(N, K, A, lda, 0, B, ldb, 0, lower_only))
         return launch_skinny(h, M, N, K, alpha, A, lda, 0, B, ldb, 0, beta, C, ldc, 0, transC, 1);
@@ -752,6 +752,7 @@ slab_status gemm_tn<float>(slab_handle* h, int cls, int M, int N, int K, float a
     g.batch = 1; g.sA = g.sB = g.sC = 0;
     g.ksplit = 1; g.part = nullptr;
     g.w16 = nullptr; g.w16_bytes = 0;
+    g.triA = triA;
     if (use_f16x3(h, cls, g)) {
         // FP16 three-product path (factor products)
     } else if (N <= 64 && !lower_only && h->wPart) {     // skinny: split K over CTAs
@@ -813,7 +814,7 @@ __global__ void __launch_bounds__(256) gemv_rows_kernel(int M, int N, int K, T a
 template <>
 slab_status gemm_tn<double>(slab_handle* h, int cls, int M, int N, int K, double alpha, const double* A,
                             int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
-                            int transC, int lower_only) {
+                            int transC, int lower_only, int /*triA: the FP64 products read all of A*/) {
     if (N <= 8 && !lower_only && M > 0) {
         SLAB_PROF(h, cls);
         gemv_rows_kernel<double, 8><<<(M + 7) / 8, 256, 0, h->stream>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc,
@@ -1190,12 +1191,12 @@ __global__ void gj_init_rows_kernel(int* act, int* pflag, int sp) {
 template <typename T>
 slab_status gemm_tn_batched(slab_handle* h, int cls, int M, int N, int K, T alpha, const T* A, int64_t lda,
                             int64_t sA, const T* B, int64_t ldb, int64_t sB, T beta, T* C, int64_t ldc,
-                            int64_t sC, int transC, int lower_only, int batch);
+                            int64_t sC, int transC, int lower_only, int batch, int triA = 0);
 
 template <>
 slab_status gemm_tn_batched<float>(slab_handle* h, int cls, int M, int N, int K, float alpha, const float* A,
                                    int64_t lda, int64_t sA, const float* B, int64_t ldb, int64_t sB, float beta,
-                                   float* C, int64_t ldc, int64_t sC, int transC, int lower_only, int batch) {
+                                   float* C, int64_t ldc, int64_t sC, int transC, int lower_only, int batch, int triA) {
     // a factor product whose operand splits do not fit the FP16 work buffer runs on slices of the
     // batch that do, rather than falling back to the slower 3xTF32 product
     if (batch > 1 && h->w16 && !h->tf32_now && K % 64 == 0 &&
@@ -1209,7 +1210,7 @@ slab_status gemm_tn_batched<float>(slab_handle* h, int cls, int M, int N, int K,
                     const int nb = std::min(bc, batch - b0);
                     const slab_status st = gemm_tn_batched<float>(h, cls, M, N, K, alpha, A + b0 * sA, lda, sA,
                                                                   B + b0 * sB, ldb, sB, beta, C + b0 * sC, ldc, sC,
-                                                                  transC, lower_only, nb);
+                                                                  transC, lower_only, nb, triA);
                     if (st) return st;
                 }
                 return SLAB_OK;
@@ -1226,6 +1227,7 @@ slab_status gemm_tn_batched<float>(slab_handle* h, int cls, int M, int N, int K,
     g.batch = batch; g.sA = sA; g.sB = sB; g.sC = sC;
     g.ksplit = 1; g.part = nullptr;
     g.w16 = nullptr; g.w16_bytes = 0;
+    g.triA = triA;
     if (use_f16x3(h, cls, g)) {
         // FP16 three-product path (factor products)
     } else if (N <= 64 && !lower_only && h->wPart) {     // skinny batches that leave SMs idle: split K as well
@@ -1248,7 +1250,7 @@ template <>
 slab_status gemm_tn_batched<double>(slab_handle* h, int cls, int M, int N, int K, double alpha, const double* A,
                                     int64_t lda, int64_t sA, const double* B, int64_t ldb, int64_t sB,
                                     double beta, double* C, int64_t ldc, int64_t sC, int transC, int lower_only,
-                                    int batch) {
+                                    int batch, int /*triA*/) {
     SLAB_PROF(h, cls);
     dim3 grid((N + TL - 1) / TL, (M + TL - 1) / TL, batch);
     gemm_tn_kernel<double><<<grid, 256, 0, h->stream>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, transC,
@@ -1499,7 +1501,8 @@ slab_status sweep_solve(slab_handle* h, int K) {
             if ((st = gemm_tn<T>(h, KC_SOLVE_PROD, sp, K, sp, T(-1), Yt, sp, Z + (j - 1) * vb, sp, T(1), X + j * vb, sp, 1, 0)))
                 return st;
         }
-        if ((st = gemm_tn<T>(h, KC_SOLVE_PROD, sp, K, sp, T(1), Lin + j * blk, sp, X + j * vb, sp, T(0), Z + j * vb, sp, 1, 0)))
+        if ((st = gemm_tn<T>(h, KC_SOLVE_PROD, sp, K, sp, T(1), Lin + j * blk, sp, X + j * vb, sp, T(0), Z + j * vb, sp, 1, 0,
+                             1)))                 // L^{-1} is lower triangular
             return st;
     }
     for (int j = NI - 1; j >= 0; --j) {   // backward: u_j = L_j^{-T} (z_j - Y_j u_{j+1})
@@ -1509,7 +1512,9 @@ slab_status sweep_solve(slab_handle* h, int K) {
                 return st;
         }
         const T* LT = F + j * 3 * blk + (j < NI - 1 ? 2 : 1) * blk;
-        if ((st = gemm_tn<T>(h, KC_SOLVE_PROD, sp, K, sp, T(1), LT, sp, Z + j * vb, sp, T(0), X + j * vb, sp, 1, 0))) return st;
+        if ((st = gemm_tn<T>(h, KC_SOLVE_PROD, sp, K, sp, T(1), LT, sp, Z + j * vb, sp, T(0), X + j * vb, sp, 1, 0,
+                             2)))                 // L^{-T} is upper triangular
+            return st;
     }
     return SLAB_OK;
 }
@@ -1660,14 +1665,15 @@ slab_status cr_solve(slab_handle* h, int K) {
     const std::vector<CrLevel> levels = cr_levels(NI, &last);
     slab_status st;
     // out_i (K x sp, RHS-major) = beta out_i + alpha M_i v_i for the nbat strided blocks i;
-    // a single product takes the split-K path
+    // a single product takes the split-K path; L^{-1} (lower) and L^{-T} (upper) are triangular
+#define TRI(Mx) ((Mx) == Lin ? 1 : ((Mx) == LT ? 2 : 0))
 #define PROD(Mx, m0, V, v0, OUT, w0, alpha_, beta_, nbat, sm, sv)                                                   \
     if ((st = (nbat) == 1                                                                                          \
                   ? gemm_tn<T>(h, KC_SOLVE_PROD, sp, K, sp, T(alpha_), Mx + (m0) * blk, sp, V + (v0) * vb, sp,      \
-                               T(beta_), OUT + (w0) * vb, sp, 1, 0)                                               \
+                               T(beta_), OUT + (w0) * vb, sp, 1, 0, TRI(Mx))                                      \
                   : gemm_tn_batched<T>(h, KC_SOLVE_PROD, sp, K, sp, T(alpha_), Mx + (m0) * blk, sp, (sm) * blk,    \
                                        V + (v0) * vb, sp, (sv) * vb, T(beta_), OUT + (w0) * vb, sp, (sv) * vb, 1, \
-                                       0, (nbat))))                                                                \
+                                       0, (nbat), TRI(Mx))))                                                       \
     return st
     for (const CrLevel& lv : levels) {
         const int o0 = lv.o0, a0 = lv.o0 - lv.step, c0 = lv.o0 + lv.step, s2 = 2 * lv.step;
@@ -1685,6 +1691,7 @@ slab_status cr_solve(slab_handle* h, int K) {
         PROD(LT, o0, Z, o0, X, o0, 1, 0, lv.nb, s2, s2);
     }
 #undef PROD
+#undef TRI
     return SLAB_OK;
 }
 
@@ -1744,11 +1751,11 @@ static slab_status ensure_panel_work(slab_handle* h, size_t bytes) {
 template <typename T>
 slab_status dense_gemm(slab_handle* h, int cls, int M, int N, int K, T alpha, const T* A, int64_t lda, int64_t sA,
                        const T* B, int64_t ldb, int64_t sB, T beta, T* C, int64_t ldc, int64_t sC, int transC,
-                       int lower_only, int batch) {
+                       int lower_only, int batch, int triA) {
     if (batch <= 0 || M <= 0 || N <= 0) return SLAB_OK;
-    if (batch == 1) return gemm_tn<T>(h, cls, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, transC, lower_only);
+    if (batch == 1) return gemm_tn<T>(h, cls, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, transC, lower_only, triA);
     return gemm_tn_batched<T>(h, cls, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, transC, lower_only,
-                              batch);
+                              batch, triA);
 }
 
 template <typename T>
@@ -1944,10 +1951,10 @@ slab_status dense_tall_cholesky(slab_handle* h, T* W, int ncols, int ident0, int
 }
 
 template slab_status dense_gemm<float>(slab_handle*, int, int, int, int, float, const float*, int64_t, int64_t,
-                                       const float*, int64_t, int64_t, float, float*, int64_t, int64_t, int, int, int);
+                                       const float*, int64_t, int64_t, float, float*, int64_t, int64_t, int, int, int, int);
 template slab_status dense_gemm<double>(slab_handle*, int, int, int, int, double, const double*, int64_t, int64_t,
                                         const double*, int64_t, int64_t, double, double*, int64_t, int64_t, int, int,
-                                        int);
+                                        int, int);
 template slab_status dense_transpose<float>(slab_handle*, const float*, int64_t, int64_t, float*, int64_t, int64_t,
                                             int, int, int);
 template slab_status dense_transpose<double>(slab_handle*, const double*, int64_t, int64_t, double*, int64_t,

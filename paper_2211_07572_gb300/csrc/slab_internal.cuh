@@ -280,7 +280,7 @@ template <typename T> slab_status tree3d_import(slab_handle* h, const double* in
 template <typename T>
 slab_status dense_gemm(slab_handle* h, int cls, int M, int N, int K, T alpha, const T* A, int64_t lda, int64_t sA,
                        const T* B, int64_t ldb, int64_t sB, T beta, T* C, int64_t ldc, int64_t sC, int transC,
-                       int lower_only, int batch);
+                       int lower_only, int batch, int triA = 0);
 template <typename T>
 slab_status dense_transpose(slab_handle* h, const T* in, int64_t ldin, int64_t sin, T* out, int64_t ldout,
                             int64_t sout, int rows, int cols, int batch);
@@ -310,6 +310,8 @@ struct TcGemmArgs {
     float* part;
     void* w16;           // split 2: operand splits and exponents, f16x3_work_bytes(M, N, K, batch, shared)
     size_t w16_bytes;
+    int triA = 0;        // splits 0 / 1: 1 A lower triangular (A[m][k] = 0 for k > m), 2 A upper (k < m):
+                         // the K range of every 128-row tile is cut to the nonzero part
 };
 // Work bytes of the split-2 product; shared: B is the first N rows of A (one split serves both).
 size_t f16x3_work_bytes(int64_t M, int64_t N, int64_t K, int batch, bool shared);

@@ -152,7 +152,7 @@ template <int BN, bool SPLIT>
 __global__ void __launch_bounds__(256, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N,
                    int K, float alpha, float beta, float* C, int64_t ldc, int64_t c_bstride, int transC,
-                   int lower_only, int ksplit, float* part, unsigned* err) {
+                   int lower_only, int triA, int ksplit, float* part, unsigned* err) {
     using Cfg = TcCfg<BN, SPLIT>;
     constexpr int STAGES = Cfg::STAGES;
     pdl_wait();
@@ -168,8 +168,11 @@ __global__ void __launch_bounds__(256, 1)
     const int bz = (int)blockIdx.z / ksplit;
     if (lower_only && bn * BN >= (bm + 1) * BM) return;        // tile strictly above the diagonal
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nk = K / ksplit / BK;
-    const int k0 = zs * nk * BK;
+    // K range of this split, cut to the nonzero part of a triangular A (all bounds multiples of BK)
+    int k0 = zs * (K / ksplit), k1 = k0 + K / ksplit;
+    if (triA == 1) k1 = min(k1, (bm + 1) * BM);
+    else if (triA == 2) k0 = max(k0, bm * BM);
+    const int nk = k1 > k0 ? (k1 - k0) / BK : 0;        // 0: the tile's product is zero
     uint8_t* base = (uint8_t*)(((uintptr_t)tc_smem + 1023) & ~(uintptr_t)1023);
     auto a_hi = [&](int s) { return base + s * Cfg::STAGE_BYTES; };
     auto b_hi = [&](int s) { return base + s * Cfg::STAGE_BYTES + Cfg::A_BYTES; };
@@ -237,7 +240,7 @@ __global__ void __launch_bounds__(256, 1)
                 }
                 mma_commit(&empty_bar[s]);
             }
-            if (ok) mma_commit(&done_bar);
+            if (ok && nk > 0) mma_commit(&done_bar);
         }
     } else if (warp >= 4) {
         if (SPLIT) {                                             // hi/lo split of each landed stage
@@ -284,7 +287,7 @@ __global__ void __launch_bounds__(256, 1)
             }
         }
         // epilogue: TMEM lanes 32*(warp-4) .. +31 are rows of the tile
-        const bool ok = !abort_flag && mbar_wait(&done_bar, 0);
+        const bool ok = !abort_flag && (nk == 0 || mbar_wait(&done_bar, 0));
         if (!ok) {
             abort_flag = 1;
             atomicOr(err, 2u);
@@ -297,7 +300,10 @@ __global__ void __launch_bounds__(256, 1)
 #pragma unroll 1
             for (int cc = 0; cc < BN / 32; ++cc) {
                 float v[32];
-                tmem_ld32(tmem + ((uint32_t)(rw * 32) << 16) + (uint32_t)(cc * 32), v);
+                if (nk > 0) tmem_ld32(tmem + ((uint32_t)(rw * 32) << 16) + (uint32_t)(cc * 32), v);
+                else
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) v[j] = 0.f;
                 if (!transC && ksplit == 1) {
                     // row-major C: stage the 32 x 32 block, then each lane walks a column of it so
                     // a warp instruction covers 32 consecutive floats of one row of C; all 32 old
@@ -414,7 +420,7 @@ slab_status launch_tc(cudaStream_t st, const TcGemmArgs& g, unsigned* err) {
     const int ks = g.ksplit > 1 ? g.ksplit : 1;
     dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, ks * g.batch);
     if (launch_pdl(tc_gemm_kernel<BN, SPLIT>, grid, dim3(256), (size_t)smem, st, ta, tb, g.M, g.N, g.K, g.alpha, g.beta,
-                   g.C, g.ldc, g.sC, g.transC, g.lower_only, ks, g.part, err) != cudaSuccess) {
+                   g.C, g.ldc, g.sC, g.transC, g.lower_only, g.triA, ks, g.part, err) != cudaSuccess) {
         cudaGetLastError();
         return SLAB_ECUDA;
     }

@@ -629,9 +629,9 @@ slab_status tree3d_up_gather(slab_handle* h, const double* F, double fscale, int
                                      h->stream>>>(a, V, F, fscale, G, g);
             SLAB_CK_LAUNCH(h);
         }
-        // y = L^{-1} g
+        // y = L^{-1} g  (L^{-1} lower triangular: each row tile reads only its nonzero part)
         if ((st = dense_gemm<T>(h, KC_TREE_UP, Mp, K, Mp, T(1), (T*)h->t3Lin + n0 * mm, Mp, mm, g + n0 * kc * Mp, Mp,
-                                (int64_t)kc * Mp, T(0), y + n0 * kc * Mp, Mp, (int64_t)kc * Mp, 1, 0, B)))
+                                (int64_t)kc * Mp, T(0), y + n0 * kc * Mp, Mp, (int64_t)kc * Mp, 1, 0, B, 1)))
             return st;
         // G = -Z_tb^T y (+ children's outer loads)
         if ((st = dense_gemm<T>(h, KC_TREE_UP, 2 * Mp, K, Mp, T(-1), (T*)h->t3ZtbT + n0 * 2 * mm, Mp, 2 * mm,
@@ -708,7 +708,7 @@ slab_status tree3d_down_scatter(slab_handle* h, double* U, int accumulate, int r
                                 (int64_t)kc * Mp, 1, 0, B)))
             return st;
         if ((st = dense_gemm<T>(h, KC_TREE_DOWN, Mp, K, Mp, T(1), (T*)h->t3LT + n0 * mm, Mp, mm, y + n0 * kc * Mp, Mp,
-                                (int64_t)kc * Mp, T(0), X + n0 * kc * Mp, Mp, (int64_t)kc * Mp, 1, 0, B)))
+                                (int64_t)kc * Mp, T(0), X + n0 * kc * Mp, Mp, (int64_t)kc * Mp, 1, 0, B, 2)))
             return st;
         {
             SLAB_PROF(h, KC_TREE_DOWN);
