@@ -580,38 +580,54 @@ __global__ void __launch_bounds__(256) panel_pair_full_kernel(T* Wt, int64_t ld,
         for (int b = 0; b < 4; ++b) dst[(int64_t)(ty + 16 * a) * ld + tx + 16 * b] = p[a][b];
 }
 
+// B = I (s_pad x s_pad): blockIdx.y is the row, threads run over its columns (coalesced stores, no
+// index division).
 template <typename T>
 __global__ void set_identity_kernel(T* B, int s_pad) {
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)s_pad * s_pad) return;
-    B[idx] = (idx / s_pad == idx % s_pad) ? T(1) : T(0);
+    T* row = B + (int64_t)blockIdx.y * s_pad;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < s_pad; c += gridDim.x * blockDim.x)
+        row[c] = (c == (int)blockIdx.y) ? T(1) : T(0);
 }
 
-// out = in^T for an n x n block (both row-major, leading dimension n), 32 x 32 smem tiles;
-// blockIdx.z selects one of a batch of blocks sin / sout elements apart.
+// out[c][r] = in[r][c] for the 64 x 64 tile (blockIdx.y, blockIdx.x) of a rows x cols block, 256
+// threads: every thread issues its 16 loads (rows of in, coalesced) before its first shared store,
+// then writes 16 elements (rows of out, coalesced).  tile[.][65]: column reads are conflict-free.
 template <typename T>
-__global__ void transpose_kernel(const T* __restrict__ in, T* __restrict__ out, int n, int64_t sin, int64_t sout) {
-    __shared__ T tile[32][33];
-    in += (int64_t)blockIdx.z * sin;
-    out += (int64_t)blockIdx.z * sout;
-    const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
-    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
-        const int r = by + j, c = bx + threadIdx.x;
-        if (r < n && c < n) tile[j][threadIdx.x] = in[(int64_t)r * n + c];
+__device__ __forceinline__ void transpose_tile64(const T* __restrict__ in, int64_t ldin, T* __restrict__ out,
+                                                 int64_t ldout, int rows, int cols) {
+    __shared__ T tile[64][65];
+    const int c0 = blockIdx.x * 64, r0 = blockIdx.y * 64;
+    const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;
+    T v[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        const int r = r0 + ty + 4 * q, c = c0 + tx;
+        v[q] = (r < rows && c < cols) ? in[(int64_t)r * ldin + c] : T(0);
     }
+#pragma unroll
+    for (int q = 0; q < 16; ++q) tile[ty + 4 * q][tx] = v[q];
     __syncthreads();
-    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
-        const int r = bx + j, c = by + threadIdx.x;
-        if (r < n && c < n) out[(int64_t)r * n + c] = tile[threadIdx.x][j];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        const int c = c0 + ty + 4 * q, r = r0 + tx;
+        if (r < rows && c < cols) out[(int64_t)c * ldout + r] = tile[tx][ty + 4 * q];
     }
+}
+
+// out = in^T for an n x n block (both row-major, leading dimension n); blockIdx.z selects one of a
+// batch of blocks sin / sout elements apart.
+template <typename T>
+__global__ void __launch_bounds__(256) transpose_kernel(const T* __restrict__ in, T* __restrict__ out, int n,
+                                                        int64_t sin, int64_t sout) {
+    transpose_tile64<T>(in + (int64_t)blockIdx.z * sin, n, out + (int64_t)blockIdx.z * sout, n, n, n);
 }
 
 template <typename T>
 slab_status transpose_batched(slab_handle* h, const T* in, int64_t sin, T* out, int64_t sout, int n, int batch) {
     if (batch <= 0) return SLAB_OK;
-    dim3 grid((n + 31) / 32, (n + 31) / 32, batch);
+    dim3 grid((n + 63) / 64, (n + 63) / 64, batch);
     SLAB_PROF(h, KC_OTHER);
-    transpose_kernel<T><<<grid, dim3(32, 8), 0, h->stream>>>(in, out, n, sin, sout);
+    transpose_kernel<T><<<grid, 256, 0, h->stream>>>(in, out, n, sin, sout);
     SLAB_CK_LAUNCH(h);
     return SLAB_OK;
 }
@@ -1469,7 +1485,7 @@ slab_status sweep_factor(slab_handle* h) {
         }
         {
             SLAB_PROF(h, KC_OTHER);
-            set_identity_kernel<T><<<(unsigned)((blk + 255) / 256), 256, 0, h->stream>>>(LT, sp);
+            set_identity_kernel<T><<<dim3((unsigned)((sp + 255) / 256), sp), 256, 0, h->stream>>>(LT, sp);
         }
         SLAB_CK_LAUNCH(h);
         if (hasY && (st = transpose<T>(h, To + j * blk, Yt, sp))) return st;      // T_{j+1,j}
@@ -1563,10 +1579,9 @@ int cr_max_batch(int NI) {
 
 template <typename T>
 __global__ void set_identity_batched_kernel(T* B, int s_pad, int64_t stride) {
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t n2 = (int64_t)s_pad * s_pad;
-    if (idx >= n2) return;
-    B[(int64_t)blockIdx.y * stride + idx] = (idx / s_pad == idx % s_pad) ? T(1) : T(0);
+    T* row = B + (int64_t)blockIdx.z * stride + (int64_t)blockIdx.y * s_pad;      // blockIdx.y: row
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < s_pad; c += gridDim.x * blockDim.x)
+        row[c] = (c == (int)blockIdx.y) ? T(1) : T(0);
 }
 
 // Cholesky with L^{-1} and L^{-T} of nb blocks D[o0 + i st] as one batch of tall eliminations
@@ -1585,8 +1600,8 @@ static slab_status cr_potrf_batch(slab_handle* h, int o0, int st_blk, int nb) {
                                    h->stream));
     {
         SLAB_PROF(h, KC_OTHER);
-        set_identity_batched_kernel<T><<<dim3((unsigned)((blk + 255) / 256), nb), 256, 0, h->stream>>>(W + blk, sp,
-                                                                                                      2 * blk);
+        set_identity_batched_kernel<T><<<dim3((unsigned)((sp + 255) / 256), sp, nb), 256, 0, h->stream>>>(W + blk, sp,
+                                                                                                        2 * blk);
     }
     SLAB_CK_LAUNCH(h);
     slab_status st;
@@ -1708,21 +1723,10 @@ template slab_status cr_solve<double>(slab_handle*, int);
 namespace {
 // out[c][r] = in[r][c] for a rows x cols block (leading dimensions ldin, ldout), batched by blockIdx.z
 template <typename T>
-__global__ void transpose_rect_kernel(const T* __restrict__ in, int64_t ldin, int64_t sin, T* __restrict__ out,
-                                      int64_t ldout, int64_t sout, int rows, int cols) {
-    __shared__ T tile[32][33];
-    in += (int64_t)blockIdx.z * sin;
-    out += (int64_t)blockIdx.z * sout;
-    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
-    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
-        const int r = r0 + j, c = c0 + threadIdx.x;
-        if (r < rows && c < cols) tile[j][threadIdx.x] = in[(int64_t)r * ldin + c];
-    }
-    __syncthreads();
-    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
-        const int c = c0 + j, r = r0 + threadIdx.x;
-        if (r < rows && c < cols) out[(int64_t)c * ldout + r] = tile[threadIdx.x][j];
-    }
+__global__ void __launch_bounds__(256) transpose_rect_kernel(const T* __restrict__ in, int64_t ldin, int64_t sin,
+                                                             T* __restrict__ out, int64_t ldout, int64_t sout,
+                                                             int rows, int cols) {
+    transpose_tile64<T>(in + (int64_t)blockIdx.z * sin, ldin, out + (int64_t)blockIdx.z * sout, ldout, rows, cols);
 }
 
 template <typename T>
@@ -1731,6 +1735,24 @@ __global__ void copy_batched_kernel(const T* __restrict__ in, int64_t sin, T* __
     in += (int64_t)blockIdx.y * sin;
     out += (int64_t)blockIdx.y * sout;
     for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256) out[i] = in[i];
+}
+
+// The same copy in 16-byte units (both blocks 16-byte aligned, strides and length multiples of 16
+// bytes), four loads in flight per thread before their stores.
+__global__ void copy16_batched_kernel(const uint4* __restrict__ in, int64_t sin, uint4* __restrict__ out, int64_t sout,
+                                      int64_t n) {
+    in += (int64_t)blockIdx.y * sin;
+    out += (int64_t)blockIdx.y * sout;
+    const int64_t stride = (int64_t)gridDim.x * 256;
+    int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    for (; i + 3 * stride < n; i += 4 * stride) {
+        uint4 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = in[i + u * stride];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) out[i + u * stride] = v[u];
+    }
+    for (; i < n; i += stride) out[i] = in[i];
 }
 }  // namespace
 
@@ -1764,10 +1786,10 @@ slab_status dense_transpose(slab_handle* h, const T* in, int64_t ldin, int64_t s
     if (batch <= 0 || rows <= 0 || cols <= 0) return SLAB_OK;
     for (int b0 = 0; b0 < batch; b0 += 65535) {
         const int nb = std::min(65535, batch - b0);
-        dim3 grid((cols + 31) / 32, (rows + 31) / 32, nb);
+        dim3 grid((cols + 63) / 64, (rows + 63) / 64, nb);
         SLAB_PROF(h, KC_OTHER);
-        transpose_rect_kernel<T><<<grid, dim3(32, 8), 0, h->stream>>>(in + b0 * sin, ldin, sin, out + b0 * sout,
-                                                                      ldout, sout, rows, cols);
+        transpose_rect_kernel<T><<<grid, 256, 0, h->stream>>>(in + b0 * sin, ldin, sin, out + b0 * sout, ldout, sout,
+                                                              rows, cols);
         SLAB_CK_LAUNCH(h);
     }
     return SLAB_OK;
@@ -1779,8 +1801,19 @@ slab_status dense_copy(slab_handle* h, const T* in, int64_t sin, T* out, int64_t
     for (int b0 = 0; b0 < batch; b0 += 65535) {
         const int nb = std::min(65535, batch - b0);
         SLAB_PROF(h, KC_OTHER);
-        copy_batched_kernel<T><<<dim3((unsigned)std::min<int64_t>((n + 255) / 256, 64), nb), 256, 0, h->stream>>>(
-            in + b0 * sin, sin, out + b0 * sout, sout, n);
+        const T* ib = in + b0 * sin;
+        T* ob = out + b0 * sout;
+        const bool v16 = ((uintptr_t)ib % 16 == 0) && ((uintptr_t)ob % 16 == 0) && (sin * sizeof(T)) % 16 == 0 &&
+                         (sout * sizeof(T)) % 16 == 0 && (n * sizeof(T)) % 16 == 0;
+        if (v16) {
+            const int64_t n16 = n * (int64_t)sizeof(T) / 16;
+            copy16_batched_kernel<<<dim3((unsigned)std::min<int64_t>((n16 + 1023) / 1024, 64), nb), 256, 0,
+                                    h->stream>>>((const uint4*)ib, sin * (int64_t)sizeof(T) / 16, (uint4*)ob,
+                                                 sout * (int64_t)sizeof(T) / 16, n16);
+        } else {
+            copy_batched_kernel<T><<<dim3((unsigned)std::min<int64_t>((n + 255) / 256, 64), nb), 256, 0,
+                                     h->stream>>>(ib, sin, ob, sout, n);
+        }
         SLAB_CK_LAUNCH(h);
     }
     return SLAB_OK;
