@@ -580,13 +580,25 @@ __global__ void __launch_bounds__(256) panel_pair_full_kernel(T* Wt, int64_t ld,
         for (int b = 0; b < 4; ++b) dst[(int64_t)(ty + 16 * a) * ld + tx + 16 * b] = p[a][b];
 }
 
-// B = I (s_pad x s_pad): blockIdx.y is the row, threads run over its columns (coalesced stores, no
-// index division).
+// Ones on the diagonal of the s_pad x s_pad block B (blockIdx.y selects one of a batch, stride apart);
+// the zeros come from a memset before it.
 template <typename T>
-__global__ void set_identity_kernel(T* B, int s_pad) {
-    T* row = B + (int64_t)blockIdx.y * s_pad;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < s_pad; c += gridDim.x * blockDim.x)
-        row[c] = (c == (int)blockIdx.y) ? T(1) : T(0);
+__global__ void set_diagonal_kernel(T* B, int s_pad, int64_t stride) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < s_pad) B[(int64_t)blockIdx.y * stride + (int64_t)i * (s_pad + 1)] = T(1);
+}
+
+// B = I for nb blocks of s_pad x s_pad, stride elements apart: a memset of each block (full
+// bandwidth) and one launch for the diagonals.
+template <typename T>
+slab_status set_identity(slab_handle* h, T* B, int s_pad, int64_t stride, int nb) {
+    const int64_t blk = (int64_t)s_pad * s_pad;
+    if (stride == blk) SLAB_CK(h, cudaMemsetAsync(B, 0, (size_t)nb * blk * sizeof(T), h->stream));
+    else
+        for (int i = 0; i < nb; ++i) SLAB_CK(h, cudaMemsetAsync(B + i * stride, 0, blk * sizeof(T), h->stream));
+    set_diagonal_kernel<T><<<dim3((unsigned)((s_pad + 255) / 256), nb), 256, 0, h->stream>>>(B, s_pad, stride);
+    SLAB_CK_LAUNCH(h);
+    return SLAB_OK;
 }
 
 // out[c][r] = in[r][c] for the 64 x 64 tile (blockIdx.y, blockIdx.x) of a rows x cols block, 256
@@ -1485,9 +1497,8 @@ slab_status sweep_factor(slab_handle* h) {
         }
         {
             SLAB_PROF(h, KC_OTHER);
-            set_identity_kernel<T><<<dim3((unsigned)((sp + 255) / 256), sp), 256, 0, h->stream>>>(LT, sp);
+            if ((st = set_identity<T>(h, LT, sp, blk, 1))) return st;
         }
-        SLAB_CK_LAUNCH(h);
         if (hasY && (st = transpose<T>(h, To + j * blk, Yt, sp))) return st;      // T_{j+1,j}
         const int lt0 = (hasY ? 2 : 1) * sp;         // first row of the identity block
         if ((st = dense_tall_cholesky<T>(h, W, sp, lt0, 1, 0))) return st;
@@ -1577,13 +1588,6 @@ int cr_max_batch(int NI) {
     return b;
 }
 
-template <typename T>
-__global__ void set_identity_batched_kernel(T* B, int s_pad, int64_t stride) {
-    T* row = B + (int64_t)blockIdx.z * stride + (int64_t)blockIdx.y * s_pad;      // blockIdx.y: row
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < s_pad; c += gridDim.x * blockDim.x)
-        row[c] = (c == (int)blockIdx.y) ? T(1) : T(0);
-}
-
 // Cholesky with L^{-1} and L^{-T} of nb blocks D[o0 + i st] as one batch of tall eliminations
 // [D ; I] in the work buffer (2 s_pad x s_pad per block).
 template <typename T>
@@ -1598,13 +1602,11 @@ static slab_status cr_potrf_batch(slab_handle* h, int o0, int st_blk, int nb) {
     for (int i = 0; i < nb; ++i)
         SLAB_CK(h, cudaMemcpyAsync(W + i * 2 * blk, D + o0 * blk + i * sb, blk * sizeof(T), cudaMemcpyDeviceToDevice,
                                    h->stream));
+    slab_status st;
     {
         SLAB_PROF(h, KC_OTHER);
-        set_identity_batched_kernel<T><<<dim3((unsigned)((sp + 255) / 256), sp, nb), 256, 0, h->stream>>>(W + blk, sp,
-                                                                                                        2 * blk);
+        if ((st = set_identity<T>(h, W + blk, sp, 2 * blk, nb))) return st;
     }
-    SLAB_CK_LAUNCH(h);
-    slab_status st;
     if ((st = dense_tall_cholesky<T>(h, W, sp, sp, nb, 2 * blk))) return st;
     for (int i = 0; i < nb; ++i)
         SLAB_CK(h, cudaMemcpyAsync(LT + o0 * blk + i * sb, W + i * 2 * blk + blk, blk * sizeof(T),
