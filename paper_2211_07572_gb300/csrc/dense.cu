@@ -27,6 +27,7 @@ namespace {
 
 constexpr int TL = SLAB_TILE;   // 64
 constexpr int TLP = TL + 1;
+constexpr int PTP = TL + 4;      // row pitch of the panel kernels' tiles: 16-byte rows, rows four banks apart
 
 // C(64x64) += op(A) op(B) over [k0, k1) (multiple of 16); 256 threads, 4x4 per thread.
 // op(A)(i,k) = TA ? A[k*lda+i] : A[i*lda+k];  op(B)(k,j) = TB ? B[j*ldb+k] : B[k*ldb+j].
@@ -145,8 +146,8 @@ __global__ void __launch_bounds__(256) gemm_tn_skinny_kernel(int M, int N, int K
     if (tid == 0) tickets[bi] = 0;
 }
 
-// Cholesky L L^T = S of the 64 x 64 tile S (smem, stride TLP; lower triangle read) and
-// Li = L^{-1} (written to smem, stride TLP), by 256 threads in 4 x 4 register blocks, as one sweep
+// Cholesky L L^T = S of the 64 x 64 tile S (smem, stride PTP; lower triangle read) and
+// Li = L^{-1} (written to smem, stride PTP), by 256 threads in 4 x 4 register blocks, as one sweep
 // of right-looking elimination over [S | I] (16 block steps of 4 columns, two barriers each).
 // Thread (ti, tj), tj <= ti, holds one block: A_ij while column block tj is not yet eliminated,
 // then X_ij, the block of X = L^{-1} under construction (X starts as I).  Block step kt:
@@ -182,7 +183,7 @@ __device__ __forceinline__ void chol_inv_tile(const T* S, T* Li, unsigned* statu
 #pragma unroll
     for (int r = 0; r < 4; ++r)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) blk[r][c] = S[(4 * ti + r) * TLP + 4 * tj + c];
+        for (int c = 0; c < 4; ++c) blk[r][c] = S[(4 * ti + r) * PTP + 4 * tj + c];
     for (int kt = 0; kt < 16; ++kt) {
         if (ti == kt && tj == kt) {               // 4x4 Cholesky and inverse in registers
             T l[4][4], li[4][4];
@@ -278,11 +279,11 @@ __device__ __forceinline__ void chol_inv_tile(const T* S, T* Li, unsigned* statu
 #pragma unroll
     for (int r = 0; r < 4; ++r)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) Li[(4 * ti + r) * TLP + 4 * tj + c] = (tj <= ti) ? blk[r][c] : T(0);
+        for (int c = 0; c < 4; ++c) Li[(4 * ti + r) * PTP + 4 * tj + c] = (tj <= ti) ? blk[r][c] : T(0);
     __syncthreads();
 }
 
-// Stage a 64 x 64 tile (row stride ld) in registers, then in shared memory (row stride TLP); 256
+// Stage a 64 x 64 tile (row stride ld) in registers, then in shared memory (row stride PTP); 256
 // threads.  Every global load of a thread is issued before its first shared store, so a tile costs
 // one memory round trip instead of one per element the thread copies.
 constexpr int TPT = TL * TL / 256;     // elements of a tile per thread
@@ -299,7 +300,39 @@ __device__ __forceinline__ void tile_stash(const T (&v)[TPT], T* dst) {
 #pragma unroll
     for (int q = 0; q < TPT; ++q) {
         const int i = threadIdx.x + 256 * q;
-        dst[(i / TL) * TLP + i % TL] = v[q];
+        dst[(i / TL) * PTP + i % TL] = v[q];
+    }
+}
+
+// Four consecutive shared-memory values, 16-byte aligned: one 128-bit load (float), two (double).
+__device__ __forceinline__ void ld4(const float* p, float v[4]) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double v[4]) {
+    const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+
+// acc[a][b] += sum_l X[ty + 16 a][l] Y[tx + 16 b][l] for 64 x 64 tiles X, Y in shared memory (row
+// pitch PTP, 16-byte aligned), four l at a time: eight vector loads per 64 FMAs; the 16 rows
+// tx + 16 b of a warp's loads are PTP = 68 words apart, so a phase of eight lanes hits eight
+// distinct bank quads.
+template <typename T>
+__device__ __forceinline__ void tile_nt(const T* X, const T* Y, T acc[4][4], int ty, int tx) {
+#pragma unroll 4
+    for (int l = 0; l < TL; l += 4) {
+        T av[4][4], bv[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) ld4(X + (ty + 16 * a) * PTP + l, av[a]);
+#pragma unroll
+        for (int b = 0; b < 4; ++b) ld4(Y + (tx + 16 * b) * PTP + l, bv[b]);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] += av[a][u] * bv[b][u];
     }
 }
 
@@ -311,9 +344,9 @@ __global__ void __launch_bounds__(256) panel_diag_kernel(const T* Wt, int64_t ld
                                                          int64_t bstride, T* Lw) {
     pdl_wait();
     pdl_trigger();
-    extern __shared__ unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     T* S = reinterpret_cast<T*>(smem_raw);
-    T* Li = S + TL * TLP;
+    T* Li = S + TL * PTP;
     const int tid = threadIdx.x;
     Wt += (int64_t)blockIdx.y * bstride;
     const T* D = Wt + (int64_t)kb * TL * ld + (int64_t)kb * TL;
@@ -325,7 +358,7 @@ __global__ void __launch_bounds__(256) panel_diag_kernel(const T* Wt, int64_t ld
     __syncthreads();
     chol_inv_tile<T>(S, Li, status);
     T* out = Lw + (int64_t)blockIdx.y * TL * TL;
-    for (int i = tid; i < TL * TL; i += 256) out[i] = Li[(i / TL) * TLP + i % TL];
+    for (int i = tid; i < TL * TL; i += 256) out[i] = Li[(i / TL) * PTP + i % TL];
 }
 
 // panel_apply_kernel: CTA x replaces the tile Wt[kb+1+x][kb] by itself times L^{-T}.  DIAG: every
@@ -337,10 +370,10 @@ __global__ void __launch_bounds__(256) panel_apply_kernel(T* Wt, int64_t ld, int
                                                           const T* Lw, unsigned* status) {
     pdl_wait();
     pdl_trigger();
-    extern __shared__ unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     T* Li = reinterpret_cast<T*>(smem_raw);
-    T* X = Li + TL * TLP;
-    T* S = X + TL * TLP;                          // DIAG only: the diagonal tile
+    T* X = Li + TL * PTP;
+    T* S = X + TL * PTP;                          // DIAG only: the diagonal tile
     const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
     const int r = kb + 1 + blockIdx.x;
     Wt += (int64_t)blockIdx.y * bstride;
@@ -360,37 +393,11 @@ __global__ void __launch_bounds__(256) panel_apply_kernel(T* Wt, int64_t ld, int
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
-    for (int l = 0; l < TL; ++l) {        // out = X Li^T
-        T av[4], bv[4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a) av[a] = X[(ty + 16 * a) * TLP + l];
-#pragma unroll
-        for (int b = 0; b < 4; ++b) bv[b] = Li[(tx + 16 * b) * TLP + l];
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
-    }
+    tile_nt<T>(X, Li, acc, ty, tx);       // out = X Li^T
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) src[(int64_t)(ty + 16 * a) * ld + tx + 16 * b] = acc[a][b];
-}
-
-// acc[a][b] += sum_l X[ty + 16 a][l] Y[tx + 16 b][l] for 64 x 64 tiles X, Y in shared memory (stride TLP).
-template <typename T>
-__device__ __forceinline__ void tile_nt(const T* X, const T* Y, T acc[4][4], int ty, int tx) {
-    for (int l = 0; l < TL; ++l) {
-        T av[4], bv[4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a) av[a] = X[(ty + 16 * a) * TLP + l];
-#pragma unroll
-        for (int b = 0; b < 4; ++b) bv[b] = Y[(tx + 16 * b) * TLP + l];
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
-    }
 }
 
 // Two panels kb, kb+1 of the tall Cholesky in one launch after panel_diag_kernel(kb): CTA x owns
@@ -407,12 +414,12 @@ __global__ void __launch_bounds__(256) panel_pair_kernel(T* Wt, int64_t ld, int 
                                                          T* Lw2, unsigned* status) {
     pdl_wait();
     pdl_trigger();
-    extern __shared__ unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     T* Li = reinterpret_cast<T*>(smem_raw);
-    T* X = Li + TL * TLP;
-    T* Y = X + TL * TLP;
-    T* C = Y + TL * TLP;
-    T* S = C + TL * TLP;                          // DIAG only: panel kb's diagonal tile
+    T* X = Li + TL * PTP;
+    T* Y = X + TL * PTP;
+    T* C = Y + TL * PTP;
+    T* S = C + TL * PTP;                          // DIAG only: panel kb's diagonal tile
     const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
     const int r = kb + 1 + blockIdx.x;
     Wt += (int64_t)blockIdx.y * bstride;
@@ -445,8 +452,8 @@ __global__ void __launch_bounds__(256) panel_pair_kernel(T* Wt, int64_t ld, int 
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
-            X[(ty + 16 * a) * TLP + tx + 16 * b] = p[a][b];
-            Y[(ty + 16 * a) * TLP + tx + 16 * b] = q[a][b];
+            X[(ty + 16 * a) * PTP + tx + 16 * b] = p[a][b];
+            Y[(ty + 16 * a) * PTP + tx + 16 * b] = q[a][b];
             if (r != kb + 1) src[(int64_t)(ty + 16 * a) * ld + tx + 16 * b] = p[a][b];
         }
     __syncthreads();
@@ -454,7 +461,7 @@ __global__ void __launch_bounds__(256) panel_pair_kernel(T* Wt, int64_t ld, int 
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) u[a][b] = C[(ty + 16 * a) * TLP + tx + 16 * b];
+        for (int b = 0; b < 4; ++b) u[a][b] = C[(ty + 16 * a) * PTP + tx + 16 * b];
     {
         T pq[4][4];
 #pragma unroll
@@ -478,11 +485,11 @@ __global__ void __launch_bounds__(256) panel_pair_kernel(T* Wt, int64_t ld, int 
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) C[(ty + 16 * a) * TLP + tx + 16 * b] = u[a][b];
+        for (int b = 0; b < 4; ++b) C[(ty + 16 * a) * PTP + tx + 16 * b] = u[a][b];
     __syncthreads();
     chol_inv_tile<T>(C, X, status);                // X := L^{-1} of panel kb+1's diagonal tile
     T* out = Lw2 + (int64_t)blockIdx.y * TL * TL;
-    for (int i = tid; i < TL * TL; i += 256) out[i] = X[(i / TL) * TLP + i % TL];
+    for (int i = tid; i < TL * TL; i += 256) out[i] = X[(i / TL) * PTP + i % TL];
 }
 
 // Panels kb and kb+1 complete in one launch (every CTA factors both diagonal tiles itself): CTA x
@@ -499,12 +506,12 @@ __global__ void __launch_bounds__(256) panel_pair_full_kernel(T* Wt, int64_t ld,
                                                               unsigned* status) {
     pdl_wait();
     pdl_trigger();
-    extern __shared__ unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     T* Li = reinterpret_cast<T*>(smem_raw);
-    T* X = Li + TL * TLP;
-    T* Y = X + TL * TLP;
-    T* C = Y + TL * TLP;
-    T* S = C + TL * TLP;
+    T* X = Li + TL * PTP;
+    T* Y = X + TL * PTP;
+    T* C = Y + TL * PTP;
+    T* S = C + TL * PTP;
     const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
     const int r = kb + 1 + blockIdx.x;
     Wt += (int64_t)blockIdx.y * bstride;
@@ -539,8 +546,8 @@ __global__ void __launch_bounds__(256) panel_pair_full_kernel(T* Wt, int64_t ld,
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
-            X[(ty + 16 * a) * TLP + tx + 16 * b] = p[a][b];
-            Y[(ty + 16 * a) * TLP + tx + 16 * b] = q[a][b];
+            X[(ty + 16 * a) * PTP + tx + 16 * b] = p[a][b];
+            Y[(ty + 16 * a) * PTP + tx + 16 * b] = q[a][b];
             if (r != kb + 1) src[(int64_t)(ty + 16 * a) * ld + tx + 16 * b] = p[a][b];
         }
     __syncthreads();
@@ -555,16 +562,16 @@ __global__ void __launch_bounds__(256) panel_pair_full_kernel(T* Wt, int64_t ld,
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
-            u[a][b] = C[(ty + 16 * a) * TLP + tx + 16 * b] - p[a][b];
-            d[a][b] = S[(ty + 16 * a) * TLP + tx + 16 * b] - q[a][b];
+            u[a][b] = C[(ty + 16 * a) * PTP + tx + 16 * b] - p[a][b];
+            d[a][b] = S[(ty + 16 * a) * PTP + tx + 16 * b] - q[a][b];
         }
     __syncthreads();
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
-            C[(ty + 16 * a) * TLP + tx + 16 * b] = u[a][b];
-            S[(ty + 16 * a) * TLP + tx + 16 * b] = d[a][b];
+            C[(ty + 16 * a) * PTP + tx + 16 * b] = u[a][b];
+            S[(ty + 16 * a) * PTP + tx + 16 * b] = d[a][b];
         }
     __syncthreads();
     chol_inv_tile<T>(S, Li, status);               // L'^{-1}
@@ -1878,7 +1885,7 @@ slab_status tall_panel(slab_handle* h, T* W, int ncols, int ident0, int kb, int 
         const int nb = std::min(65535, batch - b0);
         if (nrt > 0 && one_wave((int64_t)nrt * nb, sizeof(T))) {
             SLAB_PROF(h, KC_PANEL);
-            SLAB_CK(h, launch_pdl(panel_apply_kernel<T, true>, dim3(nrt, nb), dim3(256), smem + TL * TLP * sizeof(T),
+            SLAB_CK(h, launch_pdl(panel_apply_kernel<T, true>, dim3(nrt, nb), dim3(256), smem + TL * PTP * sizeof(T),
                                   h->stream, W + b0 * bstride, (int64_t)ncols, kb, bstride, (const T*)Lw,
                                   h->dstatus));
             SLAB_CK_LAUNCH(h);
@@ -1908,20 +1915,20 @@ template <typename T>
 slab_status tall_pair(slab_handle* h, T* W, int ncols, int ident0, int kb, int batch, int64_t bstride, size_t smem) {
     const int nrt0 = (ident0 + (kb + 1) * TL) / TL - kb - 1;      // row tiles below the diagonal, panel kb
     const int nrt1 = (ident0 + (kb + 2) * TL) / TL - kb - 2;      // and panel kb+1
-    const size_t psmem = 4 * TL * TLP * sizeof(T);
+    const size_t psmem = 4 * TL * PTP * sizeof(T);
     T* Lw = (T*)h->pnl;
     for (int b0 = 0; b0 < batch; b0 += 65535) {
         const int nb = std::min(65535, batch - b0);
         T* Lw2 = Lw + (int64_t)nb * TL * TL;
         SLAB_PROF(h, KC_PANEL);
         if (ident0 % TL == 0 && nrt1 == nrt0 && one_wave((int64_t)(nrt0 + 1) * nb, sizeof(T))) {
-            SLAB_CK(h, launch_pdl(panel_pair_full_kernel<T>, dim3(nrt0 + 1, nb), dim3(256), psmem + TL * TLP * sizeof(T),
+            SLAB_CK(h, launch_pdl(panel_pair_full_kernel<T>, dim3(nrt0 + 1, nb), dim3(256), psmem + TL * PTP * sizeof(T),
                                   h->stream, W + b0 * bstride, (int64_t)ncols, kb, bstride, h->dstatus));
             SLAB_CK_LAUNCH(h);
             continue;
         }
         if (one_wave((int64_t)nrt0 * nb, sizeof(T))) {
-            SLAB_CK(h, launch_pdl(panel_pair_kernel<T, true>, dim3(nrt0, nb), dim3(256), psmem + TL * TLP * sizeof(T),
+            SLAB_CK(h, launch_pdl(panel_pair_kernel<T, true>, dim3(nrt0, nb), dim3(256), psmem + TL * PTP * sizeof(T),
                                   h->stream, W + b0 * bstride, (int64_t)ncols, kb, bstride, (const T*)Lw, Lw2,
                                   h->dstatus));
             SLAB_CK_LAUNCH(h);
@@ -1965,9 +1972,9 @@ slab_status tall_chol_range(slab_handle* h, T* W, int ncols, int ident0, int kb0
 
 template <typename T>
 slab_status dense_tall_cholesky(slab_handle* h, T* W, int ncols, int ident0, int batch, int64_t bstride) {
-    const size_t smem = 2 * TL * TLP * sizeof(T);
+    const size_t smem = 2 * TL * PTP * sizeof(T);
     SLAB_CK(h, cudaFuncSetAttribute(panel_diag_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int tile = (int)(TL * TLP * sizeof(T));
+    const int tile = (int)(TL * PTP * sizeof(T));
     SLAB_CK(h, cudaFuncSetAttribute(panel_apply_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem));
     SLAB_CK(h, cudaFuncSetAttribute(panel_apply_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
