@@ -426,7 +426,8 @@ def run_gpu(args):
     if args.n:
         W.update(n=args.n, b=args.b or W["b"], k=args.k or W["k"])
         W["workload"] = (f"2D Helmholtz n={W['n']} b={W['b']} point source" if helm else
-                         f"2D var-coef diffusion n={W['n']} b={W['b']} k={W['k']}")
+                         f"{'3D' if W['kind'] == 'diffusion3d' else '2D'} var-coef diffusion n={W['n']} b={W['b']} "
+                         f"k={W['k']}")
     n, b, k = W["n"], W["b"], W["k"]
     dev = rank_device()
     rank, _, world = dist_env()
