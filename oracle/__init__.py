@@ -20,7 +20,9 @@ Contents
     back-solve (eq. usol_even) and their composition (Algorithms 3 and 4).
   * ``schur_dense``: the exact Schur complement A_II - A_IJ A_JJ^-1 A_JI of the
     dense matrix, the invariant the assembled T must equal.
-  * ``kappa_gradient``: dL/dkappa = -lam^T (dA/dkappa) u for the diffusion kind.
+  * ``kappa_gradient``: dL/dkappa = -lam^T (dA/dkappa) u for the diffusion and convection kinds,
+    lam solving A^T lam = dL/du (``adjoint_gradient``: a banded LU of the transposed matrix for
+    the nonsymmetric convection kind).
   * ``boundary_lift``: non-zero Dirichlet data moved into the load of the interior system.
 
 Readings of the paper used here (the paper is silent or garbled on these):
@@ -47,7 +49,8 @@ _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lib = None
 _lock = threading.Lock()
 
-POISSON, DIFFUSION, HELMHOLTZ = 0, 1, 2
+POISSON, DIFFUSION, HELMHOLTZ, CONVECTION = 0, 1, 2, 3
+PIVOTED_KINDS = (HELMHOLTZ, CONVECTION)     # banded LU with partial pivoting (indefinite / nonsymmetric)
 
 _i64 = ctypes.c_int64
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -74,7 +77,7 @@ def lib():
             L.orc_nnz_bound.argtypes = [ctypes.c_int, ctypes.c_int]
             L.orc_assemble.restype = _i64
             L.orc_assemble.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp,
-                                       ctypes.c_double, _lp, _lp, _dp]
+                                       ctypes.c_double, _dp, _lp, _lp, _dp]
             L.orc_csr_matvec.restype = None
             L.orc_csr_matvec.argtypes = [_i64, _lp, _lp, _dp, ctypes.c_int, _dp, _dp]
             L.orc_band_ld.restype = _i64
@@ -139,6 +142,14 @@ class CSR:
             out[a, c[keep]] = self.val[s:e][keep]
         return out
 
+    def transpose(self) -> "CSR":
+        """A^T as CSR (rows sorted)."""
+        rows = np.repeat(np.arange(self.N, dtype=np.int64), np.diff(self.rowptr))
+        order = np.lexsort((rows, self.col))
+        counts = np.bincount(self.col, minlength=self.N)
+        rp = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+        return CSR(self.N, rp, rows[order].copy(), self.val[order].copy())
+
     def sub_csr(self, idx: np.ndarray) -> "CSR":
         """Principal submatrix A[idx][:, idx] as CSR, idx sorted."""
         pos = -np.ones(self.N, dtype=np.int64)
@@ -164,15 +175,22 @@ def _node_arrays(dim, n, kind, kappa, c):
     return kap, cc
 
 
-def assemble(dim: int, n: int, kind: int, kappa=None, c=None, omega: float = 0.0) -> CSR:
-    """CSR assembly of the finite-difference matrix A (natural order, x fastest)."""
+def assemble(dim: int, n: int, kind: int, kappa=None, c=None, omega: float = 0.0, beta=None) -> CSR:
+    """CSR assembly of the finite-difference matrix A (natural order, x fastest).  beta: the
+    velocity components at the nodes, shape (dim, (n+1)^d), for the convection kind."""
     kap, cc = _node_arrays(dim, n, kind, kappa, c)
+    nodes = (n + 1) ** dim
+    if kind == CONVECTION:
+        bet = np.ascontiguousarray(beta, dtype=np.float64).reshape(-1)
+        assert bet.size == dim * nodes
+    else:
+        bet = np.zeros(1)
     N = (n - 1) ** dim
     nb = int(lib().orc_nnz_bound(dim, n))
     rowptr = np.zeros(N + 1, dtype=np.int64)
     col = np.zeros(nb, dtype=np.int64)
     val = np.zeros(nb, dtype=np.float64)
-    nnz = lib().orc_assemble(dim, n, kind, _p(kap), _p(cc), float(omega), _p(rowptr, _lp),
+    nnz = lib().orc_assemble(dim, n, kind, _p(kap), _p(cc), float(omega), _p(bet), _p(rowptr, _lp),
                              _p(col, _lp), _p(val))
     return CSR(N, rowptr, col[:nnz].copy(), val[:nnz].copy())
 
@@ -181,6 +199,8 @@ def boundary_lift(dim: int, n: int, kind: int, g: np.ndarray, f=None, kappa=None
     """Load of the interior system for Dirichlet data g (rows = right-hand sides, all (n+1)^d
     nodes): f + h^-2 sum over boundary neighbours Q of k_PQ g_Q (Sec. 1.1 with u = g on the
     boundary, the boundary unknowns eliminated from the interior rows)."""
+    if kind == CONVECTION:
+        raise NotImplementedError("boundary lift: symmetric kinds only")
     kap, _ = _node_arrays(dim, n, kind, kappa, None)
     G = np.ascontiguousarray(np.atleast_2d(g), dtype=np.float64)
     k = G.shape[0]
@@ -192,7 +212,7 @@ def boundary_lift(dim: int, n: int, kind: int, g: np.ndarray, f=None, kappa=None
 
 
 def assemble_problem(p) -> CSR:
-    return assemble(p.dim, p.n, p.kind, p.kappa, p.c, p.omega)
+    return assemble(p.dim, p.n, p.kind, p.kappa, p.c, p.omega, getattr(p, "beta", None))
 
 
 def residual(A: CSR, u: np.ndarray, f: np.ndarray) -> np.ndarray:
@@ -236,8 +256,14 @@ class BandLU:
 def solve(p, f=None) -> np.ndarray:
     """u = A^-1 f by the banded LU of the whole grid (the plain definition)."""
     A = assemble_problem(p)
-    lu = BandLU(A, (p.n - 1) ** (p.dim - 1), pivot=(p.kind == HELMHOLTZ))
+    lu = BandLU(A, (p.n - 1) ** (p.dim - 1), pivot=(p.kind in PIVOTED_KINDS))
     return lu.solve(p.f if f is None else f)
+
+
+def solve_transposed(p, g) -> np.ndarray:
+    """lam = A^-T g by the banded LU of the transposed matrix (the adjoint system)."""
+    At = assemble_problem(p).transpose()
+    return BandLU(At, (p.n - 1) ** (p.dim - 1), pivot=(p.kind in PIVOTED_KINDS)).solve(g)
 
 
 def dense_solve(A: np.ndarray, F: np.ndarray) -> np.ndarray:
@@ -391,7 +417,7 @@ def interior_solve(A: CSR, f: np.ndarray, ut: Sequence[np.ndarray], dim: int, n:
 def slab_solve(p, f=None) -> Tuple[np.ndarray, dict]:
     """Algorithms 3 and 4 with exact dense T: factor, then solve for p.f (or f)."""
     A = assemble_problem(p)
-    piv = p.kind == HELMHOLTZ
+    piv = p.kind in PIVOTED_KINDS
     Td, Tl, Tu = reduced_system(A, p.dim, p.n, p.b, piv)
     Sinv = sweep_build(Td, Tl, Tu)
     f = p.f if f is None else f
@@ -418,11 +444,17 @@ def kappa_gradient(dim: int, n: int, u: np.ndarray, lam: np.ndarray) -> np.ndarr
 
 
 def adjoint_gradient(p, u_target: np.ndarray):
-    """Loss L = ||u - u_t||^2 for the diffusion problem p: returns (L, u, lam, dL/dkappa)."""
+    """Loss L = ||u - u_t||^2 for the diffusion or convection problem p: returns
+    (L, u, lam, dL/dkappa), lam solving A^T lam = dL/du = 2 (u - u_t)."""
     A = assemble_problem(p)
-    lu = BandLU(A, (p.n - 1) ** (p.dim - 1), pivot=False)
+    w = (p.n - 1) ** (p.dim - 1)
+    piv = p.kind in PIVOTED_KINDS
+    lu = BandLU(A, w, pivot=piv)
     u = lu.solve(p.f)
     r = u - np.atleast_2d(u_target)
     L = float(np.sum(r * r))
-    lam = lu.solve(2.0 * r)             # A is symmetric: A^T lam = dL/du
+    if p.kind == CONVECTION:
+        lam = BandLU(A.transpose(), w, pivot=piv).solve(2.0 * r)
+    else:
+        lam = lu.solve(2.0 * r)         # A is symmetric: A^T lam = dL/du
     return L, u, lam, kappa_gradient(p.dim, p.n, u, lam)

@@ -20,12 +20,19 @@
  *   (A u)_P = h^-2 sum_{faces P~Q} k_PQ (u_P - u_Q) + q_P u_P,   u_Q = 0 on the boundary,
  * k_PQ = (kappa_P + kappa_Q)/2 for diffusion, 1 for Poisson and Helmholtz;
  * q_P = 0, except Helmholtz where q_P = -(omega / c_P)^2.
+ * Convection-diffusion (a second-order elliptic operator with a first-order term, the broad
+ * operator class of Sec. 1.1, eq. "bvp"): -div(kappa grad u) + beta . grad u, the first-order
+ * term by central differences at P,
+ *   (A u)_P += sum_a beta_a(P) (u_{P+e_a} - u_{P-e_a}) / (2h),
+ * so the entry of row P at the neighbour Q = P + s e_a (s = +-1) is -h^-2 k_PQ + s beta_a(P)/(2h)
+ * and A is not symmetric.
  * Node fields are given at all (n+1)^d nodes, C order [z][y][x].
  *
- * Gradient (adjoint of the loss L(u(kappa))): for the diffusion kind,
+ * Gradient (adjoint of the loss L(u(kappa))): for the diffusion and convection kinds (the
+ * first-order term does not depend on kappa),
  *   dL/dkappa_p = -sum_{faces f containing p} (1/2) h^-2 (lam_P - lam_Q)(u_P - u_Q),
  * with boundary values of lam and u equal to zero, since d k_f / d kappa_p = 1/2
- * and dA/dk_f = h^-2 (e_P - e_Q)(e_P - e_Q)^T.
+ * and dA/dk_f = h^-2 (e_P - e_Q)(e_P - e_Q)^T; lam solves A^T lam = dL/du.
  */
 #include <math.h>
 #include <stdint.h>
@@ -38,6 +45,7 @@
 #define ORC_POISSON 0
 #define ORC_DIFFUSION 1
 #define ORC_HELMHOLTZ 2
+#define ORC_CONVECTION 3
 
 static int64_t ipow(int64_t a, int e) { int64_t r = 1; while (e-- > 0) r *= a; return r; }
 
@@ -48,7 +56,7 @@ static int64_t node_id(int dim, int n, int x, int y, int z) {
 }
 
 static double face_coef(int kind, const double* kappa, int64_t p, int64_t q) {
-    if (kind == ORC_DIFFUSION) return 0.5 * (kappa[p] + kappa[q]);
+    if (kind == ORC_DIFFUSION || kind == ORC_CONVECTION) return 0.5 * (kappa[p] + kappa[q]);
     return 1.0;
 }
 
@@ -67,11 +75,13 @@ int64_t orc_nnz_bound(int dim, int n) {
 
 /*
  * CSR assembly of A.  rowptr has N+1 entries; col/val have orc_nnz_bound entries.
- * Columns within a row are sorted ascending.  Returns nnz.
+ * Columns within a row are sorted ascending.  Returns nnz.  beta ([dim][(n+1)^d], the velocity
+ * components x, y(, z) at the nodes) is read for the convection kind only.
  */
 int64_t orc_assemble(int dim, int n, int kind, const double* kappa, const double* c,
-                     double omega, int64_t* rowptr, int64_t* col, double* val) {
+                     double omega, const double* beta, int64_t* rowptr, int64_t* col, double* val) {
     const int m = n - 1;
+    const int64_t nodes = ipow(n + 1, dim);
     const double ih2 = (double)n * (double)n;
     const int zmax = dim == 3 ? m : 1;
     int64_t nnz = 0, row = 0;
@@ -111,8 +121,16 @@ int64_t orc_assemble(int dim, int n, int kind, const double* kappa, const double
                     int64_t Q = node_id(dim, n, bx, by, bz);
                     int64_t qrow = dim == 2 ? (int64_t)(by - 1) * m + (bx - 1)
                                             : ((int64_t)(bz - 1) * m + (by - 1)) * m + (bx - 1);
+                    double v = -ih2 * face_coef(kind, kappa, P, Q);
+                    if (kind == ORC_CONVECTION) {
+                        /* direction a and sign s of Q - P; beta_a(P) s / (2h) */
+                        const int dx = bx - x, dy = by - y, dz = bz - zz;
+                        const int a = dx ? 0 : (dy ? 1 : 2);
+                        const int sgn = dx + dy + dz;
+                        v += 0.5 * (double)n * (double)sgn * beta[(int64_t)a * nodes + P];
+                    }
                     col[nnz] = qrow;
-                    val[nnz] = -ih2 * face_coef(kind, kappa, P, Q);
+                    val[nnz] = v;
                     ++nnz;
                 }
                 rowptr[row + 1] = nnz;

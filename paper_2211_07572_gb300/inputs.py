@@ -25,8 +25,8 @@ from typing import Optional
 
 import numpy as np
 
-POISSON, DIFFUSION, HELMHOLTZ = 0, 1, 2
-KIND_NAMES = {POISSON: "poisson", DIFFUSION: "diffusion", HELMHOLTZ: "helmholtz"}
+POISSON, DIFFUSION, HELMHOLTZ, CONVECTION = 0, 1, 2, 3
+KIND_NAMES = {POISSON: "poisson", DIFFUSION: "diffusion", HELMHOLTZ: "helmholtz", CONVECTION: "convection"}
 
 
 def fourier_field(dim: int, n: int, n_modes: int, seed: int, kmax: int = 8,
@@ -97,8 +97,9 @@ class Problem:
     n: int
     b: int
     kind: int
-    kappa: Optional[np.ndarray] = None      # (n+1)^d nodes, DIFFUSION only
+    kappa: Optional[np.ndarray] = None      # (n+1)^d nodes, DIFFUSION and CONVECTION
     c: Optional[np.ndarray] = None          # (n+1)^d nodes, HELMHOLTZ only
+    beta: Optional[np.ndarray] = None       # (d, (n+1)^d) velocity components x, y(, z), CONVECTION only
     omega: float = 0.0
     f: Optional[np.ndarray] = None          # (k, (n-1)^d)
     u_exact: Optional[np.ndarray] = None    # closed-form continuous solution where known
@@ -137,6 +138,20 @@ def helmholtz(n: int, b: int, dim: int = 2, n_modes: int = 8, field_seed: int = 
     return Problem(name=f"helmholtz{dim}d_n{n}_b{b}", dim=dim, n=n, b=b, kind=HELMHOLTZ,
                    c=1.0 + contrast * r, omega=omega, f=point_source(dim, n),
                    meta=dict(n_modes=n_modes, field_seed=field_seed, ppw=ppw))
+
+
+def convection(n: int, b: int, k: int, dim: int = 2, speed: float = 20.0, n_modes: int = 16,
+               field_seed: int = 6, velocity_seeds=(7, 8, 9), rhs_seed: int = 106) -> Problem:
+    """-div(kappa grad u) + beta.grad u = f: kappa = exp(g) (g a unit-variance Fourier field, as the
+    diffusion workload), velocity components beta_a = speed * r_a with r_a 8-mode fields normalised
+    to max |r_a| = 1, f ~ N(0,1)."""
+    g = fourier_field(dim, n, n_modes, field_seed, normalize="var")
+    beta = np.stack([speed * fourier_field(dim, n, 8, velocity_seeds[a], normalize="maxabs")
+                     for a in range(dim)])
+    f = normal_rhs(dim, n, k, rhs_seed) if k > 0 else None
+    return Problem(name=f"convection{dim}d_n{n}_b{b}_k{k}", dim=dim, n=n, b=b, kind=CONVECTION,
+                   kappa=np.exp(g), beta=beta, f=f,
+                   meta=dict(speed=speed, n_modes=n_modes, field_seed=field_seed, rhs_seed=rhs_seed))
 
 
 def constant_helmholtz(n: int, b: int, omega: float, rhs_seed: int = 7, k: int = 1) -> Problem:
