@@ -988,6 +988,106 @@ def run_reference(args):
         "wall_s": time.perf_counter() - t0}))
 
 
+def run_convection(args):
+    """Nonsymmetric workload: 2-D convection-diffusion -div(kappa grad u) + beta.grad u = f, n = 2048,
+    b = 32, 16 loads, kappa = exp(16-mode field), |beta| <= 20 (8-mode fields).  A step is: factor, solve
+    with refinement to 1e-10, the adjoint solve A^T lambda = 2 (u - u_t) on the same factors (every
+    phase transposed) refined to 1e-10, and the gradient dL/dkappa of L = ||u - u_t||^2."""
+    import numpy as np
+    import torch
+
+    from paper_2211_07572_gb300 import inputs
+    from paper_2211_07572_gb300.solver import SlabSolver
+    dev = rank_device()
+    rank, _, world = dist_env()
+    n, b, k = args.n or 2048, args.b or 32, args.k or 16
+    p = inputs.convection(n, b, k)
+    kappa = torch.from_numpy(p.kappa).to(dev)
+    beta = torch.from_numpy(p.beta).to(dev)
+    f_host = torch.from_numpy(p.f).pin_memory()
+    ut_host = torch.from_numpy(inputs.normal_rhs(2, n, k, 107)).pin_memory()
+    f, ut = f_host.to(dev), ut_host.to(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(fd, utd, prec=args.precision, counts=None):
+        s = SlabSolver(2, n, b, inputs.CONVECTION, kappa=kappa, beta=beta, precision=prec, rtol=1e-10,
+                       max_refine=40, stream=stream, device=dev)
+        u, rel, it = s.solve(fd, allow_noconv=True)
+        lam, g = s.adjoint(2 * (u - utd), u, allow_noconv=True)
+        if counts is not None:
+            counts.append(sum(s.profile_read()[1].values()))
+        s.close()
+        return u, lam, g, rel, it
+
+    for _ in range(args.warmup):
+        step(f, ut)
+    sampler = ClockSampler()
+    sampler.start()
+    dist_barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    launches, its, rels = [], [], []
+    for _ in range(args.steps):
+        u, lam, g, rel, it = step(f, ut, counts=launches)
+        its.append(it)
+        rels.append(float(np.max(rel)))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dist_barrier()
+    ms = dist_max(e0.elapsed_time(e1) / args.steps)
+    # adjoint accuracy: relative residual of A^T lambda = 2 (u - u_t) in FP64
+    s = SlabSolver(2, n, b, inputs.CONVECTION, kappa=kappa, beta=beta, precision=args.precision, stream=stream,
+                   device=dev)
+    rhs = 2 * (u - ut)
+    adj_rel = float(((rhs - s.apply_transpose(lam)).norm(dim=1) / rhs.norm(dim=1)).max())
+    s.close()
+    # end to end: loads and targets from pinned host memory, u and the gradient back
+    u_host = torch.empty_like(f_host).pin_memory()
+    g_host = torch.empty((n + 1, n + 1), dtype=torch.float64).pin_memory()
+    fd, utd = torch.empty_like(f), torch.empty_like(ut)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        fd.copy_(f_host, non_blocking=True)
+        utd.copy_(ut_host, non_blocking=True)
+        u, lam, g, _, _ = step(fd, utd)
+        u_host.copy_(u, non_blocking=True)
+        g_host.copy_(g, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e = dist_max((time.perf_counter() - t0) / args.steps)
+    sampler.stop()
+    fp64 = None
+    if args.fp64_comparator:
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        step(f, ut, prec="fp64")
+        a1.record(stream)
+        torch.cuda.synchronize()
+        fp64 = dist_max(a0.elapsed_time(a1)) / 1e3
+    if rank != 0:
+        return
+    print(json.dumps({
+        "metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": {"fp32": "f32 factor (slab trees, interface), f64 residual + refinement"}.get(args.precision,
+                                                                                               args.precision),
+        "data": "synthetic",
+        "config": {"workload": f"2D convection-diffusion n={n} b={b} k={k} (kappa=exp(16-mode field), "
+                               "|beta|<=20 8-mode fields, f~N(0,1)); step = factor + solve + transposed adjoint "
+                               "solve + dL/dkappa", "n": n, "b": b, "k": k, "precision": args.precision,
+                   "l2": "every step streams > 1 GB (>> 129 MB L2); no explicit flush"},
+        "max_relres": max(rels), "refine_steps": its, "adjoint_max_relres": adj_rel,
+        "fp64_gpu": {"value": fp64, "unit": "s"} if fp64 is not None else None,
+        "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": int(2 * f_host.numel() * 8),
+                "d2h_bytes_per_step": int(u_host.numel() * 8 + g_host.numel() * 8)},
+        "gpu_launches": launches[-1] if launches else None,
+        "clocks": sampler.summary(),
+    }))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1014,9 +1114,10 @@ def main():
     ap.add_argument("--graph-steps", type=int, default=4, help="adjoint256 graph: refinement passes per solve")
     ap.add_argument("--branches", type=int, default=32, help="adjoint256 graph: parallel branches per wave")
     ap.add_argument("--workload", default="diffusion3d96",
-                    choices=["diffusion2048", "helmholtz4096", "diffusion3d96", "adjoint256", "helmholtzj0"],
+                    choices=["diffusion2048", "helmholtz4096", "diffusion3d96", "adjoint256", "helmholtzj0",
+                             "convection2048"],
                     help="diffusion3d96: the default bench line (3-D diffusion n=96, b=8, k=16); diffusion2048, "
-                         "helmholtz4096, adjoint256, helmholtzj0: the other workloads")
+                         "helmholtz4096, adjoint256, helmholtzj0, convection2048: the other workloads")
     ap.add_argument("--krylov", type=int, default=0, help="0: plain refinement; m: FP64 GMRES(m) refinement")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the fixed size heuristic for the factor products instead of the online tuner "
@@ -1043,6 +1144,8 @@ def main():
         run_adjoint_batch(args)
     elif args.workload == "helmholtzj0":
         run_j0(args)
+    elif args.workload == "convection2048":
+        run_convection(args)
     else:
         run_gpu(args)
 

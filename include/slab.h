@@ -15,8 +15,12 @@
  *
  * Operator (Sec. 2.1 eq. "discretiation" with the sign of eq. "var_helm"):
  *   (A u)_P = n^2 sum_{faces P~Q} k_PQ (u_P - u_Q) + q_P u_P,   u = 0 on the boundary,
- *   k_PQ = (kappa_P + kappa_Q)/2 (DIFFUSION) or 1 (POISSON, HELMHOLTZ),
+ *   k_PQ = (kappa_P + kappa_Q)/2 (DIFFUSION, CONVECTION) or 1 (POISSON, HELMHOLTZ),
  *   q_P = 0, or -(omega / c_P)^2 for HELMHOLTZ.
+ * CONVECTION (2-D) adds a first-order term, -div(kappa grad u) + beta . grad u (a second-order
+ * elliptic operator of the class of Sec. 1.1, eq. "bvp"), by central differences at P:
+ *   (A u)_P += sum_a beta_a(P) (u_{P+e_a} - u_{P-e_a}) n / 2,
+ * so A is not symmetric: T_{q+1,q} != T_{q,q+1}^T, and the adjoint solves with A^T.
  *
  * Conventions shared by every entry point
  *   - Node fields (kappa, c) have (n+1)^d FP64 entries, C order [z][y][x]
@@ -55,7 +59,7 @@ typedef enum {
     SLAB_EUNSUPPORTED = 7   /* valid request this build does not implement */
 } slab_status;
 
-typedef enum { SLAB_POISSON = 0, SLAB_DIFFUSION = 1, SLAB_HELMHOLTZ = 2 } slab_kind;
+typedef enum { SLAB_POISSON = 0, SLAB_DIFFUSION = 1, SLAB_HELMHOLTZ = 2, SLAB_CONVECTION = 3 } slab_kind;
 
 typedef enum {
     SLAB_PREC_FP64 = 0,     /* factor and solves in FP64 (the plain FP64 GPU path) */
@@ -95,9 +99,12 @@ typedef struct {
 
 typedef struct {
     int kind;               /* slab_kind */
-    const double* kappa;    /* device, (n+1)^d nodes; DIFFUSION only (NULL otherwise) */
+    const double* kappa;    /* device, (n+1)^d nodes; DIFFUSION and CONVECTION (NULL otherwise) */
     const double* c;        /* device, (n+1)^d nodes; HELMHOLTZ only (NULL otherwise) */
     double omega;           /* HELMHOLTZ angular frequency */
+    const double* beta;     /* device, 2 x (n+1)^2 nodes: the velocity components beta_x then
+                               beta_y, each C order [y][x]; CONVECTION only (never read for the
+                               other kinds, so callers built before this field may omit it) */
 } slab_coeffs;
 
 typedef struct {
@@ -132,8 +139,8 @@ void slab_default_opts(slab_opts* opts);
  * reduced matrix T, Stage 2 (Algorithm 1's sweep or the odd-even order, opts.stage2).  b is the interface spacing:
  * interfaces at x = q b, q = 1..n/b-1, slab interiors b-1 nodes wide.
  * Requires dim 2 or 3, b >= 2, n % b == 0 and n/b >= 2 (SLAB_EINVAL otherwise).  In 2-D the slab
- * interior width b - 1 is at most 32 (SLAB_EUNSUPPORTED otherwise); HELMHOLTZ in 3-D, and
- * SLAB_STAGE2_ODDEVEN with HELMHOLTZ, are SLAB_EUNSUPPORTED.  POISSON and DIFFUSION are factored by
+ * interior width b - 1 is at most 32 (SLAB_EUNSUPPORTED otherwise); HELMHOLTZ or CONVECTION in 3-D,
+ * and SLAB_STAGE2_ODDEVEN with HELMHOLTZ or CONVECTION, are SLAB_EUNSUPPORTED.  POISSON and DIFFUSION are factored by
  * Cholesky (slab separators and Stage 2); HELMHOLTZ (indefinite) by Gauss-Jordan
  * with partial pivoting in the slab separators, and in Stage 2 (Algorithm 1 as printed) by a
  * blocked Gauss-Jordan elimination of [S_j | T_{j,j+1} | I] with tournament pivoting
@@ -189,6 +196,10 @@ slab_status slab_apply_residual(slab_handle* h, const double* u, const double* f
 /* y = A x in FP64 for k vectors. */
 slab_status slab_apply(slab_handle* h, const double* x, double* y, int k);
 
+/* y = A^T x in FP64 for k vectors (the same stencil with its couplings transposed; equal to
+ * slab_apply for the symmetric kinds). */
+slab_status slab_apply_transpose(slab_handle* h, const double* x, double* y, int k);
+
 /*
  * Non-zero Dirichlet data (Sec. 1.1 with u = g on the boundary instead of 0).  Eliminating the
  * boundary unknowns from the interior rows gives A u = f + lift(g) with
@@ -198,15 +209,19 @@ slab_status slab_apply(slab_handle* h, const double* x, double* y, int k);
  * g: device, k x (n+1)^d FP64 over all nodes (C order [z][y][x], only boundary entries are
  * read); f: device, k x (n-1)^d interior load, or NULL for zero; f_out: device, same layout as f,
  * may be f itself.  Caller owns all buffers.  SLAB_EINVAL for a null handle, g or f_out, or
- * k < 0.  Asynchronous on the handle's stream.
+ * k < 0; SLAB_EUNSUPPORTED for CONVECTION.  Asynchronous on the handle's stream.
  */
 slab_status slab_boundary_lift(slab_handle* h, const double* g, const double* f, double* f_out, int k);
 
 /*
- * Adjoint solve and coefficient gradient (DIFFUSION).  Given dL/du (device,
- * [k][(n-1)^d]) and the state u, solves A^T lambda = dL/du with the stored
- * factors (A is symmetric here) and, if dLdkappa != NULL, accumulates into it
- * (device, (n+1)^d, k gradients summed) dL/dkappa_p = -lambda^T (dA/dkappa_p) u.
+ * Adjoint solve and coefficient gradient (DIFFUSION, CONVECTION).  Given dL/du (device,
+ * [k][(n-1)^d]) and the state u, solves A^T lambda = dL/du with the stored factors, refined
+ * like slab_solve against the FP64 residual of A^T, and, if dLdkappa != NULL, accumulates into
+ * it (device, (n+1)^d, k gradients summed) dL/dkappa_p = -lambda^T (dA/dkappa_p) u (the
+ * first-order term of CONVECTION does not depend on kappa).  For the symmetric kinds the solve
+ * is slab_solve's; for CONVECTION every phase runs transposed on the same factors: the slab
+ * trees with S^-T and the other orientation of their couplings, Algorithm 2 on T^T = U^T L^T
+ * (forward with W_j^T, backward with S_j^-T and T_{j+1,j}^T).  Status as slab_solve.
  */
 slab_status slab_adjoint(slab_handle* h, const double* dLdu, const double* u, double* lambda,
                          double* dLdkappa, int k);
@@ -238,7 +253,8 @@ slab_status slab_apply_T(slab_handle* h, const double* X, double* Y, int k, doub
 /*
  * Copy one (n-1)^(d-1) square block of the reduced matrix T (as assembled,
  * before Stage 2) to out (HOST, row-major, FP64): which = 0 gives T_qq, which
- * = 1 gives T_{q,q+1} (q = 0..N_I-2).  Synchronises the stream.
+ * = 1 gives T_{q,q+1} and which = 2 gives T_{q+1,q} (q = 0..N_I-2; assembled separately
+ * for CONVECTION, the transpose of T_{q,q+1} otherwise).  Synchronises the stream.
  */
 slab_status slab_get_T_block(slab_handle* h, int which, int q, double* out);
 

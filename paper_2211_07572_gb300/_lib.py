@@ -10,7 +10,7 @@ from . import build as _build
 c_int, c_double, c_void_p, c_int64 = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_int64
 
 SLAB_OK, SLAB_EINVAL, SLAB_ENOMEM, SLAB_ESINGULAR, SLAB_ENOCONV, SLAB_ETIMEOUT, SLAB_ECUDA, SLAB_EUNSUPPORTED = range(8)
-POISSON, DIFFUSION, HELMHOLTZ = 0, 1, 2
+POISSON, DIFFUSION, HELMHOLTZ, CONVECTION = 0, 1, 2, 3
 KERNEL_CLASSES = ("coeff", "tree_factor", "assemble_T", "panel", "trailing", "schur_update", "sweep_products",
                   "tree_up", "tree_down", "stencil", "other", "slab_panel", "slab_trailing", "slab_schur")
 PREC_FP64, PREC_FP32, PREC_TF32, PREC_FP64_TC = 0, 1, 2, 3
@@ -21,7 +21,7 @@ class SlabGrid(ctypes.Structure):
 
 
 class SlabCoeffs(ctypes.Structure):
-    _fields_ = [("kind", c_int), ("kappa", c_void_p), ("c", c_void_p), ("omega", c_double)]
+    _fields_ = [("kind", c_int), ("kappa", c_void_p), ("c", c_void_p), ("omega", c_double), ("beta", c_void_p)]
 
 
 class SlabOpts(ctypes.Structure):
@@ -49,6 +49,7 @@ SIGNATURES = {
                            ctypes.POINTER(c_int)]),
     "slab_apply_residual": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int]),
     "slab_apply": (c_int, [c_void_p, c_void_p, c_void_p, c_int]),
+    "slab_apply_transpose": (c_int, [c_void_p, c_void_p, c_void_p, c_int]),
     "slab_boundary_lift": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int]),
     "slab_adjoint": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int]),
     "slab_reduced_rhs": (c_int, [c_void_p, c_void_p, c_void_p, c_int]),

@@ -15,8 +15,9 @@
 
 #include "slab_internal.cuh"
 
-slab_status slab_cuda_check(slab_handle* h, cudaError_t e) {
-    (void)e;
+slab_status slab_cuda_check(slab_handle* h, cudaError_t e, const char* file, int line) {
+    static const bool trace = std::getenv("SLAB_CUDA_TRACE") != nullptr;
+    if (trace) std::fprintf(stderr, "slab: %s at %s:%d\n", cudaGetErrorString(e), file, line);
     if (h && h->err == SLAB_OK) h->err = SLAB_ECUDA;
     return SLAB_ECUDA;
 }
@@ -290,15 +291,19 @@ slab_status factor_impl(slab_handle* h) {
     // mixed mode: assemble T in the Stage-1 scalar, widen it, eliminate in the Stage-2 scalar
     void* Tb2 = h->Tb;
     void* To2 = h->To;
+    void* Tl2 = h->Tl;
     h->Tb = h->Tb1;
     h->To = h->To1;
+    h->Tl = h->Tl1;
     const slab_status st = stage1_impl<T>(h);
     h->Tb = Tb2;
     h->To = To2;
+    h->Tl = Tl2;
     TRY(st);
     const int64_t blk = (int64_t)h->td.s_pad * h->td.s_pad;
     TRY(widen_to_double(h, (const float*)h->Tb1, (double*)h->Tb, h->td.NI * blk));
     TRY(widen_to_double(h, (const float*)h->To1, (double*)h->To, (h->td.NI - 1) * blk));
+    if (h->Tl) TRY(widen_to_double(h, (const float*)h->Tl1, (double*)h->Tl, (h->td.NI - 1) * blk));
     h->fp64tc_now = h->fp64tc;
     const slab_status st2 = sweep_factor<double>(h);
     h->fp64tc_now = 0;
@@ -432,7 +437,10 @@ void slab_destroy(slab_handle* h) {
     void* p;
     p = h->AX; dfree(p); p = h->AY; dfree(p); p = h->DG; dfree(p); p = h->kappa; dfree(p);
     dfree(h->tLinv); dfree(h->tZtb); dfree(h->tRtb); dfree(h->tZI); dfree(h->tRI);
-    dfree(h->tWtb); dfree(h->tWI); dfree(h->ToT); dfree(h->dscratch); dfree(h->gjw); dfree(h->ozw); dfree(h->w16); dfree(h->pnl);
+    dfree(h->tWtb); dfree(h->tWI); dfree(h->ToT); dfree(h->dscratch);
+    p = h->AXT; dfree(p); p = h->AYT; dfree(p);
+    dfree(h->tLinvT); dfree(h->tZtbT); dfree(h->tWtbT); dfree(h->tZIT); dfree(h->tWIT); dfree(h->tRIc);
+    dfree(h->Tl); dfree(h->Tl1); dfree(h->SinvT); dfree(h->WT); dfree(h->TlT); dfree(h->gjw); dfree(h->ozw); dfree(h->w16); dfree(h->pnl);
     p = h->AZ; dfree(p);
     dfree(h->t3Lin); dfree(h->t3LT); dfree(h->t3Ztb); dfree(h->t3ZtbT); dfree(h->t3ZIT); dfree(h->t3ZI);
     dfree(h->t3Rtb); dfree(h->t3RI); dfree(h->t3W);
@@ -489,8 +497,9 @@ slab_status factor_create(const slab_grid* grid, const slab_coeffs* co, int b, c
     const int n = grid->n;
     if (grid->dim != 2 && grid->dim != 3) return SLAB_EINVAL;
     if (b < 2 || n < 4 || n % b != 0 || n / b < 2) return SLAB_EINVAL;
-    if (co->kind < SLAB_POISSON || co->kind > SLAB_HELMHOLTZ) return SLAB_EINVAL;
-    if (co->kind == SLAB_DIFFUSION && !co->kappa) return SLAB_EINVAL;
+    if (co->kind < SLAB_POISSON || co->kind > SLAB_CONVECTION) return SLAB_EINVAL;
+    if ((co->kind == SLAB_DIFFUSION || co->kind == SLAB_CONVECTION) && !co->kappa) return SLAB_EINVAL;
+    if (co->kind == SLAB_CONVECTION && !co->beta) return SLAB_EINVAL;
     if (co->kind == SLAB_HELMHOLTZ && !co->c) return SLAB_EINVAL;
     if (o.factor_prec < SLAB_PREC_FP64 || o.factor_prec > SLAB_PREC_TF32) return SLAB_EINVAL;
     const int want_tf32 = o.factor_prec == SLAB_PREC_TF32 || o.interface_prec == SLAB_PREC_TF32;
@@ -505,14 +514,17 @@ slab_status factor_create(const slab_grid* grid, const slab_coeffs* co, int b, c
     if (prec2 != SLAB_PREC_FP32 && prec2 != SLAB_PREC_FP64) return SLAB_EINVAL;
     if (o.factor_prec == SLAB_PREC_FP64 && prec2 == SLAB_PREC_FP32) return SLAB_EINVAL;
     if (grid->dim == 2 && b - 1 > SLAB_MAXM) return SLAB_EUNSUPPORTED;
-    if (grid->dim == 3 && co->kind == SLAB_HELMHOLTZ) return SLAB_EUNSUPPORTED;
-    if (o.stage2 == SLAB_STAGE2_ODDEVEN && co->kind == SLAB_HELMHOLTZ) return SLAB_EUNSUPPORTED;
+    const bool general = co->kind == SLAB_HELMHOLTZ || co->kind == SLAB_CONVECTION;   // LU, not Cholesky
+    const bool nonsym = co->kind == SLAB_CONVECTION;
+    if (grid->dim == 3 && general) return SLAB_EUNSUPPORTED;
+    if (o.stage2 == SLAB_STAGE2_ODDEVEN && general) return SLAB_EUNSUPPORTED;
 
     slab_handle* h = new (std::nothrow) slab_handle();
     if (!h) return SLAB_ENOMEM;
     std::memset(h, 0, sizeof(*h));
     h->arena = arena;
     h->dim = grid->dim; h->n = n; h->b = b; h->kind = co->kind; h->omega = co->omega;
+    h->beta = nonsym ? co->beta : nullptr;
     h->prec = o.factor_prec;
     h->rsz = h->prec == SLAB_PREC_FP64 ? 8 : 4;
     h->tf32 = want_tf32;
@@ -553,7 +565,11 @@ slab_status factor_create(const slab_grid* grid, const slab_coeffs* co, int b, c
     ALLOC(h->AX, nodes2 * sizeof(double));
     ALLOC(h->AY, nodes2 * sizeof(double));
     ALLOC(h->DG, nodes2 * sizeof(double));
-    if (co->kind == SLAB_DIFFUSION) ALLOC(h->kappa, nodes2 * sizeof(double));
+    if (co->kind == SLAB_DIFFUSION || nonsym) ALLOC(h->kappa, nodes2 * sizeof(double));
+    if (nonsym) {
+        ALLOC(h->AXT, nodes2 * sizeof(double));
+        ALLOC(h->AYT, nodes2 * sizeof(double));
+    }
     if (grid->dim == 3) {
         ALLOC(h->AZ, nodes2 * sizeof(double));
         h->t3plan = tree3d_plan(d.s, d.m, d.NS);
@@ -574,15 +590,25 @@ slab_status factor_create(const slab_grid* grid, const slab_coeffs* co, int b, c
         ALLOC(h->tRtb, tn * 4 * d.m * d.m * R);
         ALLOC(h->tZI, (int64_t)d.NS * d.H * 2 * d.m * d.s_pad * R);
         ALLOC(h->tRI, (int64_t)d.NS * d.H * 4 * d.m * d.s_pad * R);
+        if (nonsym) {
+            ALLOC(h->tLinvT, tn * d.m * d.m * R);
+            ALLOC(h->tZtbT, tn * 2 * d.m * d.m * R);
+            ALLOC(h->tWtbT, tn * 2 * d.m * d.m * R);
+            ALLOC(h->tZIT, (int64_t)d.NS * d.H * 2 * d.m * d.s_pad * R);
+            ALLOC(h->tWIT, (int64_t)d.NS * d.H * 2 * d.m * d.s_pad * R);
+            ALLOC(h->tRIc, (int64_t)d.NS * d.H * 4 * d.m * d.s_pad * R);
+        }
     }
     ALLOC(h->Tb, d.NI * blk * R2);
     ALLOC(h->To, (d.NI - 1) * blk * R2);
+    if (nonsym) ALLOC(h->Tl, (d.NI - 1) * blk * R2);
     if (h->prec2 != h->prec) {
         ALLOC(h->Tb1, d.NI * blk * R);
         ALLOC(h->To1, (d.NI - 1) * blk * R);
+        if (nonsym) ALLOC(h->Tl1, (d.NI - 1) * blk * R);
     }
     h->stage2 = o.stage2 == SLAB_STAGE2_ODDEVEN ||
-                (o.stage2 == SLAB_STAGE2_AUTO && co->kind != SLAB_HELMHOLTZ && d.NI >= 4 &&
+                (o.stage2 == SLAB_STAGE2_AUTO && !general && d.NI >= 4 &&
                  h->prec2 == SLAB_PREC_FP32 && oddeven_is_faster(d.NI, d.s_pad));
     if (h->stage2) {
         ALLOC(h->crD, d.NI * blk * R2);
@@ -593,20 +619,25 @@ slab_status factor_create(const slab_grid* grid, const slab_coeffs* co, int b, c
         ALLOC(h->crP, d.NI * blk * R2);
         ALLOC(h->crQt, d.NI * blk * R2);
         ALLOC(h->crQ, d.NI * blk * R2);
-    } else if (co->kind == SLAB_HELMHOLTZ) {
+    } else if (general) {
         ALLOC(h->Fct, 5 * blk * R2);                    // augmented system [S | T | I] over [T | T]
         ALLOC(h->gjw, gj_work_bytes(d.s_pad, R2));
     } else {
         ALLOC(h->Fct, d.NI * 3 * blk * R2);
     }
-    if (co->kind == SLAB_HELMHOLTZ) {
+    if (general) {
         ALLOC(h->tWtb, tn * 2 * d.m * d.m * R);
         ALLOC(h->tWI, (int64_t)d.NS * d.H * 2 * d.m * d.s_pad * R);
-        ALLOC(h->ToT, (d.NI - 1) * blk * R2);
+        if (!nonsym) ALLOC(h->ToT, (d.NI - 1) * blk * R2);     // T_{q+1,q} = T_{q,q+1}^T
+    }
+    if (nonsym) {                                               // the A^T sweep
+        ALLOC(h->SinvT, d.NI * blk * R2);
+        ALLOC(h->WT, (d.NI - 1) * blk * R2);
+        ALLOC(h->TlT, (d.NI - 1) * blk * R2);
     }
     ALLOC(h->dscratch, 256);
     if (h->fp64tc) ALLOC(h->ozw, ozaki_work_bytes(2 * (int64_t)d.s_pad + 128, 3 * (int64_t)d.s_pad, 64));
-    if (!h->tf32 && co->kind != SLAB_HELMHOLTZ &&
+    if (!h->tf32 && !general &&
         (h->prec2 == SLAB_PREC_FP32 || (h->dim == 3 && h->prec == SLAB_PREC_FP32))) {
         // largest FP16 three-product of the factor: the batched Stage-2 Schur products (s_pad^3)
         h->w16_bytes = f16x3_work_bytes(d.s_pad, d.s_pad, d.s_pad, h->stage2 ? cr_max_batch(d.NI) : 1, false);
@@ -636,6 +667,9 @@ slab_status factor_launch(slab_handle* h, const double* kappa, const double* c) 
     if (h->tZI) SLAB_CK(h, cudaMemsetAsync(h->tZI, 0, (size_t)d.NS * d.H * 2 * d.m * d.s_pad * R, h->stream));
     if (h->tRI) SLAB_CK(h, cudaMemsetAsync(h->tRI, 0, (size_t)d.NS * d.H * 4 * d.m * d.s_pad * R, h->stream));
     if (h->tWI) SLAB_CK(h, cudaMemsetAsync(h->tWI, 0, (size_t)d.NS * d.H * 2 * d.m * d.s_pad * R, h->stream));
+    if (h->tZIT) SLAB_CK(h, cudaMemsetAsync(h->tZIT, 0, (size_t)d.NS * d.H * 2 * d.m * d.s_pad * R, h->stream));
+    if (h->tWIT) SLAB_CK(h, cudaMemsetAsync(h->tWIT, 0, (size_t)d.NS * d.H * 2 * d.m * d.s_pad * R, h->stream));
+    if (h->tRIc) SLAB_CK(h, cudaMemsetAsync(h->tRIc, 0, (size_t)d.NS * d.H * 4 * d.m * d.s_pad * R, h->stream));
     if (h->kappa && kappa != h->kappa)
         SLAB_CK(h, cudaMemcpyAsync(h->kappa, kappa, nodes2 * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     slab_status st = launch_coefficients(h, kappa, c);
@@ -648,7 +682,9 @@ slab_status factor_launch(slab_handle* h, const double* kappa, const double* c) 
 static void free_factor_only(slab_handle* h) {
     dfree(h->Tb1);                                     // mixed-mode assembly buffers
     dfree(h->To1);
-    h->Tb1 = h->To1 = nullptr;
+    dfree(h->Tl1);
+    h->Tb1 = h->To1 = h->Tl1 = nullptr;
+    dfree(h->tRIc);                                    // condensed couplings (nonsymmetric kind)
     dfree(h->w16);                                     // factor-only product work
     h->w16 = nullptr;
     h->w16_bytes = 0;
@@ -671,6 +707,7 @@ slab_status slab_factor(const slab_grid* grid, const slab_coeffs* co, int b, con
     if (st) return st;
     st = factor_launch(h, co->kappa, co->c);
     if (!st) st = sync_status(h);
+    h->beta = nullptr;                                 // the caller's field is read during the call only
     if (st) {
         slab_destroy(h);
         return st;
@@ -691,7 +728,18 @@ slab_status slab_boundary_lift(slab_handle* h, const double* g, const double* f,
     if (!h || k < 0) return SLAB_EINVAL;
     if (k == 0) return SLAB_OK;
     if (!g || !f_out) return SLAB_EINVAL;
+    if (h->kind == SLAB_CONVECTION) return SLAB_EUNSUPPORTED;
     return launch_boundary_lift(h, g, f, f_out, k);
+}
+
+slab_status slab_apply_transpose(slab_handle* h, const double* x, double* y, int k) {
+    if (!h || k < 0) return SLAB_EINVAL;
+    if (k == 0) return SLAB_OK;
+    if (!x || !y) return SLAB_EINVAL;
+    h->transposed = h->kind == SLAB_CONVECTION;
+    const slab_status st = launch_apply(h, x, y, k);
+    h->transposed = 0;
+    return st;
 }
 
 slab_status slab_apply(slab_handle* h, const double* x, double* y, int k) {
@@ -905,10 +953,13 @@ slab_status slab_adjoint(slab_handle* h, const double* dLdu, const double* u, do
     if (!h || k < 0) return SLAB_EINVAL;
     if (k == 0) return SLAB_OK;
     if (!dLdu || !lambda) return SLAB_EINVAL;
-    if (dLdkappa && (h->kind != SLAB_DIFFUSION || !u)) return SLAB_EINVAL;
+    if (dLdkappa && ((h->kind != SLAB_DIFFUSION && h->kind != SLAB_CONVECTION) || !u)) return SLAB_EINVAL;
     if (dLdkappa && h->dim != 2) return SLAB_EUNSUPPORTED;
-    // every supported operator is symmetric, so A^T lambda = dL/du is solved with the same factors
+    // A^T lambda = dL/du with the same factors: the symmetric kinds' solve is slab_solve's; the
+    // nonsymmetric kind runs every phase transposed (tree passes, sweep, residual)
+    h->transposed = h->kind == SLAB_CONVECTION;
     slab_status st = slab_solve(h, dLdu, lambda, k, nullptr, nullptr);
+    h->transposed = 0;
     if (st != SLAB_OK && st != SLAB_ENOCONV) return st;
     if (dLdkappa) TRY(launch_kappa_gradient(h, u, lambda, dLdkappa, k));
     return st;
@@ -995,11 +1046,13 @@ slab_status slab_apply_T(slab_handle* h, const double* X, double* Y, int k, doub
 }
 
 slab_status slab_get_T_block(slab_handle* h, int which, int q, double* out) {
-    if (!h || !out || which < 0 || which > 1) return SLAB_EINVAL;
+    if (!h || !out || which < 0 || which > 2) return SLAB_EINVAL;
     const TreeDims& d = h->td;
     if (q < 0 || q >= (which == 0 ? d.NI : d.NI - 1)) return SLAB_EINVAL;
     const int64_t blk = (int64_t)d.s_pad * d.s_pad;
-    const unsigned char* base = (const unsigned char*)(which == 0 ? h->Tb : h->To) + q * blk * h->rsz2;
+    const bool mirror = which == 2 && !h->Tl;          // symmetric kinds: T_{q+1,q} = T_{q,q+1}^T
+    const void* src = which == 0 ? h->Tb : (which == 1 || mirror ? h->To : h->Tl);
+    const unsigned char* base = (const unsigned char*)src + q * blk * h->rsz2;
     std::vector<unsigned char> tmp((size_t)blk * h->rsz2);
     SLAB_CK(h, cudaMemcpyAsync(tmp.data(), base, tmp.size(), cudaMemcpyDeviceToHost, h->stream));
     SLAB_CK(h, cudaStreamSynchronize(h->stream));
@@ -1008,7 +1061,7 @@ slab_status slab_get_T_block(slab_handle* h, int which, int q, double* out) {
         for (int j = 0; j < d.si; ++j) {
             const int64_t e = (int64_t)i * d.s_pad + j;
             const double v = h->rsz2 == 8 ? ((const double*)tmp.data())[e] : (double)((const float*)tmp.data())[e];
-            out[(int64_t)i * d.si + j] = sc * v;
+            out[mirror ? (int64_t)j * d.si + i : (int64_t)i * d.si + j] = sc * v;
         }
     return SLAB_OK;
 }

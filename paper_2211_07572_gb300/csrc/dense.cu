@@ -1197,12 +1197,14 @@ __global__ void gj_fill_top_kernel(T* Gt, int sp, int wt, const T* __restrict__ 
     Gt[idx] = v;
 }
 
+// Bottom rows [T_{j+1,j} | T_{j+1,j+1}]: T21 given (nonsymmetric kind), else T_{j,j+1}^T from T12.
 template <typename T>
-__global__ void gj_fill_bottom_kernel(T* Gb, int sp, const T* __restrict__ T12, const T* __restrict__ T22) {
+__global__ void gj_fill_bottom_kernel(T* Gb, int sp, const T* __restrict__ T12, const T* __restrict__ T22,
+                                      const T* __restrict__ T21) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (int64_t)sp * 2 * sp) return;
     const int i = (int)(idx / (2 * sp)), c = (int)(idx % (2 * sp));
-    Gb[idx] = c < sp ? T12[(int64_t)c * sp + i] : T22[(int64_t)i * sp + (c - sp)];   // T_{j+1,j} = T_{j,j+1}^T
+    Gb[idx] = c < sp ? (T21 ? T21[(int64_t)i * sp + c] : T12[(int64_t)c * sp + i]) : T22[(int64_t)i * sp + (c - sp)];
 }
 
 // Sinv[i] = Gt[perm[i]][wt-sp ..], W[i] = Gt[perm[i]][sp .. 2sp) (W optional)
@@ -1307,6 +1309,7 @@ slab_status sweep_factor_indef(slab_handle* h) {
     T* Tb = (T*)h->Tb;
     T* To = (T*)h->To;
     T* ToT = (T*)h->ToT;
+    T* Tl = (T*)h->Tl;                   // nonsymmetric kind: T_{q+1,q} as assembled (else null)
     T* Sinv = (T*)h->Linv;
     T* Wn = (T*)h->Y;
     T* Gt = (T*)h->Fct;                  // sp x 3sp
@@ -1348,8 +1351,8 @@ slab_status sweep_factor_indef(slab_handle* h) {
             SLAB_CK_LAUNCH(h);
             if (hasNext) {
                 const int64_t n2 = 2 * blk;
-                gj_fill_bottom_kernel<T><<<(unsigned)((n2 + 255) / 256), 256, 0, h->stream>>>(Gb, sp, To + j * blk,
-                                                                                             Tb + (j + 1) * blk);
+                gj_fill_bottom_kernel<T><<<(unsigned)((n2 + 255) / 256), 256, 0, h->stream>>>(
+                    Gb, sp, To + j * blk, Tb + (j + 1) * blk, Tl ? Tl + j * blk : nullptr);
                 SLAB_CK_LAUNCH(h);
             }
             gj_init_rows_kernel<T><<<(sp + 255) / 256, 256, 0, h->stream>>>(act0, w.pflag, sp);
@@ -1408,7 +1411,12 @@ slab_status sweep_factor_indef(slab_handle* h) {
                                                                                     hasNext ? Wn + j * blk : nullptr);
             SLAB_CK_LAUNCH(h);
         }
-        if (hasNext && (st = transpose<T>(h, To + j * blk, ToT + j * blk, sp))) return st;   // T_{j+1,j}
+        if (!Tl && hasNext && (st = transpose<T>(h, To + j * blk, ToT + j * blk, sp))) return st;   // T_{j+1,j}
+        if (Tl) {                        // factors of the transposed sweep (A^T solves)
+            if ((st = transpose<T>(h, Sinv + j * blk, (T*)h->SinvT + j * blk, sp))) return st;
+            if (hasNext && (st = transpose<T>(h, Wn + j * blk, (T*)h->WT + j * blk, sp))) return st;
+            if (hasNext && (st = transpose<T>(h, Tl + j * blk, (T*)h->TlT + j * blk, sp))) return st;
+        }
     }
     return SLAB_OK;
 }
@@ -1454,7 +1462,7 @@ slab_status sweep_solve_indef(slab_handle* h, int K) {
     const int64_t vb = (int64_t)sp * h->kcap;
     T* Sinv = (T*)h->Linv;
     T* Wn = (T*)h->Y;
-    T* ToT = (T*)h->ToT;
+    T* ToT = h->Tl ? (T*)h->Tl : (T*)h->ToT;     // T_{j+1,j}
     T* X = (T*)h->wX;
     T* Z = (T*)h->wZ;
     slab_status st;
@@ -1476,12 +1484,45 @@ slab_status sweep_solve_indef(slab_handle* h, int K) {
     return SLAB_OK;
 }
 
+// Algorithm 2 for T^T (the adjoint of the nonsymmetric kind) with the factors of T = L U, L block
+// lower bidiagonal (S_j, T_{j+1,j}), U unit block upper bidiagonal (W_j): T^T = U^T L^T, so
+//   forward  y_j = f_j - W_{j-1}^T y_{j-1};   backward  x_j = S_j^{-T} (y_j - T_{j+1,j}^T x_{j+1}),
+// on X ([NI][kcap][s_pad]), result in X.
+template <typename T>
+slab_status sweep_solve_indef_transposed(slab_handle* h, int K) {
+    const int NI = h->td.NI, sp = h->td.s_pad;
+    const int64_t blk = (int64_t)sp * sp;
+    const int64_t vb = (int64_t)sp * h->kcap;
+    T* SinvT = (T*)h->SinvT;
+    T* WT = (T*)h->WT;
+    T* TlT = (T*)h->TlT;
+    T* X = (T*)h->wX;
+    T* Z = (T*)h->wZ;
+    slab_status st;
+    for (int j = 1; j < NI; ++j)
+        if ((st = gemm_tn<T>(h, KC_SOLVE_PROD, sp, K, sp, T(-1), WT + (j - 1) * blk, sp, X + (j - 1) * vb, sp, T(1),
+                             X + j * vb, sp, 1, 0)))
+            return st;
+    for (int j = NI - 1; j >= 0; --j) {
+        if (j < NI - 1 && (st = gemm_tn<T>(h, KC_SOLVE_PROD, sp, K, sp, T(-1), TlT + j * blk, sp, Z + (j + 1) * vb, sp,
+                                           T(1), X + j * vb, sp, 1, 0)))
+            return st;
+        if ((st = gemm_tn<T>(h, KC_SOLVE_PROD, sp, K, sp, T(1), SinvT + j * blk, sp, X + j * vb, sp, T(0), Z + j * vb,
+                             sp, 1, 0)))
+            return st;
+    }
+    for (int j = 0; j < NI; ++j)
+        SLAB_CK(h, cudaMemcpyAsync(X + j * vb, Z + j * vb, (size_t)K * sp * sizeof(T), cudaMemcpyDeviceToDevice,
+                                   h->stream));
+    return SLAB_OK;
+}
+
 // Factor-phase layout: Fct[j] = [S_j ; Y_j^T ; L_j^{-T}] (3 s_pad x s_pad; for the last j the
 // L^{-T} block sits right below S), plus the transposed copies Lin[j] = L_j^{-1} and Yn[j] = Y_j
 // for the solve products.
 template <typename T>
 slab_status sweep_factor(slab_handle* h) {
-    if (h->kind == SLAB_HELMHOLTZ) return sweep_factor_indef<T>(h);
+    if (h->kind == SLAB_HELMHOLTZ || h->kind == SLAB_CONVECTION) return sweep_factor_indef<T>(h);
     if (h->stage2) return cr_factor<T>(h);
     const int NI = h->td.NI, sp = h->td.s_pad;
     const int64_t blk = (int64_t)sp * sp;
@@ -1518,7 +1559,8 @@ slab_status sweep_factor(slab_handle* h) {
 // Algorithm 2 on the interface workspace X ([NI][kcap][s_pad], right-hand sides 0..K-1), result in X.
 template <typename T>
 slab_status sweep_solve(slab_handle* h, int K) {
-    if (h->kind == SLAB_HELMHOLTZ) return sweep_solve_indef<T>(h, K);
+    if (h->kind == SLAB_CONVECTION && h->transposed) return sweep_solve_indef_transposed<T>(h, K);
+    if (h->kind == SLAB_HELMHOLTZ || h->kind == SLAB_CONVECTION) return sweep_solve_indef<T>(h, K);
     if (h->stage2) return cr_solve<T>(h, K);
     const int NI = h->td.NI, sp = h->td.s_pad;
     const int64_t blk = (int64_t)sp * sp;

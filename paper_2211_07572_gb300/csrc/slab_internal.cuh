@@ -93,7 +93,11 @@ struct slab_handle {
     double* AX;               // AX[y][x]: face (x,y)-(x+1,y)
     double* AY;               // AY[y][x]: face (x,y)-(x,y+1)
     double* DG;               // DG[y][x]: diagonal of Ahat at (x,y)
-    double* kappa;            // copy of the node coefficient (DIFFUSION), for the gradient
+    double* kappa;            // copy of the node coefficient (DIFFUSION, CONVECTION), for the gradient
+    double* AXT;              // CONVECTION: AXT[y][x] = -h^2 A[(x+1,y),(x,y)] (AX: -h^2 A[(x,y),(x+1,y)])
+    double* AYT;              // CONVECTION: AYT[y][x] = -h^2 A[(x,y+1),(x,y)] (AY: -h^2 A[(x,y),(x,y+1)])
+    int transposed;           // set while a solve with A^T runs (CONVECTION adjoint)
+    const double* beta;       // CONVECTION: the caller's velocity field, set during slab_factor only
     double* AZ;               // 3-D: AZ[z][y][x]: face (x,y,z)-(x,y,z+1)
 
     // 3-D Stage 1 (tree3d.cu): per-node dense factors, node ids height-major (see Tree3Plan)
@@ -113,6 +117,12 @@ struct slab_handle {
     void* tWtb;               // Helmholtz only: [NS][s+1][m*2m] W = S^{-1} B (top/bot columns)
     void* tWI;                // Helmholtz only: [NS][H][2][m][s_pad] W for the interface columns
     void* ToT;                // Helmholtz only: [NI-1][s_pad][s_pad] T_{q+1,q} (row-major)
+    // CONVECTION only: the elimination of A^T from the same tree (see tree.cu), and Stage 2's
+    // T_{q+1,q} plus the transposed factors of the A^T sweep
+    void *tLinvT, *tZtbT, *tWtbT, *tZIT, *tWIT, *tRIc;
+    void* Tl;                 // [NI-1][s_pad][s_pad] T_{q+1,q} as assembled (Stage-2 scalar)
+    void* Tl1;                // mixed mode: T_{q+1,q} in the Stage-1 scalar (factor only)
+    void *SinvT, *WT, *TlT;   // S_j^{-T}, W_j^T, T_{j+1,j}^T (Stage-2 scalar)
     int stage2;               // 0: sequential sweep (Algorithm 1), 1: odd-even elimination order
     void *crD, *crE, *crW, *crLT, *crPt, *crP, *crQt, *crQ;   // odd-even order storage
 
@@ -355,11 +365,13 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
     return cudaLaunchKernelEx(&cfg, kernel, ((KArgs)args)...);
 }
 
-// error helper
-slab_status slab_cuda_check(slab_handle* h, cudaError_t e);
-#define SLAB_CK(h, call)                                             \
-    do {                                                             \
-        cudaError_t _e = (call);                                     \
-        if (_e != cudaSuccess) return slab_cuda_check((h), _e);      \
+// error helper: latches SLAB_ECUDA in the handle; with SLAB_CUDA_TRACE set in the environment it
+// also prints the CUDA error and the source line of the failed call (run with
+// CUDA_LAUNCH_BLOCKING=1 to attribute an asynchronous kernel fault to its launch)
+slab_status slab_cuda_check(slab_handle* h, cudaError_t e, const char* file, int line);
+#define SLAB_CK(h, call)                                                         \
+    do {                                                                         \
+        cudaError_t _e = (call);                                                 \
+        if (_e != cudaSuccess) return slab_cuda_check((h), _e, __FILE__, __LINE__); \
     } while (0)
 #define SLAB_CK_LAUNCH(h) SLAB_CK(h, cudaGetLastError())

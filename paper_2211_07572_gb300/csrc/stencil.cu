@@ -11,19 +11,32 @@
 
 namespace {
 
+// CONVECTION (beta = [2][(n+1)^2], velocity x then y): the central first-order term makes the
+// couplings direction dependent, AX[P] = -h^2 A[P, P+e_x] = k - beta_x(P) h/2 and
+// AXT[P] = -h^2 A[P+e_x, P] = k + beta_x(P+e_x) h/2 (y likewise); the other kinds leave AXT / AYT alone.
 __global__ void coeff_kernel(int n, int kind, const double* __restrict__ kappa,
-                             const double* __restrict__ c, double omega, double* AX, double* AY,
-                             double* DG) {
+                             const double* __restrict__ c, double omega, const double* __restrict__ beta,
+                             double* AX, double* AY, double* DG, double* AXT, double* AYT) {
     const int np1 = n + 1;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
     if (x > n) return;
     const int64_t P = (int64_t)y * np1 + x;
     auto face = [&](int64_t a, int64_t b2) -> double {
-        return kind == SLAB_DIFFUSION ? 0.5 * (kappa[a] + kappa[b2]) : 1.0;
+        return (kind == SLAB_DIFFUSION || kind == SLAB_CONVECTION) ? 0.5 * (kappa[a] + kappa[b2]) : 1.0;
     };
     AX[P] = x < n ? face(P, P + 1) : 0.0;
     AY[P] = y < n ? face(P, P + np1) : 0.0;
+    if (kind == SLAB_CONVECTION) {
+        const int64_t nodes = (int64_t)np1 * np1;
+        const double hh = 0.5 / n;
+        const double* bx = beta;
+        const double* by = beta + nodes;
+        AXT[P] = x < n ? AX[P] + hh * bx[P + 1] : 0.0;
+        AYT[P] = y < n ? AY[P] + hh * by[P + np1] : 0.0;
+        if (x < n) AX[P] -= hh * bx[P];
+        if (y < n) AY[P] -= hh * by[P];
+    }
     double d = 0.0;
     if (x >= 1 && x < n && y >= 1 && y < n) {
         d = face(P, P - 1) + face(P, P + 1) + face(P, P - np1) + face(P, P + np1);
@@ -35,7 +48,10 @@ __global__ void coeff_kernel(int n, int kind, const double* __restrict__ kappa,
     DG[P] = d;
 }
 
-// r = f - A u (RESID) or y = A u, 2-D, k right-hand sides.  Block: 256 threads along x; each
+// r = f - A u (RESID) or y = A u, 2-D, k right-hand sides.  Row P couples to its east / north
+// neighbours with -n^2 AX[P], -n^2 AY[P] and to its west / south neighbours with -n^2 AXW[P - e_x],
+// -n^2 AYS[P - e_y] (AXW = AX, AYS = AY for the symmetric kinds; the transposed couplings for
+// CONVECTION, and the roles swapped for A^T).  Block: 256 threads along x; each
 // block covers ST_ROWS grid rows and a group of up to ST_Q right-hand sides (blockIdx.z), so the
 // five coefficients of a node are read once per group.
 // Norms: each block writes its partial sums of r^2 and f^2 per right-hand side to part; the last
@@ -45,6 +61,8 @@ constexpr int ST_Q = 8;
 template <bool RESID, bool NORMF>
 __global__ void __launch_bounds__(256) stencil2d_kernel(int n, int k, const double* __restrict__ AX,
                                                         const double* __restrict__ AY,
+                                                        const double* __restrict__ AXW,
+                                                        const double* __restrict__ AYS,
                                                         const double* __restrict__ DG,
                                                         const double* __restrict__ u,
                                                         const double* __restrict__ f, double* r,
@@ -78,9 +96,9 @@ __global__ void __launch_bounds__(256) stencil2d_kernel(int n, int k, const doub
             const int y = y0 + yy;
             const int64_t P = (int64_t)y * np1 + x;
             const double dg = n2 * DG[P];
-            const double aw = x > 1 ? n2 * AX[P - 1] : 0.0;
+            const double aw = x > 1 ? n2 * AXW[P - 1] : 0.0;
             const double ae = x < s ? n2 * AX[P] : 0.0;
-            const double as = y > 1 ? n2 * AY[P - np1] : 0.0;
+            const double as = y > 1 ? n2 * AYS[P - np1] : 0.0;
             const double an = y < s ? n2 * AY[P] : 0.0;
             const int64_t o = (int64_t)(y - 1) * s + (x - 1);
 #pragma unroll
@@ -352,7 +370,8 @@ slab_status launch_coefficients(slab_handle* h, const double* kappa, const doubl
     }
     dim3 grid((n + 1 + 127) / 128, n + 1);
     SLAB_PROF(h, KC_COEFF);
-    coeff_kernel<<<grid, 128, 0, h->stream>>>(n, h->kind, kappa, c, h->omega, h->AX, h->AY, h->DG);
+    coeff_kernel<<<grid, 128, 0, h->stream>>>(n, h->kind, kappa, c, h->omega, h->beta, h->AX, h->AY, h->DG, h->AXT,
+                                              h->AYT);
     SLAB_CK_LAUNCH(h);
     return SLAB_OK;
 }
@@ -382,6 +401,17 @@ slab_status ensure_red(slab_handle* h, int k) {
     }
     return SLAB_OK;
 }
+
+namespace {
+// East / north and west / south coupling arrays of the 2-D stencil: A's, or A^T's while a
+// transposed solve runs (its east coupling is A's west one read from the other end of the face).
+struct Couplings { const double *e, *nn, *w, *so; };
+Couplings couplings2d(const slab_handle* h) {
+    if (!h->AXT) return {h->AX, h->AY, h->AX, h->AY};
+    if (h->transposed) return {h->AXT, h->AYT, h->AX, h->AY};
+    return {h->AX, h->AY, h->AXT, h->AYT};
+}
+}  // namespace
 
 slab_status launch_residual(slab_handle* h, const double* u, const double* f, double* r, int k,
                             double* nrm_r, double* nrm_f) {
@@ -417,12 +447,13 @@ slab_status launch_residual(slab_handle* h, const double* u, const double* f, do
         part = h->red_part; tickets = h->red_tickets;
     }
     SLAB_PROF(h, KC_STENCIL);
+    const Couplings cp = couplings2d(h);
     if (nrm_f)
-        stencil2d_kernel<true, true><<<grid, 256, 0, h->stream>>>(n, k, h->AX, h->AY, h->DG, u, f, r, nrm_r, nrm_f,
-                                                                  part, tickets);
+        stencil2d_kernel<true, true><<<grid, 256, 0, h->stream>>>(n, k, cp.e, cp.nn, cp.w, cp.so, h->DG, u, f, r,
+                                                                  nrm_r, nrm_f, part, tickets);
     else
-        stencil2d_kernel<true, false><<<grid, 256, 0, h->stream>>>(n, k, h->AX, h->AY, h->DG, u, f, r, nrm_r,
-                                                                   nullptr, part, tickets);
+        stencil2d_kernel<true, false><<<grid, 256, 0, h->stream>>>(n, k, cp.e, cp.nn, cp.w, cp.so, h->DG, u, f, r,
+                                                                   nrm_r, nullptr, part, tickets);
     SLAB_CK_LAUNCH(h);
     return SLAB_OK;
 }
@@ -455,8 +486,9 @@ slab_status launch_apply(slab_handle* h, const double* x, double* y, int k) {
     }
     dim3 grid((s + 255) / 256, (s + ST_ROWS - 1) / ST_ROWS, (k + ST_Q - 1) / ST_Q);
     SLAB_PROF(h, KC_STENCIL);
-    stencil2d_kernel<false, false><<<grid, 256, 0, h->stream>>>(n, k, h->AX, h->AY, h->DG, x, nullptr, y, nullptr,
-                                                                nullptr, nullptr, nullptr);
+    const Couplings cp = couplings2d(h);
+    stencil2d_kernel<false, false><<<grid, 256, 0, h->stream>>>(n, k, cp.e, cp.nn, cp.w, cp.so, h->DG, x, nullptr, y,
+                                                                nullptr, nullptr, nullptr, nullptr);
     SLAB_CK_LAUNCH(h);
     return SLAB_OK;
 }

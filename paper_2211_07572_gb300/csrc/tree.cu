@@ -34,6 +34,20 @@ struct TreeArgs {
     T* RI;
     T* Wtb;           // indefinite kind: W = S^{-1} B for the top/bot columns (else null)
     T* WI;            // indefinite kind: W = S^{-1} B for the interface columns, per height
+    // Nonsymmetric kind only (else null).  A^T's couplings: AXT[y][x] = -h^2 A[(x+1,y),(x,y)],
+    // AYT[y][x] = -h^2 A[(x,y+1),(x,y)] (AX / AY hold the forward ones, -h^2 A[(x,y),(x+1,y)] ...).
+    // The factor stores, besides S^{-1} (Linv), C^T (Ztb, ZI: the couplings of the other nodes
+    // into the separator) and W = S^{-1} B (Wtb, WI), the arrays of A^T's elimination: S^{-T}
+    // (LinvT), B (ZtbT, ZIT) and V = S^{-T} C^T (WtbT, WIT); RIc holds the condensed
+    // interface-row x top/bot-column couplings (the other orientation of RI).
+    const double* AXT;
+    const double* AYT;
+    T* LinvT;
+    T* ZtbT;
+    T* WtbT;
+    T* ZIT;
+    T* WIT;
+    T* RIc;
     unsigned* status;
     __device__ int64_t node(int t, int c) const { return (int64_t)t * (s + 1) + c; }
     __device__ T* linv(int t, int c) const { return Linv + node(t, c) * m * m; }
@@ -49,6 +63,13 @@ struct TreeArgs {
     __device__ T* ri(int t, int k, int tb, int side) const {
         return RI + ((((int64_t)t * H + k) * 2 + tb) * 2 + side) * m * s_pad;
     }
+    __device__ T* ric(int t, int k, int tb, int side) const {
+        return RIc + ((((int64_t)t * H + k) * 2 + tb) * 2 + side) * m * s_pad;
+    }
+    __device__ T* per_height(T* base, int t, int k, int side) const {
+        return base + (((int64_t)t * H + k) * 2 + side) * m * s_pad;
+    }
+    __device__ T* per_node(T* base, int t, int c, int blk) const { return base + node(t, c) * blk; }
 };
 
 template <typename T>
@@ -320,6 +341,257 @@ __global__ void __launch_bounds__(TB_THREADS) tree_factor_kernel(TreeArgs<T> A, 
                 }
             rtd[(int64_t)a * sp] = vt;
             rbd[(int64_t)a * sp] = vb;
+        }
+    }
+}
+
+// One height of the cyclic reduction for the nonsymmetric kind (the same elimination as the
+// indefinite kind with both orientations of every coupling kept).  Node c's separator block S,
+// its row couplings B (separator rows x {top, bot, interface} columns) and column couplings C
+// ({top, bot, interface} rows x separator columns) give
+//   R_merged = R_others - C S^{-1} B,
+// with S^{-1} from pivoted Gauss-Jordan.  Stored for A: S^{-1}, C^T, W = S^{-1} B; for A^T (whose
+// separator block is S^T, row couplings C^T, column couplings B^T): S^{-T}, B, V = S^{-T} C^T.
+// The condensed couplings are kept in both orientations: RI (top/bot rows x interface columns)
+// and RIc (interface rows x top/bot columns).  grid = (node, column chunk, slab), as above.
+template <typename T>
+__global__ void __launch_bounds__(TB_THREADS) tree_factor_ns_kernel(TreeArgs<T> A, int k) {
+    __shared__ T S[MAXM * SP2];        // S (stride SP), then W = S^{-1} B (stride SP2)
+    __shared__ T Li[MAXM * SP];        // S^{-1}
+    __shared__ T Bt[MAXM * SP2];       // B, then C^T
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int t = blockIdx.z;
+    const int c = (2 * blockIdx.x + 1) << k;
+    const int s = A.s, m = A.m;
+    if (c > s) return;
+    const int lo = c - (1 << k) + 1;
+    const int hi = min(s, c + (1 << k) - 1);
+    const int w = hi - lo + 1;
+    const int ncols = 2 * w;
+    const int q0 = blockIdx.y * TB_THREADS;
+    if (blockIdx.y > 0 && q0 >= ncols) return;
+    const int alpha = k > 0 ? c - (1 << (k - 1)) : 0;
+    const int kb = tree_right_height(s, c, k);
+    const int beta = kb >= 0 ? c + (1 << kb) : 0;
+    const int x0 = t * A.b + 1;
+    const int np1 = A.n + 1;
+    const double* DGr = A.DG + (int64_t)c * np1;
+    const double* AXr = A.AX + (int64_t)c * np1;       // -h^2 A[(x,c),(x+1,c)]
+    const double* AXTr = A.AXT + (int64_t)c * np1;     // -h^2 A[(x+1,c),(x,c)]
+    const T* Ra = alpha ? A.rtb(t, alpha) : nullptr;   // alpha's rows/cols: top 0..m-1, bot m..2m-1
+    const T* Rb = beta ? A.rtb(t, beta) : nullptr;
+    const int m2 = 2 * m;
+
+    // S = D_c + R_alpha[bot,bot] + R_beta[top,top];  B = couplings of row c to [top | bot]
+    for (int idx = tid; idx < m * m; idx += nth) {
+        const int i = idx / m, j = idx % m;
+        double v = 0.0;
+        if (i == j) v = DGr[x0 + i];
+        else if (j == i + 1) v = -AXr[x0 + i];
+        else if (j == i - 1) v = -AXTr[x0 + j];
+        T tv = (T)v;
+        if (Ra) tv += Ra[(m + i) * m2 + (m + j)];
+        if (Rb) tv += Rb[i * m2 + j];
+        S[i * SP + j] = tv;
+    }
+    for (int idx = tid; idx < m * m2; idx += nth) {
+        const int i = idx / m2, j = idx % m2;
+        T v = T(0);
+        if (j < m) {
+            if (Ra) v = Ra[(m + i) * m2 + j];                       // R_alpha[bot i][top j]
+            else if (i == j && c - 1 >= 1) v = (T)(-A.AYT[(int64_t)(c - 1) * np1 + x0 + i]);
+        } else {
+            const int jj = j - m;
+            if (Rb) v = Rb[i * m2 + m + jj];                        // R_beta[top i][bot jj]
+            else if (i == jj && c + 1 <= s) v = (T)(-A.AY[(int64_t)c * np1 + x0 + i]);
+        }
+        Bt[i * SP2 + j] = v;
+    }
+    __syncthreads();
+    gj_inv_small<T>(S, Li, m, A.status);                            // Li = S^{-1}
+    T* Wt = S;
+    for (int idx = tid; idx < m * m2; idx += nth) {                 // W = S^{-1} B (into S's buffer)
+        const int i = idx / m2, j = idx % m2;
+        T acc = T(0);
+        for (int l = 0; l < m; ++l) acc += Li[i * SP + l] * Bt[l * SP2 + j];
+        Wt[i * SP2 + j] = acc;
+    }
+    __syncthreads();
+    if (blockIdx.y == 0) {
+        T* Lg = A.linv(t, c);
+        T* LTg = A.per_node(A.LinvT, t, c, m * m);
+        for (int idx = tid; idx < m * m; idx += nth) {
+            const int i = idx / m, j = idx % m;
+            Lg[idx] = Li[i * SP + j];
+            LTg[idx] = Li[j * SP + i];
+        }
+        T* Bg = A.per_node(A.ZtbT, t, c, m * m2);
+        T* Wg = A.wtb(t, c);
+        for (int idx = tid; idx < m * m2; idx += nth) {
+            Bg[idx] = Bt[(idx / m2) * SP2 + idx % m2];
+            Wg[idx] = Wt[(idx / m2) * SP2 + idx % m2];
+        }
+    }
+    __syncthreads();
+    // C^T: Ct[i][j] = coupling of top/bot node j into separator node i
+    for (int idx = tid; idx < m * m2; idx += nth) {
+        const int i = idx / m2, j = idx % m2;
+        T v = T(0);
+        if (j < m) {
+            if (Ra) v = Ra[j * m2 + m + i];                         // R_alpha[top j][bot i]
+            else if (i == j && c - 1 >= 1) v = (T)(-A.AY[(int64_t)(c - 1) * np1 + x0 + i]);
+        } else {
+            const int jj = j - m;
+            if (Rb) v = Rb[(m + jj) * m2 + i];                      // R_beta[bot jj][top i]
+            else if (i == jj && c + 1 <= s) v = (T)(-A.AYT[(int64_t)c * np1 + x0 + i]);
+        }
+        Bt[i * SP2 + j] = v;
+    }
+    __syncthreads();
+    const T* Ct = Bt;
+    if (blockIdx.y == 0) {
+        T* Cg = A.ztb(t, c);
+        T* Vg = A.per_node(A.WtbT, t, c, m * m2);
+        for (int idx = tid; idx < m * m2; idx += nth) {
+            const int i = idx / m2, j = idx % m2;
+            Cg[idx] = Ct[i * SP2 + j];
+            T acc = T(0);                                           // V = S^{-T} C^T
+            for (int l = 0; l < m; ++l) acc += Li[l * SP + i] * Ct[l * SP2 + j];
+            Vg[idx] = acc;
+        }
+        T* Rg = A.rtb(t, c);
+        for (int idx = tid; idx < m2 * m2; idx += nth) {
+            const int a = idx / m2, bcol = idx % m2;
+            T v = T(0);
+            for (int l = 0; l < m; ++l) v -= Ct[l * SP2 + a] * Wt[l * SP2 + bcol];
+            if (a < m && bcol < m && Ra) v += Ra[a * m2 + bcol];                     // alpha top x top
+            if (a >= m && bcol >= m && Rb) v += Rb[a * m2 + bcol];                   // beta bot x bot
+            Rg[idx] = v;
+        }
+    }
+    // interface columns of the segment: one thread per column
+    const int q = q0 + tid;
+    if (q < ncols) {
+        const int side = q / w;
+        const int j = lo + q % w;
+        const int rr = j - 1;
+        const int sp = A.s_pad;
+        T vec[MAXM], z[MAXM];
+        // (1) b = coupling of the separator rows to interface node j; W column z = S^{-1} b
+#pragma unroll
+        for (int i = 0; i < MAXM; ++i) vec[i] = T(0);
+        if (j < c) {
+            const T* src = A.ri(t, k - 1, 1, side) + rr;
+#pragma unroll
+            for (int i = 0; i < MAXM; ++i) if (i < m) vec[i] = src[(int64_t)i * sp];
+        } else if (j == c) {
+            if (side == 0) {
+                if (t >= 1) vec[0] = (T)(-AXTr[x0 - 1]);              // A[(x0,c),(x0-1,c)]
+            } else {
+                if (t <= A.NS - 2) {
+#pragma unroll
+                    for (int i = 0; i < MAXM; ++i) if (i == m - 1) vec[i] = (T)(-AXr[x0 + m - 1]);
+                }
+            }
+        } else {
+            const T* src = A.ri(t, kb, 0, side) + rr;
+#pragma unroll
+            for (int i = 0; i < MAXM; ++i) if (i < m) vec[i] = src[(int64_t)i * sp];
+        }
+#pragma unroll
+        for (int i = 0; i < MAXM; ++i) {
+            T acc = T(0);
+#pragma unroll
+            for (int l = 0; l < MAXM; ++l)
+                if (l < m && i < m) acc += Li[i * SP + l] * vec[l];
+            z[i] = acc;
+        }
+        {
+            T* bd = A.per_height(A.ZIT, t, k, side) + rr;
+            T* wd = A.per_height(A.WI, t, k, side) + rr;
+#pragma unroll
+            for (int i = 0; i < MAXM; ++i)
+                if (i < m) {
+                    bd[(int64_t)i * sp] = vec[i];
+                    wd[(int64_t)i * sp] = z[i];
+                }
+        }
+        // condensed top/bot rows x this column: RI = R_child - C[tb, sep] z
+        {
+            const T* rta = (j < c) ? A.ri(t, k - 1, 0, side) + rr : nullptr;
+            const T* rbb = (j > c) ? A.ri(t, kb, 1, side) + rr : nullptr;
+            T* rtd = A.ri(t, k, 0, side) + rr;
+            T* rbd = A.ri(t, k, 1, side) + rr;
+            for (int a = 0; a < m; ++a) {
+                T vt = rta ? rta[(int64_t)a * sp] : T(0);
+                T vb = rbb ? rbb[(int64_t)a * sp] : T(0);
+#pragma unroll
+                for (int i = 0; i < MAXM; ++i)
+                    if (i < m) {
+                        vt -= Ct[i * SP2 + a] * z[i];
+                        vb -= Ct[i * SP2 + m + a] * z[i];
+                    }
+                rtd[(int64_t)a * sp] = vt;
+                rbd[(int64_t)a * sp] = vb;
+            }
+        }
+        // (2) c = coupling of interface node j into the separator columns; V column z = S^{-T} c
+#pragma unroll
+        for (int i = 0; i < MAXM; ++i) vec[i] = T(0);
+        if (j < c) {
+            const T* src = A.ric(t, k - 1, 1, side) + rr;
+#pragma unroll
+            for (int i = 0; i < MAXM; ++i) if (i < m) vec[i] = src[(int64_t)i * sp];
+        } else if (j == c) {
+            if (side == 0) {
+                if (t >= 1) vec[0] = (T)(-AXr[x0 - 1]);               // A[(x0-1,c),(x0,c)]
+            } else {
+                if (t <= A.NS - 2) {
+#pragma unroll
+                    for (int i = 0; i < MAXM; ++i) if (i == m - 1) vec[i] = (T)(-AXTr[x0 + m - 1]);
+                }
+            }
+        } else {
+            const T* src = A.ric(t, kb, 0, side) + rr;
+#pragma unroll
+            for (int i = 0; i < MAXM; ++i) if (i < m) vec[i] = src[(int64_t)i * sp];
+        }
+#pragma unroll
+        for (int i = 0; i < MAXM; ++i) {
+            T acc = T(0);
+#pragma unroll
+            for (int l = 0; l < MAXM; ++l)
+                if (l < m && i < m) acc += Li[l * SP + i] * vec[l];
+            z[i] = acc;
+        }
+        {
+            T* cd = A.zi(t, k, side) + rr;
+            T* vd = A.per_height(A.WIT, t, k, side) + rr;
+#pragma unroll
+            for (int i = 0; i < MAXM; ++i)
+                if (i < m) {
+                    cd[(int64_t)i * sp] = vec[i];
+                    vd[(int64_t)i * sp] = z[i];
+                }
+        }
+        // condensed interface row x top/bot columns: RIc = R_child - c^T W[:, tb]
+        {
+            const T* rta = (j < c) ? A.ric(t, k - 1, 0, side) + rr : nullptr;
+            const T* rbb = (j > c) ? A.ric(t, kb, 1, side) + rr : nullptr;
+            T* rtd = A.ric(t, k, 0, side) + rr;
+            T* rbd = A.ric(t, k, 1, side) + rr;
+            for (int a = 0; a < m; ++a) {
+                T vt = rta ? rta[(int64_t)a * sp] : T(0);
+                T vb = rbb ? rbb[(int64_t)a * sp] : T(0);
+#pragma unroll
+                for (int i = 0; i < MAXM; ++i)
+                    if (i < m) {
+                        vt -= vec[i] * Wt[i * SP2 + a];
+                        vb -= vec[i] * Wt[i * SP2 + m + a];
+                    }
+                rtd[(int64_t)a * sp] = vt;
+                rbd[(int64_t)a * sp] = vb;
+            }
         }
     }
 }
@@ -947,13 +1219,21 @@ __global__ void import_x_kernel(SolveArgs<T> P, const double* in, int NI, int r0
 
 template <typename T>
 TreeArgs<T> make_tree_args(slab_handle* h) {
-    TreeArgs<T> a;
+    TreeArgs<T> a{};
     a.s = h->td.s; a.s_pad = h->td.s_pad; a.m = h->td.m; a.H = h->td.H; a.NS = h->td.NS;
     a.b = h->b; a.n = h->n;
     a.AX = h->AX; a.AY = h->AY; a.DG = h->DG;
     a.Linv = (T*)h->tLinv; a.Ztb = (T*)h->tZtb; a.Rtb = (T*)h->tRtb; a.ZI = (T*)h->tZI; a.RI = (T*)h->tRI;
     a.Wtb = (T*)h->tWtb; a.WI = (T*)h->tWI;
+    a.AXT = h->AXT; a.AYT = h->AYT;
+    a.LinvT = (T*)h->tLinvT; a.ZtbT = (T*)h->tZtbT; a.WtbT = (T*)h->tWtbT;
+    a.ZIT = (T*)h->tZIT; a.WIT = (T*)h->tWIT; a.RIc = (T*)h->tRIc;
     a.status = h->dstatus;
+    if (h->transposed && h->kind == SLAB_CONVECTION) {
+        // A^T's elimination: separator inverse S^{-T}, couplings into the separators B (was C^T),
+        // the back-substitution columns V = S^{-T} C^T (was W = S^{-1} B)
+        a.Linv = a.LinvT; a.Ztb = a.ZtbT; a.ZI = a.ZIT; a.Wtb = a.WtbT; a.WI = a.WIT;
+    }
     return a;
 }
 
@@ -978,12 +1258,14 @@ slab_status tree_factor(slab_handle* h) {
     TreeArgs<T> a = make_tree_args<T>(h);
     const TreeDims& d = h->td;
     const bool indef = h->kind == SLAB_HELMHOLTZ;
+    const bool nonsym = h->kind == SLAB_CONVECTION;
     for (int k = 0; k < d.H; ++k) {
         const int cnt = tree_nodes_at(d.s, k);
         if (!cnt) continue;
         dim3 grid(cnt, chunks_at(d.s, k), d.NS);
         SLAB_PROF(h, KC_TREE_FACTOR);
-        if (indef) tree_factor_kernel<T, true><<<grid, TB_THREADS, 0, h->stream>>>(a, k);
+        if (nonsym) tree_factor_ns_kernel<T><<<grid, TB_THREADS, 0, h->stream>>>(a, k);
+        else if (indef) tree_factor_kernel<T, true><<<grid, TB_THREADS, 0, h->stream>>>(a, k);
         else tree_factor_kernel<T, false><<<grid, TB_THREADS, 0, h->stream>>>(a, k);
         SLAB_CK_LAUNCH(h);
         if (slab_debug() && slab_debug_status(h, "slab tree factor (height, nodes)", k, cnt)) return SLAB_ESINGULAR;
@@ -1024,7 +1306,7 @@ slab_status tree_down_scatter(slab_handle* h, double* U, int accumulate, int r0,
         const int dcw = down_chunk(cnt * d.NS, wmax);
         dim3 grid(cnt, (2 * wmax + dcw - 1) / dcw, d.NS);
         SLAB_PROF(h, KC_TREE_DOWN);
-        if (h->kind == SLAB_HELMHOLTZ)
+        if (h->kind == SLAB_HELMHOLTZ || h->kind == SLAB_CONVECTION)
             tree_down_kernel<T, true><<<grid, TB_THREADS, 0, h->stream>>>(p, k, U, accumulate, r0, (T*)h->wVp,
                                                                           (unsigned*)h->wVtk, dcw);
         else

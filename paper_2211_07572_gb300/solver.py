@@ -37,7 +37,8 @@ class SlabSolver:
 
     dim, n: grid (unit square/cube, h = 1/n); b: interface spacing (b | n);
     kind: 0 Poisson, 1 diffusion -div(kappa grad u), 2 Helmholtz -Lap u - (omega/c)^2 u;
-    kappa / c: node fields with (n+1)^dim entries; precision: "fp32" (FP32 factor, FP64
+    kappa / c: node fields with (n+1)^dim entries; beta: the velocity components (dim, (n+1)^dim)
+    of the convection-diffusion kind; precision: "fp32" (FP32 factor, FP64
     refinement), "tf32" (as fp32 with single-pass TF32 tensor products in the factor) or
     "fp64" (plain FP64 path); stage2: "auto", "sweep" (Algorithm 1) or
     "oddeven"; interface_precision: precision of the interface system (default: "fp64" for
@@ -46,7 +47,7 @@ class SlabSolver:
     """
 
     def __init__(self, dim: int, n: int, b: int, kind: int, kappa=None, c=None, omega: float = 0.0,
-                 precision: str = "fp32", rtol: float = 1e-10, max_refine: int = 30,
+                 beta=None, precision: str = "fp32", rtol: float = 1e-10, max_refine: int = 30,
                  stream: Optional[torch.cuda.Stream] = None, device=None, profile: bool = False,
                  stage2: str = "auto", interface_precision: Optional[str] = None, krylov: int = 0):
         self.lib = _lib.load()
@@ -56,8 +57,9 @@ class SlabSolver:
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         self._kappa = _dev(kappa, self.device)
         self._c = _dev(c, self.device)
+        self._beta = _dev(beta, self.device)
         grid = _lib.SlabGrid(dim, n)
-        co = _lib.SlabCoeffs(kind, _ptr(self._kappa), _ptr(self._c), float(omega))
+        co = _lib.SlabCoeffs(kind, _ptr(self._kappa), _ptr(self._c), float(omega), _ptr(self._beta))
         opts = _lib.SlabOpts()
         self.lib.slab_default_opts(ctypes.byref(opts))
         opts.factor_prec = _PREC[precision]
@@ -141,6 +143,12 @@ class SlabSolver:
         x = self._vec(x)
         y = torch.empty_like(x)
         _lib.check(self.lib.slab_apply(self.h, _ptr(x), _ptr(y), x.shape[0]), "apply")
+        return y
+
+    def apply_transpose(self, x) -> torch.Tensor:
+        x = self._vec(x)
+        y = torch.empty_like(x)
+        _lib.check(self.lib.slab_apply_transpose(self.h, _ptr(x), _ptr(y), x.shape[0]), "apply_transpose")
         return y
 
     def boundary_lift(self, g, f=None) -> torch.Tensor:
