@@ -1009,13 +1009,23 @@ def run_convection(args):
     f, ut = f_host.to(dev), ut_host.to(dev)
     stream = torch.cuda.current_stream(dev)
 
-    def step(fd, utd, prec=args.precision, counts=None):
+    def step(fd, utd, prec=args.precision, counts=None, pivot=args.pivot, profile=False, split=None):
         s = SlabSolver(2, n, b, inputs.CONVECTION, kappa=kappa, beta=beta, precision=prec, rtol=1e-10,
-                       max_refine=40, stream=stream, device=dev)
+                       max_refine=40, stream=stream, device=dev, pivot=pivot, profile=profile)
+        if split is not None:
+            split[1].record(stream)
         u, rel, it = s.solve(fd, allow_noconv=True)
+        if split is not None:
+            split[2].record(stream)
         lam, g = s.adjoint(2 * (u - utd), u, allow_noconv=True)
+        if split is not None:
+            split[3].record(stream)
         if counts is not None:
             counts.append(sum(s.profile_read()[1].values()))
+        if profile:
+            cls_ms, cls_cnt = s.profile_read()
+            s.close()
+            return cls_ms, cls_cnt
         s.close()
         return u, lam, g, rel, it
 
@@ -1057,6 +1067,24 @@ def run_convection(args):
         torch.cuda.synchronize()
     e2e = dist_max((time.perf_counter() - t0) / args.steps)
     sampler.stop()
+    # one step split into factor / solve / adjoint + gradient, and one with every launch timed by class
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    step(f, ut, split=ev)
+    torch.cuda.synchronize()
+    phases = {"factor": ev[0].elapsed_time(ev[1]), "solve": ev[1].elapsed_time(ev[2]),
+              "adjoint_and_gradient": ev[2].elapsed_time(ev[3])}
+    cls_ms, cls_cnt = step(f, ut, profile=True)
+    other_pivot = "local" if args.pivot == "tournament" else "tournament"
+    torch.cuda.synchronize()
+    v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    v0.record(stream)
+    _, _, _, rel_v, it_v = step(f, ut, pivot=other_pivot)
+    v1.record(stream)
+    torch.cuda.synchronize()
+    variant = {"pivot": other_pivot, "ms_per_step": v0.elapsed_time(v1), "max_relres": float(np.max(rel_v)),
+               "refine_steps": it_v}
     fp64 = None
     if args.fp64_comparator:
         torch.cuda.synchronize()
@@ -1078,8 +1106,11 @@ def run_convection(args):
         "config": {"workload": f"2D convection-diffusion n={n} b={b} k={k} (kappa=exp(16-mode field), "
                                "|beta|<=20 8-mode fields, f~N(0,1)); step = factor + solve + transposed adjoint "
                                "solve + dL/dkappa", "n": n, "b": b, "k": k, "precision": args.precision,
+                   "pivot": args.pivot,
                    "l2": "every step streams > 1 GB (>> 129 MB L2); no explicit flush"},
-        "max_relres": max(rels), "refine_steps": its, "adjoint_max_relres": adj_rel,
+        "max_relres": max(rels), "refine_steps": its, "adjoint_max_relres": adj_rel, "pivot": args.pivot,
+        "phases_ms": phases, "classes_ms": {c: round(v, 3) for c, v in cls_ms.items() if v > 0},
+        "classes_launches": {c: v for c, v in cls_cnt.items() if v > 0}, "other_pivot": variant,
         "fp64_gpu": {"value": fp64, "unit": "s"} if fp64 is not None else None,
         "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": int(2 * f_host.numel() * 8),
                 "d2h_bytes_per_step": int(u_host.numel() * 8 + g_host.numel() * 8)},
@@ -1124,6 +1155,8 @@ def main():
                          "(which decides during the warm-up steps)")
     ap.add_argument("--interface", default="default", choices=["default", "fp32", "fp64", "fp64tc", "tf32"],
                     help="precision of the interface system (fp64tc: FP64-accurate tensor-core products)")
+    ap.add_argument("--pivot", default="tournament", choices=["tournament", "local"],
+                    help="convection2048: row choice of the Gauss-Jordan interface elimination")
     ap.add_argument("--stage2", default="auto", choices=["auto", "sweep", "oddeven"],
                     help="elimination order of T (auto: odd-even for 4 or more interfaces)")
     args = ap.parse_args()

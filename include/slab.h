@@ -109,7 +109,13 @@ typedef struct {
 
 typedef struct {
     int factor_prec;        /* slab_precision */
-    int pivot;              /* reserved: 0 */
+    int pivot;              /* row choice of the interface elimination of HELMHOLTZ and CONVECTION
+                               (the Gauss-Jordan sweep): 0 = tournament pivoting over all remaining
+                               rows (default); 1 = pivot rows restricted to each 64-row diagonal
+                               block (partial pivoting inside it only), which skips the tournament and
+                               suits diagonally dominant interface systems (diffusion-dominated
+                               convection, cell Peclet number below 1).  Other values: SLAB_EINVAL;
+                               ignored by the Cholesky-based kinds */
     double rtol;            /* refinement target for max_k ||f - A u||_2 / ||f||_2 */
     int max_refine;         /* refinement steps after the first solve (0: a single pass) */
     int krylov;             /* 0: plain refinement u += A_f^{-1} (f - A u); m > 0: restarted GMRES(m)

@@ -509,6 +509,7 @@ slab_status factor_create(const slab_grid* grid, const slab_coeffs* co, int b, c
     if (o.interface_prec == SLAB_PREC_TF32) o.interface_prec = SLAB_PREC_FP32;
     if (o.stage2 < SLAB_STAGE2_AUTO || o.stage2 > SLAB_STAGE2_ODDEVEN) return SLAB_EINVAL;
     if (o.krylov < 0 || o.krylov > 200) return SLAB_EINVAL;
+    if (o.pivot < 0 || o.pivot > 1) return SLAB_EINVAL;
     int prec2 = o.interface_prec;
     if (prec2 == -1) prec2 = (co->kind == SLAB_HELMHOLTZ) ? SLAB_PREC_FP64 : o.factor_prec;
     if (prec2 != SLAB_PREC_FP32 && prec2 != SLAB_PREC_FP64) return SLAB_EINVAL;
@@ -535,6 +536,7 @@ slab_status factor_create(const slab_grid* grid, const slab_coeffs* co, int b, c
     h->rtol = o.rtol;
     h->max_refine = o.max_refine;
     h->krylov = o.krylov;
+    h->pivot_local = o.pivot == 1;
     if (o.profile) slab_profile(h, 1);
     TreeDims& d = h->td;
     d.s = n - 1;

@@ -965,12 +965,28 @@ __device__ void gj_warp_gepp(T* A, const int* rows, int nr, int* out) {
         if (lane == 0) out[j] = rows[bi];
         const T pv = A[bi * 65 + j];
         if (best > T(0)) {
+            // the pivot row in registers, the update unrolled over compile-time columns (in blocks of
+            // 8 skipped while left of j): the loads of a row are independent of its stores, so they
+            // pipeline instead of alternating load -> FMA -> store one column at a time
+            T prow[64];
+#pragma unroll
+            for (int c = 0; c < 64; ++c) prow[c] = A[bi * 65 + c];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int r = lane + 32 * q;
                 if (r < nr && !chosen[q]) {
-                    const T l = A[r * 65 + j] / pv;
-                    for (int c = j + 1; c < 64; ++c) A[r * 65 + c] -= l * A[bi * 65 + c];
+                    T* Ar = A + r * 65;
+                    const T l = Ar[j] / pv;
+#pragma unroll
+                    for (int cb = 0; cb < 8; ++cb) {
+                        if (8 * cb + 7 > j) {
+#pragma unroll
+                            for (int cc = 0; cc < 8; ++cc) {
+                                const int c = 8 * cb + cc;
+                                if (c > j) Ar[c] -= l * prow[c];
+                            }
+                        }
+                    }
                 }
             }
         }
@@ -999,16 +1015,16 @@ __global__ void __launch_bounds__(32 * GJ_WARPS) gj_tournament_kernel(const T* _
     for (int i = lane; i < nr; i += 32) rows[i] = act[node * GJ_LEAF + i];
     while (true) {
         __syncwarp();
-        // 8 loads in flight per lane (rows are scattered over G, each 64-column row segment coalesced)
-        for (int i0 = 0; i0 < nr * 64; i0 += 32 * 8) {
-            T v[8];
+        // 16 loads in flight per lane (rows are scattered over G, each 64-column row segment coalesced)
+        for (int i0 = 0; i0 < nr * 64; i0 += 32 * 16) {
+            T v[16];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
+            for (int u = 0; u < 16; ++u) {
                 const int idx = i0 + u * 32 + lane;
                 v[u] = idx < nr * 64 ? G[(int64_t)rows[idx >> 6] * ld + c0 + (idx & 63)] : T(0);
             }
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
+            for (int u = 0; u < 16; ++u) {
                 const int idx = i0 + u * 32 + lane;
                 if (idx < nr * 64) A[(idx >> 6) * 65 + (idx & 63)] = (float)v[u];
             }
@@ -1044,20 +1060,39 @@ __global__ void __launch_bounds__(32 * GJ_WARPS) gj_tournament_kernel(const T* _
     __threadfence();
     // every other warp has taken its ticket: reset them for the next panel
     for (int i = lane; i < gj_nodes(L); i += 32) w.tick[i] = 0u;
-    // remaining rows, in order
+    // remaining rows, in order: 8 groups of 32 per round, their loads issued before the ballots
     int base = 0;
-    for (int i0 = 0; i0 < nact; i0 += 32) {
-        const int i = i0 + lane;
-        int r = -1;
-        bool keep = false;
-        if (i < nact) {
-            r = act[i];
-            keep = __ldcg(w.pflag + r) != panel + 1;
+    for (int i0 = 0; i0 < nact; i0 += 32 * 8) {
+        int r[8];
+        bool keep[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = i0 + 32 * u + lane;
+            r[u] = i < nact ? act[i] : -1;
         }
-        const unsigned bal = __ballot_sync(0xffffffffu, keep);
-        if (keep) act_next[base + __popc(bal & ((1u << lane) - 1u))] = r;
-        base += __popc(bal);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) keep[u] = r[u] >= 0 && __ldcg(w.pflag + r[u]) != panel + 1;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const unsigned bal = __ballot_sync(0xffffffffu, keep[u]);
+            if (keep[u]) act_next[base + __popc(bal & ((1u << lane) - 1u))] = r[u];
+            base += __popc(bal);
+        }
     }
+}
+
+// Pivot rows restricted to the diagonal block: the panel's pivot rows are the first 64 rows not yet
+// pivoted, in order (the rows c0 .. c0+63 when every earlier panel did the same); A11's own partial
+// pivoting (gj_a11_lu_kernel) orders them.  One warp.
+__global__ void gj_local_rows_kernel(int c0, int panel, int nact, GjWork w, const int* act, int* act_next) {
+    const int lane = threadIdx.x;
+    for (int i = lane; i < 64; i += 32) {
+        const int r = act[i];
+        w.piv[i] = r;
+        w.perm[c0 + i] = r;
+        w.pflag[r] = panel + 1;
+    }
+    for (int i = 64 + lane; i < nact; i += 32) act_next[i - 64] = act[i];
 }
 
 // LU of the panel's pivot block A11 = G[piv, panel] with partial pivoting (row i of the
@@ -1366,8 +1401,11 @@ slab_status sweep_factor_indef(slab_handle* h) {
             const int L = (nact + GJ_LEAF - 1) / GJ_LEAF;
             {
                 SLAB_PROF(h, KC_PANEL);
-                gj_tournament_kernel<T><<<(L + GJ_WARPS - 1) / GJ_WARPS, 32 * GJ_WARPS, tsmem, h->stream>>>(
-                    Gt, wt, c0, kb, nact, w, act, act_next);
+                if (h->pivot_local)
+                    gj_local_rows_kernel<<<1, 32, 0, h->stream>>>(c0, kb, nact, w, act, act_next);
+                else
+                    gj_tournament_kernel<T><<<(L + GJ_WARPS - 1) / GJ_WARPS, 32 * GJ_WARPS, tsmem, h->stream>>>(
+                        Gt, wt, c0, kb, nact, w, act, act_next);
                 SLAB_CK_LAUNCH(h);
                 gj_a11_lu_kernel<T><<<1, 256, ismem, h->stream>>>(Gt, wt, c0, w.piv, A11lu, rdiag, lperm, h->dstatus);
                 SLAB_CK_LAUNCH(h);

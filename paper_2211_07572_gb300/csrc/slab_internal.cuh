@@ -97,6 +97,7 @@ struct slab_handle {
     double* AXT;              // CONVECTION: AXT[y][x] = -h^2 A[(x+1,y),(x,y)] (AX: -h^2 A[(x,y),(x+1,y)])
     double* AYT;              // CONVECTION: AYT[y][x] = -h^2 A[(x,y+1),(x,y)] (AY: -h^2 A[(x,y),(x,y+1)])
     int transposed;           // set while a solve with A^T runs (CONVECTION adjoint)
+    int pivot_local;          // Gauss-Jordan sweep: pivot rows from the diagonal 64-row block only
     const double* beta;       // CONVECTION: the caller's velocity field, set during slab_factor only
     double* AZ;               // 3-D: AZ[z][y][x]: face (x,y,z)-(x,y,z+1)
 

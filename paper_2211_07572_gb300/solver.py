@@ -43,13 +43,16 @@ class SlabSolver:
     "fp64" (plain FP64 path); stage2: "auto", "sweep" (Algorithm 1) or
     "oddeven"; interface_precision: precision of the interface system (default: "fp64" for
     Helmholtz with an FP32 factor, else the factor precision); krylov: 0 for plain iterative
-    refinement, m > 0 for restarted FP64 GMRES(m) preconditioned by the factor.
+    refinement, m > 0 for restarted FP64 GMRES(m) preconditioned by the factor; pivot: row choice of
+    the Gauss-Jordan interface elimination (Helmholtz, convection-diffusion): "tournament" over all
+    remaining rows, or "local" (inside each 64-row diagonal block, for diagonally dominant systems).
     """
 
     def __init__(self, dim: int, n: int, b: int, kind: int, kappa=None, c=None, omega: float = 0.0,
                  beta=None, precision: str = "fp32", rtol: float = 1e-10, max_refine: int = 30,
                  stream: Optional[torch.cuda.Stream] = None, device=None, profile: bool = False,
-                 stage2: str = "auto", interface_precision: Optional[str] = None, krylov: int = 0):
+                 stage2: str = "auto", interface_precision: Optional[str] = None, krylov: int = 0,
+                 pivot: str = "tournament"):
         self.lib = _lib.load()
         self.device = (torch.device(device) if device is not None
                        else torch.device("cuda", torch.cuda.current_device()))
@@ -70,6 +73,7 @@ class SlabSolver:
         opts.stage2 = _STAGE2[stage2]
         opts.interface_prec = -1 if interface_precision is None else _PREC[interface_precision]
         opts.krylov = int(krylov)
+        opts.pivot = {"tournament": 0, "local": 1}[pivot]
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             _lib.check(self.lib.slab_factor(ctypes.byref(grid), ctypes.byref(co), int(b), ctypes.byref(opts),
