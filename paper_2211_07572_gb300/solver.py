@@ -242,7 +242,7 @@ class SlabBatch:
     slab_factor_batched / slab_solve_batched / slab_adjoint_batched, each problem on a stream of
     its own, driven by up to `workers` host threads.
 
-    problems: list of dicts with keys dim, n, b, kind and kappa / c / omega as for SlabSolver.
+    problems: list of dicts with keys dim, n, b, kind and kappa / c / omega / beta as for SlabSolver.
     Vectors are lists of device tensors, one [k][N_i] tensor per problem.
     """
 
@@ -261,9 +261,10 @@ class SlabBatch:
         for i, p in enumerate(problems):
             kap = _dev(p.get("kappa"), self.device)
             cc = _dev(p.get("c"), self.device)
-            self._coef.append((kap, cc))
+            bet = _dev(p.get("beta"), self.device)
+            self._coef.append((kap, cc, bet))
             grids[i] = _lib.SlabGrid(p["dim"], p["n"])
-            coeffs[i] = _lib.SlabCoeffs(p["kind"], _ptr(kap), _ptr(cc), float(p.get("omega", 0.0)))
+            coeffs[i] = _lib.SlabCoeffs(p["kind"], _ptr(kap), _ptr(cc), float(p.get("omega", 0.0)), _ptr(bet))
             bs[i] = p["b"]
             self.meta.append((p["dim"], p["n"]))
         opts = _lib.SlabOpts()
