@@ -77,7 +77,7 @@ typedef enum {
  * ODDEVEN: the odd-even order the paper names as the more parallel alternative
  * (Sec. 4 remark on the elimination order; conclusion): log2(N_I) levels, each
  * eliminating every other remaining block in one batch; Cholesky based, so POISSON
- * and DIFFUSION only (SLAB_EUNSUPPORTED for HELMHOLTZ).  It holds about 9 s_pad^2
+ * and DIFFUSION only (SLAB_EUNSUPPORTED for HELMHOLTZ and CONVECTION).  It holds about 9 s_pad^2
  * numbers per interface in the factor versus about 5 for SWEEP.
  * ODDEVEN does about 4x the dense flops of SWEEP but in log2(N_I) batched levels, which pays
  * on the tensor-core (FP32) path; on the SIMT FP64 path SWEEP is faster.
@@ -147,12 +147,14 @@ void slab_default_opts(slab_opts* opts);
  * Requires dim 2 or 3, b >= 2, n % b == 0 and n/b >= 2 (SLAB_EINVAL otherwise).  In 2-D the slab
  * interior width b - 1 is at most 32 (SLAB_EUNSUPPORTED otherwise); HELMHOLTZ or CONVECTION in 3-D,
  * and SLAB_STAGE2_ODDEVEN with HELMHOLTZ or CONVECTION, are SLAB_EUNSUPPORTED.  POISSON and DIFFUSION are factored by
- * Cholesky (slab separators and Stage 2); HELMHOLTZ (indefinite) by Gauss-Jordan
- * with partial pivoting in the slab separators, and in Stage 2 (Algorithm 1 as printed) by a
- * blocked Gauss-Jordan elimination of [S_j | T_{j,j+1} | I] with tournament pivoting
- * (64-column panels; each panel's pivot rows are the winners of pairwise partial-pivoting
- * eliminations over groups of 128 candidate rows), in opts.factor_prec.  A zero / non-positive pivot
- * returns SLAB_ESINGULAR.  kappa/c are read during the call only.  On success
+ * Cholesky (slab separators and Stage 2); HELMHOLTZ (indefinite) and CONVECTION (nonsymmetric) by
+ * Gauss-Jordan with partial pivoting in the slab separators, and in Stage 2 (Algorithm 1 as printed)
+ * by a blocked Gauss-Jordan elimination of [S_j | T_{j,j+1} | I] over [T_{j+1,j} | T_{j+1,j+1}] with
+ * tournament pivoting (64-column panels; each panel's pivot rows are the winners of pairwise
+ * partial-pivoting eliminations over groups of 128 candidate rows; opts.pivot = 1 takes them from the
+ * diagonal block instead), in opts.factor_prec.  CONVECTION keeps both orientations of every slab
+ * coupling so that the same factors also solve with A^T (slab_adjoint).  A zero / non-positive pivot
+ * returns SLAB_ESINGULAR.  kappa/c/beta are read during the call only.  On success
  * *out is a new handle.  Synchronises opts->stream (returns after the factor).
  */
 slab_status slab_factor(const slab_grid* grid, const slab_coeffs* coeffs, int b,
@@ -395,7 +397,8 @@ const char* slab_strerror(slab_status s);
  * stay free of allocation nodes, a process whose device memory pool belongs to
  * another framework, a real-time loop that bans allocator calls.  This entry
  * point allocates nothing and needs no handle: for the 2-D grid n (h = 1/n)
- * and the operator given by kind/kappa/c/omega (as in slab_coeffs), it writes
+ * and the operator given by kind/kappa/c/omega (as in slab_coeffs; POISSON, DIFFUSION or HELMHOLTZ,
+ * SLAB_EINVAL for CONVECTION), it writes
  * r = f - A u (device, [k][(n-1)^2]) and the squared 2-norms nrm_r[q] =
  * ||r_q||^2, nrm_f[q] = ||f_q||^2 (device, k entries each), on the given
  * stream (a cudaStream_t, NULL = legacy default).  All buffers are the
