@@ -24,6 +24,8 @@ Contents
     lam solving A^T lam = dL/du (``adjoint_gradient``: a banded LU of the transposed matrix for
     the nonsymmetric convection kind).
   * ``boundary_lift``: non-zero Dirichlet data moved into the load of the interior system.
+  * ``recovery`` (submodule): randomized recovery of a rank-structured block of T from products
+    with it and its transpose (Sec. 3.3), as a HODLR matrix by the peeling scheme.
 
 Readings of the paper used here (the paper is silent or garbled on these):
   b is the interface spacing (interfaces at x = q b, slab interiors b-1 wide);
