@@ -599,7 +599,7 @@ def run_gpu(args):
         ("assemble_T", "tree_up", "tree_down", "slab_trailing", "slab_schur") if dim == 3 else ())
     dense = {c: roofline_for(c, cls_ms[c], cls_cnt[c], work, peaks, clocks, bmap)
              for c in dense_cls if cls_ms.get(c, 0) > 0}
-    # Stage 2 against the survey's count: Algorithm 1 in Cholesky form on the unpadded blocks, over
+    # Stage 2 against the algorithmic count of Algorithm 1 in Cholesky form on the unpadded blocks, over
     # the measured time of every Stage-2 factor class (panels, trailing and Schur updates)
     si = (n - 1) ** (dim - 1)
     s2_ms = sum(cls_ms.get(c, 0.0) for c in ("panel", "trailing", "schur_update"))
