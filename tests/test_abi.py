@@ -44,6 +44,34 @@ def test_argument_validation_needs_no_gpu():
     o = _lib.SlabOpts()
     lib.slab_default_opts(ctypes.byref(o))
     assert o.factor_prec == _lib.PREC_FP32 and o.rtol == 1e-10 and o.max_refine == 30
+    assert o.pivot == 0
+
+
+def test_convection_argument_validation_needs_no_gpu():
+    """The nonsymmetric kind's checks all come before any device call (the pointers below are
+    never dereferenced on the host)."""
+    from paper_2211_07572_gb300 import _lib
+    lib = _lib.load()
+    h = ctypes.c_void_p()
+    dummy = ctypes.c_void_p(256)
+    g2, g3 = _lib.SlabGrid(2, 64), _lib.SlabGrid(3, 16)
+    args = lambda g, co, b, o=None: (ctypes.byref(g), ctypes.byref(co), b, o, ctypes.byref(h))
+    no_beta = _lib.SlabCoeffs(_lib.CONVECTION, dummy, None, 0.0, None)
+    no_kappa = _lib.SlabCoeffs(_lib.CONVECTION, None, None, 0.0, dummy)
+    full = _lib.SlabCoeffs(_lib.CONVECTION, dummy, None, 0.0, dummy)
+    assert lib.slab_factor(*args(g2, no_beta, 8)) == _lib.SLAB_EINVAL
+    assert lib.slab_factor(*args(g2, no_kappa, 8)) == _lib.SLAB_EINVAL
+    assert lib.slab_factor(*args(g3, full, 4)) == _lib.SLAB_EUNSUPPORTED          # 2-D only
+    o = _lib.SlabOpts()
+    lib.slab_default_opts(ctypes.byref(o))
+    o.stage2 = 2                                                               # odd-even: Cholesky based
+    assert lib.slab_factor(*args(g2, full, 8, ctypes.byref(o))) == _lib.SLAB_EUNSUPPORTED
+    lib.slab_default_opts(ctypes.byref(o))
+    o.pivot = 2
+    assert lib.slab_factor(*args(g2, full, 8, ctypes.byref(o))) == _lib.SLAB_EINVAL
+    bad_kind = _lib.SlabCoeffs(4, dummy, None, 0.0, dummy)
+    assert lib.slab_factor(*args(g2, bad_kind, 8)) == _lib.SLAB_EINVAL
+    assert lib.slab_apply_transpose(None, None, None, 1) == _lib.SLAB_EINVAL
 
 
 def test_product_path_has_no_oracle_or_cpu_fallback():
