@@ -140,3 +140,18 @@ def test_gradient_matches_central_differences(oracle_mod):
     fd, ad, wr = np.array(fd), np.array(ad), np.array(wr)
     assert np.linalg.norm(fd - ad) / np.linalg.norm(fd) < 1e-6
     assert np.linalg.norm(fd - wr) / np.linalg.norm(fd) > 1e-3
+
+
+def test_convection_inputs_follow_the_recipe():
+    """Seeded: the same call twice gives the same fields; kappa = exp(unit-variance field) > 0;
+    each velocity component reaches the stated speed in max-abs; loads have the stated shape."""
+    p = inputs.convection(48, 8, 3, speed=20.0)
+    q = inputs.convection(48, 8, 3, speed=20.0)
+    np.testing.assert_array_equal(p.beta, q.beta)
+    np.testing.assert_array_equal(p.kappa, q.kappa)
+    np.testing.assert_array_equal(p.f, q.f)
+    assert p.beta.shape == (2, 49, 49) and p.f.shape == (3, 47 * 47)
+    assert (p.kappa > 0).all() and abs(np.log(p.kappa).std() - 1) < 1e-12
+    for a in range(2):
+        assert abs(np.abs(p.beta[a]).max() - 20.0) < 1e-12
+    assert not np.array_equal(p.beta[0], p.beta[1])
