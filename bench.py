@@ -695,22 +695,31 @@ def fp64_comparator(make64, f):
 def cpu_sample(n_full, b, k, n_sample, kind="diffusion"):
     """One oracle run (banded LU, FP64) on a bounded sample of the workload: n = n_sample, same b and
     k loads, extrapolated to n_full by the banded-LU cost model (factor ~ N w^2, solve ~ k N w with
-    N = n^d, w = n^(d-1)).  The Helmholtz sample keeps 10 points per wavelength and pivots."""
+    N = n^d, w = n^(d-1)).  The Helmholtz sample keeps 10 points per wavelength and pivots.  The
+    convection sample pivots and, like that workload's step, also factors A^T and solves the adjoint
+    system (load 2 (u - u_t))."""
     import oracle
     from paper_2211_07572_gb300 import inputs
     oracle.build()
     dim = 3 if kind == "diffusion3d" else 2
     if kind == "helmholtz":
         p = inputs.helmholtz(n_sample, b, dim=2, n_modes=8, field_seed=3)
+    elif kind == "convection":
+        p = inputs.convection(n_sample, b, k)
     elif dim == 3:
         p = inputs.diffusion(n_sample, b, k=k, dim=3, n_modes=8, field_seed=4, rhs_seed=104)
     else:
         p = inputs.diffusion(n_sample, b, k=k, n_modes=16, field_seed=2, rhs_seed=102)
+    piv = kind in ("helmholtz", "convection")
+    w = (n_sample - 1) ** (dim - 1)
     t0 = time.perf_counter()
     A = oracle.assemble_problem(p)
-    lu = oracle.BandLU(A, (n_sample - 1) ** (dim - 1), pivot=kind == "helmholtz")
+    lu = oracle.BandLU(A, w, pivot=piv)
+    lut = oracle.BandLU(A.transpose(), w, pivot=piv) if kind == "convection" else None
     t1 = time.perf_counter()
     u = lu.solve(p.f)
+    if lut is not None:
+        lut.solve(2.0 * (u - inputs.normal_rhs(2, n_sample, p.f.shape[0], 107)))
     t2 = time.perf_counter()
     rr = float(oracle.relres(A, u, p.f).max())
     scale = n_full / n_sample
@@ -1096,6 +1105,10 @@ def run_convection(args):
         fp64 = dist_max(a0.elapsed_time(a1)) / 1e3
     if rank != 0:
         return
+    cpu = None
+    if args.cpu_baseline and world == 1:
+        restore_host_affinity()                                  # the CPU baseline uses every core
+        cpu = cpu_baseline(n, b, k, kind="convection", rungs=((128, 2), (256, 2)))
     print(json.dumps({
         "metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
@@ -1112,6 +1125,7 @@ def run_convection(args):
         "phases_ms": phases, "classes_ms": {c: round(v, 3) for c, v in cls_ms.items() if v > 0},
         "classes_launches": {c: v for c, v in cls_cnt.items() if v > 0}, "other_pivot": variant,
         "fp64_gpu": {"value": fp64, "unit": "s"} if fp64 is not None else None,
+        "cpu_baseline": cpu,
         "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": int(2 * f_host.numel() * 8),
                 "d2h_bytes_per_step": int(u_host.numel() * 8 + g_host.numel() * 8)},
         "gpu_launches": launches[-1] if launches else None,
