@@ -214,6 +214,28 @@ def test_larger_grid_matches_oracle():
     assert (np.linalg.norm(u - u_o, axis=1) / np.linalg.norm(u_o, axis=1)).max() <= 1e-8
 
 
+def test_full_size_residuals_by_the_oracle():
+    """The benchmark's configuration (n = 2048, b = 32, 16 loads), beyond the oracle's banded LU:
+    the relative residuals of u (with A) and of the adjoint lambda (with A^T) on sampled loads,
+    computed by the oracle's own CSR assembly, transpose and matvec, are <= 1e-10."""
+    from paper_2211_07572_gb300.solver import SlabSolver
+    n, b, k = 2048, 32, 16
+    p = inputs.convection(n, b, k)
+    ut = inputs.normal_rhs(2, n, k, 107)
+    s = SlabSolver(2, n, b, CONV, kappa=p.kappa, beta=p.beta, rtol=1e-10, max_refine=40)
+    u, rel, _ = s.solve(_cuda(p.f))
+    g = 2 * (u - _cuda(ut))
+    lam, _ = s.adjoint(g)
+    s.close()
+    idx = [0, k // 2, k - 1]
+    us, ls, gs = u[idx].cpu().numpy(), lam[idx].cpu().numpy(), g[idx].cpu().numpy()
+    del u, lam, g
+    assert np.max(rel) <= 1e-10
+    A = oracle.assemble_problem(p)
+    assert oracle.relres(A, us, p.f[idx]).max() <= 1e-10
+    assert oracle.relres(A.transpose(), ls, gs).max() <= 1e-10
+
+
 def test_unsupported_and_invalid():
     from paper_2211_07572_gb300 import _lib
     from paper_2211_07572_gb300.solver import SlabSolver
