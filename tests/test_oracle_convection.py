@@ -155,3 +155,28 @@ def test_convection_inputs_follow_the_recipe():
     for a in range(2):
         assert abs(np.abs(p.beta[a]).max() - 20.0) < 1e-12
     assert not np.array_equal(p.beta[0], p.beta[1])
+
+
+def test_zero_velocity_is_the_diffusion_operator(oracle_mod):
+    p = _problem(2, 12, 4)
+    A0 = oracle_mod.assemble(2, 12, CONV, kappa=p.kappa, beta=np.zeros_like(p.beta)).dense()
+    Ad = oracle_mod.assemble(2, 12, inputs.DIFFUSION, kappa=p.kappa).dense()
+    np.testing.assert_array_equal(A0, Ad)
+
+
+def test_constant_coefficients_are_a_kronecker_sum(oracle_mod):
+    """kappa = 1, constant beta: A = I (x) T_x + T_y (x) I with the 1-D central-difference matrices
+    T_a = h^-2 tridiag(-1 - beta_a h/2, 2, -1 + beta_a h/2) (sub, diagonal, super; x fastest)."""
+    n, bx, by = 10, 7.0, -3.0
+    h = 1.0 / n
+    beta = np.stack([np.full((n + 1, n + 1), bx), np.full((n + 1, n + 1), by)])
+    A = oracle_mod.assemble(2, n, CONV, kappa=np.ones((n + 1, n + 1)), beta=beta).dense()
+
+    def t1(b):
+        m = n - 1
+        return (np.diag(np.full(m, 2.0)) + np.diag(np.full(m - 1, -1.0 + b * h / 2), 1)
+                + np.diag(np.full(m - 1, -1.0 - b * h / 2), -1)) / h ** 2
+
+    I = np.eye(n - 1)
+    K = np.kron(I, t1(bx)) + np.kron(t1(by), I)
+    np.testing.assert_allclose(A, K, rtol=0, atol=1e-12 * np.abs(K).max())
